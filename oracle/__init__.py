@@ -1,0 +1,194 @@
+"""FP64 CPU oracle of the EMDQ field + mosaic path (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package.  The product library never does; it and this oracle share no code.
+The arithmetic lives in ``emdq_oracle.c`` (plain C, double precision, optional OpenMP
+over pixels as the paper's CPU path uses); this module only builds and marshals.
+
+Parity status: every routine here is pinned by ``tests/test_oracle_*.py`` against closed
+forms, an independent 8-D dual-quaternion implementation, an SVD solution of the rotation
+fit, brute force on tiny inputs and statistical recovery of a known field.  The EM loop
+as a whole follows a reading of an algorithm the paper delegates to its EMDQ reference;
+its invariants are pinned, its agreement with that reference is not (parity unpinned
+against the original EMDQ).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, 'emdq_oracle.c')
+_LIB_PATH = os.path.join(_HERE, 'liboracle.so')
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, EDEGENERATE, ENOCONV = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile emdq_oracle.c into liboracle.so (OpenMP when the compiler has it)."""
+    if not force and os.path.exists(_LIB_PATH) and \
+            os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+                                               os.path.getmtime(os.path.join(_HERE, 'emdq_oracle.h'))):
+        return _LIB_PATH
+    base = ['gcc', '-O2', '-std=c11', '-fPIC', '-shared', '-ffp-contract=off',
+            '-fno-fast-math', _SRC, '-o', _LIB_PATH + '.tmp', '-lm']
+    try:
+        subprocess.run(base[:1] + ['-fopenmp'] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_LIB_PATH + '.tmp', _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [('alpha', ctypes.c_double), ('max_iters', ctypes.c_int),
+                ('tol_p', ctypes.c_double), ('sigma2_floor', ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            D, I = ctypes.c_double, ctypes.c_int
+            L.orc_alpha_for_frame.restype = D
+            L.orc_alpha_for_frame.argtypes = [I, I]
+            L.orc_dq_from_rt.argtypes = [D, D, D, P]
+            L.orc_rt_from_dq.argtypes = [P, P, P, P]
+            L.orc_apply_warp.argtypes = [D, P, D, D, P]
+            L.orc_field.argtypes = [P, P, P, I, I, I, I, I, D, P, I]
+            L.orc_field_points.argtypes = [P, P, P, I, P, I, D, P, I]
+            L.orc_mstep.argtypes = [P, P, P, I, D, P, P, P, P]
+            L.orc_residuals.argtypes = [P, P, P, P, I, D, P]
+            L.orc_fit.argtypes = [P, P, I, I, I, ctypes.POINTER(_Params), P, P, P, P, P, P, P, P]
+            L.orc_warp.argtypes = [P, I, I, I, I, P, I, I, I, I, P, I, I, I, I, I]
+            L.orc_insert_reference.argtypes = [P, I, I, I, I, P, I, I, I, I, I]
+            L.orc_max_threads.restype = I
+            _lib = L
+    return _lib
+
+
+def _d(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _p(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def max_threads() -> int:
+    return lib().orc_max_threads()
+
+
+def alpha_for_frame(w: int, h: int) -> float:
+    return lib().orc_alpha_for_frame(int(w), int(h))
+
+
+def dq_from_rt(th: float, tx: float, ty: float) -> np.ndarray:
+    q = np.zeros(4)
+    lib().orc_dq_from_rt(float(th), float(tx), float(ty), _p(q))
+    return q
+
+
+def rt_from_dq(q) -> tuple[float, float, float]:
+    q = _d(q, (4,))
+    out = [ctypes.c_double() for _ in range(3)]
+    lib().orc_rt_from_dq(_p(q), *[ctypes.cast(ctypes.pointer(o), ctypes.c_void_p) for o in out])
+    return tuple(o.value for o in out)
+
+
+def apply_warp(s: float, q, px: float, py: float) -> np.ndarray:
+    q = _d(q, (4,))
+    out = np.zeros(2)
+    lib().orc_apply_warp(float(s), _p(q), float(px), float(py), _p(out))
+    return out
+
+
+def field(q8, c, src, grid, alpha: float, nthreads: int = 0) -> np.ndarray:
+    """Dense field on grid=(x0, y0, w, h); returns [h, w, 2] float64."""
+    q8, c, src = _d(q8), _d(c), _d(src)
+    n = c.shape[0]
+    x0, y0, gw, gh = (int(v) for v in grid)
+    out = np.empty((gh, gw, 2))
+    rc = lib().orc_field(_p(q8), _p(c), _p(src), n, x0, y0, gw, gh, float(alpha), _p(out),
+                         nthreads or max_threads())
+    assert rc == OK, rc
+    return out
+
+
+def field_points(q8, c, src, pts, alpha: float, nthreads: int = 0) -> np.ndarray:
+    q8, c, src, pts = _d(q8), _d(c), _d(src), _d(pts)
+    out = np.empty((pts.shape[0], 2))
+    rc = lib().orc_field_points(_p(q8), _p(c), _p(src), c.shape[0], _p(pts), pts.shape[0],
+                                float(alpha), _p(out), nthreads or max_threads())
+    assert rc == OK, rc
+    return out
+
+
+def mstep(src, dst, p, alpha: float):
+    src, dst, p = _d(src), _d(dst), _d(p)
+    n = p.shape[0]
+    s, th, t, q8 = np.empty(n), np.empty(n), np.empty((n, 2)), np.empty((n, 8))
+    rc = lib().orc_mstep(_p(src), _p(dst), _p(p), n, float(alpha), _p(s), _p(th), _p(t), _p(q8))
+    return dict(s=s, theta=th, t=t, q8=q8, status=rc)
+
+
+def residuals(src, dst, p, q8, alpha: float) -> np.ndarray:
+    src, dst, p, q8 = _d(src), _d(dst), _d(p), _d(q8)
+    e = np.empty(p.shape[0])
+    rc = lib().orc_residuals(_p(src), _p(dst), _p(p), _p(q8), p.shape[0], float(alpha), _p(e))
+    assert rc == OK, rc
+    return e
+
+
+def fit(src, dst, frame_w: int, frame_h: int, alpha: float = 0.0, max_iters: int = 20,
+        tol_p: float = 1e-3, sigma2_floor: float = 0.25, p0=None) -> dict:
+    src, dst = _d(src), _d(dst)
+    n = src.shape[0]
+    prm = _Params(float(alpha), int(max_iters), float(tol_p), float(sigma2_floor))
+    q8, c, p = np.empty((n, 8)), np.empty(n), np.empty(n)
+    trace = np.full(max(1, max_iters), np.nan)
+    iters, s2, g = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    p0a = _d(p0) if p0 is not None else None
+    rc = lib().orc_fit(_p(src), _p(dst), n, int(frame_w), int(frame_h), ctypes.byref(prm),
+                       _p(p0a) if p0a is not None else None, _p(q8), _p(c), _p(p),
+                       ctypes.cast(ctypes.byref(iters), ctypes.c_void_p),
+                       ctypes.cast(ctypes.byref(s2), ctypes.c_void_p),
+                       ctypes.cast(ctypes.byref(g), ctypes.c_void_p), _p(trace))
+    return dict(q8=q8, c=c, p=p, iters=iters.value, sigma2=s2.value, gamma=g.value,
+                dp_trace=trace[:iters.value].copy(), status=rc)
+
+
+def warp(frame: np.ndarray, disp: np.ndarray, grid, canvas: np.ndarray, origin) -> int:
+    """Blend one frame into canvas (uint8 [CH, CW, 4], modified in place)."""
+    frame = np.ascontiguousarray(frame, dtype=np.uint8)
+    if frame.ndim == 2:
+        frame = frame[:, :, None]
+    fh, fw, ch = frame.shape
+    disp = np.ascontiguousarray(disp, dtype=np.float32)
+    assert canvas.dtype == np.uint8 and canvas.flags.c_contiguous and canvas.shape[2] == 4
+    x0, y0, gw, gh = (int(v) for v in grid)
+    return lib().orc_warp(_p(frame), fw, fh, ch, fw * ch, _p(disp), x0, y0, gw, gh,
+                          _p(canvas), canvas.shape[1], canvas.shape[0], canvas.shape[1] * 4,
+                          int(origin[0]), int(origin[1]))
+
+
+def insert_reference(frame: np.ndarray, canvas: np.ndarray, origin) -> int:
+    frame = np.ascontiguousarray(frame, dtype=np.uint8)
+    if frame.ndim == 2:
+        frame = frame[:, :, None]
+    fh, fw, ch = frame.shape
+    return lib().orc_insert_reference(_p(frame), fw, fh, ch, fw * ch, _p(canvas),
+                                      canvas.shape[1], canvas.shape[0], canvas.shape[1] * 4,
+                                      int(origin[0]), int(origin[1]))

@@ -1,0 +1,99 @@
+/*
+ * FP64 CPU oracle for the EMDQ field + mosaic path of "Real-time Nonrigid Mosaicking of
+ * Laparoscopy Images" (Zhou & Jayender).  TEST INFRASTRUCTURE ONLY: it is the judge the
+ * CUDA path is checked against and the timed CPU baseline.  Only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg may load it; the product library never does,
+ * and the two share no code.
+ *
+ * Every routine is the plain definition written out, in double precision, following the
+ * paper's equations; where the paper is silent the reading is stated beside the code.
+ *
+ * Conventions
+ *   - Pixel coordinates, origin at the centre of reference pixel (0,0), x right, y down.
+ *   - A warp function (Eq. 1) is a scale s and a planar dual quaternion q.  The planar DQ
+ *     keeps the 4 non-zero components of the 8-D DQ (Sec. III footnote):
+ *       q = (r_w, r_z, d_x, d_y),  r = (cos th/2, 0, 0, sin th/2),  d = 1/2 t^ (x) r.
+ *   - Per-match rows are stored as 8 doubles: (r_w, r_z, d_x, d_y, s, 1, 0, 0).
+ *   - Canvas pixels are 4 bytes (c0, c1, c2, weight); grey frames use c0 only.
+ */
+#ifndef EMDQ_ORACLE_H
+#define EMDQ_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_EDEGENERATE = 2, ORC_ENOCONV = 3 };
+
+typedef struct {
+    double alpha;         /* Gaussian coefficient of Eq. 4; <= 0 -> derived (Sec. III-G) */
+    int    max_iters;     /* EM iteration cap (reading: 20) */
+    double tol_p;         /* stop when max_j |dp_j| < tol_p (reading: 1e-3) */
+    double sigma2_floor;  /* lower bound of the residual variance (reading: 0.25 px^2) */
+} orc_params;
+
+/* Sec. III-G: alpha = 2e-4 / s^2 with s = (w/480 + h/270)/2. */
+double orc_alpha_for_frame(int w, int h);
+
+/* Eq. 1 + footnote: planar DQ of the rigid part (R(th), t); inverse of the same. */
+void orc_dq_from_rt(double th, double tx, double ty, double q[4]);
+void orc_rt_from_dq(const double q[4], double *th, double *tx, double *ty);
+
+/* Apply a (not necessarily unit) blended warp (s, q) to point p: normalise q by the norm
+ * of its real part, recover (R, t), return s (R p + t).  Eq. 1 with Kavan-style DQB. */
+void orc_apply_warp(double s, const double q[4], double px, double py, double out[2]);
+
+/* Eqs. 2-4: dense displacement field on the grid [gx0, gx0+gw) x [gy0, gy0+gh).
+ * q8: n rows of 8 (r_w, r_z, d_x, d_y, s, ...), c: per-match weight, src: n x 2 reference
+ * positions.  disp: gh*gw*2 (dx, dy) row-major; NaN where sum of weights is 0. */
+int orc_field(const double *q8, const double *c, const double *src, int n,
+              int gx0, int gy0, int gw, int gh, double alpha, double *disp, int nthreads);
+
+/* Same at arbitrary points pts (npts x 2). */
+int orc_field_points(const double *q8, const double *c, const double *src, int n,
+                     const double *pts, int npts, double alpha, double *disp, int nthreads);
+
+/* EM M-step (reading of Eqs. 16-20): per match i, the p-weighted Gaussian similarity fit of
+ * all matches j (including i).  Writes s[n], th[n], t[n*2] and q8[n*8].  Returns
+ * ORC_EDEGENERATE if some row has no weight or no spread. */
+int orc_mstep(const double *src, const double *dst, const double *p, int n, double alpha,
+              double *s, double *th, double *t, double *q8);
+
+/* EM leave-one-out residuals: e_j = |y_j - W_{-j}(x_j)|^2 where W_{-j} blends the warps of
+ * all i != j with weights p_i exp(-alpha |x_i - x_j|^2).  e_j = +inf when that weight sum
+ * is 0. */
+int orc_residuals(const double *src, const double *dst, const double *p, const double *q8,
+                  int n, double alpha, double *e);
+
+/* Full EMDQ fit (reading of the absent EM definition, see header of emdq_oracle.c).
+ * p0: initial inlier weights or NULL (all ones).  Outputs: q8 (n*8), c (n), p (n),
+ * *iters, *sigma2, *gamma; dp_trace (max_iters doubles, may be NULL) receives max|dp|
+ * of every iteration.  Returns ORC_OK, ORC_ENOCONV (cap reached, outputs valid),
+ * ORC_EDEGENERATE or ORC_EINVAL. */
+int orc_fit(const double *src, const double *dst, int n, int frame_w, int frame_h,
+            const orc_params *prm, const double *p0, double *q8, double *c, double *p,
+            int *iters, double *sigma2, double *gamma, double *dp_trace);
+
+/* Eqs. 23-24 as read: gather warp + capped running-average blend of one frame into the
+ * canvas over the window [gx0, gx0+gw) x [gy0, gy0+gh) of reference coordinates.
+ * Canvas pixel of reference p is p + (ox, oy).  disp: gh*gw*2 float32 (the field as the
+ * GPU stores it).  The sample position u = p + d is formed in float32 (the coverage and
+ * tap decisions are integer decisions taken in the kernel's precision); interpolation and
+ * blending are FP64. */
+int orc_warp(const uint8_t *frame, int fw, int fh, int channels, int frame_pitch,
+             const float *disp, int gx0, int gy0, int gw, int gh,
+             uint8_t *canvas, int cw, int chh, int canvas_pitch, int ox, int oy);
+
+/* Insert the reference frame at the canvas origin with weight 1 (Sec. III-F). */
+int orc_insert_reference(const uint8_t *frame, int fw, int fh, int channels, int frame_pitch,
+                         uint8_t *canvas, int cw, int chh, int canvas_pitch, int ox, int oy);
+
+/* Threads the OpenMP build uses (1 without OpenMP). */
+int orc_max_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
