@@ -189,3 +189,26 @@ def test_fit_iteration_cap_and_bad_input(orc):
     r = orc.fit(x, y, 640, 480, max_iters=4, tol_p=0.0)  # tol 0: always the full count
     assert r['iters'] == 4 and r['status'] == 3
     assert orc.fit(x[:2], y[:2], 640, 480)['status'] == 1   # EINVAL, n < 3
+
+
+def test_first_posterior_is_the_gaussian_uniform_mixture(orc):
+    """One EM iteration: the posterior of each match under a 2-D isotropic Gaussian inlier
+    density (scipy) against a uniform outlier density over the frame, with the step-0
+    residuals, sigma^2 and the initial mixing weight 1/2."""
+    from scipy.stats import multivariate_normal
+    sc = make_scene(4, 640, 480, 1)
+    x, y, _ = make_matches(sc, 1, 120, 0.25, 1.0)
+    alpha = orc.alpha_for_frame(640, 480)
+    p1 = np.ones(120)
+    m = orc.mstep(x, y, p1, alpha)
+    e0 = orc.residuals(x, y, p1, m['q8'], alpha)
+    s2 = max(e0.sum() / (2 * 120), 0.25)
+    r = orc.fit(x, y, 640, 480, max_iters=1)
+    # residual vectors: only their length enters an isotropic density
+    g = multivariate_normal(mean=[0, 0], cov=s2 * np.eye(2)).pdf(
+        np.stack([np.sqrt(e0), np.zeros(120)], 1))
+    want = 0.5 * g / (0.5 * g + 0.5 / (640 * 480))
+    np.testing.assert_allclose(r['p'], want, rtol=1e-10, atol=1e-300)
+    assert r['dp_trace'][0] == pytest.approx(np.abs(want - 1).max(), rel=1e-10)
+    # inlier weights of the output: the matches with posterior >= 1/2 keep it, others 0
+    np.testing.assert_array_equal(r['c'], np.where(r['p'] >= 0.5, r['p'], 0.0))
