@@ -1,0 +1,172 @@
+/*
+ * libemdq -- C ABI of the GB300 (sm_103a) EMDQ dense deformation field and mosaic warp of
+ * "Real-time Nonrigid Mosaicking of Laparoscopy Images" (Zhou & Jayender).
+ *
+ * The three calls of the hot path, in the order a frame uses them:
+ *   emdq_fit     feature matches -> per-match warp functions (scale + planar dual
+ *                quaternion) and inlier weights                         (Sec. II, Eqs. 16-20)
+ *   emdq_field   per-match warps -> dense displacement on a pixel grid   (Eqs. 1-4)
+ *   mosaic_warp  frame + displacement -> blended into the mosaic canvas  (Sec. III-F, Eqs. 23-24)
+ *
+ * Common rules
+ *   - Pointers documented "device" must be CUDA device (or managed) memory on the current
+ *     device; "host" pointers are ordinary host memory.  The caller owns every buffer; the
+ *     library never frees caller memory.  Scratch memory the kernels need is passed in as
+ *     a caller-allocated workspace whose size the matching *_workspace_size() returns.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream).  The return value reports argument errors and launch failures only;
+ *     errors found on the device (non-finite input, degenerate fit, iteration cap, a
+ *     bounded wait that gave up) are written to the device-side info record of the call
+ *     and are visible after the stream is synchronised.
+ *   - Coordinates are pixels with the origin at the centre of reference pixel (0, 0),
+ *     x to the right, y down.  Points are stored as interleaved float pairs (x, y).
+ *   - Warp rows are 8 floats: (r_w, r_z, d_x, d_y, s, 1, 0, 0) -- the real part
+ *     (cos th/2, sin th/2), the dual part 1/2 t^ r reduced to its two non-zero components
+ *     (the footnote to Eq. 1), the scale s of Eq. 1, a constant 1 and two zeros.
+ *   - Canvas pixels are 4 bytes (c0, c1, c2, w): colour, and the merge weight of Eq. 24.
+ *     Grey frames use c0 only.
+ *
+ * Thread safety: calls on different streams with disjoint outputs and workspaces may run
+ * concurrently.  A workspace must not be shared by two calls in flight.
+ */
+#ifndef EMDQ_H
+#define EMDQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EMDQ_ABI_VERSION 1
+
+typedef enum {
+    EMDQ_OK = 0,
+    EMDQ_EINVAL = 1,       /* bad argument: null pointer, size, layout, window off-canvas */
+    EMDQ_EDEGENERATE = 2,  /* a fit row had no weight or no spread; no inlier weight left */
+    EMDQ_ENOCONV = 3,      /* EM reached max_iters before max|dp| < tol_p; outputs valid */
+    EMDQ_ETIMEOUT = 4,     /* a bounded device-side wait gave up (kernel returned early) */
+    EMDQ_ECUDA = 5,        /* a CUDA runtime call failed (launch, attribute, memset) */
+    EMDQ_EWORKSPACE = 6,   /* workspace null or smaller than *_workspace_size() */
+    EMDQ_ENOTSUP = 7,      /* precision, size or device not supported by this build */
+    EMDQ_ENONFINITE = 8    /* an input coordinate is NaN or infinite */
+} emdq_status;
+
+/* Field precisions. */
+enum {
+    EMDQ_FP32 = 0,  /* per-pixel direct sum on the CUDA cores, FP32 (the plain path) */
+    EMDQ_BF16 = 1   /* separable Gaussian as tcgen05 GEMMs: BF16 operands, FP32 accumulate */
+};
+
+typedef struct {
+    float alpha;         /* Eq. 4 coefficient (1/H^2); <= 0: derived from the frame size by
+                            the rule of Sec. III-G, 2e-4 / s^2, s = (w/480 + h/270)/2 */
+    int   max_iters;     /* EM iteration cap (default 20) */
+    float tol_p;         /* EM stops when max_j |p_j - p_j,prev| < tol_p (default 1e-3) */
+    float sigma2_floor;  /* lower bound of the residual variance, px^2 (default 0.25) */
+    int   reserved[4];   /* zero */
+} emdq_params;
+
+/* Device-side record a fit writes when it finishes (16 bytes, 4-byte aligned). */
+typedef struct {
+    int   status;        /* emdq_status of the device part of the fit */
+    int   iters;         /* EM iterations run after step 0 */
+    float sigma2;        /* final residual variance */
+    float gamma;         /* final inlier fraction (mixing weight) */
+} emdq_fit_info;
+
+void        emdq_default_params(emdq_params *prm);
+/* Sec. III-G: alpha for a w x h frame. */
+float       emdq_alpha_for_frame(int w, int h);
+const char *emdq_status_string(int status);
+int         emdq_abi_version(void);
+
+/* ------------------------------------------------------------------ emdq_fit ---------
+ * EMDQ mismatch removal and per-match warp estimation (Sec. II: "the input of EMDQ is the
+ * coordinates of image feature matches").  The paper delegates the EM iteration to its
+ * EMDQ reference; this library implements the reading documented with the oracle:
+ *   step 0    p = p0 (or 1); M-step; leave-one-out residuals; sigma^2; gamma = 1/2
+ *   iterate   E-step: p_j = gamma G_j / (gamma G_j + (1-gamma)/(w h)),
+ *               G_j = exp(-e_j / (2 sigma^2)) / (2 pi sigma^2)
+ *             M-step: per match i the closed-form similarity of Eqs. 18-20 fitted to all
+ *               matches with weights p_j exp(-alpha |x_i - x_j|^2) (products in FP32,
+ *               accumulations in FP64)
+ *             residuals e_j = |y_j - W_{-j}(x_j)|^2 of the leave-one-out blend (Eqs. 2-4)
+ *             sigma^2 = max(sum p e / (2 sum p), floor), gamma = clamp(mean p, .05, .95)
+ *   output    q_out rows, c_out[i] = p_i if p_i >= 1/2 else 0, p_out = p
+ *
+ *   src, dst   device, n x 2 float: match positions in the reference frame and frame t
+ *   n          3 <= n <= emdq_fit_max_n()
+ *   frame_w/h  size of frame t (outlier density 1/(w h); alpha rule)
+ *   prm        host; NULL = defaults
+ *   p0         device, n float initial inlier weights, or NULL for all ones
+ *   q_out      device, n x 8 float warp rows (written)
+ *   c_out      device, n float field weights (written)
+ *   p_out      device, n float final posteriors (written), may be NULL
+ *   info       device emdq_fit_info (written)
+ *   workspace  device scratch of emdq_fit_workspace_size(n) bytes, 256-byte aligned
+ * Returns EMDQ_EINVAL / EMDQ_EWORKSPACE / EMDQ_ENOTSUP / EMDQ_ECUDA on the host; the
+ * device outcome (OK, ENOCONV, EDEGENERATE, ETIMEOUT, ENONFINITE) is in info->status.
+ */
+int         emdq_fit_max_n(void);
+size_t      emdq_fit_workspace_size(int n);
+emdq_status emdq_fit(const float *src, const float *dst, int n, int frame_w, int frame_h,
+                     const emdq_params *prm, const float *p0, float *q_out, float *c_out,
+                     float *p_out, emdq_fit_info *info, void *workspace,
+                     size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------ emdq_field -------
+ * Dense displacement field (Eqs. 2-4 with Eq. 1): for every pixel p of the grid
+ * [grid_x0, grid_x0 + grid_w) x [grid_y0, grid_y0 + grid_h) (reference coordinates),
+ *   w_i = c_i exp(-alpha |x_i - p|^2),  s_p = sum w_i s_i / sum w_i,
+ *   q_p = sum w_i q_i / sum w_i normalised by |(r_w, r_z)|,
+ *   disp(p) = s_p (R(q_p) p + t(q_p)) - p.
+ * Pixels where sum w_i = 0 get NaN.
+ *
+ *   q, c, src  device: n x 8 warp rows, n weights, n x 2 reference positions (the fit's
+ *              outputs and its src)
+ *   alpha      > 0
+ *   precision  EMDQ_FP32 or EMDQ_BF16
+ *   disp_out   device, grid_h x grid_w x 2 float, row-major (written)
+ *   workspace  device scratch of emdq_field_workspace_size(...) bytes (may be 0 bytes for
+ *              EMDQ_FP32), 256-byte aligned
+ */
+size_t      emdq_field_workspace_size(int n, int grid_w, int grid_h, int precision);
+emdq_status emdq_field(const float *q, const float *c, const float *src, int n,
+                       int grid_x0, int grid_y0, int grid_w, int grid_h, float alpha,
+                       int precision, float *disp_out, void *workspace,
+                       size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------ mosaic_warp ------
+ * Gather warp + capped running-average blend of frame t into the canvas (Sec. III-F,
+ * Eqs. 23-24 as read: the paper's printed blend lacks its normalisation and its cap reads
+ * max{w+1, 30}).  For every grid pixel p (reference coordinates), u = p + disp(p) is
+ * formed in FP32; if 0 <= u_x <= fw-1 and 0 <= u_y <= fh-1 the frame is sampled
+ * bilinearly at u and canvas pixel P = p + (origin_x, origin_y) is updated
+ *   c <- clamp(floor((w c + v)/(w + 1) + 1/2), 0, 255),  w <- min(w + 1, 30)
+ * otherwise the canvas pixel is left untouched (also for NaN displacements).
+ *
+ *   frame        device, fh rows of frame_pitch bytes, pixels of `channels` bytes (1 or 3)
+ *   disp         device, grid_h x grid_w x 2 float (emdq_field's output)
+ *   canvas       device, canvas_h rows of canvas_pitch bytes (multiple of 4, >= 4 canvas_w),
+ *                4-byte pixels, 4-byte aligned
+ *   origin_x/y   canvas position of reference pixel (0, 0)
+ * The grid, shifted by the origin, must lie inside the canvas (else EMDQ_EINVAL).
+ */
+emdq_status mosaic_warp(const uint8_t *frame, int fw, int fh, int channels, int frame_pitch,
+                        const float *disp, int grid_x0, int grid_y0, int grid_w, int grid_h,
+                        uint8_t *canvas, int canvas_w, int canvas_h, int canvas_pitch,
+                        int origin_x, int origin_y, void *stream);
+
+/* Sec. III-F: "frame 0 is inserted directly" -- copy the reference frame into the canvas
+ * at the origin with merge weight 1. */
+emdq_status mosaic_insert_reference(const uint8_t *frame, int fw, int fh, int channels,
+                                    int frame_pitch, uint8_t *canvas, int canvas_w,
+                                    int canvas_h, int canvas_pitch, int origin_x,
+                                    int origin_y, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EMDQ_H */

@@ -1,0 +1,208 @@
+"""GB300-native EMDQ dense deformation field and mosaic warp (arXiv 2103.07414).
+
+A thin binding over the C ABI of ``libemdq.so`` (declared in ``include/emdq.h``): it
+checks tensor devices, dtypes and layouts, allocates outputs and workspaces with torch,
+and passes raw device pointers and the current CUDA stream.  Every step of the path runs
+in the library's CUDA kernels; there is no CPU or PyTorch fallback -- if the library is
+missing or a CUDA device is not available, these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from ._build import LIB as _LIB_PATH, build  # noqa: F401
+
+__all__ = ['emdq_fit', 'emdq_field', 'mosaic_warp', 'mosaic_insert_reference',
+           'alpha_for_frame', 'fit_workspace_size', 'field_workspace_size', 'EmdqError',
+           'FP32', 'BF16', 'STATUS', 'lib', 'build']
+
+FP32, BF16 = 0, 1
+STATUS = {0: 'OK', 1: 'EINVAL', 2: 'EDEGENERATE', 3: 'ENOCONV', 4: 'ETIMEOUT', 5: 'ECUDA',
+          6: 'EWORKSPACE', 7: 'ENOTSUP', 8: 'ENONFINITE'}
+
+
+class EmdqError(RuntimeError):
+    def __init__(self, where: str, code: int):
+        self.code = code
+        super().__init__(f'{where}: {STATUS.get(code, code)} ({lib().emdq_status_string(code).decode()})')
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [('alpha', ctypes.c_float), ('max_iters', ctypes.c_int),
+                ('tol_p', ctypes.c_float), ('sigma2_floor', ctypes.c_float),
+                ('reserved', ctypes.c_int * 4)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libemdq.so (built in-tree by ``build()``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(f'libemdq.so not built ({_LIB_PATH}); run '
+                                   'paper_2103_07414_gb300.build() first')
+            L = ctypes.CDLL(_LIB_PATH)
+            P, I, F, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+            L.emdq_default_params.argtypes = [ctypes.POINTER(_Params)]
+            L.emdq_alpha_for_frame.restype = F
+            L.emdq_alpha_for_frame.argtypes = [I, I]
+            L.emdq_status_string.restype = ctypes.c_char_p
+            L.emdq_status_string.argtypes = [I]
+            L.emdq_abi_version.restype = I
+            L.emdq_fit_max_n.restype = I
+            L.emdq_fit_workspace_size.restype = Z
+            L.emdq_fit_workspace_size.argtypes = [I]
+            L.emdq_fit.restype = I
+            L.emdq_fit.argtypes = [P, P, I, I, I, ctypes.POINTER(_Params), P, P, P, P, P, P, Z, P]
+            L.emdq_field_workspace_size.restype = Z
+            L.emdq_field_workspace_size.argtypes = [I, I, I, I]
+            L.emdq_field.restype = I
+            L.emdq_field.argtypes = [P, P, P, I, I, I, I, I, F, I, P, P, Z, P]
+            L.mosaic_warp.restype = I
+            L.mosaic_warp.argtypes = [P, I, I, I, I, P, I, I, I, I, P, I, I, I, I, I, P]
+            L.mosaic_insert_reference.restype = I
+            L.mosaic_insert_reference.argtypes = [P, I, I, I, I, P, I, I, I, I, I, P]
+            _lib = L
+    return _lib
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(t: torch.Tensor, name: str, dtype: torch.dtype, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f'{name} must be a CUDA tensor')
+    if t.dtype != dtype:
+        raise ValueError(f'{name} must be {dtype}, got {t.dtype}')
+    if not t.is_contiguous():
+        raise ValueError(f'{name} must be contiguous')
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f'{name} must have shape {tuple(shape)}, got {tuple(t.shape)}')
+
+
+def alpha_for_frame(w: int, h: int) -> float:
+    return lib().emdq_alpha_for_frame(int(w), int(h))
+
+
+def fit_workspace_size(n: int) -> int:
+    return lib().emdq_fit_workspace_size(int(n))
+
+
+def field_workspace_size(n: int, grid_w: int, grid_h: int, precision: int) -> int:
+    return lib().emdq_field_workspace_size(int(n), int(grid_w), int(grid_h), int(precision))
+
+
+def _workspace(nbytes: int, device, given: torch.Tensor | None) -> torch.Tensor:
+    if given is not None:
+        _check(given, 'workspace', torch.uint8)
+        return given
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def emdq_fit(src: torch.Tensor, dst: torch.Tensor, frame_w: int, frame_h: int, *,
+             alpha: float = 0.0, max_iters: int = 20, tol_p: float = 1e-3,
+             sigma2_floor: float = 0.25, p0: torch.Tensor | None = None,
+             out: dict | None = None, workspace: torch.Tensor | None = None, stream=None) -> dict:
+    """EMDQ fit of n matches (src, dst: [n, 2] float32 CUDA).  Returns dict with q [n, 8],
+    c [n], p [n] and info [4] (int32 view: status, iters; float view: sigma2, gamma)."""
+    n = src.shape[0]
+    _check(src, 'src', torch.float32, (n, 2))
+    _check(dst, 'dst', torch.float32, (n, 2))
+    if p0 is not None:
+        _check(p0, 'p0', torch.float32, (n,))
+    dev = src.device
+    o = out if out is not None else {}
+    q = o.get('q') if o.get('q') is not None else torch.empty((n, 8), dtype=torch.float32, device=dev)
+    c = o.get('c') if o.get('c') is not None else torch.empty(n, dtype=torch.float32, device=dev)
+    p = o.get('p') if o.get('p') is not None else torch.empty(n, dtype=torch.float32, device=dev)
+    info = o.get('info') if o.get('info') is not None else torch.zeros(4, dtype=torch.int32, device=dev)
+    ws = _workspace(fit_workspace_size(n), dev, workspace)
+    prm = _Params(float(alpha), int(max_iters), float(tol_p), float(sigma2_floor), (ctypes.c_int * 4)())
+    rc = lib().emdq_fit(_ptr(src), _ptr(dst), n, int(frame_w), int(frame_h), ctypes.byref(prm),
+                        _ptr(p0), _ptr(q), _ptr(c), _ptr(p), _ptr(info), _ptr(ws), ws.numel(),
+                        _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_fit', rc)
+    return dict(q=q, c=c, p=p, info=info, workspace=ws)
+
+
+def read_fit_info(info: torch.Tensor) -> dict:
+    """Decode the 16-byte device record (synchronises with its stream)."""
+    h = info.cpu()
+    iv = h.view(torch.int32)
+    fv = h.view(torch.float32)
+    return dict(status=int(iv[0]), status_name=STATUS.get(int(iv[0]), '?'), iters=int(iv[1]),
+                sigma2=float(fv[2]), gamma=float(fv[3]))
+
+
+def emdq_field(q: torch.Tensor, c: torch.Tensor, src: torch.Tensor, grid, alpha: float, *,
+               precision: int = BF16, out: torch.Tensor | None = None,
+               workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Dense displacement on grid=(x0, y0, w, h): returns [h, w, 2] float32 CUDA."""
+    n = c.shape[0]
+    _check(q, 'q', torch.float32, (n, 8))
+    _check(c, 'c', torch.float32, (n,))
+    _check(src, 'src', torch.float32, (n, 2))
+    x0, y0, gw, gh = (int(v) for v in grid)
+    if out is None:
+        out = torch.empty((gh, gw, 2), dtype=torch.float32, device=q.device)
+    _check(out, 'out', torch.float32, (gh, gw, 2))
+    ws = _workspace(field_workspace_size(n, gw, gh, precision), q.device, workspace)
+    rc = lib().emdq_field(_ptr(q), _ptr(c), _ptr(src), n, x0, y0, gw, gh, float(alpha),
+                          int(precision), _ptr(out), _ptr(ws), ws.numel(), _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_field', rc)
+    return out
+
+
+def _frame_args(frame: torch.Tensor):
+    _check(frame, 'frame', torch.uint8)
+    if frame.dim() == 2:
+        fh, fw = frame.shape
+        ch = 1
+    elif frame.dim() == 3 and frame.shape[2] in (1, 3):
+        fh, fw, ch = frame.shape
+    else:
+        raise ValueError('frame must be [h, w] or [h, w, 1|3] uint8')
+    return fw, fh, ch, fw * ch
+
+
+def mosaic_warp(frame: torch.Tensor, disp: torch.Tensor, grid, canvas: torch.Tensor, origin,
+                stream=None) -> None:
+    """Blend frame into canvas ([CH, CW, 4] uint8 CUDA) through the field disp."""
+    fw, fh, ch, pitch = _frame_args(frame)
+    x0, y0, gw, gh = (int(v) for v in grid)
+    _check(disp, 'disp', torch.float32, (gh, gw, 2))
+    _check(canvas, 'canvas', torch.uint8)
+    if canvas.dim() != 3 or canvas.shape[2] != 4:
+        raise ValueError('canvas must be [h, w, 4] uint8')
+    chh, cw = canvas.shape[:2]
+    rc = lib().mosaic_warp(_ptr(frame), fw, fh, ch, pitch, _ptr(disp), x0, y0, gw, gh,
+                           _ptr(canvas), cw, chh, cw * 4, int(origin[0]), int(origin[1]),
+                           _stream(stream))
+    if rc != 0:
+        raise EmdqError('mosaic_warp', rc)
+
+
+def mosaic_insert_reference(frame: torch.Tensor, canvas: torch.Tensor, origin, stream=None) -> None:
+    fw, fh, ch, pitch = _frame_args(frame)
+    _check(canvas, 'canvas', torch.uint8)
+    chh, cw = canvas.shape[:2]
+    rc = lib().mosaic_insert_reference(_ptr(frame), fw, fh, ch, pitch, _ptr(canvas), cw, chh,
+                                       cw * 4, int(origin[0]), int(origin[1]), _stream(stream))
+    if rc != 0:
+        raise EmdqError('mosaic_insert_reference', rc)

@@ -1,0 +1,99 @@
+"""GPU parity: emdq_field (C ABI) against the oracle's FP64 field (Eqs. 2-4)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_cases import fitted_case, random_rows
+
+pytestmark = pytest.mark.gpu
+
+# Field tolerances vs the FP64 oracle, px (maximum over every compared pixel).
+TOL = {0: 1e-3, 1: 0.05}
+
+
+@pytest.fixture(scope='module')
+def emdq():
+    import paper_2103_07414_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+def _gpu_field(emdq, q8, c, src, grid, alpha, prec):
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    d = emdq.emdq_field(t(q8), t(c), t(src), grid, alpha, precision=prec)
+    torch.cuda.synchronize()
+    return d.cpu().numpy().astype(np.float64)
+
+
+def _oracle_inputs(q8, c, src):
+    # the oracle sees exactly the float32 values the GPU reads
+    f = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    return f(q8), f(c), f(src)
+
+
+PRECISIONS = [0, 1]
+
+
+@pytest.mark.parametrize('prec', PRECISIONS, ids=['fp32', 'bf16'])
+def test_field_parity_fitted_pair(emdq, orc, prec):
+    sc, cfg, src, dst, inl, r = fitted_case(orc, 'pair640', seed=0)
+    alpha = orc.alpha_for_frame(sc.w, sc.h)
+    grid = (-7, -5, 333, 141)                     # ragged in both directions
+    q8, c, s = _oracle_inputs(r['q8'], r['c'], src)
+    want = orc.field(q8, c, s, grid, alpha)
+    got = _gpu_field(emdq, r['q8'], r['c'], src, grid, np.float32(alpha), prec)
+    err = np.abs(got - want).max()
+    print(f'prec {prec}: max field error {err:.3e} px')
+    assert err <= TOL[prec]
+
+
+@pytest.mark.parametrize('prec', PRECISIONS, ids=['fp32', 'bf16'])
+def test_field_identical_transforms(emdq, orc, prec):
+    rng = np.random.default_rng(2)
+    n = 300
+    src = rng.uniform(0, 1279, (n, 2))
+    q = orc.dq_from_rt(math.radians(5), 12.0, -7.0)
+    q8 = np.tile([q[0], q[1], q[2], q[3], 1.05, 1, 0, 0], (n, 1))
+    c = rng.uniform(0.5, 1.0, n)
+    grid = (0, 0, 1280, 64)
+    alpha = orc.alpha_for_frame(1280, 1024)
+    got = _gpu_field(emdq, q8, c, src, grid, np.float32(alpha), prec)
+    want = orc.field(*_oracle_inputs(q8, c, src), grid, alpha)
+    assert np.abs(got - want).max() <= TOL[prec]
+
+
+@pytest.mark.parametrize('prec', PRECISIONS, ids=['fp32', 'bf16'])
+def test_field_no_weight_gives_nan(emdq, prec):
+    n = 40
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device='cuda')
+    q8 = t(np.tile([1, 0, 0, 0, 1, 1, 0, 0], (n, 1)))
+    d = emdq.emdq_field(q8, torch.zeros(n, device='cuda'), torch.rand(n, 2, device='cuda') * 10,
+                        (0, 0, 20, 3), 1e-3, precision=prec)
+    assert torch.isnan(d).all()
+
+
+@pytest.mark.parametrize('prec', PRECISIONS, ids=['fp32', 'bf16'])
+def test_field_full_size_sampled(emdq, orc, prec):
+    """1280x1024 frame, N=1000, the benchmark's launch; compare 4096 sampled pixels."""
+    rng = np.random.default_rng(3)
+    src, q8 = random_rows(rng, 1000, 1280, 1024)
+    c = np.where(rng.uniform(0, 1, 1000) < 0.7, rng.uniform(0.5, 1, 1000), 0.0)
+    grid = (-30, -40, 1340, 1100)
+    alpha = orc.alpha_for_frame(1280, 1024)
+    got = _gpu_field(emdq, q8, c, src, grid, np.float32(alpha), prec)
+    iy = rng.integers(0, grid[3], 4096)
+    ix = rng.integers(0, grid[2], 4096)
+    pts = np.stack([grid[0] + ix, grid[1] + iy], 1).astype(np.float64)
+    want = orc.field_points(*_oracle_inputs(q8, c, src), pts, alpha)
+    err = np.abs(got[iy, ix] - want).max()
+    print(f'prec {prec}: full-size sampled max error {err:.3e} px')
+    assert err <= TOL[prec]
+
+
+def test_field_bad_arguments(emdq):
+    q8 = torch.zeros((4, 8), device='cuda')
+    with pytest.raises(emdq.EmdqError):
+        emdq.emdq_field(q8, torch.ones(4, device='cuda'), torch.zeros(4, 2, device='cuda'),
+                        (0, 0, 4, 4), -1.0, precision=0)
