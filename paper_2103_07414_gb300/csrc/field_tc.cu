@@ -1,10 +1,354 @@
-// Tensor-core field path (placeholder until the tcgen05 kernel lands).
+// Dense field on the 5th-generation tensor cores (tcgen05, BF16 operands, FP32 accumulate).
+//
+// The Gaussian of Eq. 4 separates on a pixel grid,
+//     exp(-alpha |p - x_i|^2) = exp(-alpha (p_x - x_i)^2) exp(-alpha (p_y - y_i)^2),
+// so the six blend sums of Eqs. 2-3 (four DQ components and the scale, each relative to a
+// reference row, and the weight) are, per channel ch, a GEMM over the matches:
+//     F_ch[p_x, p_y] = sum_i Ex[p_x, i] * G_ch[p_y, i],
+//     Ex[p_x, i] = exp(-alpha (p_x - x_i)^2),
+//     G_ch[p_y, i] = c_i exp(-alpha (p_y - y_i)^2) (Q_i,ch - Q_ref,ch)   (ch < 5),
+//     G_5[p_y, i]  = c_i exp(-alpha (p_y - y_i)^2).
+// This is the same sum as the per-pixel definition, with (w + h) N exponentials instead
+// of w h N.  Subtracting the reference row (exact: the blend is linear) keeps the BF16
+// rounding of G off the large scale and dual-part values the pixel position multiplies.
+//
+// field_tc_prep_kernel writes Ex (K-major rows of pixels x) and G (K-major rows of
+// pixels y, six channel planes) as BF16 into the workspace, zero-padded to whole tiles.
+// field_tc_kernel: one CTA per 128 x 32 pixel tile.  A TMA producer thread streams
+// 64-match slices of Ex (128 rows) and of G (6 x 32 rows, one 3-D box) through a 4-stage
+// shared-memory ring; one thread issues tcgen05.mma (M = 128 pixels x, N = 192 =
+// 6 channels x 32 pixels y, K = 16) accumulating in TMEM; then the four warps read the
+// accumulators back with tcgen05.ld (thread = pixel x = TMEM lane) and evaluate Eq. 1.
+#include <mutex>
+
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
 #include "field_tc.cuh"
+#include "tc_ptx.cuh"
 
-size_t field_tc_workspace_bytes(int, int, int) { return 0; }
+namespace emdq {
 
-emdq_status field_tc_launch(const float *, const float *, const float *, int, int, int, int,
-                            int, float, const float *, float2 *, char *, size_t, cudaStream_t)
+constexpr int kTcM = 128;                // pixels x per tile (MMA M, TMEM lanes)
+constexpr int kTcPY = 32;                // pixels y per tile
+constexpr int kTcCh = 6;                 // dr_w, dr_z, dd_x, dd_y, ds, weight
+constexpr int kTcN = kTcCh * kTcPY;      // MMA N = 192
+constexpr int kTcK = 64;                 // matches per stage: one 128-byte swizzle row
+constexpr int kTcStages = 4;
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTcABytes = kTcM * kTcK * 2;
+constexpr uint32_t kTcBBytes = kTcN * kTcK * 2;
+constexpr uint32_t kTcStageBytes = kTcABytes + kTcBBytes;
+constexpr uint32_t kTcTmemCols = 256;
+constexpr size_t kTcSmemBytes = kTcStages * kTcStageBytes + 1024 /*barriers*/ + 1024 /*align*/;
+constexpr uint32_t kTcIdesc = tc::idesc_bf16_f32(kTcM, kTcN);
+constexpr int kPrepRows = 8;
+constexpr int kPrepThreads = 256;
+constexpr long long kWaitLimit = 4000000000LL;   // SM cycles (about 2 s)
+
+static_assert(kTcN % 16 == 0 && kTcN <= 256, "MMA N for M = 128");
+static_assert(kTcStageBytes % 1024 == 0 && kTcABytes % 1024 == 0, "SW128 tiles 1 KiB aligned");
+
+struct TcGeom {
+    int kp;          // matches padded to kTcK
+    int wp, hp;      // grid padded to kTcM, kTcPY
+    size_t a_bytes, b_bytes;
+};
+
+__host__ __device__ inline TcGeom tc_geom(int n, int gw, int gh)
 {
-    return EMDQ_ENOTSUP;
+    TcGeom g;
+    g.kp = (n + kTcK - 1) / kTcK * kTcK;
+    g.wp = (gw + kTcM - 1) / kTcM * kTcM;
+    g.hp = (gh + kTcPY - 1) / kTcPY * kTcPY;
+    g.a_bytes = (size_t)g.wp * g.kp * 2;
+    g.b_bytes = (size_t)kTcCh * g.hp * g.kp * 2;
+    return g;
+}
+
+__global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
+    const float *__restrict__ q, const float *__restrict__ c, const float2 *__restrict__ src,
+    int n, int kp, int gx0, int gy0, int gw, int gh, int wp, int hp, float alpha,
+    const float *__restrict__ ref, __nv_bfloat162 *__restrict__ A, __nv_bfloat162 *__restrict__ B,
+    int a_blocks)
+{
+    const int half = kp / 2;
+    if ((int)blockIdx.x < a_blocks) {
+        const int r0 = blockIdx.x * kPrepRows;
+        for (int k2 = threadIdx.x; k2 < half; k2 += kPrepThreads) {
+            const int k0 = 2 * k2, k1 = k0 + 1;
+            const float x0 = k0 < n ? src[k0].x : 0.f, x1 = k1 < n ? src[k1].x : 0.f;
+            for (int r = 0; r < kPrepRows; ++r) {
+                const int px = r0 + r;
+                if (px >= wp) break;
+                const float p = static_cast<float>(gx0 + px);
+                const bool row = px < gw;
+                const float d0 = p - x0, d1 = p - x1;
+                const float e0 = (row && k0 < n) ? expf(-alpha * d0 * d0) : 0.f;
+                const float e1 = (row && k1 < n) ? expf(-alpha * d1 * d1) : 0.f;
+                A[(size_t)px * half + k2] = __floats2bfloat162_rn(e0, e1);
+            }
+        }
+    } else {
+        const int r0 = (blockIdx.x - a_blocks) * kPrepRows;
+        float rf[5];
+#pragma unroll
+        for (int ch = 0; ch < 5; ++ch) rf[ch] = ref[ch];
+        for (int k2 = threadIdx.x; k2 < half; k2 += kPrepThreads) {
+            const int k0 = 2 * k2;
+            float y[2] = {0.f, 0.f}, cw[2] = {0.f, 0.f}, cq[2][5];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int k = k0 + u;
+#pragma unroll
+                for (int ch = 0; ch < 5; ++ch) cq[u][ch] = 0.f;
+                if (k < n) {
+                    y[u] = src[k].y;
+                    cw[u] = c[k];
+                    const float4 r = *reinterpret_cast<const float4 *>(q + 8 * (size_t)k);
+                    const float s = q[8 * (size_t)k + 4];
+                    cq[u][0] = cw[u] * (r.x - rf[0]);
+                    cq[u][1] = cw[u] * (r.y - rf[1]);
+                    cq[u][2] = cw[u] * (r.z - rf[2]);
+                    cq[u][3] = cw[u] * (r.w - rf[3]);
+                    cq[u][4] = cw[u] * (s - rf[4]);
+                }
+            }
+            for (int r = 0; r < kPrepRows; ++r) {
+                const int py = r0 + r;
+                if (py >= hp) break;
+                const float p = static_cast<float>(gy0 + py);
+                const bool row = py < gh;
+                const float d0 = p - y[0], d1 = p - y[1];
+                const float e0 = row ? expf(-alpha * d0 * d0) : 0.f;
+                const float e1 = row ? expf(-alpha * d1 * d1) : 0.f;
+#pragma unroll
+                for (int ch = 0; ch < 5; ++ch)
+                    B[((size_t)ch * hp + py) * half + k2] =
+                        __floats2bfloat162_rn(e0 * cq[0][ch], e1 * cq[1][ch]);
+                B[((size_t)5 * hp + py) * half + k2] = __floats2bfloat162_rn(e0 * cw[0], e1 * cw[1]);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int nchunks,
+    int gx0, int gy0, int gw, int gh, const float *__restrict__ ref, float2 *__restrict__ disp,
+    int *__restrict__ err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kTcStages * kTcStageBytes);
+    uint64_t *empty = full + kTcStages;
+    uint64_t *done = empty + kTcStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    int *issued = const_cast<int *>(abort_flag + 1);     // chunks whose loads were issued
+    int *consumed = issued + 1;                          // chunks whose MMAs were issued
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile_x = blockIdx.x, tile_y = blockIdx.y;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            tc::mbar_init(full + s, 1);
+            tc::mbar_init(empty + s, 1);
+        }
+        tc::mbar_init(done, 1);
+        *abort_flag = 0;
+        *issued = 0;
+        *consumed = 0;
+        tc::fence_mbar_init();
+        tc::prefetch_tmap(&tmA);
+        tc::prefetch_tmap(&tmB);
+    }
+    if (warp == 2) tc::tmem_alloc(tmem_slot, kTcTmemCols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int k = 0; k < nchunks; ++k) {
+            const int s = k % kTcStages;
+            const uint32_t ph = (k / kTcStages) & 1;
+            if (k >= kTcStages && !tc::mbar_wait(empty + s, ph ^ 1, kWaitLimit, false)) {
+                *abort_flag = 1;
+                break;
+            }
+            if (*abort_flag) break;
+            uint8_t *sa = smem + s * kTcStageBytes;
+            tc::mbar_arrive_expect_tx(full + s, kTcStageBytes);
+            tc::tma_load_2d(sa, &tmA, full + s, k * kTcK, tile_x * kTcM);
+            tc::tma_load_3d(sa + kTcABytes, &tmB, full + s, k * kTcK, tile_y * kTcPY, 0);
+            *issued = k + 1;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        for (int k = 0; k < nchunks; ++k) {
+            const int s = k % kTcStages;
+            const uint32_t ph = (k / kTcStages) & 1;
+            if (!tc::mbar_wait(full + s, ph, kWaitLimit, false)) {
+                *abort_flag = 1;
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t sa = tc::smem_u32(smem + s * kTcStageBytes);
+            const uint32_t sb = sa + kTcABytes;
+#pragma unroll
+            for (int kk = 0; kk < kTcK / 16; ++kk) {
+                // advance 16 BF16 = 32 bytes along K inside the 128-byte swizzled row
+                tc::mma_f16(tmem, tc::desc_kmajor_sw128(sa + kk * 32),
+                            tc::desc_kmajor_sw128(sb + kk * 32), kTcIdesc, (k | kk) != 0);
+            }
+            tc::mma_commit(empty + s);
+            *consumed = k + 1;
+        }
+        tc::mma_commit(done);   // tracks every MMA issued above, also after an abort
+    }
+    __syncwarp();
+
+    // epilogue: thread = pixel x = TMEM lane; 8 pixels y at a time, 6 channels each
+    const bool ok = tc::mbar_wait(done, 0, kWaitLimit, true);
+    tc::fence_after_sync();
+    if (!ok) *abort_flag = 1;
+    __syncthreads();
+    if (!*abort_flag) {
+        const float ra = ref[0], rb = ref[1], ru = ref[2], rv = ref[3], rs = ref[4];
+        const int xl = warp * 32 + lane;
+        const int x = tile_x * kTcM + xl;
+        const float px = static_cast<float>(gx0 + x);
+        const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+#pragma unroll 1
+        for (int g = 0; g < kTcPY / 8; ++g) {
+            float F[kTcCh][8];
+#pragma unroll
+            for (int ch = 0; ch < kTcCh; ++ch) tc::tmem_ld_x8(lane_base + ch * kTcPY + g * 8, F[ch]);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int y = tile_y * kTcPY + g * 8 + j;
+                if (x >= gw || y >= gh) continue;
+                const float py = static_cast<float>(gy0 + y);
+                float2 d = make_float2(NAN, NAN);
+                const float w = F[5][j];
+                if (w > 0.f) {
+                    const float inv = 1.f / w;
+                    const float2 xp = apply_blend(ra + F[0][j] * inv, rb + F[1][j] * inv,
+                                                  ru + F[2][j] * inv, rv + F[3][j] * inv,
+                                                  rs + F[4][j] * inv, px, py);
+                    d = make_float2(xp.x - px, xp.y - py);
+                }
+                disp[(size_t)y * gw + x] = d;
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) {
+        atomicMax(err, (int)EMDQ_ETIMEOUT);
+        // drain loads that were issued but never consumed before the CTA exits
+        for (int k = *consumed; k < *issued; ++k)
+            tc::mbar_wait(full + (k % kTcStages), (k / kTcStages) & 1, kWaitLimit, true);
+    }
+    __syncthreads();
+    if (warp == 2) tc::tmem_dealloc(tmem, kTcTmemCols);
+}
+
+}  // namespace emdq
+
+using namespace emdq;
+using namespace emdq_host;
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+constexpr size_t kErrBytes = 256;
+
+}  // namespace
+
+size_t field_tc_workspace_bytes(int n, int grid_w, int grid_h)
+{
+    const TcGeom g = tc_geom(n, grid_w, grid_h);
+    return kErrBytes + align_up(g.a_bytes, 1024) + align_up(g.b_bytes, 1024);
+}
+
+emdq_status field_tc_launch(const float *q, const float *c, const float *src, int n, int gx0,
+                            int gy0, int gw, int gh, float alpha, const float *ref, float2 *disp,
+                            char *ws, size_t ws_bytes, cudaStream_t st)
+{
+    const DeviceInfo &D = device_info();
+    if (D.device < 0) return EMDQ_ECUDA;
+    if (D.cc_major != 10) return EMDQ_ENOTSUP;           // tcgen05: sm_100 family only
+    if (D.smem_optin < kTcSmemBytes) return EMDQ_ENOTSUP;
+    const TcGeom g = tc_geom(n, gw, gh);
+    if (ws_bytes < field_tc_workspace_bytes(n, gw, gh)) return EMDQ_EWORKSPACE;
+    if (g.hp / kTcPY > 65535 || g.hp > (1 << 24) || g.wp > (1 << 24)) return EMDQ_ENOTSUP;
+    auto encode = encode_fn();
+    if (!encode) return EMDQ_ECUDA;
+
+    int *err = reinterpret_cast<int *>(ws);
+    auto *A = reinterpret_cast<__nv_bfloat162 *>(ws + kErrBytes);
+    auto *B = reinterpret_cast<__nv_bfloat162 *>(ws + kErrBytes + align_up(g.a_bytes, 1024));
+
+    CUtensorMap tmA, tmB;
+    {
+        cuuint64_t dims[2] = {(cuuint64_t)g.kp, (cuuint64_t)g.wp};
+        cuuint64_t strides[1] = {(cuuint64_t)g.kp * 2};
+        cuuint32_t box[2] = {kTcK, kTcM};
+        cuuint32_t estr[2] = {1, 1};
+        if (encode(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return EMDQ_ECUDA;
+    }
+    {
+        cuuint64_t dims[3] = {(cuuint64_t)g.kp, (cuuint64_t)g.hp, (cuuint64_t)kTcCh};
+        cuuint64_t strides[2] = {(cuuint64_t)g.kp * 2, (cuuint64_t)g.hp * g.kp * 2};
+        cuuint32_t box[3] = {kTcK, kTcPY, kTcCh};
+        cuuint32_t estr[3] = {1, 1, 1};
+        if (encode(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, B, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return EMDQ_ECUDA;
+    }
+
+    static std::mutex mu;
+    static int attr_dev = -1;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (attr_dev != D.device) {
+            if (cudaFuncSetAttribute(field_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kTcSmemBytes) != cudaSuccess)
+                return EMDQ_ECUDA;
+            attr_dev = D.device;
+        }
+    }
+    if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return EMDQ_ECUDA;
+    const int a_blocks = g.wp / kPrepRows;
+    const int b_blocks = g.hp / kPrepRows;
+    field_tc_prep_kernel<<<a_blocks + b_blocks, kPrepThreads, 0, st>>>(
+        q, c, reinterpret_cast<const float2 *>(src), n, g.kp, gx0, gy0, gw, gh, g.wp, g.hp, alpha,
+        ref, A, B, a_blocks);
+    if (cudaGetLastError() != cudaSuccess) return EMDQ_ECUDA;
+    dim3 grid(g.wp / kTcM, g.hp / kTcPY);
+    field_tc_kernel<<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, g.kp / kTcK, gx0, gy0, gw,
+                                                            gh, ref, disp, err);
+    return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }

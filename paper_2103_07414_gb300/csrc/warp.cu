@@ -85,12 +85,12 @@ extern "C" emdq_status mosaic_warp(const uint8_t *frame, int fw, int fh, int cha
                                    int canvas_w, int canvas_h, int canvas_pitch, int origin_x,
                                    int origin_y, void *stream)
 {
-    if (!frame || !disp || !canvas || fw < 1 || fh < 1 || (channels != 1 && channels != 3) ||
+    if (!frame || !canvas || fw < 1 || fh < 1 || (channels != 1 && channels != 3) ||
         frame_pitch < fw * channels || grid_w < 0 || grid_h < 0 || canvas_w < 1 ||
         canvas_h < 1 || canvas_pitch < 4 * canvas_w || canvas_pitch % 4 != 0)
         return EMDQ_EINVAL;
-    if (!aligned(disp, 8) || !aligned(canvas, 4)) return EMDQ_EINVAL;
-    if (grid_w == 0 || grid_h == 0) return EMDQ_OK;
+    if (grid_w == 0 || grid_h == 0) return EMDQ_OK;      // empty window: nothing to read
+    if (!disp || !aligned(disp, 8) || !aligned(canvas, 4)) return EMDQ_EINVAL;
     if ((long long)grid_x0 + origin_x < 0 || (long long)grid_y0 + origin_y < 0 ||
         (long long)grid_x0 + origin_x + grid_w > canvas_w ||
         (long long)grid_y0 + origin_y + grid_h > canvas_h)

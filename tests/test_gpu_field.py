@@ -97,3 +97,17 @@ def test_field_bad_arguments(emdq):
     with pytest.raises(emdq.EmdqError):
         emdq.emdq_field(q8, torch.ones(4, device='cuda'), torch.zeros(4, 2, device='cuda'),
                         (0, 0, 4, 4), -1.0, precision=0)
+
+
+@pytest.mark.parametrize('prec', PRECISIONS, ids=['fp32', 'bf16'])
+@pytest.mark.parametrize('n', [3, 65, 129])
+def test_field_small_and_ragged_match_counts(emdq, orc, prec, n):
+    """Match counts that leave most of a 64-match slice as padding; one-tile grids."""
+    rng = np.random.default_rng(100 + n)
+    src, q8 = random_rows(rng, n, 640, 480)
+    c = rng.uniform(0.3, 1.0, n)
+    alpha = orc.alpha_for_frame(640, 480)
+    for grid in [(5, 7, 17, 9), (-3, 100, 128, 32), (0, 0, 129, 33)]:
+        got = _gpu_field(emdq, q8, c, src, grid, np.float32(alpha), prec)
+        want = orc.field(*_oracle_inputs(q8, c, src), grid, alpha)
+        assert np.abs(got - want).max() <= TOL[prec], (grid, np.abs(got - want).max())

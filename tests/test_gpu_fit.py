@@ -52,10 +52,12 @@ def test_fit_fixed_iterations_parity(emdq, orc, name, iters):
     ds = np.abs(got['q8'][:, 4] - want['q8'][:, 4]).max()
     print(f'{name}: max |dp| {dp:.2e}, max row-prediction diff {dpos:.2e} px, max |ds| {ds:.2e}, '
           f'sigma2 {got["info"]["sigma2"]:.6f} vs {want["sigma2"]:.6f}')
-    assert dp <= 2e-3
-    assert dpos <= 2e-2
-    assert got['info']['sigma2'] == pytest.approx(want['sigma2'], rel=2e-3)
-    assert got['info']['gamma'] == pytest.approx(want['gamma'], abs=1e-3)
+    # FP32 products (relative rounding ~6e-8) on coordinates up to ~2000 px, summed over
+    # N terms: a few 1e-4 px on a row's prediction; the posteriors follow to ~1e-5
+    assert dp <= 1e-4
+    assert dpos <= 2e-3
+    assert got['info']['sigma2'] == pytest.approx(want['sigma2'], rel=1e-5)
+    assert got['info']['gamma'] == pytest.approx(want['gamma'], abs=1e-5)
     np.testing.assert_array_equal(got['q8'][:, 5:], np.tile([1, 0, 0], (len(src), 1)))
 
 
@@ -74,7 +76,7 @@ def test_fit_converged_parity(emdq, orc, name):
     np.testing.assert_array_equal((got['c'] > 0)[sure], (want['c'] > 0)[sure])
     dpos = np.abs(_apply(got['q8'], _f32(src)) - _apply(want['q8'], _f32(src)))[want['c'] > 0].max()
     print(f'{name}: iters {got["info"]["iters"]} vs {want["iters"]}, inlier row diff {dpos:.2e} px')
-    assert dpos <= 2e-2
+    assert dpos <= 2e-3
 
 
 def test_fit_exact_similarity(emdq, orc):
