@@ -6,8 +6,10 @@
 //   E-step      every CTA computes all N posteriors redundantly into shared memory
 //               (identical inputs and reduction order, hence identical convergence
 //               decisions in every CTA without an extra barrier)
-//   M-step      warp w fits rows i = w, w + 8G, ...: FP32 products over j, FP64 sums
-//               (Eqs. 18-20 in 2-D closed form)                    -> q rows (global)
+//   M-step      warp w fits rows i = w, w + 8G, ...: FP32 products over j, per-lane FP32
+//               partials, cross-lane sums in compensated (two-sum) FP32, then the
+//               centring and the closed form of Eqs. 18-20 in FP64 for the CTA's 8 rows
+//               at once (one FP64 instruction serves 8 rows: GB300's FP64 pipe is narrow)
 //   barrier
 //   residuals   warp w computes the leave-one-out blend at x_j for its rows j, the blend
 //               taken relative to row j's own warp (exact: the blend is linear) to keep
@@ -86,7 +88,7 @@ __device__ bool grid_barrier(unsigned *bar, int *flag, unsigned &epoch)
                 timed_out = 1;
                 break;
             }
-            __nanosleep(64);
+            if (spins > 2048) __nanosleep(64);   // poll hot first, then back off
         }
         __threadfence();
     }
@@ -108,46 +110,90 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
-// M-step of row i (one warp).  Local coordinates a = x_j - x_i, b = y_j - y_i keep the
-// products small; per-lane FP32 partials, FP64 across lanes and for the centring.
-__device__ void mstep_row(const FitArgs &A, const FitSmem &S, int i, int lane)
+// Error-free sum of two floats (Knuth two-sum): a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Cross-lane sum of a float carried as an unevaluated pair hi + lo (every lane ends with
+// the same pair: the xor butterfly is symmetric).
+__device__ __forceinline__ void warp_sum_ff(float v, float &hi, float &lo)
+{
+    hi = v;
+    lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, oh, s, e);
+        e = __fadd_rn(e, __fadd_rn(lo, ol));
+        hi = __fadd_rn(s, e);
+        lo = __fsub_rn(e, __fsub_rn(hi, s));
+    }
+}
+
+constexpr int kMoments = 11;
+
+// M-step partial sums of row i (one warp).  Local coordinates a = x_j - x_i,
+// b = y_j - y_i keep the products small.  Lane 0 stores the 11 sums as (hi, lo) pairs.
+__device__ void mstep_sums(const FitArgs &A, const FitSmem &S, int i, int lane, float *out)
 {
     const int n = A.n;
     const float2 xi = S.x[i], yi = S.y[i];
-    float W = 0.f, ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f, aa = 0.f, bb = 0.f;
-    float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
+    float m[kMoments];
+#pragma unroll
+    for (int k = 0; k < kMoments; ++k) m[k] = 0.f;
     for (int j = lane; j < n; j += 32) {
         const float2 xj = S.x[j], yj = S.y[j];
         const float a0 = xj.x - xi.x, a1 = xj.y - xi.y;
         const float b0 = yj.x - yi.x, b1 = yj.y - yi.y;
-        const float om = S.p[j] * expf(-A.alpha * (a0 * a0 + a1 * a1));
-        W += om;
-        ax += om * a0;
-        ay += om * a1;
-        bx += om * b0;
-        by += om * b1;
-        aa += om * (a0 * a0 + a1 * a1);
-        bb += om * (b0 * b0 + b1 * b1);
-        s00 += om * b0 * a0;
-        s01 += om * b0 * a1;
-        s10 += om * b1 * a0;
-        s11 += om * b1 * a1;
+        const float aa = a0 * a0 + a1 * a1;
+        const float om = S.p[j] * expf(-A.alpha * aa);
+        m[0] += om;
+        m[1] += om * a0;
+        m[2] += om * a1;
+        m[3] += om * b0;
+        m[4] += om * b1;
+        m[5] += om * aa;
+        m[6] += om * (b0 * b0 + b1 * b1);
+        m[7] += om * b0 * a0;
+        m[8] += om * b0 * a1;
+        m[9] += om * b1 * a0;
+        m[10] += om * b1 * a1;
     }
-    const double dW = warp_sum_d(W);
-    const double dax = warp_sum_d(ax), day = warp_sum_d(ay);
-    const double dbx = warp_sum_d(bx), dby = warp_sum_d(by);
-    const double daa = warp_sum_d(aa), dbb = warp_sum_d(bb);
-    const double d00 = warp_sum_d(s00), d01 = warp_sum_d(s01);
-    const double d10 = warp_sum_d(s10), d11 = warp_sum_d(s11);
-    if (lane != 0) return;
+#pragma unroll
+    for (int k = 0; k < kMoments; ++k) {
+        float hi, lo;
+        warp_sum_ff(m[k], hi, lo);
+        if (lane == 0) {
+            out[k] = hi;
+            out[kMoments + k] = lo;
+        }
+    }
+}
+
+// FP64 centring and closed form of row i from its (hi, lo) sums; writes the q row.
+__device__ void mstep_finish(const FitArgs &A, const FitSmem &S, int i, const float *in)
+{
+    double m[kMoments];
+#pragma unroll
+    for (int k = 0; k < kMoments; ++k)
+        m[k] = static_cast<double>(in[k]) + static_cast<double>(in[kMoments + k]);
+    const float2 xi = S.x[i], yi = S.y[i];
     float row[5] = {1.f, 0.f, 0.f, 0.f, 1.f};
+    const double dW = m[0];
     bool ok = dW > 0.0;
     if (ok) {
-        const double xb0 = dax / dW, xb1 = day / dW, yb0 = dbx / dW, yb1 = dby / dW;
-        const double vx = daa - dW * (xb0 * xb0 + xb1 * xb1);   // |vector(C_0)|^2
-        const double vy = dbb - dW * (yb0 * yb0 + yb1 * yb1);   // |vector(C_t)|^2
-        const double S00 = d00 - dW * yb0 * xb0, S01 = d01 - dW * yb0 * xb1;
-        const double S10 = d10 - dW * yb1 * xb0, S11 = d11 - dW * yb1 * xb1;
+        const double iw = 1.0 / dW;
+        const double xb0 = m[1] * iw, xb1 = m[2] * iw, yb0 = m[3] * iw, yb1 = m[4] * iw;
+        const double vx = m[5] - dW * (xb0 * xb0 + xb1 * xb1);   // |vector(C_0)|^2
+        const double vy = m[6] - dW * (yb0 * yb0 + yb1 * yb1);   // |vector(C_t)|^2
+        const double S00 = m[7] - dW * yb0 * xb0, S01 = m[8] - dW * yb0 * xb1;
+        const double S10 = m[9] - dW * yb1 * xb0, S11 = m[10] - dW * yb1 * xb1;
         // Eq. 18 in 2-D: the rotation angle th maximising tr(R^T S) has direction
         // (S00 + S11, S10 - S01); its half angle (the DQ real part) is the direction of
         // (rho + a, b), or of (b, rho - a) when a < 0 (no cancellation either way).
@@ -271,8 +317,19 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
         gamma = fminf(fmaxf(static_cast<float>(bcast[0] / n), 0.05f), 0.95f);
     }
 
+    __shared__ float msum[kFitWarps][2 * kMoments];
     auto mstep_all = [&]() {
-        for (int i = gwarp; i < n; i += nwarps) mstep_row(A, S, i, lane);
+        const int rounds = (n + nwarps - 1) / nwarps;
+        for (int r = 0; r < rounds; ++r) {
+            const int i = gwarp + r * nwarps;
+            if (i < n) mstep_sums(A, S, i, lane, msum[warp]);
+            __syncthreads();
+            if (warp == 0 && lane < kFitWarps) {
+                const int ii = blockIdx.x * kFitWarps + lane + r * nwarps;
+                if (ii < n) mstep_finish(A, S, ii, msum[lane]);
+            }
+            __syncthreads();
+        }
     };
     // residuals for this CTA's rows + its partial sums; then barrier; then sigma^2
     auto residuals_and_sigma2 = [&](float &sigma2) -> bool {
@@ -305,15 +362,21 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
             __stcg(A.partials + 2 * blockIdx.x + 1, tps);
         }
         if (!grid_barrier(A.bar, A.flag, epoch)) return false;
-        if (threadIdx.x == 0) {
+        if (warp == 0) {
+            // lane-strided FP64 partial sums, then the symmetric butterfly: the same
+            // value, bit for bit, in every CTA
             double num = 0.0, den = 0.0;
-            for (int b = 0; b < (int)gridDim.x; ++b) {
+            for (int b = lane; b < (int)gridDim.x; b += 32) {
                 num += __ldcg(A.partials + 2 * b);
                 den += __ldcg(A.partials + 2 * b + 1);
             }
-            double s2 = den > 0.0 ? num / (2.0 * den) : A.sigma2_floor;
-            bcast[1] = s2 > A.sigma2_floor ? s2 : A.sigma2_floor;
-            s_flag = __ldcg(A.flag);
+            num = warp_sum_d(num);
+            den = warp_sum_d(den);
+            if (lane == 0) {
+                const double s2 = den > 0.0 ? num / (2.0 * den) : A.sigma2_floor;
+                bcast[1] = s2 > A.sigma2_floor ? s2 : A.sigma2_floor;
+                s_flag = __ldcg(A.flag);
+            }
         }
         __syncthreads();
         sigma2 = static_cast<float>(bcast[1]);
@@ -338,7 +401,7 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
         ++it;
         // E-step: every CTA, all N posteriors
         float dpmax = 0.f;
-        double psum = 0.0;
+        float psum = 0.f;
         const float norm = 1.f / (two_pi * sigma2);
         const float outl = (1.f - gamma) * A.inv_area;
         for (int j = threadIdx.x; j < n; j += kFitThreads) {
@@ -351,13 +414,13 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dpmax = fmaxf(dpmax, __shfl_xor_sync(0xffffffffu, dpmax, o));
-        psum = warp_sum_d(psum);
+        psum = warp_sum_f(psum);
         if (lane == 0) red[warp] = dpmax;
         __syncthreads();
         float dpall = 0.f;
         for (int k = 0; k < kFitWarps; ++k) dpall = fmaxf(dpall, static_cast<float>(red[k]));
         __syncthreads();
-        const double ptot = block_sum_ordered(psum, red);
+        const double ptot = block_sum_ordered(static_cast<double>(psum), red);
         if (threadIdx.x == 0) bcast[2] = ptot;
         __syncthreads();
         const float gamma_next =
