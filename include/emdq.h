@@ -90,8 +90,8 @@ int         emdq_abi_version(void);
  *   iterate   E-step: p_j = gamma G_j / (gamma G_j + (1-gamma)/(w h)),
  *               G_j = exp(-e_j / (2 sigma^2)) / (2 pi sigma^2)
  *             M-step: per match i the closed-form similarity of Eqs. 18-20 fitted to all
- *               matches with weights p_j exp(-alpha |x_i - x_j|^2) (products in FP32,
- *               accumulations in FP64)
+ *               matches with weights p_j exp(-alpha |x_i - x_j|^2) (two passes: the
+ *               weighted centroid, then the centred moments, so FP32 sums do not cancel)
  *             residuals e_j = |y_j - W_{-j}(x_j)|^2 of the leave-one-out blend (Eqs. 2-4)
  *             sigma^2 = max(sum p e / (2 sum p), floor), gamma = clamp(mean p, .05, .95)
  *   output    q_out rows, c_out[i] = p_i if p_i >= 1/2 else 0, p_out = p

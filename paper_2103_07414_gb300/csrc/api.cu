@@ -103,8 +103,8 @@ extern "C" emdq_status emdq_field(const float *q, const float *c, const float *s
     if (grid_w == 0 || grid_h == 0) return EMDQ_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float *ref = static_cast<float *>(workspace);
-    field_ref_kernel<<<1, kRefThreads, 0, st>>>(q, c, n, ref);
     if (precision == EMDQ_FP32) {
+        field_ref_kernel<<<1, kRefThreads, 0, st>>>(q, c, n, ref);
         if ((grid_h + 7) / 8 > 65535) return EMDQ_ENOTSUP;
         dim3 grid((grid_w + 31) / 32, (grid_h + 7) / 8);
         field_direct_kernel<<<grid, kDirectThreads, 0, st>>>(

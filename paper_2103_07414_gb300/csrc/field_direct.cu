@@ -17,36 +17,11 @@ __global__ void __launch_bounds__(kRefThreads) field_ref_kernel(const float *__r
                                                                 const float *__restrict__ c,
                                                                 int n, float *__restrict__ ref)
 {
-    __shared__ double red[kRefThreads / 32][6];
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int i = threadIdx.x; i < n; i += kRefThreads) {
-        const float ci = c[i];
-        if (!(ci > 0.f)) continue;
-        const float4 r0 = *reinterpret_cast<const float4 *>(q + 8 * (size_t)i);
-        const float r4 = q[8 * (size_t)i + 4];
-        acc[0] += ci * r0.x;
-        acc[1] += ci * r0.y;
-        acc[2] += ci * r0.z;
-        acc[3] += ci * r0.w;
-        acc[4] += ci * r4;
-        acc[5] += ci;
-    }
-    for (int k = 0; k < 6; ++k)
-        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-    if ((threadIdx.x & 31) == 0)
-        for (int k = 0; k < 6; ++k) red[threadIdx.x >> 5][k] = acc[k];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t[6] = {0, 0, 0, 0, 0, 0};
-        for (int w = 0; w < kRefThreads / 32; ++w)
-            for (int k = 0; k < 6; ++k) t[k] += red[w][k];
-        if (t[5] > 0.0) {
-            for (int k = 0; k < 5; ++k) ref[k] = static_cast<float>(t[k] / t[5]);
-        } else {
-            ref[0] = 1.f; ref[1] = 0.f; ref[2] = 0.f; ref[3] = 0.f; ref[4] = 1.f;
-        }
-        ref[5] = t[5] > 0.0 ? 1.f : 0.f;   // 0 marks "no weight anywhere"
-    }
+    __shared__ float red[6 * 32];
+    float r[6];
+    reference_row(q, c, n, red, r);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; ++k) ref[k] = r[k];
 }
 
 // One thread per pixel of a 32 x 8 tile; matches in chunks of kDirectChunk through smem.

@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include "field.cuh"
 #include "field_tc.cuh"
 #include "tc_ptx.cuh"
 
@@ -69,10 +70,15 @@ __host__ __device__ inline TcGeom tc_geom(int n, int gw, int gh)
 __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
     const float *__restrict__ q, const float *__restrict__ c, const float2 *__restrict__ src,
     int n, int kp, int gx0, int gy0, int gw, int gh, int wp, int hp, float alpha,
-    const float *__restrict__ ref, __nv_bfloat162 *__restrict__ A, __nv_bfloat162 *__restrict__ B,
+    float *__restrict__ ref_out, __nv_bfloat162 *__restrict__ A, __nv_bfloat162 *__restrict__ B,
     int a_blocks)
 {
     const int half = kp / 2;
+    __shared__ float red[6 * 32];
+    float ref[6];
+    reference_row(q, c, n, red, ref);      // same bits in every block
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int k = 0; k < 6; ++k) ref_out[k] = ref[k];
     if ((int)blockIdx.x < a_blocks) {
         const int r0 = blockIdx.x * kPrepRows;
         for (int k2 = threadIdx.x; k2 < half; k2 += kPrepThreads) {
@@ -91,9 +97,7 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
         }
     } else {
         const int r0 = (blockIdx.x - a_blocks) * kPrepRows;
-        float rf[5];
-#pragma unroll
-        for (int ch = 0; ch < 5; ++ch) rf[ch] = ref[ch];
+        const float *rf = ref;
         for (int k2 = threadIdx.x; k2 < half; k2 += kPrepThreads) {
             const int k0 = 2 * k2;
             float y[2] = {0.f, 0.f}, cw[2] = {0.f, 0.f}, cq[2][5];
@@ -290,7 +294,7 @@ size_t field_tc_workspace_bytes(int n, int grid_w, int grid_h)
 }
 
 emdq_status field_tc_launch(const float *q, const float *c, const float *src, int n, int gx0,
-                            int gy0, int gw, int gh, float alpha, const float *ref, float2 *disp,
+                            int gy0, int gw, int gh, float alpha, float *ref, float2 *disp,
                             char *ws, size_t ws_bytes, cudaStream_t st)
 {
     const DeviceInfo &D = device_info();

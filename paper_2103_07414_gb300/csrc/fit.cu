@@ -6,10 +6,12 @@
 //   E-step      every CTA computes all N posteriors redundantly into shared memory
 //               (identical inputs and reduction order, hence identical convergence
 //               decisions in every CTA without an extra barrier)
-//   M-step      warp w fits rows i = w, w + 8G, ...: FP32 products over j, per-lane FP32
-//               partials, cross-lane sums in compensated (two-sum) FP32, then the
-//               centring and the closed form of Eqs. 18-20 in FP64 for the CTA's 8 rows
-//               at once (one FP64 instruction serves 8 rows: GB300's FP64 pipe is narrow)
+//   M-step      warp w fits rows i = w, w + 8G, ...  The weighted similarity fit needs
+//               the centred second moments of Eqs. 18-19; accumulating raw moments and
+//               centring afterwards cancels catastrophically (it is why an FP64 finish
+//               would be needed).  Instead two passes over j: the weighted centroid,
+//               then the moments about it, so nothing cancels and FP32 products and sums
+//               suffice (local coordinates x_j - x_i, y_j - y_i keep the values small).
 //   barrier
 //   residuals   warp w computes the leave-one-out blend at x_j for its rows j, the blend
 //               taken relative to row j's own warp (exact: the blend is linear) to keep
@@ -43,7 +45,7 @@ struct FitArgs {
     float *p_out;
     emdq_fit_info *info;
     float *e;            // n residuals^2 (workspace)
-    double *partials;    // gridDim.x x 2 (workspace)
+    float *partials;     // gridDim.x float2 partial sums (workspace)
     unsigned *bar;       // barrier arrival counter, zero at launch (workspace)
     int *flag;           // device status, zero at launch (workspace)
 };
@@ -96,13 +98,6 @@ __device__ bool grid_barrier(unsigned *bar, int *flag, unsigned &epoch)
     return !timed_out;
 }
 
-__device__ __forceinline__ double warp_sum_d(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 __device__ __forceinline__ float warp_sum_f(float v)
 {
 #pragma unroll
@@ -110,94 +105,58 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
-// Error-free sum of two floats (Knuth two-sum): a + b = s + e exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// Cross-lane sum of a float carried as an unevaluated pair hi + lo (every lane ends with
-// the same pair: the xor butterfly is symmetric).
-__device__ __forceinline__ void warp_sum_ff(float v, float &hi, float &lo)
-{
-    hi = v;
-    lo = 0.f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
-        const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
-        float s, e;
-        two_sum(hi, oh, s, e);
-        e = __fadd_rn(e, __fadd_rn(lo, ol));
-        hi = __fadd_rn(s, e);
-        lo = __fsub_rn(e, __fsub_rn(hi, s));
-    }
-}
-
-constexpr int kMoments = 11;
-
-// M-step partial sums of row i (one warp).  Local coordinates a = x_j - x_i,
-// b = y_j - y_i keep the products small.  Lane 0 stores the 11 sums as (hi, lo) pairs.
-__device__ void mstep_sums(const FitArgs &A, const FitSmem &S, int i, int lane, float *out)
+// M-step of row i (one warp): weights om_j = p_j exp(-alpha |x_j - x_i|^2).
+// Pass 1: W, the weighted centroids (local coordinates a = x_j - x_i, b = y_j - y_i).
+// Pass 2: the centred moments |a - abar|^2, |b - bbar|^2 and (b - bbar)(a - abar)^T.
+// Then Eq. 18 (rotation, 2-D closed form), Eq. 19 (norm ratio), Eq. 20 (translation).
+__device__ void mstep_row(const FitArgs &A, const FitSmem &S, int i, int lane)
 {
     const int n = A.n;
     const float2 xi = S.x[i], yi = S.y[i];
-    float m[kMoments];
-#pragma unroll
-    for (int k = 0; k < kMoments; ++k) m[k] = 0.f;
+    float W = 0.f, sa0 = 0.f, sa1 = 0.f, sb0 = 0.f, sb1 = 0.f;
     for (int j = lane; j < n; j += 32) {
         const float2 xj = S.x[j], yj = S.y[j];
         const float a0 = xj.x - xi.x, a1 = xj.y - xi.y;
-        const float b0 = yj.x - yi.x, b1 = yj.y - yi.y;
-        const float aa = a0 * a0 + a1 * a1;
-        const float om = S.p[j] * expf(-A.alpha * aa);
-        m[0] += om;
-        m[1] += om * a0;
-        m[2] += om * a1;
-        m[3] += om * b0;
-        m[4] += om * b1;
-        m[5] += om * aa;
-        m[6] += om * (b0 * b0 + b1 * b1);
-        m[7] += om * b0 * a0;
-        m[8] += om * b0 * a1;
-        m[9] += om * b1 * a0;
-        m[10] += om * b1 * a1;
+        const float om = S.p[j] * expf(-A.alpha * (a0 * a0 + a1 * a1));
+        W += om;
+        sa0 += om * a0;
+        sa1 += om * a1;
+        sb0 += om * (yj.x - yi.x);
+        sb1 += om * (yj.y - yi.y);
     }
-#pragma unroll
-    for (int k = 0; k < kMoments; ++k) {
-        float hi, lo;
-        warp_sum_ff(m[k], hi, lo);
-        if (lane == 0) {
-            out[k] = hi;
-            out[kMoments + k] = lo;
-        }
-    }
-}
-
-// FP64 centring and closed form of row i from its (hi, lo) sums; writes the q row.
-__device__ void mstep_finish(const FitArgs &A, const FitSmem &S, int i, const float *in)
-{
-    double m[kMoments];
-#pragma unroll
-    for (int k = 0; k < kMoments; ++k)
-        m[k] = static_cast<double>(in[k]) + static_cast<double>(in[kMoments + k]);
-    const float2 xi = S.x[i], yi = S.y[i];
+    W = warp_sum_f(W);
+    sa0 = warp_sum_f(sa0);
+    sa1 = warp_sum_f(sa1);
+    sb0 = warp_sum_f(sb0);
+    sb1 = warp_sum_f(sb1);
     float row[5] = {1.f, 0.f, 0.f, 0.f, 1.f};
-    const double dW = m[0];
-    bool ok = dW > 0.0;
+    bool ok = W > 0.f && isfinite(W);
     if (ok) {
-        const double iw = 1.0 / dW;
-        const double xb0 = m[1] * iw, xb1 = m[2] * iw, yb0 = m[3] * iw, yb1 = m[4] * iw;
-        const double vx = m[5] - dW * (xb0 * xb0 + xb1 * xb1);   // |vector(C_0)|^2
-        const double vy = m[6] - dW * (yb0 * yb0 + yb1 * yb1);   // |vector(C_t)|^2
-        const double S00 = m[7] - dW * yb0 * xb0, S01 = m[8] - dW * yb0 * xb1;
-        const double S10 = m[9] - dW * yb1 * xb0, S11 = m[10] - dW * yb1 * xb1;
-        // Eq. 18 in 2-D: the rotation angle th maximising tr(R^T S) has direction
-        // (S00 + S11, S10 - S01); its half angle (the DQ real part) is the direction of
-        // (rho + a, b), or of (b, rho - a) when a < 0 (no cancellation either way).
-        const float a = static_cast<float>(S00 + S11), b = static_cast<float>(S10 - S01);
+        const float ab0 = sa0 / W, ab1 = sa1 / W, bb0 = sb0 / W, bb1 = sb1 / W;
+        float vx = 0.f, vy = 0.f, c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
+        for (int j = lane; j < n; j += 32) {
+            const float2 xj = S.x[j], yj = S.y[j];
+            const float a0 = xj.x - xi.x, a1 = xj.y - xi.y;
+            const float om = S.p[j] * expf(-A.alpha * (a0 * a0 + a1 * a1));
+            const float u0 = a0 - ab0, u1 = a1 - ab1;
+            const float v0 = (yj.x - yi.x) - bb0, v1 = (yj.y - yi.y) - bb1;
+            vx += om * (u0 * u0 + u1 * u1);     // |vector(C_0)|^2
+            vy += om * (v0 * v0 + v1 * v1);     // |vector(C_t)|^2
+            c00 += om * v0 * u0;                // C_t C_0^T
+            c01 += om * v0 * u1;
+            c10 += om * v1 * u0;
+            c11 += om * v1 * u1;
+        }
+        vx = warp_sum_f(vx);
+        vy = warp_sum_f(vy);
+        c00 = warp_sum_f(c00);
+        c01 = warp_sum_f(c01);
+        c10 = warp_sum_f(c10);
+        c11 = warp_sum_f(c11);
+        // Eq. 18 in 2-D: the rotation angle th maximising tr(R^T C_t C_0^T) has direction
+        // (a, b) = (c00 + c11, c10 - c01); its half angle (the DQ real part) is the
+        // direction of (rho + a, b), or of (b, rho - a) when a < 0 (no cancellation).
+        const float a = c00 + c11, b = c10 - c01;
         const float rho = hypotf(a, b);
         float h0, h1;
         if (a >= 0.f) { h0 = rho + a; h1 = b; }
@@ -207,14 +166,14 @@ __device__ void mstep_finish(const FitArgs &A, const FitSmem &S, int i, const fl
         float c = 1.f, sn = 0.f;
         if (hn > 0.f) { c = h0 / hn; sn = h1 / hn; }
         // Eq. 19: norm ratio
-        const float sc = sqrtf(static_cast<float>(vy) / static_cast<float>(vx));
+        const float sc = sqrtf(vy / vx);
         // Eq. 20: t = ybar / s - R xbar in global coordinates
         const float ct = c * c - sn * sn, st = 2.f * c * sn;
-        const float xg0 = xi.x + static_cast<float>(xb0), xg1 = xi.y + static_cast<float>(xb1);
-        const float yg0 = yi.x + static_cast<float>(yb0), yg1 = yi.y + static_cast<float>(yb1);
+        const float xg0 = xi.x + ab0, xg1 = xi.y + ab1;
+        const float yg0 = yi.x + bb0, yg1 = yi.y + bb1;
         const float tx = yg0 / sc - (ct * xg0 - st * xg1);
         const float ty = yg1 / sc - (st * xg0 + ct * xg1);
-        ok = vx > 0.0 && isfinite(sc) && isfinite(tx) && isfinite(ty);
+        ok = vx > 0.f && isfinite(sc) && isfinite(tx) && isfinite(ty);
         if (ok) {
             row[0] = c;
             row[1] = sn;
@@ -223,6 +182,7 @@ __device__ void mstep_finish(const FitArgs &A, const FitSmem &S, int i, const fl
             row[4] = sc;
         }
     }
+    if (lane != 0) return;
     if (!ok) raise_status(A.flag, EMDQ_EDEGENERATE);
     float4 *dst = reinterpret_cast<float4 *>(A.q_out + 8 * (size_t)i);
     __stcg(dst, make_float4(row[0], row[1], row[2], row[3]));
@@ -263,17 +223,33 @@ __device__ float residual_row(const FitArgs &A, const FitSmem &S, int j, int lan
     return r0 * r0 + r1 * r1;
 }
 
-// Sum of per-warp doubles in warp order (deterministic); result valid in thread 0.
-__device__ double block_sum_ordered(double v, double *red)
+// Block-wide sums of two floats in a fixed order: warp butterflies, then every thread
+// adds the 8 warp totals in warp order, so every thread (and every CTA, given the same
+// inputs) holds the same bits.
+__device__ float2 block_sum2(float a, float b, float2 *red)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) red[w] = v;
+    a = warp_sum_f(a);
+    b = warp_sum_f(b);
+    if (lane == 0) red[w] = make_float2(a, b);
     __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < kFitWarps; ++k) s += red[k];
+    float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < kFitWarps; ++k) {
+        t.x += red[k].x;
+        t.y += red[k].y;
+    }
     __syncthreads();
-    return s;
+    return t;
+}
+
+// Grid barrier, then the device status word as every thread of every CTA sees it.
+__device__ int barrier_status(const FitArgs &A, unsigned &epoch, int *s_flag)
+{
+    const bool ok = grid_barrier(A.bar, A.flag, epoch);
+    if (threadIdx.x == 0) *s_flag = ok ? __ldcg(A.flag) : (int)EMDQ_ETIMEOUT;
+    __syncthreads();
+    return *s_flag;
 }
 
 __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
@@ -282,20 +258,20 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
     const FitSmem S = fit_smem(n);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gwarp = blockIdx.x * kFitWarps + warp, nwarps = gridDim.x * kFitWarps;
-    __shared__ double red[kFitWarps];
-    __shared__ double bcast[4];
+    __shared__ float2 red[kFitWarps];
     __shared__ int s_flag;
     unsigned epoch = 0;
 
     // stage the matches and the initial weights; every CTA checks every input
     int bad = 0;
-    double p0sum = 0.0;
+    float p0sum = 0.f;
     for (int j = threadIdx.x; j < n; j += kFitThreads) {
         const float2 x = A.src[j], y = A.dst[j];
         S.x[j] = x;
         S.y[j] = y;
         const float p = A.p0 ? A.p0[j] : 1.f;
         S.p[j] = p;
+        p0sum += p;
         bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(y.x) && isfinite(y.y) && isfinite(p));
     }
     bad = __syncthreads_or(bad);
@@ -307,101 +283,62 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
         return;
     }
     float gamma = 0.5f;
-    if (A.p0) {
-        for (int j = threadIdx.x; j < n; j += kFitThreads) p0sum += S.p[j];
-        // per-warp partials then warp-ordered sum: identical in every CTA
-        p0sum = warp_sum_d(p0sum);
-        const double tot = block_sum_ordered(p0sum, red);
-        if (threadIdx.x == 0) bcast[0] = tot;
-        __syncthreads();
-        gamma = fminf(fmaxf(static_cast<float>(bcast[0] / n), 0.05f), 0.95f);
-    }
+    if (A.p0) gamma = fminf(fmaxf(block_sum2(p0sum, 0.f, red).x / n, 0.05f), 0.95f);
 
-    __shared__ float msum[kFitWarps][2 * kMoments];
-    auto mstep_all = [&]() {
-        const int rounds = (n + nwarps - 1) / nwarps;
-        for (int r = 0; r < rounds; ++r) {
-            const int i = gwarp + r * nwarps;
-            if (i < n) mstep_sums(A, S, i, lane, msum[warp]);
-            __syncthreads();
-            if (warp == 0 && lane < kFitWarps) {
-                const int ii = blockIdx.x * kFitWarps + lane + r * nwarps;
-                if (ii < n) mstep_finish(A, S, ii, msum[lane]);
-            }
-            __syncthreads();
-        }
-    };
-    // residuals for this CTA's rows + its partial sums; then barrier; then sigma^2
-    auto residuals_and_sigma2 = [&](float &sigma2) -> bool {
-        // every CTA needs all q rows in shared memory
+    // residuals of this CTA's rows and its partial sums; barrier; sigma^2 (each warp
+    // reduces the per-CTA partials itself, in the same order)
+    auto residuals_and_sigma2 = [&](float &sigma2) -> int {
         for (int i = threadIdx.x; i < n; i += kFitThreads) {
             const float4 r0 = __ldcg(reinterpret_cast<const float4 *>(A.q_out + 8 * (size_t)i));
-            const float4 r1 = __ldcg(reinterpret_cast<const float4 *>(A.q_out + 8 * (size_t)i) + 1);
+            const float r4 = __ldcg(A.q_out + 8 * (size_t)i + 4);
             S.qa[i] = r0.x;
             S.qb[i] = r0.y;
             S.qu[i] = r0.z;
             S.qv[i] = r0.w;
-            S.qs[i] = r1.x;
+            S.qs[i] = r4;
         }
         __syncthreads();
-        double pe = 0.0, ps = 0.0;
+        float pe = 0.f, ps = 0.f;
         for (int j = gwarp; j < n; j += nwarps) {
             const float e = residual_row(A, S, j, lane);
             if (lane == 0) {
                 __stcg(A.e + j, e);
                 if (isfinite(e)) {
-                    pe += static_cast<double>(S.p[j]) * e;
+                    pe += S.p[j] * e;
                     ps += S.p[j];
                 }
             }
         }
-        const double tpe = block_sum_ordered(pe, red);
-        const double tps = block_sum_ordered(ps, red);
-        if (threadIdx.x == 0) {
-            __stcg(A.partials + 2 * blockIdx.x, tpe);
-            __stcg(A.partials + 2 * blockIdx.x + 1, tps);
+        const float2 t = block_sum2(lane == 0 ? pe : 0.f, lane == 0 ? ps : 0.f, red);
+        if (threadIdx.x == 0) __stcg(reinterpret_cast<float2 *>(A.partials) + blockIdx.x, t);
+        const int st = barrier_status(A, epoch, &s_flag);
+        if (st >= EMDQ_EDEGENERATE) return st;
+        float num = 0.f, den = 0.f;
+        for (int b = lane; b < (int)gridDim.x; b += 32) {
+            const float2 v = __ldcg(reinterpret_cast<const float2 *>(A.partials) + b);
+            num += v.x;
+            den += v.y;
         }
-        if (!grid_barrier(A.bar, A.flag, epoch)) return false;
-        if (warp == 0) {
-            // lane-strided FP64 partial sums, then the symmetric butterfly: the same
-            // value, bit for bit, in every CTA
-            double num = 0.0, den = 0.0;
-            for (int b = lane; b < (int)gridDim.x; b += 32) {
-                num += __ldcg(A.partials + 2 * b);
-                den += __ldcg(A.partials + 2 * b + 1);
-            }
-            num = warp_sum_d(num);
-            den = warp_sum_d(den);
-            if (lane == 0) {
-                const double s2 = den > 0.0 ? num / (2.0 * den) : A.sigma2_floor;
-                bcast[1] = s2 > A.sigma2_floor ? s2 : A.sigma2_floor;
-                s_flag = __ldcg(A.flag);
-            }
-        }
-        __syncthreads();
-        sigma2 = static_cast<float>(bcast[1]);
-        return s_flag < EMDQ_EDEGENERATE;
+        num = warp_sum_f(num);
+        den = warp_sum_f(den);
+        const float s2 = den > 0.f ? num / (2.f * den) : A.sigma2_floor;
+        sigma2 = fmaxf(s2, A.sigma2_floor);
+        return st;
     };
 
     // step 0
     float sigma2 = A.sigma2_floor;
-    mstep_all();
-    bool alive = grid_barrier(A.bar, A.flag, epoch);
-    if (alive) {
-        if (threadIdx.x == 0) s_flag = __ldcg(A.flag);
-        __syncthreads();
-        alive = s_flag < EMDQ_EDEGENERATE;
-    }
-    if (alive) alive = residuals_and_sigma2(sigma2);
+    for (int i = gwarp; i < n; i += nwarps) mstep_row(A, S, i, lane);
+    int st = barrier_status(A, epoch, &s_flag);
+    if (st < EMDQ_EDEGENERATE) st = residuals_and_sigma2(sigma2);
 
     int it = 0;
     bool converged = false;
     const float two_pi = 6.28318530717958647692f;
-    while (alive && it < A.max_iters) {
+    while (st < EMDQ_EDEGENERATE && it < A.max_iters) {
         ++it;
         // E-step: every CTA, all N posteriors
-        float dpmax = 0.f;
-        float psum = 0.f;
+        float dpmax = 0.f, psum = 0.f;
         const float norm = 1.f / (two_pi * sigma2);
         const float outl = (1.f - gamma) * A.inv_area;
         for (int j = threadIdx.x; j < n; j += kFitThreads) {
@@ -415,25 +352,20 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dpmax = fmaxf(dpmax, __shfl_xor_sync(0xffffffffu, dpmax, o));
         psum = warp_sum_f(psum);
-        if (lane == 0) red[warp] = dpmax;
+        if (lane == 0) red[warp] = make_float2(dpmax, psum);
         __syncthreads();
-        float dpall = 0.f;
-        for (int k = 0; k < kFitWarps; ++k) dpall = fmaxf(dpall, static_cast<float>(red[k]));
-        __syncthreads();
-        const double ptot = block_sum_ordered(static_cast<double>(psum), red);
-        if (threadIdx.x == 0) bcast[2] = ptot;
-        __syncthreads();
-        const float gamma_next =
-            fminf(fmaxf(static_cast<float>(bcast[2] / n), 0.05f), 0.95f);
-        // M-step with the new weights
-        mstep_all();
-        alive = grid_barrier(A.bar, A.flag, epoch);
-        if (alive) {
-            if (threadIdx.x == 0) s_flag = __ldcg(A.flag);
-            __syncthreads();
-            alive = s_flag < EMDQ_EDEGENERATE;
+        float dpall = 0.f, ptot = 0.f;
+#pragma unroll
+        for (int k = 0; k < kFitWarps; ++k) {
+            dpall = fmaxf(dpall, red[k].x);
+            ptot += red[k].y;
         }
-        if (alive) alive = residuals_and_sigma2(sigma2);
+        __syncthreads();
+        const float gamma_next = fminf(fmaxf(ptot / n, 0.05f), 0.95f);
+        // M-step with the new weights, then residuals and sigma^2
+        for (int i = gwarp; i < n; i += nwarps) mstep_row(A, S, i, lane);
+        st = barrier_status(A, epoch, &s_flag);
+        if (st < EMDQ_EDEGENERATE) st = residuals_and_sigma2(sigma2);
         gamma = gamma_next;
         if (dpall < A.tol) {
             converged = true;
@@ -448,12 +380,12 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
             if (A.p_out) A.p_out[j] = p;
         }
         if (threadIdx.x == 0) {
-            const int f = __ldcg(A.flag);
-            int st = EMDQ_OK;
-            if (f == EMDQ_ETIMEOUT) st = EMDQ_ETIMEOUT;
-            else if (f == EMDQ_EDEGENERATE) st = EMDQ_EDEGENERATE;
-            else if (!converged) st = EMDQ_ENOCONV;
-            A.info->status = st;
+            const int f = st >= EMDQ_EDEGENERATE ? st : __ldcg(A.flag);
+            int out = EMDQ_OK;
+            if (f == EMDQ_ETIMEOUT) out = EMDQ_ETIMEOUT;
+            else if (f == EMDQ_EDEGENERATE) out = EMDQ_EDEGENERATE;
+            else if (!converged) out = EMDQ_ENOCONV;
+            A.info->status = out;
             A.info->iters = it;
             A.info->sigma2 = sigma2;
             A.info->gamma = gamma;
@@ -551,7 +483,7 @@ extern "C" emdq_status emdq_fit(const float *src, const float *dst, int n, int f
     A.p_out = p_out;
     A.info = info;
     A.e = reinterpret_cast<float *>(ws + L.e_off);
-    A.partials = reinterpret_cast<double *>(ws + L.part_off);
+    A.partials = reinterpret_cast<float *>(ws + L.part_off);
     A.bar = reinterpret_cast<unsigned *>(ws + L.bar_off);
     A.flag = reinterpret_cast<int *>(ws + L.bar_off + 64);
 
@@ -568,3 +500,4 @@ extern "C" emdq_status emdq_fit(const float *src, const float *dst, int n, int f
     if (cudaLaunchKernelEx(&cfg, emdq_fit_kernel, A) != cudaSuccess) return EMDQ_ECUDA;
     return EMDQ_OK;
 }
+
