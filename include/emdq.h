@@ -116,6 +116,31 @@ emdq_status emdq_fit(const float *src, const float *dst, int n, int frame_w, int
                      float *p_out, emdq_fit_info *info, void *workspace,
                      size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------------------------ emdq_fit_noalloc -
+ * emdq_fit for callers that cannot allocate device memory.  The paper has no counterpart:
+ * this is a deployment variant.  Some callers must not call cudaMalloc once they are
+ * running -- a real-time video loop (cudaMalloc can stall the whole device while it
+ * runs), a plug-in inside a host application that owns every device allocation through
+ * its own pool, or a service whose memory is fixed at start-up -- and so cannot provide
+ * the workspace emdq_fit asks for.  This entry point takes the same inputs and outputs
+ * (all still allocated by the caller) and keeps its scratch in a fixed array of about
+ * 37 KB inside the library, which every GPU that loads the library holds until exit.
+ *
+ *   - n must be at most 5120 (emdq_fit_max_n()); larger n returns EMDQ_ENOTSUP.
+ *   - It allocates nothing and calls no allocating routine.  Its first call on each device
+ *     looks up the array's device address once (cudaGetSymbolAddress, with that device
+ *     current); make that first call before any stream capture.
+ *   - Every call shares the one array, which keeps the previous call's contents (the
+ *     parts that must start at zero are cleared on the call's stream).  Calls that can
+ *     overlap on the GPU -- on different streams, or on different host threads -- race on
+ *     that array: serialise them (for example, issue them all on one stream).
+ * Arguments, results and errors are those of emdq_fit.
+ */
+emdq_status emdq_fit_noalloc(const float *src, const float *dst, int n, int frame_w,
+                             int frame_h, const emdq_params *prm, const float *p0,
+                             float *q_out, float *c_out, float *p_out, emdq_fit_info *info,
+                             void *stream);
+
 /* ------------------------------------------------------------------ emdq_field -------
  * Dense displacement field (Eqs. 2-4 with Eq. 1): for every pixel p of the grid
  * [grid_x0, grid_x0 + grid_w) x [grid_y0, grid_y0 + grid_h) (reference coordinates),

@@ -501,3 +501,50 @@ extern "C" emdq_status emdq_fit(const float *src, const float *dst, int n, int f
     return EMDQ_OK;
 }
 
+// ------------------------------------------------------------------ emdq_fit_noalloc ---
+// The same fit for callers that must not allocate device memory: its scratch (residuals,
+// per-CTA partial sums, barrier counter, status word) lives in one fixed array in this
+// library's device memory, sized for the largest fit (kFitMaxN matches), instead of a
+// caller workspace.  Every GPU that loads the library holds the array until exit.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes =
+    ((sizeof(float) * kFitMaxN + 255) / 256) * 256 +          // residuals
+    ((sizeof(double) * 2 * kFitMaxGrid + 255) / 256) * 256 +  // per-CTA partial sums
+    256;                                                       // barrier counter, status
+
+static __device__ __align__(256) unsigned char g_fit_scratch[kNoAllocScratchBytes];
+
+// Device address of g_fit_scratch on the current device.  In host code the array's name
+// is only a host-side stand-in, so the address is asked of the runtime once per device,
+// with that device current, and cached.
+void *noalloc_scratch()
+{
+    static std::mutex mu;
+    static void *addr[64] = {};
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_fit_scratch) != cudaSuccess || !p) return nullptr;
+        addr[dev] = p;
+    }
+    return addr[dev];
+}
+
+}  // namespace
+
+extern "C" emdq_status emdq_fit_noalloc(const float *src, const float *dst, int n, int frame_w,
+                                        int frame_h, const emdq_params *prm, const float *p0,
+                                        float *q_out, float *c_out, float *p_out,
+                                        emdq_fit_info *info, void *stream)
+{
+    if (n > kFitMaxN) return EMDQ_ENOTSUP;   // beyond the fixed scratch array
+    if (fit_layout(n).total > kNoAllocScratchBytes) return EMDQ_ENOTSUP;
+    void *ws = noalloc_scratch();
+    if (!ws) return EMDQ_ECUDA;
+    // emdq_fit clears the barrier counter and status word before its launch
+    return emdq_fit(src, dst, n, frame_w, frame_h, prm, p0, q_out, c_out, p_out, info, ws,
+                    kNoAllocScratchBytes, stream);
+}
