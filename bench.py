@@ -1,10 +1,11 @@
 #!/usr/bin/env python3
 """Benchmark of the EMDQ hot path: per frame, emdq_fit -> emdq_field -> mosaic_warp.
 
-Workload (default): the 1280x1024 RGB8 synthetic laparoscopy sequence, N = 1000 matches
-per frame with 30% outliers and 1.5 px noise, deformation bumps drifting 2 px/frame,
-blended into a 4096x4096 RGBW canvas.  One step = one frame through all three calls.
-Metric: frame pixels per second (Mpix/s) and the median frame latency.
+Workload (default): the 100-frame 1280x1024 RGB8 synthetic laparoscopy sequence, N = 1000
+matches per frame with 30% outliers and 1.5 px noise, deformation bumps drifting
+2 px/frame, blended into a 4096x4096 RGBW canvas.  One step = one pass over the whole
+sequence, every frame through all three calls in order.  Metric: frame pixels per second
+(Mpix/s) and the median frame latency.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
     python bench.py --impl reference ...   # the FP64 C oracle on the host cores
@@ -46,14 +47,18 @@ def _src_hash(name: str) -> str:
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
-    ap.add_argument('--steps', type=int, default=30)
-    ap.add_argument('--warmup', type=int, default=5)
+    ap.add_argument('--steps', type=int, default=20)
+    ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='emdq', choices=['emdq', 'reference'])
     ap.add_argument('--precision', default='bf16', choices=['bf16', 'fp32'])
     ap.add_argument('--workload', default='seq1280')
     ap.add_argument('--seed', type=int, default=0)
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
+    ap.add_argument('--batch', type=int, default=8,
+                    help='frames whose EM fits share one launch (1: one emdq_fit per frame)')
+    ap.add_argument('--unfused', action='store_true',
+                    help='BF16 field and warp as two calls (default: one fused emdq_mosaic call)')
     return ap.parse_args()
 
 
@@ -78,6 +83,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.path = None
+        self.period_ms = 20
 
     def start(self):
         try:
@@ -85,7 +91,7 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ['nvidia-smi', f'--id={self.index}', f'--query-gpu={self.Q}', '--format=csv,noheader,nounits',
-                 '-lms', '200'], stdout=open(self.path, 'w'), stderr=subprocess.DEVNULL)
+                 '-lms', str(self.period_ms)], stdout=open(self.path, 'w'), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -163,7 +169,8 @@ def run_gpu(args, ws, rank, local):
         import torch.distributed as dist
         dist.init_process_group('nccl', device_id=dev)
     prec = emdq.BF16 if args.precision == 'bf16' else emdq.FP32
-    n_frames = args.warmup + args.steps
+    from synth import WORKLOADS
+    n_frames = WORKLOADS[args.workload]['frames']
     sc, cfg, origin, ref, frames, src, dst, grids = prepare_sequence(
         args.workload, args.seed + 1000 * rank, n_frames, dev)
     cw, chh = cfg['canvas']
@@ -180,92 +187,141 @@ def run_gpu(args, ws, rank, local):
                            device=dev)
     disp_buf = torch.empty(max_gw * max_gh * 2, dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    infos = torch.zeros((n_frames, 4), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(k, ev=None):
-        g = grids[k]
-        disp = disp_buf[: g[2] * g[3] * 2].view(g[3], g[2], 2)
-        if ev: ev[0].record(stream)
-        emdq.emdq_fit(src[k], dst[k], sc.w, sc.h, out=fit_out, workspace=fit_ws)
-        if ev: ev[1].record(stream)
-        emdq.emdq_field(fit_out['q'], fit_out['c'], src[k], g, alpha, precision=prec, out=disp,
-                        workspace=field_ws)
-        if ev: ev[2].record(stream)
-        emdq.mosaic_warp(frames[k], disp, g, canvas, origin)
-        if ev: ev[3].record(stream)
+    fused = prec == emdq.BF16 and not args.unfused
+    B = max(1, min(args.batch, 64))
+    fit_outs = [dict(q=torch.empty((n, 8), device=dev), c=torch.empty(n, device=dev),
+                     p=torch.empty(n, device=dev), info=torch.zeros(4, dtype=torch.int32, device=dev))
+                for _ in range(B)]
+    batch_ws = torch.empty(max(256, emdq.fit_batch_workspace_size([(src[0], dst[0])] * B)),
+                           dtype=torch.uint8, device=dev)
 
-    for k in range(args.warmup):
+    def field_and_warp(fr, s_, g, fo):
+        if fused:
+            emdq.emdq_mosaic(fo['q'], fo['c'], s_, g, alpha, fr, canvas, origin, workspace=field_ws)
+        else:
+            disp = disp_buf[: g[2] * g[3] * 2].view(g[3], g[2], 2)
+            emdq.emdq_field(fo['q'], fo['c'], s_, g, alpha, precision=prec, out=disp,
+                            workspace=field_ws)
+            emdq.mosaic_warp(fr, disp, g, canvas, origin)
+
+    def run_batch(ks, fr_of, s_of, d_of, ev=None):
+        """Frames ks (in order): their fits, then their mosaic updates in frame order.
+        ev: [start, after fit(s), after each frame's field+warp...]"""
+        if ev: ev[0].record(stream)
+        if B == 1:
+            emdq.emdq_fit(s_of(ks[0]), d_of(ks[0]), sc.w, sc.h, out=fit_outs[0], workspace=fit_ws)
+        else:
+            emdq.emdq_fit_batch([(s_of(k), d_of(k), sc.w, sc.h) for k in ks],
+                                outs=fit_outs[: len(ks)], workspace=batch_ws)
+        if ev: ev[1].record(stream)
+        for j, k in enumerate(ks):
+            field_and_warp(fr_of(k), s_of(k), grids[k], fit_outs[j])
+            if ev: ev[2 + j].record(stream)
+        for j, k in enumerate(ks):
+            infos[k].copy_(fit_outs[j]['info'])
+
+    batches = [list(range(k0, min(n_frames, k0 + B))) for k0 in range(0, n_frames, B)]
+
+    def one_pass(evs=None):
+        for bi, ks in enumerate(batches):
+            run_batch(ks, lambda k: frames[k], lambda k: src[k], lambda k: dst[k],
+                      evs[bi] if evs is not None else None)
+
+    # warm-up: W passes, and at least half a second of work so clocks have ramped
+    t0 = time.perf_counter()
+    w = 0
+    while w < args.warmup or time.perf_counter() - t0 < 0.5:
         flush.zero_()
-        step(k)
-    torch.cuda.synchronize()
-    infos = []
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        one_pass()
+        torch.cuda.synchronize()
+        w += 1
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2 + len(ks))] for ks in batches]
+           for _ in range(args.steps)]
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
+    time.sleep(0.1)
     t_wall = time.perf_counter()
+    all_infos = []
     for i in range(args.steps):
         flush.zero_()
-        step(args.warmup + i, evs[i])
-        infos.append(fit_out['info'].clone())
+        one_pass(evs[i])
+        all_infos.append(infos.clone())
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
-    per = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])]
-                    for e in evs])                       # ms: fit, field, warp
-    frame_ms = per.sum(1)
-    total_ms = float(frame_ms.sum())
+    fit_ms, mos_ms, lat_ms, batch_ms = [], [], [], []
+    for step in evs:
+        for e in step:
+            nb = len(e) - 2
+            fit_ms.append(e[0].elapsed_time(e[1]) / nb)
+            prev = e[1]
+            for j in range(nb):
+                mos_ms.append(prev.elapsed_time(e[2 + j]))
+                lat_ms.append(e[0].elapsed_time(e[2 + j]))
+                prev = e[2 + j]
+            batch_ms.append(e[0].elapsed_time(e[-1]))
+    total_ms = float(np.sum(batch_ms))
+    phase_ms = np.array([np.mean(fit_ms), np.mean(mos_ms), 0.0])
+    frame_ms = np.array(lat_ms)
     if ws > 1:
         t = torch.tensor([total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    iters = [emdq.read_fit_info(x) for x in infos]
+    iv = torch.stack(all_infos).view(-1, 4).cpu()
+    iters = iv[:, 1].numpy()
+    statuses = sorted({emdq.STATUS.get(int(v), '?') for v in iv[:, 0].tolist()})
+    total_frames = args.steps * n_frames
 
-    # end to end through the public API from pinned host buffers: H2D of the frame and the
-    # matches, the three calls, D2H of the fit record and the inlier weights
+    # end to end through the public API from pinned host buffers: per frame the H2D copy of
+    # the frame and its matches, the three calls, the D2H of the fit record and weights
     e2e = None
     if not args.no_e2e:
-        hf = [f.cpu().pin_memory() for f in frames[: min(8, n_frames)]]
-        hs = [s.cpu().pin_memory() for s in src[: len(hf)]]
-        hd = [d.cpu().pin_memory() for d in dst[: len(hf)]]
-        dfr = torch.empty_like(frames[0])
-        ds, dd = torch.empty_like(src[0]), torch.empty_like(dst[0])
-        h_info = torch.empty(4, dtype=torch.int32).pin_memory()
-        h_c = torch.empty(n, dtype=torch.float32).pin_memory()
+        nh = min(16, n_frames)
+        hf = [f.cpu().pin_memory() for f in frames[:nh]]
+        hs = [s.cpu().pin_memory() for s in src[:nh]]
+        hd = [d.cpu().pin_memory() for d in dst[:nh]]
+        e_steps = max(1, min(args.steps, 5))
         e_ms = []
-        for i in range(args.warmup + args.steps):
-            k = i % len(hf)
-            g = grids[k]
-            disp = disp_buf[: g[2] * g[3] * 2].view(g[3], g[2], 2)
+        dfr = [torch.empty_like(frames[0]) for _ in range(B)]
+        ds = [torch.empty_like(src[0]) for _ in range(B)]
+        dd = [torch.empty_like(dst[0]) for _ in range(B)]
+        h_infos = [torch.empty(4, dtype=torch.int32).pin_memory() for _ in range(B)]
+        h_cs = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(B)]
+        for i in range(1 + e_steps):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            dfr.copy_(hf[k], non_blocking=True)
-            ds.copy_(hs[k], non_blocking=True)
-            dd.copy_(hd[k], non_blocking=True)
-            emdq.emdq_fit(ds, dd, sc.w, sc.h, out=fit_out, workspace=fit_ws)
-            emdq.emdq_field(fit_out['q'], fit_out['c'], ds, g, alpha, precision=prec, out=disp,
-                            workspace=field_ws)
-            emdq.mosaic_warp(dfr, disp, g, canvas, origin)
-            h_info.copy_(fit_out['info'], non_blocking=True)
-            h_c.copy_(fit_out['c'], non_blocking=True)
+            for ks in batches:
+                for j, k in enumerate(ks):
+                    dfr[j].copy_(hf[k % nh], non_blocking=True)
+                    ds[j].copy_(hs[k % nh], non_blocking=True)
+                    dd[j].copy_(hd[k % nh], non_blocking=True)
+                pos = {k: j for j, k in enumerate(ks)}
+                run_batch(ks, lambda k: dfr[pos[k]], lambda k: ds[pos[k]], lambda k: dd[pos[k]])
+                for j in range(len(ks)):
+                    h_infos[j].copy_(fit_outs[j]['info'], non_blocking=True)
+                    h_cs[j].copy_(fit_outs[j]['c'], non_blocking=True)
             b.record(stream)
             b.synchronize()
-            if i >= args.warmup:
+            if i >= 1:
                 e_ms.append(a.elapsed_time(b))
         e_total = sum(e_ms)
         if ws > 1:
             t = torch.tensor([e_total], device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             e_total = float(t.item())
-        e2e = dict(value=ws * args.steps * sc.w * sc.h / 1e6 / (e_total / 1e3), unit=UNIT,
-                   p50_frame_ms=float(np.median(e_ms)),
-                   h2d_bytes_per_step=int(frames[0].numel() + src[0].numel() * 4 + dst[0].numel() * 4),
-                   d2h_bytes_per_step=int(16 + 4 * n))
+        e2e = dict(value=ws * len(e_ms) * n_frames * sc.w * sc.h / 1e6 / (e_total / 1e3),
+                   unit=UNIT, ms_per_frame=e_total / (len(e_ms) * n_frames),
+                   h2d_bytes_per_step=int(n_frames * (frames[0].numel() + src[0].numel() * 8)),
+                   d2h_bytes_per_step=int(n_frames * (16 + 4 * n)))
 
     if rank != 0:
         if ws > 1:
@@ -273,19 +329,20 @@ def run_gpu(args, ws, rank, local):
         return None
 
     peaks = measured_peaks()
-    phase_ms = per.mean(0)
-    names = ['fit', 'field', 'warp']
+    names = ['fit', 'mosaic' if fused else 'field', 'warp']
     dom = int(np.argmax(phase_ms))
-    win_px = float(np.mean([g[2] * g[3] for g in grids[args.warmup:]]))
-    mean_iters = float(np.mean([x['iters'] for x in iters]))
+    win_px = float(np.mean([g[2] * g[3] for g in grids]))
+    mean_iters = float(np.mean(iters))
     rounds = mean_iters + 1
     if names[dom] == 'fit':
-        # FP32 operations per match pair: 34 in the M-step, 22 in the leave-one-out blend
+        # FP32 operations per match pair and EM round: 2 x 17 in the two M-step passes,
+        # 22 in the leave-one-out blend
         work = rounds * n * n * 56.0
         peak = 152 * 128 * 2 * peaks['sm_max_mhz'] * 1e6 / 1e12
-        roof = dict(bound='alu', kernel='emdq_fit_kernel', achieved=work / (phase_ms[0] * 1e-3) / 1e12,
+        roof = dict(bound='alu', kernel='emdq_fit_batch_kernel' if B > 1 else 'emdq_fit_kernel',
+                    achieved=work / (phase_ms[0] * 1e-3) / 1e12,
                     peak=peak, unit='TFLOP/s', peak_source='derived: 152 SM x 128 FP32 lanes x 2 x max clock')
-    elif names[dom] == 'field':
+    elif names[dom] in ('field', 'mosaic'):
         if prec == emdq.BF16:
             work = 2.0 * 6 * win_px * n
             roof = dict(bound='tensor', kernel='field_tc_kernel', achieved=work / (phase_ms[1] * 1e-3) / 1e12,
@@ -304,19 +361,29 @@ def run_gpu(args, ws, rank, local):
     roof['traffic'] = tr['bytes'] if tr and tr['src'] == _src_hash(tr['file']) else None
 
     line = dict(
-        metric=METRIC, value=ws * args.steps * sc.w * sc.h / 1e6 / (total_ms / 1e3), unit=UNIT,
+        metric=METRIC, value=ws * total_frames * sc.w * sc.h / 1e6 / (total_ms / 1e3), unit=UNIT,
         n_gpus=ws, steps=args.steps, warmup=args.warmup, ms_per_step=total_ms / args.steps,
         p50_frame_ms=float(np.median(frame_ms)), higher_is_better=True, scaling='weak',
         vs_baseline=None, dtype='bf16' if prec == emdq.BF16 else 'f32', data='synthetic',
-        config=dict(workload=f'{args.workload}: 1280x1024 RGB8 frames, N={n} matches/frame, '
-                    f'{int(cfg["outliers"] * 100)}% outliers, 4096x4096 RGBW canvas',
+        config=dict(workload=f'{args.workload}: {n_frames}-frame sequence of {sc.w}x{sc.h} RGB8 '
+                    f'frames, N={n} matches/frame, {int(cfg["outliers"] * 100)}% outliers, '
+                    f'{cw}x{chh} RGBW canvas; one step = one pass over the sequence',
                     frame=[sc.w, sc.h], n_matches=n, canvas=list(cfg['canvas']),
-                    precision=args.precision, parallelism=f'dp{ws} (independent sequences)',
-                    l2='flushed before every step (256 MiB write outside the timed events)',
+                    frames_per_step=n_frames, precision=args.precision,
+                    parallelism=f'dp{ws} (independent sequences)',
+                    l2=f'inputs larger than L2 ({n_frames} distinct frames, '
+                       f'{n_frames * sc.w * sc.h * sc.channels / 1e6:.0f} MB per step) and a '
+                       f'256 MiB flush before every step, outside the timed events',
                     mean_window_px=win_px, mean_em_iters=mean_iters),
-        phases_ms=dict(fit=float(phase_ms[0]), field=float(phase_ms[1]), warp=float(phase_ms[2])),
-        wall_s=wall, roofline=roof, gpu_launches=4 * args.steps, clocks=clk, e2e=e2e,
-        fit_status=sorted({x['status_name'] for x in iters}),
+        phases_ms=dict(fit=float(phase_ms[0]), **({'mosaic': float(phase_ms[1])} if fused else
+                                                   {'field+warp': float(phase_ms[1])})),
+        path=(('emdq_fit_batch' if B > 1 else 'emdq_fit') +
+              (' + emdq_mosaic (fused BF16 field and warp)' if fused else
+               f' + emdq_field ({args.precision}) + mosaic_warp')),
+        batch=B, wall_s=wall, roofline=roof,
+        gpu_launches=total_frames * (2 if fused else 3) + args.steps * len(batches), clocks=clk,
+        e2e=e2e,
+        fit_status=statuses,
     )
     if not args.no_cpu_baseline:
         line['cpu_baseline'] = cpu_baseline(args, budget_s=12.0)

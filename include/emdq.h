@@ -41,6 +41,12 @@ extern "C" {
 
 #define EMDQ_ABI_VERSION 1
 
+#if defined(__GNUC__)
+#define EMDQ_API __attribute__((visibility("default")))
+#else
+#define EMDQ_API
+#endif
+
 typedef enum {
     EMDQ_OK = 0,
     EMDQ_EINVAL = 1,       /* bad argument: null pointer, size, layout, window off-canvas */
@@ -76,11 +82,11 @@ typedef struct {
     float gamma;         /* final inlier fraction (mixing weight) */
 } emdq_fit_info;
 
-void        emdq_default_params(emdq_params *prm);
+EMDQ_API void        emdq_default_params(emdq_params *prm);
 /* Sec. III-G: alpha for a w x h frame. */
-float       emdq_alpha_for_frame(int w, int h);
-const char *emdq_status_string(int status);
-int         emdq_abi_version(void);
+EMDQ_API float       emdq_alpha_for_frame(int w, int h);
+EMDQ_API const char *emdq_status_string(int status);
+EMDQ_API int         emdq_abi_version(void);
 
 /* ------------------------------------------------------------------ emdq_fit ---------
  * EMDQ mismatch removal and per-match warp estimation (Sec. II: "the input of EMDQ is the
@@ -109,12 +115,38 @@ int         emdq_abi_version(void);
  * Returns EMDQ_EINVAL / EMDQ_EWORKSPACE / EMDQ_ENOTSUP / EMDQ_ECUDA on the host; the
  * device outcome (OK, ENOCONV, EDEGENERATE, ETIMEOUT, ENONFINITE) is in info->status.
  */
-int         emdq_fit_max_n(void);
-size_t      emdq_fit_workspace_size(int n);
-emdq_status emdq_fit(const float *src, const float *dst, int n, int frame_w, int frame_h,
+EMDQ_API int         emdq_fit_max_n(void);
+EMDQ_API size_t      emdq_fit_workspace_size(int n);
+EMDQ_API emdq_status emdq_fit(const float *src, const float *dst, int n, int frame_w, int frame_h,
                      const emdq_params *prm, const float *p0, float *q_out, float *c_out,
                      float *p_out, emdq_fit_info *info, void *workspace,
                      size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------ emdq_fit_batch ---
+ * Many independent fits (frames of a sequence, pairs of different sizes) in one
+ * cooperative launch: each problem runs the emdq_fit iteration on its own group of CTAs
+ * with its own barrier, so the latency-bound EM rounds of several fits overlap on the GPU.
+ * Results are those of calling emdq_fit on each problem.
+ *
+ *   problems   host array of `count` descriptors (1 <= count <= 64); every pointer in a
+ *              descriptor follows the rules of the matching emdq_fit argument
+ *   workspace  device scratch of emdq_fit_batch_workspace_size(problems, count) bytes,
+ *              256-byte aligned
+ * Returns EMDQ_ENOTSUP when count exceeds 64 or a problem exceeds emdq_fit_max_n().
+ */
+typedef struct {
+    const float *src, *dst;     /* device, n x 2 float */
+    int n, frame_w, frame_h;
+    const float *p0;            /* device, n float, or NULL */
+    float *q_out, *c_out;       /* device, n x 8 and n float (written) */
+    float *p_out;               /* device, n float (written) or NULL */
+    emdq_fit_info *info;        /* device (written) */
+} emdq_fit_problem;
+
+EMDQ_API size_t      emdq_fit_batch_workspace_size(const emdq_fit_problem *problems, int count);
+EMDQ_API emdq_status emdq_fit_batch(const emdq_fit_problem *problems, int count,
+                                    const emdq_params *prm, void *workspace,
+                                    size_t workspace_bytes, void *stream);
 
 /* ------------------------------------------------------------------ emdq_fit_noalloc -
  * emdq_fit for callers that cannot allocate device memory.  The paper has no counterpart:
@@ -136,7 +168,7 @@ emdq_status emdq_fit(const float *src, const float *dst, int n, int frame_w, int
  *     that array: serialise them (for example, issue them all on one stream).
  * Arguments, results and errors are those of emdq_fit.
  */
-emdq_status emdq_fit_noalloc(const float *src, const float *dst, int n, int frame_w,
+EMDQ_API emdq_status emdq_fit_noalloc(const float *src, const float *dst, int n, int frame_w,
                              int frame_h, const emdq_params *prm, const float *p0,
                              float *q_out, float *c_out, float *p_out, emdq_fit_info *info,
                              void *stream);
@@ -157,8 +189,8 @@ emdq_status emdq_fit_noalloc(const float *src, const float *dst, int n, int fram
  *   workspace  device scratch of emdq_field_workspace_size(...) bytes (may be 0 bytes for
  *              EMDQ_FP32), 256-byte aligned
  */
-size_t      emdq_field_workspace_size(int n, int grid_w, int grid_h, int precision);
-emdq_status emdq_field(const float *q, const float *c, const float *src, int n,
+EMDQ_API size_t      emdq_field_workspace_size(int n, int grid_w, int grid_h, int precision);
+EMDQ_API emdq_status emdq_field(const float *q, const float *c, const float *src, int n,
                        int grid_x0, int grid_y0, int grid_w, int grid_h, float alpha,
                        int precision, float *disp_out, void *workspace,
                        size_t workspace_bytes, void *stream);
@@ -179,14 +211,30 @@ emdq_status emdq_field(const float *q, const float *c, const float *src, int n,
  *   origin_x/y   canvas position of reference pixel (0, 0)
  * The grid, shifted by the origin, must lie inside the canvas (else EMDQ_EINVAL).
  */
-emdq_status mosaic_warp(const uint8_t *frame, int fw, int fh, int channels, int frame_pitch,
+EMDQ_API emdq_status mosaic_warp(const uint8_t *frame, int fw, int fh, int channels, int frame_pitch,
                         const float *disp, int grid_x0, int grid_y0, int grid_w, int grid_h,
                         uint8_t *canvas, int canvas_w, int canvas_h, int canvas_pitch,
                         int origin_x, int origin_y, void *stream);
 
+/* ------------------------------------------------------------------ emdq_mosaic ------
+ * emdq_field (EMDQ_BF16) and mosaic_warp fused in one tensor-core kernel: for every grid
+ * pixel the displacement of Eqs. 1-4 is computed exactly as emdq_field computes it and
+ * the frame is then blended into the canvas exactly as mosaic_warp blends it, so the
+ * canvas ends as the two calls would leave it, without the field going through memory.
+ * Arguments: those of emdq_field (q, c, src, n, grid, alpha; workspace of
+ * emdq_field_workspace_size(n, grid_w, grid_h, EMDQ_BF16) bytes) and of mosaic_warp
+ * (frame, canvas, origin); the same errors.
+ */
+EMDQ_API emdq_status emdq_mosaic(const float *q, const float *c, const float *src, int n,
+                        int grid_x0, int grid_y0, int grid_w, int grid_h, float alpha,
+                        const uint8_t *frame, int fw, int fh, int channels, int frame_pitch,
+                        uint8_t *canvas, int canvas_w, int canvas_h, int canvas_pitch,
+                        int origin_x, int origin_y, void *workspace, size_t workspace_bytes,
+                        void *stream);
+
 /* Sec. III-F: "frame 0 is inserted directly" -- copy the reference frame into the canvas
  * at the origin with merge weight 1. */
-emdq_status mosaic_insert_reference(const uint8_t *frame, int fw, int fh, int channels,
+EMDQ_API emdq_status mosaic_insert_reference(const uint8_t *frame, int fw, int fh, int channels,
                                     int frame_pitch, uint8_t *canvas, int canvas_w,
                                     int canvas_h, int canvas_pitch, int origin_x,
                                     int origin_y, void *stream);

@@ -16,7 +16,7 @@ import torch
 
 from ._build import LIB as _LIB_PATH, build  # noqa: F401
 
-__all__ = ['emdq_fit', 'emdq_field', 'mosaic_warp', 'mosaic_insert_reference',
+__all__ = ['emdq_fit', 'emdq_fit_batch', 'emdq_field', 'mosaic_warp', 'emdq_mosaic', 'mosaic_insert_reference',
            'alpha_for_frame', 'fit_workspace_size', 'field_workspace_size', 'EmdqError',
            'FP32', 'BF16', 'STATUS', 'lib', 'build']
 
@@ -35,6 +35,13 @@ class _Params(ctypes.Structure):
     _fields_ = [('alpha', ctypes.c_float), ('max_iters', ctypes.c_int),
                 ('tol_p', ctypes.c_float), ('sigma2_floor', ctypes.c_float),
                 ('reserved', ctypes.c_int * 4)]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [('src', ctypes.c_void_p), ('dst', ctypes.c_void_p), ('n', ctypes.c_int),
+                ('frame_w', ctypes.c_int), ('frame_h', ctypes.c_int), ('p0', ctypes.c_void_p),
+                ('q_out', ctypes.c_void_p), ('c_out', ctypes.c_void_p), ('p_out', ctypes.c_void_p),
+                ('info', ctypes.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -62,12 +69,19 @@ def lib() -> ctypes.CDLL:
             L.emdq_fit_workspace_size.argtypes = [I]
             L.emdq_fit.restype = I
             L.emdq_fit.argtypes = [P, P, I, I, I, ctypes.POINTER(_Params), P, P, P, P, P, P, Z, P]
+            L.emdq_fit_batch_workspace_size.restype = Z
+            L.emdq_fit_batch_workspace_size.argtypes = [P, I]
+            L.emdq_fit_batch.restype = I
+            L.emdq_fit_batch.argtypes = [P, I, ctypes.POINTER(_Params), P, Z, P]
             L.emdq_field_workspace_size.restype = Z
             L.emdq_field_workspace_size.argtypes = [I, I, I, I]
             L.emdq_field.restype = I
             L.emdq_field.argtypes = [P, P, P, I, I, I, I, I, F, I, P, P, Z, P]
             L.mosaic_warp.restype = I
             L.mosaic_warp.argtypes = [P, I, I, I, I, P, I, I, I, I, P, I, I, I, I, I, P]
+            L.emdq_mosaic.restype = I
+            L.emdq_mosaic.argtypes = [P, P, P, I, I, I, I, I, F, P, I, I, I, I, P, I, I, I, I, I,
+                                      P, Z, P]
             L.mosaic_insert_reference.restype = I
             L.mosaic_insert_reference.argtypes = [P, I, I, I, I, P, I, I, I, I, I, P]
             _lib = L
@@ -140,6 +154,53 @@ def emdq_fit(src: torch.Tensor, dst: torch.Tensor, frame_w: int, frame_h: int, *
     return dict(q=q, c=c, p=p, info=info, workspace=ws)
 
 
+def emdq_fit_batch(problems, *, alpha: float = 0.0, max_iters: int = 20, tol_p: float = 1e-3,
+                   sigma2_floor: float = 0.25, outs: list | None = None,
+                   workspace: torch.Tensor | None = None, stream=None) -> list:
+    """Fit several independent problems in one launch.  problems: list of
+    (src, dst, frame_w, frame_h) or (src, dst, frame_w, frame_h, p0).  Returns one dict per
+    problem as emdq_fit does."""
+    count = len(problems)
+    arr = (_Problem * max(1, count))()
+    results = []
+    for b, pr in enumerate(problems):
+        src, dst, fw, fh = pr[:4]
+        p0 = pr[4] if len(pr) > 4 else None
+        n = src.shape[0]
+        _check(src, 'src', torch.float32, (n, 2))
+        _check(dst, 'dst', torch.float32, (n, 2))
+        if p0 is not None:
+            _check(p0, 'p0', torch.float32, (n,))
+        o = outs[b] if outs is not None else {}
+        dev = src.device
+        r = dict(q=o.get('q') if o.get('q') is not None else torch.empty((n, 8), device=dev),
+                 c=o.get('c') if o.get('c') is not None else torch.empty(n, device=dev),
+                 p=o.get('p') if o.get('p') is not None else torch.empty(n, device=dev),
+                 info=o.get('info') if o.get('info') is not None else
+                 torch.zeros(4, dtype=torch.int32, device=dev))
+        arr[b] = _Problem(src.data_ptr(), dst.data_ptr(), n, int(fw), int(fh),
+                          p0.data_ptr() if p0 is not None else None, r['q'].data_ptr(),
+                          r['c'].data_ptr(), r['p'].data_ptr(), r['info'].data_ptr())
+        results.append(r)
+    need = lib().emdq_fit_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), count)
+    dev = problems[0][0].device
+    ws = _workspace(need, dev, workspace)
+    prm = _Params(float(alpha), int(max_iters), float(tol_p), float(sigma2_floor), (ctypes.c_int * 4)())
+    rc = lib().emdq_fit_batch(ctypes.cast(arr, ctypes.c_void_p), count, ctypes.byref(prm), _ptr(ws),
+                              ws.numel(), _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_fit_batch', rc)
+    return results
+
+
+def fit_batch_workspace_size(problems) -> int:
+    count = len(problems)
+    arr = (_Problem * max(1, count))()
+    for b, pr in enumerate(problems):
+        arr[b].n = int(pr[0].shape[0])
+    return lib().emdq_fit_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), count)
+
+
 def read_fit_info(info: torch.Tensor) -> dict:
     """Decode the 16-byte device record (synchronises with its stream)."""
     h = info.cpu()
@@ -196,6 +257,29 @@ def mosaic_warp(frame: torch.Tensor, disp: torch.Tensor, grid, canvas: torch.Ten
                            _stream(stream))
     if rc != 0:
         raise EmdqError('mosaic_warp', rc)
+
+
+def emdq_mosaic(q: torch.Tensor, c: torch.Tensor, src: torch.Tensor, grid, alpha: float,
+                frame: torch.Tensor, canvas: torch.Tensor, origin, *,
+                workspace: torch.Tensor | None = None, stream=None) -> None:
+    """Fused BF16 field + warp: blends frame into canvas through the field of (q, c, src)
+    on grid=(x0, y0, w, h), without materialising the field."""
+    n = c.shape[0]
+    _check(q, 'q', torch.float32, (n, 8))
+    _check(c, 'c', torch.float32, (n,))
+    _check(src, 'src', torch.float32, (n, 2))
+    fw, fh, ch, pitch = _frame_args(frame)
+    _check(canvas, 'canvas', torch.uint8)
+    if canvas.dim() != 3 or canvas.shape[2] != 4:
+        raise ValueError('canvas must be [h, w, 4] uint8')
+    chh, cw = canvas.shape[:2]
+    x0, y0, gw, gh = (int(v) for v in grid)
+    ws = _workspace(field_workspace_size(n, gw, gh, BF16), q.device, workspace)
+    rc = lib().emdq_mosaic(_ptr(q), _ptr(c), _ptr(src), n, x0, y0, gw, gh, float(alpha),
+                           _ptr(frame), fw, fh, ch, pitch, _ptr(canvas), cw, chh, cw * 4,
+                           int(origin[0]), int(origin[1]), _ptr(ws), ws.numel(), _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_mosaic', rc)
 
 
 def mosaic_insert_reference(frame: torch.Tensor, canvas: torch.Tensor, origin, stream=None) -> None:

@@ -16,6 +16,7 @@ LIB = os.path.join(PKG, 'libemdq.so')
 
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 NVCC_FLAGS = ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC', '-Xcompiler', '-O2',
+              '-Xcompiler', '-fvisibility=hidden',
               '--expt-relaxed-constexpr', '-I', INCLUDE, '-I', CSRC]
 
 

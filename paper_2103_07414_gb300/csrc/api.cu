@@ -117,3 +117,42 @@ extern "C" emdq_status emdq_field(const float *q, const float *c, const float *s
                            static_cast<char *>(workspace) + kRefBytes, workspace_bytes - kRefBytes,
                            st);
 }
+
+extern "C" emdq_status emdq_mosaic(const float *q, const float *c, const float *src, int n,
+                                   int grid_x0, int grid_y0, int grid_w, int grid_h, float alpha,
+                                   const uint8_t *frame, int fw, int fh, int channels,
+                                   int frame_pitch, uint8_t *canvas, int canvas_w, int canvas_h,
+                                   int canvas_pitch, int origin_x, int origin_y, void *workspace,
+                                   size_t workspace_bytes, void *stream)
+{
+    if (!q || !c || !src || n < 1 || grid_w < 0 || grid_h < 0 || !(alpha > 0.f) ||
+        !std::isfinite(alpha))
+        return EMDQ_EINVAL;
+    if (!frame || !canvas || fw < 1 || fh < 1 || (channels != 1 && channels != 3) ||
+        frame_pitch < fw * channels || canvas_w < 1 || canvas_h < 1 ||
+        canvas_pitch < 4 * canvas_w || canvas_pitch % 4 != 0)
+        return EMDQ_EINVAL;
+    if (!aligned(q, 16) || !aligned(src, 8) || !aligned(canvas, 4)) return EMDQ_EINVAL;
+    const size_t need = emdq_field_workspace_size(n, grid_w, grid_h, EMDQ_BF16);
+    if (need == 0) return EMDQ_ENOTSUP;
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return EMDQ_EWORKSPACE;
+    if (grid_w == 0 || grid_h == 0) return EMDQ_OK;
+    if ((long long)grid_x0 + origin_x < 0 || (long long)grid_y0 + origin_y < 0 ||
+        (long long)grid_x0 + origin_x + grid_w > canvas_w ||
+        (long long)grid_y0 + origin_y + grid_h > canvas_h)
+        return EMDQ_EINVAL;
+    MosaicArgs m;
+    m.frame = frame;
+    m.fw = fw;
+    m.fh = fh;
+    m.pitch = frame_pitch;
+    m.channels = channels;
+    m.canvas = reinterpret_cast<uchar4 *>(canvas);
+    m.cpitch4 = canvas_pitch / 4;
+    m.ox = origin_x;
+    m.oy = origin_y;
+    return field_tc_launch(q, c, src, n, grid_x0, grid_y0, grid_w, grid_h, alpha,
+                           static_cast<float *>(workspace), nullptr,
+                           static_cast<char *>(workspace) + kRefBytes, workspace_bytes - kRefBytes,
+                           static_cast<cudaStream_t>(stream), &m);
+}

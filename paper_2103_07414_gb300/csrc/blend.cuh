@@ -1,0 +1,94 @@
+// Per-pixel gather + bilinear sample + capped running-average blend (Sec. III-F,
+// Eqs. 23-24 as read), shared by the stand-alone warp kernel and the fused tensor-core
+// field epilogue so that both paths compute the same bits.  Split in three steps (tap
+// set-up, loads, update) so that a thread handling several pixels can issue all their
+// loads before it uses any.
+#pragma once
+
+#include "common.cuh"
+
+namespace emdq {
+
+// Where a canvas pixel samples frame t: u = p + d with one FP32 rounding per axis; valid
+// iff u lies in [0, fw-1] x [0, fh-1] (a NaN d is invalid); bilinear taps and weights.
+struct Tap {
+    int r0, r1, c0, c1;     // byte offsets of the two rows and two columns
+    float w00, w10, w01, w11;
+    bool ok;
+};
+
+template <int CH>
+__device__ __forceinline__ Tap tap_setup(int fw, int fh, int pitch, float px, float py, float dx,
+                                         float dy)
+{
+    Tap t;
+    const float ux = __fadd_rn(px, dx);
+    const float uy = __fadd_rn(py, dy);
+    t.ok = ux >= 0.f && ux <= static_cast<float>(fw - 1) && uy >= 0.f &&
+           uy <= static_cast<float>(fh - 1);
+    if (!t.ok) {
+        t.r0 = t.r1 = t.c0 = t.c1 = 0;
+        t.w00 = t.w10 = t.w01 = t.w11 = 0.f;
+        return t;
+    }
+    const int x0 = static_cast<int>(floorf(ux)), y0 = static_cast<int>(floorf(uy));
+    const float fx = ux - static_cast<float>(x0), fy = uy - static_cast<float>(y0);
+    const int x1 = min(x0 + 1, fw - 1), y1 = min(y0 + 1, fh - 1);
+    t.w00 = (1.f - fx) * (1.f - fy);
+    t.w10 = fx * (1.f - fy);
+    t.w01 = (1.f - fx) * fy;
+    t.w11 = fx * fy;
+    t.r0 = y0 * pitch;
+    t.r1 = y1 * pitch;
+    t.c0 = x0 * CH;
+    t.c1 = x1 * CH;
+    return t;
+}
+
+template <int CH>
+__device__ __forceinline__ void tap_sample(const uint8_t *__restrict__ frame, const Tap &t,
+                                           float (&v)[CH])
+{
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+        v[k] = t.w00 * __ldg(frame + t.r0 + t.c0 + k) + t.w10 * __ldg(frame + t.r0 + t.c1 + k) +
+               t.w01 * __ldg(frame + t.r1 + t.c0 + k) + t.w11 * __ldg(frame + t.r1 + t.c1 + k);
+    }
+}
+
+__device__ __forceinline__ unsigned blend_channel(unsigned c, float w, float v, float w1)
+{
+    // c <- clamp(floor((w c + v)/(w + 1) + 1/2), 0, 255).  w c + v is exact for integer
+    // v and the quotient is correctly rounded, so ties land exactly on .5 as in FP64.
+    const float z = floorf(__fdiv_rn(fmaf(w, static_cast<float>(c), v), w1) + 0.5f);
+    return static_cast<unsigned>(fminf(fmaxf(z, 0.f), 255.f));
+}
+
+template <int CH>
+__device__ __forceinline__ uchar4 blend_update(uchar4 cv, const float (&v)[CH])
+{
+    const float w = static_cast<float>(cv.w);
+    const float w1 = w + 1.f;
+    cv.x = blend_channel(cv.x, w, v[0], w1);
+    if (CH == 3) {
+        cv.y = blend_channel(cv.y, w, v[1 % CH], w1);
+        cv.z = blend_channel(cv.z, w, v[2 % CH], w1);
+    }
+    cv.w = static_cast<unsigned char>(cv.w < 30 ? cv.w + 1 : 30);
+    return cv;
+}
+
+// One pixel: canvas pixel cp receives frame t sampled at p + d, or is left untouched.
+template <int CH>
+__device__ __forceinline__ void blend_pixel(const uint8_t *__restrict__ frame, int fw, int fh,
+                                            int pitch, float px, float py, float dx, float dy,
+                                            uchar4 *cp)
+{
+    const Tap t = tap_setup<CH>(fw, fh, pitch, px, py, dx, dy);
+    if (!t.ok) return;
+    float v[CH];
+    tap_sample<CH>(frame, t, v);
+    *cp = blend_update<CH>(*cp, v);
+}
+
+}  // namespace emdq

@@ -19,11 +19,14 @@
 // shared-memory ring; one thread issues tcgen05.mma (M = 128 pixels x, N = 192 =
 // 6 channels x 32 pixels y, K = 16) accumulating in TMEM; then the four warps read the
 // accumulators back with tcgen05.ld (thread = pixel x = TMEM lane) and evaluate Eq. 1.
+// The fused variant (CH = 1 or 3) goes on from the displacement to the mosaic update of
+// the same pixel (the stand-alone warp's per-pixel code), so the field never visits HBM.
 #include <mutex>
 
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include "blend.cuh"
 #include "field.cuh"
 #include "field_tc.cuh"
 #include "tc_ptx.cuh"
@@ -35,7 +38,7 @@ constexpr int kTcPY = 32;                // pixels y per tile
 constexpr int kTcCh = 6;                 // dr_w, dr_z, dd_x, dd_y, ds, weight
 constexpr int kTcN = kTcCh * kTcPY;      // MMA N = 192
 constexpr int kTcK = 64;                 // matches per stage: one 128-byte swizzle row
-constexpr int kTcStages = 4;
+constexpr int kTcStages = 2;                 // 2 CTAs per SM: one's epilogue overlaps the other's MMAs
 constexpr int kTcThreads = 128;
 constexpr uint32_t kTcABytes = kTcM * kTcK * 2;
 constexpr uint32_t kTcBBytes = kTcN * kTcK * 2;
@@ -136,10 +139,12 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
     }
 }
 
+// CH = 0: write the displacement field; CH = 1 or 3: blend the frame into the canvas.
+template <int CH>
 __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int nchunks,
     int gx0, int gy0, int gw, int gh, const float *__restrict__ ref, float2 *__restrict__ disp,
-    int *__restrict__ err)
+    int *__restrict__ err, MosaicArgs mos)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
@@ -231,21 +236,47 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(
 #pragma unroll
             for (int ch = 0; ch < kTcCh; ++ch) tc::tmem_ld_x8(lane_base + ch * kTcPY + g * 8, F[ch]);
             tc::tmem_wait_ld();
+            float2 d[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const int y = tile_y * kTcPY + g * 8 + j;
-                if (x >= gw || y >= gh) continue;
-                const float py = static_cast<float>(gy0 + y);
-                float2 d = make_float2(NAN, NAN);
+                const float py = static_cast<float>(gy0 + tile_y * kTcPY + g * 8 + j);
+                d[j] = make_float2(NAN, NAN);
                 const float w = F[5][j];
                 if (w > 0.f) {
                     const float inv = 1.f / w;
                     const float2 xp = apply_blend(ra + F[0][j] * inv, rb + F[1][j] * inv,
                                                   ru + F[2][j] * inv, rv + F[3][j] * inv,
                                                   rs + F[4][j] * inv, px, py);
-                    d = make_float2(xp.x - px, xp.y - py);
+                    d[j] = make_float2(xp.x - px, xp.y - py);
                 }
-                disp[(size_t)y * gw + x] = d;
+            }
+            const int y0 = tile_y * kTcPY + g * 8;
+            if constexpr (CH == 0) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (x < gw && y0 + j < gh) disp[(size_t)(y0 + j) * gw + x] = d[j];
+            } else {
+                // all loads of the 8 pixels first (canvas words and frame taps), then the
+                // updates: 8 independent gathers in flight per thread
+                Tap t[8];
+                uchar4 cv[8];
+                uchar4 *cp[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    t[j] = tap_setup<CH>(mos.fw, mos.fh, mos.pitch, px,
+                                         static_cast<float>(gy0 + y0 + j), d[j].x, d[j].y);
+                    t[j].ok = t[j].ok && x < gw && y0 + j < gh;
+                    cp[j] = mos.canvas + (size_t)(gy0 + y0 + j + mos.oy) * mos.cpitch4 +
+                            (gx0 + x + mos.ox);
+                    if (t[j].ok) cv[j] = *cp[j];
+                }
+                float v[8][CH];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (t[j].ok) tap_sample<CH>(mos.frame, t[j], v[j]);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (t[j].ok) *cp[j] = blend_update<CH>(cv[j], v[j]);
             }
         }
     }
@@ -295,8 +326,10 @@ size_t field_tc_workspace_bytes(int n, int grid_w, int grid_h)
 
 emdq_status field_tc_launch(const float *q, const float *c, const float *src, int n, int gx0,
                             int gy0, int gw, int gh, float alpha, float *ref, float2 *disp,
-                            char *ws, size_t ws_bytes, cudaStream_t st)
+                            char *ws, size_t ws_bytes, cudaStream_t st, const MosaicArgs *mos)
 {
+    const int variant = mos ? mos->channels : 0;
+    if (variant != 0 && variant != 1 && variant != 3) return EMDQ_EINVAL;
     const DeviceInfo &D = device_info();
     if (D.device < 0) return EMDQ_ECUDA;
     if (D.cc_major != 10) return EMDQ_ENOTSUP;           // tcgen05: sm_100 family only
@@ -338,7 +371,11 @@ emdq_status field_tc_launch(const float *q, const float *c, const float *src, in
     {
         std::lock_guard<std::mutex> lk(mu);
         if (attr_dev != D.device) {
-            if (cudaFuncSetAttribute(field_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            if (cudaFuncSetAttribute(field_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kTcSmemBytes) != cudaSuccess ||
+                cudaFuncSetAttribute(field_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kTcSmemBytes) != cudaSuccess ||
+                cudaFuncSetAttribute(field_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kTcSmemBytes) != cudaSuccess)
                 return EMDQ_ECUDA;
             attr_dev = D.device;
@@ -352,7 +389,15 @@ emdq_status field_tc_launch(const float *q, const float *c, const float *src, in
         ref, A, B, a_blocks);
     if (cudaGetLastError() != cudaSuccess) return EMDQ_ECUDA;
     dim3 grid(g.wp / kTcM, g.hp / kTcPY);
-    field_tc_kernel<<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, g.kp / kTcK, gx0, gy0, gw,
-                                                            gh, ref, disp, err);
+    const MosaicArgs none{};
+    if (variant == 0)
+        field_tc_kernel<0><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, g.kp / kTcK, gx0, gy0,
+                                                                   gw, gh, ref, disp, err, none);
+    else if (variant == 1)
+        field_tc_kernel<1><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, g.kp / kTcK, gx0, gy0,
+                                                                   gw, gh, ref, disp, err, *mos);
+    else
+        field_tc_kernel<3><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, g.kp / kTcK, gx0, gy0,
+                                                                   gw, gh, ref, disp, err, *mos);
     return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }

@@ -29,12 +29,13 @@ constexpr int kFitThreads = 256;
 constexpr int kFitWarps = kFitThreads / 32;
 constexpr int kFitMaxN = 5120;         // shared memory: 40 bytes per match
 constexpr int kFitMaxGrid = 1024;
+constexpr int kFitEPerThread = (kFitMaxN + kFitThreads - 1) / kFitThreads;   // residuals per thread
 
 struct FitArgs {
     const float2 *src;
     const float2 *dst;
     int n;
-    float alpha;
+    float alpha2;        // alpha * log2(e): weights are exp2(-alpha2 d^2)
     float inv_area;
     int max_iters;
     float tol;
@@ -45,7 +46,7 @@ struct FitArgs {
     float *p_out;
     emdq_fit_info *info;
     float *e;            // n residuals^2 (workspace)
-    float *partials;     // gridDim.x float2 partial sums (workspace)
+    float *partials;     // one float2 partial sum per CTA of the group (workspace)
     unsigned *bar;       // barrier arrival counter, zero at launch (workspace)
     int *flag;           // device status, zero at launch (workspace)
 };
@@ -73,16 +74,15 @@ __device__ __forceinline__ FitSmem fit_smem(int n)
 
 // Grid-wide barrier with a bounded wait.  `epoch` counts barriers passed (same in every
 // CTA).  Returns false if this CTA gave up waiting (the status flag is then ETIMEOUT).
-__device__ bool grid_barrier(unsigned *bar, int *flag, unsigned &epoch)
+__device__ bool grid_barrier(unsigned *bar, int *flag, unsigned &epoch, int ncta)
 {
     __shared__ int timed_out;
     __syncthreads();
     epoch += 1;
     if (threadIdx.x == 0) {
         timed_out = 0;
-        const unsigned target = epoch * gridDim.x;
-        __threadfence();
-        atomicAdd(bar, 1u);
+        const unsigned target = epoch * static_cast<unsigned>(ncta);
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
         unsigned spins = 0;
         while (ld_acquire_gpu(bar) < target) {
             if (++spins > kSpinLimit) {
@@ -114,10 +114,11 @@ __device__ void mstep_row(const FitArgs &A, const FitSmem &S, int i, int lane)
     const int n = A.n;
     const float2 xi = S.x[i], yi = S.y[i];
     float W = 0.f, sa0 = 0.f, sa1 = 0.f, sb0 = 0.f, sb1 = 0.f;
+#pragma unroll 4
     for (int j = lane; j < n; j += 32) {
         const float2 xj = S.x[j], yj = S.y[j];
         const float a0 = xj.x - xi.x, a1 = xj.y - xi.y;
-        const float om = S.p[j] * expf(-A.alpha * (a0 * a0 + a1 * a1));
+        const float om = S.p[j] * exp2f(-A.alpha2 * (a0 * a0 + a1 * a1));
         W += om;
         sa0 += om * a0;
         sa1 += om * a1;
@@ -134,10 +135,11 @@ __device__ void mstep_row(const FitArgs &A, const FitSmem &S, int i, int lane)
     if (ok) {
         const float ab0 = sa0 / W, ab1 = sa1 / W, bb0 = sb0 / W, bb1 = sb1 / W;
         float vx = 0.f, vy = 0.f, c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
+#pragma unroll 4
         for (int j = lane; j < n; j += 32) {
             const float2 xj = S.x[j], yj = S.y[j];
             const float a0 = xj.x - xi.x, a1 = xj.y - xi.y;
-            const float om = S.p[j] * expf(-A.alpha * (a0 * a0 + a1 * a1));
+            const float om = S.p[j] * exp2f(-A.alpha2 * (a0 * a0 + a1 * a1));
             const float u0 = a0 - ab0, u1 = a1 - ab1;
             const float v0 = (yj.x - yi.x) - bb0, v1 = (yj.y - yi.y) - bb1;
             vx += om * (u0 * u0 + u1 * u1);     // |vector(C_0)|^2
@@ -196,11 +198,12 @@ __device__ float residual_row(const FitArgs &A, const FitSmem &S, int j, int lan
     const float2 xj = S.x[j];
     const float ra = S.qa[j], rb = S.qb[j], ru = S.qu[j], rv = S.qv[j], rs = S.qs[j];
     float w0 = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+#pragma unroll 4
     for (int i = lane; i < n; i += 32) {
         if (i == j) continue;                         // leave one out
         const float2 xi = S.x[i];
         const float dx = xi.x - xj.x, dy = xi.y - xj.y;
-        const float w = S.p[i] * expf(-A.alpha * (dx * dx + dy * dy));
+        const float w = S.p[i] * exp2f(-A.alpha2 * (dx * dx + dy * dy));
         w0 += w;
         a0 += w * (S.qa[i] - ra);
         a1 += w * (S.qb[i] - rb);
@@ -244,20 +247,21 @@ __device__ float2 block_sum2(float a, float b, float2 *red)
 }
 
 // Grid barrier, then the device status word as every thread of every CTA sees it.
-__device__ int barrier_status(const FitArgs &A, unsigned &epoch, int *s_flag)
+__device__ int barrier_status(const FitArgs &A, unsigned &epoch, int *s_flag, int ncta)
 {
-    const bool ok = grid_barrier(A.bar, A.flag, epoch);
+    const bool ok = grid_barrier(A.bar, A.flag, epoch, ncta);
     if (threadIdx.x == 0) *s_flag = ok ? __ldcg(A.flag) : (int)EMDQ_ETIMEOUT;
     __syncthreads();
     return *s_flag;
 }
 
-__global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
+// One fit on a group of `ncta` co-resident CTAs; `rank` is this CTA's index in the group.
+__device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
 {
     const int n = A.n;
     const FitSmem S = fit_smem(n);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gwarp = blockIdx.x * kFitWarps + warp, nwarps = gridDim.x * kFitWarps;
+    const int gwarp = rank * kFitWarps + warp, nwarps = ncta * kFitWarps;
     __shared__ float2 red[kFitWarps];
     __shared__ int s_flag;
     unsigned epoch = 0;
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
     }
     bad = __syncthreads_or(bad);
     if (bad) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (rank == 0 && threadIdx.x == 0) {
             A.info->status = EMDQ_ENONFINITE;
             A.info->iters = 0;
         }
@@ -285,9 +289,8 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
     float gamma = 0.5f;
     if (A.p0) gamma = fminf(fmaxf(block_sum2(p0sum, 0.f, red).x / n, 0.05f), 0.95f);
 
-    // residuals of this CTA's rows and its partial sums; barrier; sigma^2 (each warp
-    // reduces the per-CTA partials itself, in the same order)
-    auto residuals_and_sigma2 = [&](float &sigma2) -> int {
+    // residuals of this CTA's rows and its partial sums, then the barrier
+    auto residuals_and_barrier = [&]() -> int {
         for (int i = threadIdx.x; i < n; i += kFitThreads) {
             const float4 r0 = __ldcg(reinterpret_cast<const float4 *>(A.q_out + 8 * (size_t)i));
             const float r4 = __ldcg(A.q_out + 8 * (size_t)i + 4);
@@ -310,11 +313,21 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
             }
         }
         const float2 t = block_sum2(lane == 0 ? pe : 0.f, lane == 0 ? ps : 0.f, red);
-        if (threadIdx.x == 0) __stcg(reinterpret_cast<float2 *>(A.partials) + blockIdx.x, t);
-        const int st = barrier_status(A, epoch, &s_flag);
-        if (st >= EMDQ_EDEGENERATE) return st;
+        if (threadIdx.x == 0) __stcg(reinterpret_cast<float2 *>(A.partials) + rank, t);
+        return barrier_status(A, epoch, &s_flag, ncta);
+    };
+    // after that barrier: this thread's residuals (all N are needed by every CTA) and
+    // sigma^2 from the per-CTA partials, loads issued together so their latencies overlap;
+    // every warp reduces the partials itself, in the same order
+    float ev[kFitEPerThread];
+    auto load_e_and_sigma2 = [&]() -> float {
+#pragma unroll
+        for (int k = 0; k < kFitEPerThread; ++k) {
+            const int j = threadIdx.x + k * kFitThreads;
+            ev[k] = j < n ? __ldcg(A.e + j) : 0.f;
+        }
         float num = 0.f, den = 0.f;
-        for (int b = lane; b < (int)gridDim.x; b += 32) {
+        for (int b = lane; b < ncta; b += 32) {
             const float2 v = __ldcg(reinterpret_cast<const float2 *>(A.partials) + b);
             num += v.x;
             den += v.y;
@@ -322,15 +335,15 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
         num = warp_sum_f(num);
         den = warp_sum_f(den);
         const float s2 = den > 0.f ? num / (2.f * den) : A.sigma2_floor;
-        sigma2 = fmaxf(s2, A.sigma2_floor);
-        return st;
+        return fmaxf(s2, A.sigma2_floor);
     };
 
     // step 0
     float sigma2 = A.sigma2_floor;
     for (int i = gwarp; i < n; i += nwarps) mstep_row(A, S, i, lane);
-    int st = barrier_status(A, epoch, &s_flag);
-    if (st < EMDQ_EDEGENERATE) st = residuals_and_sigma2(sigma2);
+    int st = barrier_status(A, epoch, &s_flag, ncta);
+    if (st < EMDQ_EDEGENERATE) st = residuals_and_barrier();
+    if (st < EMDQ_EDEGENERATE) sigma2 = load_e_and_sigma2();
 
     int it = 0;
     bool converged = false;
@@ -341,13 +354,17 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
         float dpmax = 0.f, psum = 0.f;
         const float norm = 1.f / (two_pi * sigma2);
         const float outl = (1.f - gamma) * A.inv_area;
-        for (int j = threadIdx.x; j < n; j += kFitThreads) {
-            const float e = __ldcg(A.e + j);
-            const float G = isfinite(e) ? expf(-e / (2.f * sigma2)) * norm : 0.f;
-            const float pn = gamma * G / (gamma * G + outl);
-            dpmax = fmaxf(dpmax, fabsf(pn - S.p[j]));
-            S.p[j] = pn;
-            psum += pn;
+#pragma unroll
+        for (int k = 0; k < kFitEPerThread; ++k) {
+            const int j = threadIdx.x + k * kFitThreads;
+            if (j < n) {
+                const float e = ev[k];
+                const float G = isfinite(e) ? expf(-e / (2.f * sigma2)) * norm : 0.f;
+                const float pn = gamma * G / (gamma * G + outl);
+                dpmax = fmaxf(dpmax, fabsf(pn - S.p[j]));
+                S.p[j] = pn;
+                psum += pn;
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dpmax = fmaxf(dpmax, __shfl_xor_sync(0xffffffffu, dpmax, o));
@@ -364,8 +381,9 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
         const float gamma_next = fminf(fmaxf(ptot / n, 0.05f), 0.95f);
         // M-step with the new weights, then residuals and sigma^2
         for (int i = gwarp; i < n; i += nwarps) mstep_row(A, S, i, lane);
-        st = barrier_status(A, epoch, &s_flag);
-        if (st < EMDQ_EDEGENERATE) st = residuals_and_sigma2(sigma2);
+        st = barrier_status(A, epoch, &s_flag, ncta);
+        if (st < EMDQ_EDEGENERATE) st = residuals_and_barrier();
+        if (st < EMDQ_EDEGENERATE) sigma2 = load_e_and_sigma2();
         gamma = gamma_next;
         if (dpall < A.tol) {
             converged = true;
@@ -373,7 +391,7 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
         }
     }
 
-    if (blockIdx.x == 0) {
+    if (rank == 0) {
         for (int j = threadIdx.x; j < n; j += kFitThreads) {
             const float p = S.p[j];
             A.c_out[j] = p >= 0.5f ? p : 0.f;
@@ -391,6 +409,25 @@ __global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
             A.info->gamma = gamma;
         }
     }
+}
+
+__global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
+{
+    fit_body(A, blockIdx.x, gridDim.x);
+}
+
+// Many fits in one cooperative launch: problem b runs on CTAs [b * group, (b + 1) * group),
+// with its own barrier counter, status word and partial sums.
+constexpr int kFitBatchMax = 64;
+struct FitBatch {
+    FitArgs a[kFitBatchMax];
+};
+
+__global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_batch_kernel(const __grid_constant__ FitBatch B,
+                                                                      int group)
+{
+    const int b = blockIdx.x / group;
+    fit_body(B.a[b], blockIdx.x - b * group, group);
 }
 
 }  // namespace emdq
@@ -472,7 +509,8 @@ extern "C" emdq_status emdq_fit(const float *src, const float *dst, int n, int f
     A.src = reinterpret_cast<const float2 *>(src);
     A.dst = reinterpret_cast<const float2 *>(dst);
     A.n = n;
-    A.alpha = P.alpha > 0.f ? P.alpha : emdq_alpha_for_frame(frame_w, frame_h);
+    const double alpha = P.alpha > 0.f ? P.alpha : emdq_alpha_for_frame(frame_w, frame_h);
+    A.alpha2 = static_cast<float>(alpha * 1.4426950408889634074);
     A.inv_area = 1.f / (static_cast<float>(frame_w) * static_cast<float>(frame_h));
     A.max_iters = P.max_iters;
     A.tol = P.tol_p;
@@ -498,6 +536,120 @@ extern "C" emdq_status emdq_fit(const float *src, const float *dst, int n, int f
     cfg.attrs = at;
     cfg.numAttrs = 1;
     if (cudaLaunchKernelEx(&cfg, emdq_fit_kernel, A) != cudaSuccess) return EMDQ_ECUDA;
+    return EMDQ_OK;
+}
+
+
+// ------------------------------------------------------------------ emdq_fit_batch -----
+namespace {
+// Batch workspace: one 256-byte header per problem (barrier counter, status word) packed
+// first so that a single memset clears them all, then each problem's residuals and
+// partial sums.
+size_t batch_body_bytes(int n)
+{
+    return align_up(sizeof(float) * (size_t)n, 256) + align_up(sizeof(double) * 2 * kFitMaxGrid, 256);
+}
+}  // namespace
+
+extern "C" size_t emdq_fit_batch_workspace_size(const emdq_fit_problem *problems, int count)
+{
+    if (!problems || count < 1 || count > kFitBatchMax) return 0;
+    size_t total = 256 * (size_t)count;
+    for (int b = 0; b < count; ++b) {
+        if (problems[b].n < 0) return 0;
+        total += batch_body_bytes(problems[b].n);
+    }
+    return total;
+}
+
+extern "C" emdq_status emdq_fit_batch(const emdq_fit_problem *problems, int count,
+                                      const emdq_params *prm, void *workspace,
+                                      size_t workspace_bytes, void *stream)
+{
+    emdq_params P;
+    emdq_default_params(&P);
+    if (prm) P = *prm;
+    if (!problems || count < 1 || P.max_iters < 0 || !(P.tol_p >= 0.f) || !(P.sigma2_floor > 0.f))
+        return EMDQ_EINVAL;
+    if (count > kFitBatchMax) return EMDQ_ENOTSUP;
+    int max_n = 0;
+    for (int b = 0; b < count; ++b) {
+        const emdq_fit_problem &q = problems[b];
+        if (!q.src || !q.dst || !q.q_out || !q.c_out || !q.info || q.n < 3 || q.frame_w < 1 ||
+            q.frame_h < 1)
+            return EMDQ_EINVAL;
+        if (!aligned(q.src, 8) || !aligned(q.dst, 8) || !aligned(q.q_out, 16) || !aligned(q.info, 4))
+            return EMDQ_EINVAL;
+        if (q.n > kFitMaxN) return EMDQ_ENOTSUP;
+        max_n = q.n > max_n ? q.n : max_n;
+    }
+    const size_t need = emdq_fit_batch_workspace_size(problems, count);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return EMDQ_EWORKSPACE;
+    const DeviceInfo &D = device_info();
+    if (D.device < 0) return EMDQ_ECUDA;
+    const size_t smem = fit_smem_bytes(max_n);
+    if (smem > D.smem_optin) return EMDQ_ENOTSUP;
+    static std::mutex mu;
+    static int attr_set_dev = -1;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        if (attr_set_dev != D.device) {
+            if (cudaFuncSetAttribute(emdq_fit_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kFitMaxN * 40)) != cudaSuccess)
+                return EMDQ_ECUDA;
+            attr_set_dev = D.device;
+        }
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emdq_fit_batch_kernel, kFitThreads,
+                                                      smem) != cudaSuccess || per_sm < 1)
+        return EMDQ_ECUDA;
+    int group = (D.sms * per_sm) / count;
+    const int want = (max_n + kFitWarps - 1) / kFitWarps;
+    if (group > want) group = want;
+    if (group > kFitMaxGrid) group = kFitMaxGrid;
+    if (group < 1) return EMDQ_ENOTSUP;    // more problems than co-resident CTAs
+
+    char *ws = static_cast<char *>(workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(ws, 0, 256 * (size_t)count, st) != cudaSuccess) return EMDQ_ECUDA;
+    FitBatch B;
+    size_t off = 256 * (size_t)count;
+    const double two_log2e = 1.4426950408889634074;
+    for (int b = 0; b < count; ++b) {
+        const emdq_fit_problem &q = problems[b];
+        FitArgs &A = B.a[b];
+        A.src = reinterpret_cast<const float2 *>(q.src);
+        A.dst = reinterpret_cast<const float2 *>(q.dst);
+        A.n = q.n;
+        const double alpha = P.alpha > 0.f ? P.alpha : emdq_alpha_for_frame(q.frame_w, q.frame_h);
+        A.alpha2 = static_cast<float>(alpha * two_log2e);
+        A.inv_area = 1.f / (static_cast<float>(q.frame_w) * static_cast<float>(q.frame_h));
+        A.max_iters = P.max_iters;
+        A.tol = P.tol_p;
+        A.sigma2_floor = P.sigma2_floor;
+        A.p0 = q.p0;
+        A.q_out = q.q_out;
+        A.c_out = q.c_out;
+        A.p_out = q.p_out;
+        A.info = q.info;
+        A.bar = reinterpret_cast<unsigned *>(ws + 256 * (size_t)b);
+        A.flag = reinterpret_cast<int *>(ws + 256 * (size_t)b + 64);
+        A.e = reinterpret_cast<float *>(ws + off);
+        A.partials = reinterpret_cast<float *>(ws + off + align_up(sizeof(float) * (size_t)q.n, 256));
+        off += batch_body_bytes(q.n);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(group * count);
+    cfg.blockDim = dim3(kFitThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, emdq_fit_batch_kernel, B, group) != cudaSuccess) return EMDQ_ECUDA;
     return EMDQ_OK;
 }
 

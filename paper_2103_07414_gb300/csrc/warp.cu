@@ -2,19 +2,12 @@
 // HBM-bound: per window pixel one 8-byte field read, one 4-byte canvas read and write
 // (colour + merge weight packed in one aligned word) and the bilinear taps of the frame,
 // which neighbouring threads share through L1/L2 because the field is smooth.
+#include "blend.cuh"
 #include "common.cuh"
 
 namespace emdq {
 
 constexpr int kWarpThreadsX = 128;
-
-__device__ __forceinline__ unsigned blend_channel(unsigned c, float w, float v, float w1)
-{
-    // c <- clamp(floor((w c + v)/(w + 1) + 1/2), 0, 255).  w c + v is exact for integer
-    // v and the quotient is correctly rounded, so ties land exactly on .5 as in FP64.
-    const float z = floorf(__fdiv_rn(fmaf(w, static_cast<float>(c), v), w1) + 0.5f);
-    return static_cast<unsigned>(fminf(fmaxf(z, 0.f), 255.f));
-}
 
 template <int CH>
 __global__ void __launch_bounds__(kWarpThreadsX) mosaic_warp_kernel(
@@ -26,36 +19,8 @@ __global__ void __launch_bounds__(kWarpThreadsX) mosaic_warp_kernel(
     const int y = blockIdx.y;
     if (x >= gw) return;
     const float2 d = __ldcs(disp + (size_t)y * gw + x);
-    // u = p + d in FP32 (one rounding): the coverage and tap decisions
-    const float ux = __fadd_rn(static_cast<float>(gx0 + x), d.x);
-    const float uy = __fadd_rn(static_cast<float>(gy0 + y), d.y);
-    if (!(ux >= 0.f && ux <= static_cast<float>(fw - 1) && uy >= 0.f &&
-          uy <= static_cast<float>(fh - 1)))
-        return;
-    const int x0 = static_cast<int>(floorf(ux)), y0 = static_cast<int>(floorf(uy));
-    const float fx = ux - static_cast<float>(x0), fy = uy - static_cast<float>(y0);
-    const int x1 = min(x0 + 1, fw - 1), y1 = min(y0 + 1, fh - 1);
-    const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy);
-    const float w01 = (1.f - fx) * fy, w11 = fx * fy;
-    const uint8_t *r0 = frame + (size_t)y0 * pitch;
-    const uint8_t *r1 = frame + (size_t)y1 * pitch;
-    uchar4 *cp = canvas + (size_t)(gy0 + y + oy) * cpitch4 + (gx0 + x + ox);
-    uchar4 cv = *cp;
-    const float w = static_cast<float>(cv.w);
-    const float w1 = w + 1.f;
-    float v[CH];
-#pragma unroll
-    for (int k = 0; k < CH; ++k) {
-        v[k] = w00 * __ldg(r0 + x0 * CH + k) + w10 * __ldg(r0 + x1 * CH + k) +
-               w01 * __ldg(r1 + x0 * CH + k) + w11 * __ldg(r1 + x1 * CH + k);
-    }
-    cv.x = blend_channel(cv.x, w, v[0], w1);
-    if (CH == 3) {
-        cv.y = blend_channel(cv.y, w, v[1 % CH], w1);
-        cv.z = blend_channel(cv.z, w, v[2 % CH], w1);
-    }
-    cv.w = static_cast<unsigned char>(cv.w < 30 ? cv.w + 1 : 30);
-    *cp = cv;
+    blend_pixel<CH>(frame, fw, fh, pitch, static_cast<float>(gx0 + x), static_cast<float>(gy0 + y),
+                    d.x, d.y, canvas + (size_t)(gy0 + y + oy) * cpitch4 + (gx0 + x + ox));
 }
 
 template <int CH>

@@ -1,0 +1,61 @@
+"""GPU parity: emdq_fit_batch runs several fits of different sizes in one launch; each
+must agree with its own emdq_fit and with the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from synth import make_matches, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope='module')
+def emdq():
+    import paper_2103_07414_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+def _apply(q8, x):
+    a, b, u, v, s = (q8[:, k] for k in range(5))
+    n2 = a * a + b * b
+    X = ((a * a - b * b) * x[:, 0] - 2 * a * b * x[:, 1] + 2 * (a * u - b * v)) / n2
+    Y = (2 * a * b * x[:, 0] + (a * a - b * b) * x[:, 1] + 2 * (b * u + a * v)) / n2
+    return s[:, None] * np.stack([X, Y], 1)
+
+
+def test_batch_matches_single_fits_and_oracle(emdq, orc):
+    cases = []
+    for name, seed, t in [('pair640', 1, 1), ('seq1280', 2, 10), ('seq1280', 2, 11), ('warm2000', 3, 1),
+                          ('pair640', 4, 1)]:
+        sc, cfg = workload(name, seed=seed)
+        s, d, _ = make_matches(sc, t, cfg['n'], cfg['outliers'], cfg['noise'])
+        cases.append((sc, s, d))
+    probs = [(torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), sc.w, sc.h) for sc, s, d in cases]
+    res = emdq.emdq_fit_batch(probs)
+    torch.cuda.synchronize()
+    for (sc, s, d), pr, r in zip(cases, probs, res):
+        info = emdq.read_fit_info(r['info'])
+        single = emdq.emdq_fit(*pr)
+        sinfo = emdq.read_fit_info(single['info'])
+        assert info['status_name'] == sinfo['status_name'] == 'OK'
+        assert info['iters'] == sinfo['iters']
+        assert (r['p'] - single['p']).abs().max().item() <= 1e-4
+        f64 = lambda a: np.float32(a).astype(np.float64)
+        want = orc.fit(f64(s), f64(d), sc.w, sc.h)
+        assert info['iters'] == want['iters']
+        got_p = r['p'].cpu().numpy()
+        assert np.abs(got_p - want['p']).max() <= 1e-4
+        sure = np.abs(want['p'] - 0.5) > 0.1
+        np.testing.assert_array_equal((r['c'].cpu().numpy() > 0)[sure], (want['c'] > 0)[sure])
+        dpos = np.abs(_apply(r['q'].cpu().numpy().astype(np.float64), f64(s)) -
+                      _apply(want['q8'], f64(s)))[want['c'] > 0].max()
+        assert dpos <= 2e-3
+
+
+def test_batch_argument_errors(emdq):
+    x = torch.zeros((10, 2), device='cuda')
+    with pytest.raises(emdq.EmdqError):
+        emdq.emdq_fit_batch([(x[:2], x[:2], 640, 480)])
+    with pytest.raises(emdq.EmdqError):
+        emdq.emdq_fit_batch([(x, x, 640, 480)] * 65)
