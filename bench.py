@@ -57,8 +57,11 @@ def parse_args():
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--batch', type=int, default=8,
                     help='frames whose EM fits share one launch (1: one emdq_fit per frame)')
-    ap.add_argument('--unfused', action='store_true',
-                    help='BF16 field and warp as two calls (default: one fused emdq_mosaic call)')
+    ap.add_argument('--fused', action='store_true',
+                    help='BF16 field and warp in one emdq_mosaic call (default: emdq_field + mosaic_warp)')
+    ap.add_argument('--no-overlap', action='store_true',
+                    help='one stream (default: the next batch of fits runs on a second stream '
+                         'while the current batch is blended)')
     return ap.parse_args()
 
 
@@ -190,13 +193,19 @@ def run_gpu(args, ws, rank, local):
     infos = torch.zeros((n_frames, 4), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    fused = prec == emdq.BF16 and not args.unfused
+    fused = prec == emdq.BF16 and args.fused
     B = max(1, min(args.batch, 64))
-    fit_outs = [dict(q=torch.empty((n, 8), device=dev), c=torch.empty(n, device=dev),
-                     p=torch.empty(n, device=dev), info=torch.zeros(4, dtype=torch.int32, device=dev))
-                for _ in range(B)]
-    batch_ws = torch.empty(max(256, emdq.fit_batch_workspace_size([(src[0], dst[0])] * B)),
-                           dtype=torch.uint8, device=dev)
+    overlap = not args.no_overlap
+    nbuf = 2 if overlap else 1            # fit outputs of two batches in flight
+    fit_outs_all = [[dict(q=torch.empty((n, 8), device=dev), c=torch.empty(n, device=dev),
+                          p=torch.empty(n, device=dev),
+                          info=torch.zeros(4, dtype=torch.int32, device=dev))
+                     for _ in range(B)] for _ in range(nbuf)]
+    batch_ws = [torch.empty(max(256, emdq.fit_batch_workspace_size([(src[0], dst[0])] * B)),
+                            dtype=torch.uint8, device=dev) for _ in range(nbuf)]
+    fit_ws_all = [torch.empty(emdq.fit_workspace_size(n), dtype=torch.uint8, device=dev)
+                  for _ in range(nbuf)]
+    fit_stream = torch.cuda.Stream(device=dev) if overlap else stream
 
     def field_and_warp(fr, s_, g, fo):
         if fused:
@@ -207,28 +216,61 @@ def run_gpu(args, ws, rank, local):
                             workspace=field_ws)
             emdq.mosaic_warp(fr, disp, g, canvas, origin)
 
-    def run_batch(ks, fr_of, s_of, d_of, ev=None):
-        """Frames ks (in order): their fits, then their mosaic updates in frame order.
-        ev: [start, after fit(s), after each frame's field+warp...]"""
-        if ev: ev[0].record(stream)
-        if B == 1:
-            emdq.emdq_fit(s_of(ks[0]), d_of(ks[0]), sc.w, sc.h, out=fit_outs[0], workspace=fit_ws)
-        else:
-            emdq.emdq_fit_batch([(s_of(k), d_of(k), sc.w, sc.h) for k in ks],
-                                outs=fit_outs[: len(ks)], workspace=batch_ws)
+    def fit_batch(bi, ks, s_of, d_of):
+        """The fits of batch bi (frames ks) on the fit stream; returns its done event."""
+        outs = fit_outs_all[bi % nbuf]
+        with torch.cuda.stream(fit_stream):
+            if B == 1:
+                emdq.emdq_fit(s_of(ks[0]), d_of(ks[0]), sc.w, sc.h, out=outs[0],
+                              workspace=fit_ws_all[bi % nbuf], stream=fit_stream)
+            else:
+                emdq.emdq_fit_batch([(s_of(k), d_of(k), sc.w, sc.h) for k in ks], outs=outs[: len(ks)],
+                                    workspace=batch_ws[bi % nbuf], stream=fit_stream)
+            done = torch.cuda.Event()
+            done.record(fit_stream)
+        return done
+
+    def blend_batch(bi, ks, fr_of, s_of, fit_done, ev=None):
+        """Field + warp of batch bi in frame order on the main stream, after its fits."""
+        stream.wait_event(fit_done)
+        outs = fit_outs_all[bi % nbuf]
         if ev: ev[1].record(stream)
         for j, k in enumerate(ks):
-            field_and_warp(fr_of(k), s_of(k), grids[k], fit_outs[j])
+            field_and_warp(fr_of(k), s_of(k), grids[k], outs[j])
             if ev: ev[2 + j].record(stream)
         for j, k in enumerate(ks):
-            infos[k].copy_(fit_outs[j]['info'])
+            infos[k].copy_(outs[j]['info'])
+        blended = torch.cuda.Event()
+        blended.record(stream)
+        return blended
+
+    def run_batches(batches_, fr_of, s_of, d_of, evs=None):
+        """Fits of batch i+1 are issued before batch i is blended, so with two streams they
+        overlap; a batch's fit outputs are reused two batches later, after its blend."""
+        blended = [None] * len(batches_)
+        done = [None] * len(batches_)
+        def issue_fit(i):
+            if i >= nbuf and blended[i - nbuf] is not None:
+                fit_stream.wait_event(blended[i - nbuf])
+            if evs is not None:
+                evs[i][0].record(fit_stream)
+            done[i] = fit_batch(i, batches_[i], s_of, d_of)
+        issue_fit(0)
+        for i, ks in enumerate(batches_):
+            if i + 1 < len(batches_):
+                if not overlap:
+                    blended[i] = blend_batch(i, ks, fr_of, s_of, done[i], evs[i] if evs else None)
+                    issue_fit(i + 1)
+                    continue
+                issue_fit(i + 1)
+            blended[i] = blend_batch(i, ks, fr_of, s_of, done[i], evs[i] if evs else None)
+        stream.wait_stream(fit_stream)
 
     batches = [list(range(k0, min(n_frames, k0 + B))) for k0 in range(0, n_frames, B)]
 
     def one_pass(evs=None):
-        for bi, ks in enumerate(batches):
-            run_batch(ks, lambda k: frames[k], lambda k: src[k], lambda k: dst[k],
-                      evs[bi] if evs is not None else None)
+        fit_stream.wait_stream(stream)        # after the L2 flush
+        run_batches(batches, lambda k: frames[k], lambda k: src[k], lambda k: dst[k], evs)
 
     # warm-up: W passes, and at least half a second of work so clocks have ramped
     t0 = time.perf_counter()
@@ -257,7 +299,10 @@ def run_gpu(args, ws, rank, local):
         torch.distributed.barrier()
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
-    fit_ms, mos_ms, lat_ms, batch_ms = [], [], [], []
+    # e[0]: the batch's fits issued (fit stream); e[1]: its blend starts (main stream, after
+    # the fits); e[2 + j]: frame j blended.  Frame latency = e[0] -> e[2 + j]; the step time
+    # is first fit issue -> last blend of the pass.
+    fit_ms, mos_ms, lat_ms, pass_ms = [], [], [], []
     for step in evs:
         for e in step:
             nb = len(e) - 2
@@ -267,8 +312,8 @@ def run_gpu(args, ws, rank, local):
                 mos_ms.append(prev.elapsed_time(e[2 + j]))
                 lat_ms.append(e[0].elapsed_time(e[2 + j]))
                 prev = e[2 + j]
-            batch_ms.append(e[0].elapsed_time(e[-1]))
-    total_ms = float(np.sum(batch_ms))
+        pass_ms.append(step[0][0].elapsed_time(step[-1][-1]))
+    total_ms = float(np.sum(pass_ms))
     phase_ms = np.array([np.mean(fit_ms), np.mean(mos_ms), 0.0])
     frame_ms = np.array(lat_ms)
     if ws > 1:
@@ -300,15 +345,18 @@ def run_gpu(args, ws, rank, local):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             for ks in batches:
+                # H2D of this batch's frames and matches, then the pipeline on device copies
                 for j, k in enumerate(ks):
                     dfr[j].copy_(hf[k % nh], non_blocking=True)
                     ds[j].copy_(hs[k % nh], non_blocking=True)
                     dd[j].copy_(hd[k % nh], non_blocking=True)
+                fit_stream.wait_stream(stream)
                 pos = {k: j for j, k in enumerate(ks)}
-                run_batch(ks, lambda k: dfr[pos[k]], lambda k: ds[pos[k]], lambda k: dd[pos[k]])
+                run_batches([ks], lambda k: dfr[pos[k]], lambda k: ds[pos[k]], lambda k: dd[pos[k]])
+                outs = fit_outs_all[0]
                 for j in range(len(ks)):
-                    h_infos[j].copy_(fit_outs[j]['info'], non_blocking=True)
-                    h_cs[j].copy_(fit_outs[j]['c'], non_blocking=True)
+                    h_infos[j].copy_(outs[j]['info'], non_blocking=True)
+                    h_cs[j].copy_(outs[j]['c'], non_blocking=True)
             b.record(stream)
             b.synchronize()
             if i >= 1:
@@ -379,7 +427,8 @@ def run_gpu(args, ws, rank, local):
                                                    {'field+warp': float(phase_ms[1])})),
         path=(('emdq_fit_batch' if B > 1 else 'emdq_fit') +
               (' + emdq_mosaic (fused BF16 field and warp)' if fused else
-               f' + emdq_field ({args.precision}) + mosaic_warp')),
+               f' + emdq_field ({args.precision}) + mosaic_warp') +
+              (', fits of the next batch on a second stream' if overlap else '')),
         batch=B, wall_s=wall, roofline=roof,
         gpu_launches=total_frames * (2 if fused else 3) + args.steps * len(batches), clocks=clk,
         e2e=e2e,
