@@ -55,7 +55,7 @@ def parse_args():
     ap.add_argument('--seed', type=int, default=0)
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
-    ap.add_argument('--batch', type=int, default=8,
+    ap.add_argument('--batch', type=int, default=16,
                     help='frames whose EM fits share one launch (1: one emdq_fit per frame)')
     ap.add_argument('--fused', action='store_true',
                     help='BF16 field and warp in one emdq_mosaic call (default: emdq_field + mosaic_warp)')

@@ -46,6 +46,7 @@ struct FitArgs {
     float *p_out;
     emdq_fit_info *info;
     float *e;            // n residuals^2 (workspace)
+    float4 *cen;         // n weighted centroids of the last M-step, local coordinates (workspace)
     float *partials;     // one float2 partial sum per CTA of the group (workspace)
     unsigned *bar;       // barrier arrival counter, zero at launch (workspace)
     int *flag;           // device status, zero at launch (workspace)
@@ -105,90 +106,137 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
-// M-step of row i (one warp): weights om_j = p_j exp(-alpha |x_j - x_i|^2).
-// Pass 1: W, the weighted centroids (local coordinates a = x_j - x_i, b = y_j - y_i).
-// Pass 2: the centred moments |a - abar|^2, |b - bbar|^2 and (b - bbar)(a - abar)^T.
-// Then Eq. 18 (rotation, 2-D closed form), Eq. 19 (norm ratio), Eq. 20 (translation).
-__device__ void mstep_row(const FitArgs &A, const FitSmem &S, int i, int lane)
+// Eqs. 18-20 from the weight W, the weighted centroids (local coordinates) and the centred
+// moments: rotation (2-D closed form), scale (norm ratio), translation.  Lane 0 writes the
+// q row and the centroid.
+__device__ __forceinline__ void mstep_finish(const FitArgs &A, int i, float2 xi, float2 yi,
+                                             float W, float ab0, float ab1, float bb0, float bb1,
+                                             float vx, float vy, float c00, float c01, float c10,
+                                             float c11, int lane)
+{
+    // Eq. 18 in 2-D: the rotation angle th maximising tr(R^T C_t C_0^T) has direction
+    // (a, b) = (c00 + c11, c10 - c01); its half angle (the DQ real part) is the direction
+    // of (rho + a, b), or of (b, rho - a) when a < 0 (no cancellation).
+    const float a = c00 + c11, b = c10 - c01;
+    const float rho = hypotf(a, b);
+    float h0, h1;
+    if (a >= 0.f) { h0 = rho + a; h1 = b; }
+    else if (b >= 0.f) { h0 = b; h1 = rho - a; }
+    else { h0 = -b; h1 = a - rho; }
+    const float hn = hypotf(h0, h1);
+    float c = 1.f, sn = 0.f;
+    if (hn > 0.f) { c = h0 / hn; sn = h1 / hn; }
+    // Eq. 19: norm ratio
+    const float sc = sqrtf(vy / vx);
+    // Eq. 20: t = ybar / s - R xbar in global coordinates
+    const float ct = c * c - sn * sn, st = 2.f * c * sn;
+    const float xg0 = xi.x + ab0, xg1 = xi.y + ab1;
+    const float yg0 = yi.x + bb0, yg1 = yi.y + bb1;
+    const float tx = yg0 / sc - (ct * xg0 - st * xg1);
+    const float ty = yg1 / sc - (st * xg0 + ct * xg1);
+    const bool ok = W > 0.f && isfinite(W) && vx > 0.f && isfinite(sc) && isfinite(tx) &&
+                    isfinite(ty);
+    if (lane != 0) return;
+    float row[5] = {1.f, 0.f, 0.f, 0.f, 1.f};
+    if (ok) {
+        row[0] = c;
+        row[1] = sn;
+        row[2] = 0.5f * (tx * c + ty * sn);
+        row[3] = 0.5f * (ty * c - tx * sn);
+        row[4] = sc;
+    } else {
+        raise_status(A.flag, EMDQ_EDEGENERATE);
+    }
+    float4 *dst = reinterpret_cast<float4 *>(A.q_out + 8 * (size_t)i);
+    __stcg(dst, make_float4(row[0], row[1], row[2], row[3]));
+    __stcg(dst + 1, make_float4(row[4], 1.f, 0.f, 0.f));
+    __stcg(A.cen + i, ok ? make_float4(ab0, ab1, bb0, bb1) : make_float4(0.f, 0.f, 0.f, 0.f));
+}
+
+// M-step of row i (one warp): weights om_j = p_j exp(-alpha |x_j - x_i|^2), local
+// coordinates a = x_j - x_i, b = y_j - y_i.  The similarity fit needs the moments about
+// the weighted centroid; summing raw moments and centring afterwards cancels.
+//   first round: two passes -- W and the centroid, then the moments about it;
+//   later rounds: one pass about the previous round's centroid s of this row (the
+//     weights change little from round to round, so the centroid moves by far less than
+//     the spread and the final correction W |centroid - s|^2 cancels nothing).
+__device__ void mstep_row(const FitArgs &A, const FitSmem &S, int i, int lane, bool first)
 {
     const int n = A.n;
     const float2 xi = S.x[i], yi = S.y[i];
-    float W = 0.f, sa0 = 0.f, sa1 = 0.f, sb0 = 0.f, sb1 = 0.f;
-#pragma unroll 4
-    for (int j = lane; j < n; j += 32) {
-        const float2 xj = S.x[j], yj = S.y[j];
-        const float a0 = xj.x - xi.x, a1 = xj.y - xi.y;
-        const float om = S.p[j] * exp2f(-A.alpha2 * (a0 * a0 + a1 * a1));
-        W += om;
-        sa0 += om * a0;
-        sa1 += om * a1;
-        sb0 += om * (yj.x - yi.x);
-        sb1 += om * (yj.y - yi.y);
-    }
-    W = warp_sum_f(W);
-    sa0 = warp_sum_f(sa0);
-    sa1 = warp_sum_f(sa1);
-    sb0 = warp_sum_f(sb0);
-    sb1 = warp_sum_f(sb1);
-    float row[5] = {1.f, 0.f, 0.f, 0.f, 1.f};
-    bool ok = W > 0.f && isfinite(W);
-    if (ok) {
-        const float ab0 = sa0 / W, ab1 = sa1 / W, bb0 = sb0 / W, bb1 = sb1 / W;
-        float vx = 0.f, vy = 0.f, c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
+    float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!first) sh = __ldcg(A.cen + i);
+    if (first) {
+        float W = 0.f, sa0 = 0.f, sa1 = 0.f, sb0 = 0.f, sb1 = 0.f;
 #pragma unroll 4
         for (int j = lane; j < n; j += 32) {
             const float2 xj = S.x[j], yj = S.y[j];
             const float a0 = xj.x - xi.x, a1 = xj.y - xi.y;
             const float om = S.p[j] * exp2f(-A.alpha2 * (a0 * a0 + a1 * a1));
-            const float u0 = a0 - ab0, u1 = a1 - ab1;
-            const float v0 = (yj.x - yi.x) - bb0, v1 = (yj.y - yi.y) - bb1;
-            vx += om * (u0 * u0 + u1 * u1);     // |vector(C_0)|^2
-            vy += om * (v0 * v0 + v1 * v1);     // |vector(C_t)|^2
-            c00 += om * v0 * u0;                // C_t C_0^T
-            c01 += om * v0 * u1;
-            c10 += om * v1 * u0;
-            c11 += om * v1 * u1;
+            W += om;
+            sa0 += om * a0;
+            sa1 += om * a1;
+            sb0 += om * (yj.x - yi.x);
+            sb1 += om * (yj.y - yi.y);
         }
-        vx = warp_sum_f(vx);
-        vy = warp_sum_f(vy);
-        c00 = warp_sum_f(c00);
-        c01 = warp_sum_f(c01);
-        c10 = warp_sum_f(c10);
-        c11 = warp_sum_f(c11);
-        // Eq. 18 in 2-D: the rotation angle th maximising tr(R^T C_t C_0^T) has direction
-        // (a, b) = (c00 + c11, c10 - c01); its half angle (the DQ real part) is the
-        // direction of (rho + a, b), or of (b, rho - a) when a < 0 (no cancellation).
-        const float a = c00 + c11, b = c10 - c01;
-        const float rho = hypotf(a, b);
-        float h0, h1;
-        if (a >= 0.f) { h0 = rho + a; h1 = b; }
-        else if (b >= 0.f) { h0 = b; h1 = rho - a; }
-        else { h0 = -b; h1 = a - rho; }
-        const float hn = hypotf(h0, h1);
-        float c = 1.f, sn = 0.f;
-        if (hn > 0.f) { c = h0 / hn; sn = h1 / hn; }
-        // Eq. 19: norm ratio
-        const float sc = sqrtf(vy / vx);
-        // Eq. 20: t = ybar / s - R xbar in global coordinates
-        const float ct = c * c - sn * sn, st = 2.f * c * sn;
-        const float xg0 = xi.x + ab0, xg1 = xi.y + ab1;
-        const float yg0 = yi.x + bb0, yg1 = yi.y + bb1;
-        const float tx = yg0 / sc - (ct * xg0 - st * xg1);
-        const float ty = yg1 / sc - (st * xg0 + ct * xg1);
-        ok = vx > 0.f && isfinite(sc) && isfinite(tx) && isfinite(ty);
-        if (ok) {
-            row[0] = c;
-            row[1] = sn;
-            row[2] = 0.5f * (tx * c + ty * sn);
-            row[3] = 0.5f * (ty * c - tx * sn);
-            row[4] = sc;
-        }
+        W = warp_sum_f(W);
+        sa0 = warp_sum_f(sa0);
+        sa1 = warp_sum_f(sa1);
+        sb0 = warp_sum_f(sb0);
+        sb1 = warp_sum_f(sb1);
+        if (W > 0.f && isfinite(W)) sh = make_float4(sa0 / W, sa1 / W, sb0 / W, sb1 / W);
     }
-    if (lane != 0) return;
-    if (!ok) raise_status(A.flag, EMDQ_EDEGENERATE);
-    float4 *dst = reinterpret_cast<float4 *>(A.q_out + 8 * (size_t)i);
-    __stcg(dst, make_float4(row[0], row[1], row[2], row[3]));
-    __stcg(dst + 1, make_float4(row[4], 1.f, 0.f, 0.f));
+    // one pass about the shift sh: W, first moments (for the small correction) and the
+    // second moments
+    float W = 0.f, su0 = 0.f, su1 = 0.f, sv0 = 0.f, sv1 = 0.f;
+    float vx = 0.f, vy = 0.f, c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
+#pragma unroll 4
+    for (int j = lane; j < n; j += 32) {
+        const float2 xj = S.x[j], yj = S.y[j];
+        const float a0 = xj.x - xi.x, a1 = xj.y - xi.y;
+        const float om = S.p[j] * exp2f(-A.alpha2 * (a0 * a0 + a1 * a1));
+        const float u0 = a0 - sh.x, u1 = a1 - sh.y;
+        const float v0 = (yj.x - yi.x) - sh.z, v1 = (yj.y - yi.y) - sh.w;
+        const float ou0 = om * u0, ou1 = om * u1;
+        W += om;
+        su0 += ou0;
+        su1 += ou1;
+        sv0 += om * v0;
+        sv1 += om * v1;
+        vx += ou0 * u0 + ou1 * u1;          // |vector(C_0)|^2 about the shift
+        vy += om * (v0 * v0 + v1 * v1);     // |vector(C_t)|^2 about the shift
+        c00 += v0 * ou0;                    // C_t C_0^T about the shift
+        c01 += v0 * ou1;
+        c10 += v1 * ou0;
+        c11 += v1 * ou1;
+    }
+    W = warp_sum_f(W);
+    su0 = warp_sum_f(su0);
+    su1 = warp_sum_f(su1);
+    sv0 = warp_sum_f(sv0);
+    sv1 = warp_sum_f(sv1);
+    vx = warp_sum_f(vx);
+    vy = warp_sum_f(vy);
+    c00 = warp_sum_f(c00);
+    c01 = warp_sum_f(c01);
+    c10 = warp_sum_f(c10);
+    c11 = warp_sum_f(c11);
+    // move the moments from the shift to the centroid: m_c = m_s - W d d'^T, d = mean - sh
+    float du0 = 0.f, du1 = 0.f, dv0 = 0.f, dv1 = 0.f;
+    if (W > 0.f) {
+        du0 = su0 / W;
+        du1 = su1 / W;
+        dv0 = sv0 / W;
+        dv1 = sv1 / W;
+    }
+    vx -= W * (du0 * du0 + du1 * du1);
+    vy -= W * (dv0 * dv0 + dv1 * dv1);
+    c00 -= W * dv0 * du0;
+    c01 -= W * dv0 * du1;
+    c10 -= W * dv1 * du0;
+    c11 -= W * dv1 * du1;
+    mstep_finish(A, i, xi, yi, W, sh.x + du0, sh.y + du1, sh.z + dv0, sh.w + dv1, vx, vy, c00,
+                 c01, c10, c11, lane);
 }
 
 // Leave-one-out residual of row j (one warp); returns e_j on lane 0.
@@ -340,7 +388,7 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
 
     // step 0
     float sigma2 = A.sigma2_floor;
-    for (int i = gwarp; i < n; i += nwarps) mstep_row(A, S, i, lane);
+    for (int i = gwarp; i < n; i += nwarps) mstep_row(A, S, i, lane, true);
     int st = barrier_status(A, epoch, &s_flag, ncta);
     if (st < EMDQ_EDEGENERATE) st = residuals_and_barrier();
     if (st < EMDQ_EDEGENERATE) sigma2 = load_e_and_sigma2();
@@ -380,7 +428,7 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
         __syncthreads();
         const float gamma_next = fminf(fmaxf(ptot / n, 0.05f), 0.95f);
         // M-step with the new weights, then residuals and sigma^2
-        for (int i = gwarp; i < n; i += nwarps) mstep_row(A, S, i, lane);
+        for (int i = gwarp; i < n; i += nwarps) mstep_row(A, S, i, lane, false);
         st = barrier_status(A, epoch, &s_flag, ncta);
         if (st < EMDQ_EDEGENERATE) st = residuals_and_barrier();
         if (st < EMDQ_EDEGENERATE) sigma2 = load_e_and_sigma2();
@@ -411,7 +459,7 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
     }
 }
 
-__global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_kernel(FitArgs A)
+__global__ void __launch_bounds__(kFitThreads, 2) emdq_fit_kernel(FitArgs A)
 {
     fit_body(A, blockIdx.x, gridDim.x);
 }
@@ -423,7 +471,7 @@ struct FitBatch {
     FitArgs a[kFitBatchMax];
 };
 
-__global__ void __launch_bounds__(kFitThreads, 1) emdq_fit_batch_kernel(const __grid_constant__ FitBatch B,
+__global__ void __launch_bounds__(kFitThreads, 2) emdq_fit_batch_kernel(const __grid_constant__ FitBatch B,
                                                                       int group)
 {
     const int b = blockIdx.x / group;
@@ -436,17 +484,20 @@ using namespace emdq;
 using namespace emdq_host;
 
 namespace {
+// Fit workspace: residuals e[n], centroids cen[n], per-CTA partial sums, then 256 bytes for
+// the barrier counter and the status word.
 struct FitLayout {
-    size_t e_off, part_off, bar_off, total;
+    size_t e_off, cen_off, part_off, bar_off, total;
 };
-FitLayout fit_layout(int n)
+constexpr size_t al256(size_t v) { return (v + 255) / 256 * 256; }
+constexpr FitLayout fit_layout(int n)
 {
-    FitLayout L;
-    L.e_off = 0;
-    L.part_off = align_up(sizeof(float) * (size_t)n, 256);
-    L.bar_off = L.part_off + align_up(sizeof(double) * 2 * kFitMaxGrid, 256);
-    L.total = L.bar_off + 256;
-    return L;
+    return FitLayout{0, al256(sizeof(float) * (size_t)n),
+                     al256(sizeof(float) * (size_t)n) + al256(sizeof(float4) * (size_t)n),
+                     al256(sizeof(float) * (size_t)n) + al256(sizeof(float4) * (size_t)n) +
+                         al256(sizeof(double) * 2 * kFitMaxGrid),
+                     al256(sizeof(float) * (size_t)n) + al256(sizeof(float4) * (size_t)n) +
+                         al256(sizeof(double) * 2 * kFitMaxGrid) + 256};
 }
 size_t fit_smem_bytes(int n) { return (size_t)n * 40; }
 }  // namespace
@@ -521,6 +572,7 @@ extern "C" emdq_status emdq_fit(const float *src, const float *dst, int n, int f
     A.p_out = p_out;
     A.info = info;
     A.e = reinterpret_cast<float *>(ws + L.e_off);
+    A.cen = reinterpret_cast<float4 *>(ws + L.cen_off);
     A.partials = reinterpret_cast<float *>(ws + L.part_off);
     A.bar = reinterpret_cast<unsigned *>(ws + L.bar_off);
     A.flag = reinterpret_cast<int *>(ws + L.bar_off + 64);
@@ -547,7 +599,7 @@ namespace {
 // partial sums.
 size_t batch_body_bytes(int n)
 {
-    return align_up(sizeof(float) * (size_t)n, 256) + align_up(sizeof(double) * 2 * kFitMaxGrid, 256);
+    return fit_layout(n).bar_off;      // e, cen and partials; the headers are packed first
 }
 }  // namespace
 
@@ -635,8 +687,10 @@ extern "C" emdq_status emdq_fit_batch(const emdq_fit_problem *problems, int coun
         A.info = q.info;
         A.bar = reinterpret_cast<unsigned *>(ws + 256 * (size_t)b);
         A.flag = reinterpret_cast<int *>(ws + 256 * (size_t)b + 64);
-        A.e = reinterpret_cast<float *>(ws + off);
-        A.partials = reinterpret_cast<float *>(ws + off + align_up(sizeof(float) * (size_t)q.n, 256));
+        const FitLayout L = fit_layout(q.n);
+        A.e = reinterpret_cast<float *>(ws + off + L.e_off);
+        A.cen = reinterpret_cast<float4 *>(ws + off + L.cen_off);
+        A.partials = reinterpret_cast<float *>(ws + off + L.part_off);
         off += batch_body_bytes(q.n);
     }
     cudaLaunchConfig_t cfg = {};
@@ -660,10 +714,7 @@ extern "C" emdq_status emdq_fit_batch(const emdq_fit_problem *problems, int coun
 // caller workspace.  Every GPU that loads the library holds the array until exit.
 namespace {
 
-constexpr size_t kNoAllocScratchBytes =
-    ((sizeof(float) * kFitMaxN + 255) / 256) * 256 +          // residuals
-    ((sizeof(double) * 2 * kFitMaxGrid + 255) / 256) * 256 +  // per-CTA partial sums
-    256;                                                       // barrier counter, status
+constexpr size_t kNoAllocScratchBytes = fit_layout(kFitMaxN).total;   // about 118 KB
 
 static __device__ __align__(256) unsigned char g_fit_scratch[kNoAllocScratchBytes];
 
