@@ -53,6 +53,10 @@ def parse_args():
     ap.add_argument('--precision', default='bf16', choices=['bf16', 'fp32'])
     ap.add_argument('--workload', default='seq1280')
     ap.add_argument('--seed', type=int, default=0)
+    ap.add_argument('--frames', type=int, default=0,
+                    help='frames per step (default: the whole sequence of the workload)')
+    ap.add_argument('--min-warmup-s', type=float, default=0.5,
+                    help='keep warming up for at least this long (clock ramp)')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--batch', type=int, default=16,
@@ -174,6 +178,8 @@ def run_gpu(args, ws, rank, local):
     prec = emdq.BF16 if args.precision == 'bf16' else emdq.FP32
     from synth import WORKLOADS
     n_frames = WORKLOADS[args.workload]['frames']
+    if args.frames > 0:
+        n_frames = min(n_frames, args.frames)
     sc, cfg, origin, ref, frames, src, dst, grids = prepare_sequence(
         args.workload, args.seed + 1000 * rank, n_frames, dev)
     cw, chh = cfg['canvas']
@@ -275,7 +281,7 @@ def run_gpu(args, ws, rank, local):
     # warm-up: W passes, and at least half a second of work so clocks have ramped
     t0 = time.perf_counter()
     w = 0
-    while w < args.warmup or time.perf_counter() - t0 < 0.5:
+    while w < args.warmup or time.perf_counter() - t0 < args.min_warmup_s:
         flush.zero_()
         one_pass()
         torch.cuda.synchronize()
