@@ -232,6 +232,40 @@ EMDQ_API emdq_status emdq_mosaic(const float *q, const float *c, const float *sr
                         int origin_x, int origin_y, void *workspace, size_t workspace_bytes,
                         void *stream);
 
+/* ------------------------------------------------------------------ learned warm start
+ * Not in the paper (the paper's EMDQ starts EM without a prior).  A 16-64-64-1 network
+ * predicts each match's initial inlier weight p0 for emdq_fit from residuals to its 8
+ * nearest matches under the step-0 warps, so that EM starts closer to its answer; plain EM
+ * (p0 = NULL) remains the fallback.  Inference and training run in these kernels.
+ *
+ * Features of match j (feat_out row, 16 floats): with q0/info0 the output of an emdq_fit
+ * call with max_iters = 0 (the step-0 warps W and residual variance s0^2) and k over the 8
+ * nearest matches (float32 squared distances, ties to the lower index):
+ *   log(1 + |y_k - W_j(x_k)| / s0) for the 8 k, sorted ascending, then
+ *   log(1 + |y_j - W_k(x_j)| / s0) for the 8 k, sorted ascending.
+ * Network parameters (emdq_mlp_param_count() = 5313 floats, device): W1[64][16], b1[64],
+ * W2[64][64], b2[64], W3[64], b3; ReLU hidden layers, logistic output.  The forward rounds
+ * parameters, inputs and hidden activations to BF16 and accumulates in FP32.
+ *
+ * emdq_mlp_train_step: mean binary cross-entropy over `batch` samples (feat rows, labels
+ * 0/1); writes the mean gradient to grad_out and the mean loss to loss_out (each may be
+ * NULL); if step >= 1, applies Adam step number `step` (beta1 0.9, beta2 0.999,
+ * eps 1e-8, learning rate lr) to the FP32 params with moments adam_m, adam_v (5313 floats
+ * each, zero before step 1).  step = 0 computes the gradient only.
+ */
+EMDQ_API int         emdq_mlp_param_count(void);
+EMDQ_API emdq_status emdq_warm_features(const float *src, const float *dst, int n,
+                                        const float *q0, const emdq_fit_info *info0,
+                                        float *feat_out, void *stream);
+EMDQ_API emdq_status emdq_warm_infer(const float *feat, int n, const float *params,
+                                     float *p0_out, void *stream);
+EMDQ_API size_t      emdq_mlp_train_workspace_size(int batch);
+EMDQ_API emdq_status emdq_mlp_train_step(const float *feat, const float *label, int batch,
+                                         float *params, float *adam_m, float *adam_v,
+                                         int step, float lr, float *grad_out, float *loss_out,
+                                         void *workspace, size_t workspace_bytes,
+                                         void *stream);
+
 /* Sec. III-F: "frame 0 is inserted directly" -- copy the reference frame into the canvas
  * at the origin with merge weight 1. */
 EMDQ_API emdq_status mosaic_insert_reference(const uint8_t *frame, int fw, int fh, int channels,

@@ -82,6 +82,15 @@ def lib() -> ctypes.CDLL:
             L.emdq_mosaic.restype = I
             L.emdq_mosaic.argtypes = [P, P, P, I, I, I, I, I, F, P, I, I, I, I, P, I, I, I, I, I,
                                       P, Z, P]
+            L.emdq_mlp_param_count.restype = I
+            L.emdq_warm_features.restype = I
+            L.emdq_warm_features.argtypes = [P, P, I, P, P, P, P]
+            L.emdq_warm_infer.restype = I
+            L.emdq_warm_infer.argtypes = [P, I, P, P, P]
+            L.emdq_mlp_train_workspace_size.restype = Z
+            L.emdq_mlp_train_workspace_size.argtypes = [I]
+            L.emdq_mlp_train_step.restype = I
+            L.emdq_mlp_train_step.argtypes = [P, P, I, P, P, P, I, F, P, P, P, Z, P]
             L.mosaic_insert_reference.restype = I
             L.mosaic_insert_reference.argtypes = [P, I, I, I, I, P, I, I, I, I, I, P]
             _lib = L
@@ -290,3 +299,80 @@ def mosaic_insert_reference(frame: torch.Tensor, canvas: torch.Tensor, origin, s
                                        cw * 4, int(origin[0]), int(origin[1]), _stream(stream))
     if rc != 0:
         raise EmdqError('mosaic_insert_reference', rc)
+
+
+# ---------------------------------------------------------------- learned warm start ----
+WARMSTART_PARAMS = os.path.join(os.path.dirname(os.path.abspath(__file__)), 'warmstart_mlp.npy')
+
+
+def mlp_param_count() -> int:
+    return lib().emdq_mlp_param_count()
+
+
+def warm_features(src: torch.Tensor, dst: torch.Tensor, q0: torch.Tensor, info0: torch.Tensor,
+                  out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """[n, 16] warm-start features from the step-0 fit (q0, info0 of emdq_fit(max_iters=0))."""
+    n = src.shape[0]
+    _check(src, 'src', torch.float32, (n, 2))
+    _check(dst, 'dst', torch.float32, (n, 2))
+    _check(q0, 'q0', torch.float32, (n, 8))
+    _check(info0, 'info0', torch.int32, (4,))
+    if out is None:
+        out = torch.empty((n, 16), dtype=torch.float32, device=src.device)
+    _check(out, 'out', torch.float32, (n, 16))
+    rc = lib().emdq_warm_features(_ptr(src), _ptr(dst), n, _ptr(q0), _ptr(info0), _ptr(out),
+                                  _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_warm_features', rc)
+    return out
+
+
+def warm_infer(feat: torch.Tensor, params: torch.Tensor, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """p0 [n] from features [n, 16] and the 5313 network parameters (float32, CUDA)."""
+    n = feat.shape[0]
+    _check(feat, 'feat', torch.float32, (n, 16))
+    _check(params, 'params', torch.float32, (mlp_param_count(),))
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=feat.device)
+    rc = lib().emdq_warm_infer(_ptr(feat), n, _ptr(params), _ptr(out), _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_warm_infer', rc)
+    return out
+
+
+def mlp_train_step(feat: torch.Tensor, label: torch.Tensor, params: torch.Tensor,
+                   adam_m: torch.Tensor | None, adam_v: torch.Tensor | None, step: int,
+                   lr: float, grad_out: torch.Tensor | None = None,
+                   loss_out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                   stream=None) -> None:
+    """One training step of the warm-start network (step 0: gradient and loss only)."""
+    b = feat.shape[0]
+    _check(feat, 'feat', torch.float32, (b, 16))
+    _check(label, 'label', torch.float32, (b,))
+    _check(params, 'params', torch.float32, (mlp_param_count(),))
+    ws = _workspace(lib().emdq_mlp_train_workspace_size(b), feat.device, workspace)
+    rc = lib().emdq_mlp_train_step(_ptr(feat), _ptr(label), b, _ptr(params), _ptr(adam_m),
+                                   _ptr(adam_v), int(step), float(lr), _ptr(grad_out),
+                                   _ptr(loss_out), _ptr(ws), ws.numel(), _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_mlp_train_step', rc)
+
+
+def load_warmstart_params(device='cuda') -> torch.Tensor:
+    """The trained warm-start parameters shipped with the package."""
+    import numpy as np
+    w = np.load(WARMSTART_PARAMS).astype(np.float32)
+    if w.shape != (mlp_param_count(),):
+        raise ValueError(f'{WARMSTART_PARAMS}: expected {mlp_param_count()} parameters')
+    return torch.from_numpy(w).to(device)
+
+
+def warm_start_p0(src: torch.Tensor, dst: torch.Tensor, frame_w: int, frame_h: int,
+                  params: torch.Tensor, *, alpha: float = 0.0, sigma2_floor: float = 0.25,
+                  stream=None) -> torch.Tensor:
+    """p0 for emdq_fit: step-0 fit (max_iters = 0), features, network."""
+    f0 = emdq_fit(src, dst, frame_w, frame_h, alpha=alpha, max_iters=0,
+                  sigma2_floor=sigma2_floor, stream=stream)
+    feat = warm_features(src, dst, f0['q'], f0['info'], stream=stream)
+    return warm_infer(feat, params, stream=stream)

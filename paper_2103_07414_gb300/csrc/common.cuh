@@ -19,6 +19,15 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
     return v;
 }
 
+// 2^x with one MUFU.EX2 (ftz: results below 2^-126 flush to 0, a weight that no sum
+// notices next to the nearest match's).
+__device__ __forceinline__ float ex2_ftz(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Blended planar DQ (a, b, u, v) = (r_w, r_z, d_x, d_y), not normalised, and scale s,
 // applied to p: s (R p + t) with R, t of the normalised DQ.  With n2 = a^2 + b^2:
 //   cos th = (a^2 - b^2)/n2, sin th = 2ab/n2, t = 2 (a u - b v, b u + a v)/n2

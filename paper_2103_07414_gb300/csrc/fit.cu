@@ -172,7 +172,7 @@ __device__ void mstep_row(const FitArgs &A, const FitSmem &S, int i, int lane, b
         for (int j = lane; j < n; j += 32) {
             const float2 xj = S.x[j], yj = S.y[j];
             const float a0 = xj.x - xi.x, a1 = xj.y - xi.y;
-            const float om = S.p[j] * exp2f(-A.alpha2 * (a0 * a0 + a1 * a1));
+            const float om = S.p[j] * ex2_ftz(-A.alpha2 * (a0 * a0 + a1 * a1));
             W += om;
             sa0 += om * a0;
             sa1 += om * a1;
@@ -194,7 +194,7 @@ __device__ void mstep_row(const FitArgs &A, const FitSmem &S, int i, int lane, b
     for (int j = lane; j < n; j += 32) {
         const float2 xj = S.x[j], yj = S.y[j];
         const float a0 = xj.x - xi.x, a1 = xj.y - xi.y;
-        const float om = S.p[j] * exp2f(-A.alpha2 * (a0 * a0 + a1 * a1));
+        const float om = S.p[j] * ex2_ftz(-A.alpha2 * (a0 * a0 + a1 * a1));
         const float u0 = a0 - sh.x, u1 = a1 - sh.y;
         const float v0 = (yj.x - yi.x) - sh.z, v1 = (yj.y - yi.y) - sh.w;
         const float ou0 = om * u0, ou1 = om * u1;
@@ -251,7 +251,7 @@ __device__ float residual_row(const FitArgs &A, const FitSmem &S, int j, int lan
         if (i == j) continue;                         // leave one out
         const float2 xi = S.x[i];
         const float dx = xi.x - xj.x, dy = xi.y - xj.y;
-        const float w = S.p[i] * exp2f(-A.alpha2 * (dx * dx + dy * dy));
+        const float w = S.p[i] * ex2_ftz(-A.alpha2 * (dx * dx + dy * dy));
         w0 += w;
         a0 += w * (S.qa[i] - ra);
         a1 += w * (S.qb[i] - rb);

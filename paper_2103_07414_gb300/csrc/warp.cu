@@ -9,18 +9,43 @@ namespace emdq {
 
 constexpr int kWarpThreadsX = 128;
 
+// Each thread blends kWarpPix pixels of one row (x = x0 + threadIdx.x + k * kWarpThreadsX,
+// coalesced for every k), issuing all their loads before any update so several gathers
+// are in flight per thread.
+constexpr int kWarpPix = 4;
+
 template <int CH>
 __global__ void __launch_bounds__(kWarpThreadsX) mosaic_warp_kernel(
     const uint8_t *__restrict__ frame, int fw, int fh, int pitch,
     const float2 *__restrict__ disp, int gx0, int gy0, int gw, int gh,
     uchar4 *__restrict__ canvas, int cpitch4, int ox, int oy)
 {
-    const int x = blockIdx.x * kWarpThreadsX + threadIdx.x;
     const int y = blockIdx.y;
-    if (x >= gw) return;
-    const float2 d = __ldcs(disp + (size_t)y * gw + x);
-    blend_pixel<CH>(frame, fw, fh, pitch, static_cast<float>(gx0 + x), static_cast<float>(gy0 + y),
-                    d.x, d.y, canvas + (size_t)(gy0 + y + oy) * cpitch4 + (gx0 + x + ox));
+    const int xb = blockIdx.x * (kWarpThreadsX * kWarpPix) + threadIdx.x;
+    float2 d[kWarpPix];
+#pragma unroll
+    for (int k = 0; k < kWarpPix; ++k) {
+        const int x = xb + k * kWarpThreadsX;
+        d[k] = x < gw ? __ldcs(disp + (size_t)y * gw + x) : make_float2(NAN, NAN);
+    }
+    Tap t[kWarpPix];
+    uchar4 cv[kWarpPix];
+    uchar4 *cp[kWarpPix];
+#pragma unroll
+    for (int k = 0; k < kWarpPix; ++k) {
+        const int x = xb + k * kWarpThreadsX;
+        t[k] = tap_setup<CH>(fw, fh, pitch, static_cast<float>(gx0 + x), static_cast<float>(gy0 + y),
+                             d[k].x, d[k].y);
+        cp[k] = canvas + (size_t)(gy0 + y + oy) * cpitch4 + (gx0 + x + ox);
+        if (t[k].ok) cv[k] = *cp[k];
+    }
+    float v[kWarpPix][CH];
+#pragma unroll
+    for (int k = 0; k < kWarpPix; ++k)
+        if (t[k].ok) tap_sample<CH>(frame, t[k], v[k]);
+#pragma unroll
+    for (int k = 0; k < kWarpPix; ++k)
+        if (t[k].ok) *cp[k] = blend_update<CH>(cv[k], v[k]);
 }
 
 template <int CH>
@@ -62,7 +87,7 @@ extern "C" emdq_status mosaic_warp(const uint8_t *frame, int fw, int fh, int cha
         return EMDQ_EINVAL;
     if (grid_h > 65535) return EMDQ_ENOTSUP;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    dim3 grid((grid_w + kWarpThreadsX - 1) / kWarpThreadsX, grid_h);
+    dim3 grid((grid_w + kWarpThreadsX * kWarpPix - 1) / (kWarpThreadsX * kWarpPix), grid_h);
     auto *cv = reinterpret_cast<uchar4 *>(canvas);
     const auto *d = reinterpret_cast<const float2 *>(disp);
     if (channels == 3)

@@ -1,0 +1,142 @@
+"""Training and evaluation driver of the learned EM warm start (test infrastructure).
+
+Training data: matches of seeded 640x480 scenes (N = 200, outlier rate 10-45 %, noise
+0.5-2 px); features from the library's step-0 fit and feature kernel; labels = the FP64
+oracle EMDQ's inlier decision at convergence (posterior >= 1/2).  Training runs on the GPU
+through the library's own forward/backward/Adam kernels (emdq_mlp_train_step).
+
+    python tests/warmstart_train.py --seeds 1000 --out gpurun_out/warmstart_mlp.npy
+
+writes the trained parameters (5313 float32) that the package ships as
+paper_2103_07414_gb300/warmstart_mlp.npy.  `evaluate` compares plain EM with the warm-started
+EM on the 1280x1024, N = 2000, 40 % outlier workload: EM iterations and field error.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def make_training_set(seeds, n=200, w=640, h=480, device='cuda'):
+    """Features (GPU kernels) and labels (oracle) of len(seeds) synthetic pairs."""
+    import torch
+
+    import oracle
+    import paper_2103_07414_gb300 as emdq
+    from synth import make_matches, make_scene
+    feats, labels = [], []
+    for seed in seeds:
+        g = np.random.Generator(np.random.Philox(key=[int(seed), 91]))
+        out_frac = float(g.uniform(0.10, 0.45))
+        noise = float(g.uniform(0.5, 2.0))
+        sc = make_scene(int(seed), w, h, 1)
+        s, d, _ = make_matches(sc, 1, n, out_frac, noise)
+        f64 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+        ref = oracle.fit(f64(s), f64(d), w, h)
+        st, dt = torch.from_numpy(s).to(device), torch.from_numpy(d).to(device)
+        f0 = emdq.emdq_fit(st, dt, w, h, max_iters=0)
+        feats.append(emdq.warm_features(st, dt, f0['q'], f0['info']))
+        labels.append(torch.from_numpy((ref['c'] > 0).astype(np.float32)).to(device))
+    return torch.cat(feats), torch.cat(labels)
+
+
+def train(feat, label, steps=3000, batch=1024, lr=3e-3, seed=0, log_every=0):
+    """Adam on the mean cross-entropy, in the library's kernels.  Returns (params, losses)."""
+    import torch
+
+    import oracle.warmstart as ows
+    import paper_2103_07414_gb300 as emdq
+    dev = feat.device
+    params = torch.from_numpy(ows.init_params(seed).astype(np.float32)).to(dev)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    loss = torch.zeros(1, device=dev)
+    xb = torch.empty((batch, 16), device=dev)
+    yb = torch.empty(batch, device=dev)
+    ws = torch.empty(emdq.lib().emdq_mlp_train_workspace_size(batch), dtype=torch.uint8, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    M = feat.shape[0]
+    perm = torch.randperm(M, device=dev, generator=gen)
+    pos = 0
+    losses = []
+    for step in range(1, steps + 1):
+        if pos + batch > M:
+            perm = torch.randperm(M, device=dev, generator=gen)
+            pos = 0
+        idx = perm[pos:pos + batch]
+        pos += batch
+        torch.index_select(feat, 0, idx, out=xb)
+        torch.index_select(label, 0, idx, out=yb)
+        emdq.mlp_train_step(xb, yb, params, m, v, step, lr, loss_out=loss, workspace=ws)
+        if log_every and step % log_every == 0:
+            losses.append((step, float(loss.item())))
+    return params, losses
+
+
+def evaluate(params, seeds=(0, 1, 2), name='warm2000', device='cuda'):
+    """Plain vs warm-started EM on a workload: iterations and field RMS error vs ground truth."""
+    import torch
+
+    import oracle
+    import paper_2103_07414_gb300 as emdq
+    from synth import gt_forward, make_matches, workload
+    rows = []
+    for seed in seeds:
+        sc, cfg = workload(name, seed=seed)
+        s, d, inl = make_matches(sc, 1, cfg['n'], cfg['outliers'], cfg['noise'])
+        st, dt = torch.from_numpy(s).to(device), torch.from_numpy(d).to(device)
+        g = np.random.default_rng(seed)
+        P = np.stack([g.uniform(96, sc.w - 96, 3000), g.uniform(96, sc.h - 96, 3000)], 1)
+        gt = gt_forward(sc, torch.from_numpy(P), 1).numpy() - P
+        alpha = float(np.float32(oracle.alpha_for_frame(sc.w, sc.h)))
+        res = {}
+        for mode in ('plain', 'warm'):
+            p0 = emdq.warm_start_p0(st, dt, sc.w, sc.h, params) if mode == 'warm' else None
+            r = emdq.emdq_fit(st, dt, sc.w, sc.h, p0=p0)
+            info = emdq.read_fit_info(r['info'])
+            q = r['q'].cpu().numpy().astype(np.float64)
+            c = r['c'].cpu().numpy().astype(np.float64)
+            dfield = oracle.field_points(q, c, np.float32(s).astype(np.float64), P, alpha)
+            err = np.sqrt(((dfield - gt) ** 2).sum(1))
+            lab = c > 0
+            res[mode] = dict(iters=info['iters'], status=info['status_name'],
+                             rms=float(np.sqrt((err ** 2).mean())),
+                             precision=float((lab & inl).sum() / max(1, lab.sum())),
+                             recall=float((lab & inl).sum() / inl.sum()))
+        rows.append(res)
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--seeds', type=int, default=1000)
+    ap.add_argument('--steps', type=int, default=3000)
+    ap.add_argument('--out', default='gpurun_out/warmstart_mlp.npy')
+    args = ap.parse_args()
+    import torch
+    t0 = time.time()
+    feat, label = make_training_set(range(10_000, 10_000 + args.seeds))
+    print(f'training set: {feat.shape[0]} matches, inlier fraction {float(label.mean()):.3f}, '
+          f'{time.time() - t0:.1f} s', flush=True)
+    t0 = time.time()
+    params, losses = train(feat, label, steps=args.steps, log_every=max(1, args.steps // 10))
+    torch.cuda.synchronize()
+    print(f'trained {args.steps} steps in {time.time() - t0:.2f} s; loss ' +
+          ', '.join(f'{s}:{l:.4f}' for s, l in losses), flush=True)
+    os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+    np.save(args.out, params.cpu().numpy())
+    for r in evaluate(params):
+        print(r, flush=True)
+
+
+if __name__ == '__main__':
+    main()
