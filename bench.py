@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--batch', type=int, default=16,
                     help='frames whose EM fits share one launch (1: one emdq_fit per frame)')
+    ap.add_argument('--no-warm', action='store_true',
+                    help='plain EM (default: learned warm start when its parameters ship)')
     ap.add_argument('--fused', action='store_true',
                     help='BF16 field and warp in one emdq_mosaic call (default: emdq_field + mosaic_warp)')
     ap.add_argument('--no-overlap', action='store_true',
@@ -212,6 +214,10 @@ def run_gpu(args, ws, rank, local):
     fit_ws_all = [torch.empty(emdq.fit_workspace_size(n), dtype=torch.uint8, device=dev)
                   for _ in range(nbuf)]
     fit_stream = torch.cuda.Stream(device=dev) if overlap else stream
+    warm = (not args.no_warm) and os.path.exists(emdq.WARMSTART_PARAMS)
+    warm_params = emdq.load_warmstart_params(dev) if warm else None
+    warm_feat = [torch.empty((n, 16), device=dev) for _ in range(B)]
+    warm_p0 = [[torch.empty(n, device=dev) for _ in range(B)] for _ in range(nbuf)]
 
     def field_and_warp(fr, s_, g, fo):
         if fused:
@@ -226,12 +232,18 @@ def run_gpu(args, ws, rank, local):
         """The fits of batch bi (frames ks) on the fit stream; returns its done event."""
         outs = fit_outs_all[bi % nbuf]
         with torch.cuda.stream(fit_stream):
+            p0s = [None] * len(ks)
+            if warm:
+                for j, k in enumerate(ks):
+                    p0s[j] = emdq.warm_start_p0(s_of(k), d_of(k), warm_params, feat=warm_feat[j],
+                                                out=warm_p0[bi % nbuf][j], stream=fit_stream)
             if B == 1:
-                emdq.emdq_fit(s_of(ks[0]), d_of(ks[0]), sc.w, sc.h, out=outs[0],
+                emdq.emdq_fit(s_of(ks[0]), d_of(ks[0]), sc.w, sc.h, p0=p0s[0], out=outs[0],
                               workspace=fit_ws_all[bi % nbuf], stream=fit_stream)
             else:
-                emdq.emdq_fit_batch([(s_of(k), d_of(k), sc.w, sc.h) for k in ks], outs=outs[: len(ks)],
-                                    workspace=batch_ws[bi % nbuf], stream=fit_stream)
+                emdq.emdq_fit_batch([(s_of(k), d_of(k), sc.w, sc.h, p0s[j]) for j, k in enumerate(ks)],
+                                    outs=outs[: len(ks)], workspace=batch_ws[bi % nbuf],
+                                    stream=fit_stream)
             done = torch.cuda.Event()
             done.record(fit_stream)
         return done
@@ -431,12 +443,13 @@ def run_gpu(args, ws, rank, local):
                     mean_window_px=win_px, mean_em_iters=mean_iters),
         phases_ms=dict(fit=float(phase_ms[0]), **({'mosaic': float(phase_ms[1])} if fused else
                                                    {'field+warp': float(phase_ms[1])})),
-        path=(('emdq_fit_batch' if B > 1 else 'emdq_fit') +
+        path=(('learned warm start + ' if warm else '') + ('emdq_fit_batch' if B > 1 else 'emdq_fit') +
               (' + emdq_mosaic (fused BF16 field and warp)' if fused else
                f' + emdq_field ({args.precision}) + mosaic_warp') +
               (', fits of the next batch on a second stream' if overlap else '')),
-        batch=B, wall_s=wall, roofline=roof,
-        gpu_launches=total_frames * (2 if fused else 3) + args.steps * len(batches), clocks=clk,
+        batch=B, warm_start=warm, wall_s=wall, roofline=roof,
+        gpu_launches=total_frames * ((2 if fused else 3) + (2 if warm else 0)) +
+        args.steps * len(batches), clocks=clk,
         e2e=e2e,
         fit_status=statuses,
     )

@@ -234,15 +234,15 @@ EMDQ_API emdq_status emdq_mosaic(const float *q, const float *c, const float *sr
 
 /* ------------------------------------------------------------------ learned warm start
  * Not in the paper (the paper's EMDQ starts EM without a prior).  A 16-64-64-1 network
- * predicts each match's initial inlier weight p0 for emdq_fit from residuals to its 8
- * nearest matches under the step-0 warps, so that EM starts closer to its answer; plain EM
+ * predicts each match's initial inlier weight p0 for emdq_fit from its 8 nearest
+ * matches, so that EM starts closer to its answer and needs fewer iterations; plain EM
  * (p0 = NULL) remains the fallback.  Inference and training run in these kernels.
  *
- * Features of match j (feat_out row, 16 floats): with q0/info0 the output of an emdq_fit
- * call with max_iters = 0 (the step-0 warps W and residual variance s0^2) and k over the 8
- * nearest matches (float32 squared distances, ties to the lower index):
- *   log(1 + |y_k - W_j(x_k)| / s0) for the 8 k, sorted ascending, then
- *   log(1 + |y_j - W_k(x_j)| / s0) for the 8 k, sorted ascending.
+ * Features of match j (feat_out row, 16 floats), k over the 8 nearest matches by
+ * |x_k - x_j| (float32 squared distances, ties to the lower index), in pixels:
+ *   log(1 + |(y_k - x_k) - (y_j - x_j)|) for the 8 k, sorted ascending (k's residual
+ *     under the translation j implies: no fit needed, robust to many outliers), then
+ *   log(1 + |x_k - x_j|) for the 8 k, ascending (the scale for judging those residuals).
  * Network parameters (emdq_mlp_param_count() = 5313 floats, device): W1[64][16], b1[64],
  * W2[64][64], b2[64], W3[64], b3; ReLU hidden layers, logistic output.  The forward rounds
  * parameters, inputs and hidden activations to BF16 and accumulates in FP32.
@@ -255,7 +255,6 @@ EMDQ_API emdq_status emdq_mosaic(const float *q, const float *c, const float *sr
  */
 EMDQ_API int         emdq_mlp_param_count(void);
 EMDQ_API emdq_status emdq_warm_features(const float *src, const float *dst, int n,
-                                        const float *q0, const emdq_fit_info *info0,
                                         float *feat_out, void *stream);
 EMDQ_API emdq_status emdq_warm_infer(const float *feat, int n, const float *params,
                                      float *p0_out, void *stream);

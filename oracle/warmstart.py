@@ -5,23 +5,24 @@ small network predicts each match's initial inlier weight p0 from residuals to i
 nearest matches, so that EM starts closer to its answer.  Every step is the plain
 definition in float64 numpy; the GPU kernels are checked against it.
 
-Features of match j (16 numbers), from the step-0 fit (the M-step with all weights 1,
-its warp rows W_i and its residual variance sigma0^2):
-  - K = 8 nearest matches k != j by |x_k - x_j| in the reference frame, ties broken by
-    the lower index.  The squared distances are compared in float32 (the kernel's
-    precision: this is an integer decision);
-  - f1_k = log(1 + |y_k - W_j(x_k)| / sigma0): the neighbours' residuals under j's warp;
-  - f2_k = log(1 + |y_j - W_k(x_j)| / sigma0): j's residual under each neighbour's warp;
+Features of match j (16 numbers), from its K = 8 nearest matches k != j by |x_k - x_j|
+in the reference frame (ties broken by the lower index; the squared distances are compared
+in float32, the kernel's precision, as this is an integer decision):
+  - f1_k = log(1 + |(y_k - x_k) - (y_j - x_j)| / 1 px): the residual of neighbour k under
+    the translation that match j implies -- a consistency test that needs no fit, so it
+    stays informative when many matches are outliers;
+  - f2_k = log(1 + |x_k - x_j| / 1 px): the neighbour's distance, the scale against which
+    the network judges the residuals (a smooth field separates nearby matches' motions
+    in proportion to their distance);
   - each group of 8 sorted ascending; features = [f1 (8), f2 (8)].
 Network: 16 -> 64 (ReLU) -> 64 (ReLU) -> 1 (logistic); loss: mean binary cross-entropy
-against the label "oracle posterior >= 1/2 at convergence"; optimiser: Adam.
+against the oracle posterior at convergence (soft labels); optimiser: Adam.
 Parameter vector (5313 values): W1[64][16], b1[64], W2[64][64], b2[64], W3[64], b3[1].
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import apply_warp
 
 K_NN = 8
 N_IN, N_H = 16, 64
@@ -69,22 +70,17 @@ def knn(src, k: int = K_NN) -> np.ndarray:
     return out
 
 
-def features(src, dst, q8, sigma2_0) -> np.ndarray:
+def features(src, dst) -> np.ndarray:
     """[n, 16] features of every match (see the module docstring)."""
     src = np.asarray(src, np.float64)
     dst = np.asarray(dst, np.float64)
-    q8 = np.asarray(q8, np.float64)
-    sig = np.sqrt(float(sigma2_0))
+    disp = dst - src
     nn = knn(src)
     n = src.shape[0]
     f = np.empty((n, 2 * K_NN))
     for j in range(n):
-        f1, f2 = [], []
-        for k in nn[j]:
-            pk = apply_warp(q8[j, 4], q8[j, :4], *src[k])
-            f1.append(np.log1p(np.hypot(*(dst[k] - pk)) / sig))
-            pj = apply_warp(q8[k, 4], q8[k, :4], *src[j])
-            f2.append(np.log1p(np.hypot(*(dst[j] - pj)) / sig))
+        f1 = [np.log1p(np.hypot(*(disp[k] - disp[j]))) for k in nn[j]]
+        f2 = [np.log1p(np.hypot(*(src[k] - src[j]))) for k in nn[j]]
         f[j, :K_NN] = np.sort(f1)
         f[j, K_NN:] = np.sort(f2)
     return f

@@ -84,7 +84,7 @@ def lib() -> ctypes.CDLL:
                                       P, Z, P]
             L.emdq_mlp_param_count.restype = I
             L.emdq_warm_features.restype = I
-            L.emdq_warm_features.argtypes = [P, P, I, P, P, P, P]
+            L.emdq_warm_features.argtypes = [P, P, I, P, P]
             L.emdq_warm_infer.restype = I
             L.emdq_warm_infer.argtypes = [P, I, P, P, P]
             L.emdq_mlp_train_workspace_size.restype = Z
@@ -309,19 +309,16 @@ def mlp_param_count() -> int:
     return lib().emdq_mlp_param_count()
 
 
-def warm_features(src: torch.Tensor, dst: torch.Tensor, q0: torch.Tensor, info0: torch.Tensor,
-                  out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """[n, 16] warm-start features from the step-0 fit (q0, info0 of emdq_fit(max_iters=0))."""
+def warm_features(src: torch.Tensor, dst: torch.Tensor, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """[n, 16] warm-start features of n matches."""
     n = src.shape[0]
     _check(src, 'src', torch.float32, (n, 2))
     _check(dst, 'dst', torch.float32, (n, 2))
-    _check(q0, 'q0', torch.float32, (n, 8))
-    _check(info0, 'info0', torch.int32, (4,))
     if out is None:
         out = torch.empty((n, 16), dtype=torch.float32, device=src.device)
     _check(out, 'out', torch.float32, (n, 16))
-    rc = lib().emdq_warm_features(_ptr(src), _ptr(dst), n, _ptr(q0), _ptr(info0), _ptr(out),
-                                  _stream(stream))
+    rc = lib().emdq_warm_features(_ptr(src), _ptr(dst), n, _ptr(out), _stream(stream))
     if rc != 0:
         raise EmdqError('emdq_warm_features', rc)
     return out
@@ -368,11 +365,9 @@ def load_warmstart_params(device='cuda') -> torch.Tensor:
     return torch.from_numpy(w).to(device)
 
 
-def warm_start_p0(src: torch.Tensor, dst: torch.Tensor, frame_w: int, frame_h: int,
-                  params: torch.Tensor, *, alpha: float = 0.0, sigma2_floor: float = 0.25,
+def warm_start_p0(src: torch.Tensor, dst: torch.Tensor, params: torch.Tensor, *,
+                  feat: torch.Tensor | None = None, out: torch.Tensor | None = None,
                   stream=None) -> torch.Tensor:
-    """p0 for emdq_fit: step-0 fit (max_iters = 0), features, network."""
-    f0 = emdq_fit(src, dst, frame_w, frame_h, alpha=alpha, max_iters=0,
-                  sigma2_floor=sigma2_floor, stream=stream)
-    feat = warm_features(src, dst, f0['q'], f0['info'], stream=stream)
-    return warm_infer(feat, params, stream=stream)
+    """p0 for emdq_fit: nearest-neighbour features, then the network."""
+    feat = warm_features(src, dst, out=feat, stream=stream)
+    return warm_infer(feat, params, out=out, stream=stream)

@@ -2,10 +2,11 @@
 // network with BF16 operands and FP32 accumulation that predicts each match's initial
 // inlier weight p0, and the kernels that train it (forward, backward, Adam).
 //
-// Features of match j (from the step-0 fit: warp rows W_i and residual variance s0^2):
-// the 8 nearest matches k != j by |x_k - x_j| (float32 squared distances, ties to the
-// lower index); f1_k = log(1 + |y_k - W_j(x_k)| / s0), f2_k = log(1 + |y_j - W_k(x_j)| / s0),
-// each group sorted ascending.  Parameters (5313 floats): W1[64][16], b1[64], W2[64][64],
+// Features of match j: its 8 nearest matches k != j by |x_k - x_j| (float32 squared
+// distances, ties to the lower index); f1_k = log(1 + |(y_k - x_k) - (y_j - x_j)|) (the
+// residual of k under the translation j implies: needs no fit, so it stays informative
+// with many outliers) and f2_k = log(1 + |x_k - x_j|) (the distance, the scale for
+// judging those residuals), in pixels, each group sorted ascending.  Parameters (5313 floats): W1[64][16], b1[64], W2[64][64],
 // b2[64], W3[64], b3.  The forward rounds parameters, inputs and hidden activations to
 // BF16 and accumulates in FP32; training keeps FP32 master weights.
 #include <cuda_bf16.h>
@@ -29,7 +30,7 @@ __device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2b
 // ------------------------------------------------------------------ features ----------
 __global__ void __launch_bounds__(kFeatThreads) warm_features_kernel(
     const float2 *__restrict__ src, const float2 *__restrict__ dst, int n,
-    const float *__restrict__ q0, const emdq_fit_info *__restrict__ info0, float *__restrict__ feat)
+    float *__restrict__ feat)
 {
     __shared__ float2 sx[kFeatChunk];
     const int j = blockIdx.x * kFeatThreads + threadIdx.x;
@@ -73,21 +74,15 @@ __global__ void __launch_bounds__(kFeatThreads) warm_features_kernel(
         }
     }
     if (j >= n) return;
-    const float s0 = sqrtf(info0->sigma2);
-    const float inv = 1.f / s0;
-    const float4 qj = *reinterpret_cast<const float4 *>(q0 + 8 * (size_t)j);
-    const float sj = q0[8 * (size_t)j + 4];
     const float2 yj = dst[j];
+    const float djx = yj.x - xj.x, djy = yj.y - xj.y;
     float f1[kKnn], f2[kKnn];
 #pragma unroll
     for (int k = 0; k < kKnn; ++k) {
         const int i = bi[k];
         const float2 xk = src[i], yk = dst[i];
-        const float2 pk = apply_blend(qj.x, qj.y, qj.z, qj.w, sj, xk.x, xk.y);
-        f1[k] = log1pf(hypotf(yk.x - pk.x, yk.y - pk.y) * inv);
-        const float4 qk = *reinterpret_cast<const float4 *>(q0 + 8 * (size_t)i);
-        const float2 pj = apply_blend(qk.x, qk.y, qk.z, qk.w, q0[8 * (size_t)i + 4], xj.x, xj.y);
-        f2[k] = log1pf(hypotf(yj.x - pj.x, yj.y - pj.y) * inv);
+        f1[k] = log1pf(hypotf((yk.x - xk.x) - djx, (yk.y - xk.y) - djy));
+        f2[k] = log1pf(sqrtf(bd[k]));      // already ascending
     }
     // sort each group ascending (odd-even transposition, fixed network)
 #pragma unroll
@@ -282,16 +277,14 @@ using namespace emdq_host;
 extern "C" int emdq_mlp_param_count(void) { return kNParams; }
 
 extern "C" emdq_status emdq_warm_features(const float *src, const float *dst, int n,
-                                          const float *q0, const emdq_fit_info *info0,
                                           float *feat_out, void *stream)
 {
-    if (!src || !dst || !q0 || !info0 || !feat_out || n < kKnn + 1) return EMDQ_EINVAL;
-    if (!aligned(src, 8) || !aligned(dst, 8) || !aligned(q0, 16) || !aligned(feat_out, 16))
+    if (!src || !dst || !feat_out || n < kKnn + 1) return EMDQ_EINVAL;
+    if (!aligned(src, 8) || !aligned(dst, 8) || !aligned(feat_out, 16))
         return EMDQ_EINVAL;
     warm_features_kernel<<<(n + kFeatThreads - 1) / kFeatThreads, kFeatThreads, 0,
                            static_cast<cudaStream_t>(stream)>>>(
-        reinterpret_cast<const float2 *>(src), reinterpret_cast<const float2 *>(dst), n, q0, info0,
-        feat_out);
+        reinterpret_cast<const float2 *>(src), reinterpret_cast<const float2 *>(dst), n, feat_out);
     return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }
 

@@ -29,11 +29,8 @@ def _pair(seed, n=200, outl=0.25, noise=1.0):
 def test_features_match_the_oracle(emdq):
     sc, s, d, _ = _pair(31, n=300)
     st, dt = torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda()
-    f0 = emdq.emdq_fit(st, dt, sc.w, sc.h, max_iters=0)
-    got = emdq.warm_features(st, dt, f0['q'], f0['info']).cpu().numpy()
-    info = emdq.read_fit_info(f0['info'])
-    want = ows.features(np.float32(s).astype(np.float64), np.float32(d).astype(np.float64),
-                        f0['q'].cpu().numpy().astype(np.float64), np.float32(info['sigma2']))
+    got = emdq.warm_features(st, dt).cpu().numpy()
+    want = ows.features(np.float32(s).astype(np.float64), np.float32(d).astype(np.float64))
     # same neighbour sets (float32 decisions on both sides); FP32 vs FP64 residuals
     assert np.abs(got - want).max() < 2e-4
 
@@ -90,7 +87,8 @@ def test_gradient_and_adam_match_the_oracle(emdq):
                                            grad.cpu().numpy().astype(np.float64),
                                            np.zeros_like(w), np.zeros_like(w), 1, 1e-3)
     assert np.abs(tw2.cpu().numpy() - w_want).max() < 1e-6
-    assert np.abs(m.cpu().numpy() - m_want).max() < 1e-9
+    # FP32 moments: one rounding of (1 - b1) g
+    assert np.all(np.abs(m.cpu().numpy() - m_want) <= 1e-6 * np.abs(m_want) + 1e-12)
 
 
 def test_training_reduces_the_loss(emdq):
@@ -104,7 +102,7 @@ def test_training_reduces_the_loss(emdq):
     emdq.mlp_train_step(feat, label, params, None, None, 0, 0.0, loss_out=l1)
     assert float(l1.item()) < 0.5 * float(l0.item())
     p = emdq.warm_infer(feat, params)
-    acc = float(((p >= 0.5).float() == label).float().mean().item())
+    acc = float(((p >= 0.5) == (label >= 0.5)).float().mean().item())
     assert acc > 0.95
 
 

@@ -72,18 +72,21 @@ def _similarity(x, s, th, t):
     return s * (x @ R.T + t)
 
 
-def test_features_vanish_on_an_exact_similarity_and_flag_an_outlier(orc):
+def test_features_on_a_translation_and_an_outlier():
+    """A pure translation: every consistency residual vanishes and the distances are the
+    nearest-neighbour distances.  One gross outlier: its residuals against its neighbours
+    exceed every inlier's smallest one."""
     g = np.random.default_rng(5)
     x = g.uniform(0, 639, (120, 2))
-    y = _similarity(x, 1.05, 0.08, np.array([12.0, -7.0]))
-    m = orc.mstep(x, y, np.ones(120), orc.alpha_for_frame(640, 480))
-    f = ws.features(x, y, m['q8'], 1.0)
-    assert np.abs(f).max() < 1e-9
-    y2 = y.copy()
+    y = x + np.array([12.0, -7.0])
+    f = ws.features(x, y)
+    assert np.abs(f[:, :8]).max() < 1e-9
+    from scipy.spatial import cKDTree
+    d, _ = cKDTree(np.float32(x).astype(np.float64)).query(np.float32(x).astype(np.float64), k=9)
+    np.testing.assert_allclose(f[:, 8:], np.log1p(d[:, 1:]), rtol=0, atol=1e-4)
+    y2 = _similarity(x, 1.02, 0.03, np.array([12.0, -7.0]))
     y2[7] += [40.0, 25.0]
-    m = orc.mstep(x, y2, np.ones(120), orc.alpha_for_frame(640, 480))
-    f = ws.features(x, y2, m['q8'], 1.0)
-    # the outlier's residual under its neighbours' warps exceeds every inlier's
+    f = ws.features(x, y2)
     others = np.delete(np.arange(120), 7)
-    assert f[7, 8:].min() > f[others, 8:].max()
+    assert f[7, :8].min() > f[others, 0].max()
     assert np.all(np.diff(f[:, :8], axis=1) >= 0) and np.all(np.diff(f[:, 8:], axis=1) >= 0)

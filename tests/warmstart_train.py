@@ -2,8 +2,10 @@
 
 Training data: matches of seeded 640x480 scenes (N = 200, outlier rate 10-45 %, noise
 0.5-2 px); features from the library's step-0 fit and feature kernel; labels = the FP64
-oracle EMDQ's inlier decision at convergence (posterior >= 1/2).  Training runs on the GPU
-through the library's own forward/backward/Adam kernels (emdq_mlp_train_step).
+oracle EMDQ's inlier posterior at convergence (a soft label: a network that predicts the
+final posterior lets EM start where it would end).  Training runs on the GPU through the
+library's own forward/backward/Adam kernels (emdq_mlp_train_step), with a cosine-decayed
+learning rate.
 
     python tests/warmstart_train.py --seeds 1000 --out gpurun_out/warmstart_mlp.npy
 
@@ -42,9 +44,8 @@ def make_training_set(seeds, n=200, w=640, h=480, device='cuda'):
         f64 = lambda a: np.asarray(a, np.float32).astype(np.float64)
         ref = oracle.fit(f64(s), f64(d), w, h)
         st, dt = torch.from_numpy(s).to(device), torch.from_numpy(d).to(device)
-        f0 = emdq.emdq_fit(st, dt, w, h, max_iters=0)
-        feats.append(emdq.warm_features(st, dt, f0['q'], f0['info']))
-        labels.append(torch.from_numpy((ref['c'] > 0).astype(np.float32)).to(device))
+        feats.append(emdq.warm_features(st, dt))
+        labels.append(torch.from_numpy(ref['p'].astype(np.float32)).to(device))
     return torch.cat(feats), torch.cat(labels)
 
 
@@ -76,7 +77,8 @@ def train(feat, label, steps=3000, batch=1024, lr=3e-3, seed=0, log_every=0):
         pos += batch
         torch.index_select(feat, 0, idx, out=xb)
         torch.index_select(label, 0, idx, out=yb)
-        emdq.mlp_train_step(xb, yb, params, m, v, step, lr, loss_out=loss, workspace=ws)
+        lr_t = 0.5 * lr * (1.0 + np.cos(np.pi * (step - 1) / steps))
+        emdq.mlp_train_step(xb, yb, params, m, v, step, lr_t, loss_out=loss, workspace=ws)
         if log_every and step % log_every == 0:
             losses.append((step, float(loss.item())))
     return params, losses
@@ -100,7 +102,7 @@ def evaluate(params, seeds=(0, 1, 2), name='warm2000', device='cuda'):
         alpha = float(np.float32(oracle.alpha_for_frame(sc.w, sc.h)))
         res = {}
         for mode in ('plain', 'warm'):
-            p0 = emdq.warm_start_p0(st, dt, sc.w, sc.h, params) if mode == 'warm' else None
+            p0 = emdq.warm_start_p0(st, dt, params) if mode == 'warm' else None
             r = emdq.emdq_fit(st, dt, sc.w, sc.h, p0=p0)
             info = emdq.read_fit_info(r['info'])
             q = r['q'].cpu().numpy().astype(np.float64)
