@@ -216,7 +216,6 @@ def run_gpu(args, ws, rank, local):
     fit_stream = torch.cuda.Stream(device=dev) if overlap else stream
     warm = (not args.no_warm) and os.path.exists(emdq.WARMSTART_PARAMS)
     warm_params = emdq.load_warmstart_params(dev) if warm else None
-    warm_feat = [torch.empty((n, 16), device=dev) for _ in range(B)]
     warm_p0 = [[torch.empty(n, device=dev) for _ in range(B)] for _ in range(nbuf)]
 
     def field_and_warp(fr, s_, g, fo):
@@ -234,9 +233,8 @@ def run_gpu(args, ws, rank, local):
         with torch.cuda.stream(fit_stream):
             p0s = [None] * len(ks)
             if warm:
-                for j, k in enumerate(ks):
-                    p0s[j] = emdq.warm_start_p0(s_of(k), d_of(k), warm_params, feat=warm_feat[j],
-                                                out=warm_p0[bi % nbuf][j], stream=fit_stream)
+                p0s = emdq.warm_start([(s_of(k), d_of(k)) for k in ks], warm_params,
+                                      outs=warm_p0[bi % nbuf][: len(ks)], stream=fit_stream)
             if B == 1:
                 emdq.emdq_fit(s_of(ks[0]), d_of(ks[0]), sc.w, sc.h, p0=p0s[0], out=outs[0],
                               workspace=fit_ws_all[bi % nbuf], stream=fit_stream)
@@ -448,8 +446,8 @@ def run_gpu(args, ws, rank, local):
                f' + emdq_field ({args.precision}) + mosaic_warp') +
               (', fits of the next batch on a second stream' if overlap else '')),
         batch=B, warm_start=warm, wall_s=wall, roofline=roof,
-        gpu_launches=total_frames * ((2 if fused else 3) + (2 if warm else 0)) +
-        args.steps * len(batches), clocks=clk,
+        gpu_launches=total_frames * (2 if fused else 3) + args.steps * len(batches) * (2 if warm else 1),
+        clocks=clk,
         e2e=e2e,
         fit_status=statuses,
     )

@@ -258,6 +258,12 @@ EMDQ_API emdq_status emdq_warm_features(const float *src, const float *dst, int 
                                         float *feat_out, void *stream);
 EMDQ_API emdq_status emdq_warm_infer(const float *feat, int n, const float *params,
                                      float *p0_out, void *stream);
+/* Features and network for `count` problems (1..64) in one launch: host arrays of device
+ * pointers src[b], dst[b] (n[b] x 2 float) and p0_out[b] (n[b] float, written); the same
+ * p0 as emdq_warm_features followed by emdq_warm_infer. */
+EMDQ_API emdq_status emdq_warm_start(const float *const *src, const float *const *dst,
+                                     const int *n, float *const *p0_out, int count,
+                                     const float *params, void *stream);
 EMDQ_API size_t      emdq_mlp_train_workspace_size(int batch);
 EMDQ_API emdq_status emdq_mlp_train_step(const float *feat, const float *label, int batch,
                                          float *params, float *adam_m, float *adam_v,

@@ -87,6 +87,8 @@ def lib() -> ctypes.CDLL:
             L.emdq_warm_features.argtypes = [P, P, I, P, P]
             L.emdq_warm_infer.restype = I
             L.emdq_warm_infer.argtypes = [P, I, P, P, P]
+            L.emdq_warm_start.restype = I
+            L.emdq_warm_start.argtypes = [P, P, P, P, I, P, P]
             L.emdq_mlp_train_workspace_size.restype = Z
             L.emdq_mlp_train_workspace_size.argtypes = [I]
             L.emdq_mlp_train_step.restype = I
@@ -354,6 +356,29 @@ def mlp_train_step(feat: torch.Tensor, label: torch.Tensor, params: torch.Tensor
                                    _ptr(loss_out), _ptr(ws), ws.numel(), _stream(stream))
     if rc != 0:
         raise EmdqError('emdq_mlp_train_step', rc)
+
+
+def warm_start(problems, params: torch.Tensor, outs: list | None = None, stream=None) -> list:
+    """p0 of several problems [(src, dst), ...] in one launch (features + network)."""
+    count = len(problems)
+    P = ctypes.c_void_p * max(1, count)
+    srcs, dsts, p0s = P(), P(), P()
+    ns = (ctypes.c_int * max(1, count))()
+    out = []
+    for b, (src, dst) in enumerate(problems):
+        n = src.shape[0]
+        _check(src, 'src', torch.float32, (n, 2))
+        _check(dst, 'dst', torch.float32, (n, 2))
+        o = outs[b] if outs is not None else torch.empty(n, dtype=torch.float32, device=src.device)
+        srcs[b], dsts[b], p0s[b], ns[b] = src.data_ptr(), dst.data_ptr(), o.data_ptr(), n
+        out.append(o)
+    _check(params, 'params', torch.float32, (mlp_param_count(),))
+    rc = lib().emdq_warm_start(ctypes.cast(srcs, ctypes.c_void_p), ctypes.cast(dsts, ctypes.c_void_p),
+                               ctypes.cast(ns, ctypes.c_void_p), ctypes.cast(p0s, ctypes.c_void_p),
+                               count, _ptr(params), _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_warm_start', rc)
+    return out
 
 
 def load_warmstart_params(device='cuda') -> torch.Tensor:

@@ -28,13 +28,13 @@ constexpr int kMlpThreads = 128;      // also the samples of one training tile
 __device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 // ------------------------------------------------------------------ features ----------
-__global__ void __launch_bounds__(kFeatThreads) warm_features_kernel(
-    const float2 *__restrict__ src, const float2 *__restrict__ dst, int n,
-    float *__restrict__ feat)
+// Features of match j (valid) of one problem; every thread of the block must call this (the
+// candidate positions are staged through shared memory sx, kFeatChunk entries).
+__device__ __forceinline__ void knn_features(const float2 *__restrict__ src,
+                                             const float2 *__restrict__ dst, int n, int j,
+                                             bool valid, float2 *sx, float (&f)[2 * kKnn])
 {
-    __shared__ float2 sx[kFeatChunk];
-    const int j = blockIdx.x * kFeatThreads + threadIdx.x;
-    const float2 xj = j < n ? src[j] : make_float2(0.f, 0.f);
+    const float2 xj = valid ? src[j] : make_float2(0.f, 0.f);
     float bd[kKnn];
     int bi[kKnn];
 #pragma unroll
@@ -45,9 +45,9 @@ __global__ void __launch_bounds__(kFeatThreads) warm_features_kernel(
     for (int base = 0; base < n; base += kFeatChunk) {
         const int m = min(kFeatChunk, n - base);
         __syncthreads();
-        for (int k = threadIdx.x; k < m; k += kFeatThreads) sx[k] = src[base + k];
+        for (int k = threadIdx.x; k < m; k += blockDim.x) sx[k] = src[base + k];
         __syncthreads();
-        if (j >= n) continue;
+        if (!valid) continue;
         for (int k = 0; k < m; ++k) {
             const int i = base + k;
             if (i == j) continue;
@@ -73,34 +73,44 @@ __global__ void __launch_bounds__(kFeatThreads) warm_features_kernel(
             }
         }
     }
-    if (j >= n) return;
+    if (!valid) return;
     const float2 yj = dst[j];
     const float djx = yj.x - xj.x, djy = yj.y - xj.y;
-    float f1[kKnn], f2[kKnn];
+    float f1[kKnn];
 #pragma unroll
     for (int k = 0; k < kKnn; ++k) {
         const int i = bi[k];
         const float2 xk = src[i], yk = dst[i];
         f1[k] = log1pf(hypotf((yk.x - xk.x) - djx, (yk.y - xk.y) - djy));
-        f2[k] = log1pf(sqrtf(bd[k]));      // already ascending
+        f[kKnn + k] = log1pf(sqrtf(bd[k]));      // already ascending
     }
-    // sort each group ascending (odd-even transposition, fixed network)
+    // sort the residuals ascending (odd-even transposition, fixed network)
 #pragma unroll
     for (int r = 0; r < kKnn; ++r)
 #pragma unroll
         for (int k = r & 1; k + 1 < kKnn; k += 2) {
-            const float a = fminf(f1[k], f1[k + 1]), b = fmaxf(f1[k], f1[k + 1]);
-            f1[k] = a;
-            f1[k + 1] = b;
-            const float c = fminf(f2[k], f2[k + 1]), d = fmaxf(f2[k], f2[k + 1]);
-            f2[k] = c;
-            f2[k + 1] = d;
+            const float lo = fminf(f1[k], f1[k + 1]), hi = fmaxf(f1[k], f1[k + 1]);
+            f1[k] = lo;
+            f1[k + 1] = hi;
         }
+#pragma unroll
+    for (int k = 0; k < kKnn; ++k) f[k] = f1[k];
+}
+
+__global__ void __launch_bounds__(kFeatThreads) warm_features_kernel(
+    const float2 *__restrict__ src, const float2 *__restrict__ dst, int n,
+    float *__restrict__ feat)
+{
+    __shared__ float2 sx[kFeatChunk];
+    const int j = blockIdx.x * kFeatThreads + threadIdx.x;
+    float f[2 * kKnn];
+    knn_features(src, dst, n, j, j < n, sx, f);
+    if (j >= n) return;
     float4 *o = reinterpret_cast<float4 *>(feat + 16 * (size_t)j);
-    o[0] = make_float4(f1[0], f1[1], f1[2], f1[3]);
-    o[1] = make_float4(f1[4], f1[5], f1[6], f1[7]);
-    o[2] = make_float4(f2[0], f2[1], f2[2], f2[3]);
-    o[3] = make_float4(f2[4], f2[5], f2[6], f2[7]);
+    o[0] = make_float4(f[0], f[1], f[2], f[3]);
+    o[1] = make_float4(f[4], f[5], f[6], f[7]);
+    o[2] = make_float4(f[8], f[9], f[10], f[11]);
+    o[3] = make_float4(f[12], f[13], f[14], f[15]);
 }
 
 // ------------------------------------------------------------------ network ------------
@@ -147,6 +157,37 @@ __global__ void __launch_bounds__(kMlpThreads) warm_infer_kernel(const float *__
     for (int m = 0; m < kNin; ++m) x[m] = bf(feat[16 * (size_t)j + m]);
     const float z = mlp_forward(sw, x, h1);
     p0[j] = 1.f / (1.f + expf(-z));
+}
+
+// Features + network for many problems in one launch: block -> (problem, 128 matches).
+constexpr int kWarmBatchMax = 64;
+struct WarmBatch {
+    const float2 *src[kWarmBatchMax];
+    const float2 *dst[kWarmBatchMax];
+    float *p0[kWarmBatchMax];
+    int n[kWarmBatchMax];
+    int first_block[kWarmBatchMax + 1];     // prefix sums of the problems' block counts
+    int count;
+};
+
+__global__ void __launch_bounds__(kFeatThreads) warm_start_batch_kernel(
+    const __grid_constant__ WarmBatch B, const float *__restrict__ w)
+{
+    __shared__ float sw[kNParams];
+    __shared__ float2 sx[kFeatChunk];
+    int b = 0;
+    while (b + 1 < B.count && (int)blockIdx.x >= B.first_block[b + 1]) ++b;
+    const int j = (blockIdx.x - B.first_block[b]) * kFeatThreads + threadIdx.x;
+    const int n = B.n[b];
+    stage_params(w, sw);
+    float f[2 * kKnn];
+    knn_features(B.src[b], B.dst[b], n, j, j < n, sx, f);
+    if (j >= n) return;
+    float x[kNin], h1[kNh];
+#pragma unroll
+    for (int m = 0; m < kNin; ++m) x[m] = bf(f[m]);
+    const float z = mlp_forward(sw, x, h1);
+    B.p0[b][j] = 1.f / (1.f + expf(-z));
 }
 
 // Gradient of the summed cross-entropy over one tile of kMlpThreads samples, written as
@@ -294,6 +335,30 @@ extern "C" emdq_status emdq_warm_infer(const float *feat, int n, const float *pa
     if (!feat || !params || !p0_out || n < 1) return EMDQ_EINVAL;
     warm_infer_kernel<<<(n + kMlpThreads - 1) / kMlpThreads, kMlpThreads, 0,
                         static_cast<cudaStream_t>(stream)>>>(feat, n, params, p0_out);
+    return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
+}
+
+extern "C" emdq_status emdq_warm_start(const float *const *src, const float *const *dst,
+                                       const int *n, float *const *p0_out, int count,
+                                       const float *params, void *stream)
+{
+    if (!src || !dst || !n || !p0_out || !params || count < 1) return EMDQ_EINVAL;
+    if (count > kWarmBatchMax) return EMDQ_ENOTSUP;
+    WarmBatch B;
+    B.count = count;
+    int blocks = 0;
+    for (int b = 0; b < count; ++b) {
+        if (!src[b] || !dst[b] || !p0_out[b] || n[b] < kKnn + 1) return EMDQ_EINVAL;
+        if (!aligned(src[b], 8) || !aligned(dst[b], 8)) return EMDQ_EINVAL;
+        B.src[b] = reinterpret_cast<const float2 *>(src[b]);
+        B.dst[b] = reinterpret_cast<const float2 *>(dst[b]);
+        B.p0[b] = p0_out[b];
+        B.n[b] = n[b];
+        B.first_block[b] = blocks;
+        blocks += (n[b] + kFeatThreads - 1) / kFeatThreads;
+    }
+    B.first_block[count] = blocks;
+    warm_start_batch_kernel<<<blocks, kFeatThreads, 0, static_cast<cudaStream_t>(stream)>>>(B, params);
     return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }
 

@@ -35,6 +35,18 @@ def test_features_match_the_oracle(emdq):
     assert np.abs(got - want).max() < 2e-4
 
 
+def test_batched_warm_start_equals_features_then_network(emdq):
+    params = emdq.load_warmstart_params()
+    probs = []
+    for seed, n in ((41, 200), (42, 1000), (43, 137)):
+        sc, s, d, _ = _pair(seed, n=n)
+        probs.append((torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda()))
+    got = emdq.warm_start(probs, params)
+    for (st, dt), p in zip(probs, got):
+        want = emdq.warm_infer(emdq.warm_features(st, dt), params)
+        assert torch.equal(p, want)
+
+
 def _bf16_forward(w, X):
     """The oracle network with the kernel's BF16 rounding of operands (for the tolerance
     check only; the reference is the FP64 forward)."""
