@@ -14,11 +14,13 @@
 //
 // field_tc_prep_kernel writes Ex (K-major rows of pixels x) and G (K-major rows of
 // pixels y, six channel planes) as BF16 into the workspace, zero-padded to whole tiles.
-// field_tc_kernel: one CTA per 128 x 32 pixel tile.  A TMA producer thread streams
-// 64-match slices of Ex (128 rows) and of G (6 x 32 rows, one 3-D box) through a 4-stage
-// shared-memory ring; one thread issues tcgen05.mma (M = 128 pixels x, N = 192 =
-// 6 channels x 32 pixels y, K = 16) accumulating in TMEM; then the four warps read the
-// accumulators back with tcgen05.ld (thread = pixel x = TMEM lane) and evaluate Eq. 1.
+// field_tc_kernel: persistent, one CTA per SM looping over 128 x 32 pixel tiles, warp
+// specialised.  Warp 0 (one thread) streams 64-match slices of Ex (128 rows) and of G
+// (6 x 32 rows, one 3-D box) through a 4-stage shared-memory ring with TMA; warp 1 (one
+// thread) issues tcgen05.mma (M = 128 pixels x, N = 192 = 6 channels x 32 pixels y,
+// K = 16) into one of two TMEM accumulators; warps 2-5 read the other accumulator back
+// with tcgen05.ld (thread = pixel x = TMEM lane) and evaluate Eq. 1, so the epilogue of a
+// tile overlaps the MMAs of the next.
 // The fused variant (CH = 1 or 3) goes on from the displacement to the mosaic update of
 // the same pixel (the stand-alone warp's per-pixel code), so the field never visits HBM.
 #include <mutex>
@@ -38,12 +40,13 @@ constexpr int kTcPY = 32;                // pixels y per tile
 constexpr int kTcCh = 6;                 // dr_w, dr_z, dd_x, dd_y, ds, weight
 constexpr int kTcN = kTcCh * kTcPY;      // MMA N = 192
 constexpr int kTcK = 64;                 // matches per stage: one 128-byte swizzle row
-constexpr int kTcStages = 2;                 // 2 CTAs per SM: one's epilogue overlaps the other's MMAs
-constexpr int kTcThreads = 128;
+constexpr int kTcStages = 4;
+constexpr int kTcThreads = 192;        // producer warp, MMA warp, 4 epilogue warps
 constexpr uint32_t kTcABytes = kTcM * kTcK * 2;
 constexpr uint32_t kTcBBytes = kTcN * kTcK * 2;
 constexpr uint32_t kTcStageBytes = kTcABytes + kTcBBytes;
-constexpr uint32_t kTcTmemCols = 256;
+constexpr uint32_t kTcAccCols = 256;     // one accumulator: 192 columns used
+constexpr uint32_t kTcTmemCols = 2 * kTcAccCols;
 constexpr size_t kTcSmemBytes = kTcStages * kTcStageBytes + 1024 /*barriers*/ + 1024 /*align*/;
 constexpr uint32_t kTcIdesc = tc::idesc_bf16_f32(kTcM, kTcN);
 constexpr int kPrepRows = 8;
@@ -77,11 +80,6 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
     int a_blocks)
 {
     const int half = kp / 2;
-    __shared__ float red[6 * 32];
-    float ref[6];
-    reference_row(q, c, n, red, ref);      // same bits in every block
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        for (int k = 0; k < 6; ++k) ref_out[k] = ref[k];
     if ((int)blockIdx.x < a_blocks) {
         const int r0 = blockIdx.x * kPrepRows;
         for (int k2 = threadIdx.x; k2 < half; k2 += kPrepThreads) {
@@ -100,7 +98,11 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
         }
     } else {
         const int r0 = (blockIdx.x - a_blocks) * kPrepRows;
-        const float *rf = ref;
+        __shared__ float red[6 * 32];
+        float rf[6];
+        reference_row(q, c, n, red, rf);      // same bits in every block
+        if (blockIdx.x == a_blocks && threadIdx.x == 0)
+            for (int k = 0; k < 6; ++k) ref_out[k] = rf[k];
         for (int k2 = threadIdx.x; k2 < half; k2 += kPrepThreads) {
             const int k0 = 2 * k2;
             float y[2] = {0.f, 0.f}, cw[2] = {0.f, 0.f}, cq[2][5];
@@ -143,26 +145,31 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
 template <int CH>
 __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int nchunks,
-    int gx0, int gy0, int gw, int gh, const float *__restrict__ ref, float2 *__restrict__ disp,
-    int *__restrict__ err, MosaicArgs mos)
+    int ntx, int ntiles, int gx0, int gy0, int gw, int gh, const float *__restrict__ ref,
+    float2 *__restrict__ disp, int *__restrict__ err, MosaicArgs mos)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + kTcStages * kTcStageBytes);
     uint64_t *empty = full + kTcStages;
-    uint64_t *done = empty + kTcStages;
+    uint64_t *acc_full = empty + kTcStages;     // [2] MMA -> epilogue
+    uint64_t *acc_empty = acc_full + 2;         // [2] epilogue -> MMA (4 warps arrive)
+    uint64_t *done = acc_empty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int *issued = const_cast<int *>(abort_flag + 1);     // chunks whose loads were issued
     int *consumed = issued + 1;                          // chunks whose MMAs were issued
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile_x = blockIdx.x, tile_y = blockIdx.y;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTcStages; ++s) {
             tc::mbar_init(full + s, 1);
             tc::mbar_init(empty + s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(acc_full + a, 1);
+            tc::mbar_init(acc_empty + a, 4);
         }
         tc::mbar_init(done, 1);
         *abort_flag = 0;
@@ -172,124 +179,164 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(
         tc::prefetch_tmap(&tmA);
         tc::prefetch_tmap(&tmB);
     }
-    if (warp == 2) tc::tmem_alloc(tmem_slot, kTcTmemCols);
+    if (warp == 1) tc::tmem_alloc(tmem_slot, kTcTmemCols);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        // TMA producer
-        for (int k = 0; k < nchunks; ++k) {
-            const int s = k % kTcStages;
-            const uint32_t ph = (k / kTcStages) & 1;
-            if (k >= kTcStages && !tc::mbar_wait(empty + s, ph ^ 1, kWaitLimit, false)) {
-                *abort_flag = 1;
-                break;
-            }
-            if (*abort_flag) break;
-            uint8_t *sa = smem + s * kTcStageBytes;
-            tc::mbar_arrive_expect_tx(full + s, kTcStageBytes);
-            tc::tma_load_2d(sa, &tmA, full + s, k * kTcK, tile_x * kTcM);
-            tc::tma_load_3d(sa + kTcABytes, &tmB, full + s, k * kTcK, tile_y * kTcPY, 0);
-            *issued = k + 1;
-        }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        for (int k = 0; k < nchunks; ++k) {
-            const int s = k % kTcStages;
-            const uint32_t ph = (k / kTcStages) & 1;
-            if (!tc::mbar_wait(full + s, ph, kWaitLimit, false)) {
-                *abort_flag = 1;
-                break;
-            }
-            tc::fence_after_sync();
-            const uint32_t sa = tc::smem_u32(smem + s * kTcStageBytes);
-            const uint32_t sb = sa + kTcABytes;
-#pragma unroll
-            for (int kk = 0; kk < kTcK / 16; ++kk) {
-                // advance 16 BF16 = 32 bytes along K inside the 128-byte swizzled row
-                tc::mma_f16(tmem, tc::desc_kmajor_sw128(sa + kk * 32),
-                            tc::desc_kmajor_sw128(sb + kk * 32), kTcIdesc, (k | kk) != 0);
-            }
-            tc::mma_commit(empty + s);
-            *consumed = k + 1;
-        }
-        tc::mma_commit(done);   // tracks every MMA issued above, also after an abort
-    }
-    __syncwarp();
-
-    // epilogue: thread = pixel x = TMEM lane; 8 pixels y at a time, 6 channels each
-    const bool ok = tc::mbar_wait(done, 0, kWaitLimit, true);
-    tc::fence_after_sync();
-    if (!ok) *abort_flag = 1;
-    __syncthreads();
-    if (!*abort_flag) {
-        const float ra = ref[0], rb = ref[1], ru = ref[2], rv = ref[3], rs = ref[4];
-        const int xl = warp * 32 + lane;
-        const int x = tile_x * kTcM + xl;
-        const float px = static_cast<float>(gx0 + x);
-        const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-#pragma unroll 1
-        for (int g = 0; g < kTcPY / 8; ++g) {
-            float F[kTcCh][8];
-#pragma unroll
-            for (int ch = 0; ch < kTcCh; ++ch) tc::tmem_ld_x8(lane_base + ch * kTcPY + g * 8, F[ch]);
-            tc::tmem_wait_ld();
-            float2 d[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float py = static_cast<float>(gy0 + tile_y * kTcPY + g * 8 + j);
-                d[j] = make_float2(NAN, NAN);
-                const float w = F[5][j];
-                if (w > 0.f) {
-                    const float inv = 1.f / w;
-                    const float2 xp = apply_blend(ra + F[0][j] * inv, rb + F[1][j] * inv,
-                                                  ru + F[2][j] * inv, rv + F[3][j] * inv,
-                                                  rs + F[4][j] * inv, px, py);
-                    d[j] = make_float2(xp.x - px, xp.y - py);
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer: every tile of this CTA, every 64-match slice
+            int chunk = 0;
+            for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+                const int tx = tile % ntx, ty = tile / ntx;
+                for (int k = 0; k < nchunks; ++k, ++chunk) {
+                    const int s = chunk % kTcStages;
+                    const uint32_t ph = (chunk / kTcStages) & 1;
+                    if (chunk >= kTcStages && !tc::mbar_wait(empty + s, ph ^ 1, kWaitLimit, false)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    uint8_t *sa = smem + s * kTcStageBytes;
+                    tc::mbar_arrive_expect_tx(full + s, kTcStageBytes);
+                    tc::tma_load_2d(sa, &tmA, full + s, k * kTcK, tx * kTcM);
+                    tc::tma_load_3d(sa + kTcABytes, &tmB, full + s, k * kTcK, ty * kTcPY, 0);
+                    *issued = chunk + 1;
                 }
             }
-            const int y0 = tile_y * kTcPY + g * 8;
-            if constexpr (CH == 0) {
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: accumulator it & 1 of tile iteration it
+            int chunk = 0, it = 0;
+            for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
+                const int a = it & 1;
+                if (it >= 2 && !tc::mbar_wait(acc_empty + a, ((it >> 1) - 1) & 1, kWaitLimit, false)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t d = tmem + a * kTcAccCols;
+                bool ok = true;
+                for (int k = 0; k < nchunks; ++k, ++chunk) {
+                    const int s = chunk % kTcStages;
+                    const uint32_t ph = (chunk / kTcStages) & 1;
+                    if (!tc::mbar_wait(full + s, ph, kWaitLimit, false)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t sa = tc::smem_u32(smem + s * kTcStageBytes);
+                    const uint32_t sb = sa + kTcABytes;
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (x < gw && y0 + j < gh) disp[(size_t)(y0 + j) * gw + x] = d[j];
-            } else {
-                // all loads of the 8 pixels first (canvas words and frame taps), then the
-                // updates: 8 independent gathers in flight per thread
-                Tap t[8];
-                uchar4 cv[8];
-                uchar4 *cp[8];
+                    for (int kk = 0; kk < kTcK / 16; ++kk) {
+                        // advance 16 BF16 = 32 bytes along K inside the 128-byte swizzled row
+                        tc::mma_f16(d, tc::desc_kmajor_sw128(sa + kk * 32),
+                                    tc::desc_kmajor_sw128(sb + kk * 32), kTcIdesc, (k | kk) != 0);
+                    }
+                    tc::mma_commit(empty + s);
+                    *consumed = chunk + 1;
+                }
+                if (!ok) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc::mma_commit(acc_full + a);
+            }
+            tc::mma_commit(done);   // tracks every MMA issued above, also after an abort
+        }
+    } else {
+        // epilogue warps 2-5: TMEM lane quadrant q = warp % 4, thread = pixel x of the tile
+        const int q = warp & 3;
+        const float ra = ref[0], rb = ref[1], ru = ref[2], rv = ref[3], rs = ref[4];
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int a = it & 1;
+            const bool ok = tc::mbar_wait(acc_full + a, (it >> 1) & 1, kWaitLimit, true);
+            tc::fence_after_sync();
+            if (!ok || *abort_flag) {
+                *abort_flag = 1;
+                break;
+            }
+            const int tx = tile % ntx, ty = tile / ntx;
+            const int x = tx * kTcM + q * 32 + lane;
+            const float px = static_cast<float>(gx0 + x);
+            const uint32_t lane_base = tmem + a * kTcAccCols + (static_cast<uint32_t>(q * 32) << 16);
+#pragma unroll 1
+            for (int g = 0; g < kTcPY / 8; ++g) {
+                float F[kTcCh][8];
+#pragma unroll
+                for (int ch = 0; ch < kTcCh; ++ch) tc::tmem_ld_x8(lane_base + ch * kTcPY + g * 8, F[ch]);
+                tc::tmem_wait_ld();
+                if (g == kTcPY / 8 - 1) {
+                    // the accumulator has been read: hand it back to the MMA warp
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(acc_empty + a);
+                }
+                float2 d[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    t[j] = tap_setup<CH>(mos.fw, mos.fh, mos.pitch, px,
-                                         static_cast<float>(gy0 + y0 + j), d[j].x, d[j].y);
-                    t[j].ok = t[j].ok && x < gw && y0 + j < gh;
-                    cp[j] = mos.canvas + (size_t)(gy0 + y0 + j + mos.oy) * mos.cpitch4 +
-                            (gx0 + x + mos.ox);
-                    if (t[j].ok) cv[j] = *cp[j];
+                    const float py = static_cast<float>(gy0 + ty * kTcPY + g * 8 + j);
+                    d[j] = make_float2(NAN, NAN);
+                    const float w = F[5][j];
+                    if (w > 0.f) {
+                        const float inv = 1.f / w;
+                        const float2 xp = apply_blend(ra + F[0][j] * inv, rb + F[1][j] * inv,
+                                                      ru + F[2][j] * inv, rv + F[3][j] * inv,
+                                                      rs + F[4][j] * inv, px, py);
+                        d[j] = make_float2(xp.x - px, xp.y - py);
+                    }
                 }
-                float v[8][CH];
+                const int y0 = ty * kTcPY + g * 8;
+                if constexpr (CH == 0) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (t[j].ok) tap_sample<CH>(mos.frame, t[j], v[j]);
+                    for (int j = 0; j < 8; ++j)
+                        if (x < gw && y0 + j < gh) disp[(size_t)(y0 + j) * gw + x] = d[j];
+                } else {
+                    // all loads of the 8 pixels first (canvas words and frame taps), then the
+                    // updates: 8 independent gathers in flight per thread
+                    Tap t[8];
+                    uchar4 cv[8];
+                    uchar4 *cp[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (t[j].ok) *cp[j] = blend_update<CH>(cv[j], v[j]);
+                    for (int j = 0; j < 8; ++j) {
+                        t[j] = tap_setup<CH>(mos.fw, mos.fh, mos.pitch, px,
+                                             static_cast<float>(gy0 + y0 + j), d[j].x, d[j].y);
+                        t[j].ok = t[j].ok && x < gw && y0 + j < gh;
+                        cp[j] = mos.canvas + (size_t)(gy0 + y0 + j + mos.oy) * mos.cpitch4 +
+                                (gx0 + x + mos.ox);
+                        if (t[j].ok) cv[j] = *cp[j];
+                    }
+                    float v[8][CH];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (t[j].ok) tap_sample<CH>(mos.frame, t[j], v[j]);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (t[j].ok) *cp[j] = blend_update<CH>(cv[j], v[j]);
+                }
             }
+        }
+    }
+    __syncwarp();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // every MMA issued has completed before the accumulators are released
+        tc::mbar_wait(done, 0, kWaitLimit, true);
+        if (*abort_flag) {
+            atomicMax(err, (int)EMDQ_ETIMEOUT);
+            // drain loads that were issued but never consumed before the CTA exits
+            for (int k = *consumed; k < *issued; ++k)
+                tc::mbar_wait(full + (k % kTcStages), (k / kTcStages) & 1, kWaitLimit, true);
         }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (threadIdx.x == 0 && *abort_flag) {
-        atomicMax(err, (int)EMDQ_ETIMEOUT);
-        // drain loads that were issued but never consumed before the CTA exits
-        for (int k = *consumed; k < *issued; ++k)
-            tc::mbar_wait(full + (k % kTcStages), (k / kTcStages) & 1, kWaitLimit, true);
-    }
-    __syncthreads();
-    if (warp == 2) tc::tmem_dealloc(tmem, kTcTmemCols);
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tmem, kTcTmemCols);
 }
 
 }  // namespace emdq
@@ -388,16 +435,18 @@ emdq_status field_tc_launch(const float *q, const float *c, const float *src, in
         q, c, reinterpret_cast<const float2 *>(src), n, g.kp, gx0, gy0, gw, gh, g.wp, g.hp, alpha,
         ref, A, B, a_blocks);
     if (cudaGetLastError() != cudaSuccess) return EMDQ_ECUDA;
-    dim3 grid(g.wp / kTcM, g.hp / kTcPY);
+    const int ntx = g.wp / kTcM, ntiles = ntx * (g.hp / kTcPY);
+    const int grid = ntiles < D.sms ? ntiles : D.sms;       // persistent: one CTA per SM
     const MosaicArgs none{};
+    const int nch = g.kp / kTcK;
     if (variant == 0)
-        field_tc_kernel<0><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, g.kp / kTcK, gx0, gy0,
-                                                                   gw, gh, ref, disp, err, none);
+        field_tc_kernel<0><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, nch, ntx, ntiles, gx0,
+                                                                   gy0, gw, gh, ref, disp, err, none);
     else if (variant == 1)
-        field_tc_kernel<1><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, g.kp / kTcK, gx0, gy0,
-                                                                   gw, gh, ref, disp, err, *mos);
+        field_tc_kernel<1><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, nch, ntx, ntiles, gx0,
+                                                                   gy0, gw, gh, ref, disp, err, *mos);
     else
-        field_tc_kernel<3><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, g.kp / kTcK, gx0, gy0,
-                                                                   gw, gh, ref, disp, err, *mos);
+        field_tc_kernel<3><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, nch, ntx, ntiles, gx0,
+                                                                   gy0, gw, gh, ref, disp, err, *mos);
     return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }

@@ -21,7 +21,7 @@ constexpr int kOffW1 = 0, kOffB1 = kNh * kNin, kOffW2 = kOffB1 + kNh, kOffB2 = k
               kOffW3 = kOffB2 + kNh, kOffB3 = kOffW3 + kNh, kNParams = kOffB3 + 1;
 static_assert(kNParams == 5313, "parameter layout");
 
-constexpr int kFeatThreads = 128;
+constexpr int kFeatThreads = 64;
 constexpr int kFeatChunk = 1024;
 constexpr int kMlpThreads = 128;      // also the samples of one training tile
 
@@ -48,6 +48,7 @@ __device__ __forceinline__ void knn_features(const float2 *__restrict__ src,
         for (int k = threadIdx.x; k < m; k += blockDim.x) sx[k] = src[base + k];
         __syncthreads();
         if (!valid) continue;
+#pragma unroll 4
         for (int k = 0; k < m; ++k) {
             const int i = base + k;
             if (i == j) continue;
@@ -133,13 +134,19 @@ __device__ __forceinline__ float mlp_forward(const float *sw, const float (&x)[k
         for (int m = 0; m < kNin; ++m) acc = fmaf(sw[kOffW1 + o * kNin + m], x[m], acc);
         h1[o] = bf(fmaxf(acc, 0.f));
     }
+    // second layer: 8 outputs at a time (8 independent accumulation chains)
     float z = sw[kOffB3];
 #pragma unroll 1
-    for (int o = 0; o < kNh; ++o) {
-        float acc = sw[kOffB2 + o];
+    for (int o0 = 0; o0 < kNh; o0 += 8) {
+        float acc[8];
 #pragma unroll
-        for (int k = 0; k < kNh; ++k) acc = fmaf(sw[kOffW2 + o * kNh + k], h1[k], acc);
-        z = fmaf(sw[kOffW3 + o], bf(fmaxf(acc, 0.f)), z);
+        for (int u = 0; u < 8; ++u) acc[u] = sw[kOffB2 + o0 + u];
+#pragma unroll
+        for (int k = 0; k < kNh; ++k)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = fmaf(sw[kOffW2 + (o0 + u) * kNh + k], h1[k], acc[u]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) z = fmaf(sw[kOffW3 + o0 + u], bf(fmaxf(acc[u], 0.f)), z);
     }
     return z;
 }
