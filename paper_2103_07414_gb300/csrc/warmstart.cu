@@ -21,20 +21,20 @@ constexpr int kOffW1 = 0, kOffB1 = kNh * kNin, kOffW2 = kOffB1 + kNh, kOffB2 = k
               kOffW3 = kOffB2 + kNh, kOffB3 = kOffW3 + kNh, kNParams = kOffB3 + 1;
 static_assert(kNParams == 5313, "parameter layout");
 
-constexpr int kFeatThreads = 64;
-constexpr int kFeatChunk = 1024;
 constexpr int kMlpThreads = 128;      // also the samples of one training tile
 
 __device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 // ------------------------------------------------------------------ features ----------
-// Features of match j (valid) of one problem; every thread of the block must call this (the
-// candidate positions are staged through shared memory sx, kFeatChunk entries).
-__device__ __forceinline__ void knn_features(const float2 *__restrict__ src,
-                                             const float2 *__restrict__ dst, int n, int j,
-                                             bool valid, float2 *sx, float (&f)[2 * kKnn])
+// One warp per match.  Each lane keeps the 8 nearest of its candidates i = lane + 32 t,
+// sorted by (distance, index); 8 rounds of a warp-wide lexicographic arg-min then pop the
+// overall 8 nearest in order -- the same set and order as a full sort.  All lanes end with
+// the 16 features.
+__device__ __forceinline__ void knn_features_warp(const float2 *__restrict__ src,
+                                                  const float2 *__restrict__ dst, int n, int j,
+                                                  int lane, float (&f)[2 * kKnn])
 {
-    const float2 xj = valid ? src[j] : make_float2(0.f, 0.f);
+    const float2 xj = src[j];
     float bd[kKnn];
     int bi[kKnn];
 #pragma unroll
@@ -42,50 +42,72 @@ __device__ __forceinline__ void knn_features(const float2 *__restrict__ src,
         bd[k] = INFINITY;
         bi[k] = 0x7fffffff;
     }
-    for (int base = 0; base < n; base += kFeatChunk) {
-        const int m = min(kFeatChunk, n - base);
-        __syncthreads();
-        for (int k = threadIdx.x; k < m; k += blockDim.x) sx[k] = src[base + k];
-        __syncthreads();
-        if (!valid) continue;
-#pragma unroll 4
-        for (int k = 0; k < m; ++k) {
-            const int i = base + k;
-            if (i == j) continue;
-            // float32, one rounding per operation (the same decision as the oracle's)
-            const float dx = __fsub_rn(sx[k].x, xj.x), dy = __fsub_rn(sx[k].y, xj.y);
-            const float d = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-            if (d < bd[kKnn - 1] || (d == bd[kKnn - 1] && i < bi[kKnn - 1])) {
-                // insert into the sorted list (by distance, then index)
-                float cd = d;
-                int ci = i;
+    for (int i = lane; i < n; i += 32) {
+        if (i == j) continue;
+        const float2 xi = src[i];
+        // float32, one rounding per operation (the same decision as the oracle's)
+        const float dx = __fsub_rn(xi.x, xj.x), dy = __fsub_rn(xi.y, xj.y);
+        const float d = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        if (d < bd[kKnn - 1] || (d == bd[kKnn - 1] && i < bi[kKnn - 1])) {
+            float cd = d;
+            int ci = i;
 #pragma unroll
-                for (int s = 0; s < kKnn; ++s) {
-                    const bool lt = cd < bd[s] || (cd == bd[s] && ci < bi[s]);
-                    const float td = bd[s];
-                    const int ti = bi[s];
-                    if (lt) {
-                        bd[s] = cd;
-                        bi[s] = ci;
-                        cd = td;
-                        ci = ti;
-                    }
+            for (int s = 0; s < kKnn; ++s) {
+                const bool lt = cd < bd[s] || (cd == bd[s] && ci < bi[s]);
+                const float td = bd[s];
+                const int ti = bi[s];
+                if (lt) {
+                    bd[s] = cd;
+                    bi[s] = ci;
+                    cd = td;
+                    ci = ti;
                 }
             }
         }
     }
-    if (!valid) return;
+    float nd[kKnn];
+    int ni[kKnn];
+#pragma unroll
+    for (int r = 0; r < kKnn; ++r) {
+        float cd = bd[0];
+        int ci = bi[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float od = __shfl_xor_sync(0xffffffffu, cd, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
+            if (od < cd || (od == cd && oi < ci)) {
+                cd = od;
+                ci = oi;
+            }
+        }
+        nd[r] = cd;
+        ni[r] = ci;
+        if (bi[0] == ci) {          // this lane held the winner: pop its head
+#pragma unroll
+            for (int s = 0; s + 1 < kKnn; ++s) {
+                bd[s] = bd[s + 1];
+                bi[s] = bi[s + 1];
+            }
+            bd[kKnn - 1] = INFINITY;
+            bi[kKnn - 1] = 0x7fffffff;
+        }
+    }
+    // lane k < 8: the residual of neighbour k under the translation match j implies
     const float2 yj = dst[j];
     const float djx = yj.x - xj.x, djy = yj.y - xj.y;
+    float mine = 0.f;
+    if (lane < kKnn) {
+        int idx = ni[0];
+#pragma unroll
+        for (int k = 1; k < kKnn; ++k)
+            if (lane == k) idx = ni[k];
+        const float2 xk = src[idx], yk = dst[idx];
+        mine = log1pf(hypotf((yk.x - xk.x) - djx, (yk.y - xk.y) - djy));
+    }
     float f1[kKnn];
 #pragma unroll
-    for (int k = 0; k < kKnn; ++k) {
-        const int i = bi[k];
-        const float2 xk = src[i], yk = dst[i];
-        f1[k] = log1pf(hypotf((yk.x - xk.x) - djx, (yk.y - xk.y) - djy));
-        f[kKnn + k] = log1pf(sqrtf(bd[k]));      // already ascending
-    }
-    // sort the residuals ascending (odd-even transposition, fixed network)
+    for (int k = 0; k < kKnn; ++k) f1[k] = __shfl_sync(0xffffffffu, mine, k);
+    // sort ascending (odd-even transposition, fixed network; every lane the same)
 #pragma unroll
     for (int r = 0; r < kKnn; ++r)
 #pragma unroll
@@ -95,106 +117,136 @@ __device__ __forceinline__ void knn_features(const float2 *__restrict__ src,
             f1[k + 1] = hi;
         }
 #pragma unroll
-    for (int k = 0; k < kKnn; ++k) f[k] = f1[k];
+    for (int k = 0; k < kKnn; ++k) {
+        f[k] = f1[k];
+        f[kKnn + k] = log1pf(sqrtf(nd[k]));      // distances, already ascending
+    }
 }
 
-__global__ void __launch_bounds__(kFeatThreads) warm_features_kernel(
-    const float2 *__restrict__ src, const float2 *__restrict__ dst, int n,
-    float *__restrict__ feat)
+__global__ void __launch_bounds__(256) warm_features_kernel(const float2 *__restrict__ src,
+                                                           const float2 *__restrict__ dst, int n,
+                                                           float *__restrict__ feat)
 {
-    __shared__ float2 sx[kFeatChunk];
-    const int j = blockIdx.x * kFeatThreads + threadIdx.x;
-    float f[2 * kKnn];
-    knn_features(src, dst, n, j, j < n, sx, f);
-    if (j >= n) return;
-    float4 *o = reinterpret_cast<float4 *>(feat + 16 * (size_t)j);
-    o[0] = make_float4(f[0], f[1], f[2], f[3]);
-    o[1] = make_float4(f[4], f[5], f[6], f[7]);
-    o[2] = make_float4(f[8], f[9], f[10], f[11]);
-    o[3] = make_float4(f[12], f[13], f[14], f[15]);
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += nw) {
+        float f[2 * kKnn];
+        knn_features_warp(src, dst, n, j, lane, f);
+        if (lane < 2 * kKnn) {
+            float v = f[0];
+#pragma unroll
+            for (int k = 1; k < 2 * kKnn; ++k)
+                if (lane == k) v = f[k];
+            feat[16 * (size_t)j + lane] = v;
+        }
+    }
 }
 
 // ------------------------------------------------------------------ network ------------
-// Parameters rounded to BF16, staged in shared memory as floats.
+// Parameters rounded to BF16, staged in shared memory as floats, with W1 and W2 transposed
+// ([in][out]) so that lane-per-output reads are conflict-free.
+constexpr int kSwW1T = 0, kSwB1 = kSwW1T + kNin * kNh, kSwW2T = kSwB1 + kNh,
+              kSwB2 = kSwW2T + kNh * kNh, kSwW3 = kSwB2 + kNh, kSwB3 = kSwW3 + kNh;
+
+// Parameters rounded to BF16 in their stored layout (for the training kernel).
 __device__ __forceinline__ void stage_params(const float *__restrict__ w, float *sw)
 {
     for (int k = threadIdx.x; k < kNParams; k += blockDim.x) sw[k] = bf(w[k]);
     __syncthreads();
 }
 
-// Forward of one sample from its BF16-rounded input: h1, h2 (post-ReLU, rounded to
-// BF16), FP32 accumulation; returns the logit z.
-__device__ __forceinline__ float mlp_forward(const float *sw, const float (&x)[kNin],
-                                             float (&h1)[kNh])
+__device__ __forceinline__ void stage_params_t(const float *__restrict__ w, float *sw)
 {
-#pragma unroll
-    for (int o = 0; o < kNh; ++o) {
-        float acc = sw[kOffB1 + o];
-#pragma unroll
-        for (int m = 0; m < kNin; ++m) acc = fmaf(sw[kOffW1 + o * kNin + m], x[m], acc);
-        h1[o] = bf(fmaxf(acc, 0.f));
+    for (int k = threadIdx.x; k < kNParams; k += blockDim.x) {
+        const float v = bf(w[k]);
+        int d;
+        if (k < kOffB1) d = kSwW1T + (k % kNin) * kNh + k / kNin;                  // W1[o][m]
+        else if (k < kOffW2) d = kSwB1 + (k - kOffB1);
+        else if (k < kOffB2) d = kSwW2T + ((k - kOffW2) % kNh) * kNh + (k - kOffW2) / kNh;
+        else if (k < kOffW3) d = kSwB2 + (k - kOffB2);
+        else if (k < kOffB3) d = kSwW3 + (k - kOffW3);
+        else d = kSwB3;
+        sw[d] = v;
     }
-    // second layer: 8 outputs at a time (8 independent accumulation chains)
-    float z = sw[kOffB3];
-#pragma unroll 1
-    for (int o0 = 0; o0 < kNh; o0 += 8) {
-        float acc[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] = sw[kOffB2 + o0 + u];
-#pragma unroll
-        for (int k = 0; k < kNh; ++k)
-#pragma unroll
-            for (int u = 0; u < 8; ++u) acc[u] = fmaf(sw[kOffW2 + (o0 + u) * kNh + k], h1[k], acc[u]);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) z = fmaf(sw[kOffW3 + o0 + u], bf(fmaxf(acc[u], 0.f)), z);
-    }
-    return z;
+    __syncthreads();
 }
 
-__global__ void __launch_bounds__(kMlpThreads) warm_infer_kernel(const float *__restrict__ feat,
+// One sample per warp: lane l computes hidden units l and l + 32 of both layers; inputs
+// rounded to BF16, FP32 accumulation; returns the logit z in every lane.
+__device__ __forceinline__ float mlp_forward_warp(const float *sw, const float (&f)[2 * kKnn],
+                                                  int lane)
+{
+    float x[kNin];
+#pragma unroll
+    for (int m = 0; m < kNin; ++m) x[m] = bf(f[m]);
+    float a0 = sw[kSwB1 + lane], a1 = sw[kSwB1 + lane + 32];
+#pragma unroll
+    for (int m = 0; m < kNin; ++m) {
+        a0 = fmaf(sw[kSwW1T + m * kNh + lane], x[m], a0);
+        a1 = fmaf(sw[kSwW1T + m * kNh + lane + 32], x[m], a1);
+    }
+    const float h0 = bf(fmaxf(a0, 0.f)), h1 = bf(fmaxf(a1, 0.f));
+    float c0 = sw[kSwB2 + lane], c1 = sw[kSwB2 + lane + 32];
+#pragma unroll
+    for (int k = 0; k < kNh; ++k) {
+        const float hk = __shfl_sync(0xffffffffu, k < 32 ? h0 : h1, k & 31);
+        c0 = fmaf(sw[kSwW2T + k * kNh + lane], hk, c0);
+        c1 = fmaf(sw[kSwW2T + k * kNh + lane + 32], hk, c1);
+    }
+    float z = sw[kSwW3 + lane] * bf(fmaxf(c0, 0.f)) + sw[kSwW3 + lane + 32] * bf(fmaxf(c1, 0.f));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+    return z + sw[kSwB3];
+}
+
+constexpr int kNetThreads = 256;
+constexpr int kNetSmem = kNParams * sizeof(float);
+
+__global__ void __launch_bounds__(kNetThreads) warm_infer_kernel(const float *__restrict__ feat,
                                                                  int n, const float *__restrict__ w,
                                                                  float *__restrict__ p0)
 {
     __shared__ float sw[kNParams];
-    stage_params(w, sw);
-    const int j = blockIdx.x * kMlpThreads + threadIdx.x;
-    if (j >= n) return;
-    float x[kNin], h1[kNh];
+    stage_params_t(w, sw);
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += nw) {
+        float f[2 * kKnn];
 #pragma unroll
-    for (int m = 0; m < kNin; ++m) x[m] = bf(feat[16 * (size_t)j + m]);
-    const float z = mlp_forward(sw, x, h1);
-    p0[j] = 1.f / (1.f + expf(-z));
+        for (int m = 0; m < 2 * kKnn; ++m) f[m] = feat[16 * (size_t)j + m];
+        const float z = mlp_forward_warp(sw, f, lane);
+        if (lane == 0) p0[j] = 1.f / (1.f + expf(-z));
+    }
 }
 
-// Features + network for many problems in one launch: block -> (problem, 128 matches).
+// Features + network for many problems in one launch, one warp per match.
 constexpr int kWarmBatchMax = 64;
 struct WarmBatch {
     const float2 *src[kWarmBatchMax];
     const float2 *dst[kWarmBatchMax];
     float *p0[kWarmBatchMax];
     int n[kWarmBatchMax];
-    int first_block[kWarmBatchMax + 1];     // prefix sums of the problems' block counts
+    int first[kWarmBatchMax + 1];       // prefix sums of the problems' match counts
     int count;
 };
 
-__global__ void __launch_bounds__(kFeatThreads) warm_start_batch_kernel(
+__global__ void __launch_bounds__(kNetThreads) warm_start_batch_kernel(
     const __grid_constant__ WarmBatch B, const float *__restrict__ w)
 {
     __shared__ float sw[kNParams];
-    __shared__ float2 sx[kFeatChunk];
+    stage_params_t(w, sw);
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int total = B.first[B.count];
     int b = 0;
-    while (b + 1 < B.count && (int)blockIdx.x >= B.first_block[b + 1]) ++b;
-    const int j = (blockIdx.x - B.first_block[b]) * kFeatThreads + threadIdx.x;
-    const int n = B.n[b];
-    stage_params(w, sw);
-    float f[2 * kKnn];
-    knn_features(B.src[b], B.dst[b], n, j, j < n, sx, f);
-    if (j >= n) return;
-    float x[kNin], h1[kNh];
-#pragma unroll
-    for (int m = 0; m < kNin; ++m) x[m] = bf(f[m]);
-    const float z = mlp_forward(sw, x, h1);
-    B.p0[b][j] = 1.f / (1.f + expf(-z));
+    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total; g += nw) {
+        while (g >= B.first[b + 1]) ++b;       // g only grows
+        const int j = g - B.first[b];
+        float f[2 * kKnn];
+        knn_features_warp(B.src[b], B.dst[b], B.n[b], j, lane, f);
+        const float z = mlp_forward_warp(sw, f, lane);
+        if (lane == 0) B.p0[b][j] = 1.f / (1.f + expf(-z));
+    }
 }
 
 // Gradient of the summed cross-entropy over one tile of kMlpThreads samples, written as
@@ -330,8 +382,8 @@ extern "C" emdq_status emdq_warm_features(const float *src, const float *dst, in
     if (!src || !dst || !feat_out || n < kKnn + 1) return EMDQ_EINVAL;
     if (!aligned(src, 8) || !aligned(dst, 8) || !aligned(feat_out, 16))
         return EMDQ_EINVAL;
-    warm_features_kernel<<<(n + kFeatThreads - 1) / kFeatThreads, kFeatThreads, 0,
-                           static_cast<cudaStream_t>(stream)>>>(
+    const int blocks = (n + 7) / 8 < 1024 ? (n + 7) / 8 : 1024;    // 8 warps per block
+    warm_features_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
         reinterpret_cast<const float2 *>(src), reinterpret_cast<const float2 *>(dst), n, feat_out);
     return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }
@@ -340,8 +392,10 @@ extern "C" emdq_status emdq_warm_infer(const float *feat, int n, const float *pa
                                        float *p0_out, void *stream)
 {
     if (!feat || !params || !p0_out || n < 1) return EMDQ_EINVAL;
-    warm_infer_kernel<<<(n + kMlpThreads - 1) / kMlpThreads, kMlpThreads, 0,
-                        static_cast<cudaStream_t>(stream)>>>(feat, n, params, p0_out);
+    const DeviceInfo &D = device_info();
+    const int want = (n + 7) / 8, cap = 2 * (D.sms > 0 ? D.sms : 152);
+    warm_infer_kernel<<<want < cap ? want : cap, kNetThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+        feat, n, params, p0_out);
     return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }
 
@@ -353,7 +407,7 @@ extern "C" emdq_status emdq_warm_start(const float *const *src, const float *con
     if (count > kWarmBatchMax) return EMDQ_ENOTSUP;
     WarmBatch B;
     B.count = count;
-    int blocks = 0;
+    int total = 0;
     for (int b = 0; b < count; ++b) {
         if (!src[b] || !dst[b] || !p0_out[b] || n[b] < kKnn + 1) return EMDQ_EINVAL;
         if (!aligned(src[b], 8) || !aligned(dst[b], 8)) return EMDQ_EINVAL;
@@ -361,11 +415,14 @@ extern "C" emdq_status emdq_warm_start(const float *const *src, const float *con
         B.dst[b] = reinterpret_cast<const float2 *>(dst[b]);
         B.p0[b] = p0_out[b];
         B.n[b] = n[b];
-        B.first_block[b] = blocks;
-        blocks += (n[b] + kFeatThreads - 1) / kFeatThreads;
+        B.first[b] = total;
+        total += n[b];
     }
-    B.first_block[count] = blocks;
-    warm_start_batch_kernel<<<blocks, kFeatThreads, 0, static_cast<cudaStream_t>(stream)>>>(B, params);
+    B.first[count] = total;
+    const DeviceInfo &D = device_info();
+    const int want = (total + 7) / 8, cap = 4 * (D.sms > 0 ? D.sms : 152);
+    warm_start_batch_kernel<<<want < cap ? want : cap, kNetThreads, 0,
+                              static_cast<cudaStream_t>(stream)>>>(B, params);
     return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }
 
