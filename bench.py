@@ -59,6 +59,9 @@ def parse_args():
                     help='keep warming up for at least this long (clock ramp)')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
+    ap.add_argument('--no-plain', action='store_true',
+                    help='skip the plain FP32 GPU comparison (per-frame emdq_fit + FP32 per-pixel '
+                         'field + warp, no warm start, no batching) measured on 10 frames')
     ap.add_argument('--batch', type=int, default=16,
                     help='frames whose EM fits share one launch (1: one emdq_fit per frame)')
     ap.add_argument('--no-warm', action='store_true',
@@ -387,6 +390,32 @@ def run_gpu(args, ws, rank, local):
                    h2d_bytes_per_step=int(n_frames * (frames[0].numel() + src[0].numel() * 8)),
                    d2h_bytes_per_step=int(n_frames * (16 + 4 * n)))
 
+    # the plain FP32 GPU form of the same path, for the headline comparison: per frame
+    # emdq_fit (no warm start) + the FP32 per-pixel field + warp, on 10 frames
+    plain = None
+    if not args.no_plain and rank == 0:
+        fws = torch.empty(emdq.field_workspace_size(n, max_gw, max_gh, emdq.FP32), dtype=torch.uint8,
+                          device=dev)
+        cv2 = canvas.clone()
+        pm = []
+        for i in range(12):
+            k = i % n_frames
+            g = grids[k]
+            disp = disp_buf[: g[2] * g[3] * 2].view(g[3], g[2], 2)
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = emdq.emdq_fit(src[k], dst[k], sc.w, sc.h, out=fit_outs_all[0][0], workspace=fit_ws_all[0])
+            emdq.emdq_field(r['q'], r['c'], src[k], g, alpha, precision=emdq.FP32, out=disp, workspace=fws)
+            emdq.mosaic_warp(frames[k], disp, g, cv2, origin)
+            b.record(stream)
+            b.synchronize()
+            if i >= 2:
+                pm.append(a.elapsed_time(b))
+        plain = dict(value=sc.w * sc.h / 1e6 / (np.mean(pm) / 1e3), unit=UNIT,
+                     ms_per_frame=float(np.mean(pm)), frames=len(pm),
+                     path='emdq_fit + emdq_field (fp32 per-pixel) + mosaic_warp, one frame at a time')
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -448,7 +477,9 @@ def run_gpu(args, ws, rank, local):
         batch=B, warm_start=warm, wall_s=wall, roofline=roof,
         gpu_launches=total_frames * (2 if fused else 3) + args.steps * len(batches) * (2 if warm else 1),
         clocks=clk,
-        e2e=e2e,
+        e2e=e2e, plain_fp32_gpu=plain,
+        speedup_vs_plain_fp32_gpu=(None if plain is None else
+                                   ws * total_frames * sc.w * sc.h / 1e6 / (total_ms / 1e3) / plain['value']),
         fit_status=statuses,
     )
     if not args.no_cpu_baseline:
