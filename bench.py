@@ -86,7 +86,7 @@ def measured_peaks() -> dict:
 
 
 class ClockSampler:
-    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    """nvidia-smi sampled every 20 ms while the timed region runs."""
     Q = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
          'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
          'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
@@ -149,6 +149,44 @@ def dist_env():
     return ws, rank, local
 
 
+# Multi-GPU: the path partitions by sequence.  Every rank mosaics its own independent
+# sequence into its own canvas, so ranks exchange nothing on the data path; only the
+# timing is combined (barrier, then the maximum over ranks of the timed region).
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Seed of the sequence rank `rank` mosaics (distinct scenes and matches per rank)."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mpix_per_s(ws: int, frames_per_rank: int, w: int, h: int, max_ms: float) -> float:
+    """Whole-job throughput: the frame pixels all ranks processed over the slowest rank's time."""
+    return ws * frames_per_rank * w * h / 1e6 / (max_ms / 1e3)
+
+
+def workload_config(args, sc, cfg, n_frames, ws) -> dict:
+    """The `config` object of the JSON line (the same for both arms)."""
+    cw, chh = cfg['canvas']
+    return dict(workload=f'{args.workload}: {n_frames}-frame sequence of {sc.w}x{sc.h} RGB8 '
+                         f'frames, N={cfg["n"]} matches/frame, {int(cfg["outliers"] * 100)}% '
+                         f'outliers, {cw}x{chh} RGBW canvas; one step = one pass over the sequence',
+                frame=[sc.w, sc.h], n_matches=cfg['n'], canvas=[cw, chh],
+                frames_per_step=n_frames, parallelism=f'dp{ws} (independent sequences)',
+                l2=f'inputs larger than L2 ({n_frames} distinct frames, '
+                   f'{n_frames * sc.w * sc.h * sc.channels / 1e6:.0f} MB per step) and a '
+                   f'256 MiB flush before every step, outside the timed events')
+
+
 def prepare_sequence(name: str, seed: int, n_frames: int, device):
     """Frames, matches and windows of the first n_frames frames of a workload (all on
     the device before timing starts)."""
@@ -186,7 +224,7 @@ def run_gpu(args, ws, rank, local):
     if args.frames > 0:
         n_frames = min(n_frames, args.frames)
     sc, cfg, origin, ref, frames, src, dst, grids = prepare_sequence(
-        args.workload, args.seed + 1000 * rank, n_frames, dev)
+        args.workload, rank_seed(args.seed, rank), n_frames, dev)
     cw, chh = cfg['canvas']
     n = cfg['n']
     canvas = torch.zeros((chh, cw, 4), dtype=torch.uint8, device=dev)
@@ -221,23 +259,27 @@ def run_gpu(args, ws, rank, local):
     warm_params = emdq.load_warmstart_params(dev) if warm else None
     warm_p0 = [[torch.empty(n, device=dev) for _ in range(B)] for _ in range(nbuf)]
 
-    def field_and_warp(fr, s_, g, fo):
+    def field_and_warp(fr, s_, g, fo, ev_field=None):
         if fused:
             emdq.emdq_mosaic(fo['q'], fo['c'], s_, g, alpha, fr, canvas, origin, workspace=field_ws)
+            if ev_field is not None: ev_field.record(stream)
         else:
             disp = disp_buf[: g[2] * g[3] * 2].view(g[3], g[2], 2)
             emdq.emdq_field(fo['q'], fo['c'], s_, g, alpha, precision=prec, out=disp,
                             workspace=field_ws)
+            if ev_field is not None: ev_field.record(stream)
             emdq.mosaic_warp(fr, disp, g, canvas, origin)
 
-    def fit_batch(bi, ks, s_of, d_of):
-        """The fits of batch bi (frames ks) on the fit stream; returns its done event."""
+    def fit_batch(bi, ks, s_of, d_of, ev=None):
+        """The fits of batch bi (frames ks) on the fit stream; returns its done event.
+        ev[1] is recorded between the warm start and the fit launch, ev[2] after the fits."""
         outs = fit_outs_all[bi % nbuf]
         with torch.cuda.stream(fit_stream):
             p0s = [None] * len(ks)
             if warm:
                 p0s = emdq.warm_start([(s_of(k), d_of(k)) for k in ks], warm_params,
                                       outs=warm_p0[bi % nbuf][: len(ks)], stream=fit_stream)
+            if ev: ev[1].record(fit_stream)
             if B == 1:
                 emdq.emdq_fit(s_of(ks[0]), d_of(ks[0]), sc.w, sc.h, p0=p0s[0], out=outs[0],
                               workspace=fit_ws_all[bi % nbuf], stream=fit_stream)
@@ -245,6 +287,7 @@ def run_gpu(args, ws, rank, local):
                 emdq.emdq_fit_batch([(s_of(k), d_of(k), sc.w, sc.h, p0s[j]) for j, k in enumerate(ks)],
                                     outs=outs[: len(ks)], workspace=batch_ws[bi % nbuf],
                                     stream=fit_stream)
+            if ev: ev[2].record(fit_stream)
             done = torch.cuda.Event()
             done.record(fit_stream)
         return done
@@ -253,10 +296,10 @@ def run_gpu(args, ws, rank, local):
         """Field + warp of batch bi in frame order on the main stream, after its fits."""
         stream.wait_event(fit_done)
         outs = fit_outs_all[bi % nbuf]
-        if ev: ev[1].record(stream)
+        if ev: ev[3].record(stream)
         for j, k in enumerate(ks):
-            field_and_warp(fr_of(k), s_of(k), grids[k], outs[j])
-            if ev: ev[2 + j].record(stream)
+            field_and_warp(fr_of(k), s_of(k), grids[k], outs[j], ev[4 + 2 * j] if ev else None)
+            if ev: ev[5 + 2 * j].record(stream)
         for j, k in enumerate(ks):
             infos[k].copy_(outs[j]['info'])
         blended = torch.cuda.Event()
@@ -273,7 +316,7 @@ def run_gpu(args, ws, rank, local):
                 fit_stream.wait_event(blended[i - nbuf])
             if evs is not None:
                 evs[i][0].record(fit_stream)
-            done[i] = fit_batch(i, batches_[i], s_of, d_of)
+            done[i] = fit_batch(i, batches_[i], s_of, d_of, evs[i] if evs is not None else None)
         issue_fit(0)
         for i, ks in enumerate(batches_):
             if i + 1 < len(batches_):
@@ -299,7 +342,7 @@ def run_gpu(args, ws, rank, local):
         one_pass()
         torch.cuda.synchronize()
         w += 1
-    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2 + len(ks))] for ks in batches]
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(4 + 2 * len(ks))] for ks in batches]
            for _ in range(args.steps)]
     if ws > 1:
         torch.distributed.barrier()
@@ -318,27 +361,30 @@ def run_gpu(args, ws, rank, local):
         torch.distributed.barrier()
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
-    # e[0]: the batch's fits issued (fit stream); e[1]: its blend starts (main stream, after
-    # the fits); e[2 + j]: frame j blended.  Frame latency = e[0] -> e[2 + j]; the step time
-    # is first fit issue -> last blend of the pass.
-    fit_ms, mos_ms, lat_ms, pass_ms = [], [], [], []
+    # per batch e[0]: its fits issued and e[1]: warm start done, e[2]: fits done (all on the
+    # fit stream); e[3]: its blend starts (main stream, after the fits); e[4 + 2j]: frame j's
+    # field done, e[5 + 2j]: its warp done.  Frame latency = e[0] -> e[5 + 2j]; the step time
+    # is first fit issue -> last warp of the pass.  Kernel durations are taken on the stream
+    # each kernel runs on.
+    lat_ms, pass_ms = [], []
+    warm_ms, fit_ms, field_ms, warp_ms = [], [], [], []
+    fit_launch_frames = []
     for step in evs:
-        for e in step:
-            nb = len(e) - 2
-            fit_ms.append(e[0].elapsed_time(e[1]) / nb)
-            prev = e[1]
+        for bi, e in enumerate(step):
+            nb = (len(e) - 4) // 2
+            warm_ms.append(e[0].elapsed_time(e[1]))
+            fit_ms.append(e[1].elapsed_time(e[2]))
+            fit_launch_frames.append(batches[bi])
+            prev = e[3]
             for j in range(nb):
-                mos_ms.append(prev.elapsed_time(e[2 + j]))
-                lat_ms.append(e[0].elapsed_time(e[2 + j]))
-                prev = e[2 + j]
+                field_ms.append(prev.elapsed_time(e[4 + 2 * j]))
+                warp_ms.append(e[4 + 2 * j].elapsed_time(e[5 + 2 * j]))
+                lat_ms.append(e[0].elapsed_time(e[5 + 2 * j]))
+                prev = e[5 + 2 * j]
         pass_ms.append(step[0][0].elapsed_time(step[-1][-1]))
     total_ms = float(np.sum(pass_ms))
-    phase_ms = np.array([np.mean(fit_ms), np.mean(mos_ms), 0.0])
     frame_ms = np.array(lat_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, ws, dev)
     iv = torch.stack(all_infos).view(-1, 4).cpu()
     iters = iv[:, 1].numpy()
     statuses = sorted({emdq.STATUS.get(int(v), '?') for v in iv[:, 0].tolist()})
@@ -381,11 +427,8 @@ def run_gpu(args, ws, rank, local):
             if i >= 1:
                 e_ms.append(a.elapsed_time(b))
         e_total = sum(e_ms)
-        if ws > 1:
-            t = torch.tensor([e_total], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_total = float(t.item())
-        e2e = dict(value=ws * len(e_ms) * n_frames * sc.w * sc.h / 1e6 / (e_total / 1e3),
+        e_total = max_over_ranks(e_total, ws, dev)
+        e2e = dict(value=job_mpix_per_s(ws, len(e_ms) * n_frames, sc.w, sc.h, e_total),
                    unit=UNIT, ms_per_frame=e_total / (len(e_ms) * n_frames),
                    h2d_bytes_per_step=int(n_frames * (frames[0].numel() + src[0].numel() * 8)),
                    d2h_bytes_per_step=int(n_frames * (16 + 4 * n)))
@@ -422,54 +465,65 @@ def run_gpu(args, ws, rank, local):
         return None
 
     peaks = measured_peaks()
-    names = ['fit', 'mosaic' if fused else 'field', 'warp']
-    dom = int(np.argmax(phase_ms))
     win_px = float(np.mean([g[2] * g[3] for g in grids]))
     mean_iters = float(np.mean(iters))
-    rounds = mean_iters + 1
-    if names[dom] == 'fit':
-        # FP32 operations per match pair and EM round: 2 x 17 in the two M-step passes,
-        # 22 in the leave-one-out blend
-        work = rounds * n * n * 56.0
-        peak = 152 * 128 * 2 * peaks['sm_max_mhz'] * 1e6 / 1e12
+    sm_mhz = (clk or {}).get('sm_mhz') or peaks['sm_max_mhz']
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    alu_src = f'derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x {sm_mhz:.0f} MHz (sampled SM clock)'
+    # per-frame EM rounds of every fit launch (step-major, the order the events were taken)
+    it_steps = [t[:, 1].cpu().numpy() for t in all_infos]
+    launch_rounds = [float(np.sum(it_steps[i // len(batches)][fit_launch_frames[i]] + 1))
+                     for i in range(len(fit_launch_frames))]
+    kernel_total = dict(fit=float(np.sum(fit_ms)), warm=float(np.sum(warm_ms)),
+                        field=float(np.sum(field_ms)), warp=float(np.sum(warp_ms)))
+    dom = max(kernel_total, key=kernel_total.get)
+    if dom == 'fit':
+        # FP32 operations per match pair and EM round (an FMA counts 2): 34 in the M-step
+        # pass, 22 in the leave-one-out blend
+        flops = float(np.sum(launch_rounds)) * n * n * 56.0 / len(fit_ms)
         roof = dict(bound='alu', kernel='emdq_fit_batch_kernel' if B > 1 else 'emdq_fit_kernel',
-                    achieved=work / (phase_ms[0] * 1e-3) / 1e12,
-                    peak=peak, unit='TFLOP/s', peak_source='derived: 152 SM x 128 FP32 lanes x 2 x max clock')
-    elif names[dom] in ('field', 'mosaic'):
+                    achieved=flops / (np.mean(fit_ms) * 1e-3) / 1e12, peak=alu_peak, unit='TFLOP/s',
+                    peak_source=alu_src, launches=len(fit_ms), mean_launch_ms=float(np.mean(fit_ms)),
+                    work_per_launch=f'{flops:.4g} FP32 flops = 56 x EM rounds x N^2 over the '
+                                    f'launch\'s {B} fits')
+    elif dom == 'warm':
+        # per match: N distance tests (4 flops) + the 16-64-64-1 network (2 x 5184 MACs)
+        flops = B * n * (4.0 * n + 2 * 5184)
+        roof = dict(bound='alu', kernel='warm_start_batch_kernel',
+                    achieved=flops / (np.mean(warm_ms) * 1e-3) / 1e12, peak=alu_peak, unit='TFLOP/s',
+                    peak_source=alu_src, launches=len(warm_ms), mean_launch_ms=float(np.mean(warm_ms)))
+    elif dom == 'field':
         if prec == emdq.BF16:
-            work = 2.0 * 6 * win_px * n
-            roof = dict(bound='tensor', kernel='field_tc_kernel', achieved=work / (phase_ms[1] * 1e-3) / 1e12,
-                        peak=peaks['bf16_tflops'], unit='TFLOP/s', peak_source=peaks['source'] + ' bf16 burst')
+            flops = 2.0 * 6 * win_px * n
+            roof = dict(bound='tensor', kernel='field_tc_kernel (+ field_tc_prep_kernel in the timing)',
+                        achieved=flops / (np.mean(field_ms) * 1e-3) / 1e12,
+                        peak=peaks['bf16_tflops'], unit='TFLOP/s',
+                        peak_source=peaks['source'] + ' bf16 burst', launches=len(field_ms),
+                        mean_launch_ms=float(np.mean(field_ms)))
         else:
-            work = win_px * n * 17.0
-            peak = 152 * 128 * 2 * peaks['sm_max_mhz'] * 1e6 / 1e12
-            roof = dict(bound='alu', kernel='field_direct_kernel', achieved=work / (phase_ms[1] * 1e-3) / 1e12,
-                        peak=peak, unit='TFLOP/s', peak_source='derived: 152 SM x 128 FP32 lanes x 2 x max clock')
+            flops = win_px * n * 17.0
+            roof = dict(bound='alu', kernel='field_direct_kernel',
+                        achieved=flops / (np.mean(field_ms) * 1e-3) / 1e12, peak=alu_peak,
+                        unit='TFLOP/s', peak_source=alu_src, launches=len(field_ms),
+                        mean_launch_ms=float(np.mean(field_ms)))
     else:
-        work = win_px * (8 + 8) + sc.w * sc.h * sc.channels
-        roof = dict(bound='hbm', kernel='mosaic_warp_kernel', achieved=work / (phase_ms[2] * 1e-3) / 1e9,
-                    peak=peaks['hbm_gbs'], unit='GB/s', peak_source=peaks['source'] + ' copy')
+        nbytes = win_px * (8 + 8) + sc.w * sc.h * sc.channels
+        roof = dict(bound='hbm', kernel='mosaic_warp_kernel',
+                    achieved=nbytes / (np.mean(warp_ms) * 1e-3) / 1e9,
+                    peak=peaks['hbm_gbs'], unit='GB/s', peak_source=peaks['source'] + ' copy',
+                    launches=len(warp_ms), mean_launch_ms=float(np.mean(warp_ms)))
     roof['frac'] = roof['achieved'] / roof['peak']
     tr = NCU_TRAFFIC.get(roof['kernel'])
     roof['traffic'] = tr['bytes'] if tr and tr['src'] == _src_hash(tr['file']) else None
 
     line = dict(
-        metric=METRIC, value=ws * total_frames * sc.w * sc.h / 1e6 / (total_ms / 1e3), unit=UNIT,
+        metric=METRIC, value=job_mpix_per_s(ws, total_frames, sc.w, sc.h, total_ms), unit=UNIT,
         n_gpus=ws, steps=args.steps, warmup=args.warmup, ms_per_step=total_ms / args.steps,
         p50_frame_ms=float(np.median(frame_ms)), higher_is_better=True, scaling='weak',
         vs_baseline=None, dtype='bf16' if prec == emdq.BF16 else 'f32', data='synthetic',
-        config=dict(workload=f'{args.workload}: {n_frames}-frame sequence of {sc.w}x{sc.h} RGB8 '
-                    f'frames, N={n} matches/frame, {int(cfg["outliers"] * 100)}% outliers, '
-                    f'{cw}x{chh} RGBW canvas; one step = one pass over the sequence',
-                    frame=[sc.w, sc.h], n_matches=n, canvas=list(cfg['canvas']),
-                    frames_per_step=n_frames, precision=args.precision,
-                    parallelism=f'dp{ws} (independent sequences)',
-                    l2=f'inputs larger than L2 ({n_frames} distinct frames, '
-                       f'{n_frames * sc.w * sc.h * sc.channels / 1e6:.0f} MB per step) and a '
-                       f'256 MiB flush before every step, outside the timed events',
+        config=dict(workload_config(args, sc, cfg, n_frames, ws), precision=args.precision,
                     mean_window_px=win_px, mean_em_iters=mean_iters),
-        phases_ms=dict(fit=float(phase_ms[0]), **({'mosaic': float(phase_ms[1])} if fused else
-                                                   {'field+warp': float(phase_ms[1])})),
+        kernel_ms_per_step={k: v / args.steps for k, v in kernel_total.items()},
         path=(('learned warm start + ' if warm else '') + ('emdq_fit_batch' if B > 1 else 'emdq_fit') +
               (' + emdq_mosaic (fused BF16 field and warp)' if fused else
                f' + emdq_field ({args.precision}) + mosaic_warp') +
@@ -479,7 +533,7 @@ def run_gpu(args, ws, rank, local):
         clocks=clk,
         e2e=e2e, plain_fp32_gpu=plain,
         speedup_vs_plain_fp32_gpu=(None if plain is None else
-                                   ws * total_frames * sc.w * sc.h / 1e6 / (total_ms / 1e3) / plain['value']),
+                                   job_mpix_per_s(ws, total_frames, sc.w, sc.h, total_ms) / plain['value']),
         fit_status=statuses,
     )
     if not args.no_cpu_baseline:
@@ -567,9 +621,9 @@ def run_reference(args, ws, rank):
                 steps=args.steps, warmup=args.warmup, ms_per_step=sec * 1e3,
                 p50_frame_ms=float(np.median(times)) * 1e3, higher_is_better=True, scaling='weak',
                 vs_baseline=None, dtype='f64', data='synthetic',
-                config=dict(workload=f'{args.workload}: 1280x1024 RGB8 frames, N={cfg["n"]} '
-                            f'matches/frame, {int(cfg["outliers"] * 100)}% outliers, 4096x4096 canvas',
-                            frame=[sc.w, sc.h], n_matches=cfg['n'], canvas=list(cfg['canvas'])),
+                config=dict(workload_config(args, sc, cfg, cfg['frames'], ws), precision='f64',
+                            sample=f'per step one frame of the sequence: full EM fit + field and '
+                                   f'warp on {frac:.3f} of the window rows, extrapolated'),
                 cpu_baseline=dict(value=value, unit=UNIT, cores=orc.max_threads(), kind='oracle',
                                   sample=f'per step: full EM fit + field and warp on {frac:.3f} of '
                                          f'the window rows, extrapolated to the full window'),
