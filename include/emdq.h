@@ -96,8 +96,9 @@ EMDQ_API int         emdq_abi_version(void);
  *   iterate   E-step: p_j = gamma G_j / (gamma G_j + (1-gamma)/(w h)),
  *               G_j = exp(-e_j / (2 sigma^2)) / (2 pi sigma^2)
  *             M-step: per match i the closed-form similarity of Eqs. 18-20 fitted to all
- *               matches with weights p_j exp(-alpha |x_i - x_j|^2) (two passes: the
- *               weighted centroid, then the centred moments, so FP32 sums do not cancel)
+ *               matches with weights p_j exp(-alpha |x_i - x_j|^2) (moments taken about
+ *               the weighted centroid -- found by a first pass at step 0, the previous
+ *               round's afterwards -- so FP32 sums do not cancel)
  *             residuals e_j = |y_j - W_{-j}(x_j)|^2 of the leave-one-out blend (Eqs. 2-4)
  *             sigma^2 = max(sum p e / (2 sum p), floor), gamma = clamp(mean p, .05, .95)
  *   output    q_out rows, c_out[i] = p_i if p_i >= 1/2 else 0, p_out = p
@@ -106,7 +107,8 @@ EMDQ_API int         emdq_abi_version(void);
  *   n          3 <= n <= emdq_fit_max_n()
  *   frame_w/h  size of frame t (outlier density 1/(w h); alpha rule)
  *   prm        host; NULL = defaults
- *   p0         device, n float initial inlier weights, or NULL for all ones
+ *   p0         device, n float initial inlier weights in [0, 1], or NULL for all ones
+ *              (a negative or non-finite weight gives info->status = EMDQ_ENONFINITE)
  *   q_out      device, n x 8 float warp rows (written)
  *   c_out      device, n float field weights (written)
  *   p_out      device, n float final posteriors (written), may be NULL

@@ -2,22 +2,30 @@
 // iteration, synchronising its CTAs with bounded grid barriers, so that a whole fit costs
 // one launch and no host round trip.
 //
-// Work split per iteration (N matches, G CTAs of 8 warps, one warp per match row):
+// Work split per iteration (N matches, G CTAs of 8 warps):
 //   E-step      every CTA computes all N posteriors redundantly into shared memory
 //               (identical inputs and reduction order, hence identical convergence
 //               decisions in every CTA without an extra barrier)
-//   M-step      warp w fits rows i = w, w + 8G, ...  The weighted similarity fit needs
-//               the centred second moments of Eqs. 18-19; accumulating raw moments and
-//               centring afterwards cancels catastrophically (it is why an FP64 finish
-//               would be needed).  Instead two passes over j: the weighted centroid,
-//               then the moments about it, so nothing cancels and FP32 products and sums
-//               suffice (local coordinates x_j - x_i, y_j - y_i keep the values small).
+//   M-step      warp w fits rows i = w, w + 8G, ..., two rows at a time so that each
+//               shared-memory load of match j serves both.  The weighted similarity fit
+//               needs the centred second moments of Eqs. 18-19; accumulating raw moments
+//               and centring afterwards cancels catastrophically (it is why an FP64 finish
+//               would be needed).  Instead the moments are taken about a shift close to
+//               the weighted centroid -- at step 0 the centroid itself from a first pass,
+//               later the previous round's centroid -- so nothing cancels and FP32
+//               products and sums suffice.
 //   barrier
-//   residuals   warp w computes the leave-one-out blend at x_j for its rows j, the blend
-//               taken relative to row j's own warp (exact: the blend is linear) to keep
-//               the FP32 sums small                                 -> e_j (global)
+//   residuals   warp w computes the leave-one-out blend at x_j for its rows j, four rows
+//               at a time, blending the warp rows relative to row 0's (exact: the blend is
+//               linear) to keep the FP32 sums small                  -> e_j (global)
 //   barrier
 //   sigma^2, gamma from the per-CTA partial sums, in a fixed order.
+//
+// Arithmetic per match pair: coordinates are staged pre-multiplied by
+// k = sqrt(alpha log2 e) and the weights p as log2 p, so the Gaussian weight
+// p_j exp(-alpha |x_i - x_j|^2) = 2^(log2 p_j - |k x_i - k x_j|^2) costs two FMAs and one
+// MUFU.EX2; the (x, y) pairs of the moment sums use Blackwell's packed FP32x2 FMA/ADD/MUL
+// (two lanes of arithmetic per instruction).
 #include <cmath>
 #include <mutex>
 
@@ -27,7 +35,8 @@ namespace emdq {
 
 constexpr int kFitThreads = 256;
 constexpr int kFitWarps = kFitThreads / 32;
-constexpr int kFitMaxN = 5120;         // shared memory: 40 bytes per match
+constexpr int kFitMaxN = 5120;         // shared memory: 44 bytes per match
+constexpr int kFitSmemPerMatch = 44;
 constexpr int kFitMaxGrid = 1024;
 constexpr int kFitEPerThread = (kFitMaxN + kFitThreads - 1) / kFitThreads;   // residuals per thread
 
@@ -35,7 +44,8 @@ struct FitArgs {
     const float2 *src;
     const float2 *dst;
     int n;
-    float alpha2;        // alpha * log2(e): weights are exp2(-alpha2 d^2)
+    float k;             // sqrt(alpha log2 e): staged coordinates are k x, k y
+    float inv_k;
     float inv_area;
     int max_iters;
     float tol;
@@ -46,30 +56,30 @@ struct FitArgs {
     float *p_out;
     emdq_fit_info *info;
     float *e;            // n residuals^2 (workspace)
-    float4 *cen;         // n weighted centroids of the last M-step, local coordinates (workspace)
+    float4 *cen;         // n weighted centroids of the last M-step, scaled local coordinates (workspace)
     float *partials;     // one float2 partial sum per CTA of the group (workspace)
     unsigned *bar;       // barrier arrival counter, zero at launch (workspace)
     int *flag;           // device status, zero at launch (workspace)
 };
 
 struct FitSmem {
-    float2 *x, *y;
-    float *p;
-    float *qa, *qb, *qu, *qv, *qs;   // warp rows, SoA
+    float4 *q;           // warp rows minus row 0's: (r_w, r_z, d_x, d_y)
+    float2 *x, *y;       // k x_j, k y_j
+    float *p;            // posteriors
+    float *lp;           // log2 of the posteriors (-inf for 0)
+    float *qs;           // scale column of the warp rows minus row 0's
 };
 
 __device__ __forceinline__ FitSmem fit_smem(int n)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FitSmem s;
-    s.x = reinterpret_cast<float2 *>(smem_raw);
+    s.q = reinterpret_cast<float4 *>(smem_raw);
+    s.x = reinterpret_cast<float2 *>(s.q + n);
     s.y = s.x + n;
     s.p = reinterpret_cast<float *>(s.y + n);
-    s.qa = s.p + n;
-    s.qb = s.qa + n;
-    s.qu = s.qb + n;
-    s.qv = s.qu + n;
-    s.qs = s.qv + n;
+    s.lp = s.p + n;
+    s.qs = s.lp + n;
     return s;
 }
 
@@ -106,18 +116,26 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
-// Eqs. 18-20 from the weight W, the weighted centroids (local coordinates) and the centred
-// moments: rotation (2-D closed form), scale (norm ratio), translation.  Lane 0 writes the
-// q row and the centroid.
-__device__ __forceinline__ void mstep_finish(const FitArgs &A, int i, float2 xi, float2 yi,
-                                             float W, float ab0, float ab1, float bb0, float bb1,
-                                             float vx, float vy, float c00, float c01, float c10,
-                                             float c11, int lane)
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// Gaussian weight 2^(lp - |d|^2) of a scaled offset d.
+__device__ __forceinline__ float gauss_w(float2 d, float lp)
+{
+    return ex2_ftz(fmaf(-d.x, d.x, fmaf(-d.y, d.y, lp)));
+}
+
+// Eqs. 18-20 for row i from the weight W, the weighted centroids relative to (x_i, y_i)
+// in scaled coordinates, and the centred moments (scaled; the factor k^2 cancels in every
+// ratio): rotation (2-D closed form of the SVD solution), scale (norm ratio), translation.
+// Lane 0 writes the q row and the centroid.
+__device__ __forceinline__ void mstep_finish(const FitArgs &A, int i, float W, float ab0,
+                                             float ab1, float bb0, float bb1, float vx, float vy,
+                                             float dot, float cross, int lane)
 {
     // Eq. 18 in 2-D: the rotation angle th maximising tr(R^T C_t C_0^T) has direction
     // (a, b) = (c00 + c11, c10 - c01); its half angle (the DQ real part) is the direction
     // of (rho + a, b), or of (b, rho - a) when a < 0 (no cancellation).
-    const float a = c00 + c11, b = c10 - c01;
+    const float a = dot, b = cross;
     const float rho = hypotf(a, b);
     float h0, h1;
     if (a >= 0.f) { h0 = rho + a; h1 = b; }
@@ -128,10 +146,12 @@ __device__ __forceinline__ void mstep_finish(const FitArgs &A, int i, float2 xi,
     if (hn > 0.f) { c = h0 / hn; sn = h1 / hn; }
     // Eq. 19: norm ratio
     const float sc = sqrtf(vy / vx);
-    // Eq. 20: t = ybar / s - R xbar in global coordinates
+    // Eq. 20: t = ybar / s - R xbar, in pixels (the centroids unscaled onto the exact
+    // match coordinates)
+    const float2 xi = __ldg(A.src + i), yi = __ldg(A.dst + i);
     const float ct = c * c - sn * sn, st = 2.f * c * sn;
-    const float xg0 = xi.x + ab0, xg1 = xi.y + ab1;
-    const float yg0 = yi.x + bb0, yg1 = yi.y + bb1;
+    const float xg0 = fmaf(ab0, A.inv_k, xi.x), xg1 = fmaf(ab1, A.inv_k, xi.y);
+    const float yg0 = fmaf(bb0, A.inv_k, yi.x), yg1 = fmaf(bb1, A.inv_k, yi.y);
     const float tx = yg0 / sc - (ct * xg0 - st * xg1);
     const float ty = yg1 / sc - (st * xg0 + ct * xg1);
     const bool ok = W > 0.f && isfinite(W) && vx > 0.f && isfinite(sc) && isfinite(tx) &&
@@ -153,125 +173,213 @@ __device__ __forceinline__ void mstep_finish(const FitArgs &A, int i, float2 xi,
     __stcg(A.cen + i, ok ? make_float4(ab0, ab1, bb0, bb1) : make_float4(0.f, 0.f, 0.f, 0.f));
 }
 
-// M-step of row i (one warp): weights om_j = p_j exp(-alpha |x_j - x_i|^2), local
-// coordinates a = x_j - x_i, b = y_j - y_i.  The similarity fit needs the moments about
-// the weighted centroid; summing raw moments and centring afterwards cancels.
+// M-step of R rows (one warp, lanes over j): weights om_j = p_j exp(-alpha |x_j - x_i|^2),
+// offsets u = x_j - x_i - shift_x, v = y_j - y_i - shift_y (scaled coordinates).  The
+// similarity fit needs the moments about the weighted centroid; summing raw moments and
+// centring afterwards cancels.
 //   first round: two passes -- W and the centroid, then the moments about it;
-//   later rounds: one pass about the previous round's centroid s of this row (the
-//     weights change little from round to round, so the centroid moves by far less than
-//     the spread and the final correction W |centroid - s|^2 cancels nothing).
-__device__ void mstep_row(const FitArgs &A, const FitSmem &S, int i, int lane, bool first)
+//   later rounds: one pass about the previous round's centroid of the row (the weights
+//     change little from round to round, so the centroid moves by far less than the spread
+//     and the final correction W |centroid - shift|^2 cancels nothing).
+// Of C_t C_0^T only the trace (c00 + c11 = sum om u.v) and the antisymmetric part
+// (c10 - c01 = sum om u x v) enter the 2-D rotation, so only those are summed.
+template <int R>
+__device__ void mstep_rows(const FitArgs &A, const FitSmem &S, const int *rows, int lane,
+                           bool first)
 {
     const int n = A.n;
-    const float2 xi = S.x[i], yi = S.y[i];
-    float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (!first) sh = __ldcg(A.cen + i);
+    float2 nxi[R], nyi[R];
+    float4 sh[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        nxi[r] = neg2(S.x[rows[r]]);
+        nyi[r] = neg2(S.y[rows[r]]);
+        sh[r] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldcg(A.cen + rows[r]);
+    }
     if (first) {
-        float W = 0.f, sa0 = 0.f, sa1 = 0.f, sb0 = 0.f, sb1 = 0.f;
-#pragma unroll 4
+        float W[R];
+        float2 sa[R], sb[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            W[r] = 0.f;
+            sa[r] = sb[r] = make_float2(0.f, 0.f);
+        }
+#pragma unroll 2
         for (int j = lane; j < n; j += 32) {
             const float2 xj = S.x[j], yj = S.y[j];
-            const float a0 = xj.x - xi.x, a1 = xj.y - xi.y;
-            const float om = S.p[j] * ex2_ftz(-A.alpha2 * (a0 * a0 + a1 * a1));
-            W += om;
-            sa0 += om * a0;
-            sa1 += om * a1;
-            sb0 += om * (yj.x - yi.x);
-            sb1 += om * (yj.y - yi.y);
+            const float lpj = S.lp[j];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float2 a = __fadd2_rn(xj, nxi[r]);
+                const float om = gauss_w(a, lpj);
+                const float2 om2 = make_float2(om, om);
+                W[r] += om;
+                sa[r] = __ffma2_rn(om2, a, sa[r]);
+                sb[r] = __ffma2_rn(om2, __fadd2_rn(yj, nyi[r]), sb[r]);
+            }
         }
-        W = warp_sum_f(W);
-        sa0 = warp_sum_f(sa0);
-        sa1 = warp_sum_f(sa1);
-        sb0 = warp_sum_f(sb0);
-        sb1 = warp_sum_f(sb1);
-        if (W > 0.f && isfinite(W)) sh = make_float4(sa0 / W, sa1 / W, sb0 / W, sb1 / W);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float w = warp_sum_f(W[r]);
+            const float a0 = warp_sum_f(sa[r].x), a1 = warp_sum_f(sa[r].y);
+            const float b0 = warp_sum_f(sb[r].x), b1 = warp_sum_f(sb[r].y);
+            if (w > 0.f && isfinite(w)) sh[r] = make_float4(a0 / w, a1 / w, b0 / w, b1 / w);
+        }
     }
-    // one pass about the shift sh: W, first moments (for the small correction) and the
-    // second moments
-    float W = 0.f, su0 = 0.f, su1 = 0.f, sv0 = 0.f, sv1 = 0.f;
-    float vx = 0.f, vy = 0.f, c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
-#pragma unroll 4
+    // one pass about the shift: W, first moments (for the small correction), the two
+    // second moments and the trace / antisymmetric part of C_t C_0^T
+    float2 nm[R], nmy[R], nmys[R];
+    float W[R];
+    float2 su[R], sv[R], vxp[R], vyp[R], dotp[R], crp[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        nm[r] = make_float2(nxi[r].x - sh[r].x, nxi[r].y - sh[r].y);
+        nmy[r] = make_float2(nyi[r].x - sh[r].z, nyi[r].y - sh[r].w);
+        nmys[r] = make_float2(nmy[r].y, nmy[r].x);
+        W[r] = 0.f;
+        su[r] = sv[r] = vxp[r] = vyp[r] = dotp[r] = crp[r] = make_float2(0.f, 0.f);
+    }
+#pragma unroll 2
     for (int j = lane; j < n; j += 32) {
         const float2 xj = S.x[j], yj = S.y[j];
-        const float a0 = xj.x - xi.x, a1 = xj.y - xi.y;
-        const float om = S.p[j] * ex2_ftz(-A.alpha2 * (a0 * a0 + a1 * a1));
-        const float u0 = a0 - sh.x, u1 = a1 - sh.y;
-        const float v0 = (yj.x - yi.x) - sh.z, v1 = (yj.y - yi.y) - sh.w;
-        const float ou0 = om * u0, ou1 = om * u1;
-        W += om;
-        su0 += ou0;
-        su1 += ou1;
-        sv0 += om * v0;
-        sv1 += om * v1;
-        vx += ou0 * u0 + ou1 * u1;          // |vector(C_0)|^2 about the shift
-        vy += om * (v0 * v0 + v1 * v1);     // |vector(C_t)|^2 about the shift
-        c00 += v0 * ou0;                    // C_t C_0^T about the shift
-        c01 += v0 * ou1;
-        c10 += v1 * ou0;
-        c11 += v1 * ou1;
+        const float lpj = S.lp[j];
+        const float2 yjs = make_float2(yj.y, yj.x);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float om = gauss_w(__fadd2_rn(xj, nxi[r]), lpj);
+            const float2 om2 = make_float2(om, om);
+            const float2 u = __fadd2_rn(xj, nm[r]);
+            const float2 v = __fadd2_rn(yj, nmy[r]);
+            const float2 vs = __fadd2_rn(yjs, nmys[r]);    // (v1, v0)
+            const float2 ou = __fmul2_rn(om2, u);
+            const float2 ov = __fmul2_rn(om2, v);
+            W[r] += om;
+            su[r] = __fadd2_rn(su[r], ou);
+            sv[r] = __fadd2_rn(sv[r], ov);
+            vxp[r] = __ffma2_rn(ou, u, vxp[r]);            // |vector(C_0)|^2 about the shift
+            vyp[r] = __ffma2_rn(ov, v, vyp[r]);            // |vector(C_t)|^2 about the shift
+            dotp[r] = __ffma2_rn(ou, v, dotp[r]);          // (c00, c11)
+            crp[r] = __ffma2_rn(ou, vs, crp[r]);           // (c10, c01)
+        }
     }
-    W = warp_sum_f(W);
-    su0 = warp_sum_f(su0);
-    su1 = warp_sum_f(su1);
-    sv0 = warp_sum_f(sv0);
-    sv1 = warp_sum_f(sv1);
-    vx = warp_sum_f(vx);
-    vy = warp_sum_f(vy);
-    c00 = warp_sum_f(c00);
-    c01 = warp_sum_f(c01);
-    c10 = warp_sum_f(c10);
-    c11 = warp_sum_f(c11);
-    // move the moments from the shift to the centroid: m_c = m_s - W d d'^T, d = mean - sh
-    float du0 = 0.f, du1 = 0.f, dv0 = 0.f, dv1 = 0.f;
-    if (W > 0.f) {
-        du0 = su0 / W;
-        du1 = su1 / W;
-        dv0 = sv0 / W;
-        dv1 = sv1 / W;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float w = warp_sum_f(W[r]);
+        const float su0 = warp_sum_f(su[r].x), su1 = warp_sum_f(su[r].y);
+        const float sv0 = warp_sum_f(sv[r].x), sv1 = warp_sum_f(sv[r].y);
+        float vx = warp_sum_f(vxp[r].x + vxp[r].y);
+        float vy = warp_sum_f(vyp[r].x + vyp[r].y);
+        float dot = warp_sum_f(dotp[r].x + dotp[r].y);
+        float cross = warp_sum_f(crp[r].x - crp[r].y);
+        // move the moments from the shift to the centroid: m_c = m_s - W d d'^T,
+        // d = mean - shift
+        float du0 = 0.f, du1 = 0.f, dv0 = 0.f, dv1 = 0.f;
+        if (w > 0.f) {
+            du0 = su0 / w;
+            du1 = su1 / w;
+            dv0 = sv0 / w;
+            dv1 = sv1 / w;
+        }
+        vx -= w * (du0 * du0 + du1 * du1);
+        vy -= w * (dv0 * dv0 + dv1 * dv1);
+        dot -= w * (dv0 * du0 + dv1 * du1);
+        cross -= w * (dv1 * du0 - dv0 * du1);
+        mstep_finish(A, rows[r], w, sh[r].x + du0, sh[r].y + du1, sh[r].z + dv0, sh[r].w + dv1,
+                     vx, vy, dot, cross, lane);
     }
-    vx -= W * (du0 * du0 + du1 * du1);
-    vy -= W * (dv0 * dv0 + dv1 * dv1);
-    c00 -= W * dv0 * du0;
-    c01 -= W * dv0 * du1;
-    c10 -= W * dv1 * du0;
-    c11 -= W * dv1 * du1;
-    mstep_finish(A, i, xi, yi, W, sh.x + du0, sh.y + du1, sh.z + dv0, sh.w + dv1, vx, vy, c00,
-                 c01, c10, c11, lane);
 }
 
-// Leave-one-out residual of row j (one warp); returns e_j on lane 0.
-__device__ float residual_row(const FitArgs &A, const FitSmem &S, int j, int lane)
+// Leave-one-out residuals of R rows j (one warp, lanes over i).  The blend at x_j of all
+// rows i != j is taken relative to row 0 (S.q holds q_i - q_0), so the sums stay small.
+// The loop sums over every i, the term i = j included, and that term -- computed bit for
+// bit as in the loop -- is subtracted afterwards; where the rest of the weight is smaller
+// than that term (an isolated match), the subtraction would cancel and the sum over
+// i != j is taken again exactly.
+template <int R>
+__device__ void residual_rows(const FitArgs &A, const FitSmem &S, const int *rows, int lane,
+                              float4 q0, float qs0, float &pe, float &ps)
 {
     const int n = A.n;
-    const float2 xj = S.x[j];
-    const float ra = S.qa[j], rb = S.qb[j], ru = S.qu[j], rv = S.qv[j], rs = S.qs[j];
-    float w0 = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
-#pragma unroll 4
-    for (int i = lane; i < n; i += 32) {
-        if (i == j) continue;                         // leave one out
-        const float2 xi = S.x[i];
-        const float dx = xi.x - xj.x, dy = xi.y - xj.y;
-        const float w = S.p[i] * ex2_ftz(-A.alpha2 * (dx * dx + dy * dy));
-        w0 += w;
-        a0 += w * (S.qa[i] - ra);
-        a1 += w * (S.qb[i] - rb);
-        a2 += w * (S.qu[i] - ru);
-        a3 += w * (S.qv[i] - rv);
-        a4 += w * (S.qs[i] - rs);
+    float2 nxj[R], A1[R], A2[R];
+    float W[R], As[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        nxj[r] = neg2(S.x[rows[r]]);
+        A1[r] = A2[r] = make_float2(0.f, 0.f);
+        W[r] = As[r] = 0.f;
     }
-    w0 = warp_sum_f(w0);
-    a0 = warp_sum_f(a0);
-    a1 = warp_sum_f(a1);
-    a2 = warp_sum_f(a2);
-    a3 = warp_sum_f(a3);
-    a4 = warp_sum_f(a4);
-    if (!(w0 > 0.f)) return INFINITY;
-    const float inv = 1.f / w0;
-    const float2 yh = apply_blend(ra + a0 * inv, rb + a1 * inv, ru + a2 * inv, rv + a3 * inv,
-                                  rs + a4 * inv, xj.x, xj.y);
-    const float2 yj = S.y[j];
-    const float r0 = yj.x - yh.x, r1 = yj.y - yh.y;
-    return r0 * r0 + r1 * r1;
+#pragma unroll 2
+    for (int i = lane; i < n; i += 32) {
+        const float2 xi = S.x[i];
+        const float lpi = S.lp[i];
+        const float4 qi = S.q[i];
+        const float qsi = S.qs[i];
+        const float2 qab = make_float2(qi.x, qi.y), quv = make_float2(qi.z, qi.w);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float w = gauss_w(__fadd2_rn(xi, nxj[r]), lpi);
+            const float2 w2 = make_float2(w, w);
+            W[r] += w;
+            A1[r] = __ffma2_rn(w2, qab, A1[r]);
+            A2[r] = __ffma2_rn(w2, quv, A2[r]);
+            As[r] = fmaf(w, qsi, As[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int j = rows[r];
+        float w = warp_sum_f(W[r]);
+        float b0 = warp_sum_f(A1[r].x), b1 = warp_sum_f(A1[r].y);
+        float b2 = warp_sum_f(A2[r].x), b3 = warp_sum_f(A2[r].y);
+        float b4 = warp_sum_f(As[r]);
+        // the term i = j: offset (0, 0), so its weight is exactly 2^lp_j
+        const float wjj = ex2_ftz(S.lp[j]);
+        const float4 qj = S.q[j];
+        const float qsj = S.qs[j];
+        w -= wjj;
+        b0 = fmaf(-wjj, qj.x, b0);
+        b1 = fmaf(-wjj, qj.y, b1);
+        b2 = fmaf(-wjj, qj.z, b2);
+        b3 = fmaf(-wjj, qj.w, b3);
+        b4 = fmaf(-wjj, qsj, b4);
+        if (!(w >= wjj)) {            // warp-uniform: isolated match, sum over i != j exactly
+            float w_ = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f, c4 = 0.f;
+            for (int i = lane; i < n; i += 32) {
+                if (i == j) continue;
+                const float wi = gauss_w(__fadd2_rn(S.x[i], nxj[r]), S.lp[i]);
+                const float4 qi = S.q[i];
+                w_ += wi;
+                c0 = fmaf(wi, qi.x, c0);
+                c1 = fmaf(wi, qi.y, c1);
+                c2 = fmaf(wi, qi.z, c2);
+                c3 = fmaf(wi, qi.w, c3);
+                c4 = fmaf(wi, S.qs[i], c4);
+            }
+            w = warp_sum_f(w_);
+            b0 = warp_sum_f(c0);
+            b1 = warp_sum_f(c1);
+            b2 = warp_sum_f(c2);
+            b3 = warp_sum_f(c3);
+            b4 = warp_sum_f(c4);
+        }
+        float e = INFINITY;
+        if (w > 0.f) {
+            const float inv = 1.f / w;
+            const float2 xj = __ldg(A.src + j), yj = __ldg(A.dst + j);
+            const float2 yh = apply_blend(fmaf(b0, inv, q0.x), fmaf(b1, inv, q0.y),
+                                          fmaf(b2, inv, q0.z), fmaf(b3, inv, q0.w),
+                                          fmaf(b4, inv, qs0), xj.x, xj.y);
+            const float r0 = yj.x - yh.x, r1 = yj.y - yh.y;
+            e = r0 * r0 + r1 * r1;
+        }
+        if (lane == 0) {
+            __stcg(A.e + j, e);
+            if (isfinite(e)) {
+                pe += S.p[j] * e;
+                ps += S.p[j];
+            }
+        }
+    }
 }
 
 // Block-wide sums of two floats in a fixed order: warp butterflies, then every thread
@@ -303,6 +411,9 @@ __device__ int barrier_status(const FitArgs &A, unsigned &epoch, int *s_flag, in
     return *s_flag;
 }
 
+// log2 of a posterior for the staged weights (-inf for 0: its weight 2^-inf is 0)
+__device__ __forceinline__ float log2_p(float p) { return __log2f(p); }
+
 // One fit on a group of `ncta` co-resident CTAs; `rank` is this CTA's index in the group.
 __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
 {
@@ -314,17 +425,19 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
     __shared__ int s_flag;
     unsigned epoch = 0;
 
-    // stage the matches and the initial weights; every CTA checks every input
+    // stage the matches (scaled) and the initial weights; every CTA checks every input
     int bad = 0;
     float p0sum = 0.f;
     for (int j = threadIdx.x; j < n; j += kFitThreads) {
         const float2 x = A.src[j], y = A.dst[j];
-        S.x[j] = x;
-        S.y[j] = y;
+        S.x[j] = make_float2(A.k * x.x, A.k * x.y);
+        S.y[j] = make_float2(A.k * y.x, A.k * y.y);
         const float p = A.p0 ? A.p0[j] : 1.f;
         S.p[j] = p;
+        S.lp[j] = A.p0 ? log2_p(p) : 0.f;
         p0sum += p;
-        bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(y.x) && isfinite(y.y) && isfinite(p));
+        bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(y.x) && isfinite(y.y) && isfinite(p) &&
+                 p >= 0.f);
     }
     bad = __syncthreads_or(bad);
     if (bad) {
@@ -337,28 +450,45 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
     float gamma = 0.5f;
     if (A.p0) gamma = fminf(fmaxf(block_sum2(p0sum, 0.f, red).x / n, 0.05f), 0.95f);
 
+    // this warp's M-step rows i = gwarp, gwarp + nwarps, ..., two at a time
+    auto mstep_all = [&](bool first) {
+        int i = gwarp;
+        for (; i + nwarps < n; i += 2 * nwarps) {
+            const int rows[2] = {i, i + nwarps};
+            mstep_rows<2>(A, S, rows, lane, first);
+        }
+        if (i < n) {
+            const int rows[1] = {i};
+            mstep_rows<1>(A, S, rows, lane, first);
+        }
+    };
     // residuals of this CTA's rows and its partial sums, then the barrier
     auto residuals_and_barrier = [&]() -> int {
+        const float4 q0 = __ldcg(reinterpret_cast<const float4 *>(A.q_out));
+        const float qs0 = __ldcg(A.q_out + 4);
         for (int i = threadIdx.x; i < n; i += kFitThreads) {
             const float4 r0 = __ldcg(reinterpret_cast<const float4 *>(A.q_out + 8 * (size_t)i));
             const float r4 = __ldcg(A.q_out + 8 * (size_t)i + 4);
-            S.qa[i] = r0.x;
-            S.qb[i] = r0.y;
-            S.qu[i] = r0.z;
-            S.qv[i] = r0.w;
-            S.qs[i] = r4;
+            S.q[i] = make_float4(r0.x - q0.x, r0.y - q0.y, r0.z - q0.z, r0.w - q0.w);
+            S.qs[i] = r4 - qs0;
         }
         __syncthreads();
         float pe = 0.f, ps = 0.f;
-        for (int j = gwarp; j < n; j += nwarps) {
-            const float e = residual_row(A, S, j, lane);
-            if (lane == 0) {
-                __stcg(A.e + j, e);
-                if (isfinite(e)) {
-                    pe += S.p[j] * e;
-                    ps += S.p[j];
-                }
-            }
+        int j = gwarp;
+        for (; j + 3 * nwarps < n; j += 4 * nwarps) {
+            const int rows[4] = {j, j + nwarps, j + 2 * nwarps, j + 3 * nwarps};
+            residual_rows<4>(A, S, rows, lane, q0, qs0, pe, ps);
+        }
+        const int rem = j < n ? (n - 1 - j) / nwarps + 1 : 0;     // 0..3 rows left
+        if (rem == 3) {
+            const int rows[3] = {j, j + nwarps, j + 2 * nwarps};
+            residual_rows<3>(A, S, rows, lane, q0, qs0, pe, ps);
+        } else if (rem == 2) {
+            const int rows[2] = {j, j + nwarps};
+            residual_rows<2>(A, S, rows, lane, q0, qs0, pe, ps);
+        } else if (rem == 1) {
+            const int rows[1] = {j};
+            residual_rows<1>(A, S, rows, lane, q0, qs0, pe, ps);
         }
         const float2 t = block_sum2(lane == 0 ? pe : 0.f, lane == 0 ? ps : 0.f, red);
         if (threadIdx.x == 0) __stcg(reinterpret_cast<float2 *>(A.partials) + rank, t);
@@ -388,7 +518,7 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
 
     // step 0
     float sigma2 = A.sigma2_floor;
-    for (int i = gwarp; i < n; i += nwarps) mstep_row(A, S, i, lane, true);
+    mstep_all(true);
     int st = barrier_status(A, epoch, &s_flag, ncta);
     if (st < EMDQ_EDEGENERATE) st = residuals_and_barrier();
     if (st < EMDQ_EDEGENERATE) sigma2 = load_e_and_sigma2();
@@ -411,6 +541,7 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
                 const float pn = gamma * G / (gamma * G + outl);
                 dpmax = fmaxf(dpmax, fabsf(pn - S.p[j]));
                 S.p[j] = pn;
+                S.lp[j] = log2_p(pn);
                 psum += pn;
             }
         }
@@ -428,7 +559,7 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
         __syncthreads();
         const float gamma_next = fminf(fmaxf(ptot / n, 0.05f), 0.95f);
         // M-step with the new weights, then residuals and sigma^2
-        for (int i = gwarp; i < n; i += nwarps) mstep_row(A, S, i, lane, false);
+        mstep_all(false);
         st = barrier_status(A, epoch, &s_flag, ncta);
         if (st < EMDQ_EDEGENERATE) st = residuals_and_barrier();
         if (st < EMDQ_EDEGENERATE) sigma2 = load_e_and_sigma2();
@@ -499,7 +630,7 @@ constexpr FitLayout fit_layout(int n)
                      al256(sizeof(float) * (size_t)n) + al256(sizeof(float4) * (size_t)n) +
                          al256(sizeof(double) * 2 * kFitMaxGrid) + 256};
 }
-size_t fit_smem_bytes(int n) { return (size_t)n * 40; }
+size_t fit_smem_bytes(int n) { return (size_t)n * kFitSmemPerMatch; }
 }  // namespace
 
 extern "C" int emdq_fit_max_n(void) { return kFitMaxN; }
@@ -537,7 +668,7 @@ extern "C" emdq_status emdq_fit(const float *src, const float *dst, int n, int f
         std::lock_guard<std::mutex> g(mu);
         if (attr_set_dev != D.device) {
             if (cudaFuncSetAttribute(emdq_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(kFitMaxN * 40)) != cudaSuccess)
+                                     (int)fit_smem_bytes(kFitMaxN)) != cudaSuccess)
                 return EMDQ_ECUDA;
             attr_set_dev = D.device;
         }
@@ -561,7 +692,8 @@ extern "C" emdq_status emdq_fit(const float *src, const float *dst, int n, int f
     A.dst = reinterpret_cast<const float2 *>(dst);
     A.n = n;
     const double alpha = P.alpha > 0.f ? P.alpha : emdq_alpha_for_frame(frame_w, frame_h);
-    A.alpha2 = static_cast<float>(alpha * 1.4426950408889634074);
+    A.k = static_cast<float>(std::sqrt(alpha * 1.4426950408889634074));
+    A.inv_k = 1.f / A.k;
     A.inv_area = 1.f / (static_cast<float>(frame_w) * static_cast<float>(frame_h));
     A.max_iters = P.max_iters;
     A.tol = P.tol_p;
@@ -647,7 +779,7 @@ extern "C" emdq_status emdq_fit_batch(const emdq_fit_problem *problems, int coun
         std::lock_guard<std::mutex> g(mu);
         if (attr_set_dev != D.device) {
             if (cudaFuncSetAttribute(emdq_fit_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(kFitMaxN * 40)) != cudaSuccess)
+                                     (int)fit_smem_bytes(kFitMaxN)) != cudaSuccess)
                 return EMDQ_ECUDA;
             attr_set_dev = D.device;
         }
@@ -667,7 +799,7 @@ extern "C" emdq_status emdq_fit_batch(const emdq_fit_problem *problems, int coun
     if (cudaMemsetAsync(ws, 0, 256 * (size_t)count, st) != cudaSuccess) return EMDQ_ECUDA;
     FitBatch B;
     size_t off = 256 * (size_t)count;
-    const double two_log2e = 1.4426950408889634074;
+    const double log2e = 1.4426950408889634074;
     for (int b = 0; b < count; ++b) {
         const emdq_fit_problem &q = problems[b];
         FitArgs &A = B.a[b];
@@ -675,7 +807,8 @@ extern "C" emdq_status emdq_fit_batch(const emdq_fit_problem *problems, int coun
         A.dst = reinterpret_cast<const float2 *>(q.dst);
         A.n = q.n;
         const double alpha = P.alpha > 0.f ? P.alpha : emdq_alpha_for_frame(q.frame_w, q.frame_h);
-        A.alpha2 = static_cast<float>(alpha * two_log2e);
+        A.k = static_cast<float>(std::sqrt(alpha * log2e));
+        A.inv_k = 1.f / A.k;
         A.inv_area = 1.f / (static_cast<float>(q.frame_w) * static_cast<float>(q.frame_h));
         A.max_iters = P.max_iters;
         A.tol = P.tol_p;
