@@ -14,6 +14,9 @@
 //
 // field_tc_prep_kernel writes Ex (K-major rows of pixels x) and G (K-major rows of
 // pixels y, six channel planes) as BF16 into the workspace, zero-padded to whole tiles.
+// Its K columns are only the matches of nonzero weight c_i (the EM outliers have c = 0
+// and add exactly nothing), so the GEMM's K shrinks by the outlier fraction; the column
+// count goes to the GEMM through device memory.
 // field_tc_kernel: persistent, one CTA per SM looping over 128 x 32 pixel tiles, warp
 // specialised.  Warp 0 (one thread) streams 64-match slices of Ex (128 rows) and of G
 // (6 x 32 rows, one 3-D box) through a 4-stage shared-memory ring with TMA; warp 1 (one
@@ -73,26 +76,67 @@ __host__ __device__ inline TcGeom tc_geom(int n, int gw, int gh)
     return g;
 }
 
+// Columns of the GEMM: the matches with c_i != 0 in index order (a match of weight 0 adds
+// exactly nothing to any of the six sums), found by every block with the same block scan.
+// Returns their number m; col(k) = the k-th such match.  Above kCompactMax matches the
+// columns are all matches, in order.
+constexpr int kCompactMax = 8192;
+
+__device__ int compact_columns(const float *__restrict__ c, int n, int *s_idx)
+{
+    __shared__ int s_warp[kPrepThreads / 32];
+    if (n > kCompactMax) return -1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int base = 0;
+    for (int k0 = 0; k0 < n; k0 += kPrepThreads) {
+        const int k = k0 + threadIdx.x;
+        const bool in = k < n && c[k] != 0.f;
+        const unsigned b = __ballot_sync(0xffffffffu, in);
+        if (lane == 0) s_warp[warp] = __popc(b);
+        __syncthreads();
+        int off = base, tot = 0;
+#pragma unroll
+        for (int w = 0; w < kPrepThreads / 32; ++w) {
+            const int cnt = s_warp[w];
+            off += w < warp ? cnt : 0;
+            tot += cnt;
+        }
+        if (in) s_idx[off + __popc(b & ((1u << lane) - 1u))] = k;
+        base += tot;
+        __syncthreads();
+    }
+    return base;
+}
+
 __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
     const float *__restrict__ q, const float *__restrict__ c, const float2 *__restrict__ src,
     int n, int kp, int gx0, int gy0, int gw, int gh, int wp, int hp, float alpha,
     float *__restrict__ ref_out, __nv_bfloat162 *__restrict__ A, __nv_bfloat162 *__restrict__ B,
-    int a_blocks)
+    int a_blocks, int *__restrict__ kcount)
 {
+    __shared__ int s_idx[kCompactMax];
     const int half = kp / 2;
+    const int mc = compact_columns(c, n, s_idx);
+    const bool compact = mc >= 0;
+    const int m = compact ? mc : n;
+    // columns written: m rounded up to whole 64-match slices (at least one), zeros past m
+    const int kc = m > 0 ? (m + kTcK - 1) / kTcK * kTcK : kTcK;
+    const int halfc = kc / 2;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *kcount = kc;
+    auto col = [&](int k) { return compact ? s_idx[k] : k; };
     if ((int)blockIdx.x < a_blocks) {
         const int r0 = blockIdx.x * kPrepRows;
-        for (int k2 = threadIdx.x; k2 < half; k2 += kPrepThreads) {
+        for (int k2 = threadIdx.x; k2 < halfc; k2 += kPrepThreads) {
             const int k0 = 2 * k2, k1 = k0 + 1;
-            const float x0 = k0 < n ? src[k0].x : 0.f, x1 = k1 < n ? src[k1].x : 0.f;
+            const float x0 = k0 < m ? src[col(k0)].x : 0.f, x1 = k1 < m ? src[col(k1)].x : 0.f;
             for (int r = 0; r < kPrepRows; ++r) {
                 const int px = r0 + r;
                 if (px >= wp) break;
                 const float p = static_cast<float>(gx0 + px);
                 const bool row = px < gw;
                 const float d0 = p - x0, d1 = p - x1;
-                const float e0 = (row && k0 < n) ? expf(-alpha * d0 * d0) : 0.f;
-                const float e1 = (row && k1 < n) ? expf(-alpha * d1 * d1) : 0.f;
+                const float e0 = (row && k0 < m) ? expf(-alpha * d0 * d0) : 0.f;
+                const float e1 = (row && k1 < m) ? expf(-alpha * d1 * d1) : 0.f;
                 A[(size_t)px * half + k2] = __floats2bfloat162_rn(e0, e1);
             }
         }
@@ -103,15 +147,16 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
         reference_row(q, c, n, red, rf);      // same bits in every block
         if (blockIdx.x == a_blocks && threadIdx.x == 0)
             for (int k = 0; k < 6; ++k) ref_out[k] = rf[k];
-        for (int k2 = threadIdx.x; k2 < half; k2 += kPrepThreads) {
+        for (int k2 = threadIdx.x; k2 < halfc; k2 += kPrepThreads) {
             const int k0 = 2 * k2;
             float y[2] = {0.f, 0.f}, cw[2] = {0.f, 0.f}, cq[2][5];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                const int k = k0 + u;
+                const int kk = k0 + u;
 #pragma unroll
                 for (int ch = 0; ch < 5; ++ch) cq[u][ch] = 0.f;
-                if (k < n) {
+                if (kk < m) {
+                    const int k = col(kk);
                     y[u] = src[k].y;
                     cw[u] = c[k];
                     const float4 r = *reinterpret_cast<const float4 *>(q + 8 * (size_t)k);
@@ -144,10 +189,14 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
 // CH = 0: write the displacement field; CH = 1 or 3: blend the frame into the canvas.
 template <int CH>
 __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(
-    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int nchunks,
-    int ntx, int ntiles, int gx0, int gy0, int gw, int gh, const float *__restrict__ ref,
-    float2 *__restrict__ disp, int *__restrict__ err, MosaicArgs mos)
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    const int *__restrict__ kcount, int ntx, int ntiles, int gx0, int gy0, int gw, int gh,
+    const float *__restrict__ ref, float2 *__restrict__ disp, int *__restrict__ err,
+    MosaicArgs mos)
 {
+    // 64-match slices along K: the prep kernel's column count (the matches of nonzero
+    // weight), a whole number of slices, at least one
+    const int nchunks = *kcount / kTcK;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -429,24 +478,24 @@ emdq_status field_tc_launch(const float *q, const float *c, const float *src, in
         }
     }
     if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return EMDQ_ECUDA;
+    int *kcount = err + 1;                  // written by the prep kernel, read by the GEMM
     const int a_blocks = g.wp / kPrepRows;
     const int b_blocks = g.hp / kPrepRows;
     field_tc_prep_kernel<<<a_blocks + b_blocks, kPrepThreads, 0, st>>>(
         q, c, reinterpret_cast<const float2 *>(src), n, g.kp, gx0, gy0, gw, gh, g.wp, g.hp, alpha,
-        ref, A, B, a_blocks);
+        ref, A, B, a_blocks, kcount);
     if (cudaGetLastError() != cudaSuccess) return EMDQ_ECUDA;
     const int ntx = g.wp / kTcM, ntiles = ntx * (g.hp / kTcPY);
     const int grid = ntiles < D.sms ? ntiles : D.sms;       // persistent: one CTA per SM
     const MosaicArgs none{};
-    const int nch = g.kp / kTcK;
     if (variant == 0)
-        field_tc_kernel<0><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, nch, ntx, ntiles, gx0,
+        field_tc_kernel<0><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, kcount, ntx, ntiles, gx0,
                                                                    gy0, gw, gh, ref, disp, err, none);
     else if (variant == 1)
-        field_tc_kernel<1><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, nch, ntx, ntiles, gx0,
+        field_tc_kernel<1><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, kcount, ntx, ntiles, gx0,
                                                                    gy0, gw, gh, ref, disp, err, *mos);
     else
-        field_tc_kernel<3><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, nch, ntx, ntiles, gx0,
+        field_tc_kernel<3><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, kcount, ntx, ntiles, gx0,
                                                                    gy0, gw, gh, ref, disp, err, *mos);
     return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }

@@ -111,3 +111,42 @@ def test_field_small_and_ragged_match_counts(emdq, orc, prec, n):
         got = _gpu_field(emdq, q8, c, src, grid, np.float32(alpha), prec)
         want = orc.field(*_oracle_inputs(q8, c, src), grid, alpha)
         assert np.abs(got - want).max() <= TOL[prec], (grid, np.abs(got - want).max())
+
+
+@pytest.mark.parametrize('prec', PRECISIONS, ids=['fp32', 'bf16'])
+@pytest.mark.parametrize('m', [1, 63, 64, 65, 128, 129])
+def test_field_sparse_weights(emdq, orc, prec, m):
+    """Only m of 300 matches carry weight (scattered, so the nonzero columns the tensor path
+    keeps land on either side of its 64-match slices); the zero-weight ones must not count."""
+    rng = np.random.default_rng(200 + m)
+    n = 300
+    src, q8 = random_rows(rng, n, 640, 480)
+    c = np.zeros(n)
+    c[rng.choice(n, m, replace=False)] = rng.uniform(0.5, 1.0, m)
+    alpha = orc.alpha_for_frame(640, 480)
+    grid = (-3, 11, 200, 45)
+    got = _gpu_field(emdq, q8, c, src, grid, np.float32(alpha), prec)
+    want = orc.field(*_oracle_inputs(q8, c, src), grid, alpha)
+    ok = np.isfinite(want)
+    assert np.array_equal(np.isfinite(got), ok)
+    assert np.abs(got[ok] - want[ok]).max() <= TOL[prec]
+
+
+@pytest.mark.parametrize('prec', PRECISIONS, ids=['fp32', 'bf16'])
+def test_field_many_matches_sampled(emdq, orc, prec):
+    """n = 9000 (beyond the tensor path's 8192-match column compaction: all columns are
+    kept), 30 % zero weights; 2048 sampled pixels."""
+    rng = np.random.default_rng(9000)
+    n = 9000
+    src, q8 = random_rows(rng, n, 1280, 1024)
+    c = np.where(rng.uniform(0, 1, n) < 0.7, rng.uniform(0.5, 1, n), 0.0)
+    grid = (0, 0, 1280, 256)
+    alpha = orc.alpha_for_frame(1280, 1024)
+    got = _gpu_field(emdq, q8, c, src, grid, np.float32(alpha), prec)
+    iy = rng.integers(0, grid[3], 2048)
+    ix = rng.integers(0, grid[2], 2048)
+    pts = np.stack([grid[0] + ix, grid[1] + iy], 1).astype(np.float64)
+    want = orc.field_points(*_oracle_inputs(q8, c, src), pts, alpha)
+    err = np.abs(got[iy, ix] - want).max()
+    print(f'prec {prec}: n=9000 sampled max error {err:.3e} px')
+    assert err <= TOL[prec]
