@@ -21,9 +21,10 @@
 // specialised.  Warp 0 (one thread) streams 64-match slices of Ex (128 rows) and of G
 // (6 x 32 rows, one 3-D box) through a 4-stage shared-memory ring with TMA; warp 1 (one
 // thread) issues tcgen05.mma (M = 128 pixels x, N = 192 = 6 channels x 32 pixels y,
-// K = 16) into one of two TMEM accumulators; warps 2-5 read the other accumulator back
-// with tcgen05.ld (thread = pixel x = TMEM lane) and evaluate Eq. 1, so the epilogue of a
-// tile overlaps the MMAs of the next.
+// K = 16) into one of two TMEM accumulators; the epilogue warps read the other
+// accumulator back with tcgen05.ld (thread = pixel x = TMEM lane; for the field two warps
+// per lane quadrant, each taking half of the 32 pixel rows) and evaluate Eq. 1, so the
+// epilogue of a tile overlaps the MMAs of the next.
 // The fused variant (CH = 1 or 3) goes on from the displacement to the mosaic update of
 // the same pixel (the stand-alone warp's per-pixel code), so the field never visits HBM.
 #include <mutex>
@@ -44,7 +45,11 @@ constexpr int kTcCh = 6;                 // dr_w, dr_z, dd_x, dd_y, ds, weight
 constexpr int kTcN = kTcCh * kTcPY;      // MMA N = 192
 constexpr int kTcK = 64;                 // matches per stage: one 128-byte swizzle row
 constexpr int kTcStages = 4;
-constexpr int kTcThreads = 192;        // producer warp, MMA warp, 4 epilogue warps
+// Epilogue warps: two per TMEM lane quadrant for the field (each half of the pixel rows),
+// one for the fused field + warp, whose larger per-pixel state would not fit the register
+// file twice.  Threads: producer warp, MMA warp, epilogue warps.
+constexpr int tc_epi_warps(int ch) { return ch == 0 ? 8 : 4; }
+constexpr int tc_threads(int ch) { return 64 + 32 * tc_epi_warps(ch); }
 constexpr uint32_t kTcABytes = kTcM * kTcK * 2;
 constexpr uint32_t kTcBBytes = kTcN * kTcK * 2;
 constexpr uint32_t kTcStageBytes = kTcABytes + kTcBBytes;
@@ -87,25 +92,33 @@ __device__ int compact_columns(const float *__restrict__ c, int n, int *s_idx)
     __shared__ int s_warp[kPrepThreads / 32];
     if (n > kCompactMax) return -1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int base = 0;
-    for (int k0 = 0; k0 < n; k0 += kPrepThreads) {
-        const int k = k0 + threadIdx.x;
-        const bool in = k < n && c[k] != 0.f;
-        const unsigned b = __ballot_sync(0xffffffffu, in);
-        if (lane == 0) s_warp[warp] = __popc(b);
-        __syncthreads();
-        int off = base, tot = 0;
-#pragma unroll
-        for (int w = 0; w < kPrepThreads / 32; ++w) {
-            const int cnt = s_warp[w];
-            off += w < warp ? cnt : 0;
-            tot += cnt;
-        }
-        if (in) s_idx[off + __popc(b & ((1u << lane) - 1u))] = k;
-        base += tot;
-        __syncthreads();
+    // thread t owns matches [t per, (t + 1) per): one flag bit each (per <= 32)
+    const int per = (n + kPrepThreads - 1) / kPrepThreads;
+    const int k0 = threadIdx.x * per;
+    unsigned mask = 0;
+    for (int u = 0; u < per; ++u) {
+        const int k = k0 + u;
+        if (k < n && c[k] != 0.f) mask |= 1u << u;
     }
-    return base;
+    const int cnt = __popc(mask);
+    int incl = cnt;                                   // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    int off = incl - cnt, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kPrepThreads / 32; ++w) {
+        const int cw = s_warp[w];
+        off += w < warp ? cw : 0;
+        tot += cw;
+    }
+    for (; mask; mask &= mask - 1) s_idx[off++] = k0 + __ffs(mask) - 1;
+    __syncthreads();
+    return tot;
 }
 
 __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
@@ -188,7 +201,7 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
 
 // CH = 0: write the displacement field; CH = 1 or 3: blend the frame into the canvas.
 template <int CH>
-__global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(
+__global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
     const int *__restrict__ kcount, int ntx, int ntiles, int gx0, int gy0, int gw, int gh,
     const float *__restrict__ ref, float2 *__restrict__ disp, int *__restrict__ err,
@@ -203,7 +216,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + kTcStages * kTcStageBytes);
     uint64_t *empty = full + kTcStages;
     uint64_t *acc_full = empty + kTcStages;     // [2] MMA -> epilogue
-    uint64_t *acc_empty = acc_full + 2;         // [2] epilogue -> MMA (4 warps arrive)
+    uint64_t *acc_empty = acc_full + 2;         // [2] epilogue -> MMA (every epilogue warp arrives)
     uint64_t *done = acc_empty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -218,7 +231,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(
         }
         for (int a = 0; a < 2; ++a) {
             tc::mbar_init(acc_full + a, 1);
-            tc::mbar_init(acc_empty + a, 4);
+            tc::mbar_init(acc_empty + a, tc_epi_warps(CH));
         }
         tc::mbar_init(done, 1);
         *abort_flag = 0;
@@ -296,8 +309,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(
             tc::mma_commit(done);   // tracks every MMA issued above, also after an abort
         }
     } else {
-        // epilogue warps 2-5: TMEM lane quadrant q = warp % 4, thread = pixel x of the tile
+        // epilogue warps: TMEM lane quadrant q = warp % 4 (the lanes a warp may access),
+        // thread = pixel x of the tile; with 8 of them warps 2-5 take pixel rows 0-15 and
+        // warps 6-9 rows 16-31 (groups of 8 rows)
+        constexpr int kGroups = kTcPY / 8 / (tc_epi_warps(CH) / 4);
         const int q = warp & 3;
+        const int g0 = ((warp - 2) >> 2) * kGroups;
         const float ra = ref[0], rb = ref[1], ru = ref[2], rv = ref[3], rs = ref[4];
         int it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -313,12 +330,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(
             const float px = static_cast<float>(gx0 + x);
             const uint32_t lane_base = tmem + a * kTcAccCols + (static_cast<uint32_t>(q * 32) << 16);
 #pragma unroll 1
-            for (int g = 0; g < kTcPY / 8; ++g) {
+            for (int g = g0; g < g0 + kGroups; ++g) {
                 float F[kTcCh][8];
 #pragma unroll
                 for (int ch = 0; ch < kTcCh; ++ch) tc::tmem_ld_x8(lane_base + ch * kTcPY + g * 8, F[ch]);
                 tc::tmem_wait_ld();
-                if (g == kTcPY / 8 - 1) {
+                if (g == g0 + kGroups - 1) {
                     // the accumulator has been read: hand it back to the MMA warp
                     tc::fence_before_sync();
                     __syncwarp();
@@ -489,13 +506,13 @@ emdq_status field_tc_launch(const float *q, const float *c, const float *src, in
     const int grid = ntiles < D.sms ? ntiles : D.sms;       // persistent: one CTA per SM
     const MosaicArgs none{};
     if (variant == 0)
-        field_tc_kernel<0><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, kcount, ntx, ntiles, gx0,
+        field_tc_kernel<0><<<grid, tc_threads(0), kTcSmemBytes, st>>>(tmA, tmB, kcount, ntx, ntiles, gx0,
                                                                    gy0, gw, gh, ref, disp, err, none);
     else if (variant == 1)
-        field_tc_kernel<1><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, kcount, ntx, ntiles, gx0,
+        field_tc_kernel<1><<<grid, tc_threads(1), kTcSmemBytes, st>>>(tmA, tmB, kcount, ntx, ntiles, gx0,
                                                                    gy0, gw, gh, ref, disp, err, *mos);
     else
-        field_tc_kernel<3><<<grid, kTcThreads, kTcSmemBytes, st>>>(tmA, tmB, kcount, ntx, ntiles, gx0,
+        field_tc_kernel<3><<<grid, tc_threads(3), kTcSmemBytes, st>>>(tmA, tmB, kcount, ntx, ntiles, gx0,
                                                                    gy0, gw, gh, ref, disp, err, *mos);
     return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }
