@@ -62,15 +62,16 @@ def parse_args():
     ap.add_argument('--no-plain', action='store_true',
                     help='skip the plain FP32 GPU comparison (per-frame emdq_fit + FP32 per-pixel '
                          'field + warp, no warm start, no batching) measured on 10 frames')
-    ap.add_argument('--batch', type=int, default=16,
+    ap.add_argument('--batch', type=int, default=50,
                     help='frames whose EM fits share one launch (1: one emdq_fit per frame)')
     ap.add_argument('--no-warm', action='store_true',
                     help='plain EM (default: learned warm start when its parameters ship)')
     ap.add_argument('--fused', action='store_true',
                     help='BF16 field and warp in one emdq_mosaic call (default: emdq_field + mosaic_warp)')
-    ap.add_argument('--no-overlap', action='store_true',
-                    help='one stream (default: the next batch of fits runs on a second stream '
-                         'while the current batch is blended)')
+    ap.add_argument('--overlap', action='store_true',
+                    help='run the next batch of fits on a second stream while the current batch is '
+                         'blended (default: one stream; the cooperative fit launch occupies every '
+                         'SM, so the two streams mostly serialise anyway)')
     return ap.parse_args()
 
 
@@ -244,7 +245,7 @@ def run_gpu(args, ws, rank, local):
 
     fused = prec == emdq.BF16 and args.fused
     B = max(1, min(args.batch, 64))
-    overlap = not args.no_overlap
+    overlap = args.overlap
     nbuf = 2 if overlap else 1            # fit outputs of two batches in flight
     fit_outs_all = [[dict(q=torch.empty((n, 8), device=dev), c=torch.empty(n, device=dev),
                           p=torch.empty(n, device=dev),

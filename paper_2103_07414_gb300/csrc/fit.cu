@@ -127,10 +127,10 @@ __device__ __forceinline__ float gauss_w(float2 d, float lp)
 // Eqs. 18-20 for row i from the weight W, the weighted centroids relative to (x_i, y_i)
 // in scaled coordinates, and the centred moments (scaled; the factor k^2 cancels in every
 // ratio): rotation (2-D closed form of the SVD solution), scale (norm ratio), translation.
-// Lane 0 writes the q row and the centroid.
+// The calling lane writes the q row and the centroid.
 __device__ __forceinline__ void mstep_finish(const FitArgs &A, int i, float W, float ab0,
                                              float ab1, float bb0, float bb1, float vx, float vy,
-                                             float dot, float cross, int lane)
+                                             float dot, float cross)
 {
     // Eq. 18 in 2-D: the rotation angle th maximising tr(R^T C_t C_0^T) has direction
     // (a, b) = (c00 + c11, c10 - c01); its half angle (the DQ real part) is the direction
@@ -156,7 +156,6 @@ __device__ __forceinline__ void mstep_finish(const FitArgs &A, int i, float W, f
     const float ty = yg1 / sc - (st * xg0 + ct * xg1);
     const bool ok = W > 0.f && isfinite(W) && vx > 0.f && isfinite(sc) && isfinite(tx) &&
                     isfinite(ty);
-    if (lane != 0) return;
     float row[5] = {1.f, 0.f, 0.f, 0.f, 1.f};
     if (ok) {
         row[0] = c;
@@ -262,34 +261,48 @@ __device__ void mstep_rows(const FitArgs &A, const FitSmem &S, const int *rows, 
             crp[r] = __ffma2_rn(ou, vs, crp[r]);           // (c10, c01)
         }
     }
+    // every lane receives every row's sums; lane r then finishes row r, so the divisions
+    // and square roots of the closed form are issued once for all R rows
+    float w = 0.f, su0 = 0.f, su1 = 0.f, sv0 = 0.f, sv1 = 0.f, vx = 0.f, vy = 0.f, dot = 0.f,
+          cross = 0.f;
+    float4 shr = sh[0];
+    int i = rows[0];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const float w = warp_sum_f(W[r]);
-        const float su0 = warp_sum_f(su[r].x), su1 = warp_sum_f(su[r].y);
-        const float sv0 = warp_sum_f(sv[r].x), sv1 = warp_sum_f(sv[r].y);
-        float vx = warp_sum_f(vxp[r].x + vxp[r].y);
-        float vy = warp_sum_f(vyp[r].x + vyp[r].y);
-        float dot = warp_sum_f(dotp[r].x + dotp[r].y);
-        float cross = warp_sum_f(crp[r].x - crp[r].y);
-        // move the moments from the shift to the centroid: m_c = m_s - W d d'^T,
-        // d = mean - shift
-        float du0 = 0.f, du1 = 0.f, dv0 = 0.f, dv1 = 0.f;
-        if (w > 0.f) {
-            du0 = su0 / w;
-            du1 = su1 / w;
-            dv0 = sv0 / w;
-            dv1 = sv1 / w;
+        const float w_ = warp_sum_f(W[r]);
+        const float su0_ = warp_sum_f(su[r].x), su1_ = warp_sum_f(su[r].y);
+        const float sv0_ = warp_sum_f(sv[r].x), sv1_ = warp_sum_f(sv[r].y);
+        const float vx_ = warp_sum_f(vxp[r].x + vxp[r].y);
+        const float vy_ = warp_sum_f(vyp[r].x + vyp[r].y);
+        const float dot_ = warp_sum_f(dotp[r].x + dotp[r].y);
+        const float cross_ = warp_sum_f(crp[r].x - crp[r].y);
+        if (r == 0 || lane == r) {
+            w = w_; su0 = su0_; su1 = su1_; sv0 = sv0_; sv1 = sv1_;
+            vx = vx_; vy = vy_; dot = dot_; cross = cross_;
+            shr = sh[r];
+            i = rows[r];
         }
-        vx -= w * (du0 * du0 + du1 * du1);
-        vy -= w * (dv0 * dv0 + dv1 * dv1);
-        dot -= w * (dv0 * du0 + dv1 * du1);
-        cross -= w * (dv1 * du0 - dv0 * du1);
-        mstep_finish(A, rows[r], w, sh[r].x + du0, sh[r].y + du1, sh[r].z + dv0, sh[r].w + dv1,
-                     vx, vy, dot, cross, lane);
     }
+    if (lane >= R) return;
+    // move the moments from the shift to the centroid: m_c = m_s - W d d'^T,
+    // d = mean - shift
+    float du0 = 0.f, du1 = 0.f, dv0 = 0.f, dv1 = 0.f;
+    if (w > 0.f) {
+        const float inv = 1.f / w;
+        du0 = su0 * inv;
+        du1 = su1 * inv;
+        dv0 = sv0 * inv;
+        dv1 = sv1 * inv;
+    }
+    vx -= w * (du0 * du0 + du1 * du1);
+    vy -= w * (dv0 * dv0 + dv1 * dv1);
+    dot -= w * (dv0 * du0 + dv1 * du1);
+    cross -= w * (dv1 * du0 - dv0 * du1);
+    mstep_finish(A, i, w, shr.x + du0, shr.y + du1, shr.z + dv0, shr.w + dv1, vx, vy, dot, cross);
 }
 
-// Leave-one-out residuals of R rows j (one warp, lanes over i).  The blend at x_j of all
+// Leave-one-out residuals of R rows j (one warp, lanes over i; lane r < R accumulates
+// row r's p e and p into pe, ps).  The blend at x_j of all
 // rows i != j is taken relative to row 0 (S.q holds q_i - q_0), so the sums stay small.
 // The loop sums over every i, the term i = j included, and that term -- computed bit for
 // bit as in the loop -- is subtracted afterwards; where the rest of the weight is smaller
@@ -325,6 +338,9 @@ __device__ void residual_rows(const FitArgs &A, const FitSmem &S, const int *row
             As[r] = fmaf(w, qsi, As[r]);
         }
     }
+    // every lane receives every row's sums; lane r then evaluates row r's residual
+    float wl = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f, c4 = 0.f;
+    int jl = rows[0];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int j = rows[r];
@@ -343,42 +359,45 @@ __device__ void residual_rows(const FitArgs &A, const FitSmem &S, const int *row
         b3 = fmaf(-wjj, qj.w, b3);
         b4 = fmaf(-wjj, qsj, b4);
         if (!(w >= wjj)) {            // warp-uniform: isolated match, sum over i != j exactly
-            float w_ = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f, c4 = 0.f;
+            float w_ = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f, d4 = 0.f;
             for (int i = lane; i < n; i += 32) {
                 if (i == j) continue;
                 const float wi = gauss_w(__fadd2_rn(S.x[i], nxj[r]), S.lp[i]);
                 const float4 qi = S.q[i];
                 w_ += wi;
-                c0 = fmaf(wi, qi.x, c0);
-                c1 = fmaf(wi, qi.y, c1);
-                c2 = fmaf(wi, qi.z, c2);
-                c3 = fmaf(wi, qi.w, c3);
-                c4 = fmaf(wi, S.qs[i], c4);
+                d0 = fmaf(wi, qi.x, d0);
+                d1 = fmaf(wi, qi.y, d1);
+                d2 = fmaf(wi, qi.z, d2);
+                d3 = fmaf(wi, qi.w, d3);
+                d4 = fmaf(wi, S.qs[i], d4);
             }
             w = warp_sum_f(w_);
-            b0 = warp_sum_f(c0);
-            b1 = warp_sum_f(c1);
-            b2 = warp_sum_f(c2);
-            b3 = warp_sum_f(c3);
-            b4 = warp_sum_f(c4);
+            b0 = warp_sum_f(d0);
+            b1 = warp_sum_f(d1);
+            b2 = warp_sum_f(d2);
+            b3 = warp_sum_f(d3);
+            b4 = warp_sum_f(d4);
         }
-        float e = INFINITY;
-        if (w > 0.f) {
-            const float inv = 1.f / w;
-            const float2 xj = __ldg(A.src + j), yj = __ldg(A.dst + j);
-            const float2 yh = apply_blend(fmaf(b0, inv, q0.x), fmaf(b1, inv, q0.y),
-                                          fmaf(b2, inv, q0.z), fmaf(b3, inv, q0.w),
-                                          fmaf(b4, inv, qs0), xj.x, xj.y);
-            const float r0 = yj.x - yh.x, r1 = yj.y - yh.y;
-            e = r0 * r0 + r1 * r1;
+        if (r == 0 || lane == r) {
+            wl = w; c0 = b0; c1 = b1; c2 = b2; c3 = b3; c4 = b4;
+            jl = j;
         }
-        if (lane == 0) {
-            __stcg(A.e + j, e);
-            if (isfinite(e)) {
-                pe += S.p[j] * e;
-                ps += S.p[j];
-            }
-        }
+    }
+    if (lane >= R) return;
+    float e = INFINITY;
+    if (wl > 0.f) {
+        const float inv = 1.f / wl;
+        const float2 xj = __ldg(A.src + jl), yj = __ldg(A.dst + jl);
+        const float2 yh = apply_blend(fmaf(c0, inv, q0.x), fmaf(c1, inv, q0.y),
+                                      fmaf(c2, inv, q0.z), fmaf(c3, inv, q0.w),
+                                      fmaf(c4, inv, qs0), xj.x, xj.y);
+        const float r0 = yj.x - yh.x, r1 = yj.y - yh.y;
+        e = r0 * r0 + r1 * r1;
+    }
+    __stcg(A.e + jl, e);
+    if (isfinite(e)) {
+        pe += S.p[jl] * e;
+        ps += S.p[jl];
     }
 }
 
@@ -490,7 +509,7 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
             const int rows[1] = {j};
             residual_rows<1>(A, S, rows, lane, q0, qs0, pe, ps);
         }
-        const float2 t = block_sum2(lane == 0 ? pe : 0.f, lane == 0 ? ps : 0.f, red);
+        const float2 t = block_sum2(pe, ps, red);
         if (threadIdx.x == 0) __stcg(reinterpret_cast<float2 *>(A.partials) + rank, t);
         return barrier_status(A, epoch, &s_flag, ncta);
     };
