@@ -68,6 +68,9 @@ def parse_args():
                     help='plain EM (default: learned warm start when its parameters ship)')
     ap.add_argument('--fused', action='store_true',
                     help='BF16 field and warp in one emdq_mosaic call (default: emdq_field + mosaic_warp)')
+    ap.add_argument('--no-graph', action='store_true',
+                    help='issue every call each step (default: the pass is captured once into a '
+                         'CUDA graph and replayed, removing per-call launch overhead)')
     ap.add_argument('--overlap', action='store_true',
                     help='run the next batch of fits on a second stream while the current batch is '
                          'blended (default: one stream; the cooperative fit launch occupies every '
@@ -343,34 +346,22 @@ def run_gpu(args, ws, rank, local):
         one_pass()
         torch.cuda.synchronize()
         w += 1
-    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(4 + 2 * len(ks))] for ks in batches]
-           for _ in range(args.steps)]
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.1)
-    t_wall = time.perf_counter()
-    all_infos = []
-    for i in range(args.steps):
-        flush.zero_()
-        one_pass(evs[i])
-        all_infos.append(infos.clone())
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    wall = time.perf_counter() - t_wall
-    clk = clocks.stop()
+    def new_events(external=False):
+        # external: recorded as real event nodes when captured into a CUDA graph, so they
+        # still time the replay
+        kw = dict(external=True) if external else {}
+        return [[torch.cuda.Event(enable_timing=True, **kw) for _ in range(4 + 2 * len(ks))]
+                for ks in batches]
+
     # per batch e[0]: its fits issued and e[1]: warm start done, e[2]: fits done (all on the
     # fit stream); e[3]: its blend starts (main stream, after the fits); e[4 + 2j]: frame j's
-    # field done, e[5 + 2j]: its warp done.  Frame latency = e[0] -> e[5 + 2j]; the step time
-    # is first fit issue -> last warp of the pass.  Kernel durations are taken on the stream
-    # each kernel runs on.
+    # field done, e[5 + 2j]: its warp done.  Frame latency = e[0] -> e[5 + 2j].  Kernel
+    # durations are taken on the stream each kernel runs on.
     lat_ms, pass_ms = [], []
     warm_ms, fit_ms, field_ms, warp_ms = [], [], [], []
     fit_launch_frames = []
-    for step in evs:
+
+    def collect(step):
         for bi, e in enumerate(step):
             nb = (len(e) - 4) // 2
             warm_ms.append(e[0].elapsed_time(e[1]))
@@ -382,7 +373,76 @@ def run_gpu(args, ws, rank, local):
                 warp_ms.append(e[4 + 2 * j].elapsed_time(e[5 + 2 * j]))
                 lat_ms.append(e[0].elapsed_time(e[5 + 2 * j]))
                 prev = e[5 + 2 * j]
-        pass_ms.append(step[0][0].elapsed_time(step[-1][-1]))
+
+    # CUDA graph of one pass (one stream): captured once, replayed every step
+    graph, graph_note, gevs = None, None, None
+    if not args.no_graph and not overlap:
+        saved = (stream, fit_stream)
+        try:
+            gevs = new_events(external=True)
+            cap = torch.cuda.Stream(device=dev)
+            cap.wait_stream(torch.cuda.current_stream())
+            g = torch.cuda.CUDAGraph()
+            stream = fit_stream = cap
+            with torch.cuda.graph(g, stream=cap):
+                run_batches(batches, lambda k: frames[k], lambda k: src[k], lambda k: dst[k], gevs)
+            graph = g
+        except Exception as ex:                      # capture refused: issue calls directly
+            graph_note = f'capture failed, calls issued directly: {type(ex).__name__}: {ex}'[:300]
+        stream, fit_stream = saved
+        torch.cuda.synchronize()
+        if graph is not None:                        # one untimed replay
+            flush.zero_()
+            graph.replay()
+            torch.cuda.synchronize()
+    evs = [new_events() for _ in range(args.steps)] if graph is None else None
+    outer = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.1)
+    t_wall = time.perf_counter()
+    all_infos = []
+    for i in range(args.steps):
+        flush.zero_()
+        if graph is not None:
+            outer[i][0].record()
+            graph.replay()
+            outer[i][1].record()
+            all_infos.append(infos.clone())
+            # the graph's events are re-recorded by every replay: read them now (the wait
+            # falls between timed steps)
+            outer[i][1].synchronize()
+            if gevs is not None:
+                try:
+                    collect(gevs)
+                except RuntimeError as ex:       # no timing from inside the graph
+                    gevs = None
+                    graph_note = f'per-kernel times from untimed direct passes: {ex}'[:200]
+            pass_ms.append(outer[i][0].elapsed_time(outer[i][1]))
+        else:
+            one_pass(evs[i])
+            all_infos.append(infos.clone())
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    if graph is None:
+        # step time: first fit issue -> last warp of the pass
+        for step in evs:
+            collect(step)
+            pass_ms.append(step[0][0].elapsed_time(step[-1][-1]))
+    elif gevs is None:
+        # the graph's events could not be read: time the kernels on direct passes instead
+        for step in [new_events() for _ in range(min(3, args.steps))]:
+            flush.zero_()
+            one_pass(step)
+            torch.cuda.synchronize()
+            collect(step)
     total_ms = float(np.sum(pass_ms))
     frame_ms = np.array(lat_ms)
     total_ms = max_over_ranks(total_ms, ws, dev)
@@ -528,8 +588,10 @@ def run_gpu(args, ws, rank, local):
         path=(('learned warm start + ' if warm else '') + ('emdq_fit_batch' if B > 1 else 'emdq_fit') +
               (' + emdq_mosaic (fused BF16 field and warp)' if fused else
                f' + emdq_field ({args.precision}) + mosaic_warp') +
-              (', fits of the next batch on a second stream' if overlap else '')),
-        batch=B, warm_start=warm, wall_s=wall, roofline=roof,
+              (', fits of the next batch on a second stream' if overlap else '') +
+              (', the pass replayed from one CUDA graph' if graph is not None else '')),
+        batch=B, warm_start=warm, cuda_graph=graph is not None,
+        **({'cuda_graph_note': graph_note} if graph_note else {}), wall_s=wall, roofline=roof,
         gpu_launches=total_frames * (2 if fused else 3) + args.steps * len(batches) * (2 if warm else 1),
         clocks=clk,
         e2e=e2e, plain_fp32_gpu=plain,
