@@ -51,7 +51,9 @@ def parse_args():
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='emdq', choices=['emdq', 'reference'])
     ap.add_argument('--precision', default='bf16', choices=['bf16', 'fp32'])
-    ap.add_argument('--workload', default='seq1280')
+    ap.add_argument('--workload', default='seq1280',
+                    help='seq1280 (the 100-frame sequence), batch64 (64 mixed-size pairs), or another '
+                         'single-size workload of synth')
     ap.add_argument('--seed', type=int, default=0)
     ap.add_argument('--frames', type=int, default=0,
                     help='frames per step (default: the whole sequence of the workload)')
@@ -555,8 +557,15 @@ def run_gpu(args, ws, rank, local):
                     peak_source=alu_src, launches=len(warm_ms), mean_launch_ms=float(np.mean(warm_ms)))
     elif dom == 'field':
         if prec == emdq.BF16:
-            flops = 2.0 * 6 * win_px * n
-            roof = dict(bound='tensor', kernel='field_tc_kernel (+ field_tc_prep_kernel in the timing)',
+            # the matches that carry weight (c > 0): zero-weight terms of Eqs. 2-3 are no work
+            nz = []
+            for bi, ks in enumerate(batches):
+                fit_batch(bi, ks, lambda k: src[k], lambda k: dst[k])
+                torch.cuda.synchronize()
+                nz += [int((fit_outs_all[bi % nbuf][j]['c'] > 0).sum().item()) for j in range(len(ks))]
+            flops = 2.0 * 6 * win_px * float(np.mean(nz))
+            roof = dict(bound='tensor', kernel='field_tc_kernel (operand prologue included)',
+                        work='2 x 6 x window pixels x matches of nonzero weight',
                         achieved=flops / (np.mean(field_ms) * 1e-3) / 1e12,
                         peak=peaks['bf16_tflops'], unit='TFLOP/s',
                         peak_source=peaks['source'] + ' bf16 burst', launches=len(field_ms),
@@ -604,6 +613,283 @@ def run_gpu(args, ws, rank, local):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return line
+
+
+MIXED_COUNT = 64
+MIXED_PAD = 256          # canvas margin around each pair's reference frame
+
+
+def mixed_config(args, ws, pairs, ctas=None) -> dict:
+    sizes = sorted({(p['scene'].w, p['scene'].h) for p in pairs})
+    ns = [p['n'] for p in pairs]
+    cfg = dict(workload=f'batch64: {len(pairs)} independent frame pairs, sizes uniform over '
+                        f'{{640x480, 1280x720, 1280x1024, 1920x1080}} RGB8, N uniform in [100, 3000], '
+                        f'outliers uniform in [10%, 40%]; one step = every pair through warm start, '
+                        f'fit, field and warp (each pair into its own canvas)',
+               pairs=len(pairs), sizes_present=[f'{w}x{h}' for w, h in sizes],
+               n_min=min(ns), n_max=max(ns), n_mean=float(sum(ns)) / len(ns),
+               frame_pixels_per_step=int(sum(p['scene'].w * p['scene'].h for p in pairs)),
+               parallelism=f'dp{ws} (independent batches)',
+               l2='inputs larger than L2 (64 distinct frames) and a 256 MiB flush before every '
+                  'step, outside the timed events')
+    if ctas is not None:
+        cfg['fit_ctas_autotuned'] = ctas
+    return cfg
+
+
+def run_gpu_mixed(args, ws, rank, local):
+    """The mixed-size batch: 64 independent pairs per step, one warm-start launch, one
+    autotuned fit launch, then field + warp per pair, the whole step one CUDA graph."""
+    import numpy as np
+    import torch
+    import paper_2103_07414_gb300 as emdq
+    from synth import canvas_origin, footprint_window, mixed_pairs, render_frame, render_reference
+
+    torch.cuda.set_device(local)
+    dev = torch.device('cuda', local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl', device_id=dev)
+    pairs = mixed_pairs(rank_seed(args.seed, rank), MIXED_COUNT)
+    P = []
+    for p in pairs:
+        sc = p['scene']
+        cw, chh = sc.w + 2 * MIXED_PAD, sc.h + 2 * MIXED_PAD
+        origin = canvas_origin(cw, chh, sc.w, sc.h)
+        canvas = torch.zeros((chh, cw, 4), dtype=torch.uint8, device=dev)
+        emdq.mosaic_insert_reference(render_reference(sc, device=dev), canvas, origin)
+        n = p['n']
+        P.append(dict(sc=sc, n=n, origin=origin, canvas=canvas, grid=footprint_window(sc, 1, cw, chh),
+                      frame=render_frame(sc, 1, device=dev), src=torch.from_numpy(p['src']).to(dev),
+                      dst=torch.from_numpy(p['dst']).to(dev), alpha=emdq.alpha_for_frame(sc.w, sc.h),
+                      out=dict(q=torch.empty((n, 8), device=dev), c=torch.empty(n, device=dev),
+                               p=torch.empty(n, device=dev),
+                               info=torch.zeros(4, dtype=torch.int32, device=dev)),
+                      p0=torch.empty(n, device=dev)))
+    warm_params = emdq.load_warmstart_params(dev)
+    probs_sd = [(x['src'], x['dst']) for x in P]
+    fit_probs = [(x['src'], x['dst'], x['sc'].w, x['sc'].h, x['p0']) for x in P]
+    batch_ws = torch.empty(emdq.fit_batch_workspace_size(probs_sd), dtype=torch.uint8, device=dev)
+    field_ws = torch.empty(max(emdq.field_workspace_size(x['n'], x['grid'][2], x['grid'][3], emdq.BF16)
+                               for x in P), dtype=torch.uint8, device=dev)
+    disp_buf = torch.empty(max(x['grid'][2] * x['grid'][3] for x in P) * 2, dtype=torch.float32,
+                           device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    infos = torch.zeros((len(P), 4), dtype=torch.int32, device=dev)
+    emdq.warm_start(probs_sd, warm_params, outs=[x['p0'] for x in P])
+    ctas, tune_ms = emdq.fit_batch_autotune(fit_probs, reps=2, outs=[x['out'] for x in P],
+                                            workspace=batch_ws)
+
+    def one_pass(ev=None):
+        # ev[0] start, ev[1] warm start done, ev[2] fits done, ev[3 + 2b] / ev[4 + 2b]: pair
+        # b's field / warp done
+        if ev: ev[0].record()
+        emdq.warm_start(probs_sd, warm_params, outs=[x['p0'] for x in P])
+        if ev: ev[1].record()
+        emdq.emdq_fit_batch(fit_probs, outs=[x['out'] for x in P], workspace=batch_ws, ctas=ctas)
+        if ev: ev[2].record()
+        for b, x in enumerate(P):
+            g = x['grid']
+            disp = disp_buf[: g[2] * g[3] * 2].view(g[3], g[2], 2)
+            emdq.emdq_field(x['out']['q'], x['out']['c'], x['src'], g, x['alpha'], precision=emdq.BF16,
+                            out=disp, workspace=field_ws)
+            if ev: ev[3 + 2 * b].record()
+            emdq.mosaic_warp(x['frame'], disp, g, x['canvas'], x['origin'])
+            if ev: ev[4 + 2 * b].record()
+        for b, x in enumerate(P):
+            infos[b].copy_(x['out']['info'])
+
+    t0 = time.perf_counter()
+    w = 0
+    while w < args.warmup or time.perf_counter() - t0 < args.min_warmup_s:
+        flush.zero_()
+        one_pass()
+        torch.cuda.synchronize()
+        w += 1
+    n_ev = 3 + 2 * len(P)
+    graph, graph_note = None, None
+    gev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(n_ev)]
+    if not args.no_graph:
+        try:
+            cap = torch.cuda.Stream(device=dev)
+            cap.wait_stream(torch.cuda.current_stream())
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=cap):
+                one_pass(gev)
+            graph = g
+        except Exception as ex:
+            graph_note = f'capture failed, calls issued directly: {type(ex).__name__}: {ex}'[:300]
+        torch.cuda.synchronize()
+    warm_ms, fit_ms, field_ms, warp_ms, step_ms = [], [], [], [], []
+
+    def collect(ev):
+        warm_ms.append(ev[0].elapsed_time(ev[1]))
+        fit_ms.append(ev[1].elapsed_time(ev[2]))
+        prev = ev[2]
+        for b in range(len(P)):
+            field_ms.append(prev.elapsed_time(ev[3 + 2 * b]))
+            warp_ms.append(ev[3 + 2 * b].elapsed_time(ev[4 + 2 * b]))
+            prev = ev[4 + 2 * b]
+
+    outer = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(args.steps)]
+    direct_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.1)
+    all_infos = []
+    for i in range(args.steps):
+        flush.zero_()
+        outer[i][0].record()
+        if graph is not None:
+            graph.replay()
+        else:
+            one_pass(direct_ev[i])
+        outer[i][1].record()
+        outer[i][1].synchronize()
+        collect(gev if graph is not None else direct_ev[i])
+        step_ms.append(outer[i][0].elapsed_time(outer[i][1]))
+        all_infos.append(infos.clone())
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(float(np.sum(step_ms)), ws, dev)
+    px = sum(x['sc'].w * x['sc'].h for x in P)
+    iv = torch.stack(all_infos).cpu()
+    iters = iv[:, :, 1].numpy()
+    statuses = sorted({emdq.STATUS.get(int(v), '?') for v in iv[:, :, 0].flatten().tolist()})
+    nz = [int((x['out']['c'] > 0).sum().item()) for x in P]
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return None
+    peaks = measured_peaks()
+    sm_mhz = (clk or {}).get('sm_mhz') or peaks['sm_max_mhz']
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    totals = dict(fit=float(np.sum(fit_ms)), warm=float(np.sum(warm_ms)), field=float(np.sum(field_ms)),
+                  warp=float(np.sum(warp_ms)))
+    dom = max(totals, key=totals.get)
+    ns = np.array([x['n'] for x in P], dtype=np.float64)
+    win = np.array([x['grid'][2] * x['grid'][3] for x in P], dtype=np.float64)
+    if dom == 'fit':
+        flops = float(np.mean([np.sum((it + 1) * ns * ns) for it in iters])) * 56.0
+        roof = dict(bound='alu', kernel='emdq_fit_batch_kernel', achieved=flops / (np.mean(fit_ms) * 1e-3) / 1e12,
+                    peak=alu_peak, unit='TFLOP/s',
+                    peak_source=f'derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x {sm_mhz:.0f} MHz',
+                    launches=len(fit_ms), mean_launch_ms=float(np.mean(fit_ms)))
+    elif dom == 'field':
+        flops = 2.0 * 6 * float(np.sum(win * np.array(nz)))
+        roof = dict(bound='tensor', kernel='field_tc_kernel (operand prologue included)',
+                    achieved=flops / (np.sum(field_ms) / args.steps * 1e-3) / 1e12,
+                    peak=peaks['bf16_tflops'], unit='TFLOP/s', peak_source=peaks['source'] + ' bf16 burst',
+                    launches=len(field_ms), mean_launch_ms=float(np.mean(field_ms)),
+                    work='2 x 6 x window pixels x matches of nonzero weight, summed over the pairs')
+    elif dom == 'warm':
+        flops = float(np.sum(ns * (4.0 * ns + 2 * 5184)))
+        roof = dict(bound='alu', kernel='warm_start_batch_kernel', achieved=flops / (np.mean(warm_ms) * 1e-3) / 1e12,
+                    peak=alu_peak, unit='TFLOP/s', peak_source='derived', launches=len(warm_ms),
+                    mean_launch_ms=float(np.mean(warm_ms)))
+    else:
+        nbytes = float(np.sum(win * 16 + np.array([x['sc'].w * x['sc'].h * 3 for x in P])))
+        roof = dict(bound='hbm', kernel='mosaic_warp_kernel',
+                    achieved=nbytes / (np.sum(warp_ms) / args.steps * 1e-3) / 1e9, peak=peaks['hbm_gbs'],
+                    unit='GB/s', peak_source=peaks['source'] + ' copy', launches=len(warp_ms),
+                    mean_launch_ms=float(np.mean(warp_ms)))
+    roof['frac'] = roof['achieved'] / roof['peak']
+    roof['traffic'] = None
+    value = ws * args.steps * px / 1e6 / (total_ms / 1e3)
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
+        ms_per_step=total_ms / args.steps, p50_frame_ms=float(np.median(step_ms)),
+        higher_is_better=True, scaling='weak', vs_baseline=None, dtype='bf16', data='synthetic',
+        config=mixed_config(args, ws, pairs, ctas),
+        kernel_ms_per_step={k: v / args.steps for k, v in totals.items()},
+        path='learned warm start (one launch) + emdq_fit_batch (one launch, autotuned CTA split) + '
+             'per pair emdq_field (bf16) + mosaic_warp' +
+             (', the step replayed from one CUDA graph' if graph is not None else ''),
+        cuda_graph=graph is not None, **({'cuda_graph_note': graph_note} if graph_note else {}),
+        autotune_fit_ms=tune_ms, mean_em_iters=float(np.mean(iters)), roofline=roof,
+        gpu_launches=args.steps * (2 + 2 * len(P)), clocks=clk, e2e=None, fit_status=statuses,
+        p50_note='per step: the whole batch of 64 pairs is one unit of latency')
+    if not args.no_cpu_baseline:
+        line['cpu_baseline'] = cpu_baseline_mixed(args, budget_s=12.0)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return line
+
+
+def oracle_pair(orc, p, frac):
+    """One mixed pair through the oracle: the full fit, field and warp on a centred band of
+    `frac` of the window's rows.  Returns seconds extrapolated to the whole window."""
+    import numpy as np
+    from synth import canvas_origin, footprint_window, render_frame
+    sc = p['scene']
+    cw, chh = sc.w + 2 * MIXED_PAD, sc.h + 2 * MIXED_PAD
+    origin = canvas_origin(cw, chh, sc.w, sc.h)
+    grid = footprint_window(sc, 1, cw, chh)
+    canvas = np.zeros((chh, cw, 4), np.uint8)
+    fr = render_frame(sc, 1).numpy()
+    s = np.float32(p['src']).astype(np.float64)
+    d = np.float32(p['dst']).astype(np.float64)
+    t0 = time.perf_counter()
+    r = orc.fit(s, d, sc.w, sc.h)
+    t1 = time.perf_counter()
+    rows = max(1, int(round(grid[3] * frac)))
+    band = (grid[0], grid[1] + (grid[3] - rows) // 2, grid[2], rows)
+    disp = orc.field(r['q8'], r['c'], s, band, orc.alpha_for_frame(sc.w, sc.h))
+    orc.warp(fr, disp.astype(np.float32), band, canvas, origin)
+    t2 = time.perf_counter()
+    return (t1 - t0) + (t2 - t1) * grid[3] / rows
+
+
+def cpu_baseline_mixed(args, budget_s=12.0):
+    """The oracle on this host's cores over the first pairs of the batch (bounded sample)."""
+    import oracle as orc
+    from synth import mixed_pairs
+    orc.build()
+    pairs = mixed_pairs(args.seed, MIXED_COUNT)
+    t_start, sec, px, k = time.perf_counter(), 0.0, 0, 0
+    while k < len(pairs) and (time.perf_counter() - t_start < budget_s or k == 0):
+        sec += oracle_pair(orc, pairs[k], 1 / 16)
+        px += pairs[k]['scene'].w * pairs[k]['scene'].h
+        k += 1
+    return dict(value=px / 1e6 / sec, unit=UNIT, cores=orc.max_threads(), kind='oracle',
+                sample=f'the first {k} pair(s) of the batch: full EM fit + field and warp on the '
+                       f'centred 1/16 of the window rows, extrapolated to the full window')
+
+
+def run_reference_mixed(args, ws, rank):
+    """--impl reference on the mixed batch: the oracle on the host cores, rank 0 only."""
+    if rank != 0:
+        return None
+    import numpy as np
+    import oracle as orc
+    from synth import mixed_pairs
+    orc.build()
+    pairs = mixed_pairs(args.seed, MIXED_COUNT)
+    times, pxs = [], []
+    for k in range(args.warmup + args.steps):
+        p = pairs[k % len(pairs)]
+        t = oracle_pair(orc, p, 1 / 16)
+        if k >= args.warmup:
+            times.append(t)
+            pxs.append(p['scene'].w * p['scene'].h)
+    value = float(np.sum(pxs)) / 1e6 / float(np.sum(times))
+    return dict(impl='reference', metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
+                warmup=args.warmup, ms_per_step=float(np.mean(times)) * 1e3,
+                p50_frame_ms=float(np.median(times)) * 1e3, higher_is_better=True, scaling='weak',
+                vs_baseline=None, dtype='f64', data='synthetic',
+                config=dict(mixed_config(args, ws, pairs), precision='f64',
+                            sample='per step one pair of the batch: full EM fit + field and warp on '
+                                   '1/16 of the window rows, extrapolated'),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=orc.max_threads(), kind='oracle',
+                                  sample='per step one pair of the batch (1/16 of the window rows, '
+                                         'extrapolated)'),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
 
 
 def oracle_frame(orc, sc, cfg, frame_np, s, d, grid, canvas, origin, frac):
@@ -696,10 +982,11 @@ def run_reference(args, ws, rank):
 def main():
     args = parse_args()
     ws, rank, local = dist_env()
+    mixed = args.workload == 'batch64'
     if args.impl == 'reference':
-        line = run_reference(args, ws, rank)
+        line = run_reference_mixed(args, ws, rank) if mixed else run_reference(args, ws, rank)
     else:
-        line = run_gpu(args, ws, rank, local)
+        line = run_gpu_mixed(args, ws, rank, local) if mixed else run_gpu(args, ws, rank, local)
     if line is not None and rank == 0:
         print(json.dumps(line))
 

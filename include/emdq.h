@@ -146,9 +146,34 @@ typedef struct {
 } emdq_fit_problem;
 
 EMDQ_API size_t      emdq_fit_batch_workspace_size(const emdq_fit_problem *problems, int count);
+/* CTAs are split over the problems in proportion to n^2 (the EM work per round), at least
+ * one and at most ceil(n / 8) each. */
 EMDQ_API emdq_status emdq_fit_batch(const emdq_fit_problem *problems, int count,
                                     const emdq_params *prm, void *workspace,
                                     size_t workspace_bytes, void *stream);
+
+/* The batch launch with an explicit split: problem b runs on ctas[b] CTAs (host array of
+ * `count` ints, each >= 1, summing to at most emdq_fit_batch_capacity(problems, count);
+ * otherwise EMDQ_EINVAL).  ctas = NULL is emdq_fit_batch.  Results do not depend on the
+ * split beyond the FP32 summation order of the sigma^2 partial sums. */
+EMDQ_API emdq_status emdq_fit_batch_ex(const emdq_fit_problem *problems, int count,
+                                       const emdq_params *prm, const int *ctas, void *workspace,
+                                       size_t workspace_bytes, void *stream);
+
+/* CTAs of the batch kernel that are co-resident on the current device for these problems
+ * (the largest n sets the shared memory per CTA); 0 on error. */
+EMDQ_API int         emdq_fit_batch_capacity(const emdq_fit_problem *problems, int count);
+
+/* Autotuner of the batch split (not in the paper: a launch-configuration search).  Runs
+ * the batch with CTAs split in proportion to n^e for e in {0, 1, 1.5, 2, 2.5, 3}, each once
+ * untimed and then `reps` times (1..100) timed with CUDA events on `stream`, and writes the
+ * fastest split to ctas_out (host, count ints) and its best time in ms to ms_out (host,
+ * may be NULL).  Synchronises the stream; refuses (EMDQ_EINVAL) while the stream is being
+ * captured.  The problems' outputs hold the last run's results. */
+EMDQ_API emdq_status emdq_fit_batch_autotune(const emdq_fit_problem *problems, int count,
+                                             const emdq_params *prm, void *workspace,
+                                             size_t workspace_bytes, void *stream, int reps,
+                                             int *ctas_out, float *ms_out);
 
 /* ------------------------------------------------------------------ emdq_fit_noalloc -
  * emdq_fit for callers that cannot allocate device memory.  The paper has no counterpart:

@@ -73,6 +73,13 @@ def lib() -> ctypes.CDLL:
             L.emdq_fit_batch_workspace_size.argtypes = [P, I]
             L.emdq_fit_batch.restype = I
             L.emdq_fit_batch.argtypes = [P, I, ctypes.POINTER(_Params), P, Z, P]
+            L.emdq_fit_batch_ex.restype = I
+            L.emdq_fit_batch_ex.argtypes = [P, I, ctypes.POINTER(_Params), P, P, Z, P]
+            L.emdq_fit_batch_capacity.restype = I
+            L.emdq_fit_batch_capacity.argtypes = [P, I]
+            L.emdq_fit_batch_autotune.restype = I
+            L.emdq_fit_batch_autotune.argtypes = [P, I, ctypes.POINTER(_Params), P, Z, P, I, P,
+                                                  ctypes.POINTER(ctypes.c_float)]
             L.emdq_field_workspace_size.restype = Z
             L.emdq_field_workspace_size.argtypes = [I, I, I, I]
             L.emdq_field.restype = I
@@ -165,12 +172,7 @@ def emdq_fit(src: torch.Tensor, dst: torch.Tensor, frame_w: int, frame_h: int, *
     return dict(q=q, c=c, p=p, info=info, workspace=ws)
 
 
-def emdq_fit_batch(problems, *, alpha: float = 0.0, max_iters: int = 20, tol_p: float = 1e-3,
-                   sigma2_floor: float = 0.25, outs: list | None = None,
-                   workspace: torch.Tensor | None = None, stream=None) -> list:
-    """Fit several independent problems in one launch.  problems: list of
-    (src, dst, frame_w, frame_h) or (src, dst, frame_w, frame_h, p0).  Returns one dict per
-    problem as emdq_fit does."""
+def _batch_args(problems, outs):
     count = len(problems)
     arr = (_Problem * max(1, count))()
     results = []
@@ -193,15 +195,61 @@ def emdq_fit_batch(problems, *, alpha: float = 0.0, max_iters: int = 20, tol_p: 
                           p0.data_ptr() if p0 is not None else None, r['q'].data_ptr(),
                           r['c'].data_ptr(), r['p'].data_ptr(), r['info'].data_ptr())
         results.append(r)
+    return arr, results
+
+
+def emdq_fit_batch(problems, *, alpha: float = 0.0, max_iters: int = 20, tol_p: float = 1e-3,
+                   sigma2_floor: float = 0.25, outs: list | None = None,
+                   workspace: torch.Tensor | None = None, ctas=None, stream=None) -> list:
+    """Fit several independent problems in one launch.  problems: list of
+    (src, dst, frame_w, frame_h) or (src, dst, frame_w, frame_h, p0).  ctas: optional CTAs per
+    problem (default: in proportion to n^2).  Returns one dict per problem as emdq_fit does."""
+    count = len(problems)
+    arr, results = _batch_args(problems, outs)
     need = lib().emdq_fit_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), count)
     dev = problems[0][0].device
     ws = _workspace(need, dev, workspace)
     prm = _Params(float(alpha), int(max_iters), float(tol_p), float(sigma2_floor), (ctypes.c_int * 4)())
-    rc = lib().emdq_fit_batch(ctypes.cast(arr, ctypes.c_void_p), count, ctypes.byref(prm), _ptr(ws),
-                              ws.numel(), _stream(stream))
+    split = None
+    if ctas is not None:
+        if len(ctas) != count:
+            raise ValueError('ctas: one entry per problem')
+        split = (ctypes.c_int * count)(*[int(v) for v in ctas])
+    rc = lib().emdq_fit_batch_ex(ctypes.cast(arr, ctypes.c_void_p), count, ctypes.byref(prm),
+                                 ctypes.cast(split, ctypes.c_void_p) if split is not None else None,
+                                 _ptr(ws), ws.numel(), _stream(stream))
     if rc != 0:
         raise EmdqError('emdq_fit_batch', rc)
     return results
+
+
+def fit_batch_capacity(problems) -> int:
+    """Co-resident CTAs of the batch kernel for these problems."""
+    count = len(problems)
+    arr = (_Problem * max(1, count))()
+    for b, pr in enumerate(problems):
+        arr[b].n = int(pr[0].shape[0])
+    return lib().emdq_fit_batch_capacity(ctypes.cast(arr, ctypes.c_void_p), count)
+
+
+def fit_batch_autotune(problems, *, reps: int = 3, alpha: float = 0.0, max_iters: int = 20,
+                       tol_p: float = 1e-3, sigma2_floor: float = 0.25, outs: list | None = None,
+                       workspace: torch.Tensor | None = None, stream=None):
+    """Time the candidate CTA splits of the library's autotuner on these problems; returns
+    (ctas per problem, best ms).  Synchronises; not inside a stream capture."""
+    count = len(problems)
+    arr, _ = _batch_args(problems, outs)
+    need = lib().emdq_fit_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), count)
+    ws = _workspace(need, problems[0][0].device, workspace)
+    prm = _Params(float(alpha), int(max_iters), float(tol_p), float(sigma2_floor), (ctypes.c_int * 4)())
+    out = (ctypes.c_int * count)()
+    ms = ctypes.c_float(0.0)
+    rc = lib().emdq_fit_batch_autotune(ctypes.cast(arr, ctypes.c_void_p), count, ctypes.byref(prm),
+                                       _ptr(ws), ws.numel(), _stream(stream), int(reps),
+                                       ctypes.cast(out, ctypes.c_void_p), ctypes.byref(ms))
+    if rc != 0:
+        raise EmdqError('emdq_fit_batch_autotune', rc)
+    return [int(v) for v in out], float(ms.value)
 
 
 def fit_batch_workspace_size(problems) -> int:

@@ -127,6 +127,9 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
     float *__restrict__ ref_out, __nv_bfloat162 *__restrict__ A, __nv_bfloat162 *__restrict__ B,
     int a_blocks, int *__restrict__ kcount)
 {
+    // the GEMM launched after this kernel may start its set-up now; it waits for this
+    // grid's completion (griddepcontrol.wait) before it reads anything written here
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ int s_idx[kCompactMax];
     const int half = kp / 2;
     const int mc = compact_columns(c, n, s_idx);
@@ -207,9 +210,6 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(
     const float *__restrict__ ref, float2 *__restrict__ disp, int *__restrict__ err,
     MosaicArgs mos)
 {
-    // 64-match slices along K: the prep kernel's column count (the matches of nonzero
-    // weight), a whole number of slices, at least one
-    const int nchunks = *kcount / kTcK;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -246,6 +246,14 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
+    // everything above is independent of the prep kernel (programmatic dependent launch);
+    // its operands, column count and reference row are read only after this wait
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // the warp launched after this kernel may start its set-up now (it waits likewise)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // 64-match slices along K: the prep kernel's column count (the matches of nonzero
+    // weight), a whole number of slices, at least one
+    const int nchunks = *kcount / kTcK;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -505,14 +513,27 @@ emdq_status field_tc_launch(const float *q, const float *c, const float *src, in
     const int ntx = g.wp / kTcM, ntiles = ntx * (g.hp / kTcPY);
     const int grid = ntiles < D.sms ? ntiles : D.sms;       // persistent: one CTA per SM
     const MosaicArgs none{};
+    // programmatic dependent launch: the GEMM's set-up overlaps the prep kernel's tail
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(tc_threads(variant));
+    cfg.dynamicSmemBytes = kTcSmemBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e;
     if (variant == 0)
-        field_tc_kernel<0><<<grid, tc_threads(0), kTcSmemBytes, st>>>(tmA, tmB, kcount, ntx, ntiles, gx0,
-                                                                   gy0, gw, gh, ref, disp, err, none);
+        e = cudaLaunchKernelEx(&cfg, field_tc_kernel<0>, tmA, tmB, (const int *)kcount, ntx, ntiles,
+                               gx0, gy0, gw, gh, (const float *)ref, disp, err, none);
     else if (variant == 1)
-        field_tc_kernel<1><<<grid, tc_threads(1), kTcSmemBytes, st>>>(tmA, tmB, kcount, ntx, ntiles, gx0,
-                                                                   gy0, gw, gh, ref, disp, err, *mos);
+        e = cudaLaunchKernelEx(&cfg, field_tc_kernel<1>, tmA, tmB, (const int *)kcount, ntx, ntiles,
+                               gx0, gy0, gw, gh, (const float *)ref, disp, err, *mos);
     else
-        field_tc_kernel<3><<<grid, tc_threads(3), kTcSmemBytes, st>>>(tmA, tmB, kcount, ntx, ntiles, gx0,
-                                                                   gy0, gw, gh, ref, disp, err, *mos);
+        e = cudaLaunchKernelEx(&cfg, field_tc_kernel<3>, tmA, tmB, (const int *)kcount, ntx, ntiles,
+                               gx0, gy0, gw, gh, (const float *)ref, disp, err, *mos);
+    if (e != cudaSuccess) return EMDQ_ECUDA;
     return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }

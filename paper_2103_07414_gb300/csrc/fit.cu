@@ -33,12 +33,13 @@
 
 namespace emdq {
 
-constexpr int kFitThreads = 256;
-constexpr int kFitWarps = kFitThreads / 32;
+// Block size: 256 threads when two CTAs fit an SM (the fit's shared memory is 44 bytes per
+// match), 512 when only one does, so an SM keeps 16 warps either way.
+constexpr int kFitThreadsSmall = 256;
+constexpr int kFitThreadsLarge = 512;
 constexpr int kFitMaxN = 5120;         // shared memory: 44 bytes per match
 constexpr int kFitSmemPerMatch = 44;
 constexpr int kFitMaxGrid = 1024;
-constexpr int kFitEPerThread = (kFitMaxN + kFitThreads - 1) / kFitThreads;   // residuals per thread
 
 struct FitArgs {
     const float2 *src;
@@ -402,8 +403,9 @@ __device__ void residual_rows(const FitArgs &A, const FitSmem &S, const int *row
 }
 
 // Block-wide sums of two floats in a fixed order: warp butterflies, then every thread
-// adds the 8 warp totals in warp order, so every thread (and every CTA, given the same
+// adds the NT/32 warp totals in warp order, so every thread (and every CTA, given the same
 // inputs) holds the same bits.
+template <int NT>
 __device__ float2 block_sum2(float a, float b, float2 *red)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -413,7 +415,7 @@ __device__ float2 block_sum2(float a, float b, float2 *red)
     __syncthreads();
     float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < kFitWarps; ++k) {
+    for (int k = 0; k < NT / 32; ++k) {
         t.x += red[k].x;
         t.y += red[k].y;
     }
@@ -433,21 +435,24 @@ __device__ int barrier_status(const FitArgs &A, unsigned &epoch, int *s_flag, in
 // log2 of a posterior for the staged weights (-inf for 0: its weight 2^-inf is 0)
 __device__ __forceinline__ float log2_p(float p) { return __log2f(p); }
 
-// One fit on a group of `ncta` co-resident CTAs; `rank` is this CTA's index in the group.
+// One fit on a group of `ncta` co-resident CTAs of NT threads; `rank` is this CTA's index
+// in the group.
+template <int NT>
 __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
 {
+    constexpr int kWarps = NT / 32;
     const int n = A.n;
     const FitSmem S = fit_smem(n);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gwarp = rank * kFitWarps + warp, nwarps = ncta * kFitWarps;
-    __shared__ float2 red[kFitWarps];
+    const int gwarp = rank * kWarps + warp, nwarps = ncta * kWarps;
+    __shared__ float2 red[kWarps];
     __shared__ int s_flag;
     unsigned epoch = 0;
 
     // stage the matches (scaled) and the initial weights; every CTA checks every input
     int bad = 0;
     float p0sum = 0.f;
-    for (int j = threadIdx.x; j < n; j += kFitThreads) {
+    for (int j = threadIdx.x; j < n; j += NT) {
         const float2 x = A.src[j], y = A.dst[j];
         S.x[j] = make_float2(A.k * x.x, A.k * x.y);
         S.y[j] = make_float2(A.k * y.x, A.k * y.y);
@@ -467,7 +472,7 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
         return;
     }
     float gamma = 0.5f;
-    if (A.p0) gamma = fminf(fmaxf(block_sum2(p0sum, 0.f, red).x / n, 0.05f), 0.95f);
+    if (A.p0) gamma = fminf(fmaxf(block_sum2<NT>(p0sum, 0.f, red).x / n, 0.05f), 0.95f);
 
     // this warp's M-step rows i = gwarp, gwarp + nwarps, ..., two at a time
     auto mstep_all = [&](bool first) {
@@ -485,7 +490,7 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
     auto residuals_and_barrier = [&]() -> int {
         const float4 q0 = __ldcg(reinterpret_cast<const float4 *>(A.q_out));
         const float qs0 = __ldcg(A.q_out + 4);
-        for (int i = threadIdx.x; i < n; i += kFitThreads) {
+        for (int i = threadIdx.x; i < n; i += NT) {
             const float4 r0 = __ldcg(reinterpret_cast<const float4 *>(A.q_out + 8 * (size_t)i));
             const float r4 = __ldcg(A.q_out + 8 * (size_t)i + 4);
             S.q[i] = make_float4(r0.x - q0.x, r0.y - q0.y, r0.z - q0.z, r0.w - q0.w);
@@ -509,20 +514,13 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
             const int rows[1] = {j};
             residual_rows<1>(A, S, rows, lane, q0, qs0, pe, ps);
         }
-        const float2 t = block_sum2(pe, ps, red);
+        const float2 t = block_sum2<NT>(pe, ps, red);
         if (threadIdx.x == 0) __stcg(reinterpret_cast<float2 *>(A.partials) + rank, t);
         return barrier_status(A, epoch, &s_flag, ncta);
     };
-    // after that barrier: this thread's residuals (all N are needed by every CTA) and
-    // sigma^2 from the per-CTA partials, loads issued together so their latencies overlap;
-    // every warp reduces the partials itself, in the same order
-    float ev[kFitEPerThread];
+    // after that barrier: sigma^2 from the per-CTA partials; every warp reduces the
+    // partials itself, in the same order
     auto load_e_and_sigma2 = [&]() -> float {
-#pragma unroll
-        for (int k = 0; k < kFitEPerThread; ++k) {
-            const int j = threadIdx.x + k * kFitThreads;
-            ev[k] = j < n ? __ldcg(A.e + j) : 0.f;
-        }
         float num = 0.f, den = 0.f;
         for (int b = lane; b < ncta; b += 32) {
             const float2 v = __ldcg(reinterpret_cast<const float2 *>(A.partials) + b);
@@ -551,11 +549,9 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
         float dpmax = 0.f, psum = 0.f;
         const float norm = 1.f / (two_pi * sigma2);
         const float outl = (1.f - gamma) * A.inv_area;
-#pragma unroll
-        for (int k = 0; k < kFitEPerThread; ++k) {
-            const int j = threadIdx.x + k * kFitThreads;
-            if (j < n) {
-                const float e = ev[k];
+        for (int j = threadIdx.x; j < n; j += NT) {
+            {
+                const float e = __ldcg(A.e + j);      // all N residuals, from every CTA
                 const float G = isfinite(e) ? expf(-e / (2.f * sigma2)) * norm : 0.f;
                 const float pn = gamma * G / (gamma * G + outl);
                 dpmax = fmaxf(dpmax, fabsf(pn - S.p[j]));
@@ -571,7 +567,7 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
         __syncthreads();
         float dpall = 0.f, ptot = 0.f;
 #pragma unroll
-        for (int k = 0; k < kFitWarps; ++k) {
+        for (int k = 0; k < kWarps; ++k) {
             dpall = fmaxf(dpall, red[k].x);
             ptot += red[k].y;
         }
@@ -590,7 +586,7 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
     }
 
     if (rank == 0) {
-        for (int j = threadIdx.x; j < n; j += kFitThreads) {
+        for (int j = threadIdx.x; j < n; j += NT) {
             const float p = S.p[j];
             A.c_out[j] = p >= 0.5f ? p : 0.f;
             if (A.p_out) A.p_out[j] = p;
@@ -609,23 +605,33 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
     }
 }
 
-__global__ void __launch_bounds__(kFitThreads, 2) emdq_fit_kernel(FitArgs A)
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) emdq_fit_kernel(FitArgs A)
 {
-    fit_body(A, blockIdx.x, gridDim.x);
+    fit_body<NT>(A, blockIdx.x, gridDim.x);
 }
 
 // Many fits in one cooperative launch: problem b runs on CTAs [b * group, (b + 1) * group),
 // with its own barrier counter, status word and partial sums.
+// Problem b owns CTAs [first[b], first[b + 1]): a split of the co-resident CTAs in
+// proportion to each problem's work, so problems of different sizes finish together.
 constexpr int kFitBatchMax = 64;
 struct FitBatch {
     FitArgs a[kFitBatchMax];
+    int first[kFitBatchMax + 1];
+    int count;
 };
 
-__global__ void __launch_bounds__(kFitThreads, 2) emdq_fit_batch_kernel(const __grid_constant__ FitBatch B,
-                                                                      int group)
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) emdq_fit_batch_kernel(const __grid_constant__ FitBatch B)
 {
-    const int b = blockIdx.x / group;
-    fit_body(B.a[b], blockIdx.x - b * group, group);
+    int lo = 0, hi = B.count - 1;          // the problem whose CTA range holds blockIdx.x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.first[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    fit_body<NT>(B.a[lo], blockIdx.x - B.first[lo], B.first[lo + 1] - B.first[lo]);
 }
 
 }  // namespace emdq
@@ -650,6 +656,58 @@ constexpr FitLayout fit_layout(int n)
                          al256(sizeof(double) * 2 * kFitMaxGrid) + 256};
 }
 size_t fit_smem_bytes(int n) { return (size_t)n * kFitSmemPerMatch; }
+
+// The shared-memory limit of every fit kernel instance, raised once per device.
+bool fit_attributes()
+{
+    static std::mutex mu;
+    static int done_dev = -1;
+    const DeviceInfo &D = device_info();
+    if (D.device < 0) return false;
+    std::lock_guard<std::mutex> g(mu);
+    if (done_dev == D.device) return true;
+    const int smax = (int)fit_smem_bytes(kFitMaxN);
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (cudaFuncSetAttribute(emdq_fit_kernel<kFitThreadsSmall>, attr, smax) != cudaSuccess ||
+        cudaFuncSetAttribute(emdq_fit_kernel<kFitThreadsLarge>, attr, smax) != cudaSuccess ||
+        cudaFuncSetAttribute(emdq_fit_batch_kernel<kFitThreadsSmall>, attr, smax) != cudaSuccess ||
+        cudaFuncSetAttribute(emdq_fit_batch_kernel<kFitThreadsLarge>, attr, smax) != cudaSuccess)
+        return false;
+    done_dev = D.device;
+    return true;
+}
+
+// Block size for `smem` bytes of shared memory per CTA (256 threads if two CTAs fit an SM,
+// else 512) and the CTAs then co-resident on the device; false on error.
+bool fit_shape(bool batch, size_t smem, int &nt, int &capacity)
+{
+    if (!fit_attributes()) return false;
+    const DeviceInfo &D = device_info();
+    int per = 0;
+    const cudaError_t e =
+        batch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per, emdq_fit_batch_kernel<kFitThreadsSmall>, kFitThreadsSmall, smem)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per, emdq_fit_kernel<kFitThreadsSmall>, kFitThreadsSmall, smem);
+    if (e != cudaSuccess) return false;
+    if (per >= 2) {
+        nt = kFitThreadsSmall;
+        capacity = per * D.sms;
+        return true;
+    }
+    const cudaError_t e2 =
+        batch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per, emdq_fit_batch_kernel<kFitThreadsLarge>, kFitThreadsLarge, smem)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per, emdq_fit_kernel<kFitThreadsLarge>, kFitThreadsLarge, smem);
+    if (e2 != cudaSuccess || per < 1) return false;
+    nt = kFitThreadsLarge;
+    capacity = per * D.sms;
+    return true;
+}
+
+// CTAs of nt threads a problem of n matches can use: one warp per row.
+int useful_ctas(int n, int nt) { return (n + nt / 32 - 1) / (nt / 32); }
 }  // namespace
 
 extern "C" int emdq_fit_max_n(void) { return kFitMaxN; }
@@ -681,23 +739,9 @@ extern "C" emdq_status emdq_fit(const float *src, const float *dst, int n, int f
     const size_t smem = fit_smem_bytes(n);
     if (smem > D.smem_optin) return EMDQ_ENOTSUP;
 
-    static std::mutex mu;
-    static int attr_set_dev = -1;
-    {
-        std::lock_guard<std::mutex> g(mu);
-        if (attr_set_dev != D.device) {
-            if (cudaFuncSetAttribute(emdq_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)fit_smem_bytes(kFitMaxN)) != cudaSuccess)
-                return EMDQ_ECUDA;
-            attr_set_dev = D.device;
-        }
-    }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emdq_fit_kernel, kFitThreads, smem) !=
-            cudaSuccess || per_sm < 1)
-        return EMDQ_ECUDA;
-    int grid = (n + kFitWarps - 1) / kFitWarps;
-    const int cap = D.sms * per_sm;
+    int nt = 0, cap = 0;
+    if (!fit_shape(false, smem, nt, cap)) return EMDQ_ECUDA;
+    int grid = useful_ctas(n, nt);
     if (grid > cap) grid = cap;
     if (grid > kFitMaxGrid) grid = kFitMaxGrid;
 
@@ -730,7 +774,7 @@ extern "C" emdq_status emdq_fit(const float *src, const float *dst, int n, int f
 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kFitThreads);
+    cfg.blockDim = dim3(nt);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
@@ -738,7 +782,10 @@ extern "C" emdq_status emdq_fit(const float *src, const float *dst, int n, int f
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, emdq_fit_kernel, A) != cudaSuccess) return EMDQ_ECUDA;
+    const cudaError_t e = nt == kFitThreadsSmall
+                              ? cudaLaunchKernelEx(&cfg, emdq_fit_kernel<kFitThreadsSmall>, A)
+                              : cudaLaunchKernelEx(&cfg, emdq_fit_kernel<kFitThreadsLarge>, A);
+    if (e != cudaSuccess) return EMDQ_ECUDA;
     return EMDQ_OK;
 }
 
@@ -765,9 +812,54 @@ extern "C" size_t emdq_fit_batch_workspace_size(const emdq_fit_problem *problems
     return total;
 }
 
-extern "C" emdq_status emdq_fit_batch(const emdq_fit_problem *problems, int count,
-                                      const emdq_params *prm, void *workspace,
-                                      size_t workspace_bytes, void *stream)
+namespace {
+
+
+// Split `total` CTAs of nt threads over the problems in proportion to n^e (e = expo), at
+// least one each and at most useful_ctas(n, nt); largest remainders take the leftovers.
+void split_ctas(const emdq_fit_problem *problems, int count, int total, int nt, double expo,
+                int *ctas)
+{
+    double wsum = 0.0;
+    for (int b = 0; b < count; ++b) wsum += std::pow((double)problems[b].n, expo);
+    double rem[kFitBatchMax];
+    int used = 0;
+    for (int b = 0; b < count; ++b) {
+        const double share = total * std::pow((double)problems[b].n, expo) / wsum;
+        int k = (int)share;
+        const int cap = useful_ctas(problems[b].n, nt);
+        if (k < 1) k = 1;
+        if (k > cap) k = cap;
+        ctas[b] = k;
+        rem[b] = k < cap ? share - (double)k : -1.0;
+        used += k;
+    }
+    while (used < total) {
+        int best = -1;
+        for (int b = 0; b < count; ++b)
+            if (rem[b] >= 0.0 && ctas[b] < useful_ctas(problems[b].n, nt) &&
+                (best < 0 || rem[b] > rem[best]))
+                best = b;
+        if (best < 0) break;
+        ++ctas[best];
+        rem[best] -= 1.0;
+        ++used;
+    }
+    while (used > total) {                 // at least one CTA each overshot the capacity
+        int best = -1;
+        for (int b = 0; b < count; ++b)
+            if (ctas[b] > 1 && (best < 0 || ctas[b] > ctas[best])) best = b;
+        if (best < 0) break;
+        --ctas[best];
+        --used;
+    }
+}
+
+}  // namespace
+
+extern "C" emdq_status emdq_fit_batch_ex(const emdq_fit_problem *problems, int count,
+                                         const emdq_params *prm, const int *ctas, void *workspace,
+                                         size_t workspace_bytes, void *stream)
 {
     emdq_params P;
     emdq_default_params(&P);
@@ -792,31 +884,32 @@ extern "C" emdq_status emdq_fit_batch(const emdq_fit_problem *problems, int coun
     if (D.device < 0) return EMDQ_ECUDA;
     const size_t smem = fit_smem_bytes(max_n);
     if (smem > D.smem_optin) return EMDQ_ENOTSUP;
-    static std::mutex mu;
-    static int attr_set_dev = -1;
+    int nt = 0, cap = 0;
+    if (!fit_shape(true, smem, nt, cap)) return EMDQ_ECUDA;
+    if (count > cap) return EMDQ_ENOTSUP;     // more problems than co-resident CTAs
+
+    FitBatch B;
+    B.count = count;
     {
-        std::lock_guard<std::mutex> g(mu);
-        if (attr_set_dev != D.device) {
-            if (cudaFuncSetAttribute(emdq_fit_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)fit_smem_bytes(kFitMaxN)) != cudaSuccess)
-                return EMDQ_ECUDA;
-            attr_set_dev = D.device;
+        int split[kFitBatchMax];
+        if (ctas) {
+            int sum = 0;
+            for (int b = 0; b < count; ++b) {
+                if (ctas[b] < 1 || ctas[b] > kFitMaxGrid) return EMDQ_EINVAL;
+                sum += ctas[b];
+            }
+            if (sum > cap) return EMDQ_EINVAL;     // would not be co-resident
+            for (int b = 0; b < count; ++b) split[b] = ctas[b];
+        } else {
+            split_ctas(problems, count, cap, nt, 2.0, split);   // EM work grows as n^2
         }
+        B.first[0] = 0;
+        for (int b = 0; b < count; ++b) B.first[b + 1] = B.first[b] + split[b];
     }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emdq_fit_batch_kernel, kFitThreads,
-                                                      smem) != cudaSuccess || per_sm < 1)
-        return EMDQ_ECUDA;
-    int group = (D.sms * per_sm) / count;
-    const int want = (max_n + kFitWarps - 1) / kFitWarps;
-    if (group > want) group = want;
-    if (group > kFitMaxGrid) group = kFitMaxGrid;
-    if (group < 1) return EMDQ_ENOTSUP;    // more problems than co-resident CTAs
 
     char *ws = static_cast<char *>(workspace);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(ws, 0, 256 * (size_t)count, st) != cudaSuccess) return EMDQ_ECUDA;
-    FitBatch B;
     size_t off = 256 * (size_t)count;
     const double log2e = 1.4426950408889634074;
     for (int b = 0; b < count; ++b) {
@@ -846,8 +939,8 @@ extern "C" emdq_status emdq_fit_batch(const emdq_fit_problem *problems, int coun
         off += batch_body_bytes(q.n);
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(group * count);
-    cfg.blockDim = dim3(kFitThreads);
+    cfg.gridDim = dim3(B.first[count]);
+    cfg.blockDim = dim3(nt);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
@@ -855,8 +948,85 @@ extern "C" emdq_status emdq_fit_batch(const emdq_fit_problem *problems, int coun
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, emdq_fit_batch_kernel, B, group) != cudaSuccess) return EMDQ_ECUDA;
+    const cudaError_t e = nt == kFitThreadsSmall
+                              ? cudaLaunchKernelEx(&cfg, emdq_fit_batch_kernel<kFitThreadsSmall>, B)
+                              : cudaLaunchKernelEx(&cfg, emdq_fit_batch_kernel<kFitThreadsLarge>, B);
+    if (e != cudaSuccess) return EMDQ_ECUDA;
     return EMDQ_OK;
+}
+
+extern "C" emdq_status emdq_fit_batch(const emdq_fit_problem *problems, int count,
+                                      const emdq_params *prm, void *workspace,
+                                      size_t workspace_bytes, void *stream)
+{
+    return emdq_fit_batch_ex(problems, count, prm, nullptr, workspace, workspace_bytes, stream);
+}
+
+extern "C" int emdq_fit_batch_capacity(const emdq_fit_problem *problems, int count)
+{
+    if (!problems || count < 1 || count > kFitBatchMax) return 0;
+    int max_n = 0;
+    for (int b = 0; b < count; ++b) max_n = problems[b].n > max_n ? problems[b].n : max_n;
+    if (max_n < 1 || max_n > kFitMaxN) return 0;
+    int nt = 0, cap = 0;
+    return fit_shape(true, fit_smem_bytes(max_n), nt, cap) ? cap : 0;
+}
+
+extern "C" emdq_status emdq_fit_batch_autotune(const emdq_fit_problem *problems, int count,
+                                               const emdq_params *prm, void *workspace,
+                                               size_t workspace_bytes, void *stream, int reps,
+                                               int *ctas_out, float *ms_out)
+{
+    if (!ctas_out || reps < 1 || reps > 100) return EMDQ_EINVAL;
+    if (!problems || count < 1 || count > kFitBatchMax) return EMDQ_EINVAL;
+    int max_n = 0;
+    for (int b = 0; b < count; ++b) max_n = problems[b].n > max_n ? problems[b].n : max_n;
+    if (max_n < 3 || max_n > kFitMaxN) return EMDQ_ENOTSUP;
+    int nt = 0, cap = 0;
+    if (!fit_shape(true, fit_smem_bytes(max_n), nt, cap)) return EMDQ_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return EMDQ_EINVAL;                    // times launches: not inside a capture
+    // candidates: CTAs in proportion to n^e, and all CTAs or the useful ones only
+    const double expos[] = {0.0, 1.0, 1.5, 2.0, 2.5, 3.0};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return EMDQ_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return EMDQ_ECUDA;
+    }
+    float best = -1.f;
+    emdq_status rc = EMDQ_OK;
+    int split[kFitBatchMax];
+    for (double expo : expos) {
+        split_ctas(problems, count, cap, nt, expo, split);
+        // one untimed launch, then the best of `reps`
+        rc = emdq_fit_batch_ex(problems, count, prm, split, workspace, workspace_bytes, stream);
+        if (rc != EMDQ_OK) break;
+        float t_best = -1.f;
+        for (int r = 0; r < reps && rc == EMDQ_OK; ++r) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) { rc = EMDQ_ECUDA; break; }
+            rc = emdq_fit_batch_ex(problems, count, prm, split, workspace, workspace_bytes, stream);
+            if (rc != EMDQ_OK) break;
+            float ms = 0.f;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = EMDQ_ECUDA;
+                break;
+            }
+            if (t_best < 0.f || ms < t_best) t_best = ms;
+        }
+        if (rc != EMDQ_OK) break;
+        if (best < 0.f || t_best < best) {
+            best = t_best;
+            for (int b = 0; b < count; ++b) ctas_out[b] = split[b];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == EMDQ_OK && ms_out) *ms_out = best;
+    return rc;
 }
 
 // ------------------------------------------------------------------ emdq_fit_noalloc ---

@@ -20,4 +20,6 @@ from .scene import (  # noqa: F401
     canvas_origin,
     workload,
     WORKLOADS,
+    mixed_pairs,
+    MIXED_SIZES,
 )

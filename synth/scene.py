@@ -260,3 +260,25 @@ def workload(name: str, seed: int = 0) -> tuple[Scene, dict]:
     cfg = dict(WORKLOADS[name])
     sc = make_scene(seed, cfg['w'], cfg['h'], cfg['channels'], drift=cfg['drift'])
     return sc, cfg
+
+
+# Mixed-size batch: independent frame pairs of uneven sizes and match counts.
+MIXED_SIZES = ((640, 480), (1280, 720), (1280, 1024), (1920, 1080))
+
+
+def mixed_pairs(seed: int, count: int = 64, channels: int = 3, n_range=(100, 3000),
+                outlier_range=(0.10, 0.40), noise: float = 1.0):
+    """`count` independent pairs: frame size uniform over MIXED_SIZES, N uniform in
+    n_range (inclusive), outlier rate uniform in outlier_range; each pair its own scene
+    (reference frame and frame 1).  Returns a list of dicts (scene, src, dst, inlier, n,
+    outliers)."""
+    g = _rng(seed, 5)
+    pairs = []
+    for b in range(count):
+        w, h = MIXED_SIZES[int(g.integers(0, len(MIXED_SIZES)))]
+        n = int(g.integers(n_range[0], n_range[1] + 1))
+        outl = float(g.uniform(*outlier_range))
+        sc = make_scene(seed * 1000 + b, w, h, channels)
+        s, d, inl = make_matches(sc, 1, n, outl, noise)
+        pairs.append(dict(scene=sc, src=s, dst=d, inlier=inl, n=n, outliers=outl))
+    return pairs

@@ -1,0 +1,38 @@
+"""The input generators (no method arithmetic): the mixed-size batch recipe and the
+sequence workloads have the sizes, counts and rates they are stated to have."""
+import numpy as np
+
+from synth import MIXED_SIZES, WORKLOADS, make_matches, mixed_pairs, workload
+
+
+def test_mixed_pairs_recipe():
+    pairs = mixed_pairs(3, 64)
+    assert len(pairs) == 64
+    sizes = {(p['scene'].w, p['scene'].h) for p in pairs}
+    assert sizes <= set(MIXED_SIZES) and len(sizes) == len(MIXED_SIZES)
+    ns = np.array([p['n'] for p in pairs])
+    assert ns.min() >= 100 and ns.max() <= 3000 and ns.std() > 400
+    for p in pairs:
+        assert p['src'].shape == (p['n'], 2) and p['dst'].shape == (p['n'], 2)
+        assert 0.10 <= p['outliers'] <= 0.40
+        frac = 1.0 - p['inlier'].mean()
+        assert abs(frac - p['outliers']) <= 1.5 / p['n'] + 1e-9
+        w, h = p['scene'].w, p['scene'].h
+        assert (p['src'][:, 0] >= 0).all() and (p['src'][:, 0] <= w - 1).all()
+        assert (p['src'][:, 1] >= 0).all() and (p['src'][:, 1] <= h - 1).all()
+
+
+def test_mixed_pairs_are_seeded():
+    a, b = mixed_pairs(5, 4), mixed_pairs(5, 4)
+    for x, y in zip(a, b):
+        assert np.array_equal(x['src'], y['src']) and np.array_equal(x['dst'], y['dst'])
+    c = mixed_pairs(6, 4)
+    assert not np.array_equal(a[0]['src'][:10], c[0]['src'][:10])
+
+
+def test_sequence_workload_shape():
+    sc, cfg = workload('seq1280', seed=0)
+    assert (sc.w, sc.h, sc.channels) == (1280, 1024, 3) and cfg['frames'] == 100
+    s, d, inl = make_matches(sc, 5, cfg['n'], cfg['outliers'], cfg['noise'])
+    assert s.shape == (1000, 2) and abs((1 - inl.mean()) - 0.3) < 0.01
+    assert set(WORKLOADS) >= {'pair640', 'seq1280', 'warm2000'}
