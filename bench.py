@@ -36,7 +36,12 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic per launch from an ncu capture of each kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by kernel and tied to the hash of the source it was
 # measured on: a changed kernel reports null until it is captured again.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # emdq_field on one 1280x1024 frame (N = 1000): field_tc_prep_kernel 0.070 MB read +
+    # field_tc_kernel 12.215 MB read, nothing written back within either kernel (ncu --set
+    # full on 16 frames of the sequence, one launch each)
+    'field': dict(bytes=12285184, file='field_tc.cu', src='2a3ebe5d91de05de'),
+}
 
 
 def _src_hash(name: str) -> str:
@@ -564,7 +569,8 @@ def run_gpu(args, ws, rank, local):
                 torch.cuda.synchronize()
                 nz += [int((fit_outs_all[bi % nbuf][j]['c'] > 0).sum().item()) for j in range(len(ks))]
             flops = 2.0 * 6 * win_px * float(np.mean(nz))
-            roof = dict(bound='tensor', kernel='field_tc_kernel (operand prologue included)',
+            roof = dict(bound='tensor',
+                        kernel='emdq_field: field_tc_prep_kernel + field_tc_kernel (one call, timed together)',
                         work='2 x 6 x window pixels x matches of nonzero weight',
                         achieved=flops / (np.mean(field_ms) * 1e-3) / 1e12,
                         peak=peaks['bf16_tflops'], unit='TFLOP/s',
@@ -583,7 +589,7 @@ def run_gpu(args, ws, rank, local):
                     peak=peaks['hbm_gbs'], unit='GB/s', peak_source=peaks['source'] + ' copy',
                     launches=len(warp_ms), mean_launch_ms=float(np.mean(warp_ms)))
     roof['frac'] = roof['achieved'] / roof['peak']
-    tr = NCU_TRAFFIC.get(roof['kernel'])
+    tr = NCU_TRAFFIC.get(dom if dom != 'field' or prec == emdq.BF16 else 'field_fp32')
     roof['traffic'] = tr['bytes'] if tr and tr['src'] == _src_hash(tr['file']) else None
 
     line = dict(
