@@ -78,6 +78,9 @@ def parse_args():
     ap.add_argument('--no-graph', action='store_true',
                     help='issue every call each step (default: the pass is captured once into a '
                          'CUDA graph and replayed, removing per-call launch overhead)')
+    ap.add_argument('--no-pipeline', action='store_true',
+                    help='field and warp of every frame on one stream (default: the warp of frame k '
+                         'on a second stream, beside the field of frame k + 1)')
     ap.add_argument('--overlap', action='store_true',
                     help='run the next batch of fits on a second stream while the current batch is '
                          'blended (default: one stream; the cooperative fit launch occupies every '
@@ -270,16 +273,52 @@ def run_gpu(args, ws, rank, local):
     warm_params = emdq.load_warmstart_params(dev) if warm else None
     warm_p0 = [[torch.empty(n, device=dev) for _ in range(B)] for _ in range(nbuf)]
 
-    def field_and_warp(fr, s_, g, fo, ev_field=None):
+    # field / warp pipeline: frame k's field (main stream) into buffer k % 2, its warp on
+    # the warp stream after that field; warps stay in frame order (the blend is
+    # order-dependent) while the field of frame k + 1 runs beside the warp of frame k
+    piped = not fused and not args.no_pipeline
+    warp_stream = torch.cuda.Stream(device=dev) if piped else None
+    disp_bufs = [disp_buf] + ([torch.empty_like(disp_buf)] if piped else [])
+    field_wss = [field_ws] + ([torch.empty_like(field_ws)] if piped else [])
+    slot_free = [None, None]        # warp-done event of the frame that last used each slot
+    frame_no = [0]
+
+    def field_and_warp(fr, s_, g, fo, ev3=None):
+        """ev3: (field done, warp start, warp done) events, or None."""
         if fused:
             emdq.emdq_mosaic(fo['q'], fo['c'], s_, g, alpha, fr, canvas, origin, workspace=field_ws)
-            if ev_field is not None: ev_field.record(stream)
-        else:
+            if ev3 is not None:
+                for e in ev3: e.record(stream)
+            return
+        if not piped:
             disp = disp_buf[: g[2] * g[3] * 2].view(g[3], g[2], 2)
             emdq.emdq_field(fo['q'], fo['c'], s_, g, alpha, precision=prec, out=disp,
                             workspace=field_ws)
-            if ev_field is not None: ev_field.record(stream)
+            if ev3 is not None:
+                ev3[0].record(stream)
+                ev3[1].record(stream)
             emdq.mosaic_warp(fr, disp, g, canvas, origin)
+            if ev3 is not None: ev3[2].record(stream)
+            return
+        slot = frame_no[0] % 2
+        frame_no[0] += 1
+        if slot_free[slot] is not None:
+            stream.wait_event(slot_free[slot])
+        disp = disp_bufs[slot][: g[2] * g[3] * 2].view(g[3], g[2], 2)
+        emdq.emdq_field(fo['q'], fo['c'], s_, g, alpha, precision=prec, out=disp,
+                        workspace=field_wss[slot])
+        # dependencies through plain events (a captured graph cannot wait on the timing
+        # events, which are external event nodes there)
+        fdone = torch.cuda.Event()
+        fdone.record(stream)
+        if ev3 is not None: ev3[0].record(stream)
+        warp_stream.wait_event(fdone)
+        if ev3 is not None: ev3[1].record(warp_stream)
+        emdq.mosaic_warp(fr, disp, g, canvas, origin, stream=warp_stream)
+        wdone = torch.cuda.Event()
+        wdone.record(warp_stream)
+        if ev3 is not None: ev3[2].record(warp_stream)
+        slot_free[slot] = wdone
 
     def fit_batch(bi, ks, s_of, d_of, ev=None):
         """The fits of batch bi (frames ks) on the fit stream; returns its done event.
@@ -309,8 +348,11 @@ def run_gpu(args, ws, rank, local):
         outs = fit_outs_all[bi % nbuf]
         if ev: ev[3].record(stream)
         for j, k in enumerate(ks):
-            field_and_warp(fr_of(k), s_of(k), grids[k], outs[j], ev[4 + 2 * j] if ev else None)
-            if ev: ev[5 + 2 * j].record(stream)
+            field_and_warp(fr_of(k), s_of(k), grids[k], outs[j],
+                           ev[4 + 3 * j: 7 + 3 * j] if ev else None)
+        if piped:
+            stream.wait_stream(warp_stream)       # the batch is blended when its warps are
+            slot_free[0] = slot_free[1] = None
         for j, k in enumerate(ks):
             infos[k].copy_(outs[j]['info'])
         blended = torch.cuda.Event()
@@ -357,29 +399,30 @@ def run_gpu(args, ws, rank, local):
         # external: recorded as real event nodes when captured into a CUDA graph, so they
         # still time the replay
         kw = dict(external=True) if external else {}
-        return [[torch.cuda.Event(enable_timing=True, **kw) for _ in range(4 + 2 * len(ks))]
+        return [[torch.cuda.Event(enable_timing=True, **kw) for _ in range(4 + 3 * len(ks))]
                 for ks in batches]
 
     # per batch e[0]: its fits issued and e[1]: warm start done, e[2]: fits done (all on the
-    # fit stream); e[3]: its blend starts (main stream, after the fits); e[4 + 2j]: frame j's
-    # field done, e[5 + 2j]: its warp done.  Frame latency = e[0] -> e[5 + 2j].  Kernel
-    # durations are taken on the stream each kernel runs on.
+    # fit stream); e[3]: its blend starts (main stream, after the fits); e[4 + 3j]: frame j's
+    # field done (main stream), e[5 + 3j] / e[6 + 3j]: its warp starts / is done (warp
+    # stream).  Frame latency = e[0] -> e[6 + 3j].  Kernel durations are taken on the stream
+    # each kernel runs on.
     lat_ms, pass_ms = [], []
     warm_ms, fit_ms, field_ms, warp_ms = [], [], [], []
     fit_launch_frames = []
 
     def collect(step):
         for bi, e in enumerate(step):
-            nb = (len(e) - 4) // 2
+            nb = (len(e) - 4) // 3
             warm_ms.append(e[0].elapsed_time(e[1]))
             fit_ms.append(e[1].elapsed_time(e[2]))
             fit_launch_frames.append(batches[bi])
             prev = e[3]
             for j in range(nb):
-                field_ms.append(prev.elapsed_time(e[4 + 2 * j]))
-                warp_ms.append(e[4 + 2 * j].elapsed_time(e[5 + 2 * j]))
-                lat_ms.append(e[0].elapsed_time(e[5 + 2 * j]))
-                prev = e[5 + 2 * j]
+                field_ms.append(prev.elapsed_time(e[4 + 3 * j]))
+                warp_ms.append(e[5 + 3 * j].elapsed_time(e[6 + 3 * j]))
+                lat_ms.append(e[0].elapsed_time(e[6 + 3 * j]))
+                prev = e[4 + 3 * j]
 
     # CUDA graph of one pass (one stream): captured once, replayed every step
     graph, graph_note, gevs = None, None, None
@@ -613,6 +656,7 @@ def run_gpu(args, ws, rank, local):
         speedup_vs_plain_fp32_gpu=(None if plain is None else
                                    job_mpix_per_s(ws, total_frames, sc.w, sc.h, total_ms) / plain['value']),
         fit_status=statuses,
+        canvas_sha256=hashlib.sha256(canvas.cpu().numpy().tobytes()).hexdigest()[:16],
     )
     if not args.no_cpu_baseline:
         line['cpu_baseline'] = cpu_baseline(args, budget_s=12.0)
@@ -686,22 +730,41 @@ def run_gpu_mixed(args, ws, rank, local):
     ctas, tune_ms = emdq.fit_batch_autotune(fit_probs, reps=2, outs=[x['out'] for x in P],
                                             workspace=batch_ws)
 
+    # field of pair b + 1 (main stream) beside the warp of pair b (warp stream), field
+    # outputs double-buffered
+    warp_stream = torch.cuda.Stream(device=dev)
+    disp_bufs = [disp_buf, torch.empty_like(disp_buf)]
+    field_wss = [field_ws, torch.empty_like(field_ws)]
+
     def one_pass(ev=None):
-        # ev[0] start, ev[1] warm start done, ev[2] fits done, ev[3 + 2b] / ev[4 + 2b]: pair
-        # b's field / warp done
+        # ev[0] start, ev[1] warm start done, ev[2] fits done, then per pair b: ev[3 + 3b]
+        # field done, ev[4 + 3b] / ev[5 + 3b] warp start / done (warp stream)
+        main = torch.cuda.current_stream()
         if ev: ev[0].record()
         emdq.warm_start(probs_sd, warm_params, outs=[x['p0'] for x in P])
         if ev: ev[1].record()
         emdq.emdq_fit_batch(fit_probs, outs=[x['out'] for x in P], workspace=batch_ws, ctas=ctas)
         if ev: ev[2].record()
+        free = [None, None]
         for b, x in enumerate(P):
             g = x['grid']
-            disp = disp_buf[: g[2] * g[3] * 2].view(g[3], g[2], 2)
+            slot = b % 2
+            if free[slot] is not None:
+                main.wait_event(free[slot])
+            disp = disp_bufs[slot][: g[2] * g[3] * 2].view(g[3], g[2], 2)
             emdq.emdq_field(x['out']['q'], x['out']['c'], x['src'], g, x['alpha'], precision=emdq.BF16,
-                            out=disp, workspace=field_ws)
-            if ev: ev[3 + 2 * b].record()
-            emdq.mosaic_warp(x['frame'], disp, g, x['canvas'], x['origin'])
-            if ev: ev[4 + 2 * b].record()
+                            out=disp, workspace=field_wss[slot])
+            fdone = torch.cuda.Event()
+            fdone.record(main)
+            if ev: ev[3 + 3 * b].record(main)
+            warp_stream.wait_event(fdone)
+            if ev: ev[4 + 3 * b].record(warp_stream)
+            emdq.mosaic_warp(x['frame'], disp, g, x['canvas'], x['origin'], stream=warp_stream)
+            wdone = torch.cuda.Event()
+            wdone.record(warp_stream)
+            if ev: ev[5 + 3 * b].record(warp_stream)
+            free[slot] = wdone
+        main.wait_stream(warp_stream)
         for b, x in enumerate(P):
             infos[b].copy_(x['out']['info'])
 
@@ -712,7 +775,7 @@ def run_gpu_mixed(args, ws, rank, local):
         one_pass()
         torch.cuda.synchronize()
         w += 1
-    n_ev = 3 + 2 * len(P)
+    n_ev = 3 + 3 * len(P)
     graph, graph_note = None, None
     gev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(n_ev)]
     if not args.no_graph:
@@ -733,9 +796,9 @@ def run_gpu_mixed(args, ws, rank, local):
         fit_ms.append(ev[1].elapsed_time(ev[2]))
         prev = ev[2]
         for b in range(len(P)):
-            field_ms.append(prev.elapsed_time(ev[3 + 2 * b]))
-            warp_ms.append(ev[3 + 2 * b].elapsed_time(ev[4 + 2 * b]))
-            prev = ev[4 + 2 * b]
+            field_ms.append(prev.elapsed_time(ev[3 + 3 * b]))
+            warp_ms.append(ev[4 + 3 * b].elapsed_time(ev[5 + 3 * b]))
+            prev = ev[3 + 3 * b]
 
     outer = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
              for _ in range(args.steps)]
@@ -815,7 +878,7 @@ def run_gpu_mixed(args, ws, rank, local):
         config=mixed_config(args, ws, pairs, ctas),
         kernel_ms_per_step={k: v / args.steps for k, v in totals.items()},
         path='learned warm start (one launch) + emdq_fit_batch (one launch, autotuned CTA split) + '
-             'per pair emdq_field (bf16) + mosaic_warp' +
+             'per pair emdq_field (bf16), its mosaic_warp on a second stream beside the next field' +
              (', the step replayed from one CUDA graph' if graph is not None else ''),
         cuda_graph=graph is not None, **({'cuda_graph_note': graph_note} if graph_note else {}),
         autotune_fit_ms=tune_ms, mean_em_iters=float(np.mean(iters)), roofline=roof,

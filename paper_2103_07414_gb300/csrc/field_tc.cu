@@ -249,8 +249,6 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(
     // everything above is independent of the prep kernel (programmatic dependent launch);
     // its operands, column count and reference row are read only after this wait
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    // the warp launched after this kernel may start its set-up now (it waits likewise)
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // 64-match slices along K: the prep kernel's column count (the matches of nonzero
     // weight), a whole number of slices, at least one
     const int nchunks = *kcount / kTcK;

@@ -254,8 +254,8 @@ __device__ void mstep_rows(const FitArgs &A, const FitSmem &S, const int *rows, 
             const float2 ou = __fmul2_rn(om2, u);
             const float2 ov = __fmul2_rn(om2, v);
             W[r] += om;
-            su[r] = __fadd2_rn(su[r], ou);
-            sv[r] = __fadd2_rn(sv[r], ov);
+            su[r] = __ffma2_rn(om2, u, su[r]);
+            sv[r] = __ffma2_rn(om2, v, sv[r]);
             vxp[r] = __ffma2_rn(ou, u, vxp[r]);            // |vector(C_0)|^2 about the shift
             vyp[r] = __ffma2_rn(ov, v, vyp[r]);            // |vector(C_t)|^2 about the shift
             dotp[r] = __ffma2_rn(ou, v, dotp[r]);          // (c00, c11)

@@ -20,9 +20,6 @@ __global__ void __launch_bounds__(kWarpThreadsX) mosaic_warp_kernel(
     const float2 *__restrict__ disp, int gx0, int gy0, int gw, int gh,
     uchar4 *__restrict__ canvas, int cpitch4, int ox, int oy)
 {
-    // launched as a programmatic dependent of the field kernel before it: nothing the field
-    // writes is read before this wait
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int y = blockIdx.y;
     const int xb = blockIdx.x * (kWarpThreadsX * kWarpPix) + threadIdx.x;
     float2 d[kWarpPix];
@@ -93,26 +90,15 @@ extern "C" emdq_status mosaic_warp(const uint8_t *frame, int fw, int fh, int cha
     dim3 grid((grid_w + kWarpThreadsX * kWarpPix - 1) / (kWarpThreadsX * kWarpPix), grid_h);
     auto *cv = reinterpret_cast<uchar4 *>(canvas);
     const auto *d = reinterpret_cast<const float2 *>(disp);
-    // programmatic dependent launch: may start while the kernel before it finishes (it
-    // waits for that kernel's results before reading the field)
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(kWarpThreadsX);
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    const uint8_t *fr = frame;
-    const int pitch4 = canvas_pitch / 4;
-    const cudaError_t e =
-        channels == 3
-            ? cudaLaunchKernelEx(&cfg, mosaic_warp_kernel<3>, fr, fw, fh, frame_pitch, d, grid_x0,
-                                 grid_y0, grid_w, grid_h, cv, pitch4, origin_x, origin_y)
-            : cudaLaunchKernelEx(&cfg, mosaic_warp_kernel<1>, fr, fw, fh, frame_pitch, d, grid_x0,
-                                 grid_y0, grid_w, grid_h, cv, pitch4, origin_x, origin_y);
-    return e == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
+    if (channels == 3)
+        mosaic_warp_kernel<3><<<grid, kWarpThreadsX, 0, st>>>(
+            frame, fw, fh, frame_pitch, d, grid_x0, grid_y0, grid_w, grid_h, cv,
+            canvas_pitch / 4, origin_x, origin_y);
+    else
+        mosaic_warp_kernel<1><<<grid, kWarpThreadsX, 0, st>>>(
+            frame, fw, fh, frame_pitch, d, grid_x0, grid_y0, grid_w, grid_h, cv,
+            canvas_pitch / 4, origin_x, origin_y);
+    return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }
 
 extern "C" emdq_status mosaic_insert_reference(const uint8_t *frame, int fw, int fh,
