@@ -37,10 +37,10 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_write.sum), keyed by kernel and tied to the hash of the source it was
 # measured on: a changed kernel reports null until it is captured again.
 NCU_TRAFFIC = {
-    # emdq_field on one 1280x1024 frame (N = 1000): field_tc_prep_kernel 0.070 MB read +
-    # field_tc_kernel 12.215 MB read, nothing written back within either kernel (ncu --set
-    # full on 16 frames of the sequence, one launch each)
-    'field': dict(bytes=12285184, file='field_tc.cu', src='2a3ebe5d91de05de'),
+    # emdq_field on one 1280x1024 frame (N = 1000): field_tc_prep_kernel 70,656 B read +
+    # field_tc_kernel 12,215,040 B read, nothing written back within either kernel (ncu
+    # --metrics dram__bytes_read.sum,dram__bytes_write.sum on frames of the sequence)
+    'field': dict(bytes=12285696, file='field_tc.cu', src='3347988fe751ff84'),
 }
 
 
