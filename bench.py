@@ -78,6 +78,8 @@ def parse_args():
     ap.add_argument('--no-graph', action='store_true',
                     help='issue every call each step (default: the pass is captured once into a '
                          'CUDA graph and replayed, removing per-call launch overhead)')
+    ap.add_argument('--field-group', type=int, default=4,
+                    help='frames per emdq_field_batch call (BF16 field, pipelined path)')
     ap.add_argument('--no-pipeline', action='store_true',
                     help='field and warp of every frame on one stream (default: the warp of frame k '
                          'on a second stream, beside the field of frame k + 1)')
@@ -273,51 +275,68 @@ def run_gpu(args, ws, rank, local):
     warm_params = emdq.load_warmstart_params(dev) if warm else None
     warm_p0 = [[torch.empty(n, device=dev) for _ in range(B)] for _ in range(nbuf)]
 
-    # field / warp pipeline: frame k's field (main stream) into buffer k % 2, its warp on
-    # the warp stream after that field; warps stay in frame order (the blend is
-    # order-dependent) while the field of frame k + 1 runs beside the warp of frame k
+    # field / warp pipeline: the fields of a group of frames (one emdq_field_batch call on the
+    # main stream) into buffer set g % 2, their warps on the warp stream after that call, in
+    # frame order (the blend is order-dependent) while the next group's fields run
     piped = not fused and not args.no_pipeline
+    G = max(1, min(16, args.field_group)) if piped and prec == emdq.BF16 else 1
     warp_stream = torch.cuda.Stream(device=dev) if piped else None
-    disp_bufs = [disp_buf] + ([torch.empty_like(disp_buf)] if piped else [])
-    field_wss = [field_ws] + ([torch.empty_like(field_ws)] if piped else [])
-    slot_free = [None, None]        # warp-done event of the frame that last used each slot
-    frame_no = [0]
+    if piped and prec == emdq.BF16:
+        zq = torch.zeros((n, 8), device=dev)
+        zc = torch.zeros(n, device=dev)
+        zs = torch.zeros((n, 2), device=dev)
+        gws = emdq.field_batch_workspace_size([(zq, zc, zs, (0, 0, max_gw, max_gh), alpha)] * G)
+        grp_ws = [torch.empty(gws, dtype=torch.uint8, device=dev) for _ in range(2)]
+        grp_disp = [[torch.empty(max_gw * max_gh * 2, dtype=torch.float32, device=dev)
+                     for _ in range(G)] for _ in range(2)]
+    elif piped:
+        grp_ws = [field_ws, torch.empty_like(field_ws)]
+        grp_disp = [[disp_buf], [torch.empty_like(disp_buf)]]
+    slot_free = [None, None]        # warp-done event of the group that last used each set
+    group_no = [0]
 
     def field_and_warp(fr, s_, g, fo, ev3=None):
-        """ev3: (field done, warp start, warp done) events, or None."""
+        """One frame, not pipelined.  ev3: (field done, warp start, warp done) events."""
         if fused:
             emdq.emdq_mosaic(fo['q'], fo['c'], s_, g, alpha, fr, canvas, origin, workspace=field_ws)
             if ev3 is not None:
                 for e in ev3: e.record(stream)
             return
-        if not piped:
-            disp = disp_buf[: g[2] * g[3] * 2].view(g[3], g[2], 2)
-            emdq.emdq_field(fo['q'], fo['c'], s_, g, alpha, precision=prec, out=disp,
-                            workspace=field_ws)
-            if ev3 is not None:
-                ev3[0].record(stream)
-                ev3[1].record(stream)
-            emdq.mosaic_warp(fr, disp, g, canvas, origin)
-            if ev3 is not None: ev3[2].record(stream)
-            return
-        slot = frame_no[0] % 2
-        frame_no[0] += 1
+        disp = disp_buf[: g[2] * g[3] * 2].view(g[3], g[2], 2)
+        emdq.emdq_field(fo['q'], fo['c'], s_, g, alpha, precision=prec, out=disp,
+                        workspace=field_ws)
+        if ev3 is not None:
+            ev3[0].record(stream)
+            ev3[1].record(stream)
+        emdq.mosaic_warp(fr, disp, g, canvas, origin)
+        if ev3 is not None: ev3[2].record(stream)
+
+    def fields_then_warps(frs, ss, gs, fos, evs3=None):
+        """A group of frames, pipelined: one batched field call, then the warps."""
+        slot = group_no[0] % 2
+        group_no[0] += 1
         if slot_free[slot] is not None:
             stream.wait_event(slot_free[slot])
-        disp = disp_bufs[slot][: g[2] * g[3] * 2].view(g[3], g[2], 2)
-        emdq.emdq_field(fo['q'], fo['c'], s_, g, alpha, precision=prec, out=disp,
-                        workspace=field_wss[slot])
+        disps = [grp_disp[slot][i][: g[2] * g[3] * 2].view(g[3], g[2], 2) for i, g in enumerate(gs)]
+        if prec == emdq.BF16:
+            emdq.emdq_field_batch([(fo['q'], fo['c'], s_, g, alpha) for fo, s_, g in zip(fos, ss, gs)],
+                                  outs=disps, workspace=grp_ws[slot])
+        else:
+            emdq.emdq_field(fos[0]['q'], fos[0]['c'], ss[0], gs[0], alpha, precision=prec,
+                            out=disps[0], workspace=grp_ws[slot])
         # dependencies through plain events (a captured graph cannot wait on the timing
         # events, which are external event nodes there)
         fdone = torch.cuda.Event()
         fdone.record(stream)
-        if ev3 is not None: ev3[0].record(stream)
+        if evs3 is not None:
+            for e3 in evs3: e3[0].record(stream)
         warp_stream.wait_event(fdone)
-        if ev3 is not None: ev3[1].record(warp_stream)
-        emdq.mosaic_warp(fr, disp, g, canvas, origin, stream=warp_stream)
+        for i in range(len(frs)):
+            if evs3 is not None: evs3[i][1].record(warp_stream)
+            emdq.mosaic_warp(frs[i], disps[i], gs[i], canvas, origin, stream=warp_stream)
+            if evs3 is not None: evs3[i][2].record(warp_stream)
         wdone = torch.cuda.Event()
         wdone.record(warp_stream)
-        if ev3 is not None: ev3[2].record(warp_stream)
         slot_free[slot] = wdone
 
     def fit_batch(bi, ks, s_of, d_of, ev=None):
@@ -347,9 +366,16 @@ def run_gpu(args, ws, rank, local):
         stream.wait_event(fit_done)
         outs = fit_outs_all[bi % nbuf]
         if ev: ev[3].record(stream)
-        for j, k in enumerate(ks):
-            field_and_warp(fr_of(k), s_of(k), grids[k], outs[j],
-                           ev[4 + 3 * j: 7 + 3 * j] if ev else None)
+        if piped:
+            for j0 in range(0, len(ks), G):
+                sub = list(range(j0, min(len(ks), j0 + G)))
+                fields_then_warps([fr_of(ks[j]) for j in sub], [s_of(ks[j]) for j in sub],
+                                  [grids[ks[j]] for j in sub], [outs[j] for j in sub],
+                                  [ev[4 + 3 * j: 7 + 3 * j] for j in sub] if ev else None)
+        else:
+            for j, k in enumerate(ks):
+                field_and_warp(fr_of(k), s_of(k), grids[k], outs[j],
+                               ev[4 + 3 * j: 7 + 3 * j] if ev else None)
         if piped:
             stream.wait_stream(warp_stream)       # the batch is blended when its warps are
             slot_free[0] = slot_free[1] = None
@@ -613,7 +639,8 @@ def run_gpu(args, ws, rank, local):
                 nz += [int((fit_outs_all[bi % nbuf][j]['c'] > 0).sum().item()) for j in range(len(ks))]
             flops = 2.0 * 6 * win_px * float(np.mean(nz))
             roof = dict(bound='tensor',
-                        kernel='emdq_field: field_tc_prep_kernel + field_tc_kernel (one call, timed together)',
+                        kernel=('emdq_field_batch' if piped else 'emdq_field') +
+                               ': field_tc_prep_kernel + field_tc_kernel (timed together, per frame)',
                         work='2 x 6 x window pixels x matches of nonzero weight',
                         achieved=flops / (np.mean(field_ms) * 1e-3) / 1e12,
                         peak=peaks['bf16_tflops'], unit='TFLOP/s',
@@ -645,10 +672,11 @@ def run_gpu(args, ws, rank, local):
         kernel_ms_per_step={k: v / args.steps for k, v in kernel_total.items()},
         path=(('learned warm start + ' if warm else '') + ('emdq_fit_batch' if B > 1 else 'emdq_fit') +
               (' + emdq_mosaic (fused BF16 field and warp)' if fused else
-               f' + emdq_field ({args.precision}) + mosaic_warp') +
+               (f' + emdq_field_batch ({G} frames per call, bf16) + mosaic_warp on a second stream'
+                if piped and prec == emdq.BF16 else f' + emdq_field ({args.precision}) + mosaic_warp')) +
               (', fits of the next batch on a second stream' if overlap else '') +
               (', the pass replayed from one CUDA graph' if graph is not None else '')),
-        batch=B, warm_start=warm, cuda_graph=graph is not None,
+        batch=B, field_group=G, warm_start=warm, cuda_graph=graph is not None,
         **({'cuda_graph_note': graph_note} if graph_note else {}), wall_s=wall, roofline=roof,
         gpu_launches=total_frames * (2 if fused else 3) + args.steps * len(batches) * (2 if warm else 1),
         clocks=clk,
@@ -730,15 +758,22 @@ def run_gpu_mixed(args, ws, rank, local):
     ctas, tune_ms = emdq.fit_batch_autotune(fit_probs, reps=2, outs=[x['out'] for x in P],
                                             workspace=batch_ws)
 
-    # field of pair b + 1 (main stream) beside the warp of pair b (warp stream), field
-    # outputs double-buffered
+    # the fields of a group of G pairs in one emdq_field_batch call (main stream), their
+    # warps on the warp stream beside the next group's fields; buffers double-buffered
+    G = max(1, min(16, args.field_group))
     warp_stream = torch.cuda.Stream(device=dev)
-    disp_bufs = [disp_buf, torch.empty_like(disp_buf)]
-    field_wss = [field_ws, torch.empty_like(field_ws)]
+    groups = [list(range(b0, min(len(P), b0 + G))) for b0 in range(0, len(P), G)]
+    gws = max(emdq.field_batch_workspace_size([(P[b]['out']['q'], P[b]['out']['c'], P[b]['src'],
+                                                P[b]['grid'], P[b]['alpha']) for b in grp])
+              for grp in groups)
+    grp_ws = [torch.empty(gws, dtype=torch.uint8, device=dev) for _ in range(2)]
+    max_px = max(x['grid'][2] * x['grid'][3] for x in P)
+    grp_disp = [[torch.empty(max_px * 2, dtype=torch.float32, device=dev) for _ in range(G)]
+                for _ in range(2)]
 
     def one_pass(ev=None):
         # ev[0] start, ev[1] warm start done, ev[2] fits done, then per pair b: ev[3 + 3b]
-        # field done, ev[4 + 3b] / ev[5 + 3b] warp start / done (warp stream)
+        # field done (its group's call), ev[4 + 3b] / ev[5 + 3b] warp start / done
         main = torch.cuda.current_stream()
         if ev: ev[0].record()
         emdq.warm_start(probs_sd, warm_params, outs=[x['p0'] for x in P])
@@ -746,23 +781,26 @@ def run_gpu_mixed(args, ws, rank, local):
         emdq.emdq_fit_batch(fit_probs, outs=[x['out'] for x in P], workspace=batch_ws, ctas=ctas)
         if ev: ev[2].record()
         free = [None, None]
-        for b, x in enumerate(P):
-            g = x['grid']
-            slot = b % 2
+        for gi, grp in enumerate(groups):
+            slot = gi % 2
             if free[slot] is not None:
                 main.wait_event(free[slot])
-            disp = disp_bufs[slot][: g[2] * g[3] * 2].view(g[3], g[2], 2)
-            emdq.emdq_field(x['out']['q'], x['out']['c'], x['src'], g, x['alpha'], precision=emdq.BF16,
-                            out=disp, workspace=field_wss[slot])
+            disps = [grp_disp[slot][i][: P[b]['grid'][2] * P[b]['grid'][3] * 2].view(
+                     P[b]['grid'][3], P[b]['grid'][2], 2) for i, b in enumerate(grp)]
+            emdq.emdq_field_batch([(P[b]['out']['q'], P[b]['out']['c'], P[b]['src'], P[b]['grid'],
+                                    P[b]['alpha']) for b in grp], outs=disps, workspace=grp_ws[slot])
             fdone = torch.cuda.Event()
             fdone.record(main)
-            if ev: ev[3 + 3 * b].record(main)
+            if ev:
+                for b in grp: ev[3 + 3 * b].record(main)
             warp_stream.wait_event(fdone)
-            if ev: ev[4 + 3 * b].record(warp_stream)
-            emdq.mosaic_warp(x['frame'], disp, g, x['canvas'], x['origin'], stream=warp_stream)
+            for i, b in enumerate(grp):
+                x = P[b]
+                if ev: ev[4 + 3 * b].record(warp_stream)
+                emdq.mosaic_warp(x['frame'], disps[i], x['grid'], x['canvas'], x['origin'], stream=warp_stream)
+                if ev: ev[5 + 3 * b].record(warp_stream)
             wdone = torch.cuda.Event()
             wdone.record(warp_stream)
-            if ev: ev[5 + 3 * b].record(warp_stream)
             free[slot] = wdone
         main.wait_stream(warp_stream)
         for b, x in enumerate(P):
@@ -852,7 +890,7 @@ def run_gpu_mixed(args, ws, rank, local):
                     launches=len(fit_ms), mean_launch_ms=float(np.mean(fit_ms)))
     elif dom == 'field':
         flops = 2.0 * 6 * float(np.sum(win * np.array(nz)))
-        roof = dict(bound='tensor', kernel='field_tc_kernel (operand prologue included)',
+        roof = dict(bound='tensor', kernel='emdq_field_batch: field_tc_prep_kernel + field_tc_kernel',
                     achieved=flops / (np.sum(field_ms) / args.steps * 1e-3) / 1e12,
                     peak=peaks['bf16_tflops'], unit='TFLOP/s', peak_source=peaks['source'] + ' bf16 burst',
                     launches=len(field_ms), mean_launch_ms=float(np.mean(field_ms)),
@@ -878,7 +916,7 @@ def run_gpu_mixed(args, ws, rank, local):
         config=mixed_config(args, ws, pairs, ctas),
         kernel_ms_per_step={k: v / args.steps for k, v in totals.items()},
         path='learned warm start (one launch) + emdq_fit_batch (one launch, autotuned CTA split) + '
-             'per pair emdq_field (bf16), its mosaic_warp on a second stream beside the next field' +
+             f'emdq_field_batch ({G} pairs per call, bf16), their mosaic_warp on a second stream' +
              (', the step replayed from one CUDA graph' if graph is not None else ''),
         cuda_graph=graph is not None, **({'cuda_graph_note': graph_note} if graph_note else {}),
         autotune_fit_ms=tune_ms, mean_em_iters=float(np.mean(iters)), roofline=roof,

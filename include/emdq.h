@@ -222,6 +222,33 @@ EMDQ_API emdq_status emdq_field(const float *q, const float *c, const float *src
                        int precision, float *disp_out, void *workspace,
                        size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------------------------ emdq_field_batch --
+ * Several BF16 fields -- the frames of a sequence or the pairs of a batch -- in one
+ * operand-preparation launch and one persistent tensor-core launch that walks the tiles of
+ * every field in turn, so the fixed cost of the two launches is paid once per batch.  Each
+ * field is exactly what emdq_field with EMDQ_BF16 computes for the same arguments.
+ *
+ *   problems   host array of `count` descriptors (1 <= count <= 16); the pointers follow the
+ *              rules of the matching emdq_field arguments
+ *   workspace  device scratch of emdq_field_batch_workspace_size(problems, count) bytes,
+ *              256-byte aligned, not shared with a call in flight
+ * Returns EMDQ_EINVAL for a bad descriptor, EMDQ_ENOTSUP for count > 16 or a device without
+ * tcgen05, EMDQ_EWORKSPACE / EMDQ_ECUDA as emdq_field.
+ */
+typedef struct {
+    const float *q;             /* device, n x 8 warp rows (emdq_fit's q_out) */
+    const float *c;             /* device, n field weights (emdq_fit's c_out) */
+    const float *src;           /* device, n x 2 match positions in the reference frame */
+    int n;
+    int grid_x0, grid_y0, grid_w, grid_h;   /* the pixel window, reference coordinates */
+    float alpha;                /* Gaussian weight exp(-alpha |p - x_i|^2) */
+    float *disp_out;            /* device, grid_h x grid_w x 2 float (written) */
+} emdq_field_problem;
+
+EMDQ_API size_t      emdq_field_batch_workspace_size(const emdq_field_problem *problems, int count);
+EMDQ_API emdq_status emdq_field_batch(const emdq_field_problem *problems, int count,
+                                      void *workspace, size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------------------------ mosaic_warp ------
  * Gather warp + capped running-average blend of frame t into the canvas (Sec. III-F,
  * Eqs. 23-24 as read: the paper's printed blend lacks its normalisation and its cap reads
@@ -242,6 +269,26 @@ EMDQ_API emdq_status mosaic_warp(const uint8_t *frame, int fw, int fh, int chann
                         const float *disp, int grid_x0, int grid_y0, int grid_w, int grid_h,
                         uint8_t *canvas, int canvas_w, int canvas_h, int canvas_pitch,
                         int origin_x, int origin_y, void *stream);
+
+/* ------------------------------------------------------------------ mosaic_warp_batch -
+ * Up to 8 frames of one sequence (same size, channels and pitch) blended into one canvas in
+ * one launch: canvas pixels are taken through the frames in array order, exactly as the
+ * same mosaic_warp calls in that order would leave them (a pixel's update depends only on
+ * its own earlier updates), with the canvas read and written once per pixel and the loads
+ * of all the frames in flight together.  Each frame has its own field and window (the rules
+ * of mosaic_warp's frame, disp and grid arguments); an empty window is skipped.
+ * Returns EMDQ_ENOTSUP for count > 8, otherwise the errors of mosaic_warp.
+ */
+typedef struct {
+    const uint8_t *frame;       /* device, fh rows of frame_pitch bytes */
+    const float *disp;          /* device, grid_h x grid_w x 2 float */
+    int grid_x0, grid_y0, grid_w, grid_h;
+} mosaic_frame;
+
+EMDQ_API emdq_status mosaic_warp_batch(const mosaic_frame *frames, int count, int fw, int fh,
+                                       int channels, int frame_pitch, uint8_t *canvas,
+                                       int canvas_w, int canvas_h, int canvas_pitch, int origin_x,
+                                       int origin_y, void *stream);
 
 /* ------------------------------------------------------------------ emdq_mosaic ------
  * emdq_field (EMDQ_BF16) and mosaic_warp fused in one tensor-core kernel: for every grid

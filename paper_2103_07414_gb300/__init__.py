@@ -37,6 +37,13 @@ class _Params(ctypes.Structure):
                 ('reserved', ctypes.c_int * 4)]
 
 
+class _FieldProblem(ctypes.Structure):
+    _fields_ = [('q', ctypes.c_void_p), ('c', ctypes.c_void_p), ('src', ctypes.c_void_p),
+                ('n', ctypes.c_int), ('grid_x0', ctypes.c_int), ('grid_y0', ctypes.c_int),
+                ('grid_w', ctypes.c_int), ('grid_h', ctypes.c_int), ('alpha', ctypes.c_float),
+                ('disp_out', ctypes.c_void_p)]
+
+
 class _Problem(ctypes.Structure):
     _fields_ = [('src', ctypes.c_void_p), ('dst', ctypes.c_void_p), ('n', ctypes.c_int),
                 ('frame_w', ctypes.c_int), ('frame_h', ctypes.c_int), ('p0', ctypes.c_void_p),
@@ -82,6 +89,10 @@ def lib() -> ctypes.CDLL:
                                                   ctypes.POINTER(ctypes.c_float)]
             L.emdq_field_workspace_size.restype = Z
             L.emdq_field_workspace_size.argtypes = [I, I, I, I]
+            L.emdq_field_batch_workspace_size.restype = Z
+            L.emdq_field_batch_workspace_size.argtypes = [P, I]
+            L.emdq_field_batch.restype = I
+            L.emdq_field_batch.argtypes = [P, I, P, Z, P]
             L.emdq_field.restype = I
             L.emdq_field.argtypes = [P, P, P, I, I, I, I, I, F, I, P, P, Z, P]
             L.mosaic_warp.restype = I
@@ -287,6 +298,48 @@ def emdq_field(q: torch.Tensor, c: torch.Tensor, src: torch.Tensor, grid, alpha:
     if rc != 0:
         raise EmdqError('emdq_field', rc)
     return out
+
+
+def _field_problems(problems, outs):
+    count = len(problems)
+    arr = (_FieldProblem * max(1, count))()
+    res = []
+    for b, (q, c, src, grid, alpha) in enumerate(problems):
+        n = c.shape[0]
+        _check(q, 'q', torch.float32, (n, 8))
+        _check(c, 'c', torch.float32, (n,))
+        _check(src, 'src', torch.float32, (n, 2))
+        x0, y0, gw, gh = (int(v) for v in grid)
+        out = outs[b] if outs is not None else torch.empty((gh, gw, 2), dtype=torch.float32,
+                                                           device=q.device)
+        _check(out, 'out', torch.float32, (gh, gw, 2))
+        arr[b] = _FieldProblem(_ptr(q), _ptr(c), _ptr(src), n, x0, y0, gw, gh, float(alpha), _ptr(out))
+        res.append(out)
+    return arr, res
+
+
+def field_batch_workspace_size(problems) -> int:
+    """Bytes of workspace for emdq_field_batch on (q, c, src, grid, alpha) problems."""
+    arr = (_FieldProblem * max(1, len(problems)))()
+    for b, (q, c, src, grid, alpha) in enumerate(problems):
+        arr[b].n = int(c.shape[0])
+        arr[b].grid_w, arr[b].grid_h = int(grid[2]), int(grid[3])
+    return lib().emdq_field_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), len(problems))
+
+
+def emdq_field_batch(problems, *, outs: list | None = None, workspace: torch.Tensor | None = None,
+                     stream=None) -> list:
+    """BF16 fields of several (q, c, src, grid, alpha) problems in one operand launch and one
+    persistent tensor-core launch; returns the [h, w, 2] fields (or fills outs)."""
+    count = len(problems)
+    arr, res = _field_problems(problems, outs)
+    need = lib().emdq_field_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), count)
+    ws = _workspace(need, problems[0][0].device, workspace)
+    rc = lib().emdq_field_batch(ctypes.cast(arr, ctypes.c_void_p), count, _ptr(ws), ws.numel(),
+                                _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_field_batch', rc)
+    return res
 
 
 def _frame_args(frame: torch.Tensor):

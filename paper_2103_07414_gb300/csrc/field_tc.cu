@@ -27,6 +27,7 @@
 // epilogue of a tile overlaps the MMAs of the next.
 // The fused variant (CH = 1 or 3) goes on from the displacement to the mosaic update of
 // the same pixel (the stand-alone warp's per-pixel code), so the field never visits HBM.
+#include <cmath>
 #include <mutex>
 
 #include <cuda_bf16.h>
@@ -92,14 +93,20 @@ __device__ int compact_columns(const float *__restrict__ c, int n, int *s_idx)
     __shared__ int s_warp[kPrepThreads / 32];
     if (n > kCompactMax) return -1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // thread t owns matches [t per, (t + 1) per): one flag bit each (per <= 32)
+    // thread t owns matches [t per, (t + 1) per): one flag bit each (per <= 32); all its
+    // loads are issued before any is used (one memory round trip)
     const int per = (n + kPrepThreads - 1) / kPrepThreads;
     const int k0 = threadIdx.x * per;
-    unsigned mask = 0;
-    for (int u = 0; u < per; ++u) {
+    float cv[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
         const int k = k0 + u;
-        if (k < n && c[k] != 0.f) mask |= 1u << u;
+        cv[u] = (u < per && k < n) ? c[k] : 0.f;
     }
+    unsigned mask = 0;
+#pragma unroll
+    for (int u = 0; u < 32; ++u)
+        if (cv[u] != 0.f) mask |= 1u << u;
     const int cnt = __popc(mask);
     int incl = cnt;                                   // inclusive scan over the warp
 #pragma unroll
@@ -121,34 +128,78 @@ __device__ int compact_columns(const float *__restrict__ c, int n, int *s_idx)
     return tot;
 }
 
-__global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
-    const float *__restrict__ q, const float *__restrict__ c, const float2 *__restrict__ src,
-    int n, int kp, int gx0, int gy0, int gw, int gh, int wp, int hp, float alpha,
-    float *__restrict__ ref_out, __nv_bfloat162 *__restrict__ A, __nv_bfloat162 *__restrict__ B,
-    int a_blocks, int *__restrict__ kcount)
+// A batch of fields (frames or pairs) run by one prep launch and one GEMM launch, so the
+// fixed costs of the two launches are paid once per batch.
+constexpr int kFieldBatchMax = 16;
+
+struct TcProblem {
+    const float *q, *c;
+    const float2 *src;
+    int n, kp, gx0, gy0, gw, gh, wp, hp;
+    float alpha;
+    __nv_bfloat162 *A, *B;       // BF16 operands (workspace)
+    float *ref;                  // reference row, 6 floats (workspace or caller)
+    int *kcount;                 // K columns the prep wrote (workspace)
+    float2 *disp;                // the displacement field (CH = 0)
+    int ntx, tile0, ntiles;      // GEMM tiles [tile0, tile0 + ntiles) of the batch
+    int block0, a_blocks, nblocks;   // prep blocks [block0, block0 + nblocks), Ex rows first
+};
+
+struct TcBatch {
+    CUtensorMap tmA[kFieldBatchMax];
+    CUtensorMap tmB[kFieldBatchMax];
+    TcProblem p[kFieldBatchMax];
+    int count, total_tiles;
+    int *err;                    // device status (ETIMEOUT), cleared by the prep launch
+};
+
+__device__ __forceinline__ int problem_of_block(const TcBatch &Bt, int blk)
+{
+    int b = 0;
+    while (b + 1 < Bt.count && Bt.p[b + 1].block0 <= blk) ++b;
+    return b;
+}
+
+__device__ __forceinline__ int problem_of_tile(const TcBatch &Bt, int tile)
+{
+    int b = 0;
+    while (b + 1 < Bt.count && Bt.p[b + 1].tile0 <= tile) ++b;
+    return b;
+}
+
+__global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(const __grid_constant__ TcBatch Bt)
 {
     // the GEMM launched after this kernel may start its set-up now; it waits for this
     // grid's completion (griddepcontrol.wait) before it reads anything written here
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ int s_idx[kCompactMax];
-    const int half = kp / 2;
+    const TcProblem &P = Bt.p[problem_of_block(Bt, blockIdx.x)];
+    const int blk = blockIdx.x - P.block0;
+    const float *__restrict__ q = P.q;
+    const float *__restrict__ c = P.c;
+    const float2 *__restrict__ src = P.src;
+    const int n = P.n, wp = P.wp, hp = P.hp, gw = P.gw, gh = P.gh;
+    const float alpha = P.alpha;
+    const int half = P.kp / 2;
     const int mc = compact_columns(c, n, s_idx);
     const bool compact = mc >= 0;
     const int m = compact ? mc : n;
     // columns written: m rounded up to whole 64-match slices (at least one), zeros past m
     const int kc = m > 0 ? (m + kTcK - 1) / kTcK * kTcK : kTcK;
     const int halfc = kc / 2;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *kcount = kc;
+    if (blk == 0 && threadIdx.x == 0) *P.kcount = kc;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *Bt.err = 0;   // raised by the GEMM only after its wait
     auto col = [&](int k) { return compact ? s_idx[k] : k; };
-    if ((int)blockIdx.x < a_blocks) {
-        const int r0 = blockIdx.x * kPrepRows;
+    if (blk < P.a_blocks) {
+        __nv_bfloat162 *__restrict__ A = P.A;
+        const int r0 = blk * kPrepRows;
         for (int k2 = threadIdx.x; k2 < halfc; k2 += kPrepThreads) {
             const int k0 = 2 * k2, k1 = k0 + 1;
             const float x0 = k0 < m ? src[col(k0)].x : 0.f, x1 = k1 < m ? src[col(k1)].x : 0.f;
             for (int r = 0; r < kPrepRows; ++r) {
                 const int px = r0 + r;
                 if (px >= wp) break;
-                const float p = static_cast<float>(gx0 + px);
+                const float p = static_cast<float>(P.gx0 + px);
                 const bool row = px < gw;
                 const float d0 = p - x0, d1 = p - x1;
                 const float e0 = (row && k0 < m) ? expf(-alpha * d0 * d0) : 0.f;
@@ -157,12 +208,13 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
             }
         }
     } else {
-        const int r0 = (blockIdx.x - a_blocks) * kPrepRows;
+        __nv_bfloat162 *__restrict__ B = P.B;
+        const int r0 = (blk - P.a_blocks) * kPrepRows;
         __shared__ float red[6 * 32];
         float rf[6];
         reference_row(q, c, n, red, rf);      // same bits in every block
-        if (blockIdx.x == a_blocks && threadIdx.x == 0)
-            for (int k = 0; k < 6; ++k) ref_out[k] = rf[k];
+        if (blk == P.a_blocks && threadIdx.x == 0)
+            for (int k = 0; k < 6; ++k) P.ref[k] = rf[k];
         for (int k2 = threadIdx.x; k2 < halfc; k2 += kPrepThreads) {
             const int k0 = 2 * k2;
             float y[2] = {0.f, 0.f}, cw[2] = {0.f, 0.f}, cq[2][5];
@@ -187,7 +239,7 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
             for (int r = 0; r < kPrepRows; ++r) {
                 const int py = r0 + r;
                 if (py >= hp) break;
-                const float p = static_cast<float>(gy0 + py);
+                const float p = static_cast<float>(P.gy0 + py);
                 const bool row = py < gh;
                 const float d0 = p - y[0], d1 = p - y[1];
                 const float e0 = row ? expf(-alpha * d0 * d0) : 0.f;
@@ -204,12 +256,11 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(
 
 // CH = 0: write the displacement field; CH = 1 or 3: blend the frame into the canvas.
 template <int CH>
-__global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(
-    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-    const int *__restrict__ kcount, int ntx, int ntiles, int gx0, int gy0, int gw, int gh,
-    const float *__restrict__ ref, float2 *__restrict__ disp, int *__restrict__ err,
-    MosaicArgs mos)
+__global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(const __grid_constant__ TcBatch Bt,
+                                                                   MosaicArgs mos)
 {
+    const int ntiles = Bt.total_tiles;
+    int *__restrict__ err = Bt.err;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -238,8 +289,10 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(
         *issued = 0;
         *consumed = 0;
         tc::fence_mbar_init();
-        tc::prefetch_tmap(&tmA);
-        tc::prefetch_tmap(&tmB);
+        for (int b = 0; b < Bt.count; ++b) {
+            tc::prefetch_tmap(&Bt.tmA[b]);
+            tc::prefetch_tmap(&Bt.tmB[b]);
+        }
     }
     if (warp == 1) tc::tmem_alloc(tmem_slot, kTcTmemCols);
     tc::fence_before_sync();
@@ -249,16 +302,18 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(
     // everything above is independent of the prep kernel (programmatic dependent launch);
     // its operands, column count and reference row are read only after this wait
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    // 64-match slices along K: the prep kernel's column count (the matches of nonzero
-    // weight), a whole number of slices, at least one
-    const int nchunks = *kcount / kTcK;
 
     if (warp == 0) {
         if (lane == 0) {
             // TMA producer: every tile of this CTA, every 64-match slice
             int chunk = 0;
             for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
-                const int tx = tile % ntx, ty = tile / ntx;
+                const int b = problem_of_tile(Bt, tile);
+                const TcProblem &P = Bt.p[b];
+                const int lt = tile - P.tile0, tx = lt % P.ntx, ty = lt / P.ntx;
+                // 64-match slices along K: the prep kernel's column count (the matches of
+                // nonzero weight), a whole number of slices, at least one
+                const int nchunks = *P.kcount / kTcK;
                 for (int k = 0; k < nchunks; ++k, ++chunk) {
                     const int s = chunk % kTcStages;
                     const uint32_t ph = (chunk / kTcStages) & 1;
@@ -268,8 +323,8 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(
                     }
                     uint8_t *sa = smem + s * kTcStageBytes;
                     tc::mbar_arrive_expect_tx(full + s, kTcStageBytes);
-                    tc::tma_load_2d(sa, &tmA, full + s, k * kTcK, tx * kTcM);
-                    tc::tma_load_3d(sa + kTcABytes, &tmB, full + s, k * kTcK, ty * kTcPY, 0);
+                    tc::tma_load_2d(sa, &Bt.tmA[b], full + s, k * kTcK, tx * kTcM);
+                    tc::tma_load_3d(sa + kTcABytes, &Bt.tmB[b], full + s, k * kTcK, ty * kTcPY, 0);
                     *issued = chunk + 1;
                 }
             }
@@ -286,6 +341,7 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(
                 }
                 tc::fence_after_sync();
                 const uint32_t d = tmem + a * kTcAccCols;
+                const int nchunks = *Bt.p[problem_of_tile(Bt, tile)].kcount / kTcK;
                 bool ok = true;
                 for (int k = 0; k < nchunks; ++k, ++chunk) {
                     const int s = chunk % kTcStages;
@@ -321,7 +377,6 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(
         constexpr int kGroups = kTcPY / 8 / (tc_epi_warps(CH) / 4);
         const int q = warp & 3;
         const int g0 = ((warp - 2) >> 2) * kGroups;
-        const float ra = ref[0], rb = ref[1], ru = ref[2], rv = ref[3], rs = ref[4];
         int it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int a = it & 1;
@@ -331,7 +386,11 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(
                 *abort_flag = 1;
                 break;
             }
-            const int tx = tile % ntx, ty = tile / ntx;
+            const TcProblem &P = Bt.p[problem_of_tile(Bt, tile)];
+            const int gx0 = P.gx0, gy0 = P.gy0, gw = P.gw, gh = P.gh;
+            float2 *__restrict__ disp = P.disp;
+            const float ra = P.ref[0], rb = P.ref[1], ru = P.ref[2], rv = P.ref[3], rs = P.ref[4];
+            const int lt = tile - P.tile0, tx = lt % P.ntx, ty = lt / P.ntx;
             const int x = tx * kTcM + q * 32 + lane;
             const float px = static_cast<float>(gx0 + x);
             const uint32_t lane_base = tmem + a * kTcAccCols + (static_cast<uint32_t>(q * 32) << 16);
@@ -443,33 +502,27 @@ size_t field_tc_workspace_bytes(int n, int grid_w, int grid_h)
     return kErrBytes + align_up(g.a_bytes, 1024) + align_up(g.b_bytes, 1024);
 }
 
-emdq_status field_tc_launch(const float *q, const float *c, const float *src, int n, int gx0,
-                            int gy0, int gw, int gh, float alpha, float *ref, float2 *disp,
-                            char *ws, size_t ws_bytes, cudaStream_t st, const MosaicArgs *mos)
+namespace {
+
+// Fill problem b of a batch: geometry, tensor maps of its operands (A at ops, B after it),
+// the reference-row, column-count and output pointers.  ops must be 256-byte aligned (TMA
+// needs 16).
+emdq_status tc_problem(TcBatch &Bt, int b, const float *q, const float *c, const float *src, int n,
+                       int gx0, int gy0, int gw, int gh, float alpha, float *ref, int *kcount,
+                       float2 *disp, char *ops)
 {
-    const int variant = mos ? mos->channels : 0;
-    if (variant != 0 && variant != 1 && variant != 3) return EMDQ_EINVAL;
-    const DeviceInfo &D = device_info();
-    if (D.device < 0) return EMDQ_ECUDA;
-    if (D.cc_major != 10) return EMDQ_ENOTSUP;           // tcgen05: sm_100 family only
-    if (D.smem_optin < kTcSmemBytes) return EMDQ_ENOTSUP;
-    const TcGeom g = tc_geom(n, gw, gh);
-    if (ws_bytes < field_tc_workspace_bytes(n, gw, gh)) return EMDQ_EWORKSPACE;
-    if (g.hp / kTcPY > 65535 || g.hp > (1 << 24) || g.wp > (1 << 24)) return EMDQ_ENOTSUP;
     auto encode = encode_fn();
     if (!encode) return EMDQ_ECUDA;
-
-    int *err = reinterpret_cast<int *>(ws);
-    auto *A = reinterpret_cast<__nv_bfloat162 *>(ws + kErrBytes);
-    auto *B = reinterpret_cast<__nv_bfloat162 *>(ws + kErrBytes + align_up(g.a_bytes, 1024));
-
-    CUtensorMap tmA, tmB;
+    const TcGeom g = tc_geom(n, gw, gh);
+    if (g.hp / kTcPY > 65535 || g.hp > (1 << 24) || g.wp > (1 << 24)) return EMDQ_ENOTSUP;
+    auto *A = reinterpret_cast<__nv_bfloat162 *>(ops);
+    auto *B = reinterpret_cast<__nv_bfloat162 *>(ops + align_up(g.a_bytes, 1024));
     {
         cuuint64_t dims[2] = {(cuuint64_t)g.kp, (cuuint64_t)g.wp};
         cuuint64_t strides[1] = {(cuuint64_t)g.kp * 2};
         cuuint32_t box[2] = {kTcK, kTcM};
         cuuint32_t estr[2] = {1, 1};
-        if (encode(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A, dims, strides, box, estr,
+        if (encode(&Bt.tmA[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return EMDQ_ECUDA;
@@ -479,12 +532,42 @@ emdq_status field_tc_launch(const float *q, const float *c, const float *src, in
         cuuint64_t strides[2] = {(cuuint64_t)g.kp * 2, (cuuint64_t)g.hp * g.kp * 2};
         cuuint32_t box[3] = {kTcK, kTcPY, kTcCh};
         cuuint32_t estr[3] = {1, 1, 1};
-        if (encode(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, B, dims, strides, box, estr,
+        if (encode(&Bt.tmB[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, B, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return EMDQ_ECUDA;
     }
+    TcProblem &P = Bt.p[b];
+    P.q = q;
+    P.c = c;
+    P.src = reinterpret_cast<const float2 *>(src);
+    P.n = n;
+    P.kp = g.kp;
+    P.gx0 = gx0;
+    P.gy0 = gy0;
+    P.gw = gw;
+    P.gh = gh;
+    P.wp = g.wp;
+    P.hp = g.hp;
+    P.alpha = alpha;
+    P.A = A;
+    P.B = B;
+    P.ref = ref;
+    P.kcount = kcount;
+    P.disp = disp;
+    P.ntx = g.wp / kTcM;
+    P.tile0 = b == 0 ? 0 : Bt.p[b - 1].tile0 + Bt.p[b - 1].ntiles;
+    P.ntiles = P.ntx * (g.hp / kTcPY);
+    P.block0 = b == 0 ? 0 : Bt.p[b - 1].block0 + Bt.p[b - 1].nblocks;
+    P.a_blocks = g.wp / kPrepRows;
+    P.nblocks = P.a_blocks + g.hp / kPrepRows;
+    return EMDQ_OK;
+}
 
+// The prep launch and the GEMM launch (a programmatic dependent of the prep) of a batch.
+emdq_status tc_run(TcBatch &Bt, int variant, const MosaicArgs *mos, cudaStream_t st)
+{
+    const DeviceInfo &D = device_info();
     static std::mutex mu;
     static int attr_dev = -1;
     {
@@ -500,16 +583,12 @@ emdq_status field_tc_launch(const float *q, const float *c, const float *src, in
             attr_dev = D.device;
         }
     }
-    if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return EMDQ_ECUDA;
-    int *kcount = err + 1;                  // written by the prep kernel, read by the GEMM
-    const int a_blocks = g.wp / kPrepRows;
-    const int b_blocks = g.hp / kPrepRows;
-    field_tc_prep_kernel<<<a_blocks + b_blocks, kPrepThreads, 0, st>>>(
-        q, c, reinterpret_cast<const float2 *>(src), n, g.kp, gx0, gy0, gw, gh, g.wp, g.hp, alpha,
-        ref, A, B, a_blocks, kcount);
+    const TcProblem &last = Bt.p[Bt.count - 1];
+    Bt.total_tiles = last.tile0 + last.ntiles;
+    const int blocks = last.block0 + last.nblocks;
+    field_tc_prep_kernel<<<blocks, kPrepThreads, 0, st>>>(Bt);
     if (cudaGetLastError() != cudaSuccess) return EMDQ_ECUDA;
-    const int ntx = g.wp / kTcM, ntiles = ntx * (g.hp / kTcPY);
-    const int grid = ntiles < D.sms ? ntiles : D.sms;       // persistent: one CTA per SM
+    const int grid = Bt.total_tiles < D.sms ? Bt.total_tiles : D.sms;   // persistent: one CTA per SM
     const MosaicArgs none{};
     // programmatic dependent launch: the GEMM's set-up overlaps the prep kernel's tail
     cudaLaunchConfig_t cfg = {};
@@ -523,15 +602,91 @@ emdq_status field_tc_launch(const float *q, const float *c, const float *src, in
     cfg.attrs = at;
     cfg.numAttrs = 1;
     cudaError_t e;
-    if (variant == 0)
-        e = cudaLaunchKernelEx(&cfg, field_tc_kernel<0>, tmA, tmB, (const int *)kcount, ntx, ntiles,
-                               gx0, gy0, gw, gh, (const float *)ref, disp, err, none);
-    else if (variant == 1)
-        e = cudaLaunchKernelEx(&cfg, field_tc_kernel<1>, tmA, tmB, (const int *)kcount, ntx, ntiles,
-                               gx0, gy0, gw, gh, (const float *)ref, disp, err, *mos);
-    else
-        e = cudaLaunchKernelEx(&cfg, field_tc_kernel<3>, tmA, tmB, (const int *)kcount, ntx, ntiles,
-                               gx0, gy0, gw, gh, (const float *)ref, disp, err, *mos);
-    if (e != cudaSuccess) return EMDQ_ECUDA;
-    return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
+    if (variant == 0) e = cudaLaunchKernelEx(&cfg, field_tc_kernel<0>, Bt, none);
+    else if (variant == 1) e = cudaLaunchKernelEx(&cfg, field_tc_kernel<1>, Bt, *mos);
+    else e = cudaLaunchKernelEx(&cfg, field_tc_kernel<3>, Bt, *mos);
+    return e == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
+}
+
+bool tc_device_ok()
+{
+    const DeviceInfo &D = device_info();
+    return D.device >= 0 && D.cc_major == 10 && D.smem_optin >= kTcSmemBytes;
+}
+
+// Batch workspace: 1024 bytes (error word at 0), then per problem 1024 bytes (reference row
+// at 0, column count at 64) and its 1024-aligned operands.
+size_t batch_problem_bytes(int n, int gw, int gh)
+{
+    const TcGeom g = tc_geom(n, gw, gh);
+    return 1024 + align_up(g.a_bytes, 1024) + align_up(g.b_bytes, 1024);
+}
+
+}  // namespace
+
+emdq_status field_tc_launch(const float *q, const float *c, const float *src, int n, int gx0,
+                            int gy0, int gw, int gh, float alpha, float *ref, float2 *disp,
+                            char *ws, size_t ws_bytes, cudaStream_t st, const MosaicArgs *mos)
+{
+    const int variant = mos ? mos->channels : 0;
+    if (variant != 0 && variant != 1 && variant != 3) return EMDQ_EINVAL;
+    const DeviceInfo &D = device_info();
+    if (D.device < 0) return EMDQ_ECUDA;
+    if (!tc_device_ok()) return EMDQ_ENOTSUP;           // tcgen05: sm_100 family only
+    if (ws_bytes < field_tc_workspace_bytes(n, gw, gh)) return EMDQ_EWORKSPACE;
+    static thread_local TcBatch Bt;
+    Bt.count = 1;
+    Bt.err = reinterpret_cast<int *>(ws);
+    int *kcount = Bt.err + 1;                 // written by the prep kernel, read by the GEMM
+    const emdq_status rc =
+        tc_problem(Bt, 0, q, c, src, n, gx0, gy0, gw, gh, alpha, ref, kcount, disp, ws + kErrBytes);
+    if (rc != EMDQ_OK) return rc;
+    return tc_run(Bt, variant, mos, st);
+}
+
+extern "C" size_t emdq_field_batch_workspace_size(const emdq_field_problem *problems, int count)
+{
+    if (!problems || count < 1 || count > kFieldBatchMax) return 0;
+    size_t total = 1024;
+    for (int b = 0; b < count; ++b) {
+        if (problems[b].n < 1 || problems[b].grid_w < 0 || problems[b].grid_h < 0) return 0;
+        total += batch_problem_bytes(problems[b].n, problems[b].grid_w, problems[b].grid_h);
+    }
+    return total;
+}
+
+extern "C" emdq_status emdq_field_batch(const emdq_field_problem *problems, int count,
+                                        void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!problems || count < 1) return EMDQ_EINVAL;
+    if (count > kFieldBatchMax) return EMDQ_ENOTSUP;
+    for (int b = 0; b < count; ++b) {
+        const emdq_field_problem &f = problems[b];
+        if (!f.q || !f.c || !f.src || !f.disp_out || f.n < 1 || f.grid_w < 1 || f.grid_h < 1 ||
+            !(f.alpha > 0.f) || !std::isfinite(f.alpha))
+            return EMDQ_EINVAL;
+        if (!aligned(f.q, 16) || !aligned(f.c, 4) || !aligned(f.src, 8) || !aligned(f.disp_out, 8))
+            return EMDQ_EINVAL;
+    }
+    const size_t need = emdq_field_batch_workspace_size(problems, count);
+    if (need == 0) return EMDQ_EINVAL;
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return EMDQ_EWORKSPACE;
+    if (device_info().device < 0) return EMDQ_ECUDA;
+    if (!tc_device_ok()) return EMDQ_ENOTSUP;
+    static thread_local TcBatch Bt;
+    char *ws = static_cast<char *>(workspace);
+    Bt.count = count;
+    Bt.err = reinterpret_cast<int *>(ws);
+    size_t off = 1024;
+    for (int b = 0; b < count; ++b) {
+        const emdq_field_problem &f = problems[b];
+        float *ref = reinterpret_cast<float *>(ws + off);
+        int *kcount = reinterpret_cast<int *>(ws + off + 64);
+        const emdq_status rc =
+            tc_problem(Bt, b, f.q, f.c, f.src, f.n, f.grid_x0, f.grid_y0, f.grid_w, f.grid_h,
+                       f.alpha, ref, kcount, reinterpret_cast<float2 *>(f.disp_out), ws + off + 1024);
+        if (rc != EMDQ_OK) return rc;
+        off += batch_problem_bytes(f.n, f.grid_w, f.grid_h);
+    }
+    return tc_run(Bt, 0, nullptr, static_cast<cudaStream_t>(stream));
 }

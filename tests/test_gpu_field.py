@@ -150,3 +150,61 @@ def test_field_many_matches_sampled(emdq, orc, prec):
     err = np.abs(got[iy, ix] - want).max()
     print(f'prec {prec}: n=9000 sampled max error {err:.3e} px')
     assert err <= TOL[prec]
+
+
+def _field_case(rng, n, w, h, zero_frac=0.3):
+    src, q8 = random_rows(rng, n, w, h)
+    c = np.where(rng.uniform(0, 1, n) < 1 - zero_frac, rng.uniform(0.5, 1, n), 0.0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    return t(q8), t(c), t(src), (q8, c, src)
+
+
+def test_field_batch_equals_single_calls(emdq):
+    """One operand launch and one persistent GEMM over several fields give each field
+    bit for bit what its own emdq_field (BF16) call gives."""
+    rng = np.random.default_rng(77)
+    specs = [(1000, 1280, 1024, (-30, -40, 1343, 1083)), (137, 640, 480, (5, 7, 17, 9)),
+             (2500, 1920, 1080, (-12, 3, 1999, 700)), (64, 640, 480, (0, 0, 129, 33)),
+             (900, 1280, 720, (100, -20, 640, 300))]
+    probs = []
+    for n, w, h, grid in specs:
+        q, c, s, _ = _field_case(rng, n, w, h)
+        probs.append((q, c, s, grid, np.float32(emdq.alpha_for_frame(w, h))))
+    got = emdq.emdq_field_batch(probs)
+    torch.cuda.synchronize()
+    for (q, c, s, grid, alpha), g in zip(probs, got):
+        want = emdq.emdq_field(q, c, s, grid, alpha, precision=emdq.BF16)
+        torch.cuda.synchronize()
+        assert torch.equal(torch.isnan(g), torch.isnan(want))
+        assert torch.equal(torch.nan_to_num(g), torch.nan_to_num(want))
+
+
+def test_field_batch_of_16_against_the_oracle(emdq, orc):
+    rng = np.random.default_rng(78)
+    probs, host = [], []
+    for b in range(16):
+        w, h = [(640, 480), (1280, 720), (1280, 1024), (1920, 1080)][b % 4]
+        n = int(rng.integers(100, 1500))
+        q, c, s, hq = _field_case(rng, n, w, h)
+        grid = (int(rng.integers(-20, 20)), int(rng.integers(-20, 20)), int(rng.integers(200, 400)),
+                int(rng.integers(40, 120)))
+        alpha = np.float32(orc.alpha_for_frame(w, h))
+        probs.append((q, c, s, grid, alpha))
+        host.append((hq, grid, alpha))
+    got = emdq.emdq_field_batch(probs)
+    torch.cuda.synchronize()
+    for g, ((q8, c, s), grid, alpha) in zip(got, host):
+        want = orc.field(*_oracle_inputs(q8, c, s), grid, float(alpha))
+        assert np.abs(g.cpu().numpy().astype(np.float64) - want).max() <= TOL[1]
+
+
+def test_field_batch_errors(emdq):
+    rng = np.random.default_rng(79)
+    q, c, s, _ = _field_case(rng, 50, 640, 480)
+    p = (q, c, s, (0, 0, 64, 32), 1e-4)
+    with pytest.raises(emdq.EmdqError):
+        emdq.emdq_field_batch([p] * 17)
+    with pytest.raises(emdq.EmdqError):
+        emdq.emdq_field_batch([(q, c, s, (0, 0, 64, 32), -1.0)])
+    with pytest.raises(emdq.EmdqError):
+        emdq.emdq_field_batch([(q, c, s, (0, 0, 0, 32), 1e-4)])
