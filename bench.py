@@ -79,7 +79,8 @@ def parse_args():
                     help='issue every call each step (default: the pass is captured once into a '
                          'CUDA graph and replayed, removing per-call launch overhead)')
     ap.add_argument('--field-group', type=int, default=4,
-                    help='frames per emdq_field_batch call (BF16 field, pipelined path)')
+                    help='frames per emdq_field_batch / mosaic_warp_batch call (BF16, pipelined '
+                         'path; at most 8 for the sequence, 16 for the mixed batch)')
     ap.add_argument('--no-pipeline', action='store_true',
                     help='field and warp of every frame on one stream (default: the warp of frame k '
                          'on a second stream, beside the field of frame k + 1)')
@@ -279,7 +280,7 @@ def run_gpu(args, ws, rank, local):
     # main stream) into buffer set g % 2, their warps on the warp stream after that call, in
     # frame order (the blend is order-dependent) while the next group's fields run
     piped = not fused and not args.no_pipeline
-    G = max(1, min(16, args.field_group)) if piped and prec == emdq.BF16 else 1
+    G = max(1, min(8, args.field_group)) if piped and prec == emdq.BF16 else 1
     warp_stream = torch.cuda.Stream(device=dev) if piped else None
     if piped and prec == emdq.BF16:
         zq = torch.zeros((n, 8), device=dev)
@@ -331,10 +332,14 @@ def run_gpu(args, ws, rank, local):
         if evs3 is not None:
             for e3 in evs3: e3[0].record(stream)
         warp_stream.wait_event(fdone)
-        for i in range(len(frs)):
-            if evs3 is not None: evs3[i][1].record(warp_stream)
-            emdq.mosaic_warp(frs[i], disps[i], gs[i], canvas, origin, stream=warp_stream)
-            if evs3 is not None: evs3[i][2].record(warp_stream)
+        # one launch blends the group's frames in order (the first frame's events span it,
+        # the others' are empty, so per-frame sums stay right)
+        if evs3 is not None: evs3[0][1].record(warp_stream)
+        emdq.mosaic_warp_batch(frs, disps, gs, canvas, origin, stream=warp_stream)
+        if evs3 is not None:
+            for i in range(len(frs)):
+                if i: evs3[i][1].record(warp_stream)
+                evs3[i][2].record(warp_stream)
         wdone = torch.cuda.Event()
         wdone.record(warp_stream)
         slot_free[slot] = wdone
@@ -672,7 +677,8 @@ def run_gpu(args, ws, rank, local):
         kernel_ms_per_step={k: v / args.steps for k, v in kernel_total.items()},
         path=(('learned warm start + ' if warm else '') + ('emdq_fit_batch' if B > 1 else 'emdq_fit') +
               (' + emdq_mosaic (fused BF16 field and warp)' if fused else
-               (f' + emdq_field_batch ({G} frames per call, bf16) + mosaic_warp on a second stream'
+               (f' + emdq_field_batch + mosaic_warp_batch ({G} frames per call, bf16; the warps on a '
+                f'second stream)'
                 if piped and prec == emdq.BF16 else f' + emdq_field ({args.precision}) + mosaic_warp')) +
               (', fits of the next batch on a second stream' if overlap else '') +
               (', the pass replayed from one CUDA graph' if graph is not None else '')),

@@ -37,6 +37,11 @@ class _Params(ctypes.Structure):
                 ('reserved', ctypes.c_int * 4)]
 
 
+class _MosaicFrame(ctypes.Structure):
+    _fields_ = [('frame', ctypes.c_void_p), ('disp', ctypes.c_void_p), ('grid_x0', ctypes.c_int),
+                ('grid_y0', ctypes.c_int), ('grid_w', ctypes.c_int), ('grid_h', ctypes.c_int)]
+
+
 class _FieldProblem(ctypes.Structure):
     _fields_ = [('q', ctypes.c_void_p), ('c', ctypes.c_void_p), ('src', ctypes.c_void_p),
                 ('n', ctypes.c_int), ('grid_x0', ctypes.c_int), ('grid_y0', ctypes.c_int),
@@ -95,6 +100,8 @@ def lib() -> ctypes.CDLL:
             L.emdq_field_batch.argtypes = [P, I, P, Z, P]
             L.emdq_field.restype = I
             L.emdq_field.argtypes = [P, P, P, I, I, I, I, I, F, I, P, P, Z, P]
+            L.mosaic_warp_batch.restype = I
+            L.mosaic_warp_batch.argtypes = [P, I, I, I, I, I, P, I, I, I, I, I, P]
             L.mosaic_warp.restype = I
             L.mosaic_warp.argtypes = [P, I, I, I, I, P, I, I, I, I, P, I, I, I, I, I, P]
             L.emdq_mosaic.restype = I
@@ -369,6 +376,31 @@ def mosaic_warp(frame: torch.Tensor, disp: torch.Tensor, grid, canvas: torch.Ten
                            _stream(stream))
     if rc != 0:
         raise EmdqError('mosaic_warp', rc)
+
+
+def mosaic_warp_batch(frames, disps, grids, canvas: torch.Tensor, origin, stream=None) -> None:
+    """Blend up to 8 frames (same size and channels) into canvas in one launch, each through
+    its own field and window; the canvas ends as after mosaic_warp on each in order."""
+    count = len(frames)
+    if not (len(disps) == len(grids) == count) or count < 1:
+        raise ValueError('one field and one window per frame')
+    fw, fh, ch, pitch = _frame_args(frames[0])
+    arr = (_MosaicFrame * count)()
+    for k, (fr, d, g) in enumerate(zip(frames, disps, grids)):
+        if _frame_args(fr) != (fw, fh, ch, pitch):
+            raise ValueError('frames of one sequence: the same size and channels')
+        x0, y0, gw, gh = (int(v) for v in g)
+        _check(d, 'disp', torch.float32, (gh, gw, 2))
+        arr[k] = _MosaicFrame(_ptr(fr), _ptr(d), x0, y0, gw, gh)
+    _check(canvas, 'canvas', torch.uint8)
+    if canvas.dim() != 3 or canvas.shape[2] != 4:
+        raise ValueError('canvas must be [h, w, 4] uint8')
+    chh, cw = canvas.shape[:2]
+    rc = lib().mosaic_warp_batch(ctypes.cast(arr, ctypes.c_void_p), count, fw, fh, ch, pitch,
+                                 _ptr(canvas), cw, chh, cw * 4, int(origin[0]), int(origin[1]),
+                                 _stream(stream))
+    if rc != 0:
+        raise EmdqError('mosaic_warp_batch', rc)
 
 
 def emdq_mosaic(q: torch.Tensor, c: torch.Tensor, src: torch.Tensor, grid, alpha: float,

@@ -48,6 +48,55 @@ __global__ void __launch_bounds__(kWarpThreadsX) mosaic_warp_kernel(
         if (t[k].ok) *cp[k] = blend_update<CH>(cv[k], v[k]);
 }
 
+// G frames of a sequence blended in one pass: the thread of canvas pixel p applies frames
+// 0..G-1 to p in order, exactly as G mosaic_warp launches would (the blend of a pixel
+// depends only on that pixel's earlier updates), but reads and writes the canvas word
+// once, and issues the field loads and bilinear taps of all G frames before any update, so
+// their memory latencies overlap.  Threads cover the union of the G windows.
+constexpr int kWarpBatchMax = 8;
+
+struct WarpFrame {
+    const uint8_t *frame;
+    const float2 *disp;
+    int gx0, gy0, gw, gh;
+};
+
+struct WarpBatch {
+    WarpFrame f[kWarpBatchMax];
+};
+
+template <int CH, int G>
+__global__ void __launch_bounds__(kWarpThreadsX) mosaic_warp_batch_kernel(
+    const __grid_constant__ WarpBatch W, int fw, int fh, int pitch, int ux0, int uy0, int uw,
+    uchar4 *__restrict__ canvas, int cpitch4, int ox, int oy)
+{
+    const int x = ux0 + blockIdx.x * kWarpThreadsX + threadIdx.x;   // reference coordinates
+    const int y = uy0 + blockIdx.y;
+    if (x >= ux0 + uw) return;
+    Tap t[G];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+        const WarpFrame &F = W.f[k];
+        const int lx = x - F.gx0, ly = y - F.gy0;
+        float2 d = make_float2(NAN, NAN);
+        if (lx >= 0 && lx < F.gw && ly >= 0 && ly < F.gh) d = __ldcs(F.disp + (size_t)ly * F.gw + lx);
+        t[k] = tap_setup<CH>(fw, fh, pitch, static_cast<float>(x), static_cast<float>(y), d.x, d.y);
+        any = any || t[k].ok;
+    }
+    if (!any) return;
+    uchar4 *cp = canvas + (size_t)(y + oy) * cpitch4 + (x + ox);
+    uchar4 cv = *cp;
+    float v[G][CH];
+#pragma unroll
+    for (int k = 0; k < G; ++k)
+        if (t[k].ok) tap_sample<CH>(W.f[k].frame, t[k], v[k]);
+#pragma unroll
+    for (int k = 0; k < G; ++k)
+        if (t[k].ok) cv = blend_update<CH>(cv, v[k]);
+    *cp = cv;
+}
+
 template <int CH>
 __global__ void insert_reference_kernel(const uint8_t *__restrict__ frame, int fw, int fh,
                                         int pitch, uchar4 *__restrict__ canvas, int cpitch4,
@@ -122,4 +171,83 @@ extern "C" emdq_status mosaic_insert_reference(const uint8_t *frame, int fw, int
         insert_reference_kernel<1><<<grid, 128, 0, st>>>(frame, fw, fh, frame_pitch, cv,
                                                          canvas_pitch / 4, origin_x, origin_y);
     return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
+}
+
+namespace {
+template <int CH, int G>
+cudaError_t launch_warp_batch(const WarpBatch &W, dim3 grid, cudaStream_t st, int fw, int fh,
+                              int pitch, int ux0, int uy0, int uw, uchar4 *cv, int cpitch4, int ox,
+                              int oy)
+{
+    mosaic_warp_batch_kernel<CH, G><<<grid, kWarpThreadsX, 0, st>>>(W, fw, fh, pitch, ux0, uy0, uw, cv,
+                                                                    cpitch4, ox, oy);
+    return cudaGetLastError();
+}
+
+template <int CH>
+cudaError_t dispatch_warp_batch(int count, const WarpBatch &W, dim3 grid, cudaStream_t st, int fw,
+                                int fh, int pitch, int ux0, int uy0, int uw, uchar4 *cv, int cpitch4,
+                                int ox, int oy)
+{
+    switch (count) {
+    case 1: return launch_warp_batch<CH, 1>(W, grid, st, fw, fh, pitch, ux0, uy0, uw, cv, cpitch4, ox, oy);
+    case 2: return launch_warp_batch<CH, 2>(W, grid, st, fw, fh, pitch, ux0, uy0, uw, cv, cpitch4, ox, oy);
+    case 3: return launch_warp_batch<CH, 3>(W, grid, st, fw, fh, pitch, ux0, uy0, uw, cv, cpitch4, ox, oy);
+    case 4: return launch_warp_batch<CH, 4>(W, grid, st, fw, fh, pitch, ux0, uy0, uw, cv, cpitch4, ox, oy);
+    case 5: return launch_warp_batch<CH, 5>(W, grid, st, fw, fh, pitch, ux0, uy0, uw, cv, cpitch4, ox, oy);
+    case 6: return launch_warp_batch<CH, 6>(W, grid, st, fw, fh, pitch, ux0, uy0, uw, cv, cpitch4, ox, oy);
+    case 7: return launch_warp_batch<CH, 7>(W, grid, st, fw, fh, pitch, ux0, uy0, uw, cv, cpitch4, ox, oy);
+    default: return launch_warp_batch<CH, 8>(W, grid, st, fw, fh, pitch, ux0, uy0, uw, cv, cpitch4, ox, oy);
+    }
+}
+}  // namespace
+
+extern "C" emdq_status mosaic_warp_batch(const mosaic_frame *frames, int count, int fw, int fh,
+                                         int channels, int frame_pitch, uint8_t *canvas,
+                                         int canvas_w, int canvas_h, int canvas_pitch, int origin_x,
+                                         int origin_y, void *stream)
+{
+    if (!frames || count < 1 || !canvas || fw < 1 || fh < 1 || (channels != 1 && channels != 3) ||
+        frame_pitch < fw * channels || canvas_w < 1 || canvas_h < 1 ||
+        canvas_pitch < 4 * canvas_w || canvas_pitch % 4 != 0)
+        return EMDQ_EINVAL;
+    if (count > kWarpBatchMax) return EMDQ_ENOTSUP;
+    if (!aligned(canvas, 4)) return EMDQ_EINVAL;
+    WarpBatch W = {};
+    long long ux0 = 0, uy0 = 0, ux1 = 0, uy1 = 0;
+    int used = 0;
+    for (int k = 0; k < count; ++k) {
+        const mosaic_frame &f = frames[k];
+        if (!f.frame || f.grid_w < 0 || f.grid_h < 0) return EMDQ_EINVAL;
+        if (f.grid_w == 0 || f.grid_h == 0) continue;      // empty window: nothing to blend
+        if (!f.disp || !aligned(f.disp, 8)) return EMDQ_EINVAL;
+        if ((long long)f.grid_x0 + origin_x < 0 || (long long)f.grid_y0 + origin_y < 0 ||
+            (long long)f.grid_x0 + origin_x + f.grid_w > canvas_w ||
+            (long long)f.grid_y0 + origin_y + f.grid_h > canvas_h)
+            return EMDQ_EINVAL;
+        W.f[used] = WarpFrame{f.frame, reinterpret_cast<const float2 *>(f.disp), f.grid_x0,
+                              f.grid_y0, f.grid_w, f.grid_h};
+        const long long x0 = f.grid_x0, y0 = f.grid_y0, x1 = x0 + f.grid_w, y1 = y0 + f.grid_h;
+        if (used == 0) {
+            ux0 = x0; uy0 = y0; ux1 = x1; uy1 = y1;
+        } else {
+            ux0 = x0 < ux0 ? x0 : ux0;
+            uy0 = y0 < uy0 ? y0 : uy0;
+            ux1 = x1 > ux1 ? x1 : ux1;
+            uy1 = y1 > uy1 ? y1 : uy1;
+        }
+        ++used;
+    }
+    if (used == 0) return EMDQ_OK;
+    const int uw = (int)(ux1 - ux0), uh = (int)(uy1 - uy0);
+    if (uh > 65535) return EMDQ_ENOTSUP;
+    const dim3 grid((uw + kWarpThreadsX - 1) / kWarpThreadsX, uh);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    auto *cv = reinterpret_cast<uchar4 *>(canvas);
+    const cudaError_t e =
+        channels == 3 ? dispatch_warp_batch<3>(used, W, grid, st, fw, fh, frame_pitch, (int)ux0,
+                                               (int)uy0, uw, cv, canvas_pitch / 4, origin_x, origin_y)
+                      : dispatch_warp_batch<1>(used, W, grid, st, fw, fh, frame_pitch, (int)ux0,
+                                               (int)uy0, uw, cv, canvas_pitch / 4, origin_x, origin_y);
+    return e == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }

@@ -115,3 +115,50 @@ def test_warp_sequence_full_size_sampled(emdq, orc):
         got = canvas[y0 + origin[1]:y0 + origin[1] + 1].cpu().numpy()
         np.testing.assert_array_equal(got[..., 3], cv_o[..., 3])
         assert np.abs(got[..., :3].astype(int) - cv_o[..., :3].astype(int)).max() <= 1
+
+
+@pytest.mark.parametrize('ch', [1, 3])
+@pytest.mark.parametrize('count', [1, 2, 3, 5, 8])
+def test_warp_batch_equals_calls_in_order(emdq, ch, count):
+    """mosaic_warp_batch leaves the canvas bit for bit as count mosaic_warp calls in order:
+    overlapping, disjoint, ragged and empty windows, integer and fractional shifts."""
+    rng = np.random.default_rng(500 + 10 * count + ch)
+    fh, fw = 97, 131
+    shape = (fh, fw) if ch == 1 else (fh, fw, ch)
+    canvas0 = rng.integers(0, 256, (300, 320, 4), dtype=np.uint8)
+    canvas0[..., 3] = rng.integers(0, 31, (300, 320), dtype=np.uint8)
+    origin = (90, 100)
+    frames, disps, grids = [], [], []
+    for k in range(count):
+        frames.append(torch.from_numpy(rng.integers(0, 256, shape, dtype=np.uint8)).cuda())
+        if k == 2:
+            grid = (40, 30, 0, 10)                               # empty window
+        else:
+            gw, gh = int(rng.integers(20, 140)), int(rng.integers(10, 110))
+            grid = (int(rng.integers(-60, 60)), int(rng.integers(-60, 60)), gw, gh)
+        d = _smooth_disp(rng, grid[3], grid[2], rng.uniform(0, 6),
+                         base=(float(rng.integers(-8, 8)), float(rng.uniform(-8, 8))))
+        if k % 3 == 1:
+            d = np.round(d)                                      # integer shifts
+        disps.append(torch.from_numpy(d).cuda())
+        grids.append(grid)
+    cv_seq = torch.from_numpy(canvas0).cuda()
+    for fr, d, g in zip(frames, disps, grids):
+        emdq.mosaic_warp(fr, d, g, cv_seq, origin)
+    cv_bat = torch.from_numpy(canvas0).cuda()
+    emdq.mosaic_warp_batch(frames, disps, grids, cv_bat, origin)
+    torch.cuda.synchronize()
+    assert torch.equal(cv_seq, cv_bat)
+
+
+def test_warp_batch_errors(emdq):
+    fr = torch.zeros((8, 8, 3), dtype=torch.uint8, device='cuda')
+    d = torch.zeros((4, 4, 2), device='cuda')
+    cv = torch.zeros((32, 32, 4), dtype=torch.uint8, device='cuda')
+    with pytest.raises(emdq.EmdqError):
+        emdq.mosaic_warp_batch([fr] * 9, [d] * 9, [(0, 0, 4, 4)] * 9, cv, (4, 4))
+    with pytest.raises(emdq.EmdqError):                    # window outside the canvas
+        emdq.mosaic_warp_batch([fr], [d], [(30, 30, 4, 4)], cv, (4, 4))
+    with pytest.raises(ValueError):
+        emdq.mosaic_warp_batch([fr, torch.zeros((8, 9, 3), dtype=torch.uint8, device='cuda')],
+                               [d, d], [(0, 0, 4, 4)] * 2, cv, (4, 4))
