@@ -84,6 +84,10 @@ def parse_args():
     ap.add_argument('--no-pipeline', action='store_true',
                     help='field and warp of every frame on one stream (default: the warp of frame k '
                          'on a second stream, beside the field of frame k + 1)')
+    ap.add_argument('--fit-ctas', type=int, default=0,
+                    help='CTAs of one fit launch, split evenly over its frames (default: every '
+                         'co-resident CTA; 152 = one per SM, which leaves room beside the GEMM '
+                         'for --overlap)')
     ap.add_argument('--overlap', action='store_true',
                     help='run the next batch of fits on a second stream while the current batch is '
                          'blended (default: one stream; the cooperative fit launch occupies every '
@@ -358,9 +362,13 @@ def run_gpu(args, ws, rank, local):
                 emdq.emdq_fit(s_of(ks[0]), d_of(ks[0]), sc.w, sc.h, p0=p0s[0], out=outs[0],
                               workspace=fit_ws_all[bi % nbuf], stream=fit_stream)
             else:
+                split = None
+                if args.fit_ctas > 0:
+                    per, extra = divmod(args.fit_ctas, len(ks))
+                    split = [max(1, per + (1 if j < extra else 0)) for j in range(len(ks))]
                 emdq.emdq_fit_batch([(s_of(k), d_of(k), sc.w, sc.h, p0s[j]) for j, k in enumerate(ks)],
                                     outs=outs[: len(ks)], workspace=batch_ws[bi % nbuf],
-                                    stream=fit_stream)
+                                    ctas=split, stream=fit_stream)
             if ev: ev[2].record(fit_stream)
             done = torch.cuda.Event()
             done.record(fit_stream)
@@ -457,7 +465,7 @@ def run_gpu(args, ws, rank, local):
 
     # CUDA graph of one pass (one stream): captured once, replayed every step
     graph, graph_note, gevs = None, None, None
-    if not args.no_graph and not overlap:
+    if not args.no_graph:
         saved = (stream, fit_stream)
         try:
             gevs = new_events(external=True)
@@ -876,6 +884,52 @@ def run_gpu_mixed(args, ws, rank, local):
     iters = iv[:, :, 1].numpy()
     statuses = sorted({emdq.STATUS.get(int(v), '?') for v in iv[:, :, 0].flatten().tolist()})
     nz = [int((x['out']['c'] > 0).sum().item()) for x in P]
+    # end to end through the single public call: per step the H2D copy of every pair's frame
+    # and matches from pinned host buffers, emdq_batch (warm start, fits, fields, warps on one
+    # stream), and the D2H of the fit records and field weights; its device time without the
+    # copies is reported beside it
+    e2e, native_ms = None, None
+    if not args.no_e2e:
+        pairs_native = [dict(src=x['src'], dst=x['dst'], frame=x['frame'], grid=x['grid'],
+                             canvas=x['canvas'], origin=x['origin']) for x in P]
+        bws = torch.empty(emdq.batch_workspace_size(pairs_native, warm=True), dtype=torch.uint8, device=dev)
+        hf = [x['frame'].cpu().pin_memory() for x in P]
+        hs = [x['src'].cpu().pin_memory() for x in P]
+        hd = [x['dst'].cpu().pin_memory() for x in P]
+        h_infos = torch.empty((len(P), 4), dtype=torch.int32).pin_memory()
+        h_cs = [torch.empty(x['n'], dtype=torch.float32).pin_memory() for x in P]
+        outs = [x['out'] for x in P]
+        e_steps = max(1, min(args.steps, 5))
+        e_ms, n_ms = [], []
+        main = torch.cuda.current_stream()
+        for i in range(2 * (1 + e_steps)):
+            copies = i % 2 == 0
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main)
+            if copies:
+                for k, x in enumerate(P):
+                    x['frame'].copy_(hf[k], non_blocking=True)
+                    x['src'].copy_(hs[k], non_blocking=True)
+                    x['dst'].copy_(hd[k], non_blocking=True)
+            emdq.emdq_batch(pairs_native, warm_params=warm_params, fit_ctas=ctas, outs=outs, workspace=bws)
+            if copies:
+                for k, x in enumerate(P):
+                    infos[k].copy_(x['out']['info'])
+                    h_cs[k].copy_(x['out']['c'], non_blocking=True)
+                h_infos.copy_(infos, non_blocking=True)
+            b.record(main)
+            b.synchronize()
+            if i >= 2:
+                (e_ms if copies else n_ms).append(a.elapsed_time(b))
+        e_total = max_over_ranks(float(np.sum(e_ms)), ws, dev)
+        native_ms = max_over_ranks(float(np.mean(n_ms)), ws, dev)
+        px_all = sum(x['sc'].w * x['sc'].h for x in P)
+        e2e = dict(value=ws * len(e_ms) * px_all / 1e6 / (e_total / 1e3), unit=UNIT,
+                   call='emdq_batch', ms_per_step=e_total / len(e_ms),
+                   h2d_bytes_per_step=int(sum(x['frame'].numel() + x['src'].numel() * 8 for x in P)),
+                   d2h_bytes_per_step=int(sum(16 + 4 * x['n'] for x in P)))
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -926,7 +980,8 @@ def run_gpu_mixed(args, ws, rank, local):
              (', the step replayed from one CUDA graph' if graph is not None else ''),
         cuda_graph=graph is not None, **({'cuda_graph_note': graph_note} if graph_note else {}),
         autotune_fit_ms=tune_ms, mean_em_iters=float(np.mean(iters)), roofline=roof,
-        gpu_launches=args.steps * (2 + 2 * len(P)), clocks=clk, e2e=None, fit_status=statuses,
+        gpu_launches=args.steps * (2 + 2 * len(groups) + len(P)), clocks=clk, e2e=e2e, fit_status=statuses,
+        emdq_batch_device_ms=native_ms,
         p50_note='per step: the whole batch of 64 pairs is one unit of latency')
     if not args.no_cpu_baseline:
         line['cpu_baseline'] = cpu_baseline_mixed(args, budget_s=12.0)

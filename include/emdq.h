@@ -290,6 +290,41 @@ EMDQ_API emdq_status mosaic_warp_batch(const mosaic_frame *frames, int count, in
                                        int canvas_w, int canvas_h, int canvas_pitch, int origin_x,
                                        int origin_y, void *stream);
 
+/* ------------------------------------------------------------------ emdq_batch -------
+ * The whole path for a batch of independent pairs in one call (not in the paper: a
+ * batching front end).  On `stream`, in order: the learned warm start of every pair (when
+ * warm_params is not NULL; else plain EM from p = 1), all EMDQ fits in one cooperative
+ * launch (CTAs split per fit_ctas, or in proportion to n^2 when it is NULL), the BF16
+ * fields of up to 16 pairs per emdq_field_batch call, and after each such call the warps of
+ * its pairs in array order (pairs that share a canvas are blended in that order).  Every
+ * pair's results are those of emdq_warm_start, emdq_fit_batch_ex, emdq_field (EMDQ_BF16)
+ * and mosaic_warp on the same arguments.  Capturable into a CUDA graph.
+ *
+ *   pairs        host array of `count` descriptors (1..64)
+ *   prm          host; NULL = defaults; alpha = 0 derives each pair's from its frame size
+ *   warm_params  device, emdq_mlp_param_count() floats, or NULL
+ *   fit_ctas     host, count ints (emdq_fit_batch_ex), or NULL
+ *   workspace    device, emdq_batch_workspace_size(pairs, count, warm_params != NULL) bytes,
+ *                256-byte aligned, not shared with a call in flight
+ */
+typedef struct {
+    const float *src, *dst;         /* device, n x 2 float: the matches */
+    int n, frame_w, frame_h;
+    const uint8_t *frame;           /* device, frame t: frame_h rows of frame_pitch bytes */
+    int channels, frame_pitch;
+    int grid_x0, grid_y0, grid_w, grid_h;   /* the window, reference coordinates */
+    uint8_t *canvas;                /* device, canvas_h rows of canvas_pitch bytes (4 per pixel) */
+    int canvas_w, canvas_h, canvas_pitch, origin_x, origin_y;
+    float *q_out, *c_out;           /* device, n x 8 and n float (written) */
+    float *p_out;                   /* device, n float (written) or NULL */
+    emdq_fit_info *info;            /* device (written) */
+} emdq_pair;
+
+EMDQ_API size_t      emdq_batch_workspace_size(const emdq_pair *pairs, int count, int warm);
+EMDQ_API emdq_status emdq_batch(const emdq_pair *pairs, int count, const emdq_params *prm,
+                                const float *warm_params, const int *fit_ctas, void *workspace,
+                                size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------------------------ emdq_mosaic ------
  * emdq_field (EMDQ_BF16) and mosaic_warp fused in one tensor-core kernel: for every grid
  * pixel the displacement of Eqs. 1-4 is computed exactly as emdq_field computes it and

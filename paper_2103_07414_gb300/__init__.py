@@ -16,7 +16,8 @@ import torch
 
 from ._build import LIB as _LIB_PATH, build  # noqa: F401
 
-__all__ = ['emdq_fit', 'emdq_fit_batch', 'emdq_field', 'mosaic_warp', 'emdq_mosaic', 'mosaic_insert_reference',
+__all__ = ['emdq_fit', 'emdq_fit_batch', 'emdq_field', 'emdq_field_batch', 'mosaic_warp',
+           'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'mosaic_insert_reference',
            'alpha_for_frame', 'fit_workspace_size', 'field_workspace_size', 'EmdqError',
            'FP32', 'BF16', 'STATUS', 'lib', 'build']
 
@@ -47,6 +48,17 @@ class _FieldProblem(ctypes.Structure):
                 ('n', ctypes.c_int), ('grid_x0', ctypes.c_int), ('grid_y0', ctypes.c_int),
                 ('grid_w', ctypes.c_int), ('grid_h', ctypes.c_int), ('alpha', ctypes.c_float),
                 ('disp_out', ctypes.c_void_p)]
+
+
+class _Pair(ctypes.Structure):
+    _fields_ = [('src', ctypes.c_void_p), ('dst', ctypes.c_void_p), ('n', ctypes.c_int),
+                ('frame_w', ctypes.c_int), ('frame_h', ctypes.c_int), ('frame', ctypes.c_void_p),
+                ('channels', ctypes.c_int), ('frame_pitch', ctypes.c_int), ('grid_x0', ctypes.c_int),
+                ('grid_y0', ctypes.c_int), ('grid_w', ctypes.c_int), ('grid_h', ctypes.c_int),
+                ('canvas', ctypes.c_void_p), ('canvas_w', ctypes.c_int), ('canvas_h', ctypes.c_int),
+                ('canvas_pitch', ctypes.c_int), ('origin_x', ctypes.c_int), ('origin_y', ctypes.c_int),
+                ('q_out', ctypes.c_void_p), ('c_out', ctypes.c_void_p), ('p_out', ctypes.c_void_p),
+                ('info', ctypes.c_void_p)]
 
 
 class _Problem(ctypes.Structure):
@@ -101,6 +113,9 @@ def lib() -> ctypes.CDLL:
             L.emdq_field.restype = I
             L.emdq_field.argtypes = [P, P, P, I, I, I, I, I, F, I, P, P, Z, P]
             L.mosaic_warp_batch.restype = I
+            L.emdq_batch_workspace_size.argtypes = [P, I, I]
+            L.emdq_batch_workspace_size.restype = Z
+            L.emdq_batch.argtypes = [P, I, ctypes.POINTER(_Params), P, P, P, Z, P]
             L.mosaic_warp_batch.argtypes = [P, I, I, I, I, I, P, I, I, I, I, I, P]
             L.mosaic_warp.restype = I
             L.mosaic_warp.argtypes = [P, I, I, I, I, P, I, I, I, I, P, I, I, I, I, I, P]
@@ -401,6 +416,75 @@ def mosaic_warp_batch(frames, disps, grids, canvas: torch.Tensor, origin, stream
                                  _stream(stream))
     if rc != 0:
         raise EmdqError('mosaic_warp_batch', rc)
+
+
+def _pair_args(pairs, outs):
+    count = len(pairs)
+    arr = (_Pair * max(1, count))()
+    results = []
+    for b, pr in enumerate(pairs):
+        src, dst, frame, canvas = pr['src'], pr['dst'], pr['frame'], pr['canvas']
+        n = src.shape[0]
+        _check(src, 'src', torch.float32, (n, 2))
+        _check(dst, 'dst', torch.float32, (n, 2))
+        fw, fh, ch, pitch = _frame_args(frame)
+        _check(canvas, 'canvas', torch.uint8)
+        if canvas.dim() != 3 or canvas.shape[2] != 4:
+            raise ValueError('canvas must be [h, w, 4] uint8')
+        chh, cw = canvas.shape[:2]
+        x0, y0, gw, gh = (int(v) for v in pr['grid'])
+        ox, oy = (int(v) for v in pr['origin'])
+        o = outs[b] if outs is not None else {}
+        dev = src.device
+        r = dict(q=o.get('q') if o.get('q') is not None else torch.empty((n, 8), device=dev),
+                 c=o.get('c') if o.get('c') is not None else torch.empty(n, device=dev),
+                 p=o.get('p') if o.get('p') is not None else torch.empty(n, device=dev),
+                 info=o.get('info') if o.get('info') is not None else
+                 torch.zeros(4, dtype=torch.int32, device=dev))
+        arr[b] = _Pair(src.data_ptr(), dst.data_ptr(), n, fw, fh, frame.data_ptr(), ch, pitch,
+                       x0, y0, gw, gh, canvas.data_ptr(), cw, chh, cw * 4, ox, oy,
+                       r['q'].data_ptr(), r['c'].data_ptr(), r['p'].data_ptr(), r['info'].data_ptr())
+        results.append(r)
+    return arr, results
+
+
+def batch_workspace_size(pairs, warm: bool = False) -> int:
+    """Bytes of workspace for emdq_batch on these pairs (with or without the warm start)."""
+    arr, _ = _pair_args(pairs, None)
+    return lib().emdq_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), len(pairs), int(warm))
+
+
+def emdq_batch(pairs, *, warm_params: torch.Tensor | None = None, fit_ctas=None,
+               alpha: float = 0.0, max_iters: int = 20, tol_p: float = 1e-3,
+               sigma2_floor: float = 0.25, outs: list | None = None,
+               workspace: torch.Tensor | None = None, stream=None) -> list:
+    """The whole path for up to 64 independent pairs in one call: warm start (if
+    warm_params), all fits in one launch, BF16 fields 16 pairs per launch pair, and each
+    pair's warp into its canvas in list order.  pairs: dicts with src, dst ([n, 2] float32),
+    frame ([h, w] or [h, w, 1|3] uint8), grid (x0, y0, w, h), canvas ([H, W, 4] uint8) and
+    origin (x, y).  Returns one dict per pair (q, c, p, info) as emdq_fit does."""
+    count = len(pairs)
+    arr, results = _pair_args(pairs, outs)
+    if warm_params is not None:
+        _check(warm_params, 'warm_params', torch.float32, (lib().emdq_mlp_param_count(),))
+    need = lib().emdq_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), count,
+                                           int(warm_params is not None))
+    if need == 0:
+        raise EmdqError('emdq_batch_workspace_size', 1)
+    ws = _workspace(need, pairs[0]['src'].device, workspace)
+    prm = _Params(float(alpha), int(max_iters), float(tol_p), float(sigma2_floor), (ctypes.c_int * 4)())
+    split = None
+    if fit_ctas is not None:
+        if len(fit_ctas) != count:
+            raise ValueError('fit_ctas: one entry per pair')
+        split = (ctypes.c_int * count)(*[int(v) for v in fit_ctas])
+    rc = lib().emdq_batch(ctypes.cast(arr, ctypes.c_void_p), count, ctypes.byref(prm),
+                          _ptr(warm_params),
+                          ctypes.cast(split, ctypes.c_void_p) if split is not None else None,
+                          _ptr(ws), ws.numel(), _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_batch', rc)
+    return results
 
 
 def emdq_mosaic(q: torch.Tensor, c: torch.Tensor, src: torch.Tensor, grid, alpha: float,

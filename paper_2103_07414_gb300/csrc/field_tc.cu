@@ -58,7 +58,11 @@ constexpr uint32_t kTcAccCols = 256;     // one accumulator: 192 columns used
 constexpr uint32_t kTcTmemCols = 2 * kTcAccCols;
 constexpr size_t kTcSmemBytes = kTcStages * kTcStageBytes + 1024 /*barriers*/ + 1024 /*align*/;
 constexpr uint32_t kTcIdesc = tc::idesc_bf16_f32(kTcM, kTcN);
-constexpr int kPrepRows = 8;
+// Operand rows per prep block: each block pays one chain of dependent loads (the
+// nonzero-weight columns, the reference row, its columns' data) before writing rows, so
+// blocks take many rows; G rows carry six planes, so they take fewer than Ex rows.
+constexpr int kPrepRowsA = 32;
+constexpr int kPrepRowsB = 16;
 constexpr int kPrepThreads = 256;
 constexpr long long kWaitLimit = 4000000000LL;   // SM cycles (about 2 s)
 
@@ -169,9 +173,6 @@ __device__ __forceinline__ int problem_of_tile(const TcBatch &Bt, int tile)
 
 __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(const __grid_constant__ TcBatch Bt)
 {
-    // the GEMM launched after this kernel may start its set-up now; it waits for this
-    // grid's completion (griddepcontrol.wait) before it reads anything written here
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ int s_idx[kCompactMax];
     const TcProblem &P = Bt.p[problem_of_block(Bt, blockIdx.x)];
     const int blk = blockIdx.x - P.block0;
@@ -179,7 +180,9 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(const __gri
     const float *__restrict__ c = P.c;
     const float2 *__restrict__ src = P.src;
     const int n = P.n, wp = P.wp, hp = P.hp, gw = P.gw, gh = P.gh;
-    const float alpha = P.alpha;
+    // exp(-alpha d^2) = 2^(-alpha log2(e) d^2) with MUFU.EX2 (the BF16 rounding of the
+    // operands dominates its error)
+    const float alpha2 = P.alpha * 1.4426950408889634f;
     const int half = P.kp / 2;
     const int mc = compact_columns(c, n, s_idx);
     const bool compact = mc >= 0;
@@ -192,24 +195,24 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(const __gri
     auto col = [&](int k) { return compact ? s_idx[k] : k; };
     if (blk < P.a_blocks) {
         __nv_bfloat162 *__restrict__ A = P.A;
-        const int r0 = blk * kPrepRows;
+        const int r0 = blk * kPrepRowsA;
         for (int k2 = threadIdx.x; k2 < halfc; k2 += kPrepThreads) {
             const int k0 = 2 * k2, k1 = k0 + 1;
             const float x0 = k0 < m ? src[col(k0)].x : 0.f, x1 = k1 < m ? src[col(k1)].x : 0.f;
-            for (int r = 0; r < kPrepRows; ++r) {
+            for (int r = 0; r < kPrepRowsA; ++r) {
                 const int px = r0 + r;
                 if (px >= wp) break;
                 const float p = static_cast<float>(P.gx0 + px);
                 const bool row = px < gw;
                 const float d0 = p - x0, d1 = p - x1;
-                const float e0 = (row && k0 < m) ? expf(-alpha * d0 * d0) : 0.f;
-                const float e1 = (row && k1 < m) ? expf(-alpha * d1 * d1) : 0.f;
+                const float e0 = (row && k0 < m) ? ex2_ftz(-alpha2 * d0 * d0) : 0.f;
+                const float e1 = (row && k1 < m) ? ex2_ftz(-alpha2 * d1 * d1) : 0.f;
                 A[(size_t)px * half + k2] = __floats2bfloat162_rn(e0, e1);
             }
         }
     } else {
         __nv_bfloat162 *__restrict__ B = P.B;
-        const int r0 = (blk - P.a_blocks) * kPrepRows;
+        const int r0 = (blk - P.a_blocks) * kPrepRowsB;
         __shared__ float red[6 * 32];
         float rf[6];
         reference_row(q, c, n, red, rf);      // same bits in every block
@@ -236,14 +239,14 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(const __gri
                     cq[u][4] = cw[u] * (s - rf[4]);
                 }
             }
-            for (int r = 0; r < kPrepRows; ++r) {
+            for (int r = 0; r < kPrepRowsB; ++r) {
                 const int py = r0 + r;
                 if (py >= hp) break;
                 const float p = static_cast<float>(P.gy0 + py);
                 const bool row = py < gh;
                 const float d0 = p - y[0], d1 = p - y[1];
-                const float e0 = row ? expf(-alpha * d0 * d0) : 0.f;
-                const float e1 = row ? expf(-alpha * d1 * d1) : 0.f;
+                const float e0 = row ? ex2_ftz(-alpha2 * d0 * d0) : 0.f;
+                const float e1 = row ? ex2_ftz(-alpha2 * d1 * d1) : 0.f;
 #pragma unroll
                 for (int ch = 0; ch < 5; ++ch)
                     B[((size_t)ch * hp + py) * half + k2] =
@@ -252,6 +255,11 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(const __gri
             }
         }
     }
+    // this block's rows are written: the GEMM launched after this kernel may start its
+    // set-up once every block is here (it still waits, griddepcontrol.wait, for the whole
+    // grid before it reads the operands).  Triggered only now, so that the GEMM's large
+    // CTAs do not crowd the prep blocks out of the SMs.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // CH = 0: write the displacement field; CH = 1 or 3: blend the frame into the canvas.
@@ -559,8 +567,8 @@ emdq_status tc_problem(TcBatch &Bt, int b, const float *q, const float *c, const
     P.tile0 = b == 0 ? 0 : Bt.p[b - 1].tile0 + Bt.p[b - 1].ntiles;
     P.ntiles = P.ntx * (g.hp / kTcPY);
     P.block0 = b == 0 ? 0 : Bt.p[b - 1].block0 + Bt.p[b - 1].nblocks;
-    P.a_blocks = g.wp / kPrepRows;
-    P.nblocks = P.a_blocks + g.hp / kPrepRows;
+    P.a_blocks = g.wp / kPrepRowsA;
+    P.nblocks = P.a_blocks + g.hp / kPrepRowsB;
     return EMDQ_OK;
 }
 
