@@ -57,8 +57,8 @@ def parse_args():
     ap.add_argument('--impl', default='emdq', choices=['emdq', 'reference'])
     ap.add_argument('--precision', default='bf16', choices=['bf16', 'fp32'])
     ap.add_argument('--workload', default='seq1280',
-                    help='seq1280 (the 100-frame sequence), batch64 (64 mixed-size pairs), or another '
-                         'single-size workload of synth')
+                    help='seq1280 (the 100-frame sequence), batch64 (64 mixed-size pairs), seq1920 '
+                         '(the 500-frame 1920x1080 sequence, N=5000), or another workload of synth')
     ap.add_argument('--seed', type=int, default=0)
     ap.add_argument('--frames', type=int, default=0,
                     help='frames per step (default: the whole sequence of the workload)')
@@ -69,8 +69,9 @@ def parse_args():
     ap.add_argument('--no-plain', action='store_true',
                     help='skip the plain FP32 GPU comparison (per-frame emdq_fit + FP32 per-pixel '
                          'field + warp, no warm start, no batching) measured on 10 frames')
-    ap.add_argument('--batch', type=int, default=50,
-                    help='frames whose EM fits share one launch (1: one emdq_fit per frame)')
+    ap.add_argument('--batch', type=int, default=0,
+                    help='frames whose EM fits share one launch (1: one emdq_fit per frame; '
+                         'default: the workload\'s, 50 or 8 for seq1920)')
     ap.add_argument('--no-warm', action='store_true',
                     help='plain EM (default: learned warm start when its parameters ship)')
     ap.add_argument('--fused', action='store_true',
@@ -205,7 +206,11 @@ def workload_config(args, sc, cfg, n_frames, ws) -> dict:
                 frames_per_step=n_frames, parallelism=f'dp{ws} (independent sequences)',
                 l2=f'inputs larger than L2 ({n_frames} distinct frames, '
                    f'{n_frames * sc.w * sc.h * sc.channels / 1e6:.0f} MB per step) and a '
-                   f'256 MiB flush before every step, outside the timed events')
+                   f'256 MiB flush before every step, outside the timed events',
+                **({'camera_pan': f'{math.hypot(*cfg["pan"]):.0f} px/frame, reversing every '
+                                  f'{cfg["pan_turn"]} frames (frame {2 * cfg["pan_turn"]} revisits '
+                                  f'the start)'} if cfg.get('pan_turn') else {}),
+                bump_drift_px_per_frame=cfg['drift'])
 
 
 def prepare_sequence(name: str, seed: int, n_frames: int, device):
@@ -264,7 +269,7 @@ def run_gpu(args, ws, rank, local):
     stream = torch.cuda.current_stream()
 
     fused = prec == emdq.BF16 and args.fused
-    B = max(1, min(args.batch, 64))
+    B = max(1, min(args.batch or cfg.get('batch', 50), 64))
     overlap = args.overlap
     nbuf = 2 if overlap else 1            # fit outputs of two batches in flight
     fit_outs_all = [[dict(q=torch.empty((n, 8), device=dev), c=torch.empty(n, device=dev),

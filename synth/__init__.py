@@ -12,6 +12,7 @@ from .scene import (  # noqa: F401
     make_scene,
     gt_forward,
     gt_inverse,
+    pan_frames,
     texture,
     render_reference,
     render_frame,

@@ -37,6 +37,8 @@ class Scene:
     bump_sigma: float
     bump_drift: np.ndarray       # (B, 2) centre motion per frame (px)
     pan: tuple = (0.0, 0.0)      # extra translation per frame (px, frame coordinates)
+    pan_turn: int = 0            # > 0: the pan reverses every pan_turn frames (out and back,
+                                 # so the camera is over the start again at frame 2 pan_turn)
     wave_k: np.ndarray = field(default=None)     # (K, 2) wave vectors (rad/px)
     wave_phi: np.ndarray = field(default=None)   # (K,) phases
     wave_amp: np.ndarray = field(default=None)   # (C, K) per-channel amplitudes
@@ -50,7 +52,7 @@ def _rng(seed: int, stream: int) -> np.random.Generator:
 def make_scene(seed: int, w: int, h: int, channels: int = 3, rot_deg: float = 5.0,
                scale: float = 1.05, trans=(12.0, -7.0), n_bumps: int = 3,
                bump_amp: float = 8.0, bump_sigma: float = 60.0, drift: float = 0.0,
-               pan=(0.0, 0.0)) -> Scene:
+               pan=(0.0, 0.0), pan_turn: int = 0) -> Scene:
     """Draw a scene: texture waves, bump centres/directions and drift directions."""
     g = _rng(seed, 1)
     bump_c = np.stack([g.uniform(0.15 * w, 0.85 * w, n_bumps),
@@ -73,7 +75,8 @@ def make_scene(seed: int, w: int, h: int, channels: int = 3, rot_deg: float = 5.
     return Scene(w=w, h=h, channels=channels, theta=math.radians(rot_deg), scale=scale,
                  trans=tuple(float(v) for v in trans), bump_c=bump_c, bump_a=bump_a,
                  bump_sigma=float(bump_sigma), bump_drift=bump_drift,
-                 pan=tuple(float(v) for v in pan), wave_k=wave_k, wave_phi=wave_phi,
+                 pan=tuple(float(v) for v in pan), pan_turn=int(pan_turn), wave_k=wave_k,
+                 wave_phi=wave_phi,
                  wave_amp=wave_amp, seed=seed)
 
 
@@ -81,12 +84,24 @@ def _t(a, like: torch.Tensor) -> torch.Tensor:
     return torch.as_tensor(np.asarray(a), dtype=torch.float64, device=like.device)
 
 
+def pan_frames(sc: Scene, t: int) -> float:
+    """Frames of pan travel at frame t: t, or a triangle wave of period 2 pan_turn."""
+    if sc.pan_turn <= 0:
+        return float(t)
+    ph = int(t) % (2 * sc.pan_turn)
+    return float(ph if ph <= sc.pan_turn else 2 * sc.pan_turn - ph)
+
+
+def _similarity_shift(sc: Scene, t: int):
+    k = pan_frames(sc, t)
+    return sc.trans[0] + sc.pan[0] * k / sc.scale, sc.trans[1] + sc.pan[1] * k / sc.scale
+
+
 def gt_forward(sc: Scene, x: torch.Tensor, t: int) -> torch.Tensor:
     """Ground-truth map from reference coordinates x[..., 2] to frame-t coordinates."""
     x = x.to(torch.float64)
     c, s = math.cos(sc.theta), math.sin(sc.theta)
-    tx = sc.trans[0] + sc.pan[0] * t / sc.scale
-    ty = sc.trans[1] + sc.pan[1] * t / sc.scale
+    tx, ty = _similarity_shift(sc, t)
     y0 = sc.scale * (c * x[..., 0] - s * x[..., 1] + tx)
     y1 = sc.scale * (s * x[..., 0] + c * x[..., 1] + ty)
     cen = _t(sc.bump_c + t * sc.bump_drift, x)
@@ -118,8 +133,7 @@ def gt_inverse(sc: Scene, y: torch.Tensor, t: int, iters: int = 10) -> torch.Ten
     """Invert the ground-truth map by Newton's method (generator-only)."""
     y = y.to(torch.float64)
     c, s = math.cos(sc.theta), math.sin(sc.theta)
-    tx = sc.trans[0] + sc.pan[0] * t / sc.scale
-    ty = sc.trans[1] + sc.pan[1] * t / sc.scale
+    tx, ty = _similarity_shift(sc, t)
     u0 = y[..., 0] / sc.scale - tx
     u1 = y[..., 1] / sc.scale - ty
     x = torch.stack([c * u0 + s * u1, -s * u0 + c * u1], dim=-1)   # similarity inverse
@@ -253,12 +267,20 @@ WORKLOADS = {
     # learned warm-start evaluation: 1280x1024, N=2000, 40% outliers
     'warm2000': dict(w=1280, h=1024, channels=3, n=2000, outliers=0.4, noise=1.5,
                      canvas=(4096, 4096), drift=0.0, frames=1),
+    # full sequence: 500 frames 1920x1080 RGB, N=5000, 30% outliers, bumps drifting 1 px/frame,
+    # camera pan of 6 px/frame (at 30 degrees to the x axis) out for 200 frames and back, so
+    # frame 400 revisits the start; fits batched 8 frames per launch; canvas 8192^2
+    'seq1920': dict(w=1920, h=1080, channels=3, n=5000, outliers=0.3, noise=1.5,
+                    canvas=(8192, 8192), drift=1.0, frames=500,
+                    pan=(6.0 * math.cos(math.radians(30.0)), 6.0 * math.sin(math.radians(30.0))),
+                    pan_turn=200, batch=8),
 }
 
 
 def workload(name: str, seed: int = 0) -> tuple[Scene, dict]:
     cfg = dict(WORKLOADS[name])
-    sc = make_scene(seed, cfg['w'], cfg['h'], cfg['channels'], drift=cfg['drift'])
+    sc = make_scene(seed, cfg['w'], cfg['h'], cfg['channels'], drift=cfg['drift'],
+                    pan=cfg.get('pan', (0.0, 0.0)), pan_turn=cfg.get('pan_turn', 0))
     return sc, cfg
 
 

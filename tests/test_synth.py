@@ -1,6 +1,7 @@
 """The input generators (no method arithmetic): the mixed-size batch recipe and the
 sequence workloads have the sizes, counts and rates they are stated to have."""
 import numpy as np
+import pytest
 
 from synth import MIXED_SIZES, WORKLOADS, make_matches, mixed_pairs, workload
 
@@ -36,3 +37,21 @@ def test_sequence_workload_shape():
     s, d, inl = make_matches(sc, 5, cfg['n'], cfg['outliers'], cfg['noise'])
     assert s.shape == (1000, 2) and abs((1 - inl.mean()) - 0.3) < 0.01
     assert set(WORKLOADS) >= {'pair640', 'seq1280', 'warm2000'}
+
+
+def test_full_sequence_pan_revisits_the_start():
+    """The 1920x1080 sequence pans 6 px/frame out for 200 frames and back: frame 400 sees
+    the reference view again (up to the drifting bumps), frame 200 is 1200 px away."""
+    import math
+    import torch
+    from synth import gt_forward, make_scene, pan_frames
+    sc, cfg = workload('seq1920')
+    assert (sc.w, sc.h, cfg['n'], cfg['frames'], cfg['canvas'], cfg['batch']) == \
+        (1920, 1080, 5000, 500, (8192, 8192), 8)
+    assert math.hypot(*sc.pan) == pytest.approx(6.0)
+    assert [pan_frames(sc, t) for t in (0, 1, 200, 201, 399, 400, 450)] == [0, 1, 200, 199, 1, 0, 50]
+    still = make_scene(0, 1920, 1080, 3, drift=0.0, pan=sc.pan, pan_turn=sc.pan_turn)
+    x = torch.tensor([[10.0, 20.0], [1500.0, 900.0]], dtype=torch.float64)
+    assert torch.allclose(gt_forward(still, x, 400), gt_forward(still, x, 0), atol=1e-9)
+    shift = gt_forward(still, x, 200) - gt_forward(still, x, 0)
+    assert torch.allclose(shift.norm(dim=1), torch.full((2,), 1200.0, dtype=torch.float64))
