@@ -26,74 +26,96 @@ constexpr int kMlpThreads = 128;      // also the samples of one training tile
 __device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 // ------------------------------------------------------------------ features ----------
-// One warp per match.  Each lane keeps the 8 nearest of its candidates i = lane + 32 t,
+// One warp per match.  Each lane keeps the 8 nearest of the candidates it is offered,
 // sorted by (distance, index); 8 rounds of a warp-wide lexicographic arg-min then pop the
 // overall 8 nearest in order -- the same set and order as a full sort.  All lanes end with
 // the 16 features.
-__device__ __forceinline__ void knn_features_warp(const float2 *__restrict__ src,
-                                                  const float2 *__restrict__ dst, int n, int j,
-                                                  int lane, float (&f)[2 * kKnn])
+struct Near8 {
+    float d[kKnn];
+    int i[kKnn];
+};
+
+__device__ __forceinline__ void near8_reset(Near8 &L)
 {
-    const float2 xj = src[j];
-    float bd[kKnn];
-    int bi[kKnn];
 #pragma unroll
     for (int k = 0; k < kKnn; ++k) {
-        bd[k] = INFINITY;
-        bi[k] = 0x7fffffff;
+        L.d[k] = INFINITY;
+        L.i[k] = 0x7fffffff;
     }
-    for (int i = lane; i < n; i += 32) {
-        if (i == j) continue;
-        const float2 xi = src[i];
-        // float32, one rounding per operation (the same decision as the oracle's)
-        const float dx = __fsub_rn(xi.x, xj.x), dy = __fsub_rn(xi.y, xj.y);
-        const float d = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-        if (d < bd[kKnn - 1] || (d == bd[kKnn - 1] && i < bi[kKnn - 1])) {
-            float cd = d;
-            int ci = i;
+}
+
+__device__ __forceinline__ bool near8_before(float d, int i, float e, int k)
+{
+    return d < e || (d == e && i < k);
+}
+
+// float32, one rounding per operation (the same decision as the oracle's)
+__device__ __forceinline__ float near_d2(float2 xi, float2 xj)
+{
+    const float dx = __fsub_rn(xi.x, xj.x), dy = __fsub_rn(xi.y, xj.y);
+    return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+}
+
+__device__ __forceinline__ void near8_offer(Near8 &L, float d, int i)
+{
+    if (!near8_before(d, i, L.d[kKnn - 1], L.i[kKnn - 1])) return;
+    float cd = d;
+    int ci = i;
 #pragma unroll
-            for (int s = 0; s < kKnn; ++s) {
-                const bool lt = cd < bd[s] || (cd == bd[s] && ci < bi[s]);
-                const float td = bd[s];
-                const int ti = bi[s];
-                if (lt) {
-                    bd[s] = cd;
-                    bi[s] = ci;
-                    cd = td;
-                    ci = ti;
-                }
-            }
+    for (int s = 0; s < kKnn; ++s) {
+        const bool lt = near8_before(cd, ci, L.d[s], L.i[s]);
+        const float td = L.d[s];
+        const int ti = L.i[s];
+        if (lt) {
+            L.d[s] = cd;
+            L.i[s] = ci;
+            cd = td;
+            ci = ti;
         }
     }
-    float nd[kKnn];
-    int ni[kKnn];
+}
+
+// The warp's 8 nearest over all lanes' lists, ascending (consumes the lists).
+__device__ __forceinline__ void near8_merge(Near8 &L, float (&nd)[kKnn], int (&ni)[kKnn])
+{
 #pragma unroll
     for (int r = 0; r < kKnn; ++r) {
-        float cd = bd[0];
-        int ci = bi[0];
+        float cd = L.d[0];
+        int ci = L.i[0];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const float od = __shfl_xor_sync(0xffffffffu, cd, o);
             const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
-            if (od < cd || (od == cd && oi < ci)) {
+            if (near8_before(od, oi, cd, ci)) {
                 cd = od;
                 ci = oi;
             }
         }
         nd[r] = cd;
         ni[r] = ci;
-        if (bi[0] == ci) {          // this lane held the winner: pop its head
+        if (L.i[0] == ci) {          // this lane held the winner: pop its head
 #pragma unroll
             for (int s = 0; s + 1 < kKnn; ++s) {
-                bd[s] = bd[s + 1];
-                bi[s] = bi[s + 1];
+                L.d[s] = L.d[s + 1];
+                L.i[s] = L.i[s + 1];
             }
-            bd[kKnn - 1] = INFINITY;
-            bi[kKnn - 1] = 0x7fffffff;
+            L.d[kKnn - 1] = INFINITY;
+            L.i[kKnn - 1] = 0x7fffffff;
         }
     }
-    // lane k < 8: the residual of neighbour k under the translation match j implies
-    const float2 yj = dst[j];
+}
+
+// The 16 features of match j from its 8 nearest (nd ascending, indices ni).
+__device__ __forceinline__ void near8_features(const float2 *__restrict__ src,
+                                               const float2 *__restrict__ dst, int j,
+                                               int n, const float (&nd)[kKnn],
+                                               const int (&ni)[kKnn], int lane,
+                                               float (&f)[2 * kKnn])
+{
+    // lane k < 8: the residual of neighbour k under the translation match j implies.  A
+    // missing neighbour (non-finite coordinates compare false, so fewer than 8 may be
+    // found) gives a NaN feature, which the fit then reports as a non-finite p0.
+    const float2 xj = src[j], yj = dst[j];
     const float djx = yj.x - xj.x, djy = yj.y - xj.y;
     float mine = 0.f;
     if (lane < kKnn) {
@@ -101,8 +123,12 @@ __device__ __forceinline__ void knn_features_warp(const float2 *__restrict__ src
 #pragma unroll
         for (int k = 1; k < kKnn; ++k)
             if (lane == k) idx = ni[k];
-        const float2 xk = src[idx], yk = dst[idx];
-        mine = log1pf(hypotf((yk.x - xk.x) - djx, (yk.y - xk.y) - djy));
+        if (idx >= 0 && idx < n) {
+            const float2 xk = src[idx], yk = dst[idx];
+            mine = log1pf(hypotf((yk.x - xk.x) - djx, (yk.y - xk.y) - djy));
+        } else {
+            mine = __int_as_float(0x7fffffff);
+        }
     }
     float f1[kKnn];
 #pragma unroll
@@ -121,6 +147,22 @@ __device__ __forceinline__ void knn_features_warp(const float2 *__restrict__ src
         f[k] = f1[k];
         f[kKnn + k] = log1pf(sqrtf(nd[k]));      // distances, already ascending
     }
+}
+
+// Brute force: every match is a candidate (lane l takes i = l + 32 t).
+__device__ __forceinline__ void knn_features_warp(const float2 *__restrict__ src,
+                                                  const float2 *__restrict__ dst, int n, int j,
+                                                  int lane, float (&f)[2 * kKnn])
+{
+    const float2 xj = src[j];
+    Near8 L;
+    near8_reset(L);
+    for (int i = lane; i < n; i += 32)
+        if (i != j) near8_offer(L, near_d2(src[i], xj), i);
+    float nd[kKnn];
+    int ni[kKnn];
+    near8_merge(L, nd, ni);
+    near8_features(src, dst, j, n, nd, ni, lane, f);
 }
 
 __global__ void __launch_bounds__(256) warm_features_kernel(const float2 *__restrict__ src,
@@ -244,6 +286,218 @@ __global__ void __launch_bounds__(kNetThreads) warm_start_batch_kernel(
         const int j = g - B.first[b];
         float f[2 * kKnn];
         knn_features_warp(B.src[b], B.dst[b], B.n[b], j, lane, f);
+        const float z = mlp_forward_warp(sw, f, lane);
+        if (lane == 0) B.p0[b][j] = 1.f / (1.f + expf(-z));
+    }
+}
+
+// The same p0 by a kNN search that visits few candidates.  A block takes up to
+// kGridQueries matches of one problem and first stages all of that problem's matches in
+// shared memory, bucketed by a uniform grid of square cells (about kGridPerCell matches per
+// cell).  A warp offers its match the matches of the 3 x 3 cells around its own.  When the
+// 8th nearest found is closer than the edge of that block of cells (with a margin that
+// covers the rounding of the cell assignment), no match outside it can be among the 8
+// nearest and the result is final; otherwise a larger block is searched, bounded by the
+// 8th nearest found, until that holds or the block is the whole grid.  The result is the 8
+// nearest by (distance, index): the set and order of the brute-force search, so the
+// features and p0 are the same bits.
+constexpr int kGridMaxN = 8192;        // matches staged per block (indices fit 16 bits)
+constexpr int kGridCells = 2048;
+constexpr float kGridPerCell = 8.f;
+constexpr int kGridQueries = 128;      // matches per block, 16 per warp
+
+struct WarmGridBatch {
+    const float2 *src[kWarmBatchMax];
+    const float2 *dst[kWarmBatchMax];
+    float *p0[kWarmBatchMax];
+    int n[kWarmBatchMax];
+    int block0[kWarmBatchMax + 1];     // prefix sums of the problems' block counts
+    int count;
+    int nmax;                          // largest n (sizes the shared-memory arrays)
+};
+
+struct GridLayout {
+    size_t pts, idx, start, cur, misc, total;
+};
+
+__host__ __device__ inline size_t al16(size_t v) { return (v + 15) / 16 * 16; }
+
+__host__ __device__ inline GridLayout grid_layout(int nmax)
+{
+    GridLayout L;
+    L.pts = al16(sizeof(float) * kNParams);
+    L.idx = L.pts + al16(sizeof(float2) * (size_t)nmax);
+    L.start = L.idx + al16(sizeof(unsigned short) * (size_t)nmax);
+    L.cur = L.start + al16(sizeof(int) * (kGridCells + 1));
+    L.misc = L.cur + al16(sizeof(int) * kGridCells);
+    L.total = L.misc + al16(sizeof(float) * 48);
+    return L;
+}
+
+struct GridGeom {
+    float x0, y0, c, inv_c;
+    int gx, gy;
+};
+
+__device__ __forceinline__ int grid_cell(const GridGeom &G, float2 x, int &cx, int &cy)
+{
+    cx = min(max(static_cast<int>((x.x - G.x0) * G.inv_c), 0), G.gx - 1);
+    cy = min(max(static_cast<int>((x.y - G.y0) * G.inv_c), 0), G.gy - 1);
+    return cy * G.gx + cx;
+}
+
+__global__ void __launch_bounds__(kNetThreads) warm_start_grid_kernel(
+    const __grid_constant__ WarmGridBatch B, const float *__restrict__ w)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const GridLayout SL = grid_layout(B.nmax);
+    float *sw = reinterpret_cast<float *>(smem);
+    float2 *pts = reinterpret_cast<float2 *>(smem + SL.pts);
+    unsigned short *idx = reinterpret_cast<unsigned short *>(smem + SL.idx);
+    int *start = reinterpret_cast<int *>(smem + SL.start);
+    int *cur = reinterpret_cast<int *>(smem + SL.cur);
+    float *misc = reinterpret_cast<float *>(smem + SL.misc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kWarps = kNetThreads / 32;
+
+    int b = 0;
+    while (b + 1 < B.count && static_cast<int>(blockIdx.x) >= B.block0[b + 1]) ++b;
+    const int n = B.n[b];
+    const float2 *__restrict__ src = B.src[b];
+    const int q0 = (blockIdx.x - B.block0[b]) * kGridQueries;
+
+    for (int k = threadIdx.x; k < kGridCells; k += kNetThreads) cur[k] = 0;
+    // extent of the matches (NaNs are ignored by fminf / fmaxf)
+    float mnx = INFINITY, mny = INFINITY, mxx = -INFINITY, mxy = -INFINITY;
+    for (int i = threadIdx.x; i < n; i += kNetThreads) {
+        const float2 x = src[i];
+        mnx = fminf(mnx, x.x);
+        mny = fminf(mny, x.y);
+        mxx = fmaxf(mxx, x.x);
+        mxy = fmaxf(mxy, x.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+        mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+        mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+        mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+    }
+    if (lane == 0) {
+        misc[4 * warp + 0] = mnx;
+        misc[4 * warp + 1] = mny;
+        misc[4 * warp + 2] = mxx;
+        misc[4 * warp + 3] = mxy;
+    }
+    stage_params_t(w, sw);                 // ends with __syncthreads
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < kWarps; ++k) {
+            mnx = fminf(mnx, misc[4 * k + 0]);
+            mny = fminf(mny, misc[4 * k + 1]);
+            mxx = fmaxf(mxx, misc[4 * k + 2]);
+            mxy = fmaxf(mxy, misc[4 * k + 3]);
+        }
+        const float wx = mxx - mnx, wy = mxy - mny;
+        GridGeom G{mnx, mny, 1.f, 1.f, 1, 1};
+        if (isfinite(wx) && isfinite(wy)) {
+            // square cells of about kGridPerCell matches (a line of matches: by its length)
+            float c = sqrtf(wx * wy * kGridPerCell / n);
+            c = fmaxf(c, fmaxf(wx, wy) * kGridPerCell / n);
+            c = fmaxf(c, 1e-3f);
+            for (;;) {
+                G.gx = static_cast<int>(wx / c) + 1;
+                G.gy = static_cast<int>(wy / c) + 1;
+                if (G.gx * G.gy <= kGridCells) break;
+                c *= 1.25f;
+            }
+            G.c = c;
+            G.inv_c = 1.f / c;
+        } else {
+            G.x0 = G.y0 = 0.f;             // one cell: every search is the whole problem
+        }
+        *reinterpret_cast<GridGeom *>(misc + 32) = G;
+    }
+    __syncthreads();
+    const GridGeom G = *reinterpret_cast<const GridGeom *>(misc + 32);
+    int cx, cy;
+    for (int i = threadIdx.x; i < n; i += kNetThreads) atomicAdd(&cur[grid_cell(G, src[i], cx, cy)], 1);
+    __syncthreads();
+    // exclusive scan of the cell counts into start[0 .. kGridCells]
+    {
+        constexpr int per = kGridCells / kNetThreads;
+        int v[per], sum = 0;
+#pragma unroll
+        for (int u = 0; u < per; ++u) {
+            v[u] = cur[threadIdx.x * per + u];
+            sum += v[u];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int *wsum = reinterpret_cast<int *>(misc);          // the extents are no longer needed
+        __syncthreads();
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        int off = incl - sum;
+        for (int k = 0; k < warp; ++k) off += wsum[k];
+#pragma unroll
+        for (int u = 0; u < per; ++u) {
+            start[threadIdx.x * per + u] = off;
+            cur[threadIdx.x * per + u] = off;
+            off += v[u];
+        }
+        if (threadIdx.x == kNetThreads - 1) start[kGridCells] = off;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kNetThreads) {
+        const float2 x = src[i];
+        const int pos = atomicAdd(&cur[grid_cell(G, x, cx, cy)], 1);
+        pts[pos] = x;
+        idx[pos] = static_cast<unsigned short>(i);
+    }
+    __syncthreads();
+
+    for (int k = warp; k < kGridQueries; k += kWarps) {
+        const int j = q0 + k;
+        if (j >= n) break;
+        const float2 xj = src[j];
+        grid_cell(G, xj, cx, cy);
+        // blocks of (2R + 1)^2 cells around x_j, R = 1, 2, 4, ..., each searched afresh with
+        // the previous block's 8th nearest as the bound, until the 8th nearest is closer
+        // than every cell outside the block
+        float nd[kKnn], td = INFINITY;
+        int ni[kKnn], ti = 0x7fffffff;
+        for (int R = 1;; R = R < 2 ? R + 1 : 2 * R) {
+            const int xl = max(cx - R, 0), xh = min(cx + R, G.gx - 1);
+            const int yl = max(cy - R, 0), yh = min(cy + R, G.gy - 1);
+            Near8 L;
+            near8_reset(L);
+            for (int row = yl; row <= yh; ++row) {
+                const int e = start[row * G.gx + xh + 1];
+                for (int t = start[row * G.gx + xl] + lane; t < e; t += 32) {
+                    const int i = idx[t];
+                    if (i == j) continue;
+                    const float d = near_d2(pts[t], xj);
+                    if (!near8_before(td, ti, d, i)) near8_offer(L, d, i);
+                }
+            }
+            near8_merge(L, nd, ni);
+            // distance from x_j to the nearest block edge that has cells beyond it
+            float bnd = INFINITY;
+            if (xl > 0) bnd = fminf(bnd, xj.x - (G.x0 + xl * G.c));
+            if (xh < G.gx - 1) bnd = fminf(bnd, (G.x0 + (xh + 1) * G.c) - xj.x);
+            if (yl > 0) bnd = fminf(bnd, xj.y - (G.y0 + yl * G.c));
+            if (yh < G.gy - 1) bnd = fminf(bnd, (G.y0 + (yh + 1) * G.c) - xj.y);
+            const float r = bnd * 0.999f - 0.01f;
+            if (bnd == INFINITY || (r > 0.f && nd[kKnn - 1] < r * r)) break;
+            td = nd[kKnn - 1];          // itself a candidate (so <= passes), or still INF
+            ti = ni[kKnn - 1];
+        }
+        float f[2 * kKnn];
+        near8_features(src, B.dst[b], j, n, nd, ni, lane, f);
         const float z = mlp_forward_warp(sw, f, lane);
         if (lane == 0) B.p0[b][j] = 1.f / (1.f + expf(-z));
     }
@@ -420,6 +674,34 @@ extern "C" emdq_status emdq_warm_start(const float *const *src, const float *con
     }
     B.first[count] = total;
     const DeviceInfo &D = device_info();
+    if (D.device < 0) return EMDQ_ECUDA;
+    int nmax = 0;
+    for (int b = 0; b < count; ++b) nmax = n[b] > nmax ? n[b] : nmax;
+    if (nmax <= kGridMaxN) {
+        static int attr_set = -1;
+        if (attr_set != D.device) {
+            if (cudaFuncSetAttribute(warm_start_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)grid_layout(kGridMaxN).total) != cudaSuccess)
+                return EMDQ_ECUDA;
+            attr_set = D.device;
+        }
+        WarmGridBatch G;
+        G.count = count;
+        G.nmax = nmax;
+        int blocks = 0;
+        for (int b = 0; b < count; ++b) {
+            G.src[b] = B.src[b];
+            G.dst[b] = B.dst[b];
+            G.p0[b] = B.p0[b];
+            G.n[b] = B.n[b];
+            G.block0[b] = blocks;
+            blocks += (n[b] + kGridQueries - 1) / kGridQueries;
+        }
+        G.block0[count] = blocks;
+        warm_start_grid_kernel<<<blocks, kNetThreads, grid_layout(nmax).total,
+                                 static_cast<cudaStream_t>(stream)>>>(G, params);
+        return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
+    }
     const int want = (total + 7) / 8, cap = 4 * (D.sms > 0 ? D.sms : 152);
     warm_start_batch_kernel<<<want < cap ? want : cap, kNetThreads, 0,
                               static_cast<cudaStream_t>(stream)>>>(B, params);

@@ -47,6 +47,45 @@ def test_batched_warm_start_equals_features_then_network(emdq):
         assert torch.equal(p, want)
 
 
+def _layout(kind, n, rng):
+    """Match positions that stress the grid search: uniform, tight clusters, a line, many
+    exact duplicates, a wide empty gap, and a frame with 1 px of height."""
+    if kind == 'uniform':
+        x = rng.uniform(0, [1920, 1080], (n, 2))
+    elif kind == 'clusters':
+        c = rng.uniform(0, [1920, 1080], (5, 2))
+        x = c[rng.integers(0, 5, n)] + rng.normal(0, 3.0, (n, 2))
+    elif kind == 'line':
+        x = np.stack([rng.uniform(0, 1920, n), np.full(n, 500.0)], 1)
+    elif kind == 'duplicates':
+        x = rng.uniform(0, [64, 48], (n, 2)).round()
+    elif kind == 'gap':
+        x = rng.uniform(0, [100, 100], (n, 2))
+        x[: n // 10] += 1800.0
+    else:                                                  # 'thin'
+        x = np.stack([rng.uniform(0, 1280, n), rng.uniform(0, 1, n)], 1)
+    y = x + rng.normal(0, 2.0, (n, 2))
+    return x.astype(np.float32), y.astype(np.float32)
+
+
+@pytest.mark.parametrize('kind', ['uniform', 'clusters', 'line', 'duplicates', 'gap', 'thin'])
+def test_batched_warm_start_search_equals_brute_force(emdq, kind):
+    """The batched warm start's grid search finds the brute-force neighbours (same p0 bits),
+    for n = 9 (the least), ragged sizes, 8192 (the most it stages) and 8193 (past it: the
+    batch then takes the brute-force kernel)."""
+    params = emdq.load_warmstart_params()
+    rng = np.random.default_rng(['uniform', 'clusters', 'line', 'duplicates', 'gap', 'thin'].index(kind))
+    for ns in ((9, 10, 300), (1000, 4999), (8192,), (8193, 40)):
+        probs = []
+        for n in ns:
+            x, y = _layout(kind, n, rng)
+            probs.append((torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()))
+        got = emdq.warm_start(probs, params)
+        for (st, dt), p in zip(probs, got):
+            want = emdq.warm_infer(emdq.warm_features(st, dt), params)
+            assert torch.equal(p, want), (kind, st.shape[0])
+
+
 def _bf16_forward(w, X):
     """The oracle network with the kernel's BF16 rounding of operands (for the tolerance
     check only; the reference is the FP64 forward)."""
