@@ -89,6 +89,10 @@ def parse_args():
                     help='CTAs of one fit launch, split evenly over its frames (default: every '
                          'co-resident CTA; 152 = one per SM, which leaves room beside the GEMM '
                          'for --overlap)')
+    ap.add_argument('--shard', default='sequence', choices=['sequence', 'canvas'],
+                    help='N > 1: every rank its own sequence (default, weak scaling), or one '
+                         'sequence split into bands of canvas rows with the fits sharded by frame '
+                         'and one all-gather of the fit rows per pass (strong scaling)')
     ap.add_argument('--overlap', action='store_true',
                     help='run the next batch of fits on a second stream while the current batch is '
                          'blended (default: one stream; the cooperative fit launch occupies every '
@@ -194,6 +198,48 @@ def max_over_ranks(x: float, ws: int, device) -> float:
 def job_mpix_per_s(ws: int, frames_per_rank: int, w: int, h: int, max_ms: float) -> float:
     """Whole-job throughput: the frame pixels all ranks processed over the slowest rank's time."""
     return ws * frames_per_rank * w * h / 1e6 / (max_ms / 1e3)
+
+
+# Multi-GPU, one sequence over several GPUs (`--shard canvas`): frame k is fitted on rank
+# k mod W; one all-gather per pass hands every rank every frame's fit (q rows and weights);
+# rank r then computes the field and warp of every frame, in frame order, on its own band of
+# canvas rows only.  A canvas pixel's updates do not depend on the window around it (the
+# field at a pixel and its blend are per-pixel), so the bands assemble into the canvas an
+# untiled run leaves, bit for bit.
+
+def canvas_band(canvas_h: int, ws: int, rank: int) -> tuple:
+    """Canvas rows [y0, y1) owned by `rank` (W bands of equal height, the last takes the rest)."""
+    return canvas_h * rank // ws, canvas_h * (rank + 1) // ws
+
+
+def clip_to_band(grid, origin, band):
+    """The rows of window `grid` (reference coordinates) that land in canvas band [y0, y1);
+    None if there are none."""
+    x0, y0, gw, gh = (int(v) for v in grid)
+    lo = max(y0, band[0] - int(origin[1]))
+    hi = min(y0 + gh, band[1] - int(origin[1]))
+    return (x0, lo, gw, hi - lo) if hi > lo and gw > 0 else None
+
+
+def frame_owner(k: int, ws: int) -> int:
+    """The rank that fits frame k."""
+    return k % ws
+
+
+def gather_fit_rows(local: dict, ws: int, rank: int, n_frames: int, n: int, device):
+    """Every frame's fit rows ([n, 9]: q rows and the weight c) on every rank, from the frames
+    each rank fitted (`local`: frame -> [n, 9]), by one all-gather of equal-sized slabs."""
+    import torch
+    per = (n_frames + ws - 1) // ws
+    mine = torch.zeros((per, n, 9), dtype=torch.float32, device=device)
+    for j, k in enumerate(range(rank, n_frames, ws)):
+        mine[j] = local[k]
+    if ws == 1:
+        return [mine[k] for k in range(n_frames)]
+    import torch.distributed as dist
+    slabs = [torch.empty_like(mine) for _ in range(ws)]
+    dist.all_gather(slabs, mine)
+    return [slabs[frame_owner(k, ws)][k // ws] for k in range(n_frames)]
 
 
 def workload_config(args, sc, cfg, n_frames, ws) -> dict:
@@ -716,6 +762,112 @@ MIXED_COUNT = 64
 MIXED_PAD = 256          # canvas margin around each pair's reference frame
 
 
+def run_gpu_tiled(args, ws, rank, local):
+    """`--shard canvas`: one sequence on W GPUs -- fits sharded by frame, one all-gather of the
+    fit rows, field + warp of every frame on each rank's band of canvas rows (strong scaling)."""
+    import numpy as np
+    import torch
+    import paper_2103_07414_gb300 as emdq
+    from synth import WORKLOADS
+
+    torch.cuda.set_device(local)
+    dev = torch.device('cuda', local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl', device_id=dev)
+    n_frames = WORKLOADS[args.workload]['frames']
+    if args.frames > 0:
+        n_frames = min(n_frames, args.frames)
+    sc, cfg, origin, ref, frames, src, dst, grids = prepare_sequence(args.workload, args.seed,
+                                                                    n_frames, dev)
+    cw, chh = cfg['canvas']
+    n = cfg['n']
+    band = canvas_band(chh, ws, rank)
+    canvas = torch.zeros((chh, cw, 4), dtype=torch.uint8, device=dev)
+    emdq.mosaic_insert_reference(ref, canvas, origin)
+    alpha = emdq.alpha_for_frame(sc.w, sc.h)
+    mine = list(range(rank, n_frames, ws))
+    B = max(1, min(args.batch or cfg.get('batch', 50), 64))
+    batches = [mine[i:i + B] for i in range(0, len(mine), B)]
+    warm_params = emdq.load_warmstart_params(dev)
+    outs = {k: dict(q=torch.empty((n, 8), device=dev), c=torch.empty(n, device=dev),
+                    p=torch.empty(n, device=dev), info=torch.zeros(4, dtype=torch.int32, device=dev))
+            for k in mine}
+    p0 = {k: torch.empty(n, device=dev) for k in mine}
+    fit_ws = torch.empty(max(256, emdq.fit_batch_workspace_size([(src[0], dst[0])] * B)),
+                         dtype=torch.uint8, device=dev)
+    clipped = [clip_to_band(g, origin, band) for g in grids]
+    todo = [k for k in range(n_frames) if clipped[k] is not None]
+    G = max(1, min(8, args.field_group))
+    groups = [todo[i:i + G] for i in range(0, len(todo), G)]
+    zq, zc, zs = torch.zeros((n, 8), device=dev), torch.zeros(n, device=dev), torch.zeros((n, 2), device=dev)
+    gw_max = max([clipped[k][2] for k in todo] + [1])
+    gh_max = max([clipped[k][3] for k in todo] + [1])
+    gws = torch.empty(emdq.field_batch_workspace_size([(zq, zc, zs, (0, 0, gw_max, gh_max), alpha)] * G),
+                      dtype=torch.uint8, device=dev)
+    disp = [torch.empty(gw_max * gh_max * 2, device=dev) for _ in range(G)]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def one_pass():
+        for ks in batches:
+            emdq.warm_start([(src[k], dst[k]) for k in ks], warm_params, outs=[p0[k] for k in ks])
+            emdq.emdq_fit_batch([(src[k], dst[k], sc.w, sc.h, p0[k]) for k in ks],
+                                outs=[outs[k] for k in ks], workspace=fit_ws)
+        rows = {k: torch.cat([outs[k]['q'], outs[k]['c'][:, None]], 1) for k in mine}
+        allrows = gather_fit_rows(rows, ws, rank, n_frames, n, dev)
+        for grp in groups:
+            ds = [disp[i][: clipped[k][2] * clipped[k][3] * 2].view(clipped[k][3], clipped[k][2], 2)
+                  for i, k in enumerate(grp)]
+            emdq.emdq_field_batch([(allrows[k][:, :8].contiguous(), allrows[k][:, 8].contiguous(), src[k],
+                                    clipped[k], alpha) for k in grp], outs=ds, workspace=gws)
+            emdq.mosaic_warp_batch([frames[k] for k in grp], ds, [clipped[k] for k in grp], canvas, origin)
+
+    t0 = time.perf_counter()
+    w = 0
+    while w < args.warmup or time.perf_counter() - t0 < args.min_warmup_s:
+        flush.zero_()
+        one_pass()
+        torch.cuda.synchronize()
+        w += 1
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.1)
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        one_pass()
+        b.record()
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(float(np.sum(step_ms)), ws, dev)
+    digest = hashlib.sha256(canvas[band[0]:band[1]].cpu().numpy().tobytes()).hexdigest()[:16]
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return None
+    value = args.steps * n_frames * sc.w * sc.h / 1e6 / (total_ms / 1e3)
+    cfgd = workload_config(args, sc, cfg, n_frames, ws)
+    cfgd['parallelism'] = f'canvas bands x{ws}: fits sharded by frame, one all-gather of the fit rows per pass'
+    return dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
+                warmup=args.warmup, ms_per_step=total_ms / args.steps,
+                p50_frame_ms=float(np.median(step_ms)) / n_frames, higher_is_better=True,
+                scaling='strong', vs_baseline=None, dtype='bf16', data='synthetic', config=cfgd,
+                path='per rank: warm start + emdq_fit_batch on frames k = rank mod W, all-gather of '
+                     'the fit rows, emdq_field_batch + mosaic_warp_batch of every frame on the '
+                     "rank's band of canvas rows, frames in order",
+                gpu_launches=args.steps * (2 * len(batches) + 3 * len(groups)), clocks=clk, e2e=None,
+                band0_sha256=digest)
+
+
 def mixed_config(args, ws, pairs, ctas=None) -> dict:
     sizes = sorted({(p['scene'].w, p['scene'].h) for p in pairs})
     ns = [p['n'] for p in pairs]
@@ -1159,7 +1311,12 @@ def main():
     if args.impl == 'reference':
         line = run_reference_mixed(args, ws, rank) if mixed else run_reference(args, ws, rank)
     else:
-        line = run_gpu_mixed(args, ws, rank, local) if mixed else run_gpu(args, ws, rank, local)
+        if mixed:
+            line = run_gpu_mixed(args, ws, rank, local)
+        elif args.shard == 'canvas':
+            line = run_gpu_tiled(args, ws, rank, local)
+        else:
+            line = run_gpu(args, ws, rank, local)
     if line is not None and rank == 0:
         print(json.dumps(line))
 

@@ -47,3 +47,40 @@ def worker(rank: int, ws: int, port: int, outdir: str, fake_ms: list[float]):
                recall=float((labels & inl).sum() / inl.sum()), status=fit['status'])
     with open(os.path.join(outdir, f'rank{rank}.json'), 'w') as f:
         json.dump(out, f)
+
+
+def tiled_worker(rank: int, ws: int, port: int, outdir: str, n_frames: int):
+    """Rank body of the canvas-band split of one sequence: this rank fits frames k = rank mod
+    W (FP64 oracle here, no GPU), the all-gather hands every rank every frame's fit rows, and
+    the rank keeps the windows clipped to its band of canvas rows."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import bench
+    import oracle
+    from synth import canvas_origin, footprint_window, make_matches, workload
+
+    dist.init_process_group('gloo', init_method=f'tcp://127.0.0.1:{port}', rank=rank,
+                            world_size=ws)
+    sc, cfg = workload('pair640', seed=4)
+    n = cfg['n']
+    cw, chh = cfg['canvas']
+    origin = canvas_origin(cw, chh, sc.w, sc.h)
+    local = {}
+    for k in range(n_frames):
+        if bench.frame_owner(k, ws) != rank:
+            continue
+        s, d, _ = make_matches(sc, 1 + k, n, cfg['outliers'], cfg['noise'])
+        f = oracle.fit(np.float32(s).astype(np.float64), np.float32(d).astype(np.float64), sc.w, sc.h)
+        local[k] = torch.from_numpy(np.concatenate([f['q8'], f['c'][:, None]], 1).astype(np.float32))
+    rows = bench.gather_fit_rows(local, ws, rank, n_frames, n, torch.device('cpu'))
+    band = bench.canvas_band(chh, ws, rank)
+    clips = [bench.clip_to_band(footprint_window(sc, 1 + k, cw, chh), origin, band)
+             for k in range(n_frames)]
+    dist.barrier()
+    dist.destroy_process_group()
+    np.save(os.path.join(outdir, f'rows{rank}.npy'), torch.stack(rows).numpy())
+    with open(os.path.join(outdir, f'tiles{rank}.json'), 'w') as f:
+        json.dump(dict(rank=rank, band=list(band), clips=[list(c) if c else None for c in clips],
+                       owned=sorted(local)), f)

@@ -1,6 +1,6 @@
-"""World-size-2 gloo test (CPU) of the multi-rank benchmark path: per-rank sequences,
-barrier, max-over-ranks timing and the whole-job throughput; the reference arm runs on
-rank 0 only."""
+"""World-size-2 gloo tests (CPU) of the multi-rank benchmark paths: per-rank sequences,
+barrier, max-over-ranks timing and the whole-job throughput; one sequence split into canvas
+bands with the fits sharded by frame and gathered; the reference arm runs on rank 0 only."""
 import json
 import os
 import socket
@@ -46,3 +46,42 @@ def test_reference_arm_runs_on_rank_zero_only():
     import bench
     # the other ranks return at once, without work (and without reading any argument)
     assert bench.run_reference(None, 2, 1) is None
+
+
+def test_two_gloo_ranks_split_one_sequence_into_canvas_bands(tmp_path, orc):
+    import numpy as np
+    import torch.multiprocessing as mp
+
+    from multirank_worker import tiled_worker
+    from synth import canvas_origin, footprint_window, make_matches, workload
+    n_frames = 5                                        # ragged: rank 0 fits 3, rank 1 fits 2
+    mp.start_processes(tiled_worker, args=(2, _free_port(), str(tmp_path), n_frames), nprocs=2,
+                       join=True, start_method='spawn')
+    rows = [np.load(tmp_path / f'rows{k}.npy') for k in range(2)]
+    tiles = [json.load(open(tmp_path / f'tiles{k}.json')) for k in range(2)]
+    assert tiles[0]['owned'] == [0, 2, 4] and tiles[1]['owned'] == [1, 3]
+    # after the all-gather both ranks hold every frame's fit rows, in frame order, equal to a
+    # fit of that frame on one rank
+    np.testing.assert_array_equal(rows[0], rows[1])
+    sc, cfg = workload('pair640', seed=4)
+    for k in (0, 3):
+        s, d, _ = make_matches(sc, 1 + k, cfg['n'], cfg['outliers'], cfg['noise'])
+        f = orc.fit(np.float32(s).astype(np.float64), np.float32(d).astype(np.float64), sc.w, sc.h)
+        want = np.concatenate([f['q8'], f['c'][:, None]], 1).astype(np.float32)
+        np.testing.assert_array_equal(rows[0][k], want)
+    # the bands tile the canvas rows exactly once; each frame's window rows split between them
+    cw, chh = cfg['canvas']
+    assert tiles[0]['band'][0] == 0 and tiles[0]['band'][1] == tiles[1]['band'][0]
+    assert tiles[1]['band'][1] == chh
+    origin = canvas_origin(cw, chh, sc.w, sc.h)
+    for k in range(n_frames):
+        g = footprint_window(sc, 1 + k, cw, chh)
+        parts = [t['clips'][k] for t in tiles if t['clips'][k] is not None]
+        assert sum(p[3] for p in parts) == g[3]
+        assert all(p[0] == g[0] and p[2] == g[2] for p in parts)
+        ys = sorted((p[1], p[1] + p[3]) for p in parts)
+        assert ys[0][0] == g[1] and ys[-1][1] == g[1] + g[3]
+        assert all(a[1] == b[0] for a, b in zip(ys, ys[1:]))
+        for t, p in zip(tiles, [t['clips'][k] for t in tiles]):
+            if p is not None:
+                assert t['band'][0] <= p[1] + origin[1] and p[1] + p[3] + origin[1] <= t['band'][1]
