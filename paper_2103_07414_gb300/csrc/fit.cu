@@ -59,6 +59,8 @@ struct FitArgs {
     float *e;            // n residuals^2 (workspace)
     float4 *cen;         // n weighted centroids of the last M-step, scaled local coordinates (workspace)
     float *partials;     // one float2 partial sum per CTA of the group (workspace)
+    int *ord;            // n: the matches in Hilbert order; each CTA writes the positions of
+                         // its own M-step rows (workspace)
     unsigned *bar;       // barrier arrival counter, zero at launch (workspace)
     int *flag;           // device status, zero at launch (workspace)
 };
@@ -173,120 +175,94 @@ __device__ __forceinline__ void mstep_finish(const FitArgs &A, int i, float W, f
     __stcg(A.cen + i, ok ? make_float4(ab0, ab1, bb0, bb1) : make_float4(0.f, 0.f, 0.f, 0.f));
 }
 
-// M-step of R rows (one warp, lanes over j): weights om_j = p_j exp(-alpha |x_j - x_i|^2),
-// offsets u = x_j - x_i - shift_x, v = y_j - y_i - shift_y (scaled coordinates).  The
-// similarity fit needs the moments about the weighted centroid; summing raw moments and
-// centring afterwards cancels.
-//   first round: two passes -- W and the centroid, then the moments about it;
-//   later rounds: one pass about the previous round's centroid of the row (the weights
-//     change little from round to round, so the centroid moves by far less than the spread
-//     and the final correction W |centroid - shift|^2 cancels nothing).
-// Of C_t C_0^T only the trace (c00 + c11 = sum om u.v) and the antisymmetric part
-// (c10 - c01 = sum om u x v) enter the 2-D rotation, so only those are summed.
+// M-step of R rows that lie next to each other (consecutive in the Hilbert order of the
+// matches; one warp, lanes over j): weights om_j = p_j exp(-alpha |x_j - x_i|^2).  The
+// similarity fit needs the moments about each row's weighted centroid; summing raw moments
+// and centring afterwards would cancel.  Here the moments of all R rows are summed about one
+// origin o, the previous round's weighted centroid of the group's first row (at step 0 that
+// centroid comes from a first pass), so the offsets u = x_j - o_x, v = y_j - o_y and the
+// products |u|^2, |v|^2, u.v, u x v are formed once per j for the R rows.  Neighbouring rows
+// have neighbouring centroids, so every row's centroid lies close to o compared with the
+// spread of its weights, and moving its moments from o to that centroid afterwards cancels
+// nothing.  Of C_t C_0^T only the trace (sum om u.v) and the antisymmetric part (sum om u x v)
+// enter the 2-D rotation, so only those are summed.
 template <int R>
-__device__ void mstep_rows(const FitArgs &A, const FitSmem &S, const int *rows, int lane,
-                           bool first)
+__device__ void mstep_group(const FitArgs &A, const FitSmem &S, const int *rows, int lane,
+                            bool first)
 {
     const int n = A.n;
-    float2 nxi[R], nyi[R];
-    float4 sh[R];
+    float2 nxi[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        nxi[r] = neg2(S.x[rows[r]]);
-        nyi[r] = neg2(S.y[rows[r]]);
-        sh[r] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldcg(A.cen + rows[r]);
-    }
+    for (int r = 0; r < R; ++r) nxi[r] = neg2(S.x[rows[r]]);
+    const float2 x0 = S.x[rows[0]], y0 = S.y[rows[0]];
+    float4 sh = first ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldcg(A.cen + rows[0]);
     if (first) {
-        float W[R];
-        float2 sa[R], sb[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            W[r] = 0.f;
-            sa[r] = sb[r] = make_float2(0.f, 0.f);
-        }
+        // the first row's weighted centroid, relative to (x_i0, y_i0)
+        const float2 ny0 = neg2(y0);
+        float W = 0.f;
+        float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
 #pragma unroll 2
         for (int j = lane; j < n; j += 32) {
-            const float2 xj = S.x[j], yj = S.y[j];
-            const float lpj = S.lp[j];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const float2 a = __fadd2_rn(xj, nxi[r]);
-                const float om = gauss_w(a, lpj);
-                const float2 om2 = make_float2(om, om);
-                W[r] += om;
-                sa[r] = __ffma2_rn(om2, a, sa[r]);
-                sb[r] = __ffma2_rn(om2, __fadd2_rn(yj, nyi[r]), sb[r]);
-            }
+            const float2 a = __fadd2_rn(S.x[j], nxi[0]);
+            const float om = gauss_w(a, S.lp[j]);
+            const float2 om2 = make_float2(om, om);
+            W += om;
+            sa = __ffma2_rn(om2, a, sa);
+            sb = __ffma2_rn(om2, __fadd2_rn(S.y[j], ny0), sb);
         }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float w = warp_sum_f(W[r]);
-            const float a0 = warp_sum_f(sa[r].x), a1 = warp_sum_f(sa[r].y);
-            const float b0 = warp_sum_f(sb[r].x), b1 = warp_sum_f(sb[r].y);
-            if (w > 0.f && isfinite(w)) sh[r] = make_float4(a0 / w, a1 / w, b0 / w, b1 / w);
-        }
+        const float w = warp_sum_f(W);
+        const float a0 = warp_sum_f(sa.x), a1 = warp_sum_f(sa.y);
+        const float b0 = warp_sum_f(sb.x), b1 = warp_sum_f(sb.y);
+        if (w > 0.f && isfinite(w)) sh = make_float4(a0 / w, a1 / w, b0 / w, b1 / w);
     }
-    // one pass about the shift: W, first moments (for the small correction), the two
-    // second moments and the trace / antisymmetric part of C_t C_0^T
-    float2 nm[R], nmy[R], nmys[R];
+    // the origin o (negated, for adds), staged coordinates
+    const float2 nox = make_float2(-(x0.x + sh.x), -(x0.y + sh.y));
+    const float2 noy = make_float2(-(y0.x + sh.z), -(y0.y + sh.w));
     float W[R];
-    float2 su[R], sv[R], vxp[R], vyp[R], dotp[R], crp[R];
+    float2 su[R], sv[R], sq[R], sc[R];     // sums of om u, om v, om (|u|^2, |v|^2), om (u.v, u x v)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        nm[r] = make_float2(nxi[r].x - sh[r].x, nxi[r].y - sh[r].y);
-        nmy[r] = make_float2(nyi[r].x - sh[r].z, nyi[r].y - sh[r].w);
-        nmys[r] = make_float2(nmy[r].y, nmy[r].x);
         W[r] = 0.f;
-        su[r] = sv[r] = vxp[r] = vyp[r] = dotp[r] = crp[r] = make_float2(0.f, 0.f);
+        su[r] = sv[r] = sq[r] = sc[r] = make_float2(0.f, 0.f);
     }
 #pragma unroll 2
     for (int j = lane; j < n; j += 32) {
         const float2 xj = S.x[j], yj = S.y[j];
         const float lpj = S.lp[j];
-        const float2 yjs = make_float2(yj.y, yj.x);
+        const float2 u = __fadd2_rn(xj, nox), v = __fadd2_rn(yj, noy);
+        const float2 g1 = make_float2(fmaf(u.x, u.x, u.y * u.y), fmaf(v.x, v.x, v.y * v.y));
+        const float2 g2 = make_float2(fmaf(u.x, v.x, u.y * v.y), fmaf(u.x, v.y, -(u.y * v.x)));
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const float om = gauss_w(__fadd2_rn(xj, nxi[r]), lpj);
             const float2 om2 = make_float2(om, om);
-            const float2 u = __fadd2_rn(xj, nm[r]);
-            const float2 v = __fadd2_rn(yj, nmy[r]);
-            const float2 vs = __fadd2_rn(yjs, nmys[r]);    // (v1, v0)
-            const float2 ou = __fmul2_rn(om2, u);
-            const float2 ov = __fmul2_rn(om2, v);
             W[r] += om;
             su[r] = __ffma2_rn(om2, u, su[r]);
             sv[r] = __ffma2_rn(om2, v, sv[r]);
-            vxp[r] = __ffma2_rn(ou, u, vxp[r]);            // |vector(C_0)|^2 about the shift
-            vyp[r] = __ffma2_rn(ov, v, vyp[r]);            // |vector(C_t)|^2 about the shift
-            dotp[r] = __ffma2_rn(ou, v, dotp[r]);          // (c00, c11)
-            crp[r] = __ffma2_rn(ou, vs, crp[r]);           // (c10, c01)
+            sq[r] = __ffma2_rn(om2, g1, sq[r]);
+            sc[r] = __ffma2_rn(om2, g2, sc[r]);
         }
     }
     // every lane receives every row's sums; lane r then finishes row r, so the divisions
     // and square roots of the closed form are issued once for all R rows
     float w = 0.f, su0 = 0.f, su1 = 0.f, sv0 = 0.f, sv1 = 0.f, vx = 0.f, vy = 0.f, dot = 0.f,
           cross = 0.f;
-    float4 shr = sh[0];
     int i = rows[0];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const float w_ = warp_sum_f(W[r]);
         const float su0_ = warp_sum_f(su[r].x), su1_ = warp_sum_f(su[r].y);
         const float sv0_ = warp_sum_f(sv[r].x), sv1_ = warp_sum_f(sv[r].y);
-        const float vx_ = warp_sum_f(vxp[r].x + vxp[r].y);
-        const float vy_ = warp_sum_f(vyp[r].x + vyp[r].y);
-        const float dot_ = warp_sum_f(dotp[r].x + dotp[r].y);
-        const float cross_ = warp_sum_f(crp[r].x - crp[r].y);
+        const float vx_ = warp_sum_f(sq[r].x), vy_ = warp_sum_f(sq[r].y);
+        const float dot_ = warp_sum_f(sc[r].x), cross_ = warp_sum_f(sc[r].y);
         if (r == 0 || lane == r) {
             w = w_; su0 = su0_; su1 = su1_; sv0 = sv0_; sv1 = sv1_;
             vx = vx_; vy = vy_; dot = dot_; cross = cross_;
-            shr = sh[r];
             i = rows[r];
         }
     }
     if (lane >= R) return;
-    // move the moments from the shift to the centroid: m_c = m_s - W d d'^T,
-    // d = mean - shift
+    // move the moments from o to the row's centroid o + d: m_c = m_o - W d d'^T
     float du0 = 0.f, du1 = 0.f, dv0 = 0.f, dv1 = 0.f;
     if (w > 0.f) {
         const float inv = 1.f / w;
@@ -299,7 +275,32 @@ __device__ void mstep_rows(const FitArgs &A, const FitSmem &S, const int *rows, 
     vy -= w * (dv0 * dv0 + dv1 * dv1);
     dot -= w * (dv0 * du0 + dv1 * du1);
     cross -= w * (dv1 * du0 - dv0 * du1);
-    mstep_finish(A, i, w, shr.x + du0, shr.y + du1, shr.z + dv0, shr.w + dv1, vx, vy, dot, cross);
+    // the centroid relative to (x_i, y_i): o + d - x_i
+    const float2 xi = S.x[i], yi = S.y[i];
+    mstep_finish(A, i, w, du0 - (nox.x + xi.x), du1 - (nox.y + xi.y), dv0 - (noy.x + yi.x),
+                 dv1 - (noy.y + yi.y), vx, vy, dot, cross);
+}
+
+// Hilbert index of (x, y), 16 bits each (the curve of order 16: consecutive indices are
+// neighbouring cells).  Quadrant by quadrant from the top bit, rotating and reflecting the
+// remaining coordinates into the quadrant's frame.
+__device__ __forceinline__ unsigned hilbert_index(unsigned x, unsigned y)
+{
+    unsigned d = 0;
+    for (unsigned s = 1u << 15; s > 0; s >>= 1) {
+        const unsigned rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
+        d += s * s * ((3u * rx) ^ ry);
+        if (ry == 0) {
+            if (rx == 1) {
+                x = 0xffffu - x;
+                y = 0xffffu - y;
+            }
+            const unsigned t = x;
+            x = y;
+            y = t;
+        }
+    }
+    return d;
 }
 
 // Leave-one-out residuals of R rows j (one warp, lanes over i; lane r < R accumulates
@@ -474,16 +475,91 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
     float gamma = 0.5f;
     if (A.p0) gamma = fminf(fmaxf(block_sum2<NT>(p0sum, 0.f, red).x / n, 0.05f), 0.95f);
 
-    // this warp's M-step rows i = gwarp, gwarp + nwarps, ..., two at a time
-    auto mstep_all = [&](bool first) {
-        int i = gwarp;
-        for (; i + nwarps < n; i += 2 * nwarps) {
-            const int rows[2] = {i, i + nwarps};
-            mstep_rows<2>(A, S, rows, lane, first);
+    // The M-step rows of this CTA: positions [pb, pe) of the Hilbert order of the matches.
+    // Every CTA sorts all the matches (the same order in each; the q staging area is free
+    // until the first residual pass) and keeps the positions of its own rows.
+    const int pb = static_cast<int>((long long)rank * n / ncta);
+    const int pe = static_cast<int>((long long)(rank + 1) * n / ncta);
+    {
+        float2 lo = make_float2(INFINITY, INFINITY), hi = make_float2(-INFINITY, -INFINITY);
+        for (int j = threadIdx.x; j < n; j += NT) {
+            const float2 x = S.x[j];
+            lo = make_float2(fminf(lo.x, x.x), fminf(lo.y, x.y));
+            hi = make_float2(fmaxf(hi.x, x.x), fmaxf(hi.y, x.y));
         }
-        if (i < n) {
-            const int rows[1] = {i};
-            mstep_rows<1>(A, S, rows, lane, first);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+            lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+            hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+            hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+        }
+        if (lane == 0) red[warp] = lo;
+        __syncthreads();
+        float2 blo = red[0];
+        for (int k = 1; k < kWarps; ++k) blo = make_float2(fminf(blo.x, red[k].x), fminf(blo.y, red[k].y));
+        __syncthreads();
+        if (lane == 0) red[warp] = hi;
+        __syncthreads();
+        float2 bhi = red[0];
+        for (int k = 1; k < kWarps; ++k) bhi = make_float2(fmaxf(bhi.x, red[k].x), fmaxf(bhi.y, red[k].y));
+        __syncthreads();
+        const float ext = fmaxf(bhi.x - blo.x, bhi.y - blo.y);
+        const float qs = ext > 0.f ? 65535.f / ext : 0.f;
+        unsigned long long *key = reinterpret_cast<unsigned long long *>(S.q);
+        int P = 1;
+        while (P < n) P <<= 1;                    // P <= 2n keys fit the 16 n bytes of S.q
+        for (int t = threadIdx.x; t < P; t += NT) {
+            unsigned long long k = ~0ull;
+            if (t < n) {
+                const float2 x = S.x[t];
+                const unsigned hx = static_cast<unsigned>(fminf(fmaxf((x.x - blo.x) * qs, 0.f), 65535.f));
+                const unsigned hy = static_cast<unsigned>(fminf(fmaxf((x.y - blo.y) * qs, 0.f), 65535.f));
+                k = (static_cast<unsigned long long>(hilbert_index(hx, hy)) << 32) | static_cast<unsigned>(t);
+            }
+            key[t] = k;
+        }
+        __syncthreads();
+        // bitonic sort of the P keys, ascending (keys are distinct: the index is the low word)
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int t = threadIdx.x; t < P / 2; t += NT) {
+                    const int a = 2 * j * (t / j) + (t & (j - 1)), b = a + j;
+                    const unsigned long long ka = key[a], kb = key[b];
+                    if ((ka > kb) == ((a & k) == 0)) {
+                        key[a] = kb;
+                        key[b] = ka;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int t = pb + threadIdx.x; t < pe; t += NT) A.ord[t] = static_cast<int>(key[t] & 0xffffffffu);
+        __syncthreads();
+    }
+    // each warp takes groups of 4 consecutive positions (the same number per warp), then
+    // one contiguous run of the remaining positions (at most 4)
+    auto mstep_all = [&](bool first) {
+        const int m = pe - pb, per = m / (4 * kWarps);
+        for (int g = 0; g < per; ++g) {
+            const int b = pb + 4 * (warp + kWarps * g);
+            const int rows[4] = {A.ord[b], A.ord[b + 1], A.ord[b + 2], A.ord[b + 3]};
+            mstep_group<4>(A, S, rows, lane, first);
+        }
+        const int base = pb + 4 * kWarps * per, left = m - 4 * kWarps * per;
+        const int lb = base + warp * left / kWarps, le = base + (warp + 1) * left / kWarps;
+        if (le - lb == 4) {
+            const int rows[4] = {A.ord[lb], A.ord[lb + 1], A.ord[lb + 2], A.ord[lb + 3]};
+            mstep_group<4>(A, S, rows, lane, first);
+        } else if (le - lb == 3) {
+            const int rows[3] = {A.ord[lb], A.ord[lb + 1], A.ord[lb + 2]};
+            mstep_group<3>(A, S, rows, lane, first);
+        } else if (le - lb == 2) {
+            const int rows[2] = {A.ord[lb], A.ord[lb + 1]};
+            mstep_group<2>(A, S, rows, lane, first);
+        } else if (le - lb == 1) {
+            const int rows[1] = {A.ord[lb]};
+            mstep_group<1>(A, S, rows, lane, first);
         }
     };
     // residuals of this CTA's rows and its partial sums, then the barrier
@@ -640,20 +716,17 @@ using namespace emdq;
 using namespace emdq_host;
 
 namespace {
-// Fit workspace: residuals e[n], centroids cen[n], per-CTA partial sums, then 256 bytes for
-// the barrier counter and the status word.
+// Fit workspace: residuals e[n], centroids cen[n], per-CTA partial sums, the row order
+// ord[n], then 256 bytes for the barrier counter and the status word.
 struct FitLayout {
-    size_t e_off, cen_off, part_off, bar_off, total;
+    size_t e_off, cen_off, part_off, ord_off, bar_off, total;
 };
 constexpr size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr FitLayout fit_layout(int n)
 {
-    return FitLayout{0, al256(sizeof(float) * (size_t)n),
-                     al256(sizeof(float) * (size_t)n) + al256(sizeof(float4) * (size_t)n),
-                     al256(sizeof(float) * (size_t)n) + al256(sizeof(float4) * (size_t)n) +
-                         al256(sizeof(double) * 2 * kFitMaxGrid),
-                     al256(sizeof(float) * (size_t)n) + al256(sizeof(float4) * (size_t)n) +
-                         al256(sizeof(double) * 2 * kFitMaxGrid) + 256};
+    const size_t e = al256(sizeof(float) * (size_t)n), cen = al256(sizeof(float4) * (size_t)n),
+                 part = al256(sizeof(double) * 2 * kFitMaxGrid), ord = al256(sizeof(int) * (size_t)n);
+    return FitLayout{0, e, e + cen, e + cen + part, e + cen + part + ord, e + cen + part + ord + 256};
 }
 size_t fit_smem_bytes(int n) { return (size_t)n * kFitSmemPerMatch; }
 
@@ -769,6 +842,7 @@ extern "C" emdq_status emdq_fit(const float *src, const float *dst, int n, int f
     A.e = reinterpret_cast<float *>(ws + L.e_off);
     A.cen = reinterpret_cast<float4 *>(ws + L.cen_off);
     A.partials = reinterpret_cast<float *>(ws + L.part_off);
+    A.ord = reinterpret_cast<int *>(ws + L.ord_off);
     A.bar = reinterpret_cast<unsigned *>(ws + L.bar_off);
     A.flag = reinterpret_cast<int *>(ws + L.bar_off + 64);
 
@@ -797,7 +871,7 @@ namespace {
 // partial sums.
 size_t batch_body_bytes(int n)
 {
-    return fit_layout(n).bar_off;      // e, cen and partials; the headers are packed first
+    return fit_layout(n).bar_off;      // e, cen, partials, ord; the headers are packed first
 }
 }  // namespace
 
@@ -936,6 +1010,7 @@ extern "C" emdq_status emdq_fit_batch_ex(const emdq_fit_problem *problems, int c
         A.e = reinterpret_cast<float *>(ws + off + L.e_off);
         A.cen = reinterpret_cast<float4 *>(ws + off + L.cen_off);
         A.partials = reinterpret_cast<float *>(ws + off + L.part_off);
+        A.ord = reinterpret_cast<int *>(ws + off + L.ord_off);
         off += batch_body_bytes(q.n);
     }
     cudaLaunchConfig_t cfg = {};
