@@ -37,10 +37,12 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_write.sum), keyed by kernel and tied to the hash of the source it was
 # measured on: a changed kernel reports null until it is captured again.
 NCU_TRAFFIC = {
-    # emdq_field on one 1280x1024 frame (N = 1000): field_tc_prep_kernel 70,656 B read +
-    # field_tc_kernel 12,215,040 B read, nothing written back within either kernel (ncu
-    # --metrics dram__bytes_read.sum,dram__bytes_write.sum on frames of the sequence)
-    'field': dict(bytes=12285696, file='field_tc.cu', src='3347988fe751ff84'),
+    # emdq_field_batch on 4 frames of the 1280x1024 sequence (N = 1000): field_tc_prep_kernel
+    # 0.18-0.21 MB read + 32.0-32.7 MB written (operands written back from L2) and
+    # field_tc_kernel 2.7-3.2 MB read + 45.0-45.3 MB written (the field), per call; the mean
+    # of three steady-state calls over the 4 frames, per frame as the roofline's unit (ncu
+    # --metrics dram__bytes_read.sum,dram__bytes_write.sum --cache-control none)
+    'field': dict(bytes=20150827, file='field_tc.cu', src='d32a3a4450fb882c'),
 }
 
 
