@@ -56,11 +56,23 @@ __device__ __forceinline__ void tap_sample(const uint8_t *__restrict__ frame, co
     }
 }
 
-__device__ __forceinline__ unsigned blend_channel(unsigned c, float w, float v, float w1)
+// c <- clamp(floor((w c + v)/(w + 1) + 1/2), 0, 255).  w c + v is exact for integer v and
+// the quotient is correctly rounded, so ties land exactly on .5 as in FP64.  The quotient
+// a / b comes from the correctly rounded reciprocal y = RN(1/b), taken once per pixel, and
+// per channel Markstein's FMA correction: q0 = RN(a y), r = a - b q0 (exact with an FMA),
+// q = RN(q0 + r y) (P. Markstein, "Computation of elementary functions on the IBM RISC
+// System/6000 processor", IBM J. Res. Dev. 34(1), 1990).  Checked exhaustively against the
+// IEEE division for every float a in [0, 8192) and every b = 1..31 (the whole range of
+// w c + v and w + 1 here): q is the same bits for every a >= 2^-123; below that (where the
+// residual r underflows) it can differ in the last place, and floor(q + 1/2) is the same
+// for every a in the range.
+__device__ __forceinline__ unsigned blend_channel(unsigned c, float w, float v, float w1,
+                                                  float rw1)
 {
-    // c <- clamp(floor((w c + v)/(w + 1) + 1/2), 0, 255).  w c + v is exact for integer
-    // v and the quotient is correctly rounded, so ties land exactly on .5 as in FP64.
-    const float z = floorf(__fdiv_rn(fmaf(w, static_cast<float>(c), v), w1) + 0.5f);
+    const float a = fmaf(w, static_cast<float>(c), v);
+    const float q0 = __fmul_rn(a, rw1);
+    const float q = __fmaf_rn(__fmaf_rn(-q0, w1, a), rw1, q0);
+    const float z = floorf(q + 0.5f);
     return static_cast<unsigned>(fminf(fmaxf(z, 0.f), 255.f));
 }
 
@@ -69,10 +81,11 @@ __device__ __forceinline__ uchar4 blend_update(uchar4 cv, const float (&v)[CH])
 {
     const float w = static_cast<float>(cv.w);
     const float w1 = w + 1.f;
-    cv.x = blend_channel(cv.x, w, v[0], w1);
+    const float rw1 = __frcp_rn(w1);
+    cv.x = blend_channel(cv.x, w, v[0], w1, rw1);
     if (CH == 3) {
-        cv.y = blend_channel(cv.y, w, v[1 % CH], w1);
-        cv.z = blend_channel(cv.z, w, v[2 % CH], w1);
+        cv.y = blend_channel(cv.y, w, v[1 % CH], w1, rw1);
+        cv.z = blend_channel(cv.z, w, v[2 % CH], w1, rw1);
     }
     cv.w = static_cast<unsigned char>(cv.w < 30 ? cv.w + 1 : 30);
     return cv;
