@@ -48,7 +48,9 @@ __global__ void __launch_bounds__(kWarpThreadsX) mosaic_warp_kernel(
         if (t[k].ok) *cp[k] = blend_update<CH>(cv[k], v[k]);
 }
 
-// G frames of a sequence blended in one pass: the thread of canvas pixel p applies frames
+// G frames of a sequence blended in one pass (held to 51 registers for G <= 4: ten blocks
+// of 128 threads per SM hide more of the gather latency than the few spilled words cost):
+// the thread of canvas pixel p applies frames
 // 0..G-1 to p in order, exactly as G mosaic_warp launches would (the blend of a pixel
 // depends only on that pixel's earlier updates), but reads and writes the canvas word
 // once, and issues the field loads and bilinear taps of all G frames before any update, so
@@ -66,7 +68,7 @@ struct WarpBatch {
 };
 
 template <int CH, int G>
-__global__ void __launch_bounds__(kWarpThreadsX) mosaic_warp_batch_kernel(
+__global__ void __launch_bounds__(kWarpThreadsX, G <= 4 ? 10 : 1) mosaic_warp_batch_kernel(
     const __grid_constant__ WarpBatch W, int fw, int fh, int pitch, int ux0, int uy0, int uw,
     uchar4 *__restrict__ canvas, int cpitch4, int ox, int oy)
 {
