@@ -745,7 +745,8 @@ def run_gpu(args, ws, rank, local):
               (', the pass replayed from one CUDA graph' if graph is not None else '')),
         batch=B, field_group=G, warm_start=warm, cuda_graph=graph is not None,
         **({'cuda_graph_note': graph_note} if graph_note else {}), wall_s=wall, roofline=roof,
-        gpu_launches=total_frames * (2 if fused else 3) + args.steps * len(batches) * (2 if warm else 1),
+        gpu_launches=(args.steps * sum(3 * ((len(ks) + G - 1) // G) for ks in batches) if G > 1 else
+                      total_frames * (2 if fused else 3)) + args.steps * len(batches) * (2 if warm else 1),
         clocks=clk,
         e2e=e2e, plain_fp32_gpu=plain,
         speedup_vs_plain_fp32_gpu=(None if plain is None else
