@@ -61,6 +61,10 @@ def lib():
             D, I = ctypes.c_double, ctypes.c_int
             L.orc_alpha_for_frame.restype = D
             L.orc_alpha_for_frame.argtypes = [I, I]
+            L.orc_beta_for_frame.restype = D
+            L.orc_beta_for_frame.argtypes = [I, I]
+            L.orc_uncertainty.argtypes = [P, P, I, I, I, I, I, D, P, I]
+            L.orc_uncertainty_points.argtypes = [P, P, I, P, I, D, P, I]
             L.orc_dq_from_rt.argtypes = [D, D, D, P]
             L.orc_rt_from_dq.argtypes = [P, P, P, P]
             L.orc_apply_warp.argtypes = [D, P, D, D, P]
@@ -132,6 +136,30 @@ def field_points(q8, c, src, pts, alpha: float, nthreads: int = 0) -> np.ndarray
     out = np.empty((pts.shape[0], 2))
     rc = lib().orc_field_points(_p(q8), _p(c), _p(src), c.shape[0], _p(pts), pts.shape[0],
                                 float(alpha), _p(out), nthreads or max_threads())
+    assert rc == OK, rc
+    return out
+
+
+def beta_for_frame(w: int, h: int) -> float:
+    return lib().orc_beta_for_frame(int(w), int(h))
+
+
+def uncertainty(c, src, grid, beta: float, nthreads: int = 0) -> np.ndarray:
+    """Eq. 8 on grid=(x0, y0, w, h): [h, w] float64, +inf where there is no inlier."""
+    c, src = _d(c), _d(src)
+    x0, y0, gw, gh = (int(v) for v in grid)
+    out = np.empty((gh, gw))
+    rc = lib().orc_uncertainty(_p(c), _p(src), c.shape[0], x0, y0, gw, gh, float(beta), _p(out),
+                               nthreads or max_threads())
+    assert rc == OK, rc
+    return out
+
+
+def uncertainty_points(c, src, pts, beta: float, nthreads: int = 0) -> np.ndarray:
+    c, src, pts = _d(c), _d(src), _d(pts)
+    out = np.empty(pts.shape[0])
+    rc = lib().orc_uncertainty_points(_p(c), _p(src), c.shape[0], _p(pts), pts.shape[0],
+                                      float(beta), _p(out), nthreads or max_threads())
     assert rc == OK, rc
     return out
 

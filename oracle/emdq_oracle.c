@@ -11,7 +11,9 @@
  *                             average of X_t / s - R X_0), then "the quaternion from R and t"
  *   Sec. III-F, Eqs. 23-24    frame 0 inserted directly; per-pixel gather and a running
  *                             average whose weight is capped at 30
- *   Sec. III-G                alpha = 2e-4 / s^2, s = (w/480 + h/270)/2
+ *   Sec. III-G                alpha = 2e-4 / s^2, beta = 3e-3 / s^2, s = (w/480 + h/270)/2
+ *   Sec. III-C, Eq. 8         uncertainty of the EMDQ field at a point: the minimum over the
+ *                             feature inliers of exp(beta d^2), d the distance to the inlier
  *
  * Readings (the paper is silent, garbled or delegates to its EMDQ reference)
  *   - Eq. 3 blends q without normalising it; a blended DQ is normalised by the norm of its
@@ -62,6 +64,12 @@ double orc_alpha_for_frame(int w, int h)
 {
     double s = (w / 480.0 + h / 270.0) / 2.0;
     return 2e-4 / (s * s);
+}
+
+double orc_beta_for_frame(int w, int h)
+{
+    double s = (w / 480.0 + h / 270.0) / 2.0;
+    return 3e-3 / (s * s);
 }
 
 /* Hamilton product of quaternions stored (w, x, y, z). */
@@ -161,6 +169,52 @@ int orc_field_points(const double *q8, const double *c, const double *src, int n
 #endif
     for (int k = 0; k < npts; ++k)
         field_at(q8, c, src, n, pts[2 * k], pts[2 * k + 1], alpha, disp + 2 * k);
+    return ORC_OK;
+}
+
+/* Eq. 8 at one point: min over the feature inliers j (the matches the fit keeps, c_j > 0)
+ * of exp(beta d_j^2), written as the paper writes it (the exponential of every distance,
+ * then the minimum); +inf when there is no inlier. */
+static double uncertainty_at(const double *c, const double *src, int n, double px, double py,
+                             double beta)
+{
+    double best = INFINITY;
+    for (int j = 0; j < n; ++j) {
+        if (!(c[j] > 0.0)) continue;
+        double dx = src[2 * j] - px, dy = src[2 * j + 1] - py;
+        double u = exp(beta * (dx * dx + dy * dy));
+        if (u < best) best = u;
+    }
+    return best;
+}
+
+int orc_uncertainty(const double *c, const double *src, int n, int gx0, int gy0, int gw, int gh,
+                    double beta, double *out, int nthreads)
+{
+    if (n < 0 || gw < 0 || gh < 0 || (n > 0 && (!c || !src)) || !out || !(beta > 0.0))
+        return ORC_EINVAL;
+    (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int y = 0; y < gh; ++y)
+        for (int x = 0; x < gw; ++x)
+            out[(size_t)y * gw + x] =
+                uncertainty_at(c, src, n, (double)(gx0 + x), (double)(gy0 + y), beta);
+    return ORC_OK;
+}
+
+int orc_uncertainty_points(const double *c, const double *src, int n, const double *pts,
+                           int npts, double beta, double *out, int nthreads)
+{
+    if (n < 0 || npts < 0 || (n > 0 && (!c || !src)) || !pts || !out || !(beta > 0.0))
+        return ORC_EINVAL;
+    (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int k = 0; k < npts; ++k)
+        out[k] = uncertainty_at(c, src, n, pts[2 * k], pts[2 * k + 1], beta);
     return ORC_OK;
 }
 

@@ -36,6 +36,8 @@ typedef struct {
 
 /* Sec. III-G: alpha = 2e-4 / s^2 with s = (w/480 + h/270)/2. */
 double orc_alpha_for_frame(int w, int h);
+/* Sec. III-G: beta = 3e-3 / s^2, the coefficient of the uncertainty (Eq. 8). */
+double orc_beta_for_frame(int w, int h);
 
 /* Eq. 1 + footnote: planar DQ of the rigid part (R(th), t); inverse of the same. */
 void orc_dq_from_rt(double th, double tx, double ty, double q[4]);
@@ -58,6 +60,12 @@ int orc_field_points(const double *q8, const double *c, const double *src, int n
 /* EM M-step (reading of Eqs. 16-20): per match i, the p-weighted Gaussian similarity fit of
  * all matches j (including i).  Writes s[n], th[n], t[n*2] and q8[n*8].  Returns
  * ORC_EDEGENERATE if some row has no weight or no spread. */
+/* Eq. 8: the uncertainty min_j exp(beta d_j^2) over the inliers (c_j > 0) at every pixel
+ * of the window (out: gh x gw) or at npts points (pts: npts x 2); +inf without inliers. */
+int orc_uncertainty(const double *c, const double *src, int n, int gx0, int gy0, int gw, int gh,
+                    double beta, double *out, int nthreads);
+int orc_uncertainty_points(const double *c, const double *src, int n, const double *pts,
+                           int npts, double beta, double *out, int nthreads);
 int orc_mstep(const double *src, const double *dst, const double *p, int n, double alpha,
               double *s, double *th, double *t, double *q8);
 
