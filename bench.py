@@ -593,6 +593,37 @@ def run_gpu(args, ws, rank, local):
     statuses = sorted({emdq.STATUS.get(int(v), '?') for v in iv[:, 0].tolist()})
     total_frames = args.steps * n_frames
 
+    # the uncertainty map of Eq. 8 (not part of the step): emdq_uncertainty on every frame's
+    # window from the fits of the first batch, timed alone on the main stream
+    unc = None
+    if rank == 0:
+        fit_batch(0, batches[0], lambda k: src[k], lambda k: dst[k])
+        torch.cuda.synchronize()
+        outs0 = fit_outs_all[0]
+        beta = emdq.beta_for_frame(sc.w, sc.h)
+        umap = torch.empty(max_gw * max_gh, dtype=torch.float32, device=dev)
+        ks0 = batches[0]
+
+        def unc_pass():
+            for j, k in enumerate(ks0):
+                g = grids[k]
+                emdq.emdq_uncertainty(outs0[j]['c'], src[k], g, beta, out=umap[: g[2] * g[3]].view(g[3], g[2]))
+
+        unc_pass()
+        u_ms = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            unc_pass()
+            b.record(stream)
+            b.synchronize()
+            u_ms.append(a.elapsed_time(b) / len(ks0))
+        upx = float(np.mean([grids[k][2] * grids[k][3] for k in ks0]))
+        unc = dict(call='emdq_uncertainty (Eq. 8), one call per frame, not part of the step',
+                   ms_per_frame=float(np.median(u_ms)), window_mpix_per_s=upx / 1e3 / float(np.median(u_ms)),
+                   bound='latency', frames=len(ks0))
+
     # end to end through the public API from pinned host buffers: per frame the H2D copy of
     # the frame and its matches, the three calls, the D2H of the fit record and weights
     e2e = None
@@ -748,7 +779,7 @@ def run_gpu(args, ws, rank, local):
         gpu_launches=(args.steps * sum(3 * ((len(ks) + G - 1) // G) for ks in batches) if G > 1 else
                       total_frames * (2 if fused else 3)) + args.steps * len(batches) * (2 if warm else 1),
         clocks=clk,
-        e2e=e2e, plain_fp32_gpu=plain,
+        e2e=e2e, plain_fp32_gpu=plain, uncertainty=unc,
         speedup_vs_plain_fp32_gpu=(None if plain is None else
                                    job_mpix_per_s(ws, total_frames, sc.w, sc.h, total_ms) / plain['value']),
         fit_status=statuses,

@@ -85,6 +85,8 @@ typedef struct {
 EMDQ_API void        emdq_default_params(emdq_params *prm);
 /* Sec. III-G: alpha for a w x h frame. */
 EMDQ_API float       emdq_alpha_for_frame(int w, int h);
+/* Sec. III-G: beta (the coefficient of the uncertainty, Eq. 8) for a w x h frame, 3e-3 / s^2. */
+EMDQ_API float       emdq_beta_for_frame(int w, int h);
 EMDQ_API const char *emdq_status_string(int status);
 EMDQ_API int         emdq_abi_version(void);
 
@@ -248,6 +250,24 @@ typedef struct {
 EMDQ_API size_t      emdq_field_batch_workspace_size(const emdq_field_problem *problems, int count);
 EMDQ_API emdq_status emdq_field_batch(const emdq_field_problem *problems, int count,
                                       void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------ emdq_uncertainty -
+ * Uncertainty of the EMDQ field (Sec. III-C, Eq. 8): at every pixel p of the window
+ * (reference coordinates, as emdq_field), the minimum over the feature inliers j (the
+ * matches the fit keeps: c_j > 0) of exp(beta |p - x_j|^2), i.e. exp(beta d^2) with d the
+ * distance to the nearest inlier.  Low near inliers, growing fast away from them; +inf where
+ * beta d^2 exceeds the FP32 range or when there is no inlier.
+ *
+ *   c, src     device, n field weights (emdq_fit's c_out) and n x 2 match positions in the
+ *              reference frame (8-byte aligned); may be NULL when n = 0
+ *   grid_*     the pixel window
+ *   beta       > 0 (emdq_beta_for_frame gives the paper's value for a frame size)
+ *   out        device, grid_h x grid_w float (written)
+ * Returns EMDQ_EINVAL for bad arguments; an empty window writes nothing.
+ */
+EMDQ_API emdq_status emdq_uncertainty(const float *c, const float *src, int n, int grid_x0,
+                                      int grid_y0, int grid_w, int grid_h, float beta, float *out,
+                                      void *stream);
 
 /* ------------------------------------------------------------------ mosaic_warp ------
  * Gather warp + capped running-average blend of frame t into the canvas (Sec. III-F,

@@ -17,7 +17,7 @@ import torch
 from ._build import LIB as _LIB_PATH, build  # noqa: F401
 
 __all__ = ['emdq_fit', 'emdq_fit_batch', 'emdq_field', 'emdq_field_batch', 'mosaic_warp',
-           'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'mosaic_insert_reference',
+           'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'emdq_uncertainty', 'mosaic_insert_reference',
            'alpha_for_frame', 'fit_workspace_size', 'field_workspace_size', 'EmdqError',
            'FP32', 'BF16', 'STATUS', 'lib', 'build']
 
@@ -113,6 +113,9 @@ def lib() -> ctypes.CDLL:
             L.emdq_field.restype = I
             L.emdq_field.argtypes = [P, P, P, I, I, I, I, I, F, I, P, P, Z, P]
             L.mosaic_warp_batch.restype = I
+            L.emdq_beta_for_frame.restype = F
+            L.emdq_beta_for_frame.argtypes = [I, I]
+            L.emdq_uncertainty.argtypes = [P, P, I, I, I, I, I, F, P, P]
             L.emdq_batch_workspace_size.argtypes = [P, I, I]
             L.emdq_batch_workspace_size.restype = Z
             L.emdq_batch.argtypes = [P, I, ctypes.POINTER(_Params), P, P, P, Z, P]
@@ -161,6 +164,10 @@ def _check(t: torch.Tensor, name: str, dtype: torch.dtype, shape=None):
 
 def alpha_for_frame(w: int, h: int) -> float:
     return lib().emdq_alpha_for_frame(int(w), int(h))
+
+
+def beta_for_frame(w: int, h: int) -> float:
+    return lib().emdq_beta_for_frame(int(w), int(h))
 
 
 def fit_workspace_size(n: int) -> int:
@@ -362,6 +369,24 @@ def emdq_field_batch(problems, *, outs: list | None = None, workspace: torch.Ten
     if rc != 0:
         raise EmdqError('emdq_field_batch', rc)
     return res
+
+
+def emdq_uncertainty(c: torch.Tensor, src: torch.Tensor, grid, beta: float, *,
+                     out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Eq. 8 on grid=(x0, y0, w, h): min over the inliers (c > 0) of exp(beta d^2), [h, w]
+    float32 CUDA (+inf without inliers or beyond the FP32 range)."""
+    n = c.shape[0]
+    _check(c, 'c', torch.float32, (n,))
+    _check(src, 'src', torch.float32, (n, 2))
+    x0, y0, gw, gh = (int(v) for v in grid)
+    if out is None:
+        out = torch.empty((gh, gw), dtype=torch.float32, device=c.device)
+    _check(out, 'out', torch.float32, (gh, gw))
+    rc = lib().emdq_uncertainty(_ptr(c), _ptr(src), n, x0, y0, gw, gh, float(beta), _ptr(out),
+                                _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_uncertainty', rc)
+    return out
 
 
 def _frame_args(frame: torch.Tensor):

@@ -57,6 +57,13 @@ extern "C" float emdq_alpha_for_frame(int w, int h)
     return static_cast<float>(2e-4 / (s * s));
 }
 
+extern "C" float emdq_beta_for_frame(int w, int h)
+{
+    // Sec. III-G: beta = 3e-3 / s^2, the same resolution scale as alpha
+    const double s = (w / 480.0 + h / 270.0) / 2.0;
+    return static_cast<float>(3e-3 / (s * s));
+}
+
 extern "C" int emdq_abi_version(void) { return EMDQ_ABI_VERSION; }
 
 extern "C" const char *emdq_status_string(int status)
