@@ -185,7 +185,7 @@ EMDQ_API emdq_status emdq_fit_batch_autotune(const emdq_fit_problem *problems, i
  * its own pool, or a service whose memory is fixed at start-up -- and so cannot provide
  * the workspace emdq_fit asks for.  This entry point takes the same inputs and outputs
  * (all still allocated by the caller) and keeps its scratch in a fixed array of about
- * 118 KB inside the library, which every GPU that loads the library holds until exit.
+ * 136 KB inside the library, which every GPU that loads the library holds until exit.
  *
  *   - n must be at most 5120 (emdq_fit_max_n()); larger n returns EMDQ_ENOTSUP.
  *   - It allocates nothing and calls no allocating routine.  Its first call on each device

@@ -1111,7 +1111,7 @@ extern "C" emdq_status emdq_fit_batch_autotune(const emdq_fit_problem *problems,
 // caller workspace.  Every GPU that loads the library holds the array until exit.
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = fit_layout(kFitMaxN).total;   // about 118 KB
+constexpr size_t kNoAllocScratchBytes = fit_layout(kFitMaxN).total;   // about 136 KB
 
 static __device__ __align__(256) unsigned char g_fit_scratch[kNoAllocScratchBytes];
 
