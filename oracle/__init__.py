@@ -64,6 +64,11 @@ def lib():
             L.orc_beta_for_frame.restype = D
             L.orc_beta_for_frame.argtypes = [I, I]
             L.orc_uncertainty.argtypes = [P, P, I, I, I, I, I, D, P, I]
+            L.orc_compose.argtypes = [P, P, P]
+            L.orc_node_track.argtypes = [P, P, P, I, P, P, P, I, D, D, P, P, I]
+            L.orc_node_merge.argtypes = [P, P, P, P, P, P, I, D, P, P]
+            L.orc_gamma_for_frame.restype = D
+            L.orc_gamma_for_frame.argtypes = [I, I]
             L.orc_uncertainty_points.argtypes = [P, P, I, P, I, D, P, I]
             L.orc_dq_from_rt.argtypes = [D, D, D, P]
             L.orc_rt_from_dq.argtypes = [P, P, P, P]
@@ -162,6 +167,43 @@ def uncertainty_points(c, src, pts, beta: float, nthreads: int = 0) -> np.ndarra
                                       float(beta), _p(out), nthreads or max_threads())
     assert rc == OK, rc
     return out
+
+
+def gamma_for_frame(w: int, h: int) -> float:
+    return lib().orc_gamma_for_frame(int(w), int(h))
+
+
+def compose(w_old, dw) -> np.ndarray:
+    """App. A: the warp row w_new with s_new q_new(x) = ds dq(s_old q_old(x))."""
+    w_old, dw = _d(w_old, (8,)), _d(dw, (8,))
+    out = np.empty(8)
+    lib().orc_compose(_p(w_old), _p(dw), _p(out))
+    return out
+
+
+def node_track(x0, w_old, s2_old, q8, c, src, alpha: float, beta: float, nthreads: int = 0):
+    """Eq. 5 + App. A + Eq. 9 for every node: (w_new [nn, 8], s2_new [nn])."""
+    x0, w_old, s2_old = _d(x0), _d(w_old), _d(s2_old)
+    q8, c, src = _d(q8), _d(c), _d(src)
+    nn = s2_old.shape[0]
+    w_new, s2_new = np.empty((nn, 8)), np.empty(nn)
+    rc = lib().orc_node_track(_p(x0), _p(w_old), _p(s2_old), nn, _p(q8), _p(c), _p(src),
+                              c.shape[0], float(alpha), float(beta), _p(w_new), _p(s2_new),
+                              nthreads or max_threads())
+    assert rc == OK, rc
+    return w_new, s2_new
+
+
+def node_merge(x0, w_track, s2_track, w_loop, s2_loop, w_key, gamma: float):
+    """Eqs. 12-15 for every node: (w_out [nn, 8], s2_out [nn])."""
+    x0, w_track, s2_track = _d(x0), _d(w_track), _d(s2_track)
+    w_loop, s2_loop, w_key = _d(w_loop), _d(s2_loop), _d(w_key)
+    nn = s2_track.shape[0]
+    w_out, s2_out = np.empty((nn, 8)), np.empty(nn)
+    rc = lib().orc_node_merge(_p(x0), _p(w_track), _p(s2_track), _p(w_loop), _p(s2_loop),
+                              _p(w_key), nn, float(gamma), _p(w_out), _p(s2_out))
+    assert rc == OK, rc
+    return w_out, s2_out
 
 
 def mstep(src, dst, p, alpha: float):

@@ -14,6 +14,9 @@
  *   Sec. III-G                alpha = 2e-4 / s^2, beta = 3e-3 / s^2, s = (w/480 + h/270)/2
  *   Sec. III-C, Eq. 8         uncertainty of the EMDQ field at a point: the minimum over the
  *                             feature inliers of exp(beta d^2), d the distance to the inlier
+ *   Eq. 5, App. A, Eq. 9      node tracking: W_i,t = f(W_i,t-1, dW_i) with f the composition
+ *                             s_new q_new(x) = ds dq(s_old q_old(x)); sigma^2 propagation
+ *   Eqs. 12-15                EKF merge of the tracking and loop-closing node warps
  *
  * Readings (the paper is silent, garbled or delegates to its EMDQ reference)
  *   - Eq. 3 blends q without normalising it; a blended DQ is normalised by the norm of its
@@ -216,6 +219,157 @@ int orc_uncertainty_points(const double *c, const double *src, int n, const doub
     for (int k = 0; k < npts; ++k)
         out[k] = uncertainty_at(c, src, n, pts[2 * k], pts[2 * k + 1], beta);
     return ORC_OK;
+}
+
+/* Row (r_w, r_z, d_x, d_y, s, 1, 0, 0) of a similarity s (R(th) x + t), r_w >= 0. */
+static void row_from_srt(double s, double th, double tx, double ty, double row[8])
+{
+    double q[4];
+    orc_dq_from_rt(th, tx, ty, q);
+    if (q[0] < 0.0)
+        for (int k = 0; k < 4; ++k) q[k] = -q[k];
+    for (int k = 0; k < 4; ++k) row[k] = q[k];
+    row[4] = s;
+    row[5] = 1.0;
+    row[6] = row[7] = 0.0;
+}
+
+/* (s, th, t) of a row whose DQ part may be unnormalised (normalised by its real part). */
+static void srt_from_row(const double row[8], double *s, double *th, double *tx, double *ty)
+{
+    double nr = sqrt(row[0] * row[0] + row[1] * row[1]);
+    double q[4] = {row[0] / nr, row[1] / nr, row[2] / nr, row[3] / nr};
+    orc_rt_from_dq(q, th, tx, ty);
+    *s = row[4];
+}
+
+/* App. A: the updated warp of a node, (s_new, q_new) with s_new q_new(x) = ds dq(s_old q_old(x))
+ * for every x: the two similarities composed -- scale ds s_old, rotation dth + th_old,
+ * translation dR t_old + dt / s_old. */
+void orc_compose(const double w_old[8], const double dw[8], double w_new[8])
+{
+    double so, tho, txo, tyo, ds, dth, dtx, dty;
+    srt_from_row(w_old, &so, &tho, &txo, &tyo);
+    srt_from_row(dw, &ds, &dth, &dtx, &dty);
+    double c = cos(dth), sn = sin(dth);
+    row_from_srt(ds * so, tho + dth, c * txo - sn * tyo + dtx / so, sn * txo + c * tyo + dty / so,
+                 w_new);
+}
+
+/* Eqs. 2-3 at a point as a warp row (the blended DQ normalised by its real part, the blended
+ * scale); returns 0 when the weights sum to 0. */
+static int warp_at(const double *q8, const double *c, const double *src, int n, double px,
+                   double py, double alpha, double row[8])
+{
+    double sw = 0.0, ss = 0.0, sq[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < n; ++i) {
+        double dx = src[2 * i] - px, dy = src[2 * i + 1] - py;
+        double w = c[i] * exp(-alpha * (dx * dx + dy * dy));
+        sw += w;
+        ss += w * q8[8 * i + 4];
+        for (int k = 0; k < 4; ++k) sq[k] += w * q8[8 * i + k];
+    }
+    if (!(sw > 0.0) || !isfinite(sw)) return 0;
+    double nr = sqrt(sq[0] * sq[0] + sq[1] * sq[1]);
+    for (int k = 0; k < 4; ++k) row[k] = sq[k] / nr;
+    row[4] = ss / sw;
+    row[5] = 1.0;
+    row[6] = row[7] = 0.0;
+    return 1;
+}
+
+/* Eq. 5 + App. A + Eq. 9 for every node i: its position at t-1, p = W_i,t-1(x_i,0); the
+ * EMDQ warp dW at p (Eqs. 2-3 over the matches of t-1 -> t, positions src in frame t-1);
+ * its uncertainty d_sigma^2 at p (Eq. 8); W_i,t = f(W_i,t-1, dW) (App. A) and
+ * sigma^2_i,t = ds^2 sigma^2_i,t-1 + d_sigma^2 (Eq. 9).  A node where the field has no weight
+ * keeps its warp and its uncertainty becomes +inf. */
+int orc_node_track(const double *x0, const double *w_old, const double *s2_old, int nn,
+                   const double *q8, const double *c, const double *src, int n, double alpha,
+                   double beta, double *w_new, double *s2_new, int nthreads)
+{
+    if (nn < 0 || n < 0 || (nn > 0 && (!x0 || !w_old || !s2_old || !w_new || !s2_new)) ||
+        (n > 0 && (!q8 || !c || !src)))
+        return ORC_EINVAL;
+    (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int i = 0; i < nn; ++i) {
+        const double *wo = w_old + 8 * (size_t)i;
+        double so, th, tx, ty, p[2], dw[8];
+        srt_from_row(wo, &so, &th, &tx, &ty);
+        double qo[4] = {wo[0], wo[1], wo[2], wo[3]};
+        double nr = sqrt(qo[0] * qo[0] + qo[1] * qo[1]);
+        for (int k = 0; k < 4; ++k) qo[k] /= nr;
+        orc_apply_warp(so, qo, x0[2 * i], x0[2 * i + 1], p);
+        const double du = uncertainty_at(c, src, n, p[0], p[1], beta);
+        if (!warp_at(q8, c, src, n, p[0], p[1], alpha, dw)) {
+            for (int k = 0; k < 8; ++k) w_new[8 * (size_t)i + k] = wo[k];
+            s2_new[i] = INFINITY;
+            continue;
+        }
+        orc_compose(wo, dw, w_new + 8 * (size_t)i);
+        s2_new[i] = dw[4] * dw[4] * s2_old[i] + du;
+    }
+    return ORC_OK;
+}
+
+/* Eqs. 12-15 for every node: eta = exp(-gamma |x_t - x_k|^2) with x_t = W_track(x_0) and
+ * x_k = W_key(x_0) (Eq. 13); A = [[st^2, eta st sl], [eta st sl, sl^2]] (Eq. 12); the merged
+ * uncertainty 1 / sum(A^-1) (Eq. 14) and the weights sigma_merge^2 A^-1 [1 1]^T (Eq. 15); the
+ * merged warp is the weighted average of the two (DQ normalised by its real part, scale
+ * averaged).  Where a weight is negative (or A is singular) the warp and uncertainty of the
+ * smaller uncertainty are taken (ties: tracking). */
+int orc_node_merge(const double *x0, const double *w_track, const double *s2_track,
+                   const double *w_loop, const double *s2_loop, const double *w_key, int nn,
+                   double gamma, double *w_out, double *s2_out)
+{
+    if (nn < 0 || (nn > 0 && (!x0 || !w_track || !s2_track || !w_loop || !s2_loop || !w_key ||
+                              !w_out || !s2_out)))
+        return ORC_EINVAL;
+    for (int i = 0; i < nn; ++i) {
+        const double *wt = w_track + 8 * (size_t)i, *wl = w_loop + 8 * (size_t)i,
+                     *wk = w_key + 8 * (size_t)i;
+        double s, th, tx, ty, qn[4], xt[2], xk[2];
+        srt_from_row(wt, &s, &th, &tx, &ty);
+        double nrt = sqrt(wt[0] * wt[0] + wt[1] * wt[1]);
+        for (int k = 0; k < 4; ++k) qn[k] = wt[k] / nrt;
+        orc_apply_warp(s, qn, x0[2 * i], x0[2 * i + 1], xt);
+        srt_from_row(wk, &s, &th, &tx, &ty);
+        double nrk = sqrt(wk[0] * wk[0] + wk[1] * wk[1]);
+        for (int k = 0; k < 4; ++k) qn[k] = wk[k] / nrk;
+        orc_apply_warp(s, qn, x0[2 * i], x0[2 * i + 1], xk);
+        const double dx = xt[0] - xk[0], dy = xt[1] - xk[1];
+        const double eta = exp(-gamma * (dx * dx + dy * dy));
+        const double vt = s2_track[i], vl = s2_loop[i], st = sqrt(vt), sl = sqrt(vl);
+        const double a01 = eta * st * sl, det = vt * vl - a01 * a01;
+        /* A^-1 = [[vl, -a01], [-a01, vt]] / det */
+        const double i00 = vl / det, i01 = -a01 / det, i11 = vt / det;
+        const double sm = 1.0 / (i00 + 2.0 * i01 + i11);
+        const double w0 = sm * (i00 + i01), w1 = sm * (i01 + i11);
+        double *wo = w_out + 8 * (size_t)i;
+        if (!(w0 >= 0.0) || !(w1 >= 0.0) || !isfinite(sm) || !isfinite(w0) || !isfinite(w1)) {
+            const double *pick = vt <= vl ? wt : wl;
+            for (int k = 0; k < 8; ++k) wo[k] = pick[k];
+            s2_out[i] = vt <= vl ? vt : vl;
+            continue;
+        }
+        double q[4];
+        for (int k = 0; k < 4; ++k) q[k] = w0 * wt[k] / nrt + w1 * wl[k] / sqrt(wl[0] * wl[0] + wl[1] * wl[1]);
+        double nq = sqrt(q[0] * q[0] + q[1] * q[1]);
+        for (int k = 0; k < 4; ++k) wo[k] = q[k] / nq;
+        wo[4] = w0 * wt[4] + w1 * wl[4];
+        wo[5] = 1.0;
+        wo[6] = wo[7] = 0.0;
+        s2_out[i] = sm;
+    }
+    return ORC_OK;
+}
+
+double orc_gamma_for_frame(int w, int h)
+{
+    double s = (w / 480.0 + h / 270.0) / 2.0;
+    return 5e-3 / (s * s);
 }
 
 int orc_mstep(const double *src, const double *dst, const double *p, int n, double alpha,

@@ -66,6 +66,18 @@ int orc_uncertainty(const double *c, const double *src, int n, int gx0, int gy0,
                     double beta, double *out, int nthreads);
 int orc_uncertainty_points(const double *c, const double *src, int n, const double *pts,
                            int npts, double beta, double *out, int nthreads);
+/* App. A: w_new (a warp row) with s_new q_new(x) = ds dq(s_old q_old(x)). */
+void orc_compose(const double w_old[8], const double dw[8], double w_new[8]);
+/* Eq. 5, App. A, Eq. 9: node warps and uncertainties after one tracking step (see the .c). */
+int orc_node_track(const double *x0, const double *w_old, const double *s2_old, int nn,
+                   const double *q8, const double *c, const double *src, int n, double alpha,
+                   double beta, double *w_new, double *s2_new, int nthreads);
+/* Eqs. 12-15: EKF merge of tracking and loop-closing node warps (see the .c). */
+int orc_node_merge(const double *x0, const double *w_track, const double *s2_track,
+                   const double *w_loop, const double *s2_loop, const double *w_key, int nn,
+                   double gamma, double *w_out, double *s2_out);
+/* Sec. III-G: gamma = 5e-3 / s^2 (Eq. 13). */
+double orc_gamma_for_frame(int w, int h);
 int orc_mstep(const double *src, const double *dst, const double *p, int n, double alpha,
               double *s, double *th, double *t, double *q8);
 
