@@ -623,6 +623,34 @@ def run_gpu(args, ws, rank, local):
         unc = dict(call='emdq_uncertainty (Eq. 8), one call per frame, not part of the step',
                    ms_per_frame=float(np.median(u_ms)), window_mpix_per_s=upx / 1e3 / float(np.median(u_ms)),
                    bound='latency', frames=len(ks0))
+        # node tracking (Eq. 5, App. A, Eq. 9) of a 30-px node lattice over the frame
+        xs, ys = np.meshgrid(np.arange(0, sc.w, 30.0), np.arange(0, sc.h, 30.0))
+        x0n = torch.tensor(np.stack([xs.ravel(), ys.ravel()], 1), dtype=torch.float32, device=dev)
+        nn = x0n.shape[0]
+        wn = torch.zeros((nn, 8), device=dev)
+        wn[:, 0] = 1.0
+        wn[:, 4] = 1.0
+        wn[:, 5] = 1.0
+        s2n = torch.ones(nn, device=dev)
+        alpha_n = emdq.alpha_for_frame(sc.w, sc.h)
+
+        def node_pass():
+            w_, v_ = wn, s2n
+            for j, k in enumerate(ks0):
+                w_, v_ = emdq.node_track(x0n, w_, v_, outs0[j]['q'], outs0[j]['c'], src[k], alpha_n, beta)
+            return w_, v_
+
+        node_pass()
+        n_ms = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            node_pass()
+            b.record(stream)
+            b.synchronize()
+            n_ms.append(a.elapsed_time(b) / len(ks0))
+        unc['node_track'] = dict(call='emdq_node_track (Eq. 5, App. A, Eq. 9), one call per frame',
+                                 nodes=nn, ms_per_frame=float(np.median(n_ms)))
 
     # end to end through the public API from pinned host buffers: per frame the H2D copy of
     # the frame and its matches, the three calls, the D2H of the fit record and weights
@@ -779,7 +807,7 @@ def run_gpu(args, ws, rank, local):
         gpu_launches=(args.steps * sum(3 * ((len(ks) + G - 1) // G) for ks in batches) if G > 1 else
                       total_frames * (2 if fused else 3)) + args.steps * len(batches) * (2 if warm else 1),
         clocks=clk,
-        e2e=e2e, plain_fp32_gpu=plain, uncertainty=unc,
+        e2e=e2e, plain_fp32_gpu=plain, beside_the_step=unc,
         speedup_vs_plain_fp32_gpu=(None if plain is None else
                                    job_mpix_per_s(ws, total_frames, sc.w, sc.h, total_ms) / plain['value']),
         fit_status=statuses,

@@ -269,6 +269,36 @@ EMDQ_API emdq_status emdq_uncertainty(const float *c, const float *src, int n, i
                                       int grid_y0, int grid_w, int grid_h, float beta, float *out,
                                       void *stream);
 
+/* ------------------------------------------------------------------ deformation nodes -
+ * The SLAM state the field is carried on (Sec. III-A): nodes i with reference positions x_i,0
+ * and warp rows W_i (r_w, r_z, d_x, d_y, s, 1, 0, 0; the node's position at t is W_i(x_i,0))
+ * and uncertainties sigma_i^2.
+ *
+ * emdq_node_track (Eq. 5, App. A, Eq. 9): for every node, p = W_i,t-1(x_i,0); dW = the Eqs. 2-3
+ * blend at p of the t-1 -> t fit (q, c, src as emdq_field takes them; src in frame t-1);
+ * W_i,t = f(W_i,t-1, dW), the warp with s_new q_new(x) = ds dq(s_old q_old(x)) (App. A);
+ * sigma_i,t^2 = ds^2 sigma_i,t-1^2 + min over the inliers of exp(beta |p - x_j|^2) (Eqs. 9, 8).
+ * A node where the field has no weight keeps its warp and gets sigma^2 = +inf.
+ *   x0        device, nn x 2 float (8-byte aligned); w_old, w_new: nn x 8 float; s2_*: nn float
+ *   alpha, beta > 0 (emdq_alpha_for_frame, emdq_beta_for_frame)
+ *
+ * emdq_node_merge (Eqs. 12-15): for every node, eta = exp(-gamma |x_t - x_k|^2) with x_t =
+ * W_track(x0), x_k = W_key(x0) (the node at the loop-closing key frame); A = [[st^2, eta st sl],
+ * [eta st sl, sl^2]]; sigma^2 = 1 / sum(A^-1); weights sigma^2 A^-1 [1 1]^T; the merged warp is
+ * the weighted average (DQ normalised by its real part, scale averaged).  Where a weight is
+ * negative the warp and uncertainty of the smaller uncertainty are taken (ties: tracking).
+ *   gamma > 0 (emdq_gamma_for_frame); w_out, s2_out may not alias the inputs
+ */
+EMDQ_API float       emdq_gamma_for_frame(int w, int h);
+EMDQ_API emdq_status emdq_node_track(const float *x0, const float *w_old, const float *s2_old,
+                                     int nn, const float *q, const float *c, const float *src,
+                                     int n, float alpha, float beta, float *w_new, float *s2_new,
+                                     void *stream);
+EMDQ_API emdq_status emdq_node_merge(const float *x0, const float *w_track, const float *s2_track,
+                                     const float *w_loop, const float *s2_loop, const float *w_key,
+                                     int nn, float gamma, float *w_out, float *s2_out,
+                                     void *stream);
+
 /* ------------------------------------------------------------------ mosaic_warp ------
  * Gather warp + capped running-average blend of frame t into the canvas (Sec. III-F,
  * Eqs. 23-24 as read: the paper's printed blend lacks its normalisation and its cap reads

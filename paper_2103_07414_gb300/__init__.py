@@ -17,7 +17,8 @@ import torch
 from ._build import LIB as _LIB_PATH, build  # noqa: F401
 
 __all__ = ['emdq_fit', 'emdq_fit_batch', 'emdq_field', 'emdq_field_batch', 'mosaic_warp',
-           'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'emdq_uncertainty', 'mosaic_insert_reference',
+           'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'emdq_uncertainty', 'node_track', 'node_merge',
+           'mosaic_insert_reference',
            'alpha_for_frame', 'fit_workspace_size', 'field_workspace_size', 'EmdqError',
            'FP32', 'BF16', 'STATUS', 'lib', 'build']
 
@@ -116,6 +117,10 @@ def lib() -> ctypes.CDLL:
             L.emdq_beta_for_frame.restype = F
             L.emdq_beta_for_frame.argtypes = [I, I]
             L.emdq_uncertainty.argtypes = [P, P, I, I, I, I, I, F, P, P]
+            L.emdq_gamma_for_frame.restype = F
+            L.emdq_gamma_for_frame.argtypes = [I, I]
+            L.emdq_node_track.argtypes = [P, P, P, I, P, P, P, I, F, F, P, P, P]
+            L.emdq_node_merge.argtypes = [P, P, P, P, P, P, I, F, P, P, P]
             L.emdq_batch_workspace_size.argtypes = [P, I, I]
             L.emdq_batch_workspace_size.restype = Z
             L.emdq_batch.argtypes = [P, I, ctypes.POINTER(_Params), P, P, P, Z, P]
@@ -387,6 +392,47 @@ def emdq_uncertainty(c: torch.Tensor, src: torch.Tensor, grid, beta: float, *,
     if rc != 0:
         raise EmdqError('emdq_uncertainty', rc)
     return out
+
+
+def gamma_for_frame(w: int, h: int) -> float:
+    return lib().emdq_gamma_for_frame(int(w), int(h))
+
+
+def node_track(x0: torch.Tensor, w_old: torch.Tensor, s2_old: torch.Tensor, q: torch.Tensor,
+               c: torch.Tensor, src: torch.Tensor, alpha: float, beta: float, stream=None):
+    """Eq. 5 + App. A + Eq. 9 for nn nodes: returns (w_new [nn, 8], s2_new [nn])."""
+    nn, n = x0.shape[0], c.shape[0]
+    _check(x0, 'x0', torch.float32, (nn, 2))
+    _check(w_old, 'w_old', torch.float32, (nn, 8))
+    _check(s2_old, 's2_old', torch.float32, (nn,))
+    _check(q, 'q', torch.float32, (n, 8))
+    _check(c, 'c', torch.float32, (n,))
+    _check(src, 'src', torch.float32, (n, 2))
+    w_new = torch.empty_like(w_old)
+    s2_new = torch.empty_like(s2_old)
+    rc = lib().emdq_node_track(_ptr(x0), _ptr(w_old), _ptr(s2_old), nn, _ptr(q), _ptr(c), _ptr(src),
+                               n, float(alpha), float(beta), _ptr(w_new), _ptr(s2_new), _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_node_track', rc)
+    return w_new, s2_new
+
+
+def node_merge(x0: torch.Tensor, w_track: torch.Tensor, s2_track: torch.Tensor, w_loop: torch.Tensor,
+               s2_loop: torch.Tensor, w_key: torch.Tensor, gamma: float, stream=None):
+    """Eqs. 12-15 for nn nodes: returns (w_out [nn, 8], s2_out [nn])."""
+    nn = x0.shape[0]
+    _check(x0, 'x0', torch.float32, (nn, 2))
+    for name, t, shape in (('w_track', w_track, (nn, 8)), ('w_loop', w_loop, (nn, 8)),
+                           ('w_key', w_key, (nn, 8)), ('s2_track', s2_track, (nn,)),
+                           ('s2_loop', s2_loop, (nn,))):
+        _check(t, name, torch.float32, shape)
+    w_out = torch.empty_like(w_track)
+    s2_out = torch.empty_like(s2_track)
+    rc = lib().emdq_node_merge(_ptr(x0), _ptr(w_track), _ptr(s2_track), _ptr(w_loop), _ptr(s2_loop),
+                               _ptr(w_key), nn, float(gamma), _ptr(w_out), _ptr(s2_out), _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_node_merge', rc)
+    return w_out, s2_out
 
 
 def _frame_args(frame: torch.Tensor):

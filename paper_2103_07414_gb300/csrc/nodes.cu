@@ -1,0 +1,211 @@
+// Deformation-node tracking and merging (Sec. III-A/C, App. A, Eqs. 5, 8, 9, 12-15).
+//
+// emdq_node_track: one warp per node.  The node's position at t-1, p = W_i,t-1(x_i,0); the
+// lanes sum the Eqs. 2-3 blend of the t-1 -> t EMDQ warps at p (FP32 weights c_j
+// exp(-alpha |p - x_j|^2)) and the nearest inlier's squared distance (Eq. 8); lane 0 composes
+// W_i,t = f(W_i,t-1, dW) -- scale ds s_old, rotation by the product of the two half-angle unit
+// complex numbers, translation dR t_old + dt / s_old (App. A's requirement s_new q_new(x) =
+// ds dq(s_old q_old(x))) -- and propagates sigma^2 = ds^2 sigma_old^2 + exp(beta d^2) (Eq. 9).
+// emdq_node_merge: one thread per node, the EKF merge of Eqs. 12-15 in closed form for the
+// 2 x 2 covariance.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace emdq {
+
+// planar DQ row (r_w, r_z, d_x, d_y) with a unit real part: translation t = 2 (d_x c - d_y s,
+// d_x s + d_y c) for r = (c, s)
+struct Sim {
+    float c, s;      // half-angle unit complex number (r_w, r_z)
+    float tx, ty;    // translation (inside the scale)
+    float sc;        // scale
+};
+
+__device__ __forceinline__ Sim sim_from_row(float rw, float rz, float dx, float dy, float sc)
+{
+    const float nr = rsqrtf(rw * rw + rz * rz);
+    Sim m;
+    m.c = rw * nr;
+    m.s = rz * nr;
+    const float ux = dx * nr, uy = dy * nr;
+    m.tx = 2.f * (ux * m.c - uy * m.s);
+    m.ty = 2.f * (ux * m.s + uy * m.c);
+    m.sc = sc;
+    return m;
+}
+
+__device__ __forceinline__ void row_from_sim(const Sim &m, float *row)
+{
+    float c = m.c, s = m.s;
+    if (c < 0.f) {
+        c = -c;
+        s = -s;
+    }
+    row[0] = c;
+    row[1] = s;
+    row[2] = 0.5f * (m.tx * c + m.ty * s);
+    row[3] = 0.5f * (-m.tx * s + m.ty * c);
+    row[4] = m.sc;
+    row[5] = 1.f;
+    row[6] = 0.f;
+    row[7] = 0.f;
+}
+
+// x -> s (R x + t); R from the half-angle number (cos th = c^2 - s^2, sin th = 2 c s)
+__device__ __forceinline__ float2 sim_apply(const Sim &m, float x, float y)
+{
+    const float ct = m.c * m.c - m.s * m.s, st = 2.f * m.c * m.s;
+    return make_float2(m.sc * (ct * x - st * y + m.tx), m.sc * (st * x + ct * y + m.ty));
+}
+
+constexpr int kNodeWarps = 8;
+
+__global__ void __launch_bounds__(32 * kNodeWarps) node_track_kernel(
+    const float2 *__restrict__ x0, const float *__restrict__ w_old, const float *__restrict__ s2_old,
+    int nn, const float *__restrict__ q, const float *__restrict__ c, const float2 *__restrict__ src,
+    int n, float alpha, float beta, float *__restrict__ w_new, float *__restrict__ s2_new)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kNodeWarps + (threadIdx.x >> 5);
+    if (i >= nn) return;
+    const float *wo = w_old + 8 * (size_t)i;
+    const Sim mo = sim_from_row(wo[0], wo[1], wo[2], wo[3], wo[4]);
+    const float2 x = x0[i];
+    const float2 p = sim_apply(mo, x.x, x.y);
+    float sw = 0.f, ss = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, dmin = INFINITY;
+    for (int j = lane; j < n; j += 32) {
+        const float cj = c[j];
+        const float2 xj = src[j];
+        const float dx = xj.x - p.x, dy = xj.y - p.y, d2 = dx * dx + dy * dy;
+        const float w = cj * expf(-alpha * d2);
+        const float4 qj = *reinterpret_cast<const float4 *>(q + 8 * (size_t)j);
+        const float sj = q[8 * (size_t)j + 4];
+        sw += w;
+        ss = fmaf(w, sj, ss);
+        s0 = fmaf(w, qj.x, s0);
+        s1 = fmaf(w, qj.y, s1);
+        s2 = fmaf(w, qj.z, s2);
+        s3 = fmaf(w, qj.w, s3);
+        if (cj > 0.f) dmin = fminf(dmin, d2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sw += __shfl_xor_sync(0xffffffffu, sw, o);
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+        dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+    }
+    if (lane != 0) return;
+    float *wn = w_new + 8 * (size_t)i;
+    if (!(sw > 0.f) || !isfinite(sw)) {
+        for (int k = 0; k < 8; ++k) wn[k] = wo[k];
+        s2_new[i] = INFINITY;
+        return;
+    }
+    const Sim md = sim_from_row(s0, s1, s2, s3, ss / sw);
+    // App. A: rotation dth + th_old (half-angle numbers multiply), translation dR t_old + dt / s_old
+    Sim mn;
+    mn.c = md.c * mo.c - md.s * mo.s;
+    mn.s = md.c * mo.s + md.s * mo.c;
+    const float ct = md.c * md.c - md.s * md.s, st = 2.f * md.c * md.s;
+    mn.tx = ct * mo.tx - st * mo.ty + md.tx / mo.sc;
+    mn.ty = st * mo.tx + ct * mo.ty + md.ty / mo.sc;
+    mn.sc = md.sc * mo.sc;
+    row_from_sim(mn, wn);
+    s2_new[i] = md.sc * md.sc * s2_old[i] + expf(beta * dmin);
+}
+
+__global__ void node_merge_kernel(const float2 *__restrict__ x0, const float *__restrict__ w_track,
+                                  const float *__restrict__ s2_track,
+                                  const float *__restrict__ w_loop,
+                                  const float *__restrict__ s2_loop, const float *__restrict__ w_key,
+                                  int nn, float gamma, float *__restrict__ w_out,
+                                  float *__restrict__ s2_out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    const float *wt = w_track + 8 * (size_t)i, *wl = w_loop + 8 * (size_t)i,
+                *wk = w_key + 8 * (size_t)i;
+    const float2 x = x0[i];
+    const Sim mt = sim_from_row(wt[0], wt[1], wt[2], wt[3], wt[4]);
+    const Sim mk = sim_from_row(wk[0], wk[1], wk[2], wk[3], wk[4]);
+    const float2 xt = sim_apply(mt, x.x, x.y), xk = sim_apply(mk, x.x, x.y);
+    const float ddx = xt.x - xk.x, ddy = xt.y - xk.y;
+    const float eta = expf(-gamma * (ddx * ddx + ddy * ddy));      // Eq. 13
+    const float vt = s2_track[i], vl = s2_loop[i];
+    const float a01 = eta * sqrtf(vt) * sqrtf(vl);                  // Eq. 12
+    // A^-1 [1 1]^T = (vl - a01, vt - a01) / det; sum(A^-1) = (vt + vl - 2 a01) / det
+    const float den = vt + vl - 2.f * a01;
+    const float w0 = (vl - a01) / den, w1 = (vt - a01) / den;         // Eq. 15
+    const float det = vt * vl - a01 * a01;
+    const float sm = det / den;                                        // Eq. 14
+    float *wo = w_out + 8 * (size_t)i;
+    if (!(w0 >= 0.f) || !(w1 >= 0.f) || !isfinite(sm) || !(det > 0.f)) {
+        const bool t = vt <= vl;
+        const float *pick = t ? wt : wl;
+        for (int k = 0; k < 8; ++k) wo[k] = pick[k];
+        s2_out[i] = t ? vt : vl;
+        return;
+    }
+    const float nt = rsqrtf(wt[0] * wt[0] + wt[1] * wt[1]), nl = rsqrtf(wl[0] * wl[0] + wl[1] * wl[1]);
+    float qv[4];
+    for (int k = 0; k < 4; ++k) qv[k] = w0 * wt[k] * nt + w1 * wl[k] * nl;
+    const float nq = rsqrtf(qv[0] * qv[0] + qv[1] * qv[1]);
+    for (int k = 0; k < 4; ++k) wo[k] = qv[k] * nq;
+    wo[4] = w0 * wt[4] + w1 * wl[4];
+    wo[5] = 1.f;
+    wo[6] = 0.f;
+    wo[7] = 0.f;
+    s2_out[i] = sm;
+}
+
+}  // namespace emdq
+
+using namespace emdq;
+using namespace emdq_host;
+
+extern "C" float emdq_gamma_for_frame(int w, int h)
+{
+    // Sec. III-G: gamma = 5e-3 / s^2 (Eq. 13), the resolution scale of alpha and beta
+    const double s = (w / 480.0 + h / 270.0) / 2.0;
+    return static_cast<float>(5e-3 / (s * s));
+}
+
+extern "C" emdq_status emdq_node_track(const float *x0, const float *w_old, const float *s2_old,
+                                       int nn, const float *q, const float *c, const float *src,
+                                       int n, float alpha, float beta, float *w_new,
+                                       float *s2_new, void *stream)
+{
+    if (nn < 0 || n < 0 || !(alpha > 0.f) || !(beta > 0.f) || !std::isfinite(alpha) ||
+        !std::isfinite(beta))
+        return EMDQ_EINVAL;
+    if (nn == 0) return EMDQ_OK;
+    if (!x0 || !w_old || !s2_old || !w_new || !s2_new || !aligned(x0, 8) ||
+        (n > 0 && (!q || !c || !src || !aligned(q, 16) || !aligned(src, 8))))
+        return EMDQ_EINVAL;
+    node_track_kernel<<<(nn + kNodeWarps - 1) / kNodeWarps, 32 * kNodeWarps, 0,
+                        static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const float2 *>(x0), w_old, s2_old, nn, q, c,
+        reinterpret_cast<const float2 *>(src), n, alpha, beta, w_new, s2_new);
+    return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
+}
+
+extern "C" emdq_status emdq_node_merge(const float *x0, const float *w_track,
+                                       const float *s2_track, const float *w_loop,
+                                       const float *s2_loop, const float *w_key, int nn,
+                                       float gamma, float *w_out, float *s2_out, void *stream)
+{
+    if (nn < 0 || !(gamma > 0.f) || !std::isfinite(gamma)) return EMDQ_EINVAL;
+    if (nn == 0) return EMDQ_OK;
+    if (!x0 || !w_track || !s2_track || !w_loop || !s2_loop || !w_key || !w_out || !s2_out ||
+        !aligned(x0, 8))
+        return EMDQ_EINVAL;
+    node_merge_kernel<<<(nn + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const float2 *>(x0), w_track, s2_track, w_loop, s2_loop, w_key, nn, gamma,
+        w_out, s2_out);
+    return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
+}
