@@ -67,6 +67,7 @@ def lib():
             L.orc_compose.argtypes = [P, P, P]
             L.orc_node_track.argtypes = [P, P, P, I, P, P, P, I, D, D, P, P, I]
             L.orc_node_merge.argtypes = [P, P, P, P, P, P, I, D, P, P]
+            L.orc_arap_smooth.argtypes = [P, P, P, I, D, I, P, P]
             L.orc_gamma_for_frame.restype = D
             L.orc_gamma_for_frame.argtypes = [I, I]
             L.orc_uncertainty_points.argtypes = [P, P, I, P, I, D, P, I]
@@ -204,6 +205,18 @@ def node_merge(x0, w_track, s2_track, w_loop, s2_loop, w_key, gamma: float):
                               _p(w_key), nn, float(gamma), _p(w_out), _p(s2_out))
     assert rc == OK, rc
     return w_out, s2_out
+
+
+def arap_smooth(x0, w_merge, s2, alpha: float, max_iters: int = 5):
+    """Sec. III-D: ARAP-smoothed node warps [nn, 8] and the cost of every iteration run."""
+    x0, w_merge, s2 = _d(x0), _d(w_merge), _d(s2)
+    nn = s2.shape[0]
+    w_out = np.empty((nn, 8))
+    costs = np.full(max(1, max_iters), np.nan)
+    rc = lib().orc_arap_smooth(_p(x0), _p(w_merge), _p(s2), nn, float(alpha), int(max_iters),
+                               _p(w_out), _p(costs))
+    assert rc == OK, rc
+    return w_out, costs[:max_iters]
 
 
 def mstep(src, dst, p, alpha: float):

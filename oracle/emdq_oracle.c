@@ -17,6 +17,8 @@
  *   Eq. 5, App. A, Eq. 9      node tracking: W_i,t = f(W_i,t-1, dW_i) with f the composition
  *                             s_new q_new(x) = ds dq(s_old q_old(x)); sigma^2 propagation
  *   Eqs. 12-15                EKF merge of the tracking and loop-closing node warps
+ *   Sec. III-D, Eqs. 21-22    ARAP smoothing of the node warps (the ARAP warp of a node is the
+ *                             weighted similarity fit of Eqs. 16-20 over the nodes with p = 1)
  *
  * Readings (the paper is silent, garbled or delegates to its EMDQ reference)
  *   - Eq. 3 blends q without normalising it; a blended DQ is normalised by the norm of its
@@ -363,6 +365,73 @@ int orc_node_merge(const double *x0, const double *w_track, const double *s2_tra
         wo[6] = wo[7] = 0.0;
         s2_out[i] = sm;
     }
+    return ORC_OK;
+}
+
+/* Average of two warp rows with weights a, b (DQ normalised by its real part, scale averaged),
+ * the reading of "weighted average" of warps used by Eqs. 15 and 22. */
+static void average_rows(const double *wa, double a, const double *wb, double b, double *out)
+{
+    double na = sqrt(wa[0] * wa[0] + wa[1] * wa[1]), nb = sqrt(wb[0] * wb[0] + wb[1] * wb[1]);
+    double q[4];
+    for (int k = 0; k < 4; ++k) q[k] = a * wa[k] / na + b * wb[k] / nb;
+    double nq = sqrt(q[0] * q[0] + q[1] * q[1]);
+    for (int k = 0; k < 4; ++k) out[k] = q[k] / nq;
+    out[4] = (a * wa[4] + b * wb[4]) / (a + b);
+    out[5] = 1.0;
+    out[6] = out[7] = 0.0;
+}
+
+static void apply_row(const double *w, double x, double y, double out[2])
+{
+    double nr = sqrt(w[0] * w[0] + w[1] * w[1]);
+    double q[4] = {w[0] / nr, w[1] / nr, w[2] / nr, w[3] / nr};
+    orc_apply_warp(w[4], q, x, y, out);
+}
+
+/* Sec. III-D: ARAP smoothing of the merged node warps.  Iteration k: the nodes' positions
+ * x_t = W^{k-1}(x_0) (W^0 = W_merge); the ARAP warp of every node from its neighbours'
+ * displacements (Eqs. ARAP1-3 = the weighted similarity fit of the M-step with p = 1 and
+ * weights exp(-alpha |x_i,0 - x_j,0|^2)); W^k = (W_merge + lambda W_ARAP) / (1 + lambda)
+ * (Eq. 22), lambda = (1 + sigma_i^2) / (1 + 100); the cost of Eq. 21 summed over the nodes,
+ * sum |W_merge(x_0) - W^k(x_0)|^2 + lambda |W_ARAP(x_0) - W^k(x_0)|^2.  Stops after max_iters
+ * iterations or when the cost increases (keeping the previous warps). */
+int orc_arap_smooth(const double *x0, const double *w_merge, const double *s2, int nn,
+                    double alpha, int max_iters, double *w_out, double *costs)
+{
+    if (nn < 1 || !x0 || !w_merge || !s2 || !w_out || max_iters < 0) return ORC_EINVAL;
+    double *xt = malloc(sizeof(double) * 2 * (size_t)nn);
+    double *ones = malloc(sizeof(double) * (size_t)nn);
+    double *sc = malloc(sizeof(double) * (size_t)nn), *th = malloc(sizeof(double) * (size_t)nn);
+    double *t = malloc(sizeof(double) * 2 * (size_t)nn), *wa = malloc(sizeof(double) * 8 * (size_t)nn);
+    double *wk = malloc(sizeof(double) * 8 * (size_t)nn);
+    if (!xt || !ones || !sc || !th || !t || !wa || !wk) {
+        free(xt); free(ones); free(sc); free(th); free(t); free(wa); free(wk);
+        return ORC_EINVAL;
+    }
+    memcpy(w_out, w_merge, sizeof(double) * 8 * (size_t)nn);
+    for (int i = 0; i < nn; ++i) ones[i] = 1.0;
+    double prev = INFINITY;
+    for (int k = 1; k <= max_iters; ++k) {
+        for (int i = 0; i < nn; ++i) apply_row(w_out + 8 * (size_t)i, x0[2 * i], x0[2 * i + 1], xt + 2 * i);
+        orc_mstep(x0, xt, ones, nn, alpha, sc, th, t, wa);
+        double cost = 0.0;
+        for (int i = 0; i < nn; ++i) {
+            const double lam = (1.0 + s2[i]) / (1.0 + 100.0);
+            average_rows(w_merge + 8 * (size_t)i, 1.0, wa + 8 * (size_t)i, lam, wk + 8 * (size_t)i);
+            double pm[2], pa[2], pk[2];
+            apply_row(w_merge + 8 * (size_t)i, x0[2 * i], x0[2 * i + 1], pm);
+            apply_row(wa + 8 * (size_t)i, x0[2 * i], x0[2 * i + 1], pa);
+            apply_row(wk + 8 * (size_t)i, x0[2 * i], x0[2 * i + 1], pk);
+            cost += (pm[0] - pk[0]) * (pm[0] - pk[0]) + (pm[1] - pk[1]) * (pm[1] - pk[1]) +
+                    lam * ((pa[0] - pk[0]) * (pa[0] - pk[0]) + (pa[1] - pk[1]) * (pa[1] - pk[1]));
+        }
+        if (costs) costs[k - 1] = cost;
+        if (cost > prev) break;
+        prev = cost;
+        memcpy(w_out, wk, sizeof(double) * 8 * (size_t)nn);
+    }
+    free(xt); free(ones); free(sc); free(th); free(t); free(wa); free(wk);
     return ORC_OK;
 }
 

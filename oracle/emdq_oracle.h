@@ -76,6 +76,10 @@ int orc_node_track(const double *x0, const double *w_old, const double *s2_old, 
 int orc_node_merge(const double *x0, const double *w_track, const double *s2_track,
                    const double *w_loop, const double *s2_loop, const double *w_key, int nn,
                    double gamma, double *w_out, double *s2_out);
+/* Sec. III-D, Eqs. 21-22: ARAP smoothing of the node warps (see the .c); costs (max_iters,
+ * may be NULL) receives the cost of every iteration run. */
+int orc_arap_smooth(const double *x0, const double *w_merge, const double *s2, int nn,
+                    double alpha, int max_iters, double *w_out, double *costs);
 /* Sec. III-G: gamma = 5e-3 / s^2 (Eq. 13). */
 double orc_gamma_for_frame(int w, int h);
 int orc_mstep(const double *src, const double *dst, const double *p, int n, double alpha,

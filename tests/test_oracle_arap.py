@@ -1,0 +1,73 @@
+"""Pins of the oracle's ARAP smoothing of node warps (Sec. III-D, Eqs. 21-22)."""
+import math
+
+import numpy as np
+import pytest
+
+
+def _row(orc, s, th, tx, ty):
+    r = np.zeros(8)
+    r[:4] = orc.dq_from_rt(th, tx, ty)
+    r[4], r[5] = s, 1.0
+    return r
+
+
+def _pos(orc, w, x0):
+    return np.array([orc.apply_warp(r[4], r[:4] / math.hypot(r[0], r[1]), x[0], x[1])
+                     for r, x in zip(w, x0)])
+
+
+def _lattice(step=40.0, w=640, h=480):
+    xs, ys = np.meshgrid(np.arange(0, w, step), np.arange(0, h, step))
+    return np.stack([xs.ravel(), ys.ravel()], 1).astype(np.float64)
+
+
+def test_a_common_similarity_is_a_fixed_point(orc):
+    x0 = _lattice()
+    S = _row(orc, 1.05, 0.08, 12.0, -7.0)
+    w = np.tile(S, (len(x0), 1))
+    out, costs = orc.arap_smooth(x0, w, np.ones(len(x0)), orc.alpha_for_frame(640, 480))
+    np.testing.assert_allclose(_pos(orc, out, x0), _pos(orc, w, x0), atol=1e-8)
+    assert costs[0] == pytest.approx(0.0, abs=1e-12)
+
+
+def test_no_iteration_returns_the_merged_warps(orc):
+    x0 = _lattice()
+    rng = np.random.default_rng(0)
+    w = np.array([_row(orc, 1.0, 0.0, *rng.normal(0, 3, 2)) for _ in x0])
+    out, _ = orc.arap_smooth(x0, w, np.ones(len(x0)), 1e-4, max_iters=0)
+    np.testing.assert_array_equal(out, w)
+
+
+def test_first_iteration_is_eq22_with_the_neighbourhood_fit(orc):
+    """One iteration: lambda = (1 + sigma^2)/101 weights the ARAP warp, which is the weighted
+    similarity fit over the nodes (the M-step with p = 1) of x_0 -> W_merge(x_0)."""
+    x0 = _lattice()
+    rng = np.random.default_rng(1)
+    w = np.array([_row(orc, rng.uniform(0.98, 1.02), rng.normal(0, 0.02), *rng.normal(0, 3, 2)) for _ in x0])
+    s2 = np.full(len(x0), 100.0)                          # lambda = 1: the plain average
+    alpha = orc.alpha_for_frame(640, 480)
+    out, _ = orc.arap_smooth(x0, w, s2, alpha, max_iters=1)
+    fit = orc.mstep(x0, _pos(orc, w, x0), np.ones(len(x0)), alpha)['q8']
+    q = w[:, :4] / np.hypot(w[:, 0], w[:, 1])[:, None] + fit[:, :4] / np.hypot(fit[:, 0], fit[:, 1])[:, None]
+    np.testing.assert_allclose(out[:, :4], q / np.hypot(q[:, 0], q[:, 1])[:, None], atol=1e-12)
+    np.testing.assert_allclose(out[:, 4], 0.5 * (w[:, 4] + fit[:, 4]), atol=1e-12)
+
+
+def test_costs_never_increase_and_noise_is_smoothed(orc):
+    """A smooth similarity plus independent per-node jitter: the iterations' costs do not
+    increase up to the stop, and the smoothed nodes lie closer to the smooth motion."""
+    x0 = _lattice(30.0)
+    rng = np.random.default_rng(2)
+    S = _row(orc, 1.03, 0.05, 8.0, 4.0)
+    w = np.array([_row(orc, 1.03 * rng.uniform(0.99, 1.01), 0.05 + rng.normal(0, 0.01), 8.0 + rng.normal(0, 2),
+                       4.0 + rng.normal(0, 2)) for _ in x0])
+    s2 = rng.uniform(1, 50, len(x0))
+    out, costs = orc.arap_smooth(x0, w, s2, orc.alpha_for_frame(640, 480))
+    ran = costs[~np.isnan(costs)]
+    kept = ran if len(ran) < 2 or ran[-1] <= ran[-2] else ran[:-1]
+    assert (np.diff(kept) <= 1e-9 * kept[0]).all()
+    truth = _pos(orc, np.tile(S, (len(x0), 1)), x0)
+    before = np.abs(_pos(orc, w, x0) - truth).mean()
+    after = np.abs(_pos(orc, out, x0) - truth).mean()
+    assert after < 0.9 * before
