@@ -651,6 +651,20 @@ def run_gpu(args, ws, rank, local):
             n_ms.append(a.elapsed_time(b) / len(ks0))
         unc['node_track'] = dict(call='emdq_node_track (Eq. 5, App. A, Eq. 9), one call per frame',
                                  nodes=nn, ms_per_frame=float(np.median(n_ms)))
+        # ARAP smoothing (Sec. III-D, 5 iterations) of the tracked lattice
+        w_t, s2_t = node_pass()
+        arap_ws = torch.empty(emdq.lib().emdq_arap_workspace_size(nn), dtype=torch.uint8, device=dev)
+        emdq.arap_smooth(x0n, w_t, s2_t, alpha_n, 5, workspace=arap_ws)
+        a_ms = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            emdq.arap_smooth(x0n, w_t, s2_t, alpha_n, 5, workspace=arap_ws)
+            b.record(stream)
+            b.synchronize()
+            a_ms.append(a.elapsed_time(b))
+        unc['arap_smooth'] = dict(call='emdq_arap_smooth (Eqs. 21-22), 5 iterations', nodes=nn,
+                                  ms_per_call=float(np.median(a_ms)))
 
     # end to end through the public API from pinned host buffers: per frame the H2D copy of
     # the frame and its matches, the three calls, the D2H of the fit record and weights

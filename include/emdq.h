@@ -299,6 +299,22 @@ EMDQ_API emdq_status emdq_node_merge(const float *x0, const float *w_track, cons
                                      int nn, float gamma, float *w_out, float *s2_out,
                                      void *stream);
 
+/* emdq_arap_smooth (Sec. III-D, Eqs. 21-22): ARAP smoothing of the merged node warps.  At
+ * most max_iters iterations (the paper uses 5) of: positions x_t = W(x_0); the ARAP warp of every
+ * node, the similarity fit of Eqs. ARAP1-3 to its neighbours' displacements x_j,0 -> x_j,t with
+ * weights exp(-alpha |x_i,0 - x_j,0|^2) (emdq_fit's step-0 M-step); W = (W_merge + lambda W_ARAP)
+ * / (1 + lambda) with lambda = (1 + sigma_i^2) / 101; stopping, with the previous warps kept,
+ * when the summed cost of Eq. 21 rises.  Runs on the stream without host synchronisation.
+ *   x0        device, nn x 2 float (8-byte aligned), 3 <= nn <= emdq_fit_max_n()
+ *   w_merge   device, nn x 8 float warp rows; s2: device, nn float merged uncertainties
+ *   w_out     device, nn x 8 float (16-byte aligned; written), not aliasing w_merge
+ *   workspace device, emdq_arap_workspace_size(nn) bytes, 256-byte aligned
+ */
+EMDQ_API size_t      emdq_arap_workspace_size(int nn);
+EMDQ_API emdq_status emdq_arap_smooth(const float *x0, const float *w_merge, const float *s2,
+                                      int nn, float alpha, int max_iters, float *w_out,
+                                      void *workspace, size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------------------------ mosaic_warp ------
  * Gather warp + capped running-average blend of frame t into the canvas (Sec. III-F,
  * Eqs. 23-24 as read: the paper's printed blend lacks its normalisation and its cap reads

@@ -17,7 +17,7 @@ import torch
 from ._build import LIB as _LIB_PATH, build  # noqa: F401
 
 __all__ = ['emdq_fit', 'emdq_fit_batch', 'emdq_field', 'emdq_field_batch', 'mosaic_warp',
-           'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'emdq_uncertainty', 'node_track', 'node_merge',
+           'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'emdq_uncertainty', 'node_track', 'node_merge', 'arap_smooth',
            'mosaic_insert_reference',
            'alpha_for_frame', 'fit_workspace_size', 'field_workspace_size', 'EmdqError',
            'FP32', 'BF16', 'STATUS', 'lib', 'build']
@@ -121,6 +121,9 @@ def lib() -> ctypes.CDLL:
             L.emdq_gamma_for_frame.argtypes = [I, I]
             L.emdq_node_track.argtypes = [P, P, P, I, P, P, P, I, F, F, P, P, P]
             L.emdq_node_merge.argtypes = [P, P, P, P, P, P, I, F, P, P, P]
+            L.emdq_arap_workspace_size.argtypes = [I]
+            L.emdq_arap_workspace_size.restype = Z
+            L.emdq_arap_smooth.argtypes = [P, P, P, I, F, I, P, P, Z, P]
             L.emdq_batch_workspace_size.argtypes = [P, I, I]
             L.emdq_batch_workspace_size.restype = Z
             L.emdq_batch.argtypes = [P, I, ctypes.POINTER(_Params), P, P, P, Z, P]
@@ -433,6 +436,25 @@ def node_merge(x0: torch.Tensor, w_track: torch.Tensor, s2_track: torch.Tensor, 
     if rc != 0:
         raise EmdqError('emdq_node_merge', rc)
     return w_out, s2_out
+
+
+def arap_smooth(x0: torch.Tensor, w_merge: torch.Tensor, s2: torch.Tensor, alpha: float,
+                max_iters: int = 5, workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Sec. III-D: ARAP-smoothed node warps [nn, 8] (at most max_iters iterations)."""
+    nn = x0.shape[0]
+    _check(x0, 'x0', torch.float32, (nn, 2))
+    _check(w_merge, 'w_merge', torch.float32, (nn, 8))
+    _check(s2, 's2', torch.float32, (nn,))
+    w_out = torch.empty_like(w_merge)
+    need = lib().emdq_arap_workspace_size(nn)
+    if need == 0:
+        raise EmdqError('emdq_arap_workspace_size', 7)
+    ws = _workspace(need, x0.device, workspace)
+    rc = lib().emdq_arap_smooth(_ptr(x0), _ptr(w_merge), _ptr(s2), nn, float(alpha), int(max_iters),
+                                _ptr(w_out), _ptr(ws), ws.numel(), _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_arap_smooth', rc)
+    return w_out
 
 
 def _frame_args(frame: torch.Tensor):

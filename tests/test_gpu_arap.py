@@ -1,0 +1,70 @@
+"""GPU parity: ARAP smoothing of node warps (Sec. III-D, Eqs. 21-22) against the FP64 oracle
+on node lattices, the fixed point of a common similarity, and argument errors."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope='module')
+def emdq():
+    import paper_2103_07414_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+def _row(orc, s, th, tx, ty):
+    r = np.zeros(8)
+    r[:4] = orc.dq_from_rt(th, tx, ty)
+    r[4], r[5] = s, 1.0
+    return r
+
+
+def _pos(orc, w, x0):
+    return np.array([orc.apply_warp(r[4], r[:4] / math.hypot(r[0], r[1]), x[0], x[1])
+                     for r, x in zip(w, x0)])
+
+
+def _f32(a):
+    return np.float32(a).astype(np.float64)
+
+
+@pytest.mark.parametrize('w,h,step,iters', [(640, 480, 40.0, 1), (640, 480, 40.0, 5), (1280, 1024, 30.0, 5)])
+def test_arap_against_the_oracle(emdq, orc, w, h, step, iters):
+    xs, ys = np.meshgrid(np.arange(0, w, step), np.arange(0, h, step))
+    x0 = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.float64)
+    rng = np.random.default_rng(int(step) + iters)
+    wm = np.array([_row(orc, 1.03 * rng.uniform(0.99, 1.01), 0.05 + rng.normal(0, 0.01),
+                        8.0 + rng.normal(0, 2), 4.0 + rng.normal(0, 2)) for _ in x0])
+    s2 = rng.uniform(1, 50, len(x0))
+    alpha = orc.alpha_for_frame(w, h)
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    got = emdq.arap_smooth(f(x0), f(wm), f(s2), np.float32(alpha), max_iters=iters)
+    torch.cuda.synchronize()
+    want, costs = orc.arap_smooth(_f32(x0), _f32(wm), _f32(s2), float(np.float32(alpha)), iters)
+    dpos = np.abs(_pos(orc, got.cpu().numpy().astype(np.float64), _f32(x0)) - _pos(orc, want, _f32(x0))).max()
+    print(f'{len(x0)} nodes, {iters} iterations: max position difference {dpos:.2e} px')
+    assert dpos <= 2e-3
+
+
+def test_common_similarity_is_kept(emdq, orc):
+    xs, ys = np.meshgrid(np.arange(0, 640, 40.0), np.arange(0, 480, 40.0))
+    x0 = np.stack([xs.ravel(), ys.ravel()], 1)
+    S = _row(orc, 1.05, 0.08, 12.0, -7.0)
+    wm = np.tile(S, (len(x0), 1))
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    got = emdq.arap_smooth(f(x0), f(wm), f(np.ones(len(x0))), np.float32(orc.alpha_for_frame(640, 480)))
+    dpos = np.abs(_pos(orc, got.cpu().numpy().astype(np.float64), x0) - _pos(orc, wm, x0)).max()
+    assert dpos <= 2e-3
+
+
+def test_arap_argument_errors(emdq):
+    z = torch.zeros((2, 2), device='cuda')
+    with pytest.raises(emdq.EmdqError):
+        emdq.arap_smooth(z, torch.zeros((2, 8), device='cuda'), torch.ones(2, device='cuda'), 1e-4)
+    z = torch.zeros((8, 2), device='cuda')
+    with pytest.raises(emdq.EmdqError):
+        emdq.arap_smooth(z, torch.zeros((8, 8), device='cuda'), torch.ones(8, device='cuda'), 0.0)
