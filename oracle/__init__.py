@@ -68,6 +68,8 @@ def lib():
             L.orc_node_track.argtypes = [P, P, P, I, P, P, P, I, D, D, P, P, I]
             L.orc_node_merge.argtypes = [P, P, P, P, P, P, I, D, P, P]
             L.orc_arap_smooth.argtypes = [P, P, P, I, D, I, P, P]
+            L.orc_node_restrict.argtypes = [P, P, I, P, P, I, D, P]
+            L.orc_keyframe_distances.argtypes = [P, P, I, I, P]
             L.orc_gamma_for_frame.restype = D
             L.orc_gamma_for_frame.argtypes = [I, I]
             L.orc_uncertainty_points.argtypes = [P, P, I, P, I, D, P, I]
@@ -217,6 +219,25 @@ def arap_smooth(x0, w_merge, s2, alpha: float, max_iters: int = 5):
                                _p(w_out), _p(costs))
     assert rc == OK, rc
     return w_out, costs[:max_iters]
+
+
+def node_restrict(x, s2, y, s2f, beta: float) -> np.ndarray:
+    """Eq. 11: node uncertainties bounded by the features'."""
+    x, s2, y, s2f = _d(x), _d(s2), _d(y), _d(s2f)
+    out = np.empty(s2.shape[0])
+    rc = lib().orc_node_restrict(_p(x), _p(s2), s2.shape[0], _p(y), _p(s2f), s2f.shape[0],
+                                 float(beta), _p(out))
+    assert rc == OK, rc
+    return out
+
+
+def keyframe_distances(xt, xk) -> np.ndarray:
+    """Eq. 6: (1/N) sum_i |x_i,t - x_i,k| for every key frame k (xk: [nk, nn, 2])."""
+    xt, xk = _d(xt), _d(xk)
+    out = np.empty(xk.shape[0])
+    rc = lib().orc_keyframe_distances(_p(xt), _p(xk), xt.shape[0], xk.shape[0], _p(out))
+    assert rc == OK, rc
+    return out
 
 
 def mstep(src, dst, p, alpha: float):

@@ -17,6 +17,9 @@
  *   Eq. 5, App. A, Eq. 9      node tracking: W_i,t = f(W_i,t-1, dW_i) with f the composition
  *                             s_new q_new(x) = ds dq(s_old q_old(x)); sigma^2 propagation
  *   Eqs. 12-15                EKF merge of the tracking and loop-closing node warps
+ *   Eq. 11                    node uncertainty bounded by the features': sigma_i^2 <=
+ *                             sigma_j,feature^2 + exp(beta d_ij^2) for every feature j
+ *   Eq. 6                     key-frame distance: mean over the nodes of |x_i,t - x_i,k|
  *   Sec. III-D, Eqs. 21-22    ARAP smoothing of the node warps (the ARAP warp of a node is the
  *                             weighted similarity fit of Eqs. 16-20 over the nodes with p = 1)
  *
@@ -432,6 +435,41 @@ int orc_arap_smooth(const double *x0, const double *w_merge, const double *s2, i
         memcpy(w_out, wk, sizeof(double) * 8 * (size_t)nn);
     }
     free(xt); free(ones); free(sc); free(th); free(t); free(wa); free(wk);
+    return ORC_OK;
+}
+
+/* Eq. 11 for every node: sigma_i^2 <- min(sigma_i^2, min_j (sigma_j^2 + exp(beta |x_i - y_j|^2)))
+ * over the features j (positions y_j and uncertainties at the same time as the nodes' x_i). */
+int orc_node_restrict(const double *x, const double *s2, int nn, const double *y,
+                      const double *s2f, int m, double beta, double *s2_out)
+{
+    if (nn < 0 || m < 0 || (nn > 0 && (!x || !s2 || !s2_out)) || (m > 0 && (!y || !s2f)) ||
+        !(beta > 0.0))
+        return ORC_EINVAL;
+    for (int i = 0; i < nn; ++i) {
+        double best = s2[i];
+        for (int j = 0; j < m; ++j) {
+            double dx = x[2 * i] - y[2 * j], dy = x[2 * i + 1] - y[2 * j + 1];
+            double b = s2f[j] + exp(beta * (dx * dx + dy * dy));
+            if (b < best) best = b;
+        }
+        s2_out[i] = best;
+    }
+    return ORC_OK;
+}
+
+/* Eq. 6 for every key frame k: (1/N) sum_i |x_i,t - x_i,k| (xk: nk x nn x 2). */
+int orc_keyframe_distances(const double *xt, const double *xk, int nn, int nk, double *out)
+{
+    if (nn < 1 || nk < 0 || !xt || (nk > 0 && (!xk || !out))) return ORC_EINVAL;
+    for (int k = 0; k < nk; ++k) {
+        double sum = 0.0;
+        for (int i = 0; i < nn; ++i) {
+            const double *p = xk + 2 * ((size_t)k * nn + i);
+            sum += hypot(xt[2 * i] - p[0], xt[2 * i + 1] - p[1]);
+        }
+        out[k] = sum / nn;
+    }
     return ORC_OK;
 }
 

@@ -80,6 +80,11 @@ int orc_node_merge(const double *x0, const double *w_track, const double *s2_tra
  * may be NULL) receives the cost of every iteration run. */
 int orc_arap_smooth(const double *x0, const double *w_merge, const double *s2, int nn,
                     double alpha, int max_iters, double *w_out, double *costs);
+/* Eq. 11: node uncertainties bounded by the features' (see the .c). */
+int orc_node_restrict(const double *x, const double *s2, int nn, const double *y,
+                      const double *s2f, int m, double beta, double *s2_out);
+/* Eq. 6: mean node distance to every key frame (see the .c). */
+int orc_keyframe_distances(const double *xt, const double *xk, int nn, int nk, double *out);
 /* Sec. III-G: gamma = 5e-3 / s^2 (Eq. 13). */
 double orc_gamma_for_frame(int w, int h);
 int orc_mstep(const double *src, const double *dst, const double *p, int n, double alpha,

@@ -146,3 +146,31 @@ def test_merge_special_cases(orc):
     x0, wt, vt, wl, vl, wk = _merge_case(orc, rng)
     wo, so = orc.node_merge(x0, wt, vt, wl, vl, wk, orc.gamma_for_frame(640, 480))
     assert (so <= np.minimum(vt, vl) * (1 + 1e-12)).all()
+
+
+def test_node_restrict_against_brute_force_and_limits(orc):
+    """Eq. 11: the bound min_j (sigma_j^2 + exp(beta d^2)) by numpy over all pairs; a node on a
+    feature is bounded by that feature's uncertainty + 1; no feature leaves sigma^2 unchanged."""
+    rng = np.random.default_rng(11)
+    x = rng.uniform(0, 640, (50, 2))
+    s2 = rng.uniform(1, 400, 50)
+    y = rng.uniform(0, 640, (80, 2))
+    s2f = rng.uniform(0, 5, 80)
+    beta = orc.beta_for_frame(640, 480)
+    got = orc.node_restrict(x, s2, y, s2f, beta)
+    d2 = ((x[:, None, :] - y[None, :, :]) ** 2).sum(-1)
+    with np.errstate(over='ignore'):                  # far pairs: exp overflows to +inf
+        want = np.minimum(s2, (s2f[None, :] + np.exp(beta * d2)).min(1))
+    np.testing.assert_allclose(got, want, rtol=1e-15)
+    on = orc.node_restrict(y[:1], np.array([1e9]), y, s2f, beta)
+    assert on[0] <= s2f[0] + 1.0
+    np.testing.assert_array_equal(orc.node_restrict(x, s2, np.zeros((0, 2)), np.zeros(0), beta), s2)
+
+
+def test_keyframe_distances(orc):
+    """Eq. 6: a key frame equal to the current nodes is at distance 0; a uniform shift by v is at
+    |v|; the mean, not the sum or the maximum."""
+    rng = np.random.default_rng(12)
+    xt = rng.uniform(0, 640, (40, 2))
+    xk = np.stack([xt, xt + [3.0, 4.0], xt + np.where(np.arange(40)[:, None] < 20, [6.0, 8.0], [0.0, 0.0])])
+    np.testing.assert_allclose(orc.keyframe_distances(xt, xk), [0.0, 5.0, 5.0], atol=1e-12)
