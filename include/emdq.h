@@ -299,6 +299,19 @@ EMDQ_API emdq_status emdq_node_merge(const float *x0, const float *w_track, cons
                                      int nn, float gamma, float *w_out, float *s2_out,
                                      void *stream);
 
+/* emdq_node_restrict (Eq. 11): s2_out_i = min(s2_i, min_j (s2f_j + exp(beta |x_i - y_j|^2))), the
+ * node uncertainties bounded by the features' (node positions x and feature positions y at the
+ * same time; nn x 2 and m x 2 float, 8-byte aligned).
+ * emdq_keyframe_distances (Eq. 6): out_k = (1/N) sum_i |xt_i - xk_k,i| for nk key frames (xk:
+ * nk x nn x 2 float, the nodes' positions at each key frame); the caller adds frame t as a key
+ * frame when the smallest of them exceeds its threshold H.
+ */
+EMDQ_API emdq_status emdq_node_restrict(const float *x, const float *s2, int nn, const float *y,
+                                        const float *s2f, int m, float beta, float *s2_out,
+                                        void *stream);
+EMDQ_API emdq_status emdq_keyframe_distances(const float *xt, const float *xk, int nn, int nk,
+                                             float *out, void *stream);
+
 /* emdq_arap_smooth (Sec. III-D, Eqs. 21-22): ARAP smoothing of the merged node warps.  At
  * most max_iters iterations (the paper uses 5) of: positions x_t = W(x_0); the ARAP warp of every
  * node, the similarity fit of Eqs. ARAP1-3 to its neighbours' displacements x_j,0 -> x_j,t with

@@ -17,7 +17,8 @@ import torch
 from ._build import LIB as _LIB_PATH, build  # noqa: F401
 
 __all__ = ['emdq_fit', 'emdq_fit_batch', 'emdq_field', 'emdq_field_batch', 'mosaic_warp',
-           'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'emdq_uncertainty', 'node_track', 'node_merge', 'arap_smooth',
+           'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'emdq_uncertainty', 'node_track', 'node_merge', 'node_restrict',
+           'keyframe_distances', 'arap_smooth',
            'mosaic_insert_reference',
            'alpha_for_frame', 'fit_workspace_size', 'field_workspace_size', 'EmdqError',
            'FP32', 'BF16', 'STATUS', 'lib', 'build']
@@ -124,6 +125,8 @@ def lib() -> ctypes.CDLL:
             L.emdq_arap_workspace_size.argtypes = [I]
             L.emdq_arap_workspace_size.restype = Z
             L.emdq_arap_smooth.argtypes = [P, P, P, I, F, I, P, P, Z, P]
+            L.emdq_node_restrict.argtypes = [P, P, I, P, P, I, F, P, P]
+            L.emdq_keyframe_distances.argtypes = [P, P, I, I, P, P]
             L.emdq_batch_workspace_size.argtypes = [P, I, I]
             L.emdq_batch_workspace_size.restype = Z
             L.emdq_batch.argtypes = [P, I, ctypes.POINTER(_Params), P, P, P, Z, P]
@@ -436,6 +439,35 @@ def node_merge(x0: torch.Tensor, w_track: torch.Tensor, s2_track: torch.Tensor, 
     if rc != 0:
         raise EmdqError('emdq_node_merge', rc)
     return w_out, s2_out
+
+
+def node_restrict(x: torch.Tensor, s2: torch.Tensor, y: torch.Tensor, s2f: torch.Tensor,
+                  beta: float, stream=None) -> torch.Tensor:
+    """Eq. 11: node uncertainties bounded by the features' (positions at the same time)."""
+    nn, m = x.shape[0], y.shape[0]
+    _check(x, 'x', torch.float32, (nn, 2))
+    _check(s2, 's2', torch.float32, (nn,))
+    _check(y, 'y', torch.float32, (m, 2))
+    _check(s2f, 's2f', torch.float32, (m,))
+    out = torch.empty_like(s2)
+    rc = lib().emdq_node_restrict(_ptr(x), _ptr(s2), nn, _ptr(y), _ptr(s2f), m, float(beta), _ptr(out),
+                                  _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_node_restrict', rc)
+    return out
+
+
+def keyframe_distances(xt: torch.Tensor, xk: torch.Tensor, stream=None) -> torch.Tensor:
+    """Eq. 6: mean node distance [nk] to every key frame (xk: [nk, nn, 2])."""
+    nn = xt.shape[0]
+    _check(xt, 'xt', torch.float32, (nn, 2))
+    nk = xk.shape[0]
+    _check(xk, 'xk', torch.float32, (nk, nn, 2))
+    out = torch.empty(nk, dtype=torch.float32, device=xt.device)
+    rc = lib().emdq_keyframe_distances(_ptr(xt), _ptr(xk), nn, nk, _ptr(out), _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_keyframe_distances', rc)
+    return out
 
 
 def arap_smooth(x0: torch.Tensor, w_merge: torch.Tensor, s2: torch.Tensor, alpha: float,

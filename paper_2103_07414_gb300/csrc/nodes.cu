@@ -8,6 +8,8 @@
 // ds dq(s_old q_old(x))) -- and propagates sigma^2 = ds^2 sigma_old^2 + exp(beta d^2) (Eq. 9).
 // emdq_node_merge: one thread per node, the EKF merge of Eqs. 12-15 in closed form for the
 // 2 x 2 covariance.
+// emdq_node_restrict: one warp per node, the bound of Eq. 11 by every feature.
+// emdq_keyframe_distances: one block per key frame, Eq. 6's mean node distance.
 #include <cmath>
 
 #include "common.cuh"
@@ -163,6 +165,45 @@ __global__ void node_merge_kernel(const float2 *__restrict__ x0, const float *__
     s2_out[i] = sm;
 }
 
+__global__ void __launch_bounds__(32 * kNodeWarps) node_restrict_kernel(
+    const float2 *__restrict__ x, const float *__restrict__ s2, int nn, const float2 *__restrict__ y,
+    const float *__restrict__ s2f, int m, float beta, float *__restrict__ s2_out)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kNodeWarps + (threadIdx.x >> 5);
+    if (i >= nn) return;
+    const float2 xi = x[i];
+    float best = INFINITY;
+    for (int j = lane; j < m; j += 32) {
+        const float2 yj = y[j];
+        const float dx = xi.x - yj.x, dy = xi.y - yj.y;
+        best = fminf(best, s2f[j] + expf(beta * (dx * dx + dy * dy)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0) s2_out[i] = fminf(s2[i], best);
+}
+
+constexpr int kKeyThreads = 256;
+
+__global__ void __launch_bounds__(kKeyThreads) keyframe_distances_kernel(
+    const float2 *__restrict__ xt, const float2 *__restrict__ xk, int nn, float *__restrict__ out)
+{
+    __shared__ float red[kKeyThreads / 32];
+    const float2 *k = xk + (size_t)blockIdx.x * nn;
+    float sum = 0.f;
+    for (int i = threadIdx.x; i < nn; i += kKeyThreads) sum += hypotf(xt[i].x - k[i].x, xt[i].y - k[i].y);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < kKeyThreads / 32; ++w) t += red[w];
+        out[blockIdx.x] = t / static_cast<float>(nn);
+    }
+}
+
 }  // namespace emdq
 
 using namespace emdq;
@@ -207,5 +248,31 @@ extern "C" emdq_status emdq_node_merge(const float *x0, const float *w_track,
     node_merge_kernel<<<(nn + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
         reinterpret_cast<const float2 *>(x0), w_track, s2_track, w_loop, s2_loop, w_key, nn, gamma,
         w_out, s2_out);
+    return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
+}
+
+extern "C" emdq_status emdq_node_restrict(const float *x, const float *s2, int nn, const float *y,
+                                          const float *s2f, int m, float beta, float *s2_out,
+                                          void *stream)
+{
+    if (nn < 0 || m < 0 || !(beta > 0.f) || !std::isfinite(beta)) return EMDQ_EINVAL;
+    if (nn == 0) return EMDQ_OK;
+    if (!x || !s2 || !s2_out || !aligned(x, 8) || (m > 0 && (!y || !s2f || !aligned(y, 8))))
+        return EMDQ_EINVAL;
+    node_restrict_kernel<<<(nn + kNodeWarps - 1) / kNodeWarps, 32 * kNodeWarps, 0,
+                           static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const float2 *>(x), s2, nn, reinterpret_cast<const float2 *>(y), s2f, m,
+        beta, s2_out);
+    return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
+}
+
+extern "C" emdq_status emdq_keyframe_distances(const float *xt, const float *xk, int nn, int nk,
+                                               float *out, void *stream)
+{
+    if (nn < 1 || nk < 0 || !xt || !aligned(xt, 8) || (nk > 0 && (!xk || !out || !aligned(xk, 8))))
+        return EMDQ_EINVAL;
+    if (nk == 0) return EMDQ_OK;
+    keyframe_distances_kernel<<<nk, kKeyThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const float2 *>(xt), reinterpret_cast<const float2 *>(xk), nn, out);
     return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }

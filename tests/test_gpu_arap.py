@@ -68,3 +68,26 @@ def test_arap_argument_errors(emdq):
     z = torch.zeros((8, 2), device='cuda')
     with pytest.raises(emdq.EmdqError):
         emdq.arap_smooth(z, torch.zeros((8, 8), device='cuda'), torch.ones(8, device='cuda'), 0.0)
+
+
+def test_field_from_the_smoothed_nodes(emdq, orc):
+    """Sec. III-D: once the nodes are tracked and smoothed the dense field is interpolated from
+    the nodes (their warps as the rows, weight 1, reference positions as the centres) with the
+    same tensor-core field; sampled pixels against the oracle's field from the same nodes."""
+    xs, ys = np.meshgrid(np.arange(0, 1280, 30.0), np.arange(0, 1024, 30.0))
+    x0 = np.stack([xs.ravel(), ys.ravel()], 1)
+    rng = np.random.default_rng(31)
+    wm = np.array([_row(orc, 1.03 * rng.uniform(0.99, 1.01), 0.05 + rng.normal(0, 0.01),
+                        8.0 + rng.normal(0, 2), 4.0 + rng.normal(0, 2)) for _ in x0])
+    s2 = rng.uniform(1, 50, len(x0))
+    alpha = np.float32(orc.alpha_for_frame(1280, 1024))
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    wn = emdq.arap_smooth(f(x0), f(wm), f(s2), alpha)
+    grid = (-20, -30, 1320, 1090)
+    disp = emdq.emdq_field(wn, torch.ones(len(x0), device='cuda'), f(x0), grid, alpha, precision=emdq.BF16)
+    torch.cuda.synchronize()
+    iy, ix = rng.integers(0, grid[3], 4096), rng.integers(0, grid[2], 4096)
+    pts = np.stack([grid[0] + ix, grid[1] + iy], 1).astype(np.float64)
+    want = orc.field_points(wn.cpu().numpy().astype(np.float64), np.ones(len(x0)), _f32(x0), pts,
+                            float(alpha))
+    assert np.abs(disp.cpu().numpy()[iy, ix] - want).max() <= 0.05

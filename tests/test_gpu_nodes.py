@@ -109,3 +109,19 @@ def test_node_argument_errors(emdq):
         emdq.node_track(z, w, v, w, v, z, 0.0, 1e-3)
     with pytest.raises(emdq.EmdqError):
         emdq.node_merge(z, w, v, w, v, w, -1.0)
+
+
+def test_node_restrict_and_keyframe_distances(emdq, orc):
+    rng = np.random.default_rng(21)
+    x = rng.uniform(0, 1280, (1500, 2))
+    s2 = rng.uniform(1, 500, 1500)
+    y = rng.uniform(0, 1280, (700, 2))
+    s2f = rng.uniform(0, 5, 700)
+    beta = orc.beta_for_frame(1280, 1024)
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    got = emdq.node_restrict(f(x), f(s2), f(y), f(s2f), np.float32(beta))
+    want = orc.node_restrict(_f32(x), _f32(s2), _f32(y), _f32(s2f), float(np.float32(beta)))
+    np.testing.assert_allclose(got.cpu().numpy(), want, rtol=1e-5)
+    xk = np.stack([x + rng.normal(0, 5 * k, x.shape) for k in range(6)])
+    d = emdq.keyframe_distances(f(x), f(xk))
+    np.testing.assert_allclose(d.cpu().numpy(), orc.keyframe_distances(_f32(x), _f32(xk)), rtol=1e-5, atol=1e-5)
