@@ -69,6 +69,7 @@ def lib():
             L.orc_node_merge.argtypes = [P, P, P, P, P, P, I, D, P, P]
             L.orc_arap_smooth.argtypes = [P, P, P, I, D, I, P, P]
             L.orc_node_restrict.argtypes = [P, P, I, P, P, I, D, P]
+            L.orc_feature_uncertainty.argtypes = [P, P, I, P, P, D, D, P, P]
             L.orc_keyframe_distances.argtypes = [P, P, I, I, P]
             L.orc_gamma_for_frame.restype = D
             L.orc_gamma_for_frame.argtypes = [I, I]
@@ -219,6 +220,16 @@ def arap_smooth(x0, w_merge, s2, alpha: float, max_iters: int = 5):
                                _p(w_out), _p(costs))
     assert rc == OK, rc
     return w_out, costs[:max_iters]
+
+
+def feature_uncertainty(src, dst, q8, c, alpha: float, beta: float, s2_prev) -> np.ndarray:
+    """Eq. 10: the features' uncertainties after one EMDQ."""
+    src, dst, q8, c, s2_prev = _d(src), _d(dst), _d(q8), _d(c), _d(s2_prev)
+    out = np.empty(c.shape[0])
+    rc = lib().orc_feature_uncertainty(_p(src), _p(dst), c.shape[0], _p(q8), _p(c), float(alpha),
+                                       float(beta), _p(s2_prev), _p(out))
+    assert rc == OK, rc
+    return out
 
 
 def node_restrict(x, s2, y, s2f, beta: float) -> np.ndarray:

@@ -17,6 +17,8 @@
  *   Eq. 5, App. A, Eq. 9      node tracking: W_i,t = f(W_i,t-1, dW_i) with f the composition
  *                             s_new q_new(x) = ds dq(s_old q_old(x)); sigma^2 propagation
  *   Eqs. 12-15                EKF merge of the tracking and loop-closing node warps
+ *   Eq. 10                    feature uncertainty: an inlier adds its squared EMDQ error, an
+ *                             outlier propagates as a node does (Eq. 9)
  *   Eq. 11                    node uncertainty bounded by the features': sigma_i^2 <=
  *                             sigma_j,feature^2 + exp(beta d_ij^2) for every feature j
  *   Eq. 6                     key-frame distance: mean over the nodes of |x_i,t - x_i,k|
@@ -470,6 +472,37 @@ int orc_keyframe_distances(const double *xt, const double *xk, int nn, int nk, d
         }
         out[k] = sum / nn;
     }
+    return ORC_OK;
+}
+
+/* Eq. 10 for every feature j after the EMDQ t-1 -> t (rows q8, field weights c, positions src
+ * in frame t-1 and dst in frame t): an inlier (c_j > 0) adds its squared error, sigma_j,EMDQ^2 =
+ * |y_j - W_-j(x_j)|^2 with W_-j the field of the other inliers at x_j (Eqs. 2-3); an outlier
+ * is propagated as Eq. 9 propagates a node, ds^2 sigma^2 + Eq. 8, with ds the field's scale at
+ * x_j.  +inf where the field has no weight. */
+int orc_feature_uncertainty(const double *src, const double *dst, int n, const double *q8,
+                            const double *c, double alpha, double beta, const double *s2_prev,
+                            double *s2_out)
+{
+    if (n < 1 || !src || !dst || !q8 || !c || !s2_prev || !s2_out || !(beta > 0.0))
+        return ORC_EINVAL;
+    double *e = malloc(sizeof(double) * (size_t)n);
+    if (!e) return ORC_EINVAL;
+    orc_residuals(src, dst, c, q8, n, alpha, e);
+    for (int j = 0; j < n; ++j) {
+        if (c[j] > 0.0) {
+            s2_out[j] = s2_prev[j] + e[j];
+            continue;
+        }
+        double row[8];
+        if (!warp_at(q8, c, src, n, src[2 * j], src[2 * j + 1], alpha, row)) {
+            s2_out[j] = INFINITY;
+            continue;
+        }
+        s2_out[j] = row[4] * row[4] * s2_prev[j] +
+                    uncertainty_at(c, src, n, src[2 * j], src[2 * j + 1], beta);
+    }
+    free(e);
     return ORC_OK;
 }
 

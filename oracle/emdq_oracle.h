@@ -80,6 +80,10 @@ int orc_node_merge(const double *x0, const double *w_track, const double *s2_tra
  * may be NULL) receives the cost of every iteration run. */
 int orc_arap_smooth(const double *x0, const double *w_merge, const double *s2, int nn,
                     double alpha, int max_iters, double *w_out, double *costs);
+/* Eq. 10: feature uncertainties after one EMDQ (see the .c). */
+int orc_feature_uncertainty(const double *src, const double *dst, int n, const double *q8,
+                            const double *c, double alpha, double beta, const double *s2_prev,
+                            double *s2_out);
 /* Eq. 11: node uncertainties bounded by the features' (see the .c). */
 int orc_node_restrict(const double *x, const double *s2, int nn, const double *y,
                       const double *s2f, int m, double beta, double *s2_out);

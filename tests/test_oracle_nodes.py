@@ -174,3 +174,29 @@ def test_keyframe_distances(orc):
     xt = rng.uniform(0, 640, (40, 2))
     xk = np.stack([xt, xt + [3.0, 4.0], xt + np.where(np.arange(40)[:, None] < 20, [6.0, 8.0], [0.0, 0.0])])
     np.testing.assert_allclose(orc.keyframe_distances(xt, xk), [0.0, 5.0, 5.0], atol=1e-12)
+
+
+def test_feature_uncertainty(orc):
+    """Eq. 10: an inlier adds its leave-one-out squared error under the field of the other
+    inliers (zero on an exact similarity), an outlier propagates as a node (Eq. 9 at its
+    position: ds^2 sigma^2 + Eq. 8)."""
+    rng = np.random.default_rng(13)
+    n = 120
+    src = rng.uniform(0, 640, (n, 2))
+    th, s, t = 0.05, 1.04, np.array([7.0, -3.0])
+    R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    dst = s * (src @ R.T + t)
+    q8 = np.tile(_row(orc, s, th, *t), (n, 1))
+    c = np.where(np.arange(n) % 4 == 0, 0.0, 0.9)
+    alpha, beta = orc.alpha_for_frame(640, 480), orc.beta_for_frame(640, 480)
+    s2 = rng.uniform(0.5, 3, n)
+    got = orc.feature_uncertainty(src, dst, q8, c, alpha, beta, s2)
+    inl = c > 0
+    np.testing.assert_allclose(got[inl], s2[inl], atol=1e-9)           # exact field: no error
+    du = orc.uncertainty_points(c, src, src[~inl], beta)
+    np.testing.assert_allclose(got[~inl], s ** 2 * s2[~inl] + du, rtol=1e-12)
+    # a displaced inlier adds its squared displacement against the others' (exact) field
+    dst2 = dst.copy()
+    dst2[1] += [3.0, 4.0]
+    got2 = orc.feature_uncertainty(src, dst2, q8, c, alpha, beta, s2)
+    assert got2[1] == pytest.approx(s2[1] + 25.0, rel=1e-9)
