@@ -306,6 +306,16 @@ EMDQ_API emdq_status emdq_node_merge(const float *x0, const float *w_track, cons
  * nk x nn x 2 float, the nodes' positions at each key frame); the caller adds frame t as a key
  * frame when the smallest of them exceeds its threshold H.
  */
+/* emdq_feature_uncertainty (Eq. 10): after the EMDQ t-1 -> t (q, c, src as emdq_field takes
+ * them, dst the matches' positions in frame t), s2_out_j = s2_prev_j + |y_j - W_-j(x_j)|^2 for an
+ * inlier (c_j > 0; W_-j the field of the other inliers at x_j), and ds^2 s2_prev_j + Eq. 8 at x_j
+ * for an outlier (ds the field's scale there, as Eq. 9 propagates a node); +inf where the field
+ * has no weight.  The caller keeps the features' identities across frames.
+ */
+EMDQ_API emdq_status emdq_feature_uncertainty(const float *src, const float *dst, int n,
+                                              const float *q, const float *c, float alpha,
+                                              float beta, const float *s2_prev, float *s2_out,
+                                              void *stream);
 EMDQ_API emdq_status emdq_node_restrict(const float *x, const float *s2, int nn, const float *y,
                                         const float *s2f, int m, float beta, float *s2_out,
                                         void *stream);

@@ -17,7 +17,7 @@ import torch
 from ._build import LIB as _LIB_PATH, build  # noqa: F401
 
 __all__ = ['emdq_fit', 'emdq_fit_batch', 'emdq_field', 'emdq_field_batch', 'mosaic_warp',
-           'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'emdq_uncertainty', 'node_track', 'node_merge', 'node_restrict',
+           'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'emdq_uncertainty', 'node_track', 'node_merge', 'node_restrict', 'feature_uncertainty',
            'keyframe_distances', 'arap_smooth',
            'mosaic_insert_reference',
            'alpha_for_frame', 'fit_workspace_size', 'field_workspace_size', 'EmdqError',
@@ -126,6 +126,7 @@ def lib() -> ctypes.CDLL:
             L.emdq_arap_workspace_size.restype = Z
             L.emdq_arap_smooth.argtypes = [P, P, P, I, F, I, P, P, Z, P]
             L.emdq_node_restrict.argtypes = [P, P, I, P, P, I, F, P, P]
+            L.emdq_feature_uncertainty.argtypes = [P, P, I, P, P, F, F, P, P, P]
             L.emdq_keyframe_distances.argtypes = [P, P, I, I, P, P]
             L.emdq_batch_workspace_size.argtypes = [P, I, I]
             L.emdq_batch_workspace_size.restype = Z
@@ -454,6 +455,23 @@ def node_restrict(x: torch.Tensor, s2: torch.Tensor, y: torch.Tensor, s2f: torch
                                   _stream(stream))
     if rc != 0:
         raise EmdqError('emdq_node_restrict', rc)
+    return out
+
+
+def feature_uncertainty(src: torch.Tensor, dst: torch.Tensor, q: torch.Tensor, c: torch.Tensor,
+                        alpha: float, beta: float, s2_prev: torch.Tensor, stream=None) -> torch.Tensor:
+    """Eq. 10: the features' uncertainties [n] after the EMDQ of (src -> dst)."""
+    n = c.shape[0]
+    _check(src, 'src', torch.float32, (n, 2))
+    _check(dst, 'dst', torch.float32, (n, 2))
+    _check(q, 'q', torch.float32, (n, 8))
+    _check(c, 'c', torch.float32, (n,))
+    _check(s2_prev, 's2_prev', torch.float32, (n,))
+    out = torch.empty_like(s2_prev)
+    rc = lib().emdq_feature_uncertainty(_ptr(src), _ptr(dst), n, _ptr(q), _ptr(c), float(alpha),
+                                        float(beta), _ptr(s2_prev), _ptr(out), _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_feature_uncertainty', rc)
     return out
 
 

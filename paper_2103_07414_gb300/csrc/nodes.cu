@@ -9,6 +9,8 @@
 // emdq_node_merge: one thread per node, the EKF merge of Eqs. 12-15 in closed form for the
 // 2 x 2 covariance.
 // emdq_node_restrict: one warp per node, the bound of Eq. 11 by every feature.
+// emdq_feature_uncertainty: one warp per feature, Eq. 10 (the leave-one-out field of the other
+// inliers at the feature: an inlier's squared error, or an outlier's scale and Eq. 8).
 // emdq_keyframe_distances: one block per key frame, Eq. 6's mean node distance.
 #include <cmath>
 
@@ -184,6 +186,57 @@ __global__ void __launch_bounds__(32 * kNodeWarps) node_restrict_kernel(
     if (lane == 0) s2_out[i] = fminf(s2[i], best);
 }
 
+__global__ void __launch_bounds__(32 * kNodeWarps) feature_uncertainty_kernel(
+    const float2 *__restrict__ src, const float2 *__restrict__ dst, int n,
+    const float *__restrict__ q, const float *__restrict__ c, float alpha, float beta,
+    const float *__restrict__ s2_prev, float *__restrict__ s2_out)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * kNodeWarps + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const float2 xj = src[j];
+    float sw = 0.f, ss = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, dmin = INFINITY;
+    for (int i = lane; i < n; i += 32) {
+        if (i == j) continue;                  // leave one out (an outlier weighs 0 anyway)
+        const float ci = c[i];
+        const float2 xi = src[i];
+        const float dx = xi.x - xj.x, dy = xi.y - xj.y, d2 = dx * dx + dy * dy;
+        const float w = ci * expf(-alpha * d2);
+        const float4 qi = *reinterpret_cast<const float4 *>(q + 8 * (size_t)i);
+        sw += w;
+        ss = fmaf(w, q[8 * (size_t)i + 4], ss);
+        s0 = fmaf(w, qi.x, s0);
+        s1 = fmaf(w, qi.y, s1);
+        s2 = fmaf(w, qi.z, s2);
+        s3 = fmaf(w, qi.w, s3);
+        if (ci > 0.f) dmin = fminf(dmin, d2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sw += __shfl_xor_sync(0xffffffffu, sw, o);
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+        dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+    }
+    if (lane != 0) return;
+    if (!(sw > 0.f) || !isfinite(sw)) {
+        s2_out[j] = INFINITY;
+        return;
+    }
+    const Sim m = sim_from_row(s0, s1, s2, s3, ss / sw);
+    if (c[j] > 0.f) {
+        const float2 yh = sim_apply(m, xj.x, xj.y);
+        const float2 yj = dst[j];
+        const float ex = yj.x - yh.x, ey = yj.y - yh.y;
+        s2_out[j] = s2_prev[j] + (ex * ex + ey * ey);
+    } else {
+        s2_out[j] = m.sc * m.sc * s2_prev[j] + expf(beta * dmin);
+    }
+}
+
 constexpr int kKeyThreads = 256;
 
 __global__ void __launch_bounds__(kKeyThreads) keyframe_distances_kernel(
@@ -274,5 +327,23 @@ extern "C" emdq_status emdq_keyframe_distances(const float *xt, const float *xk,
     if (nk == 0) return EMDQ_OK;
     keyframe_distances_kernel<<<nk, kKeyThreads, 0, static_cast<cudaStream_t>(stream)>>>(
         reinterpret_cast<const float2 *>(xt), reinterpret_cast<const float2 *>(xk), nn, out);
+    return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
+}
+
+extern "C" emdq_status emdq_feature_uncertainty(const float *src, const float *dst, int n,
+                                                const float *q, const float *c, float alpha,
+                                                float beta, const float *s2_prev, float *s2_out,
+                                                void *stream)
+{
+    if (n < 0 || !(alpha > 0.f) || !(beta > 0.f) || !std::isfinite(alpha) || !std::isfinite(beta))
+        return EMDQ_EINVAL;
+    if (n == 0) return EMDQ_OK;
+    if (!src || !dst || !q || !c || !s2_prev || !s2_out || !aligned(src, 8) || !aligned(dst, 8) ||
+        !aligned(q, 16))
+        return EMDQ_EINVAL;
+    feature_uncertainty_kernel<<<(n + kNodeWarps - 1) / kNodeWarps, 32 * kNodeWarps, 0,
+                                 static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const float2 *>(src), reinterpret_cast<const float2 *>(dst), n, q, c, alpha,
+        beta, s2_prev, s2_out);
     return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }

@@ -125,3 +125,22 @@ def test_node_restrict_and_keyframe_distances(emdq, orc):
     xk = np.stack([x + rng.normal(0, 5 * k, x.shape) for k in range(6)])
     d = emdq.keyframe_distances(f(x), f(xk))
     np.testing.assert_allclose(d.cpu().numpy(), orc.keyframe_distances(_f32(x), _f32(xk)), rtol=1e-5, atol=1e-5)
+
+
+def test_feature_uncertainty_against_the_oracle(emdq, orc):
+    sc, cfg = workload('seq1280', seed=6)
+    s, d, _ = make_matches(sc, 2, cfg['n'], cfg['outliers'], cfg['noise'])
+    fit = orc.fit(_f32(s), _f32(d), sc.w, sc.h)
+    q8, c = fit['q8'].astype(np.float32), fit['c'].astype(np.float32)
+    rng = np.random.default_rng(23)
+    s2 = rng.uniform(0.5, 3, len(c)).astype(np.float32)
+    alpha, beta = np.float32(orc.alpha_for_frame(sc.w, sc.h)), np.float32(orc.beta_for_frame(sc.w, sc.h))
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    got = emdq.feature_uncertainty(f(s), f(d), f(q8), f(c), alpha, beta, f(s2)).cpu().numpy()
+    want = orc.feature_uncertainty(_f32(s), _f32(d), _f32(q8), _f32(c), float(alpha), float(beta), _f32(s2))
+    inl = c > 0
+    # inliers: the squared error r^2 of residuals of a few px, whose FP32 field is within
+    # ~3e-4 px (the FP32 field tolerance), so within 2 |r| 3e-4 ~ 1e-2 px^2; outliers: relative
+    np.testing.assert_allclose(got[inl], want[inl], atol=1e-2, rtol=1e-4)
+    fin = ~inl & (want < 1e30)
+    np.testing.assert_allclose(got[fin], want[fin], rtol=1e-4)
