@@ -69,6 +69,7 @@ def lib():
             L.orc_node_merge.argtypes = [P, P, P, P, P, P, I, D, P, P]
             L.orc_arap_smooth.argtypes = [P, P, P, I, D, I, P, P]
             L.orc_node_restrict.argtypes = [P, P, I, P, P, I, D, P]
+            L.orc_node_init.argtypes = [P, P, I, P, I, D, P]
             L.orc_feature_uncertainty.argtypes = [P, P, I, P, P, D, D, P, P]
             L.orc_keyframe_distances.argtypes = [P, P, I, I, P]
             L.orc_gamma_for_frame.restype = D
@@ -230,6 +231,39 @@ def feature_uncertainty(src, dst, q8, c, alpha: float, beta: float, s2_prev) -> 
                                        float(beta), _p(s2_prev), _p(out))
     assert rc == OK, rc
     return out
+
+
+def node_init(x0, w, pts, alpha: float) -> np.ndarray:
+    """Sec. III-E: warps [npts, 8] of new nodes at pts from the existing nodes (x0, w)."""
+    x0, w, pts = _d(x0), _d(w), _d(pts)
+    out = np.empty((pts.shape[0], 8))
+    rc = lib().orc_node_init(_p(x0), _p(w), x0.shape[0], _p(pts), pts.shape[0], float(alpha), _p(out))
+    assert rc == OK, rc
+    return out
+
+
+def hex_nodes(w: int, h: int, spacing: float) -> np.ndarray:
+    """Sec. III-E's node set ("until all image areas are covered"), written as its definition:
+    every point of the hexagonal lattice through the image centre ((w-1)/2, (h-1)/2) with the
+    given spacing (rows spacing*sqrt(3)/2 apart, alternate rows shifted by spacing/2) that lies
+    within the lattice's covering radius spacing/sqrt(3) of the frame [0, w-1] x [0, h-1], so
+    every pixel has a node within that radius."""
+    cx, cy = (w - 1) / 2.0, (h - 1) / 2.0
+    dy = spacing * np.sqrt(3.0) / 2.0
+    m = spacing / np.sqrt(3.0)
+    pts = []
+    rmax = int(np.ceil(max(w, h) / dy)) + 2
+    cmax = int(np.ceil(max(w, h) / spacing)) + 2
+    for r in range(-rmax, rmax + 1):
+        y = cy + r * dy
+        off = 0.5 * spacing if r % 2 else 0.0
+        for k in range(-cmax, cmax + 1):
+            x = cx + off + k * spacing
+            ex = max(0.0 - x, 0.0, x - (w - 1))
+            ey = max(0.0 - y, 0.0, y - (h - 1))
+            if ex * ex + ey * ey <= m * m:
+                pts.append((x, y))
+    return np.array(pts)
 
 
 def node_restrict(x, s2, y, s2f, beta: float) -> np.ndarray:

@@ -22,6 +22,8 @@
  *   Eq. 11                    node uncertainty bounded by the features': sigma_i^2 <=
  *                             sigma_j,feature^2 + exp(beta d_ij^2) for every feature j
  *   Eq. 6                     key-frame distance: mean over the nodes of |x_i,t - x_i,k|
+ *   Sec. III-E                new nodes: a hexagonal lattice grown from the image centre; a new
+ *                             node's warp is the ARAP-weighted average of the existing nodes'
  *   Sec. III-D, Eqs. 21-22    ARAP smoothing of the node warps (the ARAP warp of a node is the
  *                             weighted similarity fit of Eqs. 16-20 over the nodes with p = 1)
  *
@@ -503,6 +505,23 @@ int orc_feature_uncertainty(const double *src, const double *dst, int n, const d
                     uncertainty_at(c, src, n, src[2 * j], src[2 * j + 1], beta);
     }
     free(e);
+    return ORC_OK;
+}
+
+/* Sec. III-E: the warps of new nodes at pts, the weighted average of the existing nodes' warps
+ * (rows w at reference positions x0, weights exp(-alpha |p - x0_j|^2), the ARAP weights): the
+ * Eqs. 2-3 blend with every weight 1.  NaN rows where the weights vanish. */
+int orc_node_init(const double *x0, const double *w, int n, const double *pts, int npts,
+                  double alpha, double *w_out)
+{
+    if (n < 1 || npts < 0 || !x0 || !w || (npts > 0 && (!pts || !w_out))) return ORC_EINVAL;
+    double *ones = malloc(sizeof(double) * (size_t)n);
+    if (!ones) return ORC_EINVAL;
+    for (int j = 0; j < n; ++j) ones[j] = 1.0;
+    for (int k = 0; k < npts; ++k)
+        if (!warp_at(w, ones, x0, n, pts[2 * k], pts[2 * k + 1], alpha, w_out + 8 * (size_t)k))
+            for (int m = 0; m < 8; ++m) w_out[8 * (size_t)k + m] = NAN;
+    free(ones);
     return ORC_OK;
 }
 

@@ -80,6 +80,9 @@ int orc_node_merge(const double *x0, const double *w_track, const double *s2_tra
  * may be NULL) receives the cost of every iteration run. */
 int orc_arap_smooth(const double *x0, const double *w_merge, const double *s2, int nn,
                     double alpha, int max_iters, double *w_out, double *costs);
+/* Sec. III-E: warps of new nodes, the weighted average of the existing nodes' (see the .c). */
+int orc_node_init(const double *x0, const double *w, int n, const double *pts, int npts,
+                  double alpha, double *w_out);
 /* Eq. 10: feature uncertainties after one EMDQ (see the .c). */
 int orc_feature_uncertainty(const double *src, const double *dst, int n, const double *q8,
                             const double *c, double alpha, double beta, const double *s2_prev,

@@ -71,3 +71,34 @@ def test_costs_never_increase_and_noise_is_smoothed(orc):
     before = np.abs(_pos(orc, w, x0) - truth).mean()
     after = np.abs(_pos(orc, out, x0) - truth).mean()
     assert after < 0.9 * before
+
+
+def test_hex_lattice_definition(orc):
+    """Sec. III-E: the lattice holds the centre, every node has its 6 neighbours at the spacing
+    unless it is near the frame edge, and it covers the frame: no pixel is farther than the
+    lattice's covering radius spacing/sqrt(3) from a node."""
+    from scipy.spatial import cKDTree
+    x = orc.hex_nodes(640, 480, 40.0)
+    assert np.any(np.all(np.isclose(x, [319.5, 239.5]), axis=1))
+    t = cKDTree(x)
+    d, _ = t.query(x, k=7)
+    inner = (x[:, 0] > 45) & (x[:, 0] < 594) & (x[:, 1] > 45) & (x[:, 1] < 434)
+    np.testing.assert_allclose(d[inner, 1:], 40.0, rtol=1e-9)
+    g = np.stack(np.meshgrid(np.arange(0, 640, 7.0), np.arange(0, 480, 7.0)), -1).reshape(-1, 2)
+    dg, _ = t.query(g)
+    assert dg.max() <= 40.0 / math.sqrt(3.0) + 1e-9
+
+
+def test_new_node_warps_are_the_weighted_average(orc):
+    x0 = _lattice()
+    S = _row(orc, 1.05, 0.08, 12.0, -7.0)
+    w = np.tile(S, (len(x0), 1))
+    pts = np.array([[10.0, 10.0], [333.3, 111.1], [700.0, 500.0]])
+    out = orc.node_init(x0, w, pts, orc.alpha_for_frame(640, 480))
+    np.testing.assert_allclose(out, np.tile(S, (3, 1)) * [1, 1, 1, 1, 1, 1, 0, 0] + [0] * 8, atol=1e-12)
+    # two nodes: the new node midway takes the plain average of their warps
+    a, b = _row(orc, 1.0, 0.0, 0.0, 0.0), _row(orc, 1.1, 0.2, 10.0, 0.0)
+    mid = orc.node_init(np.array([[0.0, 0.0], [20.0, 0.0]]), np.stack([a, b]), np.array([[10.0, 0.0]]), 1e-3)[0]
+    q = a[:4] / math.hypot(a[0], a[1]) + b[:4] / math.hypot(b[0], b[1])
+    np.testing.assert_allclose(mid[:4], q / math.hypot(q[0], q[1]), atol=1e-12)
+    assert mid[4] == pytest.approx(1.05)
