@@ -322,6 +322,22 @@ EMDQ_API emdq_status emdq_node_restrict(const float *x, const float *s2, int nn,
 EMDQ_API emdq_status emdq_keyframe_distances(const float *xt, const float *xk, int nn, int nk,
                                              float *out, void *stream);
 
+/* Node insertion (Sec. III-E).  emdq_hex_nodes (host, no GPU): the nodes of a w x h frame, the
+ * hexagonal lattice with the given spacing through the image centre ((w-1)/2, (h-1)/2; rows
+ * spacing*sqrt(3)/2 apart, alternate rows shifted by spacing/2) grown breadth-first from the
+ * centre over every node's 6 neighbours, keeping the points within the lattice's covering radius
+ * spacing/sqrt(3) of the frame, so every pixel has a node within that radius.  Writes up to
+ * `capacity` positions (x, y) to the host array x0_out in that order and returns how many there
+ * are (-1 for bad arguments).
+ * emdq_node_init: the warps of new nodes at pts (npts x 2, device), each the weighted average
+ * of the existing nodes' warps w (nn x 8 at reference positions x0, nn x 2) with the ARAP weights
+ * exp(-alpha |p - x0_j|^2) -- the Eqs. 2-3 blend with every weight 1; NaN rows where every
+ * weight vanishes.
+ */
+EMDQ_API int         emdq_hex_nodes(int w, int h, float spacing, float *x0_out, int capacity);
+EMDQ_API emdq_status emdq_node_init(const float *x0, const float *w, int nn, const float *pts,
+                                    int npts, float alpha, float *w_out, void *stream);
+
 /* emdq_arap_smooth (Sec. III-D, Eqs. 21-22): ARAP smoothing of the merged node warps.  At
  * most max_iters iterations (the paper uses 5) of: positions x_t = W(x_0); the ARAP warp of every
  * node, the similarity fit of Eqs. ARAP1-3 to its neighbours' displacements x_j,0 -> x_j,t with

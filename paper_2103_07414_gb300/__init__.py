@@ -18,7 +18,7 @@ from ._build import LIB as _LIB_PATH, build  # noqa: F401
 
 __all__ = ['emdq_fit', 'emdq_fit_batch', 'emdq_field', 'emdq_field_batch', 'mosaic_warp',
            'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'emdq_uncertainty', 'node_track', 'node_merge', 'node_restrict', 'feature_uncertainty',
-           'keyframe_distances', 'arap_smooth',
+           'keyframe_distances', 'hex_nodes', 'node_init', 'arap_smooth',
            'mosaic_insert_reference',
            'alpha_for_frame', 'fit_workspace_size', 'field_workspace_size', 'EmdqError',
            'FP32', 'BF16', 'STATUS', 'lib', 'build']
@@ -126,6 +126,9 @@ def lib() -> ctypes.CDLL:
             L.emdq_arap_workspace_size.restype = Z
             L.emdq_arap_smooth.argtypes = [P, P, P, I, F, I, P, P, Z, P]
             L.emdq_node_restrict.argtypes = [P, P, I, P, P, I, F, P, P]
+            L.emdq_hex_nodes.argtypes = [I, I, F, P, I]
+            L.emdq_hex_nodes.restype = I
+            L.emdq_node_init.argtypes = [P, P, I, P, I, F, P, P]
             L.emdq_feature_uncertainty.argtypes = [P, P, I, P, P, F, F, P, P, P]
             L.emdq_keyframe_distances.argtypes = [P, P, I, I, P, P]
             L.emdq_batch_workspace_size.argtypes = [P, I, I]
@@ -485,6 +488,32 @@ def keyframe_distances(xt: torch.Tensor, xk: torch.Tensor, stream=None) -> torch
     rc = lib().emdq_keyframe_distances(_ptr(xt), _ptr(xk), nn, nk, _ptr(out), _stream(stream))
     if rc != 0:
         raise EmdqError('emdq_keyframe_distances', rc)
+    return out
+
+
+def hex_nodes(w: int, h: int, spacing: float) -> torch.Tensor:
+    """Sec. III-E: the node lattice of a w x h frame ([nn, 2] float32, CPU, breadth-first from
+    the centre)."""
+    n = lib().emdq_hex_nodes(int(w), int(h), float(spacing), None, 0)
+    if n < 0:
+        raise ValueError('hex_nodes: bad arguments')
+    out = torch.empty((n, 2), dtype=torch.float32)
+    lib().emdq_hex_nodes(int(w), int(h), float(spacing), ctypes.c_void_p(out.data_ptr()), n)
+    return out
+
+
+def node_init(x0: torch.Tensor, w: torch.Tensor, pts: torch.Tensor, alpha: float,
+              stream=None) -> torch.Tensor:
+    """Sec. III-E: warps [npts, 8] of new nodes at pts from the existing nodes (x0, w)."""
+    nn, npts = x0.shape[0], pts.shape[0]
+    _check(x0, 'x0', torch.float32, (nn, 2))
+    _check(w, 'w', torch.float32, (nn, 8))
+    _check(pts, 'pts', torch.float32, (npts, 2))
+    out = torch.empty((npts, 8), dtype=torch.float32, device=x0.device)
+    rc = lib().emdq_node_init(_ptr(x0), _ptr(w), nn, _ptr(pts), npts, float(alpha), _ptr(out),
+                              _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_node_init', rc)
     return out
 
 

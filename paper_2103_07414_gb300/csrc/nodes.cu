@@ -12,7 +12,13 @@
 // emdq_feature_uncertainty: one warp per feature, Eq. 10 (the leave-one-out field of the other
 // inliers at the feature: an inlier's squared error, or an outlier's scale and Eq. 8).
 // emdq_keyframe_distances: one block per key frame, Eq. 6's mean node distance.
+// emdq_hex_nodes (host) and emdq_node_init: the node insertion of Sec. III-E -- the hexagonal
+// lattice grown breadth-first from the image centre over the 6 neighbours of every node, and a
+// new node's warp as the ARAP-weighted average of the existing nodes' (one warp per new node).
 #include <cmath>
+#include <deque>
+#include <set>
+#include <utility>
 
 #include "common.cuh"
 
@@ -237,6 +243,53 @@ __global__ void __launch_bounds__(32 * kNodeWarps) feature_uncertainty_kernel(
     }
 }
 
+__global__ void __launch_bounds__(32 * kNodeWarps) node_init_kernel(
+    const float2 *__restrict__ x0, const float *__restrict__ w, int nn, const float2 *__restrict__ pts,
+    int np, float alpha, float *__restrict__ w_out)
+{
+    const int lane = threadIdx.x & 31;
+    const int k = blockIdx.x * kNodeWarps + (threadIdx.x >> 5);
+    if (k >= np) return;
+    const float2 p = pts[k];
+    float sw = 0.f, ss = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    for (int j = lane; j < nn; j += 32) {
+        const float2 xj = x0[j];
+        const float dx = xj.x - p.x, dy = xj.y - p.y;
+        const float g = expf(-alpha * (dx * dx + dy * dy));
+        const float *wj = w + 8 * (size_t)j;
+        sw += g;                             // Eqs. 2-3 with every weight 1
+        ss = fmaf(g, wj[4], ss);
+        s0 = fmaf(g, wj[0], s0);
+        s1 = fmaf(g, wj[1], s1);
+        s2 = fmaf(g, wj[2], s2);
+        s3 = fmaf(g, wj[3], s3);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sw += __shfl_xor_sync(0xffffffffu, sw, o);
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+    }
+    if (lane != 0) return;
+    float *o = w_out + 8 * (size_t)k;
+    if (!(sw > 0.f) || !isfinite(sw)) {
+        for (int m = 0; m < 8; ++m) o[m] = __int_as_float(0x7fffffff);
+        return;
+    }
+    const float nq = rsqrtf(s0 * s0 + s1 * s1);
+    o[0] = s0 * nq;
+    o[1] = s1 * nq;
+    o[2] = s2 * nq;
+    o[3] = s3 * nq;
+    o[4] = ss / sw;
+    o[5] = 1.f;
+    o[6] = 0.f;
+    o[7] = 0.f;
+}
+
 constexpr int kKeyThreads = 256;
 
 __global__ void __launch_bounds__(kKeyThreads) keyframe_distances_kernel(
@@ -345,5 +398,67 @@ extern "C" emdq_status emdq_feature_uncertainty(const float *src, const float *d
                                  static_cast<cudaStream_t>(stream)>>>(
         reinterpret_cast<const float2 *>(src), reinterpret_cast<const float2 *>(dst), n, q, c, alpha,
         beta, s2_prev, s2_out);
+    return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
+}
+
+extern "C" int emdq_hex_nodes(int w, int h, float spacing, float *x0_out, int capacity)
+{
+    if (w < 1 || h < 1 || !(spacing > 0.f) || !std::isfinite(spacing) || capacity < 0 ||
+        (capacity > 0 && !x0_out))
+        return -1;
+    // lattice row r at y = cy + r dy, odd rows shifted by s/2; kept: points within the covering
+    // radius s/sqrt(3) of the frame [0, w-1] x [0, h-1]
+    const double s = spacing, dy = s * std::sqrt(3.0) / 2.0, m = s / std::sqrt(3.0);
+    const double cx = (w - 1) / 2.0, cy = (h - 1) / 2.0;
+    auto pos = [&](int r, int k, double &x, double &y) {
+        y = cy + r * dy;
+        x = cx + ((r & 1) ? 0.5 * s : 0.0) + k * s;
+    };
+    auto keep = [&](int r, int k) {
+        double x, y;
+        pos(r, k, x, y);
+        const double ex = std::max(std::max(-x, 0.0), x - (w - 1));
+        const double ey = std::max(std::max(-y, 0.0), y - (h - 1));
+        return ex * ex + ey * ey <= m * m;
+    };
+    std::set<std::pair<int, int>> seen;
+    std::deque<std::pair<int, int>> todo;
+    seen.insert({0, 0});
+    todo.push_back({0, 0});
+    int count = 0;
+    while (!todo.empty()) {
+        const auto [r, k] = todo.front();
+        todo.pop_front();
+        if (count < capacity) {
+            double x, y;
+            pos(r, k, x, y);
+            x0_out[2 * count] = static_cast<float>(x);
+            x0_out[2 * count + 1] = static_cast<float>(y);
+        }
+        ++count;
+        if (count > (1 << 26)) return -1;           // spacing far too small for the frame
+        // the 6 neighbours in the odd-row-shifted layout
+        const int k0 = (r & 1) ? k : k - 1, k1 = k0 + 1;
+        const std::pair<int, int> nb[6] = {{r, k - 1}, {r, k + 1}, {r - 1, k0}, {r - 1, k1},
+                                           {r + 1, k0}, {r + 1, k1}};
+        for (const auto &q : nb)
+            if (!seen.count(q) && keep(q.first, q.second)) {
+                seen.insert(q);
+                todo.push_back(q);
+            }
+    }
+    return count;
+}
+
+extern "C" emdq_status emdq_node_init(const float *x0, const float *w, int nn, const float *pts,
+                                      int npts, float alpha, float *w_out, void *stream)
+{
+    if (nn < 1 || npts < 0 || !(alpha > 0.f) || !std::isfinite(alpha)) return EMDQ_EINVAL;
+    if (npts == 0) return EMDQ_OK;
+    if (!x0 || !w || !pts || !w_out || !aligned(x0, 8) || !aligned(pts, 8)) return EMDQ_EINVAL;
+    node_init_kernel<<<(npts + kNodeWarps - 1) / kNodeWarps, 32 * kNodeWarps, 0,
+                       static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const float2 *>(x0), w, nn, reinterpret_cast<const float2 *>(pts), npts,
+        alpha, w_out);
     return cudaGetLastError() == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }

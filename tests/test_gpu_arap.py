@@ -91,3 +91,27 @@ def test_field_from_the_smoothed_nodes(emdq, orc):
     want = orc.field_points(wn.cpu().numpy().astype(np.float64), np.ones(len(x0)), _f32(x0), pts,
                             float(alpha))
     assert np.abs(disp.cpu().numpy()[iy, ix] - want).max() <= 0.05
+
+
+def test_node_insertion(emdq, orc):
+    """Sec. III-E: the library's lattice is the oracle's node set (breadth-first order from the
+    centre), and new nodes' warps equal the oracle's weighted averages."""
+    x = emdq.hex_nodes(1280, 1024, 30.0).numpy().astype(np.float64)
+    want = orc.hex_nodes(1280, 1024, 30.0)
+    assert len(x) == len(want)
+    a = np.array(sorted(map(tuple, np.round(x, 3))))
+    b = np.array(sorted(map(tuple, np.round(want, 3))))
+    np.testing.assert_allclose(a, b, atol=2e-3)
+    assert np.allclose(x[0], [639.5, 511.5])
+    d0 = np.hypot(*(x - x[0]).T)
+    assert (np.diff(d0[:7]) >= -1e-9).all() and np.allclose(d0[1:7], 30.0, atol=1e-3)
+    rng = np.random.default_rng(41)
+    w = np.array([_row(orc, rng.uniform(0.97, 1.03), rng.normal(0, 0.05), *rng.normal(0, 5, 2)) for _ in x])
+    pts = rng.uniform(-100, 1400, (500, 2))
+    alpha = np.float32(orc.alpha_for_frame(1280, 1024))
+    f = lambda v: torch.from_numpy(np.ascontiguousarray(v, dtype=np.float32)).cuda()
+    got = emdq.node_init(f(x), f(w), f(pts), alpha).cpu().numpy().astype(np.float64)
+    ref = orc.node_init(_f32(x), _f32(w), _f32(pts), float(alpha))
+    dpos = np.abs(_pos(orc, got, _f32(pts)) - _pos(orc, ref, _f32(pts))).max()
+    assert dpos <= 2e-3
+    np.testing.assert_allclose(got[:, 4], ref[:, 4], rtol=1e-5)
