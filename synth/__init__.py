@@ -17,6 +17,7 @@ from .scene import (  # noqa: F401
     render_reference,
     render_frame,
     make_matches,
+    make_pair_matches,
     footprint_window,
     canvas_origin,
     workload,

@@ -226,6 +226,43 @@ def make_matches(sc: Scene, t: int, n: int, outlier_frac: float, noise_sigma: fl
     return (src[perm].astype(np.float32), dst[perm].astype(np.float32), inl[perm])
 
 
+def make_pair_matches(sc: Scene, t0: int, t1: int, n: int, outlier_frac: float,
+                      noise_sigma: float, seed: int | None = None):
+    """Feature matches between frames t0 and t1 (frame 0 is the reference itself).
+
+    A feature is a reference point x seen at x in frame 0 and at GT_t(x) in frame t >= 1;
+    inliers: x uniform over the reference, src = its position in frame t0, dst = its position in
+    frame t1 plus N(0, noise^2 I), kept when both lie inside their frames; outliers: src and dst
+    independent and uniform over the frame.  Returns (src, dst [n, 2] float32, inlier bool[n],
+    x [n, 2] float64: the inliers' reference points, NaN for outliers)."""
+    g = _rng(sc.seed if seed is None else seed, 5000 + 97 * int(t0) + int(t1))
+    n_out = int(round(outlier_frac * n))
+    n_in = n - n_out
+
+    def at(t, x):
+        return x if t == 0 else gt_forward(sc, torch.from_numpy(x), t).numpy()
+
+    xs, a, b = np.empty((0, 2)), np.empty((0, 2)), np.empty((0, 2))
+    while xs.shape[0] < n_in:
+        m = 2 * (n_in - xs.shape[0]) + 16
+        x = np.stack([g.uniform(0, sc.w - 1, m), g.uniform(0, sc.h - 1, m)], axis=1)
+        p0 = at(t0, x)
+        p1 = at(t1, x) + g.normal(0.0, noise_sigma, x.shape)
+        ok = ((p0[:, 0] >= 0) & (p0[:, 0] <= sc.w - 1) & (p0[:, 1] >= 0) & (p0[:, 1] <= sc.h - 1) &
+              (p1[:, 0] >= 0) & (p1[:, 0] <= sc.w - 1) & (p1[:, 1] >= 0) & (p1[:, 1] <= sc.h - 1))
+        xs = np.concatenate([xs, x[ok]])[:n_in]
+        a = np.concatenate([a, p0[ok]])[:n_in]
+        b = np.concatenate([b, p1[ok]])[:n_in]
+    oa = np.stack([g.uniform(0, sc.w - 1, n_out), g.uniform(0, sc.h - 1, n_out)], axis=1)
+    ob = np.stack([g.uniform(0, sc.w - 1, n_out), g.uniform(0, sc.h - 1, n_out)], axis=1)
+    src = np.concatenate([a, oa])
+    dst = np.concatenate([b, ob])
+    inl = np.concatenate([np.ones(n_in, bool), np.zeros(n_out, bool)])
+    xr = np.concatenate([xs, np.full((n_out, 2), np.nan)])
+    perm = g.permutation(n)
+    return src[perm].astype(np.float32), dst[perm].astype(np.float32), inl[perm], xr[perm]
+
+
 def canvas_origin(canvas_w: int, canvas_h: int, w0: int, h0: int):
     """Canvas position of reference pixel (0, 0): the reference frame is centred."""
     return ((canvas_w - w0) // 2, (canvas_h - h0) // 2)

@@ -55,3 +55,19 @@ def test_full_sequence_pan_revisits_the_start():
     assert torch.allclose(gt_forward(still, x, 400), gt_forward(still, x, 0), atol=1e-9)
     shift = gt_forward(still, x, 200) - gt_forward(still, x, 0)
     assert torch.allclose(shift.norm(dim=1), torch.full((2,), 1200.0, dtype=torch.float64))
+
+
+def test_frame_to_frame_matches():
+    """make_pair_matches: inliers sit at the ground-truth positions of their reference points in
+    both frames (frame 0 being the reference itself), up to the stated noise in the second."""
+    import torch
+    from synth import gt_forward, make_pair_matches
+    sc, cfg = workload('seq1280', seed=3)
+    for t0, t1 in ((0, 1), (4, 5)):
+        s, d, inl, x = make_pair_matches(sc, t0, t1, 500, 0.3, 1.0)
+        assert s.shape == d.shape == (500, 2) and inl.sum() == 350
+        p0 = x[inl] if t0 == 0 else gt_forward(sc, torch.from_numpy(x[inl]), t0).numpy()
+        np.testing.assert_allclose(s[inl], p0, atol=1e-3)
+        r = d[inl] - gt_forward(sc, torch.from_numpy(x[inl]), t1).numpy()
+        assert 0.8 < r.std() < 1.2
+        assert np.isnan(x[~inl]).all()
