@@ -87,6 +87,10 @@ def parse_args():
     ap.add_argument('--no-pipeline', action='store_true',
                     help='field and warp of every frame on one stream (default: the warp of frame k '
                          'on a second stream, beside the field of frame k + 1)')
+    ap.add_argument('--one-stream', action='store_true',
+                    help='batched fields and their warps one after the other on the main stream '
+                         '(default: the warps of a group on a second stream, beside the next '
+                         "group's fields)")
     ap.add_argument('--fit-ctas', type=int, default=0,
                     help='CTAs of one fit launch, split evenly over its frames (default: every '
                          'co-resident CTA; 152 = one per SM, which leaves room beside the GEMM '
@@ -338,7 +342,7 @@ def run_gpu(args, ws, rank, local):
     # frame order (the blend is order-dependent) while the next group's fields run
     piped = not fused and not args.no_pipeline
     G = max(1, min(8, args.field_group)) if piped and prec == emdq.BF16 else 1
-    warp_stream = torch.cuda.Stream(device=dev) if piped else None
+    warp_stream = torch.cuda.Stream(device=dev) if piped and not args.one_stream else None
     if piped and prec == emdq.BF16:
         zq = torch.zeros((n, 8), device=dev)
         zc = torch.zeros(n, device=dev)
@@ -371,9 +375,11 @@ def run_gpu(args, ws, rank, local):
 
     def fields_then_warps(frs, ss, gs, fos, evs3=None):
         """A group of frames, pipelined: one batched field call, then the warps."""
+        two = not args.one_stream
+        wst = warp_stream if two else stream      # resolved per call: capture rebinds stream
         slot = group_no[0] % 2
         group_no[0] += 1
-        if slot_free[slot] is not None:
+        if two and slot_free[slot] is not None:
             stream.wait_event(slot_free[slot])
         disps = [grp_disp[slot][i][: g[2] * g[3] * 2].view(g[3], g[2], 2) for i, g in enumerate(gs)]
         if prec == emdq.BF16:
@@ -384,22 +390,24 @@ def run_gpu(args, ws, rank, local):
                             out=disps[0], workspace=grp_ws[slot])
         # dependencies through plain events (a captured graph cannot wait on the timing
         # events, which are external event nodes there)
-        fdone = torch.cuda.Event()
-        fdone.record(stream)
         if evs3 is not None:
             for e3 in evs3: e3[0].record(stream)
-        warp_stream.wait_event(fdone)
+        if two:
+            fdone = torch.cuda.Event()
+            fdone.record(stream)
+            wst.wait_event(fdone)
         # one launch blends the group's frames in order (the first frame's events span it,
         # the others' are empty, so per-frame sums stay right)
-        if evs3 is not None: evs3[0][1].record(warp_stream)
-        emdq.mosaic_warp_batch(frs, disps, gs, canvas, origin, stream=warp_stream)
+        if evs3 is not None: evs3[0][1].record(wst)
+        emdq.mosaic_warp_batch(frs, disps, gs, canvas, origin, stream=wst)
         if evs3 is not None:
             for i in range(len(frs)):
-                if i: evs3[i][1].record(warp_stream)
-                evs3[i][2].record(warp_stream)
-        wdone = torch.cuda.Event()
-        wdone.record(warp_stream)
-        slot_free[slot] = wdone
+                if i: evs3[i][1].record(wst)
+                evs3[i][2].record(wst)
+        if two:
+            wdone = torch.cuda.Event()
+            wdone.record(wst)
+            slot_free[slot] = wdone
 
     def fit_batch(bi, ks, s_of, d_of, ev=None):
         """The fits of batch bi (frames ks) on the fit stream; returns its done event.
@@ -442,7 +450,7 @@ def run_gpu(args, ws, rank, local):
             for j, k in enumerate(ks):
                 field_and_warp(fr_of(k), s_of(k), grids[k], outs[j],
                                ev[4 + 3 * j: 7 + 3 * j] if ev else None)
-        if piped:
+        if piped and not args.one_stream:
             stream.wait_stream(warp_stream)       # the batch is blended when its warps are
             slot_free[0] = slot_free[1] = None
         for j, k in enumerate(ks):
@@ -811,8 +819,9 @@ def run_gpu(args, ws, rank, local):
         kernel_ms_per_step={k: v / args.steps for k, v in kernel_total.items()},
         path=(('learned warm start + ' if warm else '') + ('emdq_fit_batch' if B > 1 else 'emdq_fit') +
               (' + emdq_mosaic (fused BF16 field and warp)' if fused else
-               (f' + emdq_field_batch + mosaic_warp_batch ({G} frames per call, bf16; the warps on a '
-                f'second stream)'
+               (f' + emdq_field_batch + mosaic_warp_batch ({G} frames per call, bf16; ' +
+                ('each call after the other on one stream)' if args.one_stream else
+                 'the warps on a second stream)')
                 if piped and prec == emdq.BF16 else f' + emdq_field ({args.precision}) + mosaic_warp')) +
               (', fits of the next batch on a second stream' if overlap else '') +
               (', the pass replayed from one CUDA graph' if graph is not None else '')),
