@@ -121,6 +121,38 @@ __device__ __forceinline__ float warp_sum_f(float v)
 
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
+// Warp totals of K values of each of 4 rows (v[r][k]): two halving steps over the row index
+// (across lanes 1 and 2 apart every lane keeps the rows of its own lane bits and sends the
+// others), then butterflies over the remaining lane bits.  Lane L ends with the K totals of
+// row L & 3, after 9K shuffles instead of the 20K of one butterfly per value; the order of
+// the additions is fixed, so a row's totals are the same bits on every call.
+template <int K>
+__device__ __forceinline__ void rows4_sum(const float (&v)[4][K], int lane, float (&t)[K])
+{
+    const bool b0 = lane & 1, b1 = lane & 2;
+    float h[2][K];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float keep = b0 ? v[2 * p + 1][k] : v[2 * p][k];
+            const float send = b0 ? v[2 * p][k] : v[2 * p + 1][k];
+            h[p][k] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float keep = b1 ? h[1][k] : h[0][k];
+        const float send = b1 ? h[0][k] : h[1][k];
+        t[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
+    }
+}
+
 // Gaussian weight 2^(lp - |d|^2) of a scaled offset d.
 __device__ __forceinline__ float gauss_w(float2 d, float lp)
 {
@@ -243,25 +275,30 @@ __device__ void mstep_group(const FitArgs &A, const FitSmem &S, const int *rows,
             sc[r] = __ffma2_rn(om2, g2, sc[r]);
         }
     }
-    // every lane receives every row's sums; lane r then finishes row r, so the divisions
-    // and square roots of the closed form are issued once for all R rows
-    float w = 0.f, su0 = 0.f, su1 = 0.f, sv0 = 0.f, sv1 = 0.f, vx = 0.f, vy = 0.f, dot = 0.f,
-          cross = 0.f;
+    // lane r receives row r's sums and finishes row r, so the divisions and square roots of
+    // the closed form are issued once for all R rows
+    float v9[4][9], t[9];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const bool on = r < R;
+        v9[r][0] = on ? W[r < R ? r : 0] : 0.f;
+        v9[r][1] = on ? su[r < R ? r : 0].x : 0.f;
+        v9[r][2] = on ? su[r < R ? r : 0].y : 0.f;
+        v9[r][3] = on ? sv[r < R ? r : 0].x : 0.f;
+        v9[r][4] = on ? sv[r < R ? r : 0].y : 0.f;
+        v9[r][5] = on ? sq[r < R ? r : 0].x : 0.f;
+        v9[r][6] = on ? sq[r < R ? r : 0].y : 0.f;
+        v9[r][7] = on ? sc[r < R ? r : 0].x : 0.f;
+        v9[r][8] = on ? sc[r < R ? r : 0].y : 0.f;
+    }
+    rows4_sum<9>(v9, lane, t);
+    if (lane >= R) return;
     int i = rows[0];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const float w_ = warp_sum_f(W[r]);
-        const float su0_ = warp_sum_f(su[r].x), su1_ = warp_sum_f(su[r].y);
-        const float sv0_ = warp_sum_f(sv[r].x), sv1_ = warp_sum_f(sv[r].y);
-        const float vx_ = warp_sum_f(sq[r].x), vy_ = warp_sum_f(sq[r].y);
-        const float dot_ = warp_sum_f(sc[r].x), cross_ = warp_sum_f(sc[r].y);
-        if (r == 0 || lane == r) {
-            w = w_; su0 = su0_; su1 = su1_; sv0 = sv0_; sv1 = sv1_;
-            vx = vx_; vy = vy_; dot = dot_; cross = cross_;
-            i = rows[r];
-        }
-    }
-    if (lane >= R) return;
+    for (int r = 1; r < R; ++r)
+        if (lane == r) i = rows[r];
+    const float w = t[0], su0 = t[1], su1 = t[2], sv0 = t[3], sv1 = t[4];
+    float vx = t[5], vy = t[6], dot = t[7], cross = t[8];
     // move the moments from o to the row's centroid o + d: m_c = m_o - W d d'^T
     float du0 = 0.f, du1 = 0.f, dv0 = 0.f, dv1 = 0.f;
     if (w > 0.f) {
@@ -340,49 +377,60 @@ __device__ void residual_rows(const FitArgs &A, const FitSmem &S, const int *row
             As[r] = fmaf(w, qsi, As[r]);
         }
     }
-    // every lane receives every row's sums; lane r then evaluates row r's residual
-    float wl = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f, c4 = 0.f;
+    // lane r receives row r's sums and evaluates row r's residual
+    float v6[4][6], t[6];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const bool on = r < R;
+        const int rr = r < R ? r : 0;
+        v6[r][0] = on ? W[rr] : 0.f;
+        v6[r][1] = on ? A1[rr].x : 0.f;
+        v6[r][2] = on ? A1[rr].y : 0.f;
+        v6[r][3] = on ? A2[rr].x : 0.f;
+        v6[r][4] = on ? A2[rr].y : 0.f;
+        v6[r][5] = on ? As[rr] : 0.f;
+    }
+    rows4_sum<6>(v6, lane, t);
     int jl = rows[0];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int j = rows[r];
-        float w = warp_sum_f(W[r]);
-        float b0 = warp_sum_f(A1[r].x), b1 = warp_sum_f(A1[r].y);
-        float b2 = warp_sum_f(A2[r].x), b3 = warp_sum_f(A2[r].y);
-        float b4 = warp_sum_f(As[r]);
-        // the term i = j: offset (0, 0), so its weight is exactly 2^lp_j
-        const float wjj = ex2_ftz(S.lp[j]);
-        const float4 qj = S.q[j];
-        const float qsj = S.qs[j];
-        w -= wjj;
-        b0 = fmaf(-wjj, qj.x, b0);
-        b1 = fmaf(-wjj, qj.y, b1);
-        b2 = fmaf(-wjj, qj.z, b2);
-        b3 = fmaf(-wjj, qj.w, b3);
-        b4 = fmaf(-wjj, qsj, b4);
-        if (!(w >= wjj)) {            // warp-uniform: isolated match, sum over i != j exactly
-            float w_ = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f, d4 = 0.f;
-            for (int i = lane; i < n; i += 32) {
-                if (i == j) continue;
-                const float wi = gauss_w(__fadd2_rn(S.x[i], nxj[r]), S.lp[i]);
-                const float4 qi = S.q[i];
-                w_ += wi;
-                d0 = fmaf(wi, qi.x, d0);
-                d1 = fmaf(wi, qi.y, d1);
-                d2 = fmaf(wi, qi.z, d2);
-                d3 = fmaf(wi, qi.w, d3);
-                d4 = fmaf(wi, S.qs[i], d4);
-            }
-            w = warp_sum_f(w_);
-            b0 = warp_sum_f(d0);
-            b1 = warp_sum_f(d1);
-            b2 = warp_sum_f(d2);
-            b3 = warp_sum_f(d3);
-            b4 = warp_sum_f(d4);
+    for (int r = 1; r < R; ++r)
+        if ((lane & 3) == r) jl = rows[r];
+    // the term i = j: offset (0, 0), so its weight is exactly 2^lp_j
+    const float wjj = ex2_ftz(S.lp[jl]);
+    const float4 qj = S.q[jl];
+    const float qsj = S.qs[jl];
+    float wl = t[0] - wjj;
+    float c0 = fmaf(-wjj, qj.x, t[1]), c1 = fmaf(-wjj, qj.y, t[2]);
+    float c2 = fmaf(-wjj, qj.z, t[3]), c3 = fmaf(-wjj, qj.w, t[4]);
+    float c4 = fmaf(-wjj, qsj, t[5]);
+    // isolated matches (the rest of the weight below the own term): the sum over i != j
+    // taken again exactly, one flagged row at a time by the whole warp
+    unsigned slow = __ballot_sync(0xffffffffu, lane < R && !(wl >= wjj));
+    while (slow) {
+        const int r = __ffs(slow) - 1;
+        slow &= slow - 1;
+        const int j = __shfl_sync(0xffffffffu, jl, r);
+        const float2 nx = neg2(S.x[j]);
+        float w_ = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f, d4 = 0.f;
+        for (int i = lane; i < n; i += 32) {
+            if (i == j) continue;
+            const float wi = gauss_w(__fadd2_rn(S.x[i], nx), S.lp[i]);
+            const float4 qi = S.q[i];
+            w_ += wi;
+            d0 = fmaf(wi, qi.x, d0);
+            d1 = fmaf(wi, qi.y, d1);
+            d2 = fmaf(wi, qi.z, d2);
+            d3 = fmaf(wi, qi.w, d3);
+            d4 = fmaf(wi, S.qs[i], d4);
         }
-        if (r == 0 || lane == r) {
-            wl = w; c0 = b0; c1 = b1; c2 = b2; c3 = b3; c4 = b4;
-            jl = j;
+        w_ = warp_sum_f(w_);
+        d0 = warp_sum_f(d0);
+        d1 = warp_sum_f(d1);
+        d2 = warp_sum_f(d2);
+        d3 = warp_sum_f(d3);
+        d4 = warp_sum_f(d4);
+        if (lane == r) {
+            wl = w_; c0 = d0; c1 = d1; c2 = d2; c3 = d3; c4 = d4;
         }
     }
     if (lane >= R) return;
