@@ -91,6 +91,10 @@ def parse_args():
                     help='batched fields and their warps one after the other on the main stream '
                          '(default: the warps of a group on a second stream, beside the next '
                          "group's fields)")
+    ap.add_argument('--no-hoist-warm', action='store_true',
+                    help='every warm start just before its fits (default: the warm start of batch '
+                         "i + 1 on a third stream beside batch i's fields and warps, as it reads only "
+                         'the matches; its fits still follow the blend)')
     ap.add_argument('--fit-ctas', type=int, default=0,
                     help='CTAs of one fit launch, split evenly over its frames (default: every '
                          'co-resident CTA; 152 = one per SM, which leaves room beside the GEMM '
@@ -324,10 +328,11 @@ def run_gpu(args, ws, rank, local):
     B = max(1, min(args.batch or cfg.get('batch', 50), 64))
     overlap = args.overlap
     nbuf = 2 if overlap else 1            # fit outputs of two batches in flight
-    fit_outs_all = [[dict(q=torch.empty((n, 8), device=dev), c=torch.empty(n, device=dev),
+    c_all = torch.empty((nbuf, B, n), device=dev)       # a batch's weights in one block
+    fit_outs_all = [[dict(q=torch.empty((n, 8), device=dev), c=c_all[u, b],
                           p=torch.empty(n, device=dev),
                           info=torch.zeros(4, dtype=torch.int32, device=dev))
-                     for _ in range(B)] for _ in range(nbuf)]
+                     for b in range(B)] for u in range(nbuf)]
     batch_ws = [torch.empty(max(256, emdq.fit_batch_workspace_size([(src[0], dst[0])] * B)),
                             dtype=torch.uint8, device=dev) for _ in range(nbuf)]
     fit_ws_all = [torch.empty(emdq.fit_workspace_size(n), dtype=torch.uint8, device=dev)
@@ -336,6 +341,9 @@ def run_gpu(args, ws, rank, local):
     warm = (not args.no_warm) and os.path.exists(emdq.WARMSTART_PARAMS)
     warm_params = emdq.load_warmstart_params(dev) if warm else None
     warm_p0 = [[torch.empty(n, device=dev) for _ in range(B)] for _ in range(nbuf)]
+    hoist = warm and not args.no_hoist_warm and not overlap
+    warm_stream = torch.cuda.Stream(device=dev) if hoist else None
+    warm_done = {}                  # batch -> (p0 list, event) of a warm start issued ahead
 
     # field / warp pipeline: the fields of a group of frames (one emdq_field_batch call on the
     # main stream) into buffer set g % 2, their warps on the warp stream after that call, in
@@ -409,15 +417,32 @@ def run_gpu(args, ws, rank, local):
             wdone.record(wst)
             slot_free[slot] = wdone
 
+    def warm_ahead(bi, ks, s_of, d_of, after, ev=None, ready=None):
+        """The warm start of batch bi on the warm stream once `after` (the previous batch's
+        fits, the last reader of the p0 buffers) is done; ev[0] / ev[-1] bracket it."""
+        warm_stream.wait_event(after)
+        if ready: ready(bi, warm_stream)
+        if ev: ev[0].record(warm_stream)
+        p0s = emdq.warm_start([(s_of(k), d_of(k)) for k in ks], warm_params,
+                              outs=warm_p0[bi % nbuf][: len(ks)], stream=warm_stream)
+        if ev: ev[-1].record(warm_stream)
+        wd = torch.cuda.Event()
+        wd.record(warm_stream)
+        warm_done[bi] = (p0s, wd)
+
     def fit_batch(bi, ks, s_of, d_of, ev=None):
         """The fits of batch bi (frames ks) on the fit stream; returns its done event.
-        ev[1] is recorded between the warm start and the fit launch, ev[2] after the fits."""
+        ev[-1] is recorded after the warm start, ev[1] before the fit launch, ev[2] after it."""
         outs = fit_outs_all[bi % nbuf]
         with torch.cuda.stream(fit_stream):
             p0s = [None] * len(ks)
-            if warm:
+            if bi in warm_done:
+                p0s, wd = warm_done.pop(bi)
+                fit_stream.wait_event(wd)
+            elif warm:
                 p0s = emdq.warm_start([(s_of(k), d_of(k)) for k in ks], warm_params,
                                       outs=warm_p0[bi % nbuf][: len(ks)], stream=fit_stream)
+                if ev: ev[-1].record(fit_stream)
             if ev: ev[1].record(fit_stream)
             if B == 1:
                 emdq.emdq_fit(s_of(ks[0]), d_of(ks[0]), sc.w, sc.h, p0=p0s[0], out=outs[0],
@@ -459,26 +484,38 @@ def run_gpu(args, ws, rank, local):
         blended.record(stream)
         return blended
 
-    def run_batches(batches_, fr_of, s_of, d_of, evs=None):
+    def run_batches(batches_, fr_of, s_of, d_of, evs=None, ready=None, pre_blend=None,
+                    post_blend=None):
         """Fits of batch i+1 are issued before batch i is blended, so with two streams they
-        overlap; a batch's fit outputs are reused two batches later, after its blend."""
+        overlap; a batch's fit outputs are reused two batches later, after its blend.
+        ready(i, stream): makes the stream wait for batch i's matches; pre_blend(i) /
+        post_blend(i): issued just before / after batch i's blend (inputs arriving from the
+        host, results going back)."""
         blended = [None] * len(batches_)
         done = [None] * len(batches_)
+        def blend(i, ks):
+            if pre_blend: pre_blend(i)
+            blended[i] = blend_batch(i, ks, fr_of, s_of, done[i], evs[i] if evs else None)
+            if post_blend: post_blend(i)
         def issue_fit(i):
+            if ready: ready(i, fit_stream)
             if i >= nbuf and blended[i - nbuf] is not None:
                 fit_stream.wait_event(blended[i - nbuf])
-            if evs is not None:
+            if evs is not None and i not in warm_done:
                 evs[i][0].record(fit_stream)
             done[i] = fit_batch(i, batches_[i], s_of, d_of, evs[i] if evs is not None else None)
         issue_fit(0)
         for i, ks in enumerate(batches_):
             if i + 1 < len(batches_):
                 if not overlap:
-                    blended[i] = blend_batch(i, ks, fr_of, s_of, done[i], evs[i] if evs else None)
+                    if hoist:
+                        warm_ahead(i + 1, batches_[i + 1], s_of, d_of, done[i],
+                                   evs[i + 1] if evs is not None else None, ready)
+                    blend(i, ks)
                     issue_fit(i + 1)
                     continue
                 issue_fit(i + 1)
-            blended[i] = blend_batch(i, ks, fr_of, s_of, done[i], evs[i] if evs else None)
+            blend(i, ks)
         stream.wait_stream(fit_stream)
 
     batches = [list(range(k0, min(n_frames, k0 + B))) for k0 in range(0, n_frames, B)]
@@ -499,7 +536,7 @@ def run_gpu(args, ws, rank, local):
         # external: recorded as real event nodes when captured into a CUDA graph, so they
         # still time the replay
         kw = dict(external=True) if external else {}
-        return [[torch.cuda.Event(enable_timing=True, **kw) for _ in range(4 + 3 * len(ks))]
+        return [[torch.cuda.Event(enable_timing=True, **kw) for _ in range(5 + 3 * len(ks))]
                 for ks in batches]
 
     # per batch e[0]: its fits issued and e[1]: warm start done, e[2]: fits done (all on the
@@ -513,8 +550,8 @@ def run_gpu(args, ws, rank, local):
 
     def collect(step):
         for bi, e in enumerate(step):
-            nb = (len(e) - 4) // 3
-            warm_ms.append(e[0].elapsed_time(e[1]))
+            nb = (len(e) - 5) // 3
+            warm_ms.append(e[0].elapsed_time(e[-1]) if warm else 0.0)
             fit_ms.append(e[1].elapsed_time(e[2]))
             fit_launch_frames.append(batches[bi])
             prev = e[3]
@@ -540,6 +577,7 @@ def run_gpu(args, ws, rank, local):
         except Exception as ex:                      # capture refused: issue calls directly
             graph_note = f'capture failed, calls issued directly: {type(ex).__name__}: {ex}'[:300]
         stream, fit_stream = saved
+        warm_done.clear()
         torch.cuda.synchronize()
         if graph is not None:                        # one untimed replay
             flush.zero_()
@@ -585,7 +623,7 @@ def run_gpu(args, ws, rank, local):
         # step time: first fit issue -> last warp of the pass
         for step in evs:
             collect(step)
-            pass_ms.append(step[0][0].elapsed_time(step[-1][-1]))
+            pass_ms.append(step[0][0].elapsed_time(step[-1][-2]))
     elif gevs is None:
         # the graph's events could not be read: time the kernels on direct passes instead
         for step in [new_events() for _ in range(min(3, args.steps))]:
@@ -674,38 +712,103 @@ def run_gpu(args, ws, rank, local):
         unc['arap_smooth'] = dict(call='emdq_arap_smooth (Eqs. 21-22), 5 iterations', nodes=nn,
                                   ms_per_call=float(np.median(a_ms)))
 
-    # end to end through the public API from pinned host buffers: per frame the H2D copy of
-    # the frame and its matches, the three calls, the D2H of the fit record and weights
+    # end to end through the public API from pinned host buffers: every frame and its
+    # matches in pinned host memory; per batch one H2D copy of its frames and one of each
+    # match array (split where the host rows wrap) on a copy stream, into two device slots
+    # used alternately, so a batch's copies run beside the previous batch's compute; a
+    # batch's fits wait for its matches only, its blend for its frames; after its blend the
+    # D2H of its fit records and weights, and the copies of the batch two ahead into the
+    # freed slot
     e2e = None
     if not args.no_e2e:
-        nh = min(16, n_frames)
-        hf = [f.cpu().pin_memory() for f in frames[:nh]]
-        hs = [s.cpu().pin_memory() for s in src[:nh]]
-        hd = [d.cpu().pin_memory() for d in dst[:nh]]
+        nh = min(n_frames, 100)
+        hF = torch.stack([f.cpu() for f in frames[:nh]]).pin_memory()
+        hS = torch.stack([s_.cpu() for s_ in src[:nh]]).pin_memory()
+        hD = torch.stack([d_.cpu() for d_ in dst[:nh]]).pin_memory()
         e_steps = max(1, min(args.steps, 5))
         e_ms = []
-        dfr = [torch.empty_like(frames[0]) for _ in range(B)]
-        ds = [torch.empty_like(src[0]) for _ in range(B)]
-        dd = [torch.empty_like(dst[0]) for _ in range(B)]
-        h_infos = [torch.empty(4, dtype=torch.int32).pin_memory() for _ in range(B)]
-        h_cs = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(B)]
+        cstream = torch.cuda.Stream(device=dev)
+        dF = [torch.empty((B,) + tuple(frames[0].shape), dtype=frames[0].dtype, device=dev)
+              for _ in range(2)]
+        dS = [torch.empty((B, n, 2), dtype=torch.float32, device=dev) for _ in range(2)]
+        dD = [torch.empty((B, n, 2), dtype=torch.float32, device=dev) for _ in range(2)]
+        h_infos = torch.empty((n_frames, 4), dtype=torch.int32).pin_memory()
+        h_cs = torch.empty((n_frames, n), dtype=torch.float32).pin_memory()
+        pos = {k: (i % 2, j) for i, ks in enumerate(batches) for j, k in enumerate(ks)}
+
+        def host_runs(ks):
+            """(first slot row, first host row, count) of the contiguous runs of ks % nh."""
+            out, j0 = [], 0
+            for j in range(1, len(ks) + 1):
+                if j == len(ks) or ks[j] % nh != ks[j - 1] % nh + 1:
+                    out.append((j0, ks[j0] % nh, j - j0))
+                    j0 = j
+            return out
+
+        def e2e_step():
+            m_ev, f_ev, free = {}, {}, {}
+
+            def copy_in(i):
+                sl = i % 2
+                if sl in free:
+                    cstream.wait_event(free[sl])
+                with torch.cuda.stream(cstream):
+                    for j0, h0, cnt in host_runs(batches[i]):
+                        dS[sl][j0:j0 + cnt].copy_(hS[h0:h0 + cnt], non_blocking=True)
+                        dD[sl][j0:j0 + cnt].copy_(hD[h0:h0 + cnt], non_blocking=True)
+                    m_ev[i] = torch.cuda.Event()
+                    m_ev[i].record(cstream)
+                    for j0, h0, cnt in host_runs(batches[i]):
+                        dF[sl][j0:j0 + cnt].copy_(hF[h0:h0 + cnt], non_blocking=True)
+                    f_ev[i] = torch.cuda.Event()
+                    f_ev[i].record(cstream)
+
+            def post(i):
+                k0, cnt = batches[i][0], len(batches[i])
+                h_infos[k0:k0 + cnt].copy_(infos[k0:k0 + cnt], non_blocking=True)
+                h_cs[k0:k0 + cnt].copy_(c_all[i % nbuf, :cnt], non_blocking=True)
+                free[i % 2] = torch.cuda.Event()
+                free[i % 2].record(stream)
+                if i + 2 < len(batches):
+                    copy_in(i + 2)
+
+            cstream.wait_stream(stream)
+            for i in range(min(2, len(batches))):
+                copy_in(i)
+            fit_stream.wait_stream(stream)
+            run_batches(batches, lambda k: dF[pos[k][0]][pos[k][1]], lambda k: dS[pos[k][0]][pos[k][1]],
+                        lambda k: dD[pos[k][0]][pos[k][1]],
+                        ready=lambda i, st: st.wait_event(m_ev[i]),
+                        pre_blend=lambda i: stream.wait_event(f_ev[i]), post_blend=post)
+            stream.wait_stream(cstream)
+
+        # the step (copies in, calls, copies out) captured once into a CUDA graph like the
+        # device pass, every replay copying the pinned host inputs again; direct calls if the
+        # capture is refused
+        e_graph, e_note = None, None
+        if graph is not None:
+            saved = (stream, fit_stream)
+            try:
+                cap = torch.cuda.Stream(device=dev)
+                cap.wait_stream(torch.cuda.current_stream())
+                g2 = torch.cuda.CUDAGraph()
+                stream = fit_stream = cap
+                with torch.cuda.graph(g2, stream=cap):
+                    e2e_step()
+                e_graph = g2
+            except Exception as ex:
+                e_note = f'capture failed, calls issued directly: {type(ex).__name__}: {ex}'[:300]
+            stream, fit_stream = saved
+            warm_done.clear()
+            torch.cuda.synchronize()
         for i in range(1 + e_steps):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            for ks in batches:
-                # H2D of this batch's frames and matches, then the pipeline on device copies
-                for j, k in enumerate(ks):
-                    dfr[j].copy_(hf[k % nh], non_blocking=True)
-                    ds[j].copy_(hs[k % nh], non_blocking=True)
-                    dd[j].copy_(hd[k % nh], non_blocking=True)
-                fit_stream.wait_stream(stream)
-                pos = {k: j for j, k in enumerate(ks)}
-                run_batches([ks], lambda k: dfr[pos[k]], lambda k: ds[pos[k]], lambda k: dd[pos[k]])
-                outs = fit_outs_all[0]
-                for j in range(len(ks)):
-                    h_infos[j].copy_(outs[j]['info'], non_blocking=True)
-                    h_cs[j].copy_(outs[j]['c'], non_blocking=True)
+            if e_graph is not None:
+                e_graph.replay()
+            else:
+                e2e_step()
             b.record(stream)
             b.synchronize()
             if i >= 1:
@@ -715,7 +818,8 @@ def run_gpu(args, ws, rank, local):
         e2e = dict(value=job_mpix_per_s(ws, len(e_ms) * n_frames, sc.w, sc.h, e_total),
                    unit=UNIT, ms_per_frame=e_total / (len(e_ms) * n_frames),
                    h2d_bytes_per_step=int(n_frames * (frames[0].numel() + src[0].numel() * 8)),
-                   d2h_bytes_per_step=int(n_frames * (16 + 4 * n)))
+                   d2h_bytes_per_step=int(n_frames * (16 + 4 * n)), cuda_graph=e_graph is not None,
+                   **({'cuda_graph_note': e_note} if e_note else {}))
 
     # the plain FP32 GPU form of the same path, for the headline comparison: per frame
     # emdq_fit (no warm start) + the FP32 per-pixel field + warp, on 10 frames
@@ -824,6 +928,7 @@ def run_gpu(args, ws, rank, local):
                  'the warps on a second stream)')
                 if piped and prec == emdq.BF16 else f' + emdq_field ({args.precision}) + mosaic_warp')) +
               (', fits of the next batch on a second stream' if overlap else '') +
+              (', warm starts one batch ahead on a third stream' if hoist else '') +
               (', the pass replayed from one CUDA graph' if graph is not None else '')),
         batch=B, field_group=G, warm_start=warm, cuda_graph=graph is not None,
         **({'cuda_graph_note': graph_note} if graph_note else {}), wall_s=wall, roofline=roof,
