@@ -49,6 +49,40 @@ def test_field_parity_fitted_pair(emdq, orc, prec):
     assert err <= TOL[prec]
 
 
+def test_field_tiny_brute_force_8d_dq(emdq, orc):
+    """N = 3..8 on a 16x16 grid, the FP32 path against an independent 8-D dual-quaternion
+    blend (Kavan) in float64, not against the oracle.  (The BF16 path's worst-case operand
+    rounding on rows this far apart exceeds its tolerance; it is held to the oracle on the
+    workloads' transforms instead.)"""
+    from dq8 import axis_angle, dq_from_rotation_translation, dqb_point
+    rng = np.random.default_rng(16)
+    alpha = np.float32(0.01)
+    for trial in range(4):
+        n = int(rng.integers(3, 9))
+        src = rng.uniform(0, 16, (n, 2)).astype(np.float32)
+        ths = rng.uniform(-0.5, 0.5, n)
+        ts = rng.uniform(-20, 20, (n, 2))
+        ss = rng.uniform(0.8, 1.25, n)
+        c = rng.uniform(0.0, 1.0, n).astype(np.float32)
+        c[0] = 1.0
+        q8 = np.stack([[*orc.dq_from_rt(ths[i], ts[i, 0], ts[i, 1]), ss[i], 1.0, 0.0, 0.0]
+                       for i in range(n)])
+        reals, duals = zip(*[dq_from_rotation_translation(axis_angle([0, 0, 1], ths[i]),
+                                                          [ts[i, 0], ts[i, 1], 0.0])
+                             for i in range(n)])
+        reals, duals = np.array(reals), np.array(duals)
+        got = _gpu_field(emdq, q8, c, src, (0, 0, 16, 16), alpha, 0)
+        s64, c64 = src.astype(np.float64), c.astype(np.float64)
+        err = 0.0
+        for y in range(16):
+            for x in range(16):
+                w = c64 * np.exp(-float(alpha) * ((s64 - [x, y]) ** 2).sum(1))
+                want = dqb_point(w, ss, reals, duals, (x, y))
+                err = max(err, float(np.abs(got[y, x] - (want[:2] - [x, y])).max()))
+        print(f'n={n}: max error against the 8-D DQ blend {err:.2e} px')
+        assert err <= TOL[0]
+
+
 @pytest.mark.parametrize('prec', PRECISIONS, ids=['fp32', 'bf16'])
 def test_field_identical_transforms(emdq, orc, prec):
     rng = np.random.default_rng(2)
