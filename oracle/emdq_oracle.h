@@ -1,6 +1,6 @@
 /*
  * FP64 CPU oracle for the EMDQ field + mosaic path of "Real-time Nonrigid Mosaicking of
- * Laparoscopy Images" (Zhou & Jayender).  TEST INFRASTRUCTURE ONLY: it is the judge the
+ * Laparoscopy Images" (Zhou & Jayender).  TEST INFRASTRUCTURE ONLY: it is the reference the
  * CUDA path is checked against and the timed CPU baseline.  Only the tests, the smoke
  * check and the benchmark's CPU-baseline leg may load it; the product library never does,
  * and the two share no code.

@@ -12,7 +12,7 @@ in float32, the kernel's precision, as this is an integer decision):
     the translation that match j implies -- a consistency test that needs no fit, so it
     stays informative when many matches are outliers;
   - f2_k = log(1 + |x_k - x_j| / 1 px): the neighbour's distance, the scale against which
-    the network judges the residuals (a smooth field separates nearby matches' motions
+    the network weighs the residuals (a smooth field separates nearby matches' motions
     in proportion to their distance);
   - each group of 8 sorted ascending; features = [f1 (8), f2 (8)].
 Network: 16 -> 64 (ReLU) -> 64 (ReLU) -> 1 (logistic); loss: mean binary cross-entropy

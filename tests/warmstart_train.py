@@ -7,7 +7,7 @@ final posterior lets EM start where it would end).  Training runs on the GPU thr
 library's own forward/backward/Adam kernels (emdq_mlp_train_step), with a cosine-decayed
 learning rate.
 
-    python tests/warmstart_train.py --seeds 1000 --out gpurun_out/warmstart_mlp.npy
+    python tests/warmstart_train.py --seeds 1000 --out warmstart_mlp.npy
 
 writes the trained parameters (5313 float32) that the package ships as
 paper_2103_07414_gb300/warmstart_mlp.npy.  `evaluate` compares plain EM with the warm-started
@@ -122,7 +122,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--seeds', type=int, default=1000)
     ap.add_argument('--steps', type=int, default=3000)
-    ap.add_argument('--out', default='gpurun_out/warmstart_mlp.npy')
+    ap.add_argument('--out', default='warmstart_mlp.npy')
     args = ap.parse_args()
     import torch
     t0 = time.time()
