@@ -102,3 +102,83 @@ def test_new_node_warps_are_the_weighted_average(orc):
     q = a[:4] / math.hypot(a[0], a[1]) + b[:4] / math.hypot(b[0], b[1])
     np.testing.assert_allclose(mid[:4], q / math.hypot(q[0], q[1]), atol=1e-12)
     assert mid[4] == pytest.approx(1.05)
+
+
+def _jittered(orc, x0, rng):
+    return np.array([_row(orc, rng.uniform(0.97, 1.03), rng.normal(0.03, 0.03), *rng.normal([6.0, -4.0], 3))
+                     for _ in x0])
+
+
+def _average(wa, a, wb, b):
+    """Eq. 22's weighted average of two rows: the unit DQs and the scales with weights a, b."""
+    a = np.broadcast_to(np.asarray(a, float), (len(wa),))
+    b = np.broadcast_to(np.asarray(b, float), (len(wa),))
+    q = a[:, None] * wa[:, :4] / np.hypot(wa[:, 0], wa[:, 1])[:, None] + b[:, None] * wb[:, :4] / np.hypot(wb[:, 0], wb[:, 1])[:, None]
+    return q / np.hypot(q[:, 0], q[:, 1])[:, None], (a * wa[:, 4] + b * wb[:, 4]) / (a + b)
+
+
+def test_iterations_follow_eq22_and_eq21_with_per_node_lambda(orc):
+    """Per-node lambda = (1 + sigma^2)/101 away from 1: iteration 1 averages W_merge (weight 1)
+    with the neighbourhood fit of x_0 -> W_merge(x_0) (weight lambda); its Eq. 21 cost is
+    sum |W_merge(x_0) - W^1(x_0)|^2 + lambda |W_ARAP(x_0) - W^1(x_0)|^2; iteration 2 fits
+    x_0 -> W^1(x_0), the positions of the first iteration's warps, again averages with W_merge,
+    and is kept only if its cost does not rise."""
+    x0 = _lattice(35.0)
+    rng = np.random.default_rng(3)
+    w = _jittered(orc, x0, rng)
+    s2 = rng.uniform(0.0, 400.0, len(x0))
+    lam = (1.0 + s2) / 101.0
+    alpha = orc.alpha_for_frame(640, 480)
+    ones = np.ones(len(x0))
+    w1, c1 = orc.arap_smooth(x0, w, s2, alpha, max_iters=1)
+    fit1 = orc.mstep(x0, _pos(orc, w, x0), ones, alpha)['q8']
+    q, s = _average(w, ones, fit1, lam)
+    np.testing.assert_allclose(w1[:, :4], q, atol=1e-12)
+    np.testing.assert_allclose(w1[:, 4], s, atol=1e-12)
+    p1, pm, pa = _pos(orc, w1, x0), _pos(orc, w, x0), _pos(orc, fit1, x0)
+    cost = (((pm - p1) ** 2).sum(1) + lam * ((pa - p1) ** 2).sum(1)).sum()
+    assert c1[0] == pytest.approx(cost, rel=1e-9)
+    w2, c2 = orc.arap_smooth(x0, w, s2, alpha, max_iters=2)
+    fit2 = orc.mstep(x0, p1, ones, alpha)['q8']
+    q, s = _average(w, ones, fit2, lam)
+    cand = np.concatenate([q, s[:, None], np.tile([1.0, 0.0, 0.0], (len(s), 1))], 1)
+    pc, pa2 = _pos(orc, cand, x0), _pos(orc, fit2, x0)
+    cost2 = (((pm - pc) ** 2).sum(1) + lam * ((pa2 - pc) ** 2).sum(1)).sum()
+    assert c2[1] == pytest.approx(cost2, rel=1e-9)
+    if c2[1] > c2[0]:                                       # the cost rose: W^1 is kept
+        np.testing.assert_array_equal(w2, w1)
+    else:
+        np.testing.assert_allclose(w2, cand, atol=1e-12)
+
+
+def test_new_node_warp_moves_it_with_the_node_field(orc):
+    """Sec. III-E on warps that vary over the nodes: a new node at p takes the blend of the
+    node warps with weights exp(-alpha |p - x0_j|^2), so its warp maps p where the dense field
+    of the nodes (Eqs. 2-4 at the point, every node weight 1) does."""
+    x0 = _lattice(45.0)
+    rng = np.random.default_rng(4)
+    w = _jittered(orc, x0, rng)
+    alpha = orc.alpha_for_frame(640, 480)
+    pts = rng.uniform(-30, 670, (15, 2))
+    out = orc.node_init(x0, w, pts, alpha)
+    want = pts + orc.field_points(w, np.ones(len(x0)), x0, pts, alpha)
+    np.testing.assert_allclose(_pos(orc, out, pts), want, atol=1e-9)
+
+
+@pytest.mark.parametrize('w,h,spacing', [(640, 480, 40.0), (1280, 1024, 30.0), (1920, 1080, 55.0),
+                                         (500, 333, 37.0), (101, 77, 13.0), (257, 911, 21.5)])
+def test_hex_lattice_covers_every_frame_pixel(orc, w, h, spacing):
+    """Coverage at several frame sizes and spacings, the corners included: every pixel of the
+    frame is within the covering radius spacing/sqrt(3) of a node, and no node lies farther
+    than that radius from the frame."""
+    from scipy.spatial import cKDTree
+    x = orc.hex_nodes(w, h, spacing)
+    m = spacing / math.sqrt(3.0)
+    gx = np.unique(np.concatenate([np.arange(0, w, 3.0), [w - 1.0]]))
+    gy = np.unique(np.concatenate([np.arange(0, h, 3.0), [h - 1.0]]))
+    g = np.stack(np.meshgrid(gx, gy), -1).reshape(-1, 2)
+    d, _ = cKDTree(x).query(g)
+    assert d.max() <= m + 1e-9
+    ex = np.maximum(np.maximum(-x[:, 0], 0.0), x[:, 0] - (w - 1))
+    ey = np.maximum(np.maximum(-x[:, 1], 0.0), x[:, 1] - (h - 1))
+    assert (np.hypot(ex, ey) <= m + 1e-9).all()

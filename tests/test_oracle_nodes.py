@@ -200,3 +200,61 @@ def test_feature_uncertainty(orc):
     dst2[1] += [3.0, 4.0]
     got2 = orc.feature_uncertainty(src, dst2, q8, c, alpha, beta, s2)
     assert got2[1] == pytest.approx(s2[1] + 25.0, rel=1e-9)
+
+
+def _varied_rows(orc, rng, n):
+    return np.array([_row(orc, rng.uniform(0.9, 1.1), rng.uniform(-0.15, 0.15), *rng.uniform(-25, 25, 2))
+                     for _ in range(n)])
+
+
+def test_node_track_moves_each_node_with_the_field_at_its_position(orc):
+    """Eq. 5 on a field that varies over the image: a node's new warp maps x_0 to where the
+    EMDQ field (Eqs. 2-4, evaluated independently at points) takes the node's position at t-1,
+    p = W_old(x_0), not its reference position; Eq. 9 uses the field's scale at p."""
+    rng = np.random.default_rng(21)
+    n, nn = 80, 30
+    src = rng.uniform(0, 640, (n, 2))
+    q8 = _varied_rows(orc, rng, n)
+    c = np.where(rng.uniform(0, 1, n) < 0.8, rng.uniform(0.5, 1.0, n), 0.0)
+    x0 = rng.uniform(100, 540, (nn, 2))
+    w_old = np.array([_row(orc, rng.uniform(0.95, 1.05), rng.uniform(-0.1, 0.1), *rng.uniform(-60, 60, 2))
+                      for _ in range(nn)])
+    s2_old = rng.uniform(0.5, 5.0, nn)
+    alpha, beta = orc.alpha_for_frame(640, 480), orc.beta_for_frame(640, 480)
+    w_new, s2_new = orc.node_track(x0, w_old, s2_old, q8, c, src, alpha, beta)
+    for i in range(nn):
+        p = _apply(orc, w_old[i], x0[i:i + 1])
+        assert np.hypot(*(p[0] - x0[i])) > 5.0                 # the node has moved away from x_0
+        want = p + orc.field_points(q8, c, src, p, alpha)
+        np.testing.assert_allclose(_apply(orc, w_new[i], x0[i:i + 1]), want, atol=1e-9)
+        wgt = c * np.exp(-alpha * ((src - p[0]) ** 2).sum(1))
+        ds = (wgt * q8[:, 4]).sum() / wgt.sum()
+        du = orc.uncertainty_points(c, src, p, beta)[0]
+        assert s2_new[i] == pytest.approx(ds ** 2 * s2_old[i] + du, rel=1e-12)
+
+
+def test_gamma_scales_with_the_squared_frame_scale(orc):
+    """Sec. III-G: gamma is multiplied by 1/s^2, s = (w/480 + h/270)/2; at 960x540 s = 2."""
+    g = json.load(open(GOLDEN))['gamma']['value']
+    assert orc.gamma_for_frame(960, 540) == pytest.approx(g / 4.0, rel=1e-15)
+    assert orc.gamma_for_frame(240, 135) == pytest.approx(g * 4.0, rel=1e-15)
+
+
+def test_feature_uncertainty_of_an_inlier_on_a_varying_field(orc):
+    """Eq. 10's inlier term on a field that varies over the image: the squared distance from
+    y_j to where the field of the other matches (Eqs. 2-4 at the point, with match j removed)
+    takes x_j."""
+    rng = np.random.default_rng(22)
+    n = 60
+    src = rng.uniform(0, 640, (n, 2))
+    q8 = _varied_rows(orc, rng, n)
+    c = np.where(np.arange(n) % 5 == 0, 0.0, rng.uniform(0.6, 1.0, n))
+    dst = src + rng.normal(0, 4, (n, 2)) + [5.0, -3.0]
+    alpha, beta = orc.alpha_for_frame(640, 480), orc.beta_for_frame(640, 480)
+    s2 = rng.uniform(0.5, 3, n)
+    got = orc.feature_uncertainty(src, dst, q8, c, alpha, beta, s2)
+    for j in np.flatnonzero(c > 0)[:12]:
+        keep = np.arange(n) != j
+        pj = src[j:j + 1]
+        yhat = pj + orc.field_points(q8[keep], c[keep], src[keep], pj, alpha)
+        assert got[j] == pytest.approx(s2[j] + float(((dst[j] - yhat[0]) ** 2).sum()), rel=1e-9)
