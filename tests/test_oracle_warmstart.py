@@ -90,3 +90,7 @@ def test_features_on_a_translation_and_an_outlier():
     others = np.delete(np.arange(120), 7)
     assert f[7, :8].min() > f[others, 0].max()
     assert np.all(np.diff(f[:, :8], axis=1) >= 0) and np.all(np.diff(f[:, 8:], axis=1) >= 0)
+    # the distance features are those of the matches in the reference frame (x), whatever
+    # the motion: under a scaling by 2 they stay the nearest-neighbour distances of x
+    f = ws.features(x, 2.0 * x)
+    np.testing.assert_allclose(f[:, 8:], np.log1p(d[:, 1:]), rtol=0, atol=1e-4)
