@@ -194,7 +194,8 @@ def test_fit_iteration_cap_and_bad_input(orc):
 def test_first_posterior_is_the_gaussian_uniform_mixture(orc):
     """One EM iteration: the posterior of each match under a 2-D isotropic Gaussian inlier
     density (scipy) against a uniform outlier density over the frame, with the step-0
-    residuals, sigma^2 and the initial mixing weight 1/2."""
+    residuals, sigma^2 and the initial mixing weight 1/2 (with warm-start weights p0: step 0
+    weighted by p0 and the mixing weight the mean of p0)."""
     from scipy.stats import multivariate_normal
     sc = make_scene(4, 640, 480, 1)
     x, y, _ = make_matches(sc, 1, 120, 0.25, 1.0)
@@ -212,3 +213,14 @@ def test_first_posterior_is_the_gaussian_uniform_mixture(orc):
     assert r['dp_trace'][0] == pytest.approx(np.abs(want - 1).max(), rel=1e-10)
     # inlier weights of the output: the matches with posterior >= 1/2 keep it, others 0
     np.testing.assert_array_equal(r['c'], np.where(r['p'] >= 0.5, r['p'], 0.0))
+    # with warm-start weights p0: step 0 weighted by p0, the mixing weight its mean
+    p0 = np.random.default_rng(8).uniform(0.2, 1.0, 120)
+    m = orc.mstep(x, y, p0, alpha)
+    e0 = orc.residuals(x, y, p0, m['q8'], alpha)
+    s2 = max((p0 * e0).sum() / (2 * p0.sum()), 0.25)
+    gam = min(max(p0.mean(), 0.05), 0.95)
+    r = orc.fit(x, y, 640, 480, max_iters=1, p0=p0)
+    g = multivariate_normal(mean=[0, 0], cov=s2 * np.eye(2)).pdf(
+        np.stack([np.sqrt(e0), np.zeros(120)], 1))
+    want = gam * g / (gam * g + (1 - gam) / (640 * 480))
+    np.testing.assert_allclose(r['p'], want, rtol=1e-10, atol=1e-300)
