@@ -71,3 +71,57 @@ def test_host_only_entry_points(libemdq):
     assert rc == 1
     rc = L.mosaic_warp(None, 4, 4, 3, 12, None, 0, 0, 4, 4, None, 8, 8, 32, 0, 0, None)
     assert rc == 1
+
+
+def test_host_constants_and_node_lattice_against_the_oracle(libemdq, orc):
+    """Host-side parts of the node layer, no GPU: the frame-scaled coefficients of Sec. III-G
+    (alpha, beta, gamma = 2e-4, 3e-3, 5e-3 over s^2) and the breadth-first node lattice of
+    Sec. III-E, the same point set as the oracle's definition (order aside), starting at the
+    image centre."""
+    import numpy as np
+    from scipy.spatial import cKDTree
+    import paper_2103_07414_gb300 as pkg
+    L = pkg.lib()
+    for w, h in ((480, 270), (640, 480), (1280, 1024), (1920, 1080), (333, 917)):
+        assert L.emdq_alpha_for_frame(w, h) == pytest.approx(orc.alpha_for_frame(w, h), rel=1e-6)
+        assert L.emdq_beta_for_frame(w, h) == pytest.approx(orc.beta_for_frame(w, h), rel=1e-6)
+        assert L.emdq_gamma_for_frame(w, h) == pytest.approx(orc.gamma_for_frame(w, h), rel=1e-6)
+    for w, h, sp in ((640, 480, 40.0), (1280, 1024, 30.0), (1920, 1080, 55.0), (101, 77, 13.0),
+                     (257, 911, 21.5), (5, 3, 100.0)):
+        got = pkg.hex_nodes(w, h, sp).numpy().astype(np.float64)
+        want = orc.hex_nodes(w, h, sp)
+        assert got.shape == want.shape, (w, h, sp)
+        np.testing.assert_allclose(got[0], [(w - 1) / 2.0, (h - 1) / 2.0], atol=1e-4)
+        d, idx = cKDTree(want).query(got)
+        assert d.max() < 1e-3 and len(set(idx.tolist())) == len(want)
+    # a short output array receives the first nodes and the full count is returned
+    n = L.emdq_hex_nodes(640, 480, 40.0, None, 0)
+    buf = (ctypes.c_float * 30)()
+    assert L.emdq_hex_nodes(640, 480, 40.0, buf, 10) == n
+    np.testing.assert_allclose(np.frombuffer(buf, np.float32)[:20].reshape(10, 2),
+                               pkg.hex_nodes(640, 480, 40.0).numpy()[:10])
+    assert np.frombuffer(buf, np.float32)[20:].max() == 0.0      # nothing past the capacity
+    for bad in ((0, 480, 40.0), (640, -1, 40.0), (640, 480, 0.0), (640, 480, float('nan'))):
+        assert L.emdq_hex_nodes(*bad, None, 0) == -1
+
+
+def test_node_layer_argument_errors_on_the_host(libemdq):
+    """The node-layer calls reject bad arguments before any CUDA call (EMDQ_EINVAL = 1)."""
+    import paper_2103_07414_gb300 as pkg
+    L = pkg.lib()
+    f = ctypes.c_float
+    assert L.emdq_node_track(None, None, None, 5, None, None, None, 10, f(1e-4), f(1e-3), None,
+                             None, None) == 1
+    assert L.emdq_node_track(None, None, None, 5, None, None, None, 10, f(-1.0), f(1e-3), None,
+                             None, None) == 1
+    assert L.emdq_node_merge(None, None, None, None, None, None, 5, f(5e-3), None, None,
+                             None) == 1
+    assert L.emdq_node_merge(None, None, None, None, None, None, 5, f(0.0), None, None,
+                             None) == 1
+    assert L.emdq_node_restrict(None, None, 5, None, None, 3, f(3e-3), None, None) == 1
+    assert L.emdq_keyframe_distances(None, None, 5, 2, None, None) == 1
+    assert L.emdq_feature_uncertainty(None, None, 5, None, None, f(1e-4), f(3e-3), None, None,
+                                      None) == 1
+    assert L.emdq_node_init(None, None, 5, None, 3, f(1e-4), None, None) == 1
+    assert L.emdq_uncertainty(None, None, 5, 0, 0, 4, 4, f(3e-3), None, None) == 1
+    assert L.emdq_arap_smooth(None, None, None, 5, f(1e-4), 5, None, None, 0, None) == 1
