@@ -218,6 +218,17 @@ def job_mpix_per_s(ws: int, frames_per_rank: int, w: int, h: int, max_ms: float)
 # field at a pixel and its blend are per-pixel), so the bands assemble into the canvas an
 # untiled run leaves, bit for bit.
 
+def contiguous_runs(ks, nh: int) -> list:
+    """The frames ks of a batch as runs over host rows k % nh: (first batch slot, first host
+    row, count) for every stretch of consecutive host rows, so that each run is one copy."""
+    out, j0 = [], 0
+    for j in range(1, len(ks) + 1):
+        if j == len(ks) or ks[j] % nh != ks[j - 1] % nh + 1:
+            out.append((j0, ks[j0] % nh, j - j0))
+            j0 = j
+    return out
+
+
 def canvas_band(canvas_h: int, ws: int, rank: int) -> tuple:
     """Canvas rows [y0, y1) owned by `rank` (W bands of equal height, the last takes the rest)."""
     return canvas_h * rank // ws, canvas_h * (rank + 1) // ws
@@ -737,15 +748,6 @@ def run_gpu(args, ws, rank, local):
         h_cs = torch.empty((n_frames, n), dtype=torch.float32).pin_memory()
         pos = {k: (i % 2, j) for i, ks in enumerate(batches) for j, k in enumerate(ks)}
 
-        def host_runs(ks):
-            """(first slot row, first host row, count) of the contiguous runs of ks % nh."""
-            out, j0 = [], 0
-            for j in range(1, len(ks) + 1):
-                if j == len(ks) or ks[j] % nh != ks[j - 1] % nh + 1:
-                    out.append((j0, ks[j0] % nh, j - j0))
-                    j0 = j
-            return out
-
         def e2e_step():
             m_ev, f_ev, free = {}, {}, {}
 
@@ -754,12 +756,12 @@ def run_gpu(args, ws, rank, local):
                 if sl in free:
                     cstream.wait_event(free[sl])
                 with torch.cuda.stream(cstream):
-                    for j0, h0, cnt in host_runs(batches[i]):
+                    for j0, h0, cnt in contiguous_runs(batches[i], nh):
                         dS[sl][j0:j0 + cnt].copy_(hS[h0:h0 + cnt], non_blocking=True)
                         dD[sl][j0:j0 + cnt].copy_(hD[h0:h0 + cnt], non_blocking=True)
                     m_ev[i] = torch.cuda.Event()
                     m_ev[i].record(cstream)
-                    for j0, h0, cnt in host_runs(batches[i]):
+                    for j0, h0, cnt in contiguous_runs(batches[i], nh):
                         dF[sl][j0:j0 + cnt].copy_(hF[h0:h0 + cnt], non_blocking=True)
                     f_ev[i] = torch.cuda.Event()
                     f_ev[i].record(cstream)

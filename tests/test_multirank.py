@@ -85,3 +85,18 @@ def test_two_gloo_ranks_split_one_sequence_into_canvas_bands(tmp_path, orc):
         for t, p in zip(tiles, [t['clips'][k] for t in tiles]):
             if p is not None:
                 assert t['band'][0] <= p[1] + origin[1] and p[1] + p[3] + origin[1] <= t['band'][1]
+
+
+def test_contiguous_runs_of_host_rows():
+    """The end-to-end leg copies a batch's frames in runs of consecutive host rows k % nh:
+    one run when the batch does not wrap, two when it crosses a multiple of nh, every frame
+    exactly once and in batch order."""
+    import bench
+    assert bench.contiguous_runs(list(range(50, 100)), 100) == [(0, 50, 50)]
+    assert bench.contiguous_runs(list(range(96, 104)), 100) == [(0, 96, 4), (4, 0, 4)]
+    assert bench.contiguous_runs([7], 16) == [(0, 7, 1)]
+    for ks, nh in ((list(range(0, 64)), 16), (list(range(13, 77)), 20), (list(range(99, 101)), 100)):
+        runs = bench.contiguous_runs(ks, nh)
+        rows = [h + i for _, h, c in runs for i in range(c)]
+        slots = [j + i for j, _, c in runs for i in range(c)]
+        assert rows == [k % nh for k in ks] and slots == list(range(len(ks)))
