@@ -274,6 +274,16 @@ EMDQ_API emdq_status emdq_uncertainty(const float *c, const float *src, int n, i
  * and warp rows W_i (r_w, r_z, d_x, d_y, s, 1, 0, 0; the node's position at t is W_i(x_i,0))
  * and uncertainties sigma_i^2.
  *
+ * Common to emdq_node_track, emdq_node_merge, emdq_node_restrict, emdq_keyframe_distances,
+ * emdq_feature_uncertainty and emdq_node_init: every array is a caller-owned device buffer
+ * (positions nx2 float, 8-byte aligned; warp rows nx8 float, 16-byte aligned where a fit's q is
+ * taken) and the library allocates nothing; the call is asynchronous on `stream` and outputs may
+ * not alias inputs.  EMDQ_EINVAL, before any launch: a negative count, a coefficient (alpha,
+ * beta, gamma) that is not positive and finite, or a missing or misaligned array the call needs
+ * (emdq_keyframe_distances also needs nn >= 1, emdq_node_init nn >= 1).  A count of 0 for what
+ * is written (nodes, features, key frames, points) returns EMDQ_OK without work.  EMDQ_ECUDA if
+ * the launch fails.
+ *
  * emdq_node_track (Eq. 5, App. A, Eq. 9): for every node, p = W_i,t-1(x_i,0); dW = the Eqs. 2-3
  * blend at p of the t-1 -> t fit (q, c, src as emdq_field takes them; src in frame t-1);
  * W_i,t = f(W_i,t-1, dW), the warp with s_new q_new(x) = ds dq(s_old q_old(x)) (App. A);
