@@ -263,7 +263,8 @@ EMDQ_API emdq_status emdq_field_batch(const emdq_field_problem *problems, int co
  *   grid_*     the pixel window
  *   beta       > 0 (emdq_beta_for_frame gives the paper's value for a frame size)
  *   out        device, grid_h x grid_w float (written)
- * Returns EMDQ_EINVAL for bad arguments; an empty window writes nothing.
+ * Returns EMDQ_EINVAL for bad arguments, EMDQ_ENOTSUP for a window taller than 524,280 rows
+ * (65535 tiles of 8 rows); an empty window writes nothing.
  */
 EMDQ_API emdq_status emdq_uncertainty(const float *c, const float *src, int n, int grid_x0,
                                       int grid_y0, int grid_w, int grid_h, float beta, float *out,
@@ -358,6 +359,9 @@ EMDQ_API emdq_status emdq_node_init(const float *x0, const float *w, int nn, con
  *   w_merge   device, nn x 8 float warp rows; s2: device, nn float merged uncertainties
  *   w_out     device, nn x 8 float (16-byte aligned; written), not aliasing w_merge
  *   workspace device, emdq_arap_workspace_size(nn) bytes, 256-byte aligned
+ * Returns EMDQ_EINVAL for bad arguments, EMDQ_ENOTSUP above emdq_fit_max_n() nodes,
+ * EMDQ_EWORKSPACE for a missing, short or misaligned workspace (all before any launch), and
+ * EMDQ_ECUDA if a copy or launch fails.
  */
 EMDQ_API size_t      emdq_arap_workspace_size(int nn);
 EMDQ_API emdq_status emdq_arap_smooth(const float *x0, const float *w_merge, const float *s2,
