@@ -319,25 +319,35 @@ def fit(src, dst, frame_w: int, frame_h: int, alpha: float = 0.0, max_iters: int
                 dp_trace=trace[:iters.value].copy(), status=rc)
 
 
-def warp(frame: np.ndarray, disp: np.ndarray, grid, canvas: np.ndarray, origin) -> int:
-    """Blend one frame into canvas (uint8 [CH, CW, 4], modified in place)."""
-    frame = np.ascontiguousarray(frame, dtype=np.uint8)
+def _pitched(frame: np.ndarray):
+    """(uint8 [fh, fw, ch] array, row pitch in bytes): a view whose rows are tight but lie
+    further apart (a frame inside a wider buffer) keeps its pitch; anything else is copied."""
+    frame = np.asarray(frame)
     if frame.ndim == 2:
         frame = frame[:, :, None]
+    fh, fw, ch = frame.shape
+    if (frame.dtype == np.uint8 and frame.strides[2] == 1 and frame.strides[1] == ch and
+            frame.strides[0] >= fw * ch):
+        return frame, frame.strides[0]
+    frame = np.ascontiguousarray(frame, dtype=np.uint8)
+    return frame, fw * ch
+
+
+def warp(frame: np.ndarray, disp: np.ndarray, grid, canvas: np.ndarray, origin) -> int:
+    """Blend one frame into canvas (uint8 [CH, CW, 4], modified in place)."""
+    frame, pitch = _pitched(frame)
     fh, fw, ch = frame.shape
     disp = np.ascontiguousarray(disp, dtype=np.float32)
     assert canvas.dtype == np.uint8 and canvas.flags.c_contiguous and canvas.shape[2] == 4
     x0, y0, gw, gh = (int(v) for v in grid)
-    return lib().orc_warp(_p(frame), fw, fh, ch, fw * ch, _p(disp), x0, y0, gw, gh,
+    return lib().orc_warp(_p(frame), fw, fh, ch, pitch, _p(disp), x0, y0, gw, gh,
                           _p(canvas), canvas.shape[1], canvas.shape[0], canvas.shape[1] * 4,
                           int(origin[0]), int(origin[1]))
 
 
 def insert_reference(frame: np.ndarray, canvas: np.ndarray, origin) -> int:
-    frame = np.ascontiguousarray(frame, dtype=np.uint8)
-    if frame.ndim == 2:
-        frame = frame[:, :, None]
+    frame, pitch = _pitched(frame)
     fh, fw, ch = frame.shape
-    return lib().orc_insert_reference(_p(frame), fw, fh, ch, fw * ch, _p(canvas),
+    return lib().orc_insert_reference(_p(frame), fw, fh, ch, pitch, _p(canvas),
                                       canvas.shape[1], canvas.shape[0], canvas.shape[1] * 4,
                                       int(origin[0]), int(origin[1]))

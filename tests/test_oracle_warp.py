@@ -114,3 +114,50 @@ def test_insert_reference(orc):
     assert orc.insert_reference(f, cv, (2, 3)) == 0
     np.testing.assert_array_equal(cv[3:8, 2:8, :3], f)
     assert (cv[3:8, 2:8, 3] == 1).all() and cv[..., 3].sum() == 30
+
+
+def test_frame_rows_are_read_through_the_pitch(orc):
+    """A frame stored inside a wider buffer (rows further apart than w x channels bytes, other
+    data between them) warps and inserts exactly as the same frame stored tightly."""
+    rng = np.random.default_rng(5)
+    buf = rng.integers(0, 256, (20, 41, 3), dtype=np.uint8)     # 11 columns of other data per row
+    view = buf[:, :30]
+    tight = np.ascontiguousarray(view)
+    d = rng.uniform(-3, 3, (24, 36, 2)).astype(np.float32)
+    a, b = _canvas(), _canvas()
+    orc.warp(view, d, (-3, -2, 36, 24), a, (10, 12))
+    orc.warp(tight, d, (-3, -2, 36, 24), b, (10, 12))
+    np.testing.assert_array_equal(a, b)
+    assert (a[..., 3] > 0).sum() > 400
+    a, b = _canvas(), _canvas()
+    orc.insert_reference(view, a, (5, 6))
+    orc.insert_reference(tight, b, (5, 6))
+    np.testing.assert_array_equal(a, b)
+
+
+def test_rgb_channels_are_sampled_separately(orc):
+    """Three channels holding three different linear ramps: bilinear sampling is exact on each."""
+    ys, xs = np.mgrid[0:16, 0:16]
+    coef = [(5, 7, 10), (3, 2, 40), (9, 1, 5)]                       # maxima 190, 115, 155
+    frame = np.stack([a * xs + b * ys + c for a, b, c in coef], -1).astype(np.uint8)
+    rng = np.random.default_rng(6)
+    d = rng.uniform(-0.5, 0.5, (8, 8, 2)).astype(np.float32)
+    cv = _canvas(32, 32)
+    orc.warp(frame, d, (4, 4, 8, 8), cv, (0, 0))
+    for y in range(8):
+        for x in range(8):
+            ux = float(np.float32(np.float32(4 + x) + d[y, x, 0]))
+            uy = float(np.float32(np.float32(4 + y) + d[y, x, 1]))
+            for k, (a, b, c) in enumerate(coef):
+                assert cv[4 + y, 4 + x, k] == np.floor(a * ux + b * uy + c + 0.5)
+
+
+def test_sample_position_is_formed_in_float32(orc):
+    """The sample position u = p + d is rounded to FP32 before the coverage test (the kernel's
+    precision): 2^-22 past the last column rounds back onto it and is inside."""
+    frame = np.full((10, 10), 90, np.uint8)
+    cv = _canvas(16, 16)
+    d = np.zeros((1, 2, 2), np.float32)
+    d[0, :, 0] = 2.0 ** -22                 # p = 8: inside; p = 9: 9 + 2^-22 rounds to 9.0
+    orc.warp(frame, d, (8, 0, 2, 1), cv, (0, 0))
+    assert list(cv[0, 8:10, 3]) == [1, 1] and list(cv[0, 8:10, 0]) == [90, 90]
