@@ -295,6 +295,27 @@ MUTATIONS = [
     ('warp', 'clamp_hi', 'oracle/emdq_oracle.c',
      'return r < 0.0 ? 0.0 : (r > 255.0 ? 255.0 : r);',
      'return r < 0.0 ? 0.0 : r;'),
+    ('field', 'fld_noc', 'oracle/emdq_oracle.c',
+     '        double w = c[i] * exp(-alpha * (dx * dx + dy * dy));\n        sw += w;\n        ss += w * q8[8 * i + 4];',
+     '        double w = exp(-alpha * (dx * dx + dy * dy));\n        sw += w;\n        ss += w * q8[8 * i + 4];'),
+    ('field', 'fld_sdiv', 'oracle/emdq_oracle.c',
+     'orc_apply_warp(ss / sw, q, px, py, xp);',
+     'orc_apply_warp(ss, q, px, py, xp);'),
+    ('field', 'fld_sq_unw', 'oracle/emdq_oracle.c',
+     '        for (int k = 0; k < 4; ++k) sq[k] += w * q8[8 * i + k];\n    }\n    if (!(sw > 0.0) || !isfinite(sw)) {\n        out[0]',
+     '        for (int k = 0; k < 4; ++k) sq[k] += q8[8 * i + k];\n    }\n    if (!(sw > 0.0) || !isfinite(sw)) {\n        out[0]'),
+    ('field', 'fld_pos', 'oracle/emdq_oracle.c',
+     '    out[0] = xp[0] - px;',
+     '    out[0] = xp[0];'),
+    ('field', 'rot_sign', 'oracle/emdq_oracle.c',
+     '    out[0] = s * (c * px - sn * py + tx);',
+     '    out[0] = s * (c * px + sn * py + tx);'),
+    ('field', 'half_angle', 'oracle/emdq_oracle.c',
+     '    *th = 2.0 * atan2(r[3], r[0]);',
+     '    *th = atan2(r[3], r[0]);'),
+    ('field', 'fld_wx', 'oracle/emdq_oracle.c',
+     '        double dx = src[2 * i] - px, dy = src[2 * i + 1] - py;\n        double w = c[i] * exp(-alpha * (dx * dx + dy * dy));\n        sw += w;',
+     '        double dx = src[2 * i] - px, dy = src[2 * i + 1] - py;\n        double w = c[i] * exp(-alpha * (dx * dx));\n        sw += w;'),
 ]
 
 
@@ -324,7 +345,7 @@ def run_one(scratch: str, file: str, old: str, new: str) -> str:
 def main() -> int:
     ap = argparse.ArgumentParser(description=__doc__.split('\n')[0])
     ap.add_argument('--scratch', default=None, help='scratch directory (re-created per mistake)')
-    ap.add_argument('--only', default=None, help='one group: core, nodes, warmstart or warp')
+    ap.add_argument('--only', default=None, help='one group: core, field, nodes, warmstart or warp')
     ap.add_argument('--list', action='store_true', help='list the mistakes and exit')
     args = ap.parse_args()
     todo = [m for m in MUTATIONS if args.only in (None, m[0])]
