@@ -68,6 +68,7 @@ def lib():
             L.orc_node_track.argtypes = [P, P, P, I, P, P, P, I, D, D, P, P, I]
             L.orc_node_merge.argtypes = [P, P, P, P, P, P, I, D, P, P]
             L.orc_arap_smooth.argtypes = [P, P, P, I, D, I, P, P]
+            L.orc_arap_fit.argtypes = [P, P, I, D, P, P, P, P]
             L.orc_node_restrict.argtypes = [P, P, I, P, P, I, D, P]
             L.orc_node_init.argtypes = [P, P, I, P, I, D, P]
             L.orc_feature_uncertainty.argtypes = [P, P, I, P, P, D, D, P, P]
@@ -221,6 +222,15 @@ def arap_smooth(x0, w_merge, s2, alpha: float, max_iters: int = 5):
                                _p(w_out), _p(costs))
     assert rc == OK, rc
     return w_out, costs[:max_iters]
+
+
+def arap_fit(x0, xt, alpha: float):
+    """Sec. III-D, Eqs. 16-17 and ARAP1-3: every node's ARAP warp from the motion x0 -> xt."""
+    x0, xt = _d(x0), _d(xt)
+    nn = x0.shape[0]
+    s, th, t, q8 = np.empty(nn), np.empty(nn), np.empty((nn, 2)), np.empty((nn, 8))
+    rc = lib().orc_arap_fit(_p(x0), _p(xt), nn, float(alpha), _p(s), _p(th), _p(t), _p(q8))
+    return dict(s=s, theta=th, t=t, q8=q8, status=rc)
 
 
 def feature_uncertainty(src, dst, q8, c, alpha: float, beta: float, s2_prev) -> np.ndarray:

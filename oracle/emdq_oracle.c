@@ -24,16 +24,19 @@
  *   Eq. 6                     key-frame distance: mean over the nodes of |x_i,t - x_i,k|
  *   Sec. III-E                new nodes: a hexagonal lattice grown from the image centre; a new
  *                             node's warp is the ARAP-weighted average of the existing nodes'
- *   Sec. III-D, Eqs. 21-22    ARAP smoothing of the node warps (the ARAP warp of a node is the
- *                             weighted similarity fit of Eqs. 16-20 over the nodes with p = 1)
+ *   Sec. III-D, Eqs. 16-22    ARAP smoothing of the node warps; the ARAP warp of a node is
+ *                             Eqs. 16-17 and ARAP1-3 as printed: columns w_j^i (x_j - x_i)
+ *                             centred on node i, the weight inside each column
  *
  * Readings (the paper is silent, garbled or delegates to its EMDQ reference)
  *   - Eq. 3 blends q without normalising it; a blended DQ is normalised by the norm of its
  *     real part before use (dual-quaternion blending).  In the planar case the real and
  *     dual parts are orthogonal, so that is the whole normalisation.
- *   - Eq. 18's C_0, C_t put the weight inside each column, centred on node i; the M-step
- *     here centres on the weighted centroids and applies each weight once (weighted least
- *     squares).  The rotation is the det=+1 solution, written in 2-D closed form.
+ *   - Eqs. 16-17 put the weight inside each column of C_0, C_t, centred on node i.  The EM
+ *     M-step (EMDQ's own fit, which the paper does not print) centres on the weighted
+ *     centroids and applies each weight once (weighted least squares); the ARAP fit of
+ *     Sec. III-D keeps the printed columns.  In both the rotation is the det=+1 solution,
+ *     written in 2-D closed form.
  *   - The EM iteration itself (the paper treats EMDQ as a black box):
  *       step 0   p_j = 1 (or a given p0); M-step; leave-one-out residuals e_j;
  *                sigma^2 = max(sum p e / (2 sum p), floor); gamma = 0.5
@@ -396,10 +399,68 @@ static void apply_row(const double *w, double x, double y, double out[2])
     orc_apply_warp(w[4], q, x, y, out);
 }
 
+/* Sec. III-D, Eqs. 16-17 and ARAP1-3 as printed: the ARAP warp of every node i from the
+ * motion x_j,0 -> x_j,t of all nodes j.  The columns of C_0 and C_t are
+ * w_j^i (x_j,0 - x_i,0) and w_j^i (x_j,t - x_i,t), w_j^i = exp(-alpha |x_i,0 - x_j,0|^2):
+ * centred on node i, the weight inside each column, no column dropped (the paper drops
+ * columns of small weight only for speed).  ARAP1: R = U V^T from svd(C_t C_0^T), the det=+1
+ * rotation, in 2-D the angle atan2(M10 - M01, M00 + M11) of M = C_t C_0^T.  ARAP2: s =
+ * |vector(C_t)| / |vector(C_0)|.  ARAP3: t = the w-weighted average over j of
+ * x_j,t / s - R x_j,0.  Then the quaternion from R and t.  Writes s[nn], th[nn], t[nn*2] and
+ * q8[nn*8]; ORC_EDEGENERATE if some node has no spread. */
+int orc_arap_fit(const double *x0, const double *xt, int nn, double alpha, double *s, double *th,
+                 double *t, double *q8)
+{
+    if (nn < 1 || !x0 || !xt || !s || !th || !t || !q8) return ORC_EINVAL;
+    int bad = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(| : bad)
+#endif
+    for (int i = 0; i < nn; ++i) {
+        double M[2][2] = {{0.0, 0.0}, {0.0, 0.0}};   /* C_t C_0^T */
+        double n0 = 0.0, nt = 0.0;                    /* |vector(C_0)|^2, |vector(C_t)|^2 */
+        for (int j = 0; j < nn; ++j) {
+            double ex = x0[2 * j] - x0[2 * i], ey = x0[2 * j + 1] - x0[2 * i + 1];
+            double w = exp(-alpha * (ex * ex + ey * ey));
+            double c0[2] = {w * ex, w * ey};
+            double ct[2] = {w * (xt[2 * j] - xt[2 * i]), w * (xt[2 * j + 1] - xt[2 * i + 1])};
+            for (int r = 0; r < 2; ++r)
+                for (int k = 0; k < 2; ++k) M[r][k] += ct[r] * c0[k];
+            n0 += c0[0] * c0[0] + c0[1] * c0[1];
+            nt += ct[0] * ct[0] + ct[1] * ct[1];
+        }
+        double ang = atan2(M[1][0] - M[0][1], M[0][0] + M[1][1]);     /* ARAP1 */
+        double sc = sqrt(nt) / sqrt(n0);                             /* ARAP2 */
+        double cr = cos(ang), sr = sin(ang);
+        double W = 0.0, tx = 0.0, ty = 0.0;                          /* ARAP3 */
+        for (int j = 0; j < nn; ++j) {
+            double ex = x0[2 * j] - x0[2 * i], ey = x0[2 * j + 1] - x0[2 * i + 1];
+            double w = exp(-alpha * (ex * ex + ey * ey));
+            W += w;
+            tx += w * (xt[2 * j] / sc - (cr * x0[2 * j] - sr * x0[2 * j + 1]));
+            ty += w * (xt[2 * j + 1] / sc - (sr * x0[2 * j] + cr * x0[2 * j + 1]));
+        }
+        tx /= W;
+        ty /= W;
+        if (!(n0 > 0.0) || !isfinite(sc) || !isfinite(tx) || !isfinite(ty)) bad = 1;
+        s[i] = sc;
+        th[i] = ang;
+        t[2 * i] = tx;
+        t[2 * i + 1] = ty;
+        double q[4];
+        orc_dq_from_rt(ang, tx, ty, q);
+        for (int k = 0; k < 4; ++k) q8[8 * i + k] = q[k];
+        q8[8 * i + 4] = sc;
+        q8[8 * i + 5] = 1.0;
+        q8[8 * i + 6] = 0.0;
+        q8[8 * i + 7] = 0.0;
+    }
+    return bad ? ORC_EDEGENERATE : ORC_OK;
+}
+
 /* Sec. III-D: ARAP smoothing of the merged node warps.  Iteration k: the nodes' positions
- * x_t = W^{k-1}(x_0) (W^0 = W_merge); the ARAP warp of every node from its neighbours'
- * displacements (Eqs. ARAP1-3 = the weighted similarity fit of the M-step with p = 1 and
- * weights exp(-alpha |x_i,0 - x_j,0|^2)); W^k = (W_merge + lambda W_ARAP) / (1 + lambda)
+ * x_t = W^{k-1}(x_0) (W^0 = W_merge); the ARAP warp of every node from the nodes'
+ * displacements x_0 -> x_t (orc_arap_fit); W^k = (W_merge + lambda W_ARAP) / (1 + lambda)
  * (Eq. 22), lambda = (1 + sigma_i^2) / (1 + 100); the cost of Eq. 21 summed over the nodes,
  * sum |W_merge(x_0) - W^k(x_0)|^2 + lambda |W_ARAP(x_0) - W^k(x_0)|^2.  Stops after max_iters
  * iterations or when the cost increases (keeping the previous warps). */
@@ -408,20 +469,18 @@ int orc_arap_smooth(const double *x0, const double *w_merge, const double *s2, i
 {
     if (nn < 1 || !x0 || !w_merge || !s2 || !w_out || max_iters < 0) return ORC_EINVAL;
     double *xt = malloc(sizeof(double) * 2 * (size_t)nn);
-    double *ones = malloc(sizeof(double) * (size_t)nn);
     double *sc = malloc(sizeof(double) * (size_t)nn), *th = malloc(sizeof(double) * (size_t)nn);
     double *t = malloc(sizeof(double) * 2 * (size_t)nn), *wa = malloc(sizeof(double) * 8 * (size_t)nn);
     double *wk = malloc(sizeof(double) * 8 * (size_t)nn);
-    if (!xt || !ones || !sc || !th || !t || !wa || !wk) {
-        free(xt); free(ones); free(sc); free(th); free(t); free(wa); free(wk);
+    if (!xt || !sc || !th || !t || !wa || !wk) {
+        free(xt); free(sc); free(th); free(t); free(wa); free(wk);
         return ORC_EINVAL;
     }
     memcpy(w_out, w_merge, sizeof(double) * 8 * (size_t)nn);
-    for (int i = 0; i < nn; ++i) ones[i] = 1.0;
     double prev = INFINITY;
     for (int k = 1; k <= max_iters; ++k) {
         for (int i = 0; i < nn; ++i) apply_row(w_out + 8 * (size_t)i, x0[2 * i], x0[2 * i + 1], xt + 2 * i);
-        orc_mstep(x0, xt, ones, nn, alpha, sc, th, t, wa);
+        orc_arap_fit(x0, xt, nn, alpha, sc, th, t, wa);
         double cost = 0.0;
         for (int i = 0; i < nn; ++i) {
             const double lam = (1.0 + s2[i]) / (1.0 + 100.0);
@@ -438,7 +497,7 @@ int orc_arap_smooth(const double *x0, const double *w_merge, const double *s2, i
         prev = cost;
         memcpy(w_out, wk, sizeof(double) * 8 * (size_t)nn);
     }
-    free(xt); free(ones); free(sc); free(th); free(t); free(wa); free(wk);
+    free(xt); free(sc); free(th); free(t); free(wa); free(wk);
     return ORC_OK;
 }
 

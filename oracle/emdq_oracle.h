@@ -76,6 +76,11 @@ int orc_node_track(const double *x0, const double *w_old, const double *s2_old, 
 int orc_node_merge(const double *x0, const double *w_track, const double *s2_track,
                    const double *w_loop, const double *s2_loop, const double *w_key, int nn,
                    double gamma, double *w_out, double *s2_out);
+/* Sec. III-D, Eqs. 16-17 and ARAP1-3 as printed: the ARAP warp of every node from the nodes'
+ * motion x0 -> xt, with node-centred columns weighted inside (see the .c).  Writes s[nn],
+ * th[nn], t[nn*2] and q8[nn*8]; ORC_EDEGENERATE if some node has no spread. */
+int orc_arap_fit(const double *x0, const double *xt, int nn, double alpha, double *s, double *th,
+                 double *t, double *q8);
 /* Sec. III-D, Eqs. 21-22: ARAP smoothing of the node warps (see the .c); costs (max_iters,
  * may be NULL) receives the cost of every iteration run. */
 int orc_arap_smooth(const double *x0, const double *w_merge, const double *s2, int nn,

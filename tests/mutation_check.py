@@ -178,6 +178,31 @@ MUTATIONS = [
     ('nodes', 'arap_pos_merge', 'oracle/emdq_oracle.c',
      'for (int i = 0; i < nn; ++i) apply_row(w_out + 8 * (size_t)i,',
      'for (int i = 0; i < nn; ++i) apply_row(w_merge + 8 * (size_t)i,'),
+    ('nodes', 'arap_centroid', 'oracle/emdq_oracle.c',
+     'orc_arap_fit(x0, xt, nn, alpha, sc, th, t, wa);',
+     '{ double *one = malloc(sizeof(double) * (size_t)nn); for (int i = 0; i < nn; ++i) one[i] = 1.0;'
+     ' orc_mstep(x0, xt, one, nn, alpha, sc, th, t, wa); free(one); }'),
+    ('nodes', 'arap_w_once', 'oracle/emdq_oracle.c',
+     'double c0[2] = {w * ex, w * ey};',
+     'double c0[2] = {ex, ey};'),
+    ('nodes', 'arap_ct_x0', 'oracle/emdq_oracle.c',
+     'w * (xt[2 * j] - xt[2 * i]), w * (xt[2 * j + 1] - xt[2 * i + 1])',
+     'w * (xt[2 * j] - x0[2 * i]), w * (xt[2 * j + 1] - x0[2 * i + 1])'),
+    ('nodes', 'arap_s_inv', 'oracle/emdq_oracle.c',
+     'double sc = sqrt(nt) / sqrt(n0);',
+     'double sc = sqrt(n0) / sqrt(nt);'),
+    ('nodes', 'arap_angle', 'oracle/emdq_oracle.c',
+     'double ang = atan2(M[1][0] - M[0][1], M[0][0] + M[1][1]);',
+     'double ang = atan2(M[0][1] - M[1][0], M[0][0] + M[1][1]);'),
+    ('nodes', 'arap_M_transp', 'oracle/emdq_oracle.c',
+     'for (int k = 0; k < 2; ++k) M[r][k] += ct[r] * c0[k];',
+     'for (int k = 0; k < 2; ++k) M[r][k] += c0[r] * ct[k];'),
+    ('nodes', 'arap_t_w2', 'oracle/emdq_oracle.c',
+     '            W += w;\n            tx += w * (xt[2 * j] / sc',
+     '            w *= w;\n            W += w;\n            tx += w * (xt[2 * j] / sc'),
+    ('nodes', 'arap_t_nos', 'oracle/emdq_oracle.c',
+     'ty += w * (xt[2 * j + 1] / sc - (sr',
+     'ty += w * (xt[2 * j + 1] - (sr'),
     ('nodes', 'arap_cost_lam', 'oracle/emdq_oracle.c',
      'lam * ((pa[0] - pk[0])',
      '((pa[0] - pk[0])'),

@@ -39,16 +39,106 @@ def test_no_iteration_returns_the_merged_warps(orc):
     np.testing.assert_array_equal(out, w)
 
 
+def _hand_three_nodes():
+    """Eqs. 16-17 and ARAP1-3 worked by hand on three nodes x_0 = (0,0), (1,0), (0,1) that move
+    to x_t = (0,0), (2,0), (0,1) (a stretch along x), alpha = ln 2, so a node at distance 1
+    weighs 1/2 and one at distance sqrt(2) weighs 1/4.
+
+    Node 0: columns of C_0 (1/2, 0), (0, 1/2) and of C_t (1, 0), (0, 1/2) (its own column is
+    zero); C_t C_0^T = [[1/2, 0], [0, 1/4]], angle atan2(0, 3/4) = 0; s = sqrt(5/4) / sqrt(1/2)
+    = sqrt(5/2); t = [1 (0,0) + 1/2 (2/s - 1, 0) + 1/2 (0, 1/s - 1)] / 2.
+    Node 1: C_0 (-1/2, 0), (-1/4, 1/4); C_t (-1, 0), (-1/2, 1/4); C_t C_0^T = [[5/8, -1/8],
+    [-1/16, 1/16]], angle atan2(1/16, 11/16); s = sqrt(21/16) / sqrt(6/16) = sqrt(7/2);
+    t = [1/2 (0,0) + 1 (2/s - c, -sn) + 1/4 (sn, 1/s - c)] / (7/4).
+    Node 2: C_0 (0, -1/2), (1/4, -1/4); C_t (0, -1/2), (1/2, -1/4); C_t C_0^T = [[1/8, -1/8],
+    [-1/16, 5/16]], angle atan2(1/16, 7/16); s = sqrt(9/16) / sqrt(6/16) = sqrt(3/2);
+    t = [1/2 (0,0) + 1/4 (2/s - c, -sn) + 1 (sn, 1/s - c)] / (7/4)."""
+    out = []
+    s0 = math.sqrt(2.5)
+    out.append((s0, 0.0, ((2 / s0 - 1) / 4, (1 / s0 - 1) / 4)))
+    s1, a1 = math.sqrt(3.5), math.atan2(1.0, 11.0)
+    c, sn = math.cos(a1), math.sin(a1)
+    out.append((s1, a1, ((2 / s1 - c + sn / 4) / 1.75, (-sn + (1 / s1 - c) / 4) / 1.75)))
+    s2, a2 = math.sqrt(1.5), math.atan2(1.0, 7.0)
+    c, sn = math.cos(a2), math.sin(a2)
+    out.append((s2, a2, (((2 / s2 - c) / 4 + sn) / 1.75, (-sn / 4 + 1 / s2 - c) / 1.75)))
+    return out
+
+
+def test_arap_fit_worked_by_hand_on_three_nodes(orc):
+    """Sec. III-D as printed: node-centred columns with the weight inside each column (so C_t
+    C_0^T carries w^2), the scale as the norm ratio of those columns, the translation the
+    w-weighted average of x_t / s - R x_0.  Against values derived by hand."""
+    x0 = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    xt = np.array([[0.0, 0.0], [2.0, 0.0], [0.0, 1.0]])
+    got = orc.arap_fit(x0, xt, math.log(2.0))
+    assert got['status'] == 0
+    for i, (s, a, t) in enumerate(_hand_three_nodes()):
+        assert got['s'][i] == pytest.approx(s, abs=1e-13)
+        assert got['theta'][i] == pytest.approx(a, abs=1e-13)
+        np.testing.assert_allclose(got['t'][i], t, atol=1e-13)
+        np.testing.assert_allclose(got['q8'][i, :4], orc.dq_from_rt(a, *t), atol=1e-13)
+        assert got['q8'][i, 4] == pytest.approx(s, abs=1e-13)
+    # the centroid-centred, weight-once fit of the EM M-step differs on this case
+    m = orc.mstep(x0, xt, np.ones(3), math.log(2.0))
+    assert np.abs(m['theta'] - got['theta']).max() > 1e-2
+    assert np.abs(m['s'] - got['s']).max() > 1e-2
+
+
+def test_arap_fit_translation_is_the_weighted_average(orc):
+    """ARAP3 with the printed R and s: on random motion the translation equals the
+    exp(-alpha d^2)-weighted mean of x_t / s - R x_0 (every node j, itself with weight 1), and
+    R, s are invariant to a common shift of x_t (node-centred columns), which moves t by the
+    shift / s."""
+    rng = np.random.default_rng(7)
+    x0 = rng.uniform(0, 300, (12, 2))
+    xt = x0 + rng.normal(0, 4, (12, 2))
+    alpha = 1e-4
+    a = orc.arap_fit(x0, xt, alpha)
+    shift = np.array([13.0, -5.0])
+    b = orc.arap_fit(x0, xt + shift, alpha)
+    np.testing.assert_allclose(b['theta'], a['theta'], atol=1e-12)
+    np.testing.assert_allclose(b['s'], a['s'], rtol=1e-12)
+    np.testing.assert_allclose(b['t'], a['t'] + shift / a['s'][:, None], atol=1e-9)
+    for i in range(12):
+        w = np.exp(-alpha * ((x0 - x0[i]) ** 2).sum(1))
+        R = np.array([[math.cos(a['theta'][i]), -math.sin(a['theta'][i])],
+                      [math.sin(a['theta'][i]), math.cos(a['theta'][i])]])
+        v = xt / a['s'][i] - x0 @ R.T
+        np.testing.assert_allclose(a['t'][i], (w[:, None] * v).sum(0) / w.sum(), atol=1e-9)
+
+
+def test_arap_fit_rotation_from_the_svd(orc):
+    """ARAP1 via numpy's SVD on a rotated, anisotropically stretched lattice: R = U V^T of the
+    2 x 2 matrix (det > 0 here, so no reflection fix is involved) has the oracle's angle for
+    every node."""
+    x0 = _lattice(50.0, 300, 250)
+    th = 0.3
+    R0 = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    xt = (x0 * [1.2, 0.9]) @ R0.T + [5.0, 2.0]
+    alpha = 2e-4
+    got = orc.arap_fit(x0, xt, alpha)
+    for i in range(0, len(x0), 7):
+        w = np.exp(-alpha * ((x0 - x0[i]) ** 2).sum(1))
+        C0 = (w[:, None] * (x0 - x0[i])).T
+        Ct = (w[:, None] * (xt - xt[i])).T
+        U, _, Vt = np.linalg.svd(Ct @ C0.T)
+        assert np.linalg.det(U @ Vt) > 0
+        R = U @ Vt
+        assert math.atan2(R[1, 0], R[0, 0]) == pytest.approx(got['theta'][i], abs=1e-12)
+        assert got['s'][i] == pytest.approx(np.linalg.norm(Ct) / np.linalg.norm(C0), rel=1e-12)
+
+
 def test_first_iteration_is_eq22_with_the_neighbourhood_fit(orc):
-    """One iteration: lambda = (1 + sigma^2)/101 weights the ARAP warp, which is the weighted
-    similarity fit over the nodes (the M-step with p = 1) of x_0 -> W_merge(x_0)."""
+    """One iteration: lambda = (1 + sigma^2)/101 weights the ARAP warp, which is the ARAP fit
+    (Eqs. 16-17, ARAP1-3) of the nodes' motion x_0 -> W_merge(x_0)."""
     x0 = _lattice()
     rng = np.random.default_rng(1)
     w = np.array([_row(orc, rng.uniform(0.98, 1.02), rng.normal(0, 0.02), *rng.normal(0, 3, 2)) for _ in x0])
     s2 = np.full(len(x0), 100.0)                          # lambda = 1: the plain average
     alpha = orc.alpha_for_frame(640, 480)
     out, _ = orc.arap_smooth(x0, w, s2, alpha, max_iters=1)
-    fit = orc.mstep(x0, _pos(orc, w, x0), np.ones(len(x0)), alpha)['q8']
+    fit = orc.arap_fit(x0, _pos(orc, w, x0), alpha)['q8']
     q = w[:, :4] / np.hypot(w[:, 0], w[:, 1])[:, None] + fit[:, :4] / np.hypot(fit[:, 0], fit[:, 1])[:, None]
     np.testing.assert_allclose(out[:, :4], q / np.hypot(q[:, 0], q[:, 1])[:, None], atol=1e-12)
     np.testing.assert_allclose(out[:, 4], 0.5 * (w[:, 4] + fit[:, 4]), atol=1e-12)
@@ -119,7 +209,7 @@ def _average(wa, a, wb, b):
 
 def test_iterations_follow_eq22_and_eq21_with_per_node_lambda(orc):
     """Per-node lambda = (1 + sigma^2)/101 away from 1: iteration 1 averages W_merge (weight 1)
-    with the neighbourhood fit of x_0 -> W_merge(x_0) (weight lambda); its Eq. 21 cost is
+    with the ARAP fit of x_0 -> W_merge(x_0) (weight lambda); its Eq. 21 cost is
     sum |W_merge(x_0) - W^1(x_0)|^2 + lambda |W_ARAP(x_0) - W^1(x_0)|^2; iteration 2 fits
     x_0 -> W^1(x_0), the positions of the first iteration's warps, again averages with W_merge,
     and is kept only if its cost does not rise."""
@@ -131,7 +221,7 @@ def test_iterations_follow_eq22_and_eq21_with_per_node_lambda(orc):
     alpha = orc.alpha_for_frame(640, 480)
     ones = np.ones(len(x0))
     w1, c1 = orc.arap_smooth(x0, w, s2, alpha, max_iters=1)
-    fit1 = orc.mstep(x0, _pos(orc, w, x0), ones, alpha)['q8']
+    fit1 = orc.arap_fit(x0, _pos(orc, w, x0), alpha)['q8']
     q, s = _average(w, ones, fit1, lam)
     np.testing.assert_allclose(w1[:, :4], q, atol=1e-12)
     np.testing.assert_allclose(w1[:, 4], s, atol=1e-12)
@@ -139,7 +229,7 @@ def test_iterations_follow_eq22_and_eq21_with_per_node_lambda(orc):
     cost = (((pm - p1) ** 2).sum(1) + lam * ((pa - p1) ** 2).sum(1)).sum()
     assert c1[0] == pytest.approx(cost, rel=1e-9)
     w2, c2 = orc.arap_smooth(x0, w, s2, alpha, max_iters=2)
-    fit2 = orc.mstep(x0, p1, ones, alpha)['q8']
+    fit2 = orc.arap_fit(x0, p1, alpha)['q8']
     q, s = _average(w, ones, fit2, lam)
     cand = np.concatenate([q, s[:, None], np.tile([1.0, 0.0, 0.0], (len(s), 1))], 1)
     pc, pa2 = _pos(orc, cand, x0), _pos(orc, fit2, x0)
