@@ -721,7 +721,7 @@ def run_gpu(args, ws, rank, local):
             b.record(stream)
             b.synchronize()
             a_ms.append(a.elapsed_time(b))
-        unc['arap_smooth'] = dict(call='emdq_arap_smooth (Eqs. 21-22), 5 iterations', nodes=nn,
+        unc['arap_smooth'] = dict(call='emdq_arap_smooth (Eqs. 16-17, ARAP1-3, 21-22), 5 iterations', nodes=nn,
                                   ms_per_call=float(np.median(a_ms)))
 
     # end to end through the public API from pinned host buffers: every frame and its

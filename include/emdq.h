@@ -71,7 +71,14 @@ typedef struct {
     int   max_iters;     /* EM iteration cap (default 20) */
     float tol_p;         /* EM stops when max_j |p_j - p_j,prev| < tol_p (default 1e-3) */
     float sigma2_floor;  /* lower bound of the residual variance, px^2 (default 0.25) */
-    int   reserved[4];   /* zero */
+    int   reserved[4];   /* zero, except for two settings of the fit's bounded device-side
+                            waits (emdq_fit, emdq_fit_batch and the calls built on them):
+                            [0] > 0 lowers the bound of every grid-barrier wait to that many
+                            polls (default about 4 million, half a second; larger values keep
+                            the default); [1] != 0 is a test of that bound: every barrier then
+                            waits for one arrival more than the grid makes, no wait can end,
+                            every CTA gives up after its bound and the fit's info record says
+                            EMDQ_ETIMEOUT.  [2], [3]: zero. */
 } emdq_params;
 
 /* Device-side record a fit writes when it finishes (16 bytes, 4-byte aligned). */
@@ -349,19 +356,22 @@ EMDQ_API int         emdq_hex_nodes(int w, int h, float spacing, float *x0_out, 
 EMDQ_API emdq_status emdq_node_init(const float *x0, const float *w, int nn, const float *pts,
                                     int npts, float alpha, float *w_out, void *stream);
 
-/* emdq_arap_smooth (Sec. III-D, Eqs. 21-22): ARAP smoothing of the merged node warps.  At
- * most max_iters iterations (the paper uses 5) of: positions x_t = W(x_0); the ARAP warp of every
- * node, the similarity fit of Eqs. ARAP1-3 to its neighbours' displacements x_j,0 -> x_j,t with
- * weights exp(-alpha |x_i,0 - x_j,0|^2) (emdq_fit's step-0 M-step); W = (W_merge + lambda W_ARAP)
- * / (1 + lambda) with lambda = (1 + sigma_i^2) / 101; stopping, with the previous warps kept,
- * when the summed cost of Eq. 21 rises.  Runs on the stream without host synchronisation.
- *   x0        device, nn x 2 float (8-byte aligned), 3 <= nn <= emdq_fit_max_n()
+/* emdq_arap_smooth (Sec. III-D, Eqs. 16-17, ARAP1-3, 21-22): ARAP smoothing of the merged node
+ * warps.  At most max_iters iterations (the paper uses 5) of: positions x_t = W(x_0); the ARAP
+ * warp of every node i as printed -- C_0 and C_t with the columns w_j (x_j,0 - x_i,0) and
+ * w_j (x_j,t - x_i,t) over every node j, w_j = exp(-alpha |x_i,0 - x_j,0|^2), rotation U V^T of
+ * svd(C_t C_0^T) (the det = +1 solution), scale |C_t| / |C_0|, translation the w-weighted average
+ * of x_j,t / s - R x_j,0 (a node whose columns all vanish keeps its current warp as its ARAP
+ * warp); W = (W_merge + lambda W_ARAP) / (1 + lambda) with lambda = (1 + sigma_i^2) / 101;
+ * stopping, with the previous warps kept, when the summed cost of Eq. 21 rises.  Runs on the
+ * stream without host synchronisation.
+ *   x0        device, nn x 2 float (8-byte aligned), 3 <= nn <= 2^22
  *   w_merge   device, nn x 8 float warp rows; s2: device, nn float merged uncertainties
  *   w_out     device, nn x 8 float (16-byte aligned; written), not aliasing w_merge
  *   workspace device, emdq_arap_workspace_size(nn) bytes, 256-byte aligned
- * Returns EMDQ_EINVAL for bad arguments, EMDQ_ENOTSUP above emdq_fit_max_n() nodes,
- * EMDQ_EWORKSPACE for a missing, short or misaligned workspace (all before any launch), and
- * EMDQ_ECUDA if a copy or launch fails.
+ * Returns EMDQ_EINVAL for bad arguments, EMDQ_ENOTSUP above 2^22 nodes, EMDQ_EWORKSPACE for a
+ * missing, short or misaligned workspace (all before any launch), and EMDQ_ECUDA if a copy or
+ * launch fails.
  */
 EMDQ_API size_t      emdq_arap_workspace_size(int nn);
 EMDQ_API emdq_status emdq_arap_smooth(const float *x0, const float *w_merge, const float *s2,

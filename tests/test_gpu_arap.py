@@ -1,5 +1,7 @@
-"""GPU parity: ARAP smoothing of node warps (Sec. III-D, Eqs. 21-22) against the FP64 oracle
-on node lattices, the fixed point of a common similarity, and argument errors."""
+"""GPU parity: ARAP smoothing of node warps (Sec. III-D, Eqs. 16-17, ARAP1-3, 21-22) against the
+FP64 oracle on node lattices and on a few nodes moved anisotropically (where the printed,
+node-centred ARAP fit and a centroid-centred fit differ), the fixed point of a common
+similarity, and argument errors."""
 import math
 
 import numpy as np
@@ -48,6 +50,24 @@ def test_arap_against_the_oracle(emdq, orc, w, h, step, iters):
     dpos = np.abs(_pos(orc, got.cpu().numpy().astype(np.float64), _f32(x0)) - _pos(orc, want, _f32(x0))).max()
     print(f'{len(x0)} nodes, {iters} iterations: max position difference {dpos:.2e} px')
     assert dpos <= 2e-3
+
+
+@pytest.mark.parametrize('iters', [1, 3])
+def test_arap_few_nodes_stretched(emdq, orc, iters):
+    """Four nodes whose merged warps stretch them along x by different amounts: the ARAP warps
+    are far from a common similarity, so the node-centred, weight-squared fit of the printed
+    Eqs. 16-17 gives other warps than a centroid-centred one; the GPU follows the oracle."""
+    x0 = np.array([[100.0, 100.0], [160.0, 100.0], [100.0, 150.0], [170.0, 170.0]])
+    wm = np.array([_row(orc, 1.0, 0.0, 0.0, 0.0), _row(orc, 1.4, 0.0, -160.0 * 0.4 / 1.4, 5.0),
+                   _row(orc, 1.1, 0.05, 3.0, -4.0), _row(orc, 0.9, -0.1, 25.0, 30.0)])
+    s2 = np.array([10.0, 100.0, 300.0, 1.0])
+    alpha = np.float32(1.0 / 80.0 ** 2)
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    got = emdq.arap_smooth(f(x0), f(wm), f(s2), alpha, max_iters=iters).cpu().numpy().astype(np.float64)
+    want, _ = orc.arap_smooth(_f32(x0), _f32(wm), _f32(s2), float(alpha), iters)
+    dpos = np.abs(_pos(orc, got, x0) - _pos(orc, want, x0)).max()
+    np.testing.assert_allclose(got[:, 4], want[:, 4], rtol=2e-6)
+    assert dpos <= 1e-3, dpos
 
 
 def test_common_similarity_is_kept(emdq, orc):
