@@ -203,9 +203,11 @@ def _workspace(nbytes: int, device, given: torch.Tensor | None) -> torch.Tensor:
 def emdq_fit(src: torch.Tensor, dst: torch.Tensor, frame_w: int, frame_h: int, *,
              alpha: float = 0.0, max_iters: int = 20, tol_p: float = 1e-3,
              sigma2_floor: float = 0.25, p0: torch.Tensor | None = None,
-             out: dict | None = None, workspace: torch.Tensor | None = None, stream=None) -> dict:
+             out: dict | None = None, workspace: torch.Tensor | None = None, stream=None,
+             reserved=(0, 0, 0, 0)) -> dict:
     """EMDQ fit of n matches (src, dst: [n, 2] float32 CUDA).  Returns dict with q [n, 8],
-    c [n], p [n] and info [4] (int32 view: status, iters; float view: sigma2, gamma)."""
+    c [n], p [n] and info [4] (int32 view: status, iters; float view: sigma2, gamma).
+    reserved: emdq_params.reserved (the bounded waits' settings)."""
     n = src.shape[0]
     _check(src, 'src', torch.float32, (n, 2))
     _check(dst, 'dst', torch.float32, (n, 2))
@@ -218,7 +220,8 @@ def emdq_fit(src: torch.Tensor, dst: torch.Tensor, frame_w: int, frame_h: int, *
     p = o.get('p') if o.get('p') is not None else torch.empty(n, dtype=torch.float32, device=dev)
     info = o.get('info') if o.get('info') is not None else torch.zeros(4, dtype=torch.int32, device=dev)
     ws = _workspace(fit_workspace_size(n), dev, workspace)
-    prm = _Params(float(alpha), int(max_iters), float(tol_p), float(sigma2_floor), (ctypes.c_int * 4)())
+    prm = _Params(float(alpha), int(max_iters), float(tol_p), float(sigma2_floor),
+                  (ctypes.c_int * 4)(*reserved))
     rc = lib().emdq_fit(_ptr(src), _ptr(dst), n, int(frame_w), int(frame_h), ctypes.byref(prm),
                         _ptr(p0), _ptr(q), _ptr(c), _ptr(p), _ptr(info), _ptr(ws), ws.numel(),
                         _stream(stream))
@@ -255,7 +258,8 @@ def _batch_args(problems, outs):
 
 def emdq_fit_batch(problems, *, alpha: float = 0.0, max_iters: int = 20, tol_p: float = 1e-3,
                    sigma2_floor: float = 0.25, outs: list | None = None,
-                   workspace: torch.Tensor | None = None, ctas=None, stream=None) -> list:
+                   workspace: torch.Tensor | None = None, ctas=None, stream=None,
+                   reserved=(0, 0, 0, 0)) -> list:
     """Fit several independent problems in one launch.  problems: list of
     (src, dst, frame_w, frame_h) or (src, dst, frame_w, frame_h, p0).  ctas: optional CTAs per
     problem (default: in proportion to n^2).  Returns one dict per problem as emdq_fit does."""
@@ -264,7 +268,8 @@ def emdq_fit_batch(problems, *, alpha: float = 0.0, max_iters: int = 20, tol_p: 
     need = lib().emdq_fit_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), count)
     dev = problems[0][0].device
     ws = _workspace(need, dev, workspace)
-    prm = _Params(float(alpha), int(max_iters), float(tol_p), float(sigma2_floor), (ctypes.c_int * 4)())
+    prm = _Params(float(alpha), int(max_iters), float(tol_p), float(sigma2_floor),
+                  (ctypes.c_int * 4)(*reserved))
     split = None
     if ctas is not None:
         if len(ctas) != count:

@@ -63,6 +63,9 @@ struct FitArgs {
                          // its own M-step rows (workspace)
     unsigned *bar;       // barrier arrival counter, zero at launch (workspace)
     int *flag;           // device status, zero at launch (workspace)
+    unsigned spin_limit; // bound of every barrier wait (polls; kSpinLimit unless lowered)
+    unsigned bar_extra;  // arrivals a barrier waits for beyond the grid's (0; 1 only to test
+                         // the bounded wait: no barrier can then be passed)
 };
 
 struct FitSmem {
@@ -87,19 +90,21 @@ __device__ __forceinline__ FitSmem fit_smem(int n)
 }
 
 // Grid-wide barrier with a bounded wait.  `epoch` counts barriers passed (same in every
-// CTA).  Returns false if this CTA gave up waiting (the status flag is then ETIMEOUT).
-__device__ bool grid_barrier(unsigned *bar, int *flag, unsigned &epoch, int ncta)
+// CTA).  Waits for ncta + extra arrivals per barrier, at most spin_limit polls.  Returns
+// false if this CTA gave up waiting (the status flag is then ETIMEOUT).
+__device__ bool grid_barrier(unsigned *bar, int *flag, unsigned &epoch, int ncta,
+                             unsigned spin_limit, unsigned extra)
 {
     __shared__ int timed_out;
     __syncthreads();
     epoch += 1;
     if (threadIdx.x == 0) {
         timed_out = 0;
-        const unsigned target = epoch * static_cast<unsigned>(ncta);
+        const unsigned target = epoch * (static_cast<unsigned>(ncta) + extra);
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
         unsigned spins = 0;
         while (ld_acquire_gpu(bar) < target) {
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 raise_status(flag, EMDQ_ETIMEOUT);
                 timed_out = 1;
                 break;
@@ -475,7 +480,7 @@ __device__ float2 block_sum2(float a, float b, float2 *red)
 // Grid barrier, then the device status word as every thread of every CTA sees it.
 __device__ int barrier_status(const FitArgs &A, unsigned &epoch, int *s_flag, int ncta)
 {
-    const bool ok = grid_barrier(A.bar, A.flag, epoch, ncta);
+    const bool ok = grid_barrier(A.bar, A.flag, epoch, ncta, A.spin_limit, A.bar_extra);
     if (threadIdx.x == 0) *s_flag = ok ? __ldcg(A.flag) : (int)EMDQ_ETIMEOUT;
     __syncthreads();
     return *s_flag;
@@ -839,6 +844,19 @@ extern "C" size_t emdq_fit_workspace_size(int n)
     return fit_layout(n).total;
 }
 
+namespace {
+// The wait settings of emdq_params.reserved: [0] > 0 lowers the bound of every barrier wait to
+// that many polls; [1] != 0 makes every barrier wait for one arrival more than the grid makes,
+// so that no wait can end (a test of the bounded wait: the fit then reports ETIMEOUT).
+void wait_hooks(const emdq_params &P, FitArgs &A)
+{
+    A.spin_limit = P.reserved[0] > 0 && static_cast<unsigned>(P.reserved[0]) < kSpinLimit
+                       ? static_cast<unsigned>(P.reserved[0])
+                       : kSpinLimit;
+    A.bar_extra = P.reserved[1] != 0 ? 1u : 0u;
+}
+}  // namespace
+
 extern "C" emdq_status emdq_fit(const float *src, const float *dst, int n, int frame_w,
                                 int frame_h, const emdq_params *prm, const float *p0,
                                 float *q_out, float *c_out, float *p_out, emdq_fit_info *info,
@@ -893,6 +911,7 @@ extern "C" emdq_status emdq_fit(const float *src, const float *dst, int n, int f
     A.ord = reinterpret_cast<int *>(ws + L.ord_off);
     A.bar = reinterpret_cast<unsigned *>(ws + L.bar_off);
     A.flag = reinterpret_cast<int *>(ws + L.bar_off + 64);
+    wait_hooks(P, A);
 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -1054,6 +1073,7 @@ extern "C" emdq_status emdq_fit_batch_ex(const emdq_fit_problem *problems, int c
         A.info = q.info;
         A.bar = reinterpret_cast<unsigned *>(ws + 256 * (size_t)b);
         A.flag = reinterpret_cast<int *>(ws + 256 * (size_t)b + 64);
+        wait_hooks(P, A);
         const FitLayout L = fit_layout(q.n);
         A.e = reinterpret_cast<float *>(ws + off + L.e_off);
         A.cen = reinterpret_cast<float4 *>(ws + off + L.cen_off);
@@ -1188,8 +1208,18 @@ extern "C" emdq_status emdq_fit_noalloc(const float *src, const float *dst, int 
                                         float *q_out, float *c_out, float *p_out,
                                         emdq_fit_info *info, void *stream)
 {
+    // the argument errors of emdq_fit come first, so that a bad argument gives EMDQ_EINVAL
+    // whatever n is; only then is a valid n checked against the array (fit_layout grows with
+    // n, so n <= kFitMaxN bounds the scratch a fit needs)
+    emdq_params P;
+    emdq_default_params(&P);
+    if (prm) P = *prm;
+    if (!src || !dst || !q_out || !c_out || !info || n < 3 || frame_w < 1 || frame_h < 1 ||
+        P.max_iters < 0 || !(P.tol_p >= 0.f) || !(P.sigma2_floor > 0.f))
+        return EMDQ_EINVAL;
+    if (!aligned(src, 8) || !aligned(dst, 8) || !aligned(q_out, 16) || !aligned(info, 4))
+        return EMDQ_EINVAL;
     if (n > kFitMaxN) return EMDQ_ENOTSUP;   // beyond the fixed scratch array
-    if (fit_layout(n).total > kNoAllocScratchBytes) return EMDQ_ENOTSUP;
     void *ws = noalloc_scratch();
     if (!ws) return EMDQ_ECUDA;
     // emdq_fit clears the barrier counter and status word before its launch

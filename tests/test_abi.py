@@ -125,3 +125,21 @@ def test_node_layer_argument_errors_on_the_host(libemdq):
     assert L.emdq_node_init(None, None, 5, None, 3, f(1e-4), None, None) == 1
     assert L.emdq_uncertainty(None, None, 5, 0, 0, 4, 4, f(3e-3), None, None) == 1
     assert L.emdq_arap_smooth(None, None, None, 5, f(1e-4), 5, None, None, 0, None) == 1
+
+
+def test_noalloc_fit_argument_errors_on_the_host(libemdq):
+    """emdq_fit_noalloc reports emdq_fit's argument errors first (EMDQ_EINVAL = 1 for a negative
+    n or a null pointer, whatever n is) and EMDQ_ENOTSUP (7) only for a valid call with more
+    matches than its fixed array holds; all before any CUDA call."""
+    import paper_2103_07414_gb300 as pkg
+    L = pkg.lib()
+    P, I = ctypes.c_void_p, ctypes.c_int
+    L.emdq_fit_noalloc.restype = I
+    L.emdq_fit_noalloc.argtypes = [P, P, I, I, I, ctypes.POINTER(pkg._Params), P, P, P, P, P, P]
+    big = L.emdq_fit_max_n() + 1
+    fake = ctypes.c_void_p(1 << 20)           # aligned and never dereferenced: rejected first
+    assert L.emdq_fit_noalloc(None, None, -100, 640, 480, None, None, None, None, None, None, None) == 1
+    assert L.emdq_fit_noalloc(fake, fake, -100, 640, 480, None, None, fake, fake, None, fake, None) == 1
+    assert L.emdq_fit_noalloc(None, None, big, 640, 480, None, None, None, None, None, None, None) == 1
+    assert L.emdq_fit_noalloc(fake, fake, big, 640, 0, None, None, fake, fake, None, fake, None) == 1
+    assert L.emdq_fit_noalloc(fake, fake, big, 640, 480, None, None, fake, fake, None, fake, None) == 7

@@ -75,6 +75,31 @@ def test_noalloc_fit_matches_fit_on_two_calls_in_a_row(emdq):
         assert info['sigma2'] == pytest.approx(rinfo['sigma2'], rel=1e-5)
 
 
+def test_noalloc_calls_allocate_no_device_memory(emdq):
+    """After a first call (which looks up the array's address and loads the kernels), further
+    calls change neither what torch has allocated nor the device's free memory: the outputs
+    are the caller's, the scratch is the library's fixed array."""
+    sc, src, dst = _case('seq1280', 13)
+    rc, q, c, p, info = _noalloc_fit(emdq, src, dst, sc.w, sc.h)   # warm-up call
+    assert rc == 0
+    torch.cuda.synchronize()
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    prm = emdq._Params(0.0, 20, 1e-3, 0.25, (ctypes.c_int * 4)())
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    torch_before = torch.cuda.memory_allocated()
+    free_before, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        rc = emdq.lib().emdq_fit_noalloc(ptr(src), ptr(dst), src.shape[0], sc.w, sc.h,
+                                         ctypes.byref(prm), None, ptr(q), ptr(c), ptr(p),
+                                         ptr(info), stream)
+        assert rc == 0
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_allocated() == torch_before
+    assert free_after == free_before
+    assert emdq.read_fit_info(info)['status_name'] == 'OK'
+
+
 def test_noalloc_rejects_sizes_beyond_its_array(emdq):
     n = emdq.lib().emdq_fit_max_n() + 1
     src = torch.zeros((n, 2), device='cuda')
