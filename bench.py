@@ -67,6 +67,11 @@ def parse_args():
     ap.add_argument('--min-warmup-s', type=float, default=0.5,
                     help='keep warming up for at least this long (clock ramp)')
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--no-extras', action='store_true',
+                    help='skip the sub-results printed beside the default seq1280 line (latency '
+                         'mode, the 64-pair mixed batch, the 1920x1080 sequence)')
+    ap.add_argument('--no-beside', action='store_true',
+                    help='skip the calls timed beside the step (uncertainty, node tracking, ARAP)')
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--no-plain', action='store_true',
                     help='skip the plain FP32 GPU comparison (per-frame emdq_fit + FP32 per-pixel '
@@ -544,6 +549,19 @@ def run_gpu(args, ws, rank, local):
         one_pass()
         torch.cuda.synchronize()
         w += 1
+    # the field tile height for this sequence's field groups, chosen by the library's
+    # autotuner on the last batch's first group (recorded per size class, so the calls below,
+    # and the graph captured from them, use it)
+    field_tune = None
+    if piped and prec == emdq.BF16:
+        lb = len(batches) - 1
+        ks_t = batches[lb][:G]
+        fo_t = fit_outs_all[lb % nbuf]
+        probs_t = [(fo_t[j]['q'], fo_t[j]['c'], src[k], grids[k], alpha) for j, k in enumerate(ks_t)]
+        outs_t = [grp_disp[0][i][: grids[k][2] * grids[k][3] * 2].view(grids[k][3], grids[k][2], 2)
+                  for i, k in enumerate(ks_t)]
+        py, ms = emdq.field_batch_autotune(probs_t, reps=5, outs=outs_t, workspace=grp_ws[0])
+        field_tune = dict(tile_rows=py, ms_per_call=ms, frames_per_call=len(ks_t))
     def new_events(external=False):
         # external: recorded as real event nodes when captured into a CUDA graph, so they
         # still time the replay
@@ -654,7 +672,7 @@ def run_gpu(args, ws, rank, local):
     # the uncertainty map of Eq. 8 (not part of the step): emdq_uncertainty on every frame's
     # window from the fits of the first batch, timed alone on the main stream
     unc = None
-    if rank == 0:
+    if rank == 0 and not args.no_beside:
         fit_batch(0, batches[0], lambda k: src[k], lambda k: dst[k])
         torch.cuda.synchronize()
         outs0 = fit_outs_all[0]
@@ -933,7 +951,7 @@ def run_gpu(args, ws, rank, local):
               (', fits of the next batch on a second stream' if overlap else '') +
               (', warm starts one batch ahead on a third stream' if hoist else '') +
               (', the pass replayed from one CUDA graph' if graph is not None else '')),
-        batch=B, field_group=G, warm_start=warm, cuda_graph=graph is not None,
+        batch=B, field_group=G, field_autotune=field_tune, warm_start=warm, cuda_graph=graph is not None,
         **({'cuda_graph_note': graph_note} if graph_note else {}), wall_s=wall, roofline=roof,
         gpu_launches=(args.steps * sum(3 * ((len(ks) + G - 1) // G) for ks in batches) if G > 1 else
                       total_frames * (2 if fused else 3)) + args.steps * len(batches) * (2 if warm else 1),
@@ -1177,6 +1195,19 @@ def run_gpu_mixed(args, ws, rank, local):
         one_pass()
         torch.cuda.synchronize()
         w += 1
+    # the field tile height of every group, chosen by the library's autotuner (recorded per
+    # size class, so the step's emdq_field_batch calls use it)
+    field_tiles = []
+    for grp in groups:
+        disps = [grp_disp[0][i][: P[b]['grid'][2] * P[b]['grid'][3] * 2].view(
+                 P[b]['grid'][3], P[b]['grid'][2], 2) for i, b in enumerate(grp)]
+        py, _ = emdq.field_batch_autotune([(P[b]['out']['q'], P[b]['out']['c'], P[b]['src'], P[b]['grid'],
+                                            P[b]['alpha']) for b in grp], reps=3, outs=disps,
+                                          workspace=grp_ws[0])
+        field_tiles.append(py)
+    field_tiles = [emdq.field_batch_tile_rows([(P[b]['out']['q'], P[b]['out']['c'], P[b]['src'],
+                                                P[b]['grid'], P[b]['alpha']) for b in grp])
+                   for grp in groups]
     n_ev = 3 + 3 * len(P)
     graph, graph_note = None, None
     gev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(n_ev)]
@@ -1329,7 +1360,8 @@ def run_gpu_mixed(args, ws, rank, local):
              f'emdq_field_batch ({G} pairs per call, bf16), their mosaic_warp on a second stream' +
              (', the step replayed from one CUDA graph' if graph is not None else ''),
         cuda_graph=graph is not None, **({'cuda_graph_note': graph_note} if graph_note else {}),
-        autotune_fit_ms=tune_ms, mean_em_iters=float(np.mean(iters)), roofline=roof,
+        autotune_fit_ms=tune_ms, field_tile_rows=field_tiles, mean_em_iters=float(np.mean(iters)),
+        roofline=roof,
         gpu_launches=args.steps * (2 + 2 * len(groups) + len(P)), clocks=clk, e2e=e2e, fit_status=statuses,
         emdq_batch_device_ms=native_ms,
         p50_note='per step: the whole batch of 64 pairs is one unit of latency')
@@ -1372,12 +1404,12 @@ def cpu_baseline_mixed(args, budget_s=12.0):
     pairs = mixed_pairs(args.seed, MIXED_COUNT)
     t_start, sec, px, k = time.perf_counter(), 0.0, 0, 0
     while k < len(pairs) and (time.perf_counter() - t_start < budget_s or k == 0):
-        sec += oracle_pair(orc, pairs[k], 1 / 16)
+        sec += oracle_pair(orc, pairs[k], 1.0)
         px += pairs[k]['scene'].w * pairs[k]['scene'].h
         k += 1
     return dict(value=px / 1e6 / sec, unit=UNIT, cores=orc.max_threads(), kind='oracle',
-                sample=f'the first {k} pair(s) of the batch: full EM fit + field and warp on the '
-                       f'centred 1/16 of the window rows, extrapolated to the full window')
+                sample=f'the first {k} pair(s) of the batch: full EM fit + field and warp over '
+                       f'the whole window')
 
 
 def run_reference_mixed(args, ws, rank):
@@ -1392,7 +1424,7 @@ def run_reference_mixed(args, ws, rank):
     times, pxs = [], []
     for k in range(args.warmup + args.steps):
         p = pairs[k % len(pairs)]
-        t = oracle_pair(orc, p, 1 / 16)
+        t = oracle_pair(orc, p, 1.0)
         if k >= args.warmup:
             times.append(t)
             pxs.append(p['scene'].w * p['scene'].h)
@@ -1402,11 +1434,10 @@ def run_reference_mixed(args, ws, rank):
                 p50_frame_ms=float(np.median(times)) * 1e3, higher_is_better=True, scaling='weak',
                 vs_baseline=None, dtype='f64', data='synthetic',
                 config=dict(mixed_config(args, ws, pairs), precision='f64',
-                            sample='per step one pair of the batch: full EM fit + field and warp on '
-                                   '1/16 of the window rows, extrapolated'),
+                            sample='per step one pair of the batch: full EM fit + field and warp over '
+                                   'the whole window'),
                 cpu_baseline=dict(value=value, unit=UNIT, cores=orc.max_threads(), kind='oracle',
-                                  sample='per step one pair of the batch (1/16 of the window rows, '
-                                         'extrapolated)'),
+                                  sample='per step one pair of the batch, whole window'),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
 
 
@@ -1437,7 +1468,7 @@ def cpu_baseline(args, budget_s=12.0):
     origin = canvas_origin(cw, chh, sc.w, sc.h)
     canvas = np.zeros((chh, cw, 4), np.uint8)
     per_frame, t_start, frames = [], time.perf_counter(), 0
-    frac = 0.125
+    frac = 1.0              # whole windows, as the reference arm samples them
     while time.perf_counter() - t_start < budget_s or frames == 0:
         t = 1 + frames
         fr = render_frame(sc, t).numpy()
@@ -1448,8 +1479,8 @@ def cpu_baseline(args, budget_s=12.0):
         frames += 1
     sec = float(np.mean(per_frame))
     return dict(value=sc.w * sc.h / 1e6 / sec, unit=UNIT, cores=orc.max_threads(), kind='oracle',
-                sample=f'{frames} frame(s): full EM fit + field and warp on the centred 1/8 of '
-                       f'the window rows, extrapolated to the full window',
+                sample=f'{frames} frame(s) of the sequence: full EM fit + field and warp over '
+                       f'the whole window',
                 ms_per_frame=sec * 1e3)
 
 
@@ -1497,6 +1528,46 @@ def run_reference(args, ws, rank):
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
 
 
+SUB_KEYS = ('value', 'unit', 'ms_per_step', 'p50_frame_ms', 'dtype', 'config', 'path',
+            'kernel_ms_per_step', 'roofline', 'cpu_baseline', 'e2e', 'clocks', 'fit_status',
+            'mean_em_iters', 'gpu_launches', 'steps', 'warmup', 'p50_note', 'field_autotune',
+            'field_tile_rows')
+
+
+def sub_result(line: dict) -> dict:
+    return {k: line[k] for k in SUB_KEYS if k in line and line[k] is not None}
+
+
+def extras(args, local) -> dict:
+    """Results printed beside the default line (one GPU): the latency mode of the same
+    sequence (one frame in flight: warm start, fit, BF16 field and warp per frame), the
+    64-pair mixed batch and the 500-frame 1920x1080 sequence, each with its roofline object
+    and its own bounded oracle sample."""
+    import copy
+    import torch
+    out = {}
+
+    def sub(**kw):
+        a = copy.copy(args)
+        a.no_e2e, a.no_plain, a.no_beside, a.frames = True, True, True, 0
+        a.min_warmup_s = 0.2
+        for k, v in kw.items():
+            setattr(a, k, v)
+        return a
+
+    lat = run_gpu(sub(batch=1, field_group=1, steps=min(args.steps, 5), no_cpu_baseline=True), 1, 0, local)
+    out['latency_mode'] = dict(
+        sub_result(lat), mode='one frame in flight: per frame the learned warm start, emdq_fit, one '
+                              'BF16 field and one warp, the fields of frame k+1 beside the warp of frame k',
+        ms_per_frame=lat['ms_per_step'] / lat['config']['frames_per_step'])
+    torch.cuda.empty_cache()
+    out['batch64'] = sub_result(run_gpu_mixed(sub(workload='batch64', steps=min(args.steps, 10)), 1, 0, local))
+    torch.cuda.empty_cache()
+    out['seq1920'] = sub_result(run_gpu(sub(workload='seq1920', steps=2, batch=0), 1, 0, local))
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse_args()
     ws, rank, local = dist_env()
@@ -1510,6 +1581,11 @@ def main():
             line = run_gpu_tiled(args, ws, rank, local)
         else:
             line = run_gpu(args, ws, rank, local)
+        if (line is not None and ws == 1 and args.workload == 'seq1280' and args.shard == 'sequence'
+                and not args.no_extras and args.frames == 0):
+            ex = extras(args, local)
+            line['latency_mode'] = ex.pop('latency_mode')
+            line['other_workloads'] = ex
     if line is not None and rank == 0:
         print(json.dumps(line))
 

@@ -258,6 +258,35 @@ EMDQ_API size_t      emdq_field_batch_workspace_size(const emdq_field_problem *p
 EMDQ_API emdq_status emdq_field_batch(const emdq_field_problem *problems, int count,
                                       void *workspace, size_t workspace_bytes, void *stream);
 
+/* Tile shape of the batched field (no counterpart in the paper: a launch configuration).  The
+ * tensor-core GEMM covers each window in tiles of 128 pixels x `tile_rows` pixel rows (the MMA
+ * computes all six blend sums of the tile's rows at once, N = 6 tile_rows); tile_rows is one
+ * of 16, 24, 32 (the default) and 40.  Every tile height gives the same field bits (each
+ * output's accumulation over the matches is the same); it changes only the speed: taller
+ * tiles carry more multiply-adds per operand byte and per MMA, shorter ones make more tiles
+ * for windows too small to occupy every SM.
+ *   emdq_field_batch_ex        emdq_field_batch with an explicit tile height (EMDQ_ENOTSUP
+ *                              for another value); the same workspace size
+ *   emdq_field_batch_tile_rows the tile height emdq_field_batch uses for such a batch: the
+ *                              one the autotuner recorded for its size class (the mean window
+ *                              size and mean match count, each to a power of two, and the
+ *                              field count), else 32; -1 for bad arguments
+ *   emdq_field_batch_autotune  times every tile height on this batch (one untimed call, then
+ *                              `reps` calls each, CUDA events on `stream`; synchronises the
+ *                              stream), records the fastest for the batch's size class, and
+ *                              returns it in *tile_rows_out with its time per call in *ms_out
+ *                              (either may be NULL).  The outputs hold the last call's field.
+ *                              The record is per process and host-thread-safe.
+ */
+EMDQ_API emdq_status emdq_field_batch_ex(const emdq_field_problem *problems, int count,
+                                         int tile_rows, void *workspace, size_t workspace_bytes,
+                                         void *stream);
+EMDQ_API int         emdq_field_batch_tile_rows(const emdq_field_problem *problems, int count);
+EMDQ_API emdq_status emdq_field_batch_autotune(const emdq_field_problem *problems, int count,
+                                               void *workspace, size_t workspace_bytes,
+                                               void *stream, int reps, int *tile_rows_out,
+                                               float *ms_out);
+
 /* ------------------------------------------------------------------ emdq_uncertainty -
  * Uncertainty of the EMDQ field (Sec. III-C, Eq. 8): at every pixel p of the window
  * (reference coordinates, as emdq_field), the minimum over the feature inliers j (the

@@ -16,7 +16,8 @@ import torch
 
 from ._build import LIB as _LIB_PATH, build  # noqa: F401
 
-__all__ = ['emdq_fit', 'emdq_fit_batch', 'emdq_field', 'emdq_field_batch', 'mosaic_warp',
+__all__ = ['emdq_fit', 'emdq_fit_batch', 'emdq_field', 'emdq_field_batch', 'field_batch_autotune',
+           'field_batch_tile_rows', 'mosaic_warp',
            'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'emdq_uncertainty', 'node_track', 'node_merge', 'node_restrict', 'feature_uncertainty',
            'keyframe_distances', 'hex_nodes', 'node_init', 'arap_smooth',
            'mosaic_insert_reference',
@@ -112,6 +113,12 @@ def lib() -> ctypes.CDLL:
             L.emdq_field_batch_workspace_size.argtypes = [P, I]
             L.emdq_field_batch.restype = I
             L.emdq_field_batch.argtypes = [P, I, P, Z, P]
+            L.emdq_field_batch_ex.restype = I
+            L.emdq_field_batch_ex.argtypes = [P, I, I, P, Z, P]
+            L.emdq_field_batch_tile_rows.restype = I
+            L.emdq_field_batch_tile_rows.argtypes = [P, I]
+            L.emdq_field_batch_autotune.restype = I
+            L.emdq_field_batch_autotune.argtypes = [P, I, P, Z, P, I, P, P]
             L.emdq_field.restype = I
             L.emdq_field.argtypes = [P, P, P, I, I, I, I, I, F, I, P, P, Z, P]
             L.mosaic_warp_batch.restype = I
@@ -377,18 +384,48 @@ def field_batch_workspace_size(problems) -> int:
 
 
 def emdq_field_batch(problems, *, outs: list | None = None, workspace: torch.Tensor | None = None,
-                     stream=None) -> list:
+                     stream=None, tile_rows: int | None = None) -> list:
     """BF16 fields of several (q, c, src, grid, alpha) problems in one operand launch and one
-    persistent tensor-core launch; returns the [h, w, 2] fields (or fills outs)."""
+    persistent tensor-core launch; returns the [h, w, 2] fields (or fills outs).  tile_rows:
+    the GEMM's tile height (16, 24, 32 or 40); default: the autotuned or built-in choice."""
     count = len(problems)
     arr, res = _field_problems(problems, outs)
     need = lib().emdq_field_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), count)
     ws = _workspace(need, problems[0][0].device, workspace)
-    rc = lib().emdq_field_batch(ctypes.cast(arr, ctypes.c_void_p), count, _ptr(ws), ws.numel(),
-                                _stream(stream))
+    if tile_rows is None:
+        rc = lib().emdq_field_batch(ctypes.cast(arr, ctypes.c_void_p), count, _ptr(ws), ws.numel(),
+                                    _stream(stream))
+    else:
+        rc = lib().emdq_field_batch_ex(ctypes.cast(arr, ctypes.c_void_p), count, int(tile_rows),
+                                       _ptr(ws), ws.numel(), _stream(stream))
     if rc != 0:
         raise EmdqError('emdq_field_batch', rc)
     return res
+
+
+def field_batch_tile_rows(problems) -> int:
+    """The tile height emdq_field_batch uses for a batch like this one."""
+    arr = (_FieldProblem * max(1, len(problems)))()
+    for b, (q, c, src, grid, alpha) in enumerate(problems):
+        arr[b].n = int(c.shape[0])
+        arr[b].grid_w, arr[b].grid_h = int(grid[2]), int(grid[3])
+    return lib().emdq_field_batch_tile_rows(ctypes.cast(arr, ctypes.c_void_p), len(problems))
+
+
+def field_batch_autotune(problems, *, reps: int = 5, outs: list | None = None,
+                         workspace: torch.Tensor | None = None, stream=None) -> tuple:
+    """Time every tile height on this batch and record the fastest for its size class:
+    returns (tile_rows, ms per call).  Synchronises the stream."""
+    count = len(problems)
+    arr, res = _field_problems(problems, outs)
+    need = lib().emdq_field_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), count)
+    ws = _workspace(need, problems[0][0].device, workspace)
+    py, ms = ctypes.c_int(0), ctypes.c_float(0.0)
+    rc = lib().emdq_field_batch_autotune(ctypes.cast(arr, ctypes.c_void_p), count, _ptr(ws), ws.numel(),
+                                         _stream(stream), int(reps), ctypes.byref(py), ctypes.byref(ms))
+    if rc != 0:
+        raise EmdqError('emdq_field_batch_autotune', rc)
+    return py.value, ms.value
 
 
 def emdq_uncertainty(c: torch.Tensor, src: torch.Tensor, grid, beta: float, *,

@@ -29,6 +29,7 @@
 // the same pixel (the stand-alone warp's per-pixel code), so the field never visits HBM.
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -41,23 +42,36 @@
 namespace emdq {
 
 constexpr int kTcM = 128;                // pixels x per tile (MMA M, TMEM lanes)
-constexpr int kTcPY = 32;                // pixels y per tile
 constexpr int kTcCh = 6;                 // dr_w, dr_z, dd_x, dd_y, ds, weight
-constexpr int kTcN = kTcCh * kTcPY;      // MMA N = 192
 constexpr int kTcK = 64;                 // matches per stage: one 128-byte swizzle row
 constexpr int kTcStages = 4;
+// Pixel rows per tile (PY): MMA N = 6 PY.  32 is the default; the autotuner may choose
+// another per size class (more rows: more MACs per operand byte and per MMA; fewer rows:
+// more tiles, for windows too small to fill every SM).
+constexpr int kTcPYDefault = 32;
+constexpr int kTcPYChoices[4] = {16, 24, 32, 40};
+constexpr int kTcPYMax = 40;
 // Epilogue warps: two per TMEM lane quadrant for the field (each half of the pixel rows),
 // one for the fused field + warp, whose larger per-pixel state would not fit the register
 // file twice.  Threads: producer warp, MMA warp, epilogue warps.
 constexpr int tc_epi_warps(int ch) { return ch == 0 ? 8 : 4; }
 constexpr int tc_threads(int ch) { return 64 + 32 * tc_epi_warps(ch); }
 constexpr uint32_t kTcABytes = kTcM * kTcK * 2;
-constexpr uint32_t kTcBBytes = kTcN * kTcK * 2;
-constexpr uint32_t kTcStageBytes = kTcABytes + kTcBBytes;
-constexpr uint32_t kTcAccCols = 256;     // one accumulator: 192 columns used
+constexpr uint32_t kTcAccCols = 256;     // one accumulator: 6 PY <= 240 columns used
 constexpr uint32_t kTcTmemCols = 2 * kTcAccCols;
-constexpr size_t kTcSmemBytes = kTcStages * kTcStageBytes + 1024 /*barriers*/ + 1024 /*align*/;
-constexpr uint32_t kTcIdesc = tc::idesc_bf16_f32(kTcM, kTcN);
+
+template <int PY>
+struct TcShape {
+    static constexpr int N = kTcCh * PY;                       // MMA N
+    static constexpr uint32_t BBytes = N * kTcK * 2;
+    static constexpr uint32_t StageBytes = kTcABytes + BBytes;
+    static constexpr size_t SmemBytes = kTcStages * StageBytes + 1024 /*barriers*/ + 1024 /*align*/;
+    static constexpr uint32_t Idesc = tc::idesc_bf16_f32(kTcM, N);
+    static_assert(PY % 8 == 0 && N % 16 == 0 && N <= 240, "MMA N for M = 128 (one accumulator)");
+    static_assert(StageBytes % 1024 == 0 && kTcABytes % 1024 == 0, "SW128 tiles 1 KiB aligned");
+    static_assert((PY * 128) % 1024 == 0 || PY % 8 == 0, "8-row groups of the B planes");
+};
+constexpr size_t kTcSmemMax = TcShape<kTcPYMax>::SmemBytes;
 // Operand rows per prep block: each block pays one chain of dependent loads (the
 // nonzero-weight columns, the reference row, its columns' data) before writing rows, so
 // blocks take many rows; G rows carry six planes, so they take fewer than Ex rows.
@@ -66,24 +80,33 @@ constexpr int kPrepRowsB = 16;
 constexpr int kPrepThreads = 256;
 constexpr long long kWaitLimit = 4000000000LL;   // SM cycles (about 2 s)
 
-static_assert(kTcN % 16 == 0 && kTcN <= 256, "MMA N for M = 128");
-static_assert(kTcStageBytes % 1024 == 0 && kTcABytes % 1024 == 0, "SW128 tiles 1 KiB aligned");
-
 struct TcGeom {
     int kp;          // matches padded to kTcK
-    int wp, hp;      // grid padded to kTcM, kTcPY
+    int wp, hp;      // grid padded to kTcM, the tile's PY rows
     size_t a_bytes, b_bytes;
 };
 
-__host__ __device__ inline TcGeom tc_geom(int n, int gw, int gh)
+__host__ __device__ inline TcGeom tc_geom(int n, int gw, int gh, int py)
 {
     TcGeom g;
     g.kp = (n + kTcK - 1) / kTcK * kTcK;
     g.wp = (gw + kTcM - 1) / kTcM * kTcM;
-    g.hp = (gh + kTcPY - 1) / kTcPY * kTcPY;
+    g.hp = (gh + py - 1) / py * py;
     g.a_bytes = (size_t)g.wp * g.kp * 2;
     g.b_bytes = (size_t)kTcCh * g.hp * g.kp * 2;
     return g;
+}
+
+// Operand bytes of a problem for whichever tile height is chosen (the largest padding).
+inline size_t tc_operand_bytes_max(int n, int gw, int gh)
+{
+    size_t b = 0;
+    for (int py : kTcPYChoices) {
+        const TcGeom g = tc_geom(n, gw, gh, py);
+        const size_t v = ((g.a_bytes + 1023) / 1024 + (g.b_bytes + 1023) / 1024) * 1024;
+        b = v > b ? v : b;
+    }
+    return b;
 }
 
 // Columns of the GEMM: the matches with c_i != 0 in index order (a match of weight 0 adds
@@ -263,10 +286,14 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(const __gri
 }
 
 // CH = 0: write the displacement field; CH = 1 or 3: blend the frame into the canvas.
-template <int CH>
+// Tiles of kTcM x PY pixels.
+template <int CH, int PY>
 __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(const __grid_constant__ TcBatch Bt,
                                                                    MosaicArgs mos)
 {
+    using S = TcShape<PY>;
+    constexpr uint32_t kTcStageBytes = S::StageBytes;
+    constexpr uint32_t kTcIdesc = S::Idesc;
     const int ntiles = Bt.total_tiles;
     int *__restrict__ err = Bt.err;
     extern __shared__ uint8_t smem_raw[];
@@ -332,7 +359,7 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(const __gri
                     uint8_t *sa = smem + s * kTcStageBytes;
                     tc::mbar_arrive_expect_tx(full + s, kTcStageBytes);
                     tc::tma_load_2d(sa, &Bt.tmA[b], full + s, k * kTcK, tx * kTcM);
-                    tc::tma_load_3d(sa + kTcABytes, &Bt.tmB[b], full + s, k * kTcK, ty * kTcPY, 0);
+                    tc::tma_load_3d(sa + kTcABytes, &Bt.tmB[b], full + s, k * kTcK, ty * PY, 0);
                     *issued = chunk + 1;
                 }
             }
@@ -380,11 +407,14 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(const __gri
         }
     } else {
         // epilogue warps: TMEM lane quadrant q = warp % 4 (the lanes a warp may access),
-        // thread = pixel x of the tile; with 8 of them warps 2-5 take pixel rows 0-15 and
-        // warps 6-9 rows 16-31 (groups of 8 rows)
-        constexpr int kGroups = kTcPY / 8 / (tc_epi_warps(CH) / 4);
+        // thread = pixel x of the tile; the tile's groups of 8 pixel rows are dealt to the
+        // warp sets in turn (with 8 warps: warps 2-5 take groups 0, 2, ..., warps 6-9 groups
+        // 1, 3, ...)
+        constexpr int kSets = tc_epi_warps(CH) / 4;
+        constexpr int kAllGroups = PY / 8;
         const int q = warp & 3;
-        const int g0 = ((warp - 2) >> 2) * kGroups;
+        const int g0 = (warp - 2) >> 2;
+        const int g_last = g0 + (kAllGroups - 1 - g0) / kSets * kSets;
         int it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int a = it & 1;
@@ -403,12 +433,12 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(const __gri
             const float px = static_cast<float>(gx0 + x);
             const uint32_t lane_base = tmem + a * kTcAccCols + (static_cast<uint32_t>(q * 32) << 16);
 #pragma unroll 1
-            for (int g = g0; g < g0 + kGroups; ++g) {
+            for (int g = g0; g < kAllGroups; g += kSets) {
                 float F[kTcCh][8];
 #pragma unroll
-                for (int ch = 0; ch < kTcCh; ++ch) tc::tmem_ld_x8(lane_base + ch * kTcPY + g * 8, F[ch]);
+                for (int ch = 0; ch < kTcCh; ++ch) tc::tmem_ld_x8(lane_base + ch * PY + g * 8, F[ch]);
                 tc::tmem_wait_ld();
-                if (g == g0 + kGroups - 1) {
+                if (g == g_last) {
                     // the accumulator has been read: hand it back to the MMA warp
                     tc::fence_before_sync();
                     __syncwarp();
@@ -417,7 +447,7 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(const __gri
                 float2 d[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const float py = static_cast<float>(gy0 + ty * kTcPY + g * 8 + j);
+                    const float py = static_cast<float>(gy0 + ty * PY + g * 8 + j);
                     d[j] = make_float2(NAN, NAN);
                     const float w = F[5][j];
                     if (w > 0.f) {
@@ -428,7 +458,7 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(const __gri
                         d[j] = make_float2(xp.x - px, xp.y - py);
                     }
                 }
-                const int y0 = ty * kTcPY + g * 8;
+                const int y0 = ty * PY + g * 8;
                 if constexpr (CH == 0) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
@@ -506,8 +536,7 @@ constexpr size_t kErrBytes = 256;
 
 size_t field_tc_workspace_bytes(int n, int grid_w, int grid_h)
 {
-    const TcGeom g = tc_geom(n, grid_w, grid_h);
-    return kErrBytes + align_up(g.a_bytes, 1024) + align_up(g.b_bytes, 1024);
+    return kErrBytes + tc_operand_bytes_max(n, grid_w, grid_h);
 }
 
 namespace {
@@ -517,12 +546,12 @@ namespace {
 // needs 16).
 emdq_status tc_problem(TcBatch &Bt, int b, const float *q, const float *c, const float *src, int n,
                        int gx0, int gy0, int gw, int gh, float alpha, float *ref, int *kcount,
-                       float2 *disp, char *ops)
+                       float2 *disp, char *ops, int py)
 {
     auto encode = encode_fn();
     if (!encode) return EMDQ_ECUDA;
-    const TcGeom g = tc_geom(n, gw, gh);
-    if (g.hp / kTcPY > 65535 || g.hp > (1 << 24) || g.wp > (1 << 24)) return EMDQ_ENOTSUP;
+    const TcGeom g = tc_geom(n, gw, gh, py);
+    if (g.hp / py > 65535 || g.hp > (1 << 24) || g.wp > (1 << 24)) return EMDQ_ENOTSUP;
     auto *A = reinterpret_cast<__nv_bfloat162 *>(ops);
     auto *B = reinterpret_cast<__nv_bfloat162 *>(ops + align_up(g.a_bytes, 1024));
     {
@@ -538,7 +567,7 @@ emdq_status tc_problem(TcBatch &Bt, int b, const float *q, const float *c, const
     {
         cuuint64_t dims[3] = {(cuuint64_t)g.kp, (cuuint64_t)g.hp, (cuuint64_t)kTcCh};
         cuuint64_t strides[2] = {(cuuint64_t)g.kp * 2, (cuuint64_t)g.hp * g.kp * 2};
-        cuuint32_t box[3] = {kTcK, kTcPY, kTcCh};
+        cuuint32_t box[3] = {kTcK, (cuuint32_t)py, kTcCh};
         cuuint32_t estr[3] = {1, 1, 1};
         if (encode(&Bt.tmB[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, B, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -565,15 +594,30 @@ emdq_status tc_problem(TcBatch &Bt, int b, const float *q, const float *c, const
     P.disp = disp;
     P.ntx = g.wp / kTcM;
     P.tile0 = b == 0 ? 0 : Bt.p[b - 1].tile0 + Bt.p[b - 1].ntiles;
-    P.ntiles = P.ntx * (g.hp / kTcPY);
+    P.ntiles = P.ntx * (g.hp / py);
     P.block0 = b == 0 ? 0 : Bt.p[b - 1].block0 + Bt.p[b - 1].nblocks;
     P.a_blocks = g.wp / kPrepRowsA;
-    P.nblocks = P.a_blocks + g.hp / kPrepRowsB;
+    P.nblocks = P.a_blocks + (g.hp + kPrepRowsB - 1) / kPrepRowsB;
     return EMDQ_OK;
 }
 
-// The prep launch and the GEMM launch (a programmatic dependent of the prep) of a batch.
-emdq_status tc_run(TcBatch &Bt, int variant, const MosaicArgs *mos, cudaStream_t st)
+template <int CH, int PY>
+cudaError_t tc_set_smem()
+{
+    return cudaFuncSetAttribute(field_tc_kernel<CH, PY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TcShape<PY>::SmemBytes);
+}
+
+template <int CH, int PY>
+cudaError_t tc_launch_gemm(cudaLaunchConfig_t &cfg, const TcBatch &Bt, const MosaicArgs &mos)
+{
+    cfg.dynamicSmemBytes = TcShape<PY>::SmemBytes;
+    return cudaLaunchKernelEx(&cfg, field_tc_kernel<CH, PY>, Bt, mos);
+}
+
+// The prep launch and the GEMM launch (a programmatic dependent of the prep) of a batch
+// whose problems were filled for tiles of py pixel rows.
+emdq_status tc_run(TcBatch &Bt, int variant, int py, const MosaicArgs *mos, cudaStream_t st)
 {
     const DeviceInfo &D = device_info();
     static std::mutex mu;
@@ -581,12 +625,9 @@ emdq_status tc_run(TcBatch &Bt, int variant, const MosaicArgs *mos, cudaStream_t
     {
         std::lock_guard<std::mutex> lk(mu);
         if (attr_dev != D.device) {
-            if (cudaFuncSetAttribute(field_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kTcSmemBytes) != cudaSuccess ||
-                cudaFuncSetAttribute(field_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kTcSmemBytes) != cudaSuccess ||
-                cudaFuncSetAttribute(field_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kTcSmemBytes) != cudaSuccess)
+            if (tc_set_smem<0, 16>() != cudaSuccess || tc_set_smem<0, 24>() != cudaSuccess ||
+                tc_set_smem<0, 32>() != cudaSuccess || tc_set_smem<0, 40>() != cudaSuccess ||
+                tc_set_smem<1, 32>() != cudaSuccess || tc_set_smem<3, 32>() != cudaSuccess)
                 return EMDQ_ECUDA;
             attr_dev = D.device;
         }
@@ -602,7 +643,6 @@ emdq_status tc_run(TcBatch &Bt, int variant, const MosaicArgs *mos, cudaStream_t
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(tc_threads(variant));
-    cfg.dynamicSmemBytes = kTcSmemBytes;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -610,24 +650,80 @@ emdq_status tc_run(TcBatch &Bt, int variant, const MosaicArgs *mos, cudaStream_t
     cfg.attrs = at;
     cfg.numAttrs = 1;
     cudaError_t e;
-    if (variant == 0) e = cudaLaunchKernelEx(&cfg, field_tc_kernel<0>, Bt, none);
-    else if (variant == 1) e = cudaLaunchKernelEx(&cfg, field_tc_kernel<1>, Bt, *mos);
-    else e = cudaLaunchKernelEx(&cfg, field_tc_kernel<3>, Bt, *mos);
+    if (variant == 0) {
+        switch (py) {
+        case 16: e = tc_launch_gemm<0, 16>(cfg, Bt, none); break;
+        case 24: e = tc_launch_gemm<0, 24>(cfg, Bt, none); break;
+        case 40: e = tc_launch_gemm<0, 40>(cfg, Bt, none); break;
+        default: e = tc_launch_gemm<0, 32>(cfg, Bt, none); break;
+        }
+    } else if (variant == 1) {
+        e = tc_launch_gemm<1, 32>(cfg, Bt, *mos);
+    } else {
+        e = tc_launch_gemm<3, 32>(cfg, Bt, *mos);
+    }
     return e == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }
 
 bool tc_device_ok()
 {
     const DeviceInfo &D = device_info();
-    return D.device >= 0 && D.cc_major == 10 && D.smem_optin >= kTcSmemBytes;
+    return D.device >= 0 && D.cc_major == 10 && D.smem_optin >= kTcSmemMax;
+}
+
+bool tc_py_ok(int py)
+{
+    for (int c : kTcPYChoices)
+        if (c == py) return true;
+    return false;
+}
+
+// The tile height chosen for a batch: the autotuner's choice for the batch's size class
+// (mean window pixels and mean match count, each to a power of two), else the default.
+struct TileChoice {
+    int key, py;
+};
+std::mutex g_tile_mu;
+std::vector<TileChoice> g_tile_choices;
+
+int tile_class(const emdq_field_problem *problems, int count)
+{
+    double px = 0.0, n = 0.0;
+    for (int b = 0; b < count; ++b) {
+        px += (double)problems[b].grid_w * problems[b].grid_h;
+        n += problems[b].n;
+    }
+    px /= count;
+    n /= count;
+    const int lp = px > 1.0 ? (int)std::floor(std::log2(px)) : 0;
+    const int ln = n > 1.0 ? (int)std::floor(std::log2(n)) : 0;
+    return (lp << 8) | (ln << 3) | (count > 7 ? 7 : count);
+}
+
+int chosen_tile_rows(int key)
+{
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    for (const TileChoice &t : g_tile_choices)
+        if (t.key == key) return t.py;
+    return kTcPYDefault;
+}
+
+void record_tile_rows(int key, int py)
+{
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    for (TileChoice &t : g_tile_choices)
+        if (t.key == key) {
+            t.py = py;
+            return;
+        }
+    g_tile_choices.push_back({key, py});
 }
 
 // Batch workspace: 1024 bytes (error word at 0), then per problem 1024 bytes (reference row
 // at 0, column count at 64) and its 1024-aligned operands.
 size_t batch_problem_bytes(int n, int gw, int gh)
 {
-    const TcGeom g = tc_geom(n, gw, gh);
-    return 1024 + align_up(g.a_bytes, 1024) + align_up(g.b_bytes, 1024);
+    return 1024 + tc_operand_bytes_max(n, gw, gh);
 }
 
 }  // namespace
@@ -646,10 +742,10 @@ emdq_status field_tc_launch(const float *q, const float *c, const float *src, in
     Bt.count = 1;
     Bt.err = reinterpret_cast<int *>(ws);
     int *kcount = Bt.err + 1;                 // written by the prep kernel, read by the GEMM
-    const emdq_status rc =
-        tc_problem(Bt, 0, q, c, src, n, gx0, gy0, gw, gh, alpha, ref, kcount, disp, ws + kErrBytes);
+    const emdq_status rc = tc_problem(Bt, 0, q, c, src, n, gx0, gy0, gw, gh, alpha, ref, kcount,
+                                      disp, ws + kErrBytes, kTcPYDefault);
     if (rc != EMDQ_OK) return rc;
-    return tc_run(Bt, variant, mos, st);
+    return tc_run(Bt, variant, kTcPYDefault, mos, st);
 }
 
 extern "C" size_t emdq_field_batch_workspace_size(const emdq_field_problem *problems, int count)
@@ -663,11 +759,13 @@ extern "C" size_t emdq_field_batch_workspace_size(const emdq_field_problem *prob
     return total;
 }
 
-extern "C" emdq_status emdq_field_batch(const emdq_field_problem *problems, int count,
-                                        void *workspace, size_t workspace_bytes, void *stream)
+namespace {
+
+emdq_status field_batch_run(const emdq_field_problem *problems, int count, int py, void *workspace,
+                            size_t workspace_bytes, void *stream)
 {
     if (!problems || count < 1) return EMDQ_EINVAL;
-    if (count > kFieldBatchMax) return EMDQ_ENOTSUP;
+    if (count > kFieldBatchMax || !tc_py_ok(py)) return EMDQ_ENOTSUP;
     for (int b = 0; b < count; ++b) {
         const emdq_field_problem &f = problems[b];
         if (!f.q || !f.c || !f.src || !f.disp_out || f.n < 1 || f.grid_w < 1 || f.grid_h < 1 ||
@@ -692,9 +790,77 @@ extern "C" emdq_status emdq_field_batch(const emdq_field_problem *problems, int 
         int *kcount = reinterpret_cast<int *>(ws + off + 64);
         const emdq_status rc =
             tc_problem(Bt, b, f.q, f.c, f.src, f.n, f.grid_x0, f.grid_y0, f.grid_w, f.grid_h,
-                       f.alpha, ref, kcount, reinterpret_cast<float2 *>(f.disp_out), ws + off + 1024);
+                       f.alpha, ref, kcount, reinterpret_cast<float2 *>(f.disp_out), ws + off + 1024,
+                       py);
         if (rc != EMDQ_OK) return rc;
         off += batch_problem_bytes(f.n, f.grid_w, f.grid_h);
     }
-    return tc_run(Bt, 0, nullptr, static_cast<cudaStream_t>(stream));
+    return tc_run(Bt, 0, py, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+}  // namespace
+
+extern "C" emdq_status emdq_field_batch(const emdq_field_problem *problems, int count,
+                                        void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!problems || count < 1) return EMDQ_EINVAL;
+    return field_batch_run(problems, count, chosen_tile_rows(tile_class(problems, count)), workspace,
+                           workspace_bytes, stream);
+}
+
+extern "C" emdq_status emdq_field_batch_ex(const emdq_field_problem *problems, int count,
+                                           int tile_rows, void *workspace, size_t workspace_bytes,
+                                           void *stream)
+{
+    return field_batch_run(problems, count, tile_rows, workspace, workspace_bytes, stream);
+}
+
+extern "C" int emdq_field_batch_tile_rows(const emdq_field_problem *problems, int count)
+{
+    if (!problems || count < 1 || count > kFieldBatchMax) return -1;
+    return chosen_tile_rows(tile_class(problems, count));
+}
+
+extern "C" emdq_status emdq_field_batch_autotune(const emdq_field_problem *problems, int count,
+                                                 void *workspace, size_t workspace_bytes,
+                                                 void *stream, int reps, int *tile_rows_out,
+                                                 float *ms_out)
+{
+    if (!problems || count < 1 || reps < 1) return EMDQ_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return EMDQ_ECUDA;
+    }
+    emdq_status rc = EMDQ_OK;
+    int best_py = kTcPYDefault;
+    float best = -1.f;
+    for (int py : kTcPYChoices) {
+        // one untimed call (operands, caches), then reps timed calls
+        rc = field_batch_run(problems, count, py, workspace, workspace_bytes, stream);
+        if (rc != EMDQ_OK) break;
+        if (cudaEventRecord(e0, st) != cudaSuccess) { rc = EMDQ_ECUDA; break; }
+        for (int r = 0; r < reps && rc == EMDQ_OK; ++r)
+            rc = field_batch_run(problems, count, py, workspace, workspace_bytes, stream);
+        if (rc != EMDQ_OK) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = EMDQ_ECUDA;
+            break;
+        }
+        ms /= reps;
+        if (best < 0.f || ms < best) {
+            best = ms;
+            best_py = py;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != EMDQ_OK) return rc;
+    record_tile_rows(tile_class(problems, count), best_py);
+    if (tile_rows_out) *tile_rows_out = best_py;
+    if (ms_out) *ms_out = best;
+    return EMDQ_OK;
 }

@@ -242,3 +242,44 @@ def test_field_batch_errors(emdq):
         emdq.emdq_field_batch([(q, c, s, (0, 0, 64, 32), -1.0)])
     with pytest.raises(emdq.EmdqError):
         emdq.emdq_field_batch([(q, c, s, (0, 0, 0, 32), 1e-4)])
+
+
+@pytest.mark.parametrize('tile_rows', [16, 24, 40])
+def test_field_batch_every_tile_height_gives_the_same_bits(emdq, tile_rows):
+    """The tile height changes only how the GEMM covers the window: every output's
+    accumulation over the matches is the same, so the fields are bit for bit those of the
+    default tile height, on ragged windows (heights that are no multiple of any tile)."""
+    rng = np.random.default_rng(80 + tile_rows)
+    specs = [(1000, 1280, 1024, (-30, -40, 1343, 1083)), (137, 640, 480, (5, 7, 17, 9)),
+             (2500, 1920, 1080, (-12, 3, 1999, 701)), (64, 640, 480, (0, 0, 129, 33))]
+    probs = []
+    for n, w, h, grid in specs:
+        q, c, s, _ = _field_case(rng, n, w, h)
+        probs.append((q, c, s, grid, np.float32(emdq.alpha_for_frame(w, h))))
+    ref = emdq.emdq_field_batch(probs, tile_rows=32)
+    got = emdq.emdq_field_batch(probs, tile_rows=tile_rows)
+    torch.cuda.synchronize()
+    for g, r in zip(got, ref):
+        assert torch.equal(torch.isnan(g), torch.isnan(r))
+        assert torch.equal(torch.nan_to_num(g), torch.nan_to_num(r))
+
+
+def test_field_batch_autotune_records_its_choice(emdq):
+    """The autotuner times every tile height, returns the fastest and records it for the
+    batch's size class: emdq_field_batch then uses it (and a bad height is refused)."""
+    rng = np.random.default_rng(90)
+    probs = []
+    for _ in range(3):
+        q, c, s, _ = _field_case(rng, 700, 1280, 1024)
+        probs.append((q, c, s, (-10, -20, 1300, 1070), np.float32(emdq.alpha_for_frame(1280, 1024))))
+    before = emdq.emdq_field_batch(probs, tile_rows=32)
+    py, ms = emdq.field_batch_autotune(probs, reps=3)
+    print(f'chosen tile height {py}, {ms * 1e3:.1f} us per call')
+    assert py in (16, 24, 32, 40) and ms > 0
+    assert emdq.field_batch_tile_rows(probs) == py
+    after = emdq.emdq_field_batch(probs)
+    torch.cuda.synchronize()
+    for a, b in zip(after, before):
+        assert torch.equal(torch.nan_to_num(a), torch.nan_to_num(b))
+    with pytest.raises(emdq.EmdqError):
+        emdq.emdq_field_batch(probs, tile_rows=48)
