@@ -143,3 +143,18 @@ def test_noalloc_fit_argument_errors_on_the_host(libemdq):
     assert L.emdq_fit_noalloc(None, None, big, 640, 480, None, None, None, None, None, None, None) == 1
     assert L.emdq_fit_noalloc(fake, fake, big, 640, 0, None, None, fake, fake, None, fake, None) == 1
     assert L.emdq_fit_noalloc(fake, fake, big, 640, 480, None, None, fake, fake, None, fake, None) == 7
+
+
+def test_warm_start_training_initialisation_on_the_host():
+    """The package's training starts from He-normal weights in the kernels' packed layout:
+    5313 parameters, zero biases, deterministic per seed (no GPU needed)."""
+    import torch
+    from paper_2103_07414_gb300.training import init_params
+    p = init_params(3, device='cpu')
+    q = init_params(3, device='cpu')
+    assert p.shape == (16 * 64 + 64 + 64 * 64 + 64 + 64 + 1,) and p.dtype == torch.float32
+    assert torch.equal(p, q) and not torch.equal(p, init_params(4, device='cpu'))
+    W1, b1 = p[:1024], p[1024:1088]
+    W2, b2 = p[1088:5184], p[5184:5248]
+    assert float(b1.abs().max()) == 0.0 and float(b2.abs().max()) == 0.0 and float(p[-1]) == 0.0
+    assert abs(float(W1.std()) - (2 / 16) ** 0.5) < 0.05 and abs(float(W2.std()) - (2 / 64) ** 0.5) < 0.02

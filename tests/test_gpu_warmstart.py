@@ -143,7 +143,8 @@ def test_gradient_and_adam_match_the_oracle(emdq):
 
 
 def test_training_reduces_the_loss(emdq):
-    from warmstart_train import make_training_set, train
+    from warmstart_train import make_training_set
+    from paper_2103_07414_gb300.training import train
     feat, label = make_training_set(range(500, 540))
     p0 = torch.from_numpy(ows.init_params(0).astype(np.float32)).cuda()
     l0 = torch.zeros(1, device='cuda')

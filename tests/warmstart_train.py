@@ -1,11 +1,12 @@
-"""Training and evaluation driver of the learned EM warm start (test infrastructure).
+"""Training data and evaluation of the learned EM warm start (test infrastructure: the labels
+and the evaluation's reference field come from the FP64 oracle).
 
 Training data: matches of seeded 640x480 scenes (N = 200, outlier rate 10-45 %, noise
-0.5-2 px); features from the library's step-0 fit and feature kernel; labels = the FP64
-oracle EMDQ's inlier posterior at convergence (a soft label: a network that predicts the
-final posterior lets EM start where it would end).  Training runs on the GPU through the
-library's own forward/backward/Adam kernels (emdq_mlp_train_step), with a cosine-decayed
-learning rate.
+0.5-2 px); features from the library's feature kernel; labels = the FP64 oracle EMDQ's inlier
+posterior at convergence (a soft label: a network that predicts the final posterior lets EM
+start where it would end).  The training itself is the package's
+(paper_2103_07414_gb300.training.train): the library's own forward/backward/Adam kernels
+(emdq_mlp_train_step), with a cosine-decayed learning rate.
 
     python tests/warmstart_train.py --seeds 1000 --out warmstart_mlp.npy
 
@@ -47,41 +48,6 @@ def make_training_set(seeds, n=200, w=640, h=480, device='cuda'):
         feats.append(emdq.warm_features(st, dt))
         labels.append(torch.from_numpy(ref['p'].astype(np.float32)).to(device))
     return torch.cat(feats), torch.cat(labels)
-
-
-def train(feat, label, steps=3000, batch=1024, lr=3e-3, seed=0, log_every=0):
-    """Adam on the mean cross-entropy, in the library's kernels.  Returns (params, losses)."""
-    import torch
-
-    import oracle.warmstart as ows
-    import paper_2103_07414_gb300 as emdq
-    dev = feat.device
-    params = torch.from_numpy(ows.init_params(seed).astype(np.float32)).to(dev)
-    m = torch.zeros_like(params)
-    v = torch.zeros_like(params)
-    loss = torch.zeros(1, device=dev)
-    xb = torch.empty((batch, 16), device=dev)
-    yb = torch.empty(batch, device=dev)
-    ws = torch.empty(emdq.lib().emdq_mlp_train_workspace_size(batch), dtype=torch.uint8, device=dev)
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(seed)
-    M = feat.shape[0]
-    perm = torch.randperm(M, device=dev, generator=gen)
-    pos = 0
-    losses = []
-    for step in range(1, steps + 1):
-        if pos + batch > M:
-            perm = torch.randperm(M, device=dev, generator=gen)
-            pos = 0
-        idx = perm[pos:pos + batch]
-        pos += batch
-        torch.index_select(feat, 0, idx, out=xb)
-        torch.index_select(label, 0, idx, out=yb)
-        lr_t = 0.5 * lr * (1.0 + np.cos(np.pi * (step - 1) / steps))
-        emdq.mlp_train_step(xb, yb, params, m, v, step, lr_t, loss_out=loss, workspace=ws)
-        if log_every and step % log_every == 0:
-            losses.append((step, float(loss.item())))
-    return params, losses
 
 
 def evaluate(params, seeds=(0, 1, 2), name='warm2000', device='cuda'):
@@ -130,6 +96,7 @@ def main():
     print(f'training set: {feat.shape[0]} matches, inlier fraction {float(label.mean()):.3f}, '
           f'{time.time() - t0:.1f} s', flush=True)
     t0 = time.time()
+    from paper_2103_07414_gb300.training import train
     params, losses = train(feat, label, steps=args.steps, log_every=max(1, args.steps // 10))
     torch.cuda.synchronize()
     print(f'trained {args.steps} steps in {time.time() - t0:.2f} s; loss ' +
