@@ -223,9 +223,47 @@ __device__ __forceinline__ void mstep_finish(const FitArgs &A, int i, float W, f
 // spread of its weights, and moving its moments from o to that centroid afterwards cancels
 // nothing.  Of C_t C_0^T only the trace (sum om u.v) and the antisymmetric part (sum om u x v)
 // enter the 2-D rotation, so only those are summed.
+// The totals of a row group as one lane keeps them until its row is finished: the nine sums
+// about the group's origin, the origin (negated: x, y parts) and the row (-1: none).
+struct RowSums {
+    float t[9];
+    float2 nox, noy;
+    int i;
+};
+
+// Eqs. 18-20 for the row a lane holds (see mstep_group): the moments moved from the group's
+// origin to the row's centroid, then the closed form.
+__device__ __forceinline__ void mstep_row(const FitArgs &A, const FitSmem &S, const RowSums &k)
+{
+    if (k.i < 0) return;
+    const float w = k.t[0], su0 = k.t[1], su1 = k.t[2], sv0 = k.t[3], sv1 = k.t[4];
+    float vx = k.t[5], vy = k.t[6], dot = k.t[7], cross = k.t[8];
+    // move the moments from o to the row's centroid o + d: m_c = m_o - W d d'^T
+    float du0 = 0.f, du1 = 0.f, dv0 = 0.f, dv1 = 0.f;
+    if (w > 0.f) {
+        const float inv = 1.f / w;
+        du0 = su0 * inv;
+        du1 = su1 * inv;
+        dv0 = sv0 * inv;
+        dv1 = sv1 * inv;
+    }
+    vx -= w * (du0 * du0 + du1 * du1);
+    vy -= w * (dv0 * dv0 + dv1 * dv1);
+    dot -= w * (dv0 * du0 + dv1 * du1);
+    cross -= w * (dv1 * du0 - dv0 * du1);
+    // the centroid relative to (x_i, y_i): o + d - x_i
+    const float2 xi = S.x[k.i], yi = S.y[k.i];
+    mstep_finish(A, k.i, w, du0 - (k.nox.x + xi.x), du1 - (k.nox.y + xi.y),
+                 dv0 - (k.noy.x + yi.x), dv1 - (k.noy.y + yi.y), vx, vy, dot, cross);
+}
+
+// The sums of a group of R rows (R <= 4); afterwards lane 4 slot + r keeps row r's totals in
+// `keep` (the group's slot among the warp's groups waiting to be finished, slot < 8), so that
+// the closed forms of up to 32 rows are then evaluated at once, one row per lane
+// (mstep_row), instead of four lanes finishing four rows after every group.
 template <int R>
 __device__ void mstep_group(const FitArgs &A, const FitSmem &S, const int *rows, int lane,
-                            bool first)
+                            bool first, int slot, RowSums &keep)
 {
     const int n = A.n;
     float2 nxi[R];
@@ -280,8 +318,7 @@ __device__ void mstep_group(const FitArgs &A, const FitSmem &S, const int *rows,
             sc[r] = __ffma2_rn(om2, g2, sc[r]);
         }
     }
-    // lane r receives row r's sums and finishes row r, so the divisions and square roots of
-    // the closed form are issued once for all R rows
+    // the warp totals of the R rows: lanes 4 slot .. 4 slot + R - 1 keep them
     float v9[4][9], t[9];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -297,30 +334,17 @@ __device__ void mstep_group(const FitArgs &A, const FitSmem &S, const int *rows,
         v9[r][8] = on ? sc[r < R ? r : 0].y : 0.f;
     }
     rows4_sum<9>(v9, lane, t);
-    if (lane >= R) return;
-    int i = rows[0];
+    if ((lane >> 2) != slot) return;
+    const int r = lane & 3;
+    int i = -1;
 #pragma unroll
-    for (int r = 1; r < R; ++r)
-        if (lane == r) i = rows[r];
-    const float w = t[0], su0 = t[1], su1 = t[2], sv0 = t[3], sv1 = t[4];
-    float vx = t[5], vy = t[6], dot = t[7], cross = t[8];
-    // move the moments from o to the row's centroid o + d: m_c = m_o - W d d'^T
-    float du0 = 0.f, du1 = 0.f, dv0 = 0.f, dv1 = 0.f;
-    if (w > 0.f) {
-        const float inv = 1.f / w;
-        du0 = su0 * inv;
-        du1 = su1 * inv;
-        dv0 = sv0 * inv;
-        dv1 = sv1 * inv;
-    }
-    vx -= w * (du0 * du0 + du1 * du1);
-    vy -= w * (dv0 * dv0 + dv1 * dv1);
-    dot -= w * (dv0 * du0 + dv1 * du1);
-    cross -= w * (dv1 * du0 - dv0 * du1);
-    // the centroid relative to (x_i, y_i): o + d - x_i
-    const float2 xi = S.x[i], yi = S.y[i];
-    mstep_finish(A, i, w, du0 - (nox.x + xi.x), du1 - (nox.y + xi.y), dv0 - (noy.x + yi.x),
-                 dv1 - (noy.y + yi.y), vx, vy, dot, cross);
+    for (int rr = 0; rr < R; ++rr)
+        if (r == rr) i = rows[rr];
+    keep.i = i;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) keep.t[k] = t[k];
+    keep.nox = nox;
+    keep.noy = noy;
 }
 
 // Hilbert index of (x, y), 16 bits each (the curve of order 16: consecutive indices are
@@ -352,9 +376,19 @@ __device__ __forceinline__ unsigned hilbert_index(unsigned x, unsigned y)
 // bit as in the loop -- is subtracted afterwards; where the rest of the weight is smaller
 // than that term (an isolated match), the subtraction would cancel and the sum over
 // i != j is taken again exactly.
+// The totals of a residual row as one lane keeps them until the row is evaluated: the six
+// sums over every i (the term i = j included) and the row (-1: none).
+struct ResSums {
+    float t[6];
+    int j;
+};
+
+// Lane 4 slot + r keeps row r's totals in `keep` (slot < 8, the group's place among the
+// warp's groups waiting), so that up to 32 residuals are then evaluated at once, one row per
+// lane (residual_finish), instead of four lanes after every group.
 template <int R>
 __device__ void residual_rows(const FitArgs &A, const FitSmem &S, const int *rows, int lane,
-                              float4 q0, float qs0, float &pe, float &ps)
+                              int slot, ResSums &keep)
 {
     const int n = A.n;
     float2 nxj[R], A1[R], A2[R];
@@ -382,7 +416,7 @@ __device__ void residual_rows(const FitArgs &A, const FitSmem &S, const int *row
             As[r] = fmaf(w, qsi, As[r]);
         }
     }
-    // lane r receives row r's sums and evaluates row r's residual
+    // the warp totals of the R rows: lanes 4 slot .. 4 slot + R - 1 keep them
     float v6[4][6], t[6];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -396,10 +430,26 @@ __device__ void residual_rows(const FitArgs &A, const FitSmem &S, const int *row
         v6[r][5] = on ? As[rr] : 0.f;
     }
     rows4_sum<6>(v6, lane, t);
-    int jl = rows[0];
+    if ((lane >> 2) != slot) return;
+    const int r = lane & 3;
+    int j = -1;
 #pragma unroll
-    for (int r = 1; r < R; ++r)
-        if ((lane & 3) == r) jl = rows[r];
+    for (int rr = 0; rr < R; ++rr)
+        if (r == rr) j = rows[rr];
+    keep.j = j;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) keep.t[k] = t[k];
+}
+
+// The leave-one-out residual of the row each lane keeps (all lanes of the warp take part:
+// isolated rows are summed again by the whole warp); adds p e and p of its row to pe, ps.
+__device__ void residual_finish(const FitArgs &A, const FitSmem &S, const ResSums &keep, int lane,
+                                float4 q0, float qs0, float &pe, float &ps)
+{
+    const int n = A.n;
+    const bool has = keep.j >= 0;
+    const int jl = has ? keep.j : 0;
+    const float *t = keep.t;
     // the term i = j: offset (0, 0), so its weight is exactly 2^lp_j
     const float wjj = ex2_ftz(S.lp[jl]);
     const float4 qj = S.q[jl];
@@ -410,7 +460,7 @@ __device__ void residual_rows(const FitArgs &A, const FitSmem &S, const int *row
     float c4 = fmaf(-wjj, qsj, t[5]);
     // isolated matches (the rest of the weight below the own term): the sum over i != j
     // taken again exactly, one flagged row at a time by the whole warp
-    unsigned slow = __ballot_sync(0xffffffffu, lane < R && !(wl >= wjj));
+    unsigned slow = __ballot_sync(0xffffffffu, has && !(wl >= wjj));
     while (slow) {
         const int r = __ffs(slow) - 1;
         slow &= slow - 1;
@@ -438,7 +488,7 @@ __device__ void residual_rows(const FitArgs &A, const FitSmem &S, const int *row
             wl = w_; c0 = d0; c1 = d1; c2 = d2; c3 = d3; c4 = d4;
         }
     }
-    if (lane >= R) return;
+    if (!has) return;
     float e = INFINITY;
     if (wl > 0.f) {
         const float inv = 1.f / wl;
@@ -592,28 +642,39 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
     }
     // each warp takes groups of 4 consecutive positions (the same number per warp), then
     // one contiguous run of the remaining positions (at most 4)
+    // (the closed forms of a warp's rows are evaluated 32 at a time, one row per lane, after
+    // every 8 groups and at the end)
     auto mstep_all = [&](bool first) {
         const int m = pe - pb, per = m / (4 * kWarps);
+        RowSums keep;
+        keep.i = -1;
+        int slot = 0;
         for (int g = 0; g < per; ++g) {
             const int b = pb + 4 * (warp + kWarps * g);
             const int rows[4] = {A.ord[b], A.ord[b + 1], A.ord[b + 2], A.ord[b + 3]};
-            mstep_group<4>(A, S, rows, lane, first);
+            mstep_group<4>(A, S, rows, lane, first, slot, keep);
+            if (++slot == 8) {
+                mstep_row(A, S, keep);
+                keep.i = -1;
+                slot = 0;
+            }
         }
         const int base = pb + 4 * kWarps * per, left = m - 4 * kWarps * per;
         const int lb = base + warp * left / kWarps, le = base + (warp + 1) * left / kWarps;
         if (le - lb == 4) {
             const int rows[4] = {A.ord[lb], A.ord[lb + 1], A.ord[lb + 2], A.ord[lb + 3]};
-            mstep_group<4>(A, S, rows, lane, first);
+            mstep_group<4>(A, S, rows, lane, first, slot, keep);
         } else if (le - lb == 3) {
             const int rows[3] = {A.ord[lb], A.ord[lb + 1], A.ord[lb + 2]};
-            mstep_group<3>(A, S, rows, lane, first);
+            mstep_group<3>(A, S, rows, lane, first, slot, keep);
         } else if (le - lb == 2) {
             const int rows[2] = {A.ord[lb], A.ord[lb + 1]};
-            mstep_group<2>(A, S, rows, lane, first);
+            mstep_group<2>(A, S, rows, lane, first, slot, keep);
         } else if (le - lb == 1) {
             const int rows[1] = {A.ord[lb]};
-            mstep_group<1>(A, S, rows, lane, first);
+            mstep_group<1>(A, S, rows, lane, first, slot, keep);
         }
+        mstep_row(A, S, keep);
     };
     // residuals of this CTA's rows and its partial sums, then the barrier
     auto residuals_and_barrier = [&]() -> int {
@@ -627,22 +688,31 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
         }
         __syncthreads();
         float pe = 0.f, ps = 0.f;
+        ResSums keep;
+        keep.j = -1;
+        int slot = 0;
         int j = gwarp;
         for (; j + 3 * nwarps < n; j += 4 * nwarps) {
             const int rows[4] = {j, j + nwarps, j + 2 * nwarps, j + 3 * nwarps};
-            residual_rows<4>(A, S, rows, lane, q0, qs0, pe, ps);
+            residual_rows<4>(A, S, rows, lane, slot, keep);
+            if (++slot == 8) {
+                residual_finish(A, S, keep, lane, q0, qs0, pe, ps);
+                keep.j = -1;
+                slot = 0;
+            }
         }
         const int rem = j < n ? (n - 1 - j) / nwarps + 1 : 0;     // 0..3 rows left
         if (rem == 3) {
             const int rows[3] = {j, j + nwarps, j + 2 * nwarps};
-            residual_rows<3>(A, S, rows, lane, q0, qs0, pe, ps);
+            residual_rows<3>(A, S, rows, lane, slot, keep);
         } else if (rem == 2) {
             const int rows[2] = {j, j + nwarps};
-            residual_rows<2>(A, S, rows, lane, q0, qs0, pe, ps);
+            residual_rows<2>(A, S, rows, lane, slot, keep);
         } else if (rem == 1) {
             const int rows[1] = {j};
-            residual_rows<1>(A, S, rows, lane, q0, qs0, pe, ps);
+            residual_rows<1>(A, S, rows, lane, slot, keep);
         }
+        residual_finish(A, S, keep, lane, q0, qs0, pe, ps);
         const float2 t = block_sum2<NT>(pe, ps, red);
         if (threadIdx.x == 0) __stcg(reinterpret_cast<float2 *>(A.partials) + rank, t);
         return barrier_status(A, epoch, &s_flag, ncta);
