@@ -583,7 +583,13 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
     // until the first residual pass) and keeps the positions of its own rows.
     const int pb = static_cast<int>((long long)rank * n / ncta);
     const int pe = static_cast<int>((long long)(rank + 1) * n / ncta);
-    {
+    if ((n + ncta - 1) / ncta <= kWarps) {
+        // at most one row per warp in every CTA of the problem (the same decision in all of
+        // them): every row is its own group (its origin its own previous centroid), so the
+        // order of the rows changes nothing and the sort is skipped
+        for (int t = pb + threadIdx.x; t < pe; t += NT) A.ord[t] = t;
+        __syncthreads();
+    } else {
         float2 lo = make_float2(INFINITY, INFINITY), hi = make_float2(-INFINITY, -INFINITY);
         for (int j = threadIdx.x; j < n; j += NT) {
             const float2 x = S.x[j];

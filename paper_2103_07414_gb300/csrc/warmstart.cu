@@ -314,6 +314,7 @@ struct WarmGridBatch {
     int block0[kWarmBatchMax + 1];     // prefix sums of the problems' block counts
     int count;
     int nmax;                          // largest n (sizes the shared-memory arrays)
+    int queries;                       // matches per block (kGridQueries, fewer for small launches)
 };
 
 struct GridLayout {
@@ -364,7 +365,7 @@ __global__ void __launch_bounds__(kNetThreads) warm_start_grid_kernel(
     while (b + 1 < B.count && static_cast<int>(blockIdx.x) >= B.block0[b + 1]) ++b;
     const int n = B.n[b];
     const float2 *__restrict__ src = B.src[b];
-    const int q0 = (blockIdx.x - B.block0[b]) * kGridQueries;
+    const int q0 = (blockIdx.x - B.block0[b]) * B.queries;
 
     for (int k = threadIdx.x; k < kGridCells; k += kNetThreads) cur[k] = 0;
     // extent of the matches (NaNs are ignored by fminf / fmaxf)
@@ -460,7 +461,7 @@ __global__ void __launch_bounds__(kNetThreads) warm_start_grid_kernel(
     }
     __syncthreads();
 
-    for (int k = warp; k < kGridQueries; k += kWarps) {
+    for (int k = warp; k < B.queries; k += kWarps) {
         const int j = q0 + k;
         if (j >= n) break;
         const float2 xj = src[j];
@@ -688,6 +689,13 @@ extern "C" emdq_status emdq_warm_start(const float *const *src, const float *con
         WarmGridBatch G;
         G.count = count;
         G.nmax = nmax;
+        // kGridQueries matches per block; a launch too small to give every SM a block (one
+        // frame, a few pairs) takes fewer per block, down to one per warp, so that its
+        // latency is not set by a few blocks walking many matches each (each block stages its
+        // problem's matches: more blocks repeat that work, which large launches avoid)
+        int q = kGridQueries;
+        while (q > kNetThreads / 32 && (total + q - 1) / q < D.sms) q >>= 1;
+        G.queries = q;
         int blocks = 0;
         for (int b = 0; b < count; ++b) {
             G.src[b] = B.src[b];
@@ -695,7 +703,7 @@ extern "C" emdq_status emdq_warm_start(const float *const *src, const float *con
             G.p0[b] = B.p0[b];
             G.n[b] = B.n[b];
             G.block0[b] = blocks;
-            blocks += (n[b] + kGridQueries - 1) / kGridQueries;
+            blocks += (n[b] + q - 1) / q;
         }
         G.block0[count] = blocks;
         warm_start_grid_kernel<<<blocks, kNetThreads, grid_layout(nmax).total,
