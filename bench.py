@@ -37,12 +37,12 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_write.sum), keyed by kernel and tied to the hash of the source it was
 # measured on: a changed kernel reports null until it is captured again.
 NCU_TRAFFIC = {
-    # emdq_field_batch on 4 frames of the 1280x1024 sequence (N = 1000): field_tc_prep_kernel
-    # 0.18-0.21 MB read + 32.0-32.7 MB written (operands written back from L2) and
-    # field_tc_kernel 2.7-3.2 MB read + 45.0-45.3 MB written (the field), per call; the mean
-    # of three steady-state calls over the 4 frames, per frame as the roofline's unit (ncu
-    # --metrics dram__bytes_read.sum,dram__bytes_write.sum --cache-control none)
-    'field': dict(bytes=20150827, file='field_tc.cu', src='d32a3a4450fb882c'),
+    # emdq_field_batch on 4 frames of the 1280x1024 sequence (N = 1000, tiles of 40 pixel
+    # rows): field_tc_prep_kernel 0.17-0.18 MB read + 33.1-33.9 MB written (operands written
+    # back from L2) and field_tc_kernel 2.7-3.2 MB read + 44.8-46.2 MB written (the field), per
+    # call; the mean of six steady-state calls over the 4 frames, per frame as the roofline's
+    # unit (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --cache-control none)
+    'field': dict(bytes=20752693, file='field_tc.cu', src='59fcdfa971cfd282'),
 }
 
 
@@ -86,6 +86,9 @@ def parse_args():
     ap.add_argument('--no-graph', action='store_true',
                     help='issue every call each step (default: the pass is captured once into a '
                          'CUDA graph and replayed, removing per-call launch overhead)')
+    ap.add_argument('--field-tile-rows', type=int, default=0,
+                    help='tile height of the field GEMM (16, 24, 32, 40); 0: chosen by the '
+                         "library's autotuner on the workload")
     ap.add_argument('--field-group', type=int, default=4,
                     help='frames per emdq_field_batch / mosaic_warp_batch call (BF16, pipelined '
                          'path; at most 8 for the sequence, 16 for the mixed batch)')
@@ -409,7 +412,7 @@ def run_gpu(args, ws, rank, local):
         disps = [grp_disp[slot][i][: g[2] * g[3] * 2].view(g[3], g[2], 2) for i, g in enumerate(gs)]
         if prec == emdq.BF16:
             emdq.emdq_field_batch([(fo['q'], fo['c'], s_, g, alpha) for fo, s_, g in zip(fos, ss, gs)],
-                                  outs=disps, workspace=grp_ws[slot])
+                                  outs=disps, workspace=grp_ws[slot], tile_rows=args.field_tile_rows or None)
         else:
             emdq.emdq_field(fos[0]['q'], fos[0]['c'], ss[0], gs[0], alpha, precision=prec,
                             out=disps[0], workspace=grp_ws[slot])
@@ -560,8 +563,12 @@ def run_gpu(args, ws, rank, local):
         probs_t = [(fo_t[j]['q'], fo_t[j]['c'], src[k], grids[k], alpha) for j, k in enumerate(ks_t)]
         outs_t = [grp_disp[0][i][: grids[k][2] * grids[k][3] * 2].view(grids[k][3], grids[k][2], 2)
                   for i, k in enumerate(ks_t)]
-        py, ms = emdq.field_batch_autotune(probs_t, reps=5, outs=outs_t, workspace=grp_ws[0])
-        field_tune = dict(tile_rows=py, ms_per_call=ms, frames_per_call=len(ks_t))
+        if args.field_tile_rows:
+            py = args.field_tile_rows
+            field_tune = dict(tile_rows=py, chosen='by --field-tile-rows')
+        else:
+            py, ms = emdq.field_batch_autotune(probs_t, reps=5, outs=outs_t, workspace=grp_ws[0])
+            field_tune = dict(tile_rows=py, ms_per_call=ms, frames_per_call=len(ks_t))
     def new_events(external=False):
         # external: recorded as real event nodes when captured into a CUDA graph, so they
         # still time the replay
