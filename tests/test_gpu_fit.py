@@ -119,3 +119,24 @@ def test_fit_device_errors(emdq):
     big = emdq.lib().emdq_fit_max_n() + 1
     with pytest.raises(emdq.EmdqError):
         _gpu_fit(emdq, np.zeros((big, 2)), np.zeros((big, 2)), 640, 480)
+
+
+def test_fit_at_the_largest_n(emdq, orc):
+    """A fit of exactly emdq_fit_max_n() matches (the shared-memory limit of one CTA) on a
+    1920x1080 scene, two fixed EM iterations, against the oracle; one match more is refused."""
+    n = emdq.lib().emdq_fit_max_n()
+    sc = make_scene(12, 1920, 1080, 3, drift=1.0)
+    src, dst, inl = make_matches(sc, 1, n, 0.3, 1.5)
+    assert src.shape[0] == n
+    want = orc.fit(_f32(src), _f32(dst), sc.w, sc.h, max_iters=2, tol_p=0.0)
+    got = _gpu_fit(emdq, src, dst, sc.w, sc.h, max_iters=2, tol_p=0.0)
+    assert got['info']['status_name'] == 'ENOCONV' and got['info']['iters'] == 2
+    dp = np.abs(got['p'] - want['p']).max()
+    dpos = np.abs(_apply(got['q8'], _f32(src)) - _apply(want['q8'], _f32(src)))[want['p'] > 0.5].max()
+    print(f'n = {n}: max |dp| {dp:.2e}, max inlier row-prediction diff {dpos:.2e} px')
+    assert dp <= 1e-4
+    assert dpos <= 2e-3
+    assert got['info']['sigma2'] == pytest.approx(want['sigma2'], rel=1e-5)
+    s2, d2, _ = make_matches(sc, 1, n + 1, 0.3, 1.5)
+    with pytest.raises(emdq.EmdqError):
+        _gpu_fit(emdq, s2, d2, sc.w, sc.h)
