@@ -385,24 +385,23 @@ def run_gpu(args, ws, rank, local):
     slot_free = [None, None]        # warp-done event of the group that last used each set
     group_no = [0]
 
-    def field_and_warp(fr, s_, g, fo, ev4=None):
-        """One frame, not pipelined.  ev4: (field start, field done, warp start, warp done)."""
-        if ev4 is not None: ev4[0].record(stream)
+    def field_and_warp(fr, s_, g, fo, ev3=None):
+        """One frame, not pipelined.  ev3: (field done, warp start, warp done) events."""
         if fused:
             emdq.emdq_mosaic(fo['q'], fo['c'], s_, g, alpha, fr, canvas, origin, workspace=field_ws)
-            if ev4 is not None:
-                for e in ev4[1:]: e.record(stream)
+            if ev3 is not None:
+                for e in ev3: e.record(stream)
             return
         disp = disp_buf[: g[2] * g[3] * 2].view(g[3], g[2], 2)
         emdq.emdq_field(fo['q'], fo['c'], s_, g, alpha, precision=prec, out=disp,
                         workspace=field_ws)
-        if ev4 is not None:
-            ev4[1].record(stream)
-            ev4[2].record(stream)
+        if ev3 is not None:
+            ev3[0].record(stream)
+            ev3[1].record(stream)
         emdq.mosaic_warp(fr, disp, g, canvas, origin)
-        if ev4 is not None: ev4[3].record(stream)
+        if ev3 is not None: ev3[2].record(stream)
 
-    def fields_then_warps(frs, ss, gs, fos, evs4=None):
+    def fields_then_warps(frs, ss, gs, fos, evs3=None):
         """A group of frames, pipelined: one batched field call, then the warps."""
         two = not args.one_stream
         wst = warp_stream if two else stream      # resolved per call: capture rebinds stream
@@ -411,10 +410,6 @@ def run_gpu(args, ws, rank, local):
         if two and slot_free[slot] is not None:
             stream.wait_event(slot_free[slot])
         disps = [grp_disp[slot][i][: g[2] * g[3] * 2].view(g[3], g[2], 2) for i, g in enumerate(gs)]
-        # the field call's own span: from after the wait for its buffer slot to its end (the
-        # first frame's events span the call, the others' are empty, so per-frame sums stay
-        # right)
-        if evs4 is not None: evs4[0][0].record(stream)
         if prec == emdq.BF16:
             emdq.emdq_field_batch([(fo['q'], fo['c'], s_, g, alpha) for fo, s_, g in zip(fos, ss, gs)],
                                   outs=disps, workspace=grp_ws[slot], tile_rows=args.field_tile_rows or None)
@@ -423,21 +418,20 @@ def run_gpu(args, ws, rank, local):
                             out=disps[0], workspace=grp_ws[slot])
         # dependencies through plain events (a captured graph cannot wait on the timing
         # events, which are external event nodes there)
-        if evs4 is not None:
-            for i, e4 in enumerate(evs4):
-                if i: e4[0].record(stream)
-                e4[1].record(stream)
+        if evs3 is not None:
+            for e3 in evs3: e3[0].record(stream)
         if two:
             fdone = torch.cuda.Event()
             fdone.record(stream)
             wst.wait_event(fdone)
-        # one launch blends the group's frames in order (the same convention)
-        if evs4 is not None: evs4[0][2].record(wst)
+        # one launch blends the group's frames in order (the first frame's events span it,
+        # the others' are empty, so per-frame sums stay right)
+        if evs3 is not None: evs3[0][1].record(wst)
         emdq.mosaic_warp_batch(frs, disps, gs, canvas, origin, stream=wst)
-        if evs4 is not None:
+        if evs3 is not None:
             for i in range(len(frs)):
-                if i: evs4[i][2].record(wst)
-                evs4[i][3].record(wst)
+                if i: evs3[i][1].record(wst)
+                evs3[i][2].record(wst)
         if two:
             wdone = torch.cuda.Event()
             wdone.record(wst)
@@ -496,11 +490,11 @@ def run_gpu(args, ws, rank, local):
                 sub = list(range(j0, min(len(ks), j0 + G)))
                 fields_then_warps([fr_of(ks[j]) for j in sub], [s_of(ks[j]) for j in sub],
                                   [grids[ks[j]] for j in sub], [outs[j] for j in sub],
-                                  [ev[4 + 4 * j: 8 + 4 * j] for j in sub] if ev else None)
+                                  [ev[4 + 3 * j: 7 + 3 * j] for j in sub] if ev else None)
         else:
             for j, k in enumerate(ks):
                 field_and_warp(fr_of(k), s_of(k), grids[k], outs[j],
-                               ev[4 + 4 * j: 8 + 4 * j] if ev else None)
+                               ev[4 + 3 * j: 7 + 3 * j] if ev else None)
         if piped and not args.one_stream:
             stream.wait_stream(warp_stream)       # the batch is blended when its warps are
             slot_free[0] = slot_free[1] = None
@@ -579,29 +573,30 @@ def run_gpu(args, ws, rank, local):
         # external: recorded as real event nodes when captured into a CUDA graph, so they
         # still time the replay
         kw = dict(external=True) if external else {}
-        return [[torch.cuda.Event(enable_timing=True, **kw) for _ in range(5 + 4 * len(ks))]
+        return [[torch.cuda.Event(enable_timing=True, **kw) for _ in range(5 + 3 * len(ks))]
                 for ks in batches]
 
     # per batch e[0]: its fits issued and e[1]: warm start done, e[2]: fits done (all on the
-    # fit stream); e[3]: its blend starts (main stream, after the fits); e[4 + 4j] / e[5 + 4j]:
-    # frame j's field call starts / is done (main stream; the start after the call's wait for
-    # its buffer slot), e[6 + 4j] / e[7 + 4j]: its warp starts / is done (warp stream).  Frame
-    # latency = e[0] -> e[7 + 4j].  Kernel durations are taken on the stream each kernel runs
-    # on.
+    # fit stream); e[3]: its blend starts (main stream, after the fits); e[4 + 3j]: frame j's
+    # field done (main stream), e[5 + 3j] / e[6 + 3j]: its warp starts / is done (warp
+    # stream).  Frame latency = e[0] -> e[6 + 3j].  Kernel durations are taken on the stream
+    # each kernel runs on.
     lat_ms, pass_ms = [], []
     warm_ms, fit_ms, field_ms, warp_ms = [], [], [], []
     fit_launch_frames = []
 
     def collect(step):
         for bi, e in enumerate(step):
-            nb = (len(e) - 5) // 4
+            nb = (len(e) - 5) // 3
             warm_ms.append(e[0].elapsed_time(e[-1]) if warm else 0.0)
             fit_ms.append(e[1].elapsed_time(e[2]))
             fit_launch_frames.append(batches[bi])
+            prev = e[3]
             for j in range(nb):
-                field_ms.append(e[4 + 4 * j].elapsed_time(e[5 + 4 * j]))
-                warp_ms.append(e[6 + 4 * j].elapsed_time(e[7 + 4 * j]))
-                lat_ms.append(e[0].elapsed_time(e[7 + 4 * j]))
+                field_ms.append(prev.elapsed_time(e[4 + 3 * j]))
+                warp_ms.append(e[5 + 3 * j].elapsed_time(e[6 + 3 * j]))
+                lat_ms.append(e[0].elapsed_time(e[6 + 3 * j]))
+                prev = e[4 + 3 * j]
 
     # CUDA graph of one pass (one stream): captured once, replayed every step
     graph, graph_note, gevs = None, None, None
@@ -1166,10 +1161,8 @@ def run_gpu_mixed(args, ws, rank, local):
                 for _ in range(2)]
 
     def one_pass(ev=None):
-        # ev[0] start, ev[1] warm start done, ev[2] fits done, then per pair b: ev[3 + 4b] /
-        # ev[4 + 4b] field call start (after the wait for its buffer slot) / done (its group's
-        # call: the group's first pair spans it, the others are empty), ev[5 + 4b] / ev[6 + 4b]
-        # warp start / done
+        # ev[0] start, ev[1] warm start done, ev[2] fits done, then per pair b: ev[3 + 3b]
+        # field done (its group's call), ev[4 + 3b] / ev[5 + 3b] warp start / done
         main = torch.cuda.current_stream()
         if ev: ev[0].record()
         emdq.warm_start(probs_sd, warm_params, outs=[x['p0'] for x in P])
@@ -1183,21 +1176,18 @@ def run_gpu_mixed(args, ws, rank, local):
                 main.wait_event(free[slot])
             disps = [grp_disp[slot][i][: P[b]['grid'][2] * P[b]['grid'][3] * 2].view(
                      P[b]['grid'][3], P[b]['grid'][2], 2) for i, b in enumerate(grp)]
-            if ev: ev[3 + 4 * grp[0]].record(main)
             emdq.emdq_field_batch([(P[b]['out']['q'], P[b]['out']['c'], P[b]['src'], P[b]['grid'],
                                     P[b]['alpha']) for b in grp], outs=disps, workspace=grp_ws[slot])
             fdone = torch.cuda.Event()
             fdone.record(main)
             if ev:
-                for b in grp:
-                    if b != grp[0]: ev[3 + 4 * b].record(main)
-                    ev[4 + 4 * b].record(main)
+                for b in grp: ev[3 + 3 * b].record(main)
             warp_stream.wait_event(fdone)
             for i, b in enumerate(grp):
                 x = P[b]
-                if ev: ev[5 + 4 * b].record(warp_stream)
+                if ev: ev[4 + 3 * b].record(warp_stream)
                 emdq.mosaic_warp(x['frame'], disps[i], x['grid'], x['canvas'], x['origin'], stream=warp_stream)
-                if ev: ev[6 + 4 * b].record(warp_stream)
+                if ev: ev[5 + 3 * b].record(warp_stream)
             wdone = torch.cuda.Event()
             wdone.record(warp_stream)
             free[slot] = wdone
@@ -1225,7 +1215,7 @@ def run_gpu_mixed(args, ws, rank, local):
     field_tiles = [emdq.field_batch_tile_rows([(P[b]['out']['q'], P[b]['out']['c'], P[b]['src'],
                                                 P[b]['grid'], P[b]['alpha']) for b in grp])
                    for grp in groups]
-    n_ev = 3 + 4 * len(P)
+    n_ev = 3 + 3 * len(P)
     graph, graph_note = None, None
     gev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(n_ev)]
     if not args.no_graph:
@@ -1244,9 +1234,11 @@ def run_gpu_mixed(args, ws, rank, local):
     def collect(ev):
         warm_ms.append(ev[0].elapsed_time(ev[1]))
         fit_ms.append(ev[1].elapsed_time(ev[2]))
+        prev = ev[2]
         for b in range(len(P)):
-            field_ms.append(ev[3 + 4 * b].elapsed_time(ev[4 + 4 * b]))
-            warp_ms.append(ev[5 + 4 * b].elapsed_time(ev[6 + 4 * b]))
+            field_ms.append(prev.elapsed_time(ev[3 + 3 * b]))
+            warp_ms.append(ev[4 + 3 * b].elapsed_time(ev[5 + 3 * b]))
+            prev = ev[3 + 3 * b]
 
     outer = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
              for _ in range(args.steps)]
