@@ -43,6 +43,13 @@ NCU_TRAFFIC = {
     # call; the mean of six steady-state calls over the 4 frames, per frame as the roofline's
     # unit (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --cache-control none)
     'field': dict(bytes=20752693, file='field_tc.cu', src='59fcdfa971cfd282'),
+    # emdq_mosaic_batch on the 1280x1024 sequence (calls of 13, 13, 13 and 11 frames per
+    # 50-frame batch, tiles of 40 pixel rows): per 13-frame call field_tc_prep_kernel 0.2-0.6 MB
+    # read + 90 MB written (operands) and mosaic_tc_kernel 276-282 MB read (operands of 13
+    # frames, more than L2 holds, frames, canvas) + 67 MB written (the operands' remaining
+    # write-back, the canvas); the 16 launches of the timed pass over its 100 frames, per frame
+    # (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --cache-control none)
+    'mosaic': dict(bytes=33698237, file='field_tc.cu', src='d23e94dd07f053ca'),
 }
 
 
@@ -89,9 +96,15 @@ def parse_args():
     ap.add_argument('--field-tile-rows', type=int, default=0,
                     help='tile height of the field GEMM (16, 24, 32, 40); 0: chosen by the '
                          "library's autotuner on the workload")
-    ap.add_argument('--field-group', type=int, default=4,
-                    help='frames per emdq_field_batch / mosaic_warp_batch call (BF16, pipelined '
-                         'path; at most 8 for the sequence, 16 for the mixed batch)')
+    ap.add_argument('--field-group', type=int, default=0,
+                    help='frames per emdq_mosaic_batch (at most 16) or emdq_field_batch / '
+                         'mosaic_warp_batch (at most 8; 16 for the mixed batch) call (BF16, '
+                         'pipelined path); 0: for emdq_mosaic_batch the fewest calls per fit '
+                         'batch, frames spread evenly (13 for batches of 50), else 4')
+    ap.add_argument('--split-group', action='store_true',
+                    help='a group of frames as emdq_field_batch, then mosaic_warp_batch on a second '
+                         'stream (default for the sequence: one emdq_mosaic_batch call, field and '
+                         'warp fused, the field never written)')
     ap.add_argument('--no-pipeline', action='store_true',
                     help='field and warp of every frame on one stream (default: the warp of frame k '
                          'on a second stream, beside the field of frame k + 1)')
@@ -369,13 +382,24 @@ def run_gpu(args, ws, rank, local):
     # main stream) into buffer set g % 2, their warps on the warp stream after that call, in
     # frame order (the blend is order-dependent) while the next group's fields run
     piped = not fused and not args.no_pipeline
-    G = max(1, min(8, args.field_group)) if piped and prec == emdq.BF16 else 1
-    warp_stream = torch.cuda.Stream(device=dev) if piped and not args.one_stream else None
+    group_fused = piped and prec == emdq.BF16 and not args.split_group
+    if not (piped and prec == emdq.BF16):
+        G = 1
+    elif args.field_group > 0:
+        G = max(1, min(16 if group_fused else 8, args.field_group))
+    elif group_fused:
+        G = -(-B // -(-B // 16))          # ceil(B / calls), calls = ceil(B / 16)
+    else:
+        G = 4
+    warp_stream = (torch.cuda.Stream(device=dev) if piped and not args.one_stream and not group_fused
+                   else None)
     if piped and prec == emdq.BF16:
         zq = torch.zeros((n, 8), device=dev)
         zc = torch.zeros(n, device=dev)
         zs = torch.zeros((n, 2), device=dev)
-        gws = emdq.field_batch_workspace_size([(zq, zc, zs, (0, 0, max_gw, max_gh), alpha)] * G)
+        gws = max(emdq.field_batch_workspace_size([(zq, zc, zs, (0, 0, max_gw, max_gh), alpha)] * G),
+                  emdq.mosaic_batch_workspace_size([(zq, zc, zs, (0, 0, max_gw, max_gh), alpha,
+                                                     frames[0])] * G))
         grp_ws = [torch.empty(gws, dtype=torch.uint8, device=dev) for _ in range(2)]
         grp_disp = [[torch.empty(max_gw * max_gh * 2, dtype=torch.float32, device=dev)
                      for _ in range(G)] for _ in range(2)]
@@ -407,6 +431,15 @@ def run_gpu(args, ws, rank, local):
         wst = warp_stream if two else stream      # resolved per call: capture rebinds stream
         slot = group_no[0] % 2
         group_no[0] += 1
+        if group_fused:
+            # one call: the group's fields and warps, the canvas words on chip per tile
+            emdq.emdq_mosaic_batch([(fo['q'], fo['c'], s_, g, alpha, fr)
+                                    for fo, s_, g, fr in zip(fos, ss, gs, frs)],
+                                   canvas, origin, workspace=grp_ws[slot],
+                                   tile_rows=args.field_tile_rows or None)
+            if evs3 is not None:       # one event per call: the group's last frame blended
+                evs3[-1][2].record(stream)
+            return
         if two and slot_free[slot] is not None:
             stream.wait_event(slot_free[slot])
         disps = [grp_disp[slot][i][: g[2] * g[3] * 2].view(g[3], g[2], 2) for i, g in enumerate(gs)]
@@ -495,7 +528,7 @@ def run_gpu(args, ws, rank, local):
             for j, k in enumerate(ks):
                 field_and_warp(fr_of(k), s_of(k), grids[k], outs[j],
                                ev[4 + 3 * j: 7 + 3 * j] if ev else None)
-        if piped and not args.one_stream:
+        if warp_stream is not None:
             stream.wait_stream(warp_stream)       # the batch is blended when its warps are
             slot_free[0] = slot_free[1] = None
         for j, k in enumerate(ks):
@@ -556,7 +589,9 @@ def run_gpu(args, ws, rank, local):
     # autotuner on the last batch's first group (recorded per size class, so the calls below,
     # and the graph captured from them, use it)
     field_tune = None
-    if piped and prec == emdq.BF16:
+    if group_fused:
+        field_tune = dict(call='emdq_mosaic_batch', tile_rows=args.field_tile_rows or 'library default')
+    elif piped and prec == emdq.BF16:
         lb = len(batches) - 1
         ks_t = batches[lb][:G]
         fo_t = fit_outs_all[lb % nbuf]
@@ -592,6 +627,17 @@ def run_gpu(args, ws, rank, local):
             fit_ms.append(e[1].elapsed_time(e[2]))
             fit_launch_frames.append(batches[bi])
             prev = e[3]
+            if group_fused:
+                # one event per group call: the call's span goes to its first frame (per-frame
+                # sums stay right), every frame of the group is done when the call is
+                for j0 in range(0, nb, G):
+                    last = e[6 + 3 * (min(nb, j0 + G) - 1)]
+                    for j in range(j0, min(nb, j0 + G)):
+                        field_ms.append(prev.elapsed_time(last) if j == j0 else 0.0)
+                        warp_ms.append(0.0)
+                        lat_ms.append(e[0].elapsed_time(last))
+                    prev = last
+                continue
             for j in range(nb):
                 field_ms.append(prev.elapsed_time(e[4 + 3 * j]))
                 warp_ms.append(e[5 + 3 * j].elapsed_time(e[6 + 3 * j]))
@@ -892,6 +938,10 @@ def run_gpu(args, ws, rank, local):
                      for i in range(len(fit_launch_frames))]
     kernel_total = dict(fit=float(np.sum(fit_ms)), warm=float(np.sum(warm_ms)),
                         field=float(np.sum(field_ms)), warp=float(np.sum(warp_ms)))
+    if group_fused:
+        # one call per group does both: its time is the field events' span
+        kernel_total = dict(fit=kernel_total['fit'], warm=kernel_total['warm'],
+                            mosaic=kernel_total['field'])
     dom = max(kernel_total, key=kernel_total.get)
     if dom == 'fit':
         # FP32 operations per match pair and EM round (an FMA counts 2): 34 in the M-step
@@ -908,7 +958,7 @@ def run_gpu(args, ws, rank, local):
         roof = dict(bound='alu', kernel='warm_start_batch_kernel',
                     achieved=flops / (np.mean(warm_ms) * 1e-3) / 1e12, peak=alu_peak, unit='TFLOP/s',
                     peak_source=alu_src, launches=len(warm_ms), mean_launch_ms=float(np.mean(warm_ms)))
-    elif dom == 'field':
+    elif dom in ('field', 'mosaic'):
         if prec == emdq.BF16:
             # the matches that carry weight (c > 0): zero-weight terms of Eqs. 2-3 are no work
             nz = []
@@ -918,8 +968,12 @@ def run_gpu(args, ws, rank, local):
                 nz += [int((fit_outs_all[bi % nbuf][j]['c'] > 0).sum().item()) for j in range(len(ks))]
             flops = 2.0 * 6 * win_px * float(np.mean(nz))
             roof = dict(bound='tensor',
-                        kernel=('emdq_field_batch' if piped else 'emdq_field') +
-                               ': field_tc_prep_kernel + field_tc_kernel (timed together, per frame)',
+                        kernel=('emdq_mosaic_batch: field_tc_prep_kernel + mosaic_tc_kernel (the '
+                                'field GEMM with the warp in its epilogue)'
+                                if group_fused else
+                                ('emdq_field_batch' if piped else 'emdq_field') +
+                                ': field_tc_prep_kernel + field_tc_kernel') +
+                               ' (timed together, per frame)',
                         work='2 x 6 x window pixels x matches of nonzero weight',
                         achieved=flops / (np.mean(field_ms) * 1e-3) / 1e12,
                         peak=peaks['bf16_tflops'], unit='TFLOP/s',
@@ -951,6 +1005,7 @@ def run_gpu(args, ws, rank, local):
         kernel_ms_per_step={k: v / args.steps for k, v in kernel_total.items()},
         path=(('learned warm start + ' if warm else '') + ('emdq_fit_batch' if B > 1 else 'emdq_fit') +
               (' + emdq_mosaic (fused BF16 field and warp)' if fused else
+               f' + emdq_mosaic_batch ({G} frames per call, bf16 field and warp fused)' if group_fused else
                (f' + emdq_field_batch + mosaic_warp_batch ({G} frames per call, bf16; ' +
                 ('each call after the other on one stream)' if args.one_stream else
                  'the warps on a second stream)')
@@ -960,7 +1015,8 @@ def run_gpu(args, ws, rank, local):
               (', the pass replayed from one CUDA graph' if graph is not None else '')),
         batch=B, field_group=G, field_autotune=field_tune, warm_start=warm, cuda_graph=graph is not None,
         **({'cuda_graph_note': graph_note} if graph_note else {}), wall_s=wall, roofline=roof,
-        gpu_launches=(args.steps * sum(3 * ((len(ks) + G - 1) // G) for ks in batches) if G > 1 else
+        gpu_launches=(args.steps * sum((2 if group_fused else 3) * ((len(ks) + G - 1) // G)
+                                       for ks in batches) if G > 1 else
                       total_frames * (2 if fused else 3)) + args.steps * len(batches) * (2 if warm else 1),
         clocks=clk,
         e2e=e2e, plain_fp32_gpu=plain, beside_the_step=unc,
@@ -1016,7 +1072,7 @@ def run_gpu_tiled(args, ws, rank, local):
                          dtype=torch.uint8, device=dev)
     clipped = [clip_to_band(g, origin, band) for g in grids]
     todo = [k for k in range(n_frames) if clipped[k] is not None]
-    G = max(1, min(8, args.field_group))
+    G = max(1, min(8, args.field_group or 4))
     groups = [todo[i:i + G] for i in range(0, len(todo), G)]
     zq, zc, zs = torch.zeros((n, 8), device=dev), torch.zeros(n, device=dev), torch.zeros((n, 2), device=dev)
     gw_max = max([clipped[k][2] for k in todo] + [1])
@@ -1149,7 +1205,7 @@ def run_gpu_mixed(args, ws, rank, local):
 
     # the fields of a group of G pairs in one emdq_field_batch call (main stream), their
     # warps on the warp stream beside the next group's fields; buffers double-buffered
-    G = max(1, min(16, args.field_group))
+    G = max(1, min(16, args.field_group or 4))
     warp_stream = torch.cuda.Stream(device=dev)
     groups = [list(range(b0, min(len(P), b0 + G))) for b0 in range(0, len(P), G)]
     gws = max(emdq.field_batch_workspace_size([(P[b]['out']['q'], P[b]['out']['c'], P[b]['src'],
@@ -1547,7 +1603,7 @@ def sub_result(line: dict) -> dict:
 
 def extras(args, local) -> dict:
     """Results printed beside the default line (one GPU): the latency mode of the same
-    sequence (one frame in flight: warm start, fit, BF16 field and warp per frame), the
+    sequence (one frame in flight: warm start, fit, fused BF16 field and warp per frame), the
     64-pair mixed batch and the 500-frame 1920x1080 sequence, each with its roofline object
     and its own bounded oracle sample."""
     import copy
@@ -1564,8 +1620,8 @@ def extras(args, local) -> dict:
 
     lat = run_gpu(sub(batch=1, field_group=1, steps=min(args.steps, 5), no_cpu_baseline=True), 1, 0, local)
     out['latency_mode'] = dict(
-        sub_result(lat), mode='one frame in flight: per frame the learned warm start, emdq_fit, one '
-                              'BF16 field and one warp, the fields of frame k+1 beside the warp of frame k',
+        sub_result(lat), mode='one frame in flight: per frame the learned warm start, emdq_fit and one '
+                              'fused BF16 field and warp (emdq_mosaic_batch of one frame)',
         ms_per_frame=lat['ms_per_step'] / lat['config']['frames_per_step'])
     torch.cuda.empty_cache()
     out['batch64'] = sub_result(run_gpu_mixed(sub(workload='batch64', steps=min(args.steps, 10)), 1, 0, local))

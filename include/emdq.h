@@ -484,7 +484,7 @@ EMDQ_API emdq_status emdq_batch(const emdq_pair *pairs, int count, const emdq_pa
                                 size_t workspace_bytes, void *stream);
 
 /* ------------------------------------------------------------------ emdq_mosaic ------
- * emdq_field (EMDQ_BF16) and mosaic_warp fused in one tensor-core kernel: for every grid
+ * emdq_field (EMDQ_BF16) and mosaic_warp fused in one tensor-core pass: for every grid
  * pixel the displacement of Eqs. 1-4 is computed exactly as emdq_field computes it and
  * the frame is then blended into the canvas exactly as mosaic_warp blends it, so the
  * canvas ends as the two calls would leave it, without the field going through memory.
@@ -498,6 +498,54 @@ EMDQ_API emdq_status emdq_mosaic(const float *q, const float *c, const float *sr
                         uint8_t *canvas, int canvas_w, int canvas_h, int canvas_pitch,
                         int origin_x, int origin_y, void *workspace, size_t workspace_bytes,
                         void *stream);
+
+/* ------------------------------------------------------------------ emdq_mosaic_batch -
+ * The dense field and the mosaic update of a group of frames of one sequence in one pass
+ * (Eqs. 1-4 and Sec. III-F, Eqs. 23-24, as emdq_field_batch followed by mosaic_warp_batch
+ * compute them).  The canvas ends bit for bit as after emdq_field_batch of the problems and
+ * mosaic_warp_batch of their frames, in order; the field itself is never written.  One
+ * operand-preparation launch, then one persistent tensor-core launch over the tiles of the
+ * union of the windows: for each tile the frames whose window meets it, in order, each
+ * frame's field of the tile followed at every pixel by the frame's sample at p + d(p) and the
+ * capped running average, the canvas words held on chip from the tile's first frame to its
+ * last.  Not a step of the paper: a fusion of two of its steps.  emdq_mosaic is this call
+ * with one frame.
+ *
+ *   problems      host array of `count` descriptors (1 <= count <= 16): each frame's fit (q,
+ *                 c, src, n as emdq_field), its window (grid_*, reference coordinates; not
+ *                 empty; inside the canvas after the origin shift), alpha, and `frame`, the
+ *                 device frame t (fw x fh, `channels` 1 or 3, rows `frame_pitch` bytes apart)
+ *   canvas        device, 4-byte pixels (c0, c1, c2, w) as mosaic_warp, origin as mosaic_warp;
+ *                 no other call may write the union of the windows while this one runs
+ *   tile_rows     (_ex) the tiles' pixel rows: 16, 24, 32 or 40 (the default)
+ *   workspace     device scratch of emdq_mosaic_batch_workspace_size(problems, count) bytes,
+ *                 256-byte aligned, not shared with a call in flight
+ * Asynchronous on `stream`.  Returns EMDQ_EINVAL for a bad descriptor or a window outside the
+ * canvas, EMDQ_ENOTSUP for count > 16, another tile height or a device without tcgen05,
+ * EMDQ_EWORKSPACE / EMDQ_ECUDA as emdq_field; a bounded device wait that gives up (about 2 s)
+ * is recorded as EMDQ_ETIMEOUT in the workspace's first word (the canvas is then undefined).
+ */
+typedef struct {
+    const float *q;             /* device, n x 8 warp rows (emdq_fit's q_out) */
+    const float *c;             /* device, n field weights (emdq_fit's c_out) */
+    const float *src;           /* device, n x 2 match positions in the reference frame */
+    int n;
+    int grid_x0, grid_y0, grid_w, grid_h;   /* the pixel window, reference coordinates */
+    float alpha;                /* Gaussian weight exp(-alpha |p - x_i|^2) */
+    const uint8_t *frame;       /* device frame t */
+} emdq_mosaic_problem;
+
+EMDQ_API size_t      emdq_mosaic_batch_workspace_size(const emdq_mosaic_problem *problems, int count);
+EMDQ_API emdq_status emdq_mosaic_batch(const emdq_mosaic_problem *problems, int count, int fw,
+                                       int fh, int channels, int frame_pitch, uint8_t *canvas,
+                                       int canvas_w, int canvas_h, int canvas_pitch, int origin_x,
+                                       int origin_y, void *workspace, size_t workspace_bytes,
+                                       void *stream);
+EMDQ_API emdq_status emdq_mosaic_batch_ex(const emdq_mosaic_problem *problems, int count, int fw,
+                                          int fh, int channels, int frame_pitch, uint8_t *canvas,
+                                          int canvas_w, int canvas_h, int canvas_pitch,
+                                          int origin_x, int origin_y, int tile_rows,
+                                          void *workspace, size_t workspace_bytes, void *stream);
 
 /* ------------------------------------------------------------------ learned warm start
  * Not in the paper (the paper's EMDQ starts EM without a prior).  A 16-64-64-1 network

@@ -17,7 +17,7 @@ import torch
 from ._build import LIB as _LIB_PATH, build  # noqa: F401
 
 __all__ = ['emdq_fit', 'emdq_fit_batch', 'emdq_field', 'emdq_field_batch', 'field_batch_autotune',
-           'field_batch_tile_rows', 'mosaic_warp',
+           'field_batch_tile_rows', 'emdq_mosaic_batch', 'mosaic_batch_workspace_size', 'mosaic_warp',
            'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'emdq_uncertainty', 'node_track', 'node_merge', 'node_restrict', 'feature_uncertainty',
            'keyframe_distances', 'hex_nodes', 'node_init', 'arap_smooth',
            'mosaic_insert_reference',
@@ -51,6 +51,13 @@ class _FieldProblem(ctypes.Structure):
                 ('n', ctypes.c_int), ('grid_x0', ctypes.c_int), ('grid_y0', ctypes.c_int),
                 ('grid_w', ctypes.c_int), ('grid_h', ctypes.c_int), ('alpha', ctypes.c_float),
                 ('disp_out', ctypes.c_void_p)]
+
+
+class _MosaicProblem(ctypes.Structure):
+    _fields_ = [('q', ctypes.c_void_p), ('c', ctypes.c_void_p), ('src', ctypes.c_void_p),
+                ('n', ctypes.c_int), ('grid_x0', ctypes.c_int), ('grid_y0', ctypes.c_int),
+                ('grid_w', ctypes.c_int), ('grid_h', ctypes.c_int), ('alpha', ctypes.c_float),
+                ('frame', ctypes.c_void_p)]
 
 
 class _Pair(ctypes.Structure):
@@ -119,6 +126,12 @@ def lib() -> ctypes.CDLL:
             L.emdq_field_batch_tile_rows.argtypes = [P, I]
             L.emdq_field_batch_autotune.restype = I
             L.emdq_field_batch_autotune.argtypes = [P, I, P, Z, P, I, P, P]
+            L.emdq_mosaic_batch_workspace_size.restype = Z
+            L.emdq_mosaic_batch_workspace_size.argtypes = [P, I]
+            L.emdq_mosaic_batch_ex.restype = I
+            L.emdq_mosaic_batch_ex.argtypes = [P, I, I, I, I, I, P, I, I, I, I, I, I, P, Z, P]
+            L.emdq_mosaic_batch.restype = I
+            L.emdq_mosaic_batch.argtypes = [P, I, I, I, I, I, P, I, I, I, I, I, P, Z, P]
             L.emdq_field.restype = I
             L.emdq_field.argtypes = [P, P, P, I, I, I, I, I, F, I, P, P, Z, P]
             L.mosaic_warp_batch.restype = I
@@ -401,6 +414,55 @@ def emdq_field_batch(problems, *, outs: list | None = None, workspace: torch.Ten
     if rc != 0:
         raise EmdqError('emdq_field_batch', rc)
     return res
+
+
+def _mosaic_problems(problems):
+    arr = (_MosaicProblem * max(1, len(problems)))()
+    fargs = None
+    for b, (q, c, src, grid, alpha, frame) in enumerate(problems):
+        n = c.shape[0]
+        _check(q, 'q', torch.float32, (n, 8))
+        _check(c, 'c', torch.float32, (n,))
+        _check(src, 'src', torch.float32, (n, 2))
+        fa = _frame_args(frame)
+        if fargs is not None and fa != fargs:
+            raise ValueError('frames of one sequence: the same size, channels and pitch')
+        fargs = fa
+        x0, y0, gw, gh = (int(v) for v in grid)
+        arr[b] = _MosaicProblem(_ptr(q), _ptr(c), _ptr(src), n, x0, y0, gw, gh, float(alpha), _ptr(frame))
+    return arr, fargs
+
+
+def mosaic_batch_workspace_size(problems) -> int:
+    arr, _ = _mosaic_problems(problems)
+    return lib().emdq_mosaic_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), len(problems))
+
+
+def emdq_mosaic_batch(problems, canvas: torch.Tensor, origin, *, tile_rows: int | None = None,
+                      workspace: torch.Tensor | None = None, stream=None) -> None:
+    """BF16 field and mosaic update of a group of frames of one sequence in one pass:
+    problems = [(q, c, src, grid, alpha, frame), ...] in frame order; the canvas ends bit for bit
+    as after emdq_field_batch then mosaic_warp_batch."""
+    count = len(problems)
+    if count < 1:
+        raise ValueError('at least one frame')
+    arr, (fw, fh, ch, pitch) = _mosaic_problems(problems)
+    _check(canvas, 'canvas', torch.uint8)
+    if canvas.dim() != 3 or canvas.shape[2] != 4:
+        raise ValueError('canvas must be [h, w, 4] uint8')
+    need = lib().emdq_mosaic_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), count)
+    if need == 0:
+        raise EmdqError('emdq_mosaic_batch_workspace_size', 1)
+    ws = _workspace(need, canvas.device, workspace)
+    ox, oy = (int(v) for v in origin)
+    args = [ctypes.cast(arr, ctypes.c_void_p), count, fw, fh, ch, pitch, _ptr(canvas), canvas.shape[1],
+            canvas.shape[0], canvas.shape[1] * 4, ox, oy]
+    if tile_rows is None:
+        rc = lib().emdq_mosaic_batch(*args, _ptr(ws), ws.numel(), _stream(stream))
+    else:
+        rc = lib().emdq_mosaic_batch_ex(*args, int(tile_rows), _ptr(ws), ws.numel(), _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_mosaic_batch', rc)
 
 
 def field_batch_tile_rows(problems) -> int:

@@ -25,8 +25,11 @@
 // accumulator back with tcgen05.ld (thread = pixel x = TMEM lane; for the field two warps
 // per lane quadrant, each taking half of the 32 pixel rows) and evaluate Eq. 1, so the
 // epilogue of a tile overlaps the MMAs of the next.
-// The fused variant (CH = 1 or 3) goes on from the displacement to the mosaic update of
-// the same pixel (the stand-alone warp's per-pixel code), so the field never visits HBM.
+// mosaic_tc_kernel: the same GEMM over the tiles of the union of a group of frames' windows,
+// each tile taken through the frames whose window meets it, in order; its epilogue goes on
+// from each pixel's displacement to the frame's sample and the canvas update (the
+// stand-alone warp's per-pixel code), with the tile's canvas words held in registers from
+// its first frame to its last, so the field never visits HBM.
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -51,11 +54,16 @@ constexpr int kTcStages = 4;
 constexpr int kTcPYDefault = 32;
 constexpr int kTcPYChoices[4] = {16, 24, 32, 40};
 constexpr int kTcPYMax = 40;
-// Epilogue warps: two per TMEM lane quadrant for the field (each half of the pixel rows),
-// one for the fused field + warp, whose larger per-pixel state would not fit the register
-// file twice.  Threads: producer warp, MMA warp, epilogue warps.
-constexpr int tc_epi_warps(int ch) { return ch == 0 ? 8 : 4; }
-constexpr int tc_threads(int ch) { return 64 + 32 * tc_epi_warps(ch); }
+// Epilogue warps: two per TMEM lane quadrant for the field (each half of the pixel rows);
+// five per quadrant for the fused field + warp, whose epilogue issues ~200 instructions and
+// two dependent memory round trips per pixel and frame (one warp per 8-row group of a
+// 40-row tile: with fewer, the epilogue, not the MMA, sets the rate).  Threads: producer
+// warp, MMA warp, epilogue warps.
+constexpr int kTcEpiWarps = 8;
+constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;
+constexpr int kMosEpiWarps = 20;
+constexpr int kMosThreads = 64 + 32 * kMosEpiWarps;
+constexpr int kMosPYDefault = 40;
 constexpr uint32_t kTcABytes = kTcM * kTcK * 2;
 constexpr uint32_t kTcAccCols = 256;     // one accumulator: 6 PY <= 240 columns used
 constexpr uint32_t kTcTmemCols = 2 * kTcAccCols;
@@ -167,7 +175,7 @@ struct TcProblem {
     __nv_bfloat162 *A, *B;       // BF16 operands (workspace)
     float *ref;                  // reference row, 6 floats (workspace or caller)
     int *kcount;                 // K columns the prep wrote (workspace)
-    float2 *disp;                // the displacement field (CH = 0)
+    float2 *disp;                // the displacement field (field_tc_kernel)
     int ntx, tile0, ntiles;      // GEMM tiles [tile0, tile0 + ntiles) of the batch
     int block0, a_blocks, nblocks;   // prep blocks [block0, block0 + nblocks), Ex rows first
 };
@@ -285,11 +293,9 @@ __global__ void __launch_bounds__(kPrepThreads) field_tc_prep_kernel(const __gri
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// CH = 0: write the displacement field; CH = 1 or 3: blend the frame into the canvas.
-// Tiles of kTcM x PY pixels.
-template <int CH, int PY>
-__global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(const __grid_constant__ TcBatch Bt,
-                                                                   MosaicArgs mos)
+// The displacement field of every problem of the batch, tiles of kTcM x PY pixels.
+template <int PY>
+__global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(const __grid_constant__ TcBatch Bt)
 {
     using S = TcShape<PY>;
     constexpr uint32_t kTcStageBytes = S::StageBytes;
@@ -317,7 +323,7 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(const __gri
         }
         for (int a = 0; a < 2; ++a) {
             tc::mbar_init(acc_full + a, 1);
-            tc::mbar_init(acc_empty + a, tc_epi_warps(CH));
+            tc::mbar_init(acc_empty + a, kTcEpiWarps);
         }
         tc::mbar_init(done, 1);
         *abort_flag = 0;
@@ -410,7 +416,7 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(const __gri
         // thread = pixel x of the tile; the tile's groups of 8 pixel rows are dealt to the
         // warp sets in turn (with 8 warps: warps 2-5 take groups 0, 2, ..., warps 6-9 groups
         // 1, 3, ...)
-        constexpr int kSets = tc_epi_warps(CH) / 4;
+        constexpr int kSets = kTcEpiWarps / 4;
         constexpr int kAllGroups = PY / 8;
         const int q = warp & 3;
         const int g0 = (warp - 2) >> 2;
@@ -459,33 +465,9 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(const __gri
                     }
                 }
                 const int y0 = ty * PY + g * 8;
-                if constexpr (CH == 0) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (x < gw && y0 + j < gh) disp[(size_t)(y0 + j) * gw + x] = d[j];
-                } else {
-                    // all loads of the 8 pixels first (canvas words and frame taps), then the
-                    // updates: 8 independent gathers in flight per thread
-                    Tap t[8];
-                    uchar4 cv[8];
-                    uchar4 *cp[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        t[j] = tap_setup<CH>(mos.fw, mos.fh, mos.pitch, px,
-                                             static_cast<float>(gy0 + y0 + j), d[j].x, d[j].y);
-                        t[j].ok = t[j].ok && x < gw && y0 + j < gh;
-                        cp[j] = mos.canvas + (size_t)(gy0 + y0 + j + mos.oy) * mos.cpitch4 +
-                                (gx0 + x + mos.ox);
-                        if (t[j].ok) cv[j] = *cp[j];
-                    }
-                    float v[8][CH];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (t[j].ok) tap_sample<CH>(mos.frame, t[j], v[j]);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (t[j].ok) *cp[j] = blend_update<CH>(cv[j], v[j]);
-                }
+                for (int j = 0; j < 8; ++j)
+                    if (x < gw && y0 + j < gh) disp[(size_t)(y0 + j) * gw + x] = d[j];
             }
         }
     }
@@ -498,6 +480,282 @@ __global__ void __launch_bounds__(tc_threads(CH), 1) field_tc_kernel(const __gri
         if (*abort_flag) {
             atomicMax(err, (int)EMDQ_ETIMEOUT);
             // drain loads that were issued but never consumed before the CTA exits
+            for (int k = *consumed; k < *issued; ++k)
+                tc::mbar_wait(full + (k % kTcStages), (k / kTcStages) & 1, kWaitLimit, true);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tmem, kTcTmemCols);
+}
+
+// ------------------------------------------------------------------------- fused mosaic
+// Frames and canvas of a group of frames blended in one pass; the tiles are those of the
+// union of the group's windows (reference coordinates).
+struct MosaicBatch {
+    const uint8_t *frame[kFieldBatchMax];
+    int fw, fh, pitch;
+    uchar4 *canvas;
+    int cpitch4, ox, oy;
+    int ux0, uy0, uw, uh;     // union of the windows
+    int ntx, ntiles;          // tiles across / in all of the union
+};
+
+// Does problem P's window meet the tile at (x0, y0)?
+template <int PY>
+__device__ __forceinline__ bool tile_meets(const TcProblem &P, int x0, int y0)
+{
+    return x0 < P.gx0 + P.gw && x0 + kTcM > P.gx0 && y0 < P.gy0 + P.gh && y0 + PY > P.gy0;
+}
+
+// The first problem after b whose window meets the tile (Bt.count if none).
+template <int PY>
+__device__ __forceinline__ int next_meeting(const TcBatch &Bt, int b, int x0, int y0)
+{
+    for (++b; b < Bt.count; ++b)
+        if (tile_meets<PY>(Bt.p[b], x0, y0)) break;
+    return b;
+}
+
+// Items: (tile, frame) pairs, tiles of the union in this CTA's turn, the frames meeting each
+// in order.  The TMA and MMA warps run them as field_tc_kernel runs tiles (the operand rows
+// of the tile's pixels in that frame's operands; outside its padded window TMA fills zeros,
+// and outside its window the operands are zero, so the weight channel there is 0).  The
+// epilogue warps: TMEM lane quadrant q = warp % 4, thread = pixel x; warp set s (four warps,
+// one per quadrant) takes the tile's 8-row groups s, s + kSets, ...; it reads its canvas
+// words once per tile, updates them through the tile's frames in order (each pixel's
+// displacement from Eq. 1, then the sample and the capped running average of
+// mosaic_warp_batch) and writes them back once.
+template <int CH, int PY>
+__global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_constant__ TcBatch Bt,
+                                                                 const __grid_constant__ MosaicBatch M)
+{
+    using S = TcShape<PY>;
+    constexpr uint32_t kStageBytes = S::StageBytes;
+    constexpr int kSets = kMosEpiWarps / 4;
+    constexpr int kAllGroups = PY / 8;
+    constexpr int kMyGroups = (kAllGroups + kSets - 1) / kSets;
+    int *__restrict__ err = Bt.err;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kTcStages * kStageBytes);
+    uint64_t *empty = full + kTcStages;
+    uint64_t *acc_full = empty + kTcStages;
+    uint64_t *acc_empty = acc_full + 2;
+    uint64_t *done = acc_empty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    int *issued = const_cast<int *>(abort_flag + 1);
+    int *consumed = issued + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            tc::mbar_init(full + s, 1);
+            tc::mbar_init(empty + s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(acc_full + a, 1);
+            tc::mbar_init(acc_empty + a, kMosEpiWarps);
+        }
+        tc::mbar_init(done, 1);
+        *abort_flag = 0;
+        *issued = 0;
+        *consumed = 0;
+        tc::fence_mbar_init();
+        for (int b = 0; b < Bt.count; ++b) {
+            tc::prefetch_tmap(&Bt.tmA[b]);
+            tc::prefetch_tmap(&Bt.tmB[b]);
+        }
+    }
+    if (warp == 1) tc::tmem_alloc(tmem_slot, kTcTmemCols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    // the prep launch's operands are complete from here on
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int chunk = 0;
+            for (int tile = blockIdx.x; tile < M.ntiles && !*abort_flag; tile += gridDim.x) {
+                const int x0 = M.ux0 + (tile % M.ntx) * kTcM, y0 = M.uy0 + (tile / M.ntx) * PY;
+                for (int b = next_meeting<PY>(Bt, -1, x0, y0); b < Bt.count && !*abort_flag;
+                     b = next_meeting<PY>(Bt, b, x0, y0)) {
+                    const TcProblem &P = Bt.p[b];
+                    const int nchunks = *P.kcount / kTcK;
+                    for (int k = 0; k < nchunks; ++k, ++chunk) {
+                        const int s = chunk % kTcStages;
+                        const uint32_t ph = (chunk / kTcStages) & 1;
+                        if (chunk >= kTcStages && !tc::mbar_wait(empty + s, ph ^ 1, kWaitLimit, false)) {
+                            *abort_flag = 1;
+                            break;
+                        }
+                        uint8_t *sa = smem + s * kStageBytes;
+                        tc::mbar_arrive_expect_tx(full + s, kStageBytes);
+                        tc::tma_load_2d(sa, &Bt.tmA[b], full + s, k * kTcK, x0 - P.gx0);
+                        tc::tma_load_3d(sa + kTcABytes, &Bt.tmB[b], full + s, k * kTcK, y0 - P.gy0, 0);
+                        *issued = chunk + 1;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // item it into accumulator it & 1
+            int chunk = 0, it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < M.ntiles && ok; tile += gridDim.x) {
+                const int x0 = M.ux0 + (tile % M.ntx) * kTcM, y0 = M.uy0 + (tile / M.ntx) * PY;
+                for (int b = next_meeting<PY>(Bt, -1, x0, y0); b < Bt.count && ok;
+                     b = next_meeting<PY>(Bt, b, x0, y0), ++it) {
+                    const int a = it & 1;
+                    if (it >= 2 && !tc::mbar_wait(acc_empty + a, ((it >> 1) - 1) & 1, kWaitLimit, false)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t d = tmem + a * kTcAccCols;
+                    const int nchunks = *Bt.p[b].kcount / kTcK;
+                    for (int k = 0; k < nchunks; ++k, ++chunk) {
+                        const int s = chunk % kTcStages;
+                        const uint32_t ph = (chunk / kTcStages) & 1;
+                        if (!tc::mbar_wait(full + s, ph, kWaitLimit, false)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after_sync();
+                        const uint32_t sa = tc::smem_u32(smem + s * kStageBytes);
+                        const uint32_t sb = sa + kTcABytes;
+#pragma unroll
+                        for (int kk = 0; kk < kTcK / 16; ++kk)
+                            tc::mma_f16(d, tc::desc_kmajor_sw128(sa + kk * 32),
+                                        tc::desc_kmajor_sw128(sb + kk * 32), S::Idesc, (k | kk) != 0);
+                        tc::mma_commit(empty + s);
+                        *consumed = chunk + 1;
+                    }
+                    if (ok) tc::mma_commit(acc_full + a);
+                }
+            }
+            if (!ok) *abort_flag = 1;
+            tc::mma_commit(done);   // tracks every MMA issued above, also after an abort
+        }
+    } else {
+        const int q = warp & 3;
+        const int set = (warp - 2) >> 2;
+        const bool idle = set >= kAllGroups;           // no 8-row group for this set
+        const int g_last = idle ? 0 : set + (kAllGroups - 1 - set) / kSets * kSets;
+        int it = 0;
+        bool alive = true;
+        for (int tile = blockIdx.x; tile < M.ntiles && alive; tile += gridDim.x) {
+            const int x0 = M.ux0 + (tile % M.ntx) * kTcM, y0 = M.uy0 + (tile / M.ntx) * PY;
+            int b = next_meeting<PY>(Bt, -1, x0, y0);
+            if (b >= Bt.count) continue;                 // no window meets this tile
+            const int x = x0 + q * 32 + lane;
+            const bool col_in = x < M.ux0 + M.uw;
+            const float px = static_cast<float>(x);
+            uchar4 cv[kMyGroups][8];
+#pragma unroll
+            for (int gi = 0; gi < kMyGroups; ++gi) {
+                const int g = set + gi * kSets;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int y = y0 + g * 8 + j;
+                    if (g < kAllGroups && col_in && y < M.uy0 + M.uh)
+                        cv[gi][j] = M.canvas[(size_t)(y + M.oy) * M.cpitch4 + (x + M.ox)];
+                }
+            }
+            for (; b < Bt.count; b = next_meeting<PY>(Bt, b, x0, y0), ++it) {
+                const int a = it & 1;
+                const bool ok = tc::mbar_wait(acc_full + a, (it >> 1) & 1, kWaitLimit, true);
+                tc::fence_after_sync();
+                if (!ok || *abort_flag) {
+                    *abort_flag = 1;
+                    alive = false;
+                    break;
+                }
+                if (idle) {
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(acc_empty + a);
+                    continue;
+                }
+                const TcProblem &P = Bt.p[b];
+                const uint8_t *__restrict__ frame = M.frame[b];
+                const float ra = P.ref[0], rb = P.ref[1], ru = P.ref[2], rv = P.ref[3], rs = P.ref[4];
+                const uint32_t lane_base = tmem + a * kTcAccCols + (static_cast<uint32_t>(q * 32) << 16);
+#pragma unroll
+                for (int gi = 0; gi < kMyGroups; ++gi) {
+                    const int g = set + gi * kSets;
+                    if (g >= kAllGroups) break;
+#pragma unroll
+                    for (int h = 0; h < 8; h += 4) {
+                        // four rows' channels at a time (the register budget of 20 warps)
+                        float F[kTcCh][4];
+#pragma unroll
+                        for (int ch = 0; ch < kTcCh; ++ch)
+                            tc::tmem_ld_x4(lane_base + ch * PY + g * 8 + h, F[ch]);
+                        tc::tmem_wait_ld();
+                        if (g == g_last && h == 4) {
+                            // the accumulator has been read: hand it back to the MMA warp
+                            tc::fence_before_sync();
+                            __syncwarp();
+                            if (lane == 0) tc::mbar_arrive(acc_empty + a);
+                        }
+                        // the four displacements first (the channels' registers free
+                        // before the taps), then each pixel's sample and update
+                        float dx[4], dy[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float py = static_cast<float>(y0 + g * 8 + h + j);
+                            dx[j] = NAN;
+                            dy[j] = NAN;
+                            const float w = F[5][j];
+                            if (w > 0.f) {
+                                const float inv = 1.f / w;
+                                const float2 xp = apply_blend(ra + F[0][j] * inv, rb + F[1][j] * inv,
+                                                              ru + F[2][j] * inv, rv + F[3][j] * inv,
+                                                              rs + F[4][j] * inv, px, py);
+                                dx[j] = xp.x - px;
+                                dy[j] = xp.y - py;
+                            }
+                        }
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int y = y0 + g * 8 + h + j;
+                            Tap t = tap_setup<CH>(M.fw, M.fh, M.pitch, px, static_cast<float>(y),
+                                                  dx[j], dy[j]);
+                            t.ok = t.ok && col_in && y < M.uy0 + M.uh;
+                            float v[CH];
+                            if (t.ok) tap_sample<CH>(frame, t, v);
+                            if (t.ok) cv[gi][h + j] = blend_update<CH>(cv[gi][h + j], v);
+                        }
+                    }
+                }
+            }
+            if (!alive) break;
+#pragma unroll
+            for (int gi = 0; gi < kMyGroups; ++gi) {
+                const int g = set + gi * kSets;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int y = y0 + g * 8 + j;
+                    if (g < kAllGroups && col_in && y < M.uy0 + M.uh)
+                        M.canvas[(size_t)(y + M.oy) * M.cpitch4 + (x + M.ox)] = cv[gi][j];
+                }
+            }
+        }
+    }
+    __syncwarp();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::mbar_wait(done, 0, kWaitLimit, true);
+        if (*abort_flag) {
+            atomicMax(err, (int)EMDQ_ETIMEOUT);
             for (int k = *consumed; k < *issued; ++k)
                 tc::mbar_wait(full + (k % kTcStages), (k / kTcStages) & 1, kWaitLimit, true);
         }
@@ -601,23 +859,38 @@ emdq_status tc_problem(TcBatch &Bt, int b, const float *q, const float *c, const
     return EMDQ_OK;
 }
 
-template <int CH, int PY>
+template <int PY>
 cudaError_t tc_set_smem()
 {
-    return cudaFuncSetAttribute(field_tc_kernel<CH, PY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(field_tc_kernel<PY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)TcShape<PY>::SmemBytes);
 }
 
-template <int CH, int PY>
-cudaError_t tc_launch_gemm(cudaLaunchConfig_t &cfg, const TcBatch &Bt, const MosaicArgs &mos)
+template <int PY>
+cudaError_t tc_launch_gemm(cudaLaunchConfig_t &cfg, const TcBatch &Bt)
 {
     cfg.dynamicSmemBytes = TcShape<PY>::SmemBytes;
-    return cudaLaunchKernelEx(&cfg, field_tc_kernel<CH, PY>, Bt, mos);
+    return cudaLaunchKernelEx(&cfg, field_tc_kernel<PY>, Bt);
+}
+
+// A programmatic dependent launch of `blocks` CTAs of `threads` on st: its set-up (barriers,
+// TMEM) overlaps the tail of the prep launch before it.
+cudaLaunchConfig_t pdl_config(int blocks, int threads, cudaStream_t st, cudaLaunchAttribute *at)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(threads);
+    cfg.stream = st;
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
 }
 
 // The prep launch and the GEMM launch (a programmatic dependent of the prep) of a batch
 // whose problems were filled for tiles of py pixel rows.
-emdq_status tc_run(TcBatch &Bt, int variant, int py, const MosaicArgs *mos, cudaStream_t st)
+emdq_status tc_run(TcBatch &Bt, int py, cudaStream_t st)
 {
     const DeviceInfo &D = device_info();
     static std::mutex mu;
@@ -625,9 +898,8 @@ emdq_status tc_run(TcBatch &Bt, int variant, int py, const MosaicArgs *mos, cuda
     {
         std::lock_guard<std::mutex> lk(mu);
         if (attr_dev != D.device) {
-            if (tc_set_smem<0, 16>() != cudaSuccess || tc_set_smem<0, 24>() != cudaSuccess ||
-                tc_set_smem<0, 32>() != cudaSuccess || tc_set_smem<0, 40>() != cudaSuccess ||
-                tc_set_smem<1, 32>() != cudaSuccess || tc_set_smem<3, 32>() != cudaSuccess)
+            if (tc_set_smem<16>() != cudaSuccess || tc_set_smem<24>() != cudaSuccess ||
+                tc_set_smem<32>() != cudaSuccess || tc_set_smem<40>() != cudaSuccess)
                 return EMDQ_ECUDA;
             attr_dev = D.device;
         }
@@ -638,30 +910,79 @@ emdq_status tc_run(TcBatch &Bt, int variant, int py, const MosaicArgs *mos, cuda
     field_tc_prep_kernel<<<blocks, kPrepThreads, 0, st>>>(Bt);
     if (cudaGetLastError() != cudaSuccess) return EMDQ_ECUDA;
     const int grid = Bt.total_tiles < D.sms ? Bt.total_tiles : D.sms;   // persistent: one CTA per SM
-    const MosaicArgs none{};
-    // programmatic dependent launch: the GEMM's set-up overlaps the prep kernel's tail
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(tc_threads(variant));
-    cfg.stream = st;
     cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cudaLaunchConfig_t cfg = pdl_config(grid, kTcThreads, st, at);
     cudaError_t e;
-    if (variant == 0) {
-        switch (py) {
-        case 16: e = tc_launch_gemm<0, 16>(cfg, Bt, none); break;
-        case 24: e = tc_launch_gemm<0, 24>(cfg, Bt, none); break;
-        case 40: e = tc_launch_gemm<0, 40>(cfg, Bt, none); break;
-        default: e = tc_launch_gemm<0, 32>(cfg, Bt, none); break;
-        }
-    } else if (variant == 1) {
-        e = tc_launch_gemm<1, 32>(cfg, Bt, *mos);
-    } else {
-        e = tc_launch_gemm<3, 32>(cfg, Bt, *mos);
+    switch (py) {
+    case 16: e = tc_launch_gemm<16>(cfg, Bt); break;
+    case 24: e = tc_launch_gemm<24>(cfg, Bt); break;
+    case 40: e = tc_launch_gemm<40>(cfg, Bt); break;
+    default: e = tc_launch_gemm<32>(cfg, Bt); break;
     }
+    return e == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
+}
+
+template <int CH, int PY>
+cudaError_t mosaic_launch(cudaLaunchConfig_t &cfg, const TcBatch &Bt, const MosaicBatch &M)
+{
+    static std::mutex mu;
+    static int attr_dev = -1;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (attr_dev != device_info().device) {
+            const cudaError_t e = cudaFuncSetAttribute(mosaic_tc_kernel<CH, PY>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)TcShape<PY>::SmemBytes);
+            if (e != cudaSuccess) return e;
+            attr_dev = device_info().device;
+        }
+    }
+    cfg.dynamicSmemBytes = TcShape<PY>::SmemBytes;
+    return cudaLaunchKernelEx(&cfg, mosaic_tc_kernel<CH, PY>, Bt, M);
+}
+
+template <int CH>
+cudaError_t mosaic_dispatch(int py, cudaLaunchConfig_t &cfg, const TcBatch &Bt, const MosaicBatch &M)
+{
+    switch (py) {
+    case 16: return mosaic_launch<CH, 16>(cfg, Bt, M);
+    case 24: return mosaic_launch<CH, 24>(cfg, Bt, M);
+    case 32: return mosaic_launch<CH, 32>(cfg, Bt, M);
+    default: return mosaic_launch<CH, 40>(cfg, Bt, M);
+    }
+}
+
+// The prep launch and the fused launch of a group of frames whose problems were filled for
+// tiles of py rows; M carries the frames, the canvas and the origin, and gets the union.
+emdq_status mosaic_run(TcBatch &Bt, MosaicBatch &M, int channels, int py, cudaStream_t st)
+{
+    long long ux0 = 0, uy0 = 0, ux1 = 0, uy1 = 0;
+    for (int b = 0; b < Bt.count; ++b) {
+        const TcProblem &P = Bt.p[b];
+        const long long x0 = P.gx0, y0 = P.gy0, x1 = x0 + P.gw, y1 = y0 + P.gh;
+        ux0 = (b == 0 || x0 < ux0) ? x0 : ux0;
+        uy0 = (b == 0 || y0 < uy0) ? y0 : uy0;
+        ux1 = (b == 0 || x1 > ux1) ? x1 : ux1;
+        uy1 = (b == 0 || y1 > uy1) ? y1 : uy1;
+    }
+    const long long uw = ux1 - ux0, uh = uy1 - uy0;
+    const long long ntx = (uw + kTcM - 1) / kTcM, nty = (uh + py - 1) / py;
+    if (ntx * nty > (1 << 30)) return EMDQ_ENOTSUP;
+    M.ux0 = (int)ux0;
+    M.uy0 = (int)uy0;
+    M.uw = (int)uw;
+    M.uh = (int)uh;
+    M.ntx = (int)ntx;
+    M.ntiles = (int)(ntx * nty);
+    const TcProblem &last = Bt.p[Bt.count - 1];
+    Bt.total_tiles = last.tile0 + last.ntiles;
+    field_tc_prep_kernel<<<last.block0 + last.nblocks, kPrepThreads, 0, st>>>(Bt);
+    if (cudaGetLastError() != cudaSuccess) return EMDQ_ECUDA;
+    const DeviceInfo &D = device_info();
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = pdl_config(M.ntiles < D.sms ? M.ntiles : D.sms, kMosThreads, st, at);
+    const cudaError_t e = channels == 3 ? mosaic_dispatch<3>(py, cfg, Bt, M)
+                                        : mosaic_dispatch<1>(py, cfg, Bt, M);
     return e == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }
 
@@ -732,8 +1053,7 @@ emdq_status field_tc_launch(const float *q, const float *c, const float *src, in
                             int gy0, int gw, int gh, float alpha, float *ref, float2 *disp,
                             char *ws, size_t ws_bytes, cudaStream_t st, const MosaicArgs *mos)
 {
-    const int variant = mos ? mos->channels : 0;
-    if (variant != 0 && variant != 1 && variant != 3) return EMDQ_EINVAL;
+    if (mos && mos->channels != 1 && mos->channels != 3) return EMDQ_EINVAL;
     const DeviceInfo &D = device_info();
     if (D.device < 0) return EMDQ_ECUDA;
     if (!tc_device_ok()) return EMDQ_ENOTSUP;           // tcgen05: sm_100 family only
@@ -742,10 +1062,22 @@ emdq_status field_tc_launch(const float *q, const float *c, const float *src, in
     Bt.count = 1;
     Bt.err = reinterpret_cast<int *>(ws);
     int *kcount = Bt.err + 1;                 // written by the prep kernel, read by the GEMM
+    const int py = mos ? kMosPYDefault : kTcPYDefault;
     const emdq_status rc = tc_problem(Bt, 0, q, c, src, n, gx0, gy0, gw, gh, alpha, ref, kcount,
-                                      disp, ws + kErrBytes, kTcPYDefault);
+                                      disp, ws + kErrBytes, py);
     if (rc != EMDQ_OK) return rc;
-    return tc_run(Bt, variant, kTcPYDefault, mos, st);
+    if (!mos) return tc_run(Bt, py, st);
+    // one frame through the fused group path
+    static thread_local MosaicBatch M;
+    M.frame[0] = mos->frame;
+    M.fw = mos->fw;
+    M.fh = mos->fh;
+    M.pitch = mos->pitch;
+    M.canvas = mos->canvas;
+    M.cpitch4 = mos->cpitch4;
+    M.ox = mos->ox;
+    M.oy = mos->oy;
+    return mosaic_run(Bt, M, mos->channels, py, st);
 }
 
 extern "C" size_t emdq_field_batch_workspace_size(const emdq_field_problem *problems, int count)
@@ -795,7 +1127,7 @@ emdq_status field_batch_run(const emdq_field_problem *problems, int count, int p
         if (rc != EMDQ_OK) return rc;
         off += batch_problem_bytes(f.n, f.grid_w, f.grid_h);
     }
-    return tc_run(Bt, 0, py, nullptr, static_cast<cudaStream_t>(stream));
+    return tc_run(Bt, py, static_cast<cudaStream_t>(stream));
 }
 
 }  // namespace
@@ -863,4 +1195,82 @@ extern "C" emdq_status emdq_field_batch_autotune(const emdq_field_problem *probl
     if (tile_rows_out) *tile_rows_out = best_py;
     if (ms_out) *ms_out = best;
     return EMDQ_OK;
+}
+
+// ------------------------------------------------------------------ emdq_mosaic_batch
+extern "C" size_t emdq_mosaic_batch_workspace_size(const emdq_mosaic_problem *problems, int count)
+{
+    if (!problems || count < 1 || count > kFieldBatchMax) return 0;
+    size_t total = 1024;
+    for (int b = 0; b < count; ++b) {
+        if (problems[b].n < 1 || problems[b].grid_w < 0 || problems[b].grid_h < 0) return 0;
+        total += batch_problem_bytes(problems[b].n, problems[b].grid_w, problems[b].grid_h);
+    }
+    return total;
+}
+
+extern "C" emdq_status emdq_mosaic_batch_ex(const emdq_mosaic_problem *problems, int count, int fw,
+                                            int fh, int channels, int frame_pitch, uint8_t *canvas,
+                                            int canvas_w, int canvas_h, int canvas_pitch,
+                                            int origin_x, int origin_y, int tile_rows,
+                                            void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!problems || count < 1 || !canvas || fw < 1 || fh < 1 || (channels != 1 && channels != 3) ||
+        frame_pitch < fw * channels || canvas_w < 1 || canvas_h < 1 ||
+        canvas_pitch < 4 * canvas_w || canvas_pitch % 4 != 0)
+        return EMDQ_EINVAL;
+    if (count > kFieldBatchMax || !tc_py_ok(tile_rows)) return EMDQ_ENOTSUP;
+    if (!aligned(canvas, 4)) return EMDQ_EINVAL;
+    for (int b = 0; b < count; ++b) {
+        const emdq_mosaic_problem &f = problems[b];
+        if (!f.q || !f.c || !f.src || !f.frame || f.n < 1 || f.grid_w < 1 || f.grid_h < 1 ||
+            !(f.alpha > 0.f) || !std::isfinite(f.alpha))
+            return EMDQ_EINVAL;
+        if (!aligned(f.q, 16) || !aligned(f.c, 4) || !aligned(f.src, 8)) return EMDQ_EINVAL;
+        if ((long long)f.grid_x0 + origin_x < 0 || (long long)f.grid_y0 + origin_y < 0 ||
+            (long long)f.grid_x0 + origin_x + f.grid_w > canvas_w ||
+            (long long)f.grid_y0 + origin_y + f.grid_h > canvas_h)
+            return EMDQ_EINVAL;
+    }
+    const size_t need = emdq_mosaic_batch_workspace_size(problems, count);
+    if (need == 0) return EMDQ_EINVAL;
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return EMDQ_EWORKSPACE;
+    if (device_info().device < 0) return EMDQ_ECUDA;
+    if (!tc_device_ok()) return EMDQ_ENOTSUP;
+    static thread_local TcBatch Bt;
+    static thread_local MosaicBatch M;
+    char *ws = static_cast<char *>(workspace);
+    Bt.count = count;
+    Bt.err = reinterpret_cast<int *>(ws);
+    size_t off = 1024;
+    for (int b = 0; b < count; ++b) {
+        const emdq_mosaic_problem &f = problems[b];
+        float *ref = reinterpret_cast<float *>(ws + off);
+        int *kcount = reinterpret_cast<int *>(ws + off + 64);
+        const emdq_status rc = tc_problem(Bt, b, f.q, f.c, f.src, f.n, f.grid_x0, f.grid_y0,
+                                          f.grid_w, f.grid_h, f.alpha, ref, kcount, nullptr,
+                                          ws + off + 1024, tile_rows);
+        if (rc != EMDQ_OK) return rc;
+        M.frame[b] = f.frame;
+        off += batch_problem_bytes(f.n, f.grid_w, f.grid_h);
+    }
+    M.fw = fw;
+    M.fh = fh;
+    M.pitch = frame_pitch;
+    M.canvas = reinterpret_cast<uchar4 *>(canvas);
+    M.cpitch4 = canvas_pitch / 4;
+    M.ox = origin_x;
+    M.oy = origin_y;
+    return mosaic_run(Bt, M, channels, tile_rows, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" emdq_status emdq_mosaic_batch(const emdq_mosaic_problem *problems, int count, int fw,
+                                         int fh, int channels, int frame_pitch, uint8_t *canvas,
+                                         int canvas_w, int canvas_h, int canvas_pitch, int origin_x,
+                                         int origin_y, void *workspace, size_t workspace_bytes,
+                                         void *stream)
+{
+    return emdq_mosaic_batch_ex(problems, count, fw, fh, channels, frame_pitch, canvas, canvas_w,
+                                canvas_h, canvas_pitch, origin_x, origin_y, kMosPYDefault, workspace,
+                                workspace_bytes, stream);
 }

@@ -152,6 +152,18 @@ __device__ __forceinline__ void tmem_ld_x8(uint32_t taddr, float (&v)[8])
     for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// 32 lanes x 32 bits, 4 consecutive columns.
+__device__ __forceinline__ void tmem_ld_x4(uint32_t taddr, float (&v)[4])
+{
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __uint_as_float(r[k]);
+}
+
 __device__ __forceinline__ void tmem_wait_ld()
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");

@@ -145,6 +145,39 @@ def test_noalloc_fit_argument_errors_on_the_host(libemdq):
     assert L.emdq_fit_noalloc(fake, fake, big, 640, 480, None, None, fake, fake, None, fake, None) == 7
 
 
+def test_mosaic_batch_argument_errors_on_the_host(libemdq):
+    """emdq_mosaic_batch rejects bad groups before any CUDA call: a null or empty problem list,
+    a bad frame or canvas description (EMDQ_EINVAL = 1), more than 16 frames or a tile height
+    other than 16/24/32/40 (EMDQ_ENOTSUP = 7), an empty window or one outside the canvas (1),
+    and a workspace smaller than its size query or not 256-byte aligned (EMDQ_EWORKSPACE = 6)."""
+    import paper_2103_07414_gb300 as pkg
+    L = pkg.lib()
+    fake = 1 << 20                            # aligned and never dereferenced
+    def group(count, grid=(0, 0, 64, 48), n=100):
+        arr = (pkg._MosaicProblem * count)()
+        for b in range(count):
+            arr[b] = pkg._MosaicProblem(fake, fake, fake, n, *grid, 1e-3, fake)
+        return ctypes.cast(arr, ctypes.c_void_p)
+    cv = ctypes.c_void_p(fake)
+    args = lambda g, k: (g, k, 640, 480, 3, 1920, cv, 1000, 800, 4000, 10, 10)
+    ws = ctypes.c_void_p(1 << 24)
+    size = L.emdq_mosaic_batch_workspace_size(group(2), 2)
+    assert size > 1024
+    assert L.emdq_mosaic_batch_workspace_size(group(17), 17) == 0
+    assert L.emdq_mosaic_batch(None, 1, *args(None, 1)[2:], ws, size, None) == 1
+    assert L.emdq_mosaic_batch(*args(group(1), 0), ws, size, None) == 1
+    assert L.emdq_mosaic_batch(group(1), 1, 640, 480, 2, 1920, cv, 1000, 800, 4000, 10, 10, ws, size, None) == 1
+    assert L.emdq_mosaic_batch(group(1), 1, 640, 480, 3, 1000, cv, 1000, 800, 4000, 10, 10, ws, size, None) == 1
+    assert L.emdq_mosaic_batch(group(1), 1, 640, 480, 3, 1920, cv, 1000, 800, 3999, 10, 10, ws, size, None) == 1
+    assert L.emdq_mosaic_batch(*args(group(17), 17), ws, size, None) == 7
+    assert L.emdq_mosaic_batch_ex(*args(group(2), 2), 48, ws, size, None) == 7
+    assert L.emdq_mosaic_batch(*args(group(1, grid=(0, 0, 0, 48)), 1), ws, size, None) == 1
+    assert L.emdq_mosaic_batch(*args(group(1, grid=(985, 0, 10, 10)), 1), ws, size, None) == 1
+    assert L.emdq_mosaic_batch(*args(group(1, grid=(-11, 0, 10, 10)), 1), ws, size, None) == 1
+    assert L.emdq_mosaic_batch(*args(group(2), 2), ws, size - 1, None) == 6
+    assert L.emdq_mosaic_batch(*args(group(2), 2), ctypes.c_void_p(fake + 16), size, None) == 6
+
+
 def test_warm_start_training_initialisation_on_the_host():
     """The package's training starts from He-normal weights in the kernels' packed layout:
     5313 parameters, zero biases, deterministic per seed (no GPU needed)."""
