@@ -421,7 +421,8 @@ EMDQ_API emdq_status emdq_arap_smooth(const float *x0, const float *w_merge, con
  *   canvas       device, canvas_h rows of canvas_pitch bytes (multiple of 4, >= 4 canvas_w),
  *                4-byte pixels, 4-byte aligned
  *   origin_x/y   canvas position of reference pixel (0, 0)
- * The grid, shifted by the origin, must lie inside the canvas (else EMDQ_EINVAL).
+ * The grid, shifted by the origin, must lie inside the canvas (else EMDQ_EINVAL); a frame of
+ * fh x frame_pitch bytes must hold fewer than 2^31 bytes (else EMDQ_ENOTSUP).
  */
 EMDQ_API emdq_status mosaic_warp(const uint8_t *frame, int fw, int fh, int channels, int frame_pitch,
                         const float *disp, int grid_x0, int grid_y0, int grid_w, int grid_h,
@@ -521,9 +522,10 @@ EMDQ_API emdq_status emdq_mosaic(const float *q, const float *c, const float *sr
  *   workspace     device scratch of emdq_mosaic_batch_workspace_size(problems, count) bytes,
  *                 256-byte aligned, not shared with a call in flight
  * Asynchronous on `stream`.  Returns EMDQ_EINVAL for a bad descriptor or a window outside the
- * canvas, EMDQ_ENOTSUP for count > 16, another tile height or a device without tcgen05,
- * EMDQ_EWORKSPACE / EMDQ_ECUDA as emdq_field; a bounded device wait that gives up (about 2 s)
- * is recorded as EMDQ_ETIMEOUT in the workspace's first word (the canvas is then undefined).
+ * canvas, EMDQ_ENOTSUP for count > 16, another tile height, a frame of 2^31 bytes or more or a
+ * device without tcgen05, EMDQ_EWORKSPACE / EMDQ_ECUDA as emdq_field; a bounded device wait
+ * that gives up (about 2 s) is recorded as EMDQ_ETIMEOUT in the workspace's first word (the
+ * canvas is then undefined).
  */
 typedef struct {
     const float *q;             /* device, n x 8 warp rows (emdq_fit's q_out) */

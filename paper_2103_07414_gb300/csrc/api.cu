@@ -140,6 +140,7 @@ extern "C" emdq_status emdq_mosaic(const float *q, const float *c, const float *
         canvas_pitch < 4 * canvas_w || canvas_pitch % 4 != 0)
         return EMDQ_EINVAL;
     if (!aligned(q, 16) || !aligned(src, 8) || !aligned(canvas, 4)) return EMDQ_EINVAL;
+    if ((long long)fh * frame_pitch > 0x7fffffffLL) return EMDQ_ENOTSUP;   // 32-bit tap offsets
     const size_t need = emdq_field_workspace_size(n, grid_w, grid_h, EMDQ_BF16);
     if (need == 0) return EMDQ_ENOTSUP;
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return EMDQ_EWORKSPACE;

@@ -49,10 +49,15 @@ template <int CH>
 __device__ __forceinline__ void tap_sample(const uint8_t *__restrict__ frame, const Tap &t,
                                            float (&v)[CH])
 {
+    // byte offsets in 32 bits (a frame holds fewer than 2^31 bytes; the entry points check)
+    const uint8_t *p00 = frame + static_cast<unsigned>(t.r0 + t.c0);
+    const uint8_t *p10 = frame + static_cast<unsigned>(t.r0 + t.c1);
+    const uint8_t *p01 = frame + static_cast<unsigned>(t.r1 + t.c0);
+    const uint8_t *p11 = frame + static_cast<unsigned>(t.r1 + t.c1);
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
-        v[k] = t.w00 * __ldg(frame + t.r0 + t.c0 + k) + t.w10 * __ldg(frame + t.r0 + t.c1 + k) +
-               t.w01 * __ldg(frame + t.r1 + t.c0 + k) + t.w11 * __ldg(frame + t.r1 + t.c1 + k);
+        v[k] = t.w00 * __ldg(p00 + k) + t.w10 * __ldg(p10 + k) + t.w01 * __ldg(p01 + k) +
+               t.w11 * __ldg(p11 + k);
     }
 }
 
@@ -65,23 +70,26 @@ __device__ __forceinline__ void tap_sample(const uint8_t *__restrict__ frame, co
 // IEEE division for every float a in [0, 8192) and every b = 1..31 (the whole range of
 // w c + v and w + 1 here): q is the same bits for every a >= 2^-123; below that (where the
 // residual r underflows) it can differ in the last place, and floor(q + 1/2) is the same
-// for every a in the range.
+// for every a in the range.  The clamp to [0, 255] never binds, so it is not evaluated: the
+// four tap weights are products of numbers in [0, 1] whose exact sum is 1, so the rounded
+// sample v lies in [0, 255 (1 + 2^-21)], and with c <= 255 the quotient q stays below 255.5
+// and at or above 0.
 __device__ __forceinline__ unsigned blend_channel(unsigned c, float w, float v, float w1,
                                                   float rw1)
 {
     const float a = fmaf(w, static_cast<float>(c), v);
     const float q0 = __fmul_rn(a, rw1);
     const float q = __fmaf_rn(__fmaf_rn(-q0, w1, a), rw1, q0);
-    const float z = floorf(q + 0.5f);
-    return static_cast<unsigned>(fminf(fmaxf(z, 0.f), 255.f));
+    return static_cast<unsigned>(floorf(q + 0.5f));
 }
 
+// The update of one canvas pixel from its sample v, with rw1 = RN(1/(w + 1)) for the pixel's
+// weight w (a kernel that updates many pixels may take it from a table of the 31 values).
 template <int CH>
-__device__ __forceinline__ uchar4 blend_update(uchar4 cv, const float (&v)[CH])
+__device__ __forceinline__ uchar4 blend_update_r(uchar4 cv, const float (&v)[CH], float rw1)
 {
     const float w = static_cast<float>(cv.w);
     const float w1 = w + 1.f;
-    const float rw1 = __frcp_rn(w1);
     cv.x = blend_channel(cv.x, w, v[0], w1, rw1);
     if (CH == 3) {
         cv.y = blend_channel(cv.y, w, v[1 % CH], w1, rw1);
@@ -89,6 +97,12 @@ __device__ __forceinline__ uchar4 blend_update(uchar4 cv, const float (&v)[CH])
     }
     cv.w = static_cast<unsigned char>(cv.w < 30 ? cv.w + 1 : 30);
     return cv;
+}
+
+template <int CH>
+__device__ __forceinline__ uchar4 blend_update(uchar4 cv, const float (&v)[CH])
+{
+    return blend_update_r<CH>(cv, v, __frcp_rn(static_cast<float>(cv.w) + 1.f));
 }
 
 // One pixel: canvas pixel cp receives frame t sampled at p + d, or is left untouched.

@@ -550,6 +550,10 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
     int *issued = const_cast<int *>(abort_flag + 1);
     int *consumed = issued + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // RN(1 / (w + 1)) for the canvas weights w = 0..30 (the blend's divisor), one shared load per
+    // pixel instead of a reciprocal sequence
+    __shared__ float rw1_of[32];
+    if (threadIdx.x < 32) rw1_of[threadIdx.x] = __frcp_rn(static_cast<float>(threadIdx.x) + 1.f);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTcStages; ++s) {
@@ -731,7 +735,8 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
                             t.ok = t.ok && col_in && y < M.uy0 + M.uh;
                             float v[CH];
                             if (t.ok) tap_sample<CH>(frame, t, v);
-                            if (t.ok) cv[gi][h + j] = blend_update<CH>(cv[gi][h + j], v);
+                            if (t.ok)
+                                cv[gi][h + j] = blend_update_r<CH>(cv[gi][h + j], v, rw1_of[cv[gi][h + j].w]);
                         }
                     }
                 }
@@ -1220,6 +1225,7 @@ extern "C" emdq_status emdq_mosaic_batch_ex(const emdq_mosaic_problem *problems,
         canvas_pitch < 4 * canvas_w || canvas_pitch % 4 != 0)
         return EMDQ_EINVAL;
     if (count > kFieldBatchMax || !tc_py_ok(tile_rows)) return EMDQ_ENOTSUP;
+    if ((long long)fh * frame_pitch > 0x7fffffffLL) return EMDQ_ENOTSUP;   // 32-bit tap offsets
     if (!aligned(canvas, 4)) return EMDQ_EINVAL;
     for (int b = 0; b < count; ++b) {
         const emdq_mosaic_problem &f = problems[b];

@@ -130,6 +130,7 @@ extern "C" emdq_status mosaic_warp(const uint8_t *frame, int fw, int fh, int cha
         frame_pitch < fw * channels || grid_w < 0 || grid_h < 0 || canvas_w < 1 ||
         canvas_h < 1 || canvas_pitch < 4 * canvas_w || canvas_pitch % 4 != 0)
         return EMDQ_EINVAL;
+    if ((long long)fh * frame_pitch > 0x7fffffffLL) return EMDQ_ENOTSUP;   // 32-bit tap offsets
     if (grid_w == 0 || grid_h == 0) return EMDQ_OK;      // empty window: nothing to read
     if (!disp || !aligned(disp, 8) || !aligned(canvas, 4)) return EMDQ_EINVAL;
     if ((long long)grid_x0 + origin_x < 0 || (long long)grid_y0 + origin_y < 0 ||
@@ -214,6 +215,7 @@ extern "C" emdq_status mosaic_warp_batch(const mosaic_frame *frames, int count, 
         canvas_pitch < 4 * canvas_w || canvas_pitch % 4 != 0)
         return EMDQ_EINVAL;
     if (count > kWarpBatchMax) return EMDQ_ENOTSUP;
+    if ((long long)fh * frame_pitch > 0x7fffffffLL) return EMDQ_ENOTSUP;   // 32-bit tap offsets
     if (!aligned(canvas, 4)) return EMDQ_EINVAL;
     WarpBatch W = {};
     long long ux0 = 0, uy0 = 0, ux1 = 0, uy1 = 0;

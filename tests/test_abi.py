@@ -148,7 +148,8 @@ def test_noalloc_fit_argument_errors_on_the_host(libemdq):
 def test_mosaic_batch_argument_errors_on_the_host(libemdq):
     """emdq_mosaic_batch rejects bad groups before any CUDA call: a null or empty problem list,
     a bad frame or canvas description (EMDQ_EINVAL = 1), more than 16 frames or a tile height
-    other than 16/24/32/40 (EMDQ_ENOTSUP = 7), an empty window or one outside the canvas (1),
+    other than 16/24/32/40 or a frame of 2^31 bytes or more (EMDQ_ENOTSUP = 7; mosaic_warp
+    too), an empty window or one outside the canvas (1),
     and a workspace smaller than its size query or not 256-byte aligned (EMDQ_EWORKSPACE = 6)."""
     import paper_2103_07414_gb300 as pkg
     L = pkg.lib()
@@ -174,6 +175,8 @@ def test_mosaic_batch_argument_errors_on_the_host(libemdq):
     assert L.emdq_mosaic_batch(*args(group(1, grid=(0, 0, 0, 48)), 1), ws, size, None) == 1
     assert L.emdq_mosaic_batch(*args(group(1, grid=(985, 0, 10, 10)), 1), ws, size, None) == 1
     assert L.emdq_mosaic_batch(*args(group(1, grid=(-11, 0, 10, 10)), 1), ws, size, None) == 1
+    assert L.emdq_mosaic_batch(group(1), 1, 640, 1024, 3, 1 << 21, cv, 1000, 800, 4000, 10, 10, ws, size, None) == 7
+    assert L.mosaic_warp(fake, 640, 1024, 3, 1 << 21, fake, 0, 0, 4, 4, fake, 8, 8, 32, 0, 0, None) == 7
     assert L.emdq_mosaic_batch(*args(group(2), 2), ws, size - 1, None) == 6
     assert L.emdq_mosaic_batch(*args(group(2), 2), ctypes.c_void_p(fake + 16), size, None) == 6
 
