@@ -58,6 +58,58 @@ def _src_hash(name: str) -> str:
     return hashlib.sha256(open(p, 'rb').read()).hexdigest()[:16] if os.path.exists(p) else ''
 
 
+def fit_phase_candidates(iters, max_iters=20):
+    """Round schedules for emdq_fit_batch_phases at quantiles of `iters` (the rounds each fit
+    took in a warm-up): None (one launch) first."""
+    import numpy as np
+    iters = np.asarray(iters, dtype=float)
+    cands = [None]
+    for fr in ((0.75,), (0.5, 0.8), (0.6, 0.8, 0.9), (0.5, 0.7, 0.85, 0.95)):
+        ph = sorted({min(max_iters, max(1, int(np.ceil(np.quantile(iters, f))))) for f in fr} | {max_iters})
+        if tuple(ph) not in cands and len(ph) > 1:
+            cands.append(tuple(ph))
+    return cands
+
+
+def tune_fit_phases(emdq, sets, iters, max_iters=20, reps=3, margin=0.02):
+    """The fit schedule of a workload: one launch or emdq_fit_batch_phases with EM round counts
+    at quantiles of `iters` (the rounds its fits took in a warm-up).  sets: batches
+    (problems, outs, workspace, ctas) to time on, each candidate replayed `reps` times from a
+    captured CUDA graph per batch and summed over them; phases are kept only if they beat one
+    launch by more than `margin`.  Returns (None or the phases, {schedule: ms per pass})."""
+    import numpy as np
+    import torch
+    cands = fit_phase_candidates(iters, max_iters)
+    st = torch.cuda.Stream()
+    times = {}
+    for c in cands:
+        total = 0.0
+        for probs, outs, ws, ctas in sets:
+            kw = dict(ctas=ctas) if c is None else dict(phases=list(c))
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(st):
+                emdq.emdq_fit_batch(probs, outs=outs, workspace=ws, stream=st, **kw)
+                torch.cuda.synchronize()
+                with torch.cuda.graph(g, stream=st):
+                    for _ in range(reps):
+                        emdq.emdq_fit_batch(probs, outs=outs, workspace=ws, stream=st, **kw)
+            ts = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                g.replay()
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1) / reps)
+            total += float(np.median(ts))
+        times[c] = total
+    best = min((c for c in cands if c is not None), key=times.get, default=None)
+    if best is None or times[best] > (1.0 - margin) * times[None]:
+        best = None
+    return (None if best is None else list(best)), {
+        ('one launch' if k is None else ','.join(map(str, k))): round(v, 4) for k, v in times.items()}
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
@@ -105,6 +157,10 @@ def parse_args():
                     help='a group of frames as emdq_field_batch, then mosaic_warp_batch on a second '
                          'stream (default for the sequence: one emdq_mosaic_batch call, field and '
                          'warp fused, the field never written)')
+    ap.add_argument('--no-fit-phases', action='store_true',
+                    help='every fit batch in one launch (default: the schedule, one launch or '
+                         'emdq_fit_batch_phases at quantiles of the warm-up rounds, timed after '
+                         'the warm-up and the fastest kept)')
     ap.add_argument('--no-pipeline', action='store_true',
                     help='field and warp of every frame on one stream (default: the warp of frame k '
                          'on a second stream, beside the field of frame k + 1)')
@@ -483,6 +539,8 @@ def run_gpu(args, ws, rank, local):
         wd.record(warm_stream)
         warm_done[bi] = (p0s, wd)
 
+    fit_sched = dict(phases=None)          # set by the schedule tuner after the warm-up
+
     def fit_batch(bi, ks, s_of, d_of, ev=None):
         """The fits of batch bi (frames ks) on the fit stream; returns its done event.
         ev[-1] is recorded after the warm start, ev[1] before the fit launch, ev[2] after it."""
@@ -507,7 +565,8 @@ def run_gpu(args, ws, rank, local):
                     split = [max(1, per + (1 if j < extra else 0)) for j in range(len(ks))]
                 emdq.emdq_fit_batch([(s_of(k), d_of(k), sc.w, sc.h, p0s[j]) for j, k in enumerate(ks)],
                                     outs=outs[: len(ks)], workspace=batch_ws[bi % nbuf],
-                                    ctas=split, stream=fit_stream)
+                                    ctas=split, stream=fit_stream,
+                                    phases=fit_sched['phases'] if split is None else None)
             if ev: ev[2].record(fit_stream)
             done = torch.cuda.Event()
             done.record(fit_stream)
@@ -585,6 +644,32 @@ def run_gpu(args, ws, rank, local):
         one_pass()
         torch.cuda.synchronize()
         w += 1
+    # the fit schedule: one launch per batch or emdq_fit_batch_phases at quantiles of the
+    # rounds the fits took in the warm-up, each timed on whole passes of the step (the fit
+    # inside the step runs slower than alone, so a fit timed alone is no guide); phases are
+    # kept only if they beat one launch by more than 2 %
+    fit_tune = None
+    if B > 1 and args.fit_ctas == 0 and not args.no_fit_phases:
+        # each candidate schedule timed on whole passes of the step (untimed pass, then two)
+        times = {}
+        for c in fit_phase_candidates(infos[:, 1].cpu().numpy()):
+            fit_sched['phases'] = None if c is None else list(c)
+            ts = []
+            for r in range(3):
+                flush.zero_()
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record()
+                one_pass()
+                b_.record()
+                b_.synchronize()
+                if r:
+                    ts.append(a_.elapsed_time(b_))
+            times[c] = float(np.mean(ts))
+        best = min((c for c in times if c is not None), key=times.get, default=None)
+        ph = None if best is None or times[best] > 0.98 * times[None] else list(best)
+        ms = {('one launch' if k is None else ','.join(map(str, k))): round(v, 4) for k, v in times.items()}
+        fit_sched['phases'] = ph
+        fit_tune = dict(chosen='one launch' if ph is None else ph, ms_per_pass=ms)
     # the field tile height for this sequence's field groups, chosen by the library's
     # autotuner on the last batch's first group (recorded per size class, so the calls below,
     # and the graph captured from them, use it)
@@ -947,7 +1032,9 @@ def run_gpu(args, ws, rank, local):
         # FP32 operations per match pair and EM round (an FMA counts 2): 34 in the M-step
         # pass, 22 in the leave-one-out blend
         flops = float(np.sum(launch_rounds)) * n * n * 56.0 / len(fit_ms)
-        roof = dict(bound='alu', kernel='emdq_fit_batch_kernel' if B > 1 else 'emdq_fit_kernel',
+        roof = dict(bound='alu', kernel=('emdq_fit_batch_kernel' + (' + emdq_fit_batch_next_kernel'
+                                                                     if fit_sched['phases'] else '')
+                                         if B > 1 else 'emdq_fit_kernel'),
                     achieved=flops / (np.mean(fit_ms) * 1e-3) / 1e12, peak=alu_peak, unit='TFLOP/s',
                     peak_source=alu_src, launches=len(fit_ms), mean_launch_ms=float(np.mean(fit_ms)),
                     work_per_launch=f'{flops:.4g} FP32 flops = 56 x EM rounds x N^2 over the '
@@ -1004,6 +1091,7 @@ def run_gpu(args, ws, rank, local):
                     mean_window_px=win_px, mean_em_iters=mean_iters),
         kernel_ms_per_step={k: v / args.steps for k, v in kernel_total.items()},
         path=(('learned warm start + ' if warm else '') + ('emdq_fit_batch' if B > 1 else 'emdq_fit') +
+              (f' in phases {fit_sched["phases"]} (emdq_fit_batch_phases)' if fit_sched['phases'] else '') +
               (' + emdq_mosaic (fused BF16 field and warp)' if fused else
                f' + emdq_mosaic_batch ({G} frames per call, bf16 field and warp fused)' if group_fused else
                (f' + emdq_field_batch + mosaic_warp_batch ({G} frames per call, bf16; ' +
@@ -1013,11 +1101,14 @@ def run_gpu(args, ws, rank, local):
               (', fits of the next batch on a second stream' if overlap else '') +
               (', warm starts one batch ahead on a third stream' if hoist else '') +
               (', the pass replayed from one CUDA graph' if graph is not None else '')),
-        batch=B, field_group=G, field_autotune=field_tune, warm_start=warm, cuda_graph=graph is not None,
+        batch=B, field_group=G, field_autotune=field_tune, fit_schedule=fit_tune, warm_start=warm,
+        cuda_graph=graph is not None,
         **({'cuda_graph_note': graph_note} if graph_note else {}), wall_s=wall, roofline=roof,
         gpu_launches=(args.steps * sum((2 if group_fused else 3) * ((len(ks) + G - 1) // G)
                                        for ks in batches) if G > 1 else
-                      total_frames * (2 if fused else 3)) + args.steps * len(batches) * (2 if warm else 1),
+                      total_frames * (2 if fused else 3)) +
+                     args.steps * len(batches) * ((2 if warm else 1) +
+                                                  (len(fit_sched['phases']) - 1 if fit_sched['phases'] else 0)),
         clocks=clk,
         e2e=e2e, plain_fp32_gpu=plain, beside_the_step=unc,
         speedup_vs_plain_fp32_gpu=(None if plain is None else
@@ -1202,6 +1293,13 @@ def run_gpu_mixed(args, ws, rank, local):
     emdq.warm_start(probs_sd, warm_params, outs=[x['p0'] for x in P])
     ctas, tune_ms = emdq.fit_batch_autotune(fit_probs, reps=2, outs=[x['out'] for x in P],
                                             workspace=batch_ws)
+    # then one launch with that split, or the batch in phases (the rounds of the autotuner's runs)
+    fit_phases, fit_tune = None, None
+    if not args.no_fit_phases:
+        its = [int(x['out']['info'][1].item()) for x in P]
+        fit_phases, ms = tune_fit_phases(emdq, [(fit_probs, [x['out'] for x in P], batch_ws, ctas)], its)
+        fit_tune = dict(chosen='one launch (autotuned split)' if fit_phases is None else fit_phases,
+                        ms_per_launch=ms)
 
     # the fields of a group of G pairs in one emdq_field_batch call (main stream), their
     # warps on the warp stream beside the next group's fields; buffers double-buffered
@@ -1223,7 +1321,8 @@ def run_gpu_mixed(args, ws, rank, local):
         if ev: ev[0].record()
         emdq.warm_start(probs_sd, warm_params, outs=[x['p0'] for x in P])
         if ev: ev[1].record()
-        emdq.emdq_fit_batch(fit_probs, outs=[x['out'] for x in P], workspace=batch_ws, ctas=ctas)
+        emdq.emdq_fit_batch(fit_probs, outs=[x['out'] for x in P], workspace=batch_ws,
+                            ctas=ctas if fit_phases is None else None, phases=fit_phases)
         if ev: ev[2].record()
         free = [None, None]
         for gi, grp in enumerate(groups):
@@ -1356,7 +1455,8 @@ def run_gpu_mixed(args, ws, rank, local):
                     x['frame'].copy_(hf[k], non_blocking=True)
                     x['src'].copy_(hs[k], non_blocking=True)
                     x['dst'].copy_(hd[k], non_blocking=True)
-            emdq.emdq_batch(pairs_native, warm_params=warm_params, fit_ctas=ctas, outs=outs, workspace=bws)
+            emdq.emdq_batch(pairs_native, warm_params=warm_params, outs=outs, workspace=bws,
+                            fit_ctas=ctas if fit_phases is None else None, fit_phases=fit_phases)
             if copies:
                 for k, x in enumerate(P):
                     infos[k].copy_(x['out']['info'])
@@ -1388,7 +1488,8 @@ def run_gpu_mixed(args, ws, rank, local):
     win = np.array([x['grid'][2] * x['grid'][3] for x in P], dtype=np.float64)
     if dom == 'fit':
         flops = float(np.mean([np.sum((it + 1) * ns * ns) for it in iters])) * 56.0
-        roof = dict(bound='alu', kernel='emdq_fit_batch_kernel', achieved=flops / (np.mean(fit_ms) * 1e-3) / 1e12,
+        roof = dict(bound='alu', kernel='emdq_fit_batch_kernel' + (' + emdq_fit_batch_next_kernel'
+                                                                    if fit_phases else ''), achieved=flops / (np.mean(fit_ms) * 1e-3) / 1e12,
                     peak=alu_peak, unit='TFLOP/s',
                     peak_source=f'derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x {sm_mhz:.0f} MHz',
                     launches=len(fit_ms), mean_launch_ms=float(np.mean(fit_ms)))
@@ -1419,13 +1520,17 @@ def run_gpu_mixed(args, ws, rank, local):
         higher_is_better=True, scaling='weak', vs_baseline=None, dtype='bf16', data='synthetic',
         config=mixed_config(args, ws, pairs, ctas),
         kernel_ms_per_step={k: v / args.steps for k, v in totals.items()},
-        path='learned warm start (one launch) + emdq_fit_batch (one launch, autotuned CTA split) + '
+        path='learned warm start (one launch) + ' +
+             ('emdq_fit_batch (one launch, autotuned CTA split)' if fit_phases is None else
+              f'emdq_fit_batch in phases {fit_phases} (emdq_fit_batch_phases)') + ' + '
              f'emdq_field_batch ({G} pairs per call, bf16), their mosaic_warp on a second stream' +
              (', the step replayed from one CUDA graph' if graph is not None else ''),
         cuda_graph=graph is not None, **({'cuda_graph_note': graph_note} if graph_note else {}),
-        autotune_fit_ms=tune_ms, field_tile_rows=field_tiles, mean_em_iters=float(np.mean(iters)),
+        autotune_fit_ms=tune_ms, fit_schedule=fit_tune, field_tile_rows=field_tiles,
+        mean_em_iters=float(np.mean(iters)),
         roofline=roof,
-        gpu_launches=args.steps * (2 + 2 * len(groups) + len(P)), clocks=clk, e2e=e2e, fit_status=statuses,
+        gpu_launches=args.steps * (2 + (len(fit_phases) - 1 if fit_phases else 0) + 2 * len(groups) + len(P)),
+        clocks=clk, e2e=e2e, fit_status=statuses,
         emdq_batch_device_ms=native_ms,
         p50_note='per step: the whole batch of 64 pairs is one unit of latency')
     if not args.no_cpu_baseline:
@@ -1591,7 +1696,7 @@ def run_reference(args, ws, rank):
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
 
 
-SUB_KEYS = ('value', 'unit', 'ms_per_step', 'p50_frame_ms', 'dtype', 'config', 'path',
+SUB_KEYS = ('value', 'unit', 'ms_per_step', 'p50_frame_ms', 'dtype', 'config', 'path', 'fit_schedule',
             'kernel_ms_per_step', 'roofline', 'cpu_baseline', 'e2e', 'clocks', 'fit_status',
             'mean_em_iters', 'gpu_launches', 'steps', 'warmup', 'p50_note', 'field_autotune',
             'field_tile_rows')

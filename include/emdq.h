@@ -163,11 +163,33 @@ EMDQ_API emdq_status emdq_fit_batch(const emdq_fit_problem *problems, int count,
 
 /* The batch launch with an explicit split: problem b runs on ctas[b] CTAs (host array of
  * `count` ints, each >= 1, summing to at most emdq_fit_batch_capacity(problems, count);
- * otherwise EMDQ_EINVAL).  ctas = NULL is emdq_fit_batch.  Results do not depend on the
- * split beyond the FP32 summation order of the sigma^2 partial sums. */
+ * otherwise EMDQ_EINVAL).  ctas = NULL is emdq_fit_batch.  Results depend on the split only
+ * through FP32 rounding: the summation order of the sigma^2 partial sums and the M-step's
+ * groups of rows (each CTA groups its own range of rows). */
 EMDQ_API emdq_status emdq_fit_batch_ex(const emdq_fit_problem *problems, int count,
                                        const emdq_params *prm, const int *ctas, void *workspace,
                                        size_t workspace_bytes, void *stream);
+
+/* The batch in phases, for batches whose fits need very different numbers of EM rounds (one
+ * slow fit otherwise holds the whole launch while the CTAs of the others idle).  Phase 1 is
+ * emdq_fit_batch with max_iters = phase_iters[0].  Each later phase k is one more cooperative
+ * launch in which the fits that ran phase_iters[k-1] rounds without converging (status
+ * EMDQ_ENOCONV) take every CTA, split on the device in proportion to n^2, and continue for at
+ * most phase_iters[k] - phase_iters[k-1] more rounds from the state their last round left (the
+ * posteriors p_out, sigma^2 and gamma of the fit record, the order, centroids and residuals in
+ * the workspace): the same iteration as one launch, with the FP32 roundings of the new split
+ * (the M-step's row groups, the sigma^2 partial sums).  Finished fits are left as they are.
+ * info->iters counts every phase's rounds; phase_iters[nphases - 1] takes the place of
+ * prm->max_iters.  The workspace must not change between the phases (it is one call).
+ *
+ *   phase_iters  host, nphases (1..16) strictly increasing round counts >= 1
+ *   problems     as emdq_fit_batch; every p_out must be non-NULL (EMDQ_EINVAL otherwise)
+ *   workspace    as emdq_fit_batch (the same size)
+ * Asynchronous on `stream`, all phases on the device (no host synchronisation between them). */
+EMDQ_API emdq_status emdq_fit_batch_phases(const emdq_fit_problem *problems, int count,
+                                           const emdq_params *prm, const int *phase_iters,
+                                           int nphases, void *workspace, size_t workspace_bytes,
+                                           void *stream);
 
 /* CTAs of the batch kernel that are co-resident on the current device for these problems
  * (the largest n sets the shared memory per CTA); 0 on error. */
@@ -483,6 +505,13 @@ EMDQ_API size_t      emdq_batch_workspace_size(const emdq_pair *pairs, int count
 EMDQ_API emdq_status emdq_batch(const emdq_pair *pairs, int count, const emdq_params *prm,
                                 const float *warm_params, const int *fit_ctas, void *workspace,
                                 size_t workspace_bytes, void *stream);
+/* emdq_batch with the fits in phases (emdq_fit_batch_phases; fit_phases: host, nphases round
+ * counts; every pair's p_out non-NULL; not together with fit_ctas, else EMDQ_EINVAL).
+ * fit_phases = NULL is emdq_batch. */
+EMDQ_API emdq_status emdq_batch_ex(const emdq_pair *pairs, int count, const emdq_params *prm,
+                                   const float *warm_params, const int *fit_ctas,
+                                   const int *fit_phases, int nphases, void *workspace,
+                                   size_t workspace_bytes, void *stream);
 
 /* ------------------------------------------------------------------ emdq_mosaic ------
  * emdq_field (EMDQ_BF16) and mosaic_warp fused in one tensor-core pass: for every grid

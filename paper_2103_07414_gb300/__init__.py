@@ -109,6 +109,8 @@ def lib() -> ctypes.CDLL:
             L.emdq_fit_batch.argtypes = [P, I, ctypes.POINTER(_Params), P, Z, P]
             L.emdq_fit_batch_ex.restype = I
             L.emdq_fit_batch_ex.argtypes = [P, I, ctypes.POINTER(_Params), P, P, Z, P]
+            L.emdq_fit_batch_phases.restype = I
+            L.emdq_fit_batch_phases.argtypes = [P, I, ctypes.POINTER(_Params), P, I, P, Z, P]
             L.emdq_fit_batch_capacity.restype = I
             L.emdq_fit_batch_capacity.argtypes = [P, I]
             L.emdq_fit_batch_autotune.restype = I
@@ -154,6 +156,8 @@ def lib() -> ctypes.CDLL:
             L.emdq_batch_workspace_size.argtypes = [P, I, I]
             L.emdq_batch_workspace_size.restype = Z
             L.emdq_batch.argtypes = [P, I, ctypes.POINTER(_Params), P, P, P, Z, P]
+            L.emdq_batch_ex.restype = I
+            L.emdq_batch_ex.argtypes = [P, I, ctypes.POINTER(_Params), P, P, P, I, P, Z, P]
             L.mosaic_warp_batch.argtypes = [P, I, I, I, I, I, P, I, I, I, I, I, P]
             L.mosaic_warp.restype = I
             L.mosaic_warp.argtypes = [P, I, I, I, I, P, I, I, I, I, P, I, I, I, I, I, P]
@@ -279,10 +283,12 @@ def _batch_args(problems, outs):
 def emdq_fit_batch(problems, *, alpha: float = 0.0, max_iters: int = 20, tol_p: float = 1e-3,
                    sigma2_floor: float = 0.25, outs: list | None = None,
                    workspace: torch.Tensor | None = None, ctas=None, stream=None,
-                   reserved=(0, 0, 0, 0)) -> list:
+                   reserved=(0, 0, 0, 0), phases=None) -> list:
     """Fit several independent problems in one launch.  problems: list of
     (src, dst, frame_w, frame_h) or (src, dst, frame_w, frame_h, p0).  ctas: optional CTAs per
-    problem (default: in proportion to n^2).  Returns one dict per problem as emdq_fit does."""
+    problem (default: in proportion to n^2).  phases: increasing EM round counts for
+    emdq_fit_batch_phases (the last one replaces max_iters; not with ctas).  Returns one dict
+    per problem as emdq_fit does."""
     count = len(problems)
     arr, results = _batch_args(problems, outs)
     need = lib().emdq_fit_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), count)
@@ -290,6 +296,16 @@ def emdq_fit_batch(problems, *, alpha: float = 0.0, max_iters: int = 20, tol_p: 
     ws = _workspace(need, dev, workspace)
     prm = _Params(float(alpha), int(max_iters), float(tol_p), float(sigma2_floor),
                   (ctypes.c_int * 4)(*reserved))
+    if phases is not None:
+        if ctas is not None:
+            raise ValueError('phases and ctas: one or the other')
+        ph = (ctypes.c_int * max(1, len(phases)))(*[int(v) for v in phases])
+        rc = lib().emdq_fit_batch_phases(ctypes.cast(arr, ctypes.c_void_p), count, ctypes.byref(prm),
+                                         ctypes.cast(ph, ctypes.c_void_p), len(phases), _ptr(ws),
+                                         ws.numel(), _stream(stream))
+        if rc != 0:
+            raise EmdqError('emdq_fit_batch_phases', rc)
+        return results
     split = None
     if ctas is not None:
         if len(ctas) != count:
@@ -733,12 +749,13 @@ def batch_workspace_size(pairs, warm: bool = False) -> int:
 def emdq_batch(pairs, *, warm_params: torch.Tensor | None = None, fit_ctas=None,
                alpha: float = 0.0, max_iters: int = 20, tol_p: float = 1e-3,
                sigma2_floor: float = 0.25, outs: list | None = None,
-               workspace: torch.Tensor | None = None, stream=None) -> list:
+               workspace: torch.Tensor | None = None, stream=None, fit_phases=None) -> list:
     """The whole path for up to 64 independent pairs in one call: warm start (if
     warm_params), all fits in one launch, BF16 fields 16 pairs per launch pair, and each
     pair's warp into its canvas in list order.  pairs: dicts with src, dst ([n, 2] float32),
     frame ([h, w] or [h, w, 1|3] uint8), grid (x0, y0, w, h), canvas ([H, W, 4] uint8) and
-    origin (x, y).  Returns one dict per pair (q, c, p, info) as emdq_fit does."""
+    origin (x, y).  fit_phases: the fits in phases (emdq_batch_ex; not with fit_ctas).  Returns
+    one dict per pair (q, c, p, info) as emdq_fit does."""
     count = len(pairs)
     arr, results = _pair_args(pairs, outs)
     if warm_params is not None:
@@ -754,10 +771,18 @@ def emdq_batch(pairs, *, warm_params: torch.Tensor | None = None, fit_ctas=None,
         if len(fit_ctas) != count:
             raise ValueError('fit_ctas: one entry per pair')
         split = (ctypes.c_int * count)(*[int(v) for v in fit_ctas])
-    rc = lib().emdq_batch(ctypes.cast(arr, ctypes.c_void_p), count, ctypes.byref(prm),
-                          _ptr(warm_params),
-                          ctypes.cast(split, ctypes.c_void_p) if split is not None else None,
-                          _ptr(ws), ws.numel(), _stream(stream))
+    if fit_phases is not None:
+        ph = (ctypes.c_int * max(1, len(fit_phases)))(*[int(v) for v in fit_phases])
+        rc = lib().emdq_batch_ex(ctypes.cast(arr, ctypes.c_void_p), count, ctypes.byref(prm),
+                                 _ptr(warm_params),
+                                 ctypes.cast(split, ctypes.c_void_p) if split is not None else None,
+                                 ctypes.cast(ph, ctypes.c_void_p), len(fit_phases), _ptr(ws),
+                                 ws.numel(), _stream(stream))
+    else:
+        rc = lib().emdq_batch(ctypes.cast(arr, ctypes.c_void_p), count, ctypes.byref(prm),
+                              _ptr(warm_params),
+                              ctypes.cast(split, ctypes.c_void_p) if split is not None else None,
+                              _ptr(ws), ws.numel(), _stream(stream))
     if rc != 0:
         raise EmdqError('emdq_batch', rc)
     return results

@@ -67,11 +67,13 @@ extern "C" size_t emdq_batch_workspace_size(const emdq_pair *pairs, int count, i
     return batch_layout(pairs, count, warm != 0, L) ? L.total : 0;
 }
 
-extern "C" emdq_status emdq_batch(const emdq_pair *pairs, int count, const emdq_params *prm,
-                                  const float *warm_params, const int *fit_ctas, void *workspace,
-                                  size_t workspace_bytes, void *stream)
+extern "C" emdq_status emdq_batch_ex(const emdq_pair *pairs, int count, const emdq_params *prm,
+                                     const float *warm_params, const int *fit_ctas,
+                                     const int *fit_phases, int nphases, void *workspace,
+                                     size_t workspace_bytes, void *stream)
 {
     if (!pairs || count < 1) return EMDQ_EINVAL;
+    if (fit_phases && fit_ctas) return EMDQ_EINVAL;     // a phased batch splits on its own
     if (count > kBatchMax) return EMDQ_ENOTSUP;
     for (int b = 0; b < count; ++b) {
         const emdq_pair &p = pairs[b];
@@ -110,8 +112,10 @@ extern "C" emdq_status emdq_batch(const emdq_pair *pairs, int count, const emdq_
             fp[b] = emdq_fit_problem{p.src, p.dst, p.n, p.frame_w, p.frame_h, p0[b],
                                      p.q_out, p.c_out, p.p_out, p.info};
         }
-        const emdq_status rc = emdq_fit_batch_ex(fp, count, &P, fit_ctas, ws + L.fit,
-                                                 L.field - L.fit, stream);
+        const emdq_status rc =
+            fit_phases ? emdq_fit_batch_phases(fp, count, &P, fit_phases, nphases, ws + L.fit,
+                                               L.field - L.fit, stream)
+                       : emdq_fit_batch_ex(fp, count, &P, fit_ctas, ws + L.fit, L.field - L.fit, stream);
         if (rc != EMDQ_OK) return rc;
     }
     // 3. fields of up to 16 pairs per launch pair, then their warps in pair order
@@ -138,4 +142,12 @@ extern "C" emdq_status emdq_batch(const emdq_pair *pairs, int count, const emdq_
         }
     }
     return EMDQ_OK;
+}
+
+extern "C" emdq_status emdq_batch(const emdq_pair *pairs, int count, const emdq_params *prm,
+                                  const float *warm_params, const int *fit_ctas, void *workspace,
+                                  size_t workspace_bytes, void *stream)
+{
+    return emdq_batch_ex(pairs, count, prm, warm_params, fit_ctas, nullptr, 0, workspace,
+                         workspace_bytes, stream);
 }

@@ -542,7 +542,13 @@ __device__ __forceinline__ float log2_p(float p) { return __log2f(p); }
 // One fit on a group of `ncta` co-resident CTAs of NT threads; `rank` is this CTA's index
 // in the group.
 template <int NT>
-__device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
+// p0: the initial weights (null: all 1); max_iters: EM rounds this launch may run; iters_base:
+// rounds run by earlier launches of the same fit (added to the reported count).  resume: the
+// fit continues a launch that ran iters_base rounds without converging: p0 is its posterior,
+// and its row order, centroids, residuals and its sigma^2 and gamma (the fit record) are the
+// state after its last round, so step 0 is not run again and EM goes on with the next E-step.
+__device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta, const float *p0,
+                                         int max_iters, int iters_base, bool resume)
 {
     constexpr int kWarps = NT / 32;
     const int n = A.n;
@@ -560,9 +566,9 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
         const float2 x = A.src[j], y = A.dst[j];
         S.x[j] = make_float2(A.k * x.x, A.k * x.y);
         S.y[j] = make_float2(A.k * y.x, A.k * y.y);
-        const float p = A.p0 ? A.p0[j] : 1.f;
+        const float p = p0 ? p0[j] : 1.f;
         S.p[j] = p;
-        S.lp[j] = A.p0 ? log2_p(p) : 0.f;
+        S.lp[j] = p0 ? log2_p(p) : 0.f;
         p0sum += p;
         bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(y.x) && isfinite(y.y) && isfinite(p) &&
                  p >= 0.f);
@@ -576,14 +582,17 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
         return;
     }
     float gamma = 0.5f;
-    if (A.p0) gamma = fminf(fmaxf(block_sum2<NT>(p0sum, 0.f, red).x / n, 0.05f), 0.95f);
+    if (resume) gamma = __ldcg(&A.info->gamma);
+    else if (p0) gamma = fminf(fmaxf(block_sum2<NT>(p0sum, 0.f, red).x / n, 0.05f), 0.95f);
 
     // The M-step rows of this CTA: positions [pb, pe) of the Hilbert order of the matches.
     // Every CTA sorts all the matches (the same order in each; the q staging area is free
     // until the first residual pass) and keeps the positions of its own rows.
     const int pb = static_cast<int>((long long)rank * n / ncta);
     const int pe = static_cast<int>((long long)(rank + 1) * n / ncta);
-    if ((n + ncta - 1) / ncta <= kWarps) {
+    if (resume) {
+        // the order of the earlier launch (all n positions, written by its CTAs) stands
+    } else if ((n + ncta - 1) / ncta <= kWarps) {
         // at most one row per warp in every CTA of the problem (the same decision in all of
         // them): every row is its own group (its origin its own previous centroid), so the
         // order of the rows changes nothing and the sort is skipped
@@ -738,17 +747,22 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
         return fmaxf(s2, A.sigma2_floor);
     };
 
-    // step 0
+    // step 0 (a resumed fit has its residuals and sigma^2 from the earlier launch)
     float sigma2 = A.sigma2_floor;
-    mstep_all(true);
-    int st = barrier_status(A, epoch, &s_flag, ncta);
-    if (st < EMDQ_EDEGENERATE) st = residuals_and_barrier();
-    if (st < EMDQ_EDEGENERATE) sigma2 = load_e_and_sigma2();
+    int st = EMDQ_OK;
+    if (resume) {
+        sigma2 = __ldcg(&A.info->sigma2);
+    } else {
+        mstep_all(true);
+        st = barrier_status(A, epoch, &s_flag, ncta);
+        if (st < EMDQ_EDEGENERATE) st = residuals_and_barrier();
+        if (st < EMDQ_EDEGENERATE) sigma2 = load_e_and_sigma2();
+    }
 
     int it = 0;
     bool converged = false;
     const float two_pi = 6.28318530717958647692f;
-    while (st < EMDQ_EDEGENERATE && it < A.max_iters) {
+    while (st < EMDQ_EDEGENERATE && it < max_iters) {
         ++it;
         // E-step: every CTA, all N posteriors
         float dpmax = 0.f, psum = 0.f;
@@ -803,7 +817,7 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
             else if (f == EMDQ_EDEGENERATE) out = EMDQ_EDEGENERATE;
             else if (!converged) out = EMDQ_ENOCONV;
             A.info->status = out;
-            A.info->iters = it;
+            A.info->iters = iters_base + it;
             A.info->sigma2 = sigma2;
             A.info->gamma = gamma;
         }
@@ -813,7 +827,7 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta)
 template <int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) emdq_fit_kernel(FitArgs A)
 {
-    fit_body<NT>(A, blockIdx.x, gridDim.x);
+    fit_body<NT>(A, blockIdx.x, gridDim.x, A.p0, A.max_iters, 0, false);
 }
 
 // Many fits in one cooperative launch: problem b runs on CTAs [b * group, (b + 1) * group),
@@ -821,6 +835,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) emdq_fit_kernel(FitArgs A)
 // Problem b owns CTAs [first[b], first[b + 1]): a split of the co-resident CTAs in
 // proportion to each problem's work, so problems of different sizes finish together.
 constexpr int kFitBatchMax = 64;
+constexpr int kFitMaxPhases = 16;     // phases of emdq_fit_batch_phases
 struct FitBatch {
     FitArgs a[kFitBatchMax];
     int first[kFitBatchMax + 1];
@@ -836,7 +851,73 @@ __global__ void __launch_bounds__(NT, 512 / NT) emdq_fit_batch_kernel(const __gr
         if (B.first[mid] <= (int)blockIdx.x) lo = mid;
         else hi = mid - 1;
     }
-    fit_body<NT>(B.a[lo], blockIdx.x - B.first[lo], B.first[lo + 1] - B.first[lo]);
+    const FitArgs &A = B.a[lo];
+    fit_body<NT>(A, blockIdx.x - B.first[lo], B.first[lo + 1] - B.first[lo], A.p0, A.max_iters, 0, false);
+}
+
+// CTAs of NT threads a problem of n matches can use: one warp per row.
+__host__ __device__ constexpr int fit_useful_ctas(int n, int nt) { return (n + nt / 32 - 1) / (nt / 32); }
+
+// A later phase of a phased batch: the problems that ran `before` EM rounds without converging
+// (status EMDQ_ENOCONV, before rounds) take every CTA of this launch, split in proportion to n^2
+// (at least one each, at most one warp per row, largest remainders first), and each continues
+// for at most `add` more rounds from the state its last round left: the posteriors p_out, the
+// row order, centroids and residuals in the workspace, sigma^2 and gamma in its fit record.  It
+// goes on with the next E-step, as one launch running every round would; only the split of the
+// rows over CTAs (the M-step's groups, the order of the sigma^2 partial sums), and with it the
+// FP32 rounding, differs.  Every CTA computes the same split; CTAs left over return at once.
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) emdq_fit_batch_next_kernel(const __grid_constant__ FitBatch B,
+                                                                         int before, int add)
+{
+    __shared__ int pick[3];                 // this CTA's problem, rank and CTA count
+    if (threadIdx.x == 0) {
+        int ctas[kFitBatchMax];
+        double rem[kFitBatchMax], wsum = 0.0;
+        bool on[kFitBatchMax];
+        for (int b = 0; b < B.count; ++b) {
+            const emdq_fit_info *f = B.a[b].info;
+            on[b] = __ldcg(&f->status) == EMDQ_ENOCONV && __ldcg(&f->iters) == before;
+            if (on[b]) wsum += (double)B.a[b].n * (double)B.a[b].n;
+        }
+        const int total = gridDim.x;
+        int used = 0;
+        for (int b = 0; b < B.count; ++b) {
+            ctas[b] = 0;
+            rem[b] = -1.0;
+            if (!on[b]) continue;
+            const double share = total * ((double)B.a[b].n * (double)B.a[b].n) / wsum;
+            const int cap = fit_useful_ctas(B.a[b].n, NT);
+            int k = (int)share;
+            if (k < 1) k = 1;
+            if (k > cap) k = cap;
+            ctas[b] = k;
+            rem[b] = k < cap ? share - (double)k : -1.0;
+            used += k;
+        }
+        while (used < total) {
+            int best = -1;
+            for (int b = 0; b < B.count; ++b)
+                if (rem[b] >= 0.0 && ctas[b] < fit_useful_ctas(B.a[b].n, NT) && (best < 0 || rem[b] > rem[best]))
+                    best = b;
+            if (best < 0) break;
+            ++ctas[best];
+            rem[best] -= 1.0;
+            ++used;
+        }
+        pick[0] = -1;
+        for (int b = 0, first = 0; b < B.count; first += ctas[b], ++b)
+            if (first <= (int)blockIdx.x && (int)blockIdx.x < first + ctas[b]) {
+                pick[0] = b;
+                pick[1] = blockIdx.x - first;
+                pick[2] = ctas[b];
+            }
+    }
+    __syncthreads();
+    const int b = pick[0];
+    if (b < 0) return;                      // no problem left for this CTA
+    const FitArgs &A = B.a[b];
+    fit_body<NT>(A, pick[1], pick[2], A.p_out, add, before, true);
 }
 
 }  // namespace emdq
@@ -873,7 +954,9 @@ bool fit_attributes()
     if (cudaFuncSetAttribute(emdq_fit_kernel<kFitThreadsSmall>, attr, smax) != cudaSuccess ||
         cudaFuncSetAttribute(emdq_fit_kernel<kFitThreadsLarge>, attr, smax) != cudaSuccess ||
         cudaFuncSetAttribute(emdq_fit_batch_kernel<kFitThreadsSmall>, attr, smax) != cudaSuccess ||
-        cudaFuncSetAttribute(emdq_fit_batch_kernel<kFitThreadsLarge>, attr, smax) != cudaSuccess)
+        cudaFuncSetAttribute(emdq_fit_batch_kernel<kFitThreadsLarge>, attr, smax) != cudaSuccess ||
+        cudaFuncSetAttribute(emdq_fit_batch_next_kernel<kFitThreadsSmall>, attr, smax) != cudaSuccess ||
+        cudaFuncSetAttribute(emdq_fit_batch_next_kernel<kFitThreadsLarge>, attr, smax) != cudaSuccess)
         return false;
     done_dev = D.device;
     return true;
@@ -909,7 +992,7 @@ bool fit_shape(bool batch, size_t smem, int &nt, int &capacity)
 }
 
 // CTAs of nt threads a problem of n matches can use: one warp per row.
-int useful_ctas(int n, int nt) { return (n + nt / 32 - 1) / (nt / 32); }
+int useful_ctas(int n, int nt) { return fit_useful_ctas(n, nt); }
 }  // namespace
 
 extern "C" int emdq_fit_max_n(void) { return kFitMaxN; }
@@ -1074,13 +1157,15 @@ void split_ctas(const emdq_fit_problem *problems, int count, int total, int nt, 
 
 }  // namespace
 
-extern "C" emdq_status emdq_fit_batch_ex(const emdq_fit_problem *problems, int count,
-                                         const emdq_params *prm, const int *ctas, void *workspace,
-                                         size_t workspace_bytes, void *stream)
+namespace {
+
+// The checks, the CTA split and the per-problem arguments of a batched fit; on success B, nt
+// (threads per CTA), smem and cap (co-resident CTAs) are set and every problem's barrier words
+// are cleared on st.
+emdq_status fit_batch_setup(const emdq_fit_problem *problems, int count, const emdq_params &P,
+                            const int *ctas, void *workspace, size_t workspace_bytes,
+                            cudaStream_t st, FitBatch &B, int &nt, size_t &smem, int &cap)
 {
-    emdq_params P;
-    emdq_default_params(&P);
-    if (prm) P = *prm;
     if (!problems || count < 1 || P.max_iters < 0 || !(P.tol_p >= 0.f) || !(P.sigma2_floor > 0.f))
         return EMDQ_EINVAL;
     if (count > kFitBatchMax) return EMDQ_ENOTSUP;
@@ -1099,13 +1184,13 @@ extern "C" emdq_status emdq_fit_batch_ex(const emdq_fit_problem *problems, int c
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return EMDQ_EWORKSPACE;
     const DeviceInfo &D = device_info();
     if (D.device < 0) return EMDQ_ECUDA;
-    const size_t smem = fit_smem_bytes(max_n);
+    smem = fit_smem_bytes(max_n);
     if (smem > D.smem_optin) return EMDQ_ENOTSUP;
-    int nt = 0, cap = 0;
+    nt = 0;
+    cap = 0;
     if (!fit_shape(true, smem, nt, cap)) return EMDQ_ECUDA;
     if (count > cap) return EMDQ_ENOTSUP;     // more problems than co-resident CTAs
 
-    FitBatch B;
     B.count = count;
     {
         int split[kFitBatchMax];
@@ -1125,7 +1210,6 @@ extern "C" emdq_status emdq_fit_batch_ex(const emdq_fit_problem *problems, int c
     }
 
     char *ws = static_cast<char *>(workspace);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(ws, 0, 256 * (size_t)count, st) != cudaSuccess) return EMDQ_ECUDA;
     size_t off = 256 * (size_t)count;
     const double log2e = 1.4426950408889634074;
@@ -1157,8 +1241,17 @@ extern "C" emdq_status emdq_fit_batch_ex(const emdq_fit_problem *problems, int c
         A.ord = reinterpret_cast<int *>(ws + off + L.ord_off);
         off += batch_body_bytes(q.n);
     }
+    return EMDQ_OK;
+}
+
+// One cooperative launch of `grid` CTAs: the first phase (add < 0: every problem from its p0,
+// its own CTA range) or a later one (the problems unconverged after `before` rounds, `add`
+// more rounds).
+emdq_status fit_batch_launch(const FitBatch &B, int grid, int nt, size_t smem, cudaStream_t st,
+                             int before, int add)
+{
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(B.first[count]);
+    cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(nt);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -1167,10 +1260,77 @@ extern "C" emdq_status emdq_fit_batch_ex(const emdq_fit_problem *problems, int c
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+    cudaError_t e;
+    if (add < 0)
+        e = nt == kFitThreadsSmall ? cudaLaunchKernelEx(&cfg, emdq_fit_batch_kernel<kFitThreadsSmall>, B)
+                                   : cudaLaunchKernelEx(&cfg, emdq_fit_batch_kernel<kFitThreadsLarge>, B);
+    else
+        e = nt == kFitThreadsSmall
+                ? cudaLaunchKernelEx(&cfg, emdq_fit_batch_next_kernel<kFitThreadsSmall>, B, before, add)
+                : cudaLaunchKernelEx(&cfg, emdq_fit_batch_next_kernel<kFitThreadsLarge>, B, before, add);
+    return e == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
+}
+
+}  // namespace
+
+extern "C" emdq_status emdq_fit_batch_ex(const emdq_fit_problem *problems, int count,
+                                         const emdq_params *prm, const int *ctas, void *workspace,
+                                         size_t workspace_bytes, void *stream)
+{
+    emdq_params P;
+    emdq_default_params(&P);
+    if (prm) P = *prm;
+    static thread_local FitBatch B;
+    int nt = 0, cap = 0;
+    size_t smem = 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const emdq_status rc = fit_batch_setup(problems, count, P, ctas, workspace, workspace_bytes, st,
+                                           B, nt, smem, cap);
+    if (rc != EMDQ_OK) return rc;
+    return fit_batch_launch(B, B.first[count], nt, smem, st, 0, -1);
+}
+
+extern "C" emdq_status emdq_fit_batch_phases(const emdq_fit_problem *problems, int count,
+                                             const emdq_params *prm, const int *phase_iters,
+                                             int nphases, void *workspace, size_t workspace_bytes,
+                                             void *stream)
+{
+    if (!phase_iters || nphases < 1 || nphases > kFitMaxPhases) return EMDQ_EINVAL;
+    for (int k = 0; k < nphases; ++k)
+        if (phase_iters[k] < 1 || (k > 0 && phase_iters[k] <= phase_iters[k - 1])) return EMDQ_EINVAL;
+    if (problems && count >= 1 && count <= kFitBatchMax)
+        for (int b = 0; b < count; ++b)
+            if (!problems[b].p_out) return EMDQ_EINVAL;     // the next phase starts from it
+    emdq_params P;
+    emdq_default_params(&P);
+    if (prm) P = *prm;
+    P.max_iters = phase_iters[0];
+    static thread_local FitBatch B;
+    int nt = 0, cap = 0;
+    size_t smem = 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    emdq_status rc = fit_batch_setup(problems, count, P, nullptr, workspace, workspace_bytes, st, B,
+                                     nt, smem, cap);
+    if (rc != EMDQ_OK) return rc;
+    rc = fit_batch_launch(B, B.first[count], nt, smem, st, 0, -1);
+    if (rc != EMDQ_OK || nphases == 1) return rc;
+    // later phases: every co-resident CTA of the continuation kernel
+    int per = 0;
     const cudaError_t e = nt == kFitThreadsSmall
-                              ? cudaLaunchKernelEx(&cfg, emdq_fit_batch_kernel<kFitThreadsSmall>, B)
-                              : cudaLaunchKernelEx(&cfg, emdq_fit_batch_kernel<kFitThreadsLarge>, B);
-    if (e != cudaSuccess) return EMDQ_ECUDA;
+                              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &per, emdq_fit_batch_next_kernel<kFitThreadsSmall>, nt, smem)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &per, emdq_fit_batch_next_kernel<kFitThreadsLarge>, nt, smem);
+    if (e != cudaSuccess || per < 1) return EMDQ_ECUDA;
+    int grid = per * device_info().sms;
+    if (grid > cap) grid = cap;
+    for (int k = 1; k < nphases; ++k) {
+        // the barrier words start every launch at zero
+        if (cudaMemsetAsync(workspace, 0, 256 * (size_t)count, st) != cudaSuccess) return EMDQ_ECUDA;
+        rc = fit_batch_launch(B, grid, nt, smem, st, phase_iters[k - 1],
+                              phase_iters[k] - phase_iters[k - 1]);
+        if (rc != EMDQ_OK) return rc;
+    }
     return EMDQ_OK;
 }
 

@@ -181,6 +181,31 @@ def test_mosaic_batch_argument_errors_on_the_host(libemdq):
     assert L.emdq_mosaic_batch(*args(group(2), 2), ctypes.c_void_p(fake + 16), size, None) == 6
 
 
+def test_fit_batch_phases_argument_errors_on_the_host(libemdq):
+    """emdq_fit_batch_phases rejects, before any CUDA call (EMDQ_EINVAL = 1): no phases, more
+    than 16, counts that do not increase or are below 1, and a problem without p_out (a later
+    phase starts from it)."""
+    import paper_2103_07414_gb300 as pkg
+    L = pkg.lib()
+    fake = 1 << 20
+    arr = (pkg._Problem * 2)()
+    for b in range(2):
+        arr[b] = pkg._Problem(fake, fake, 100, 640, 480, None, fake, fake, fake, fake)
+    probs = ctypes.cast(arr, ctypes.c_void_p)
+    ws = ctypes.c_void_p(1 << 24)
+    def call(phases, pr=probs):
+        ph = (ctypes.c_int * max(1, len(phases)))(*phases)
+        return L.emdq_fit_batch_phases(pr, 2, None, ctypes.cast(ph, ctypes.c_void_p), len(phases),
+                                       ws, 1 << 30, None)
+    assert call([]) == 1
+    assert call(list(range(1, 18))) == 1
+    assert call([5, 5]) == 1
+    assert call([6, 4]) == 1
+    assert call([0, 4]) == 1
+    arr[1] = pkg._Problem(fake, fake, 100, 640, 480, None, fake, fake, None, fake)
+    assert call([6, 10]) == 1
+
+
 def test_warm_start_training_initialisation_on_the_host():
     """The package's training starts from He-normal weights in the kernels' packed layout:
     5313 parameters, zero biases, deterministic per seed (no GPU needed)."""

@@ -40,7 +40,7 @@ def _mixed(emdq, seed, count, shared_canvas=False):
     return out
 
 
-def _components(emdq, P, warm_params, fit_ctas=None):
+def _components(emdq, P, warm_params, fit_ctas=None, fit_phases=None):
     """The documented order: warm start, all fits, then per group of 16 the fields and the
     warps in pair order."""
     p0 = None
@@ -48,7 +48,7 @@ def _components(emdq, P, warm_params, fit_ctas=None):
         p0 = emdq.warm_start([(x['src'], x['dst']) for x in P], warm_params)
     probs = [(x['src'], x['dst'], x['sc'].w, x['sc'].h) + ((p0[b],) if p0 is not None else ())
              for b, x in enumerate(P)]
-    fits = emdq.emdq_fit_batch(probs, ctas=fit_ctas)
+    fits = emdq.emdq_fit_batch(probs, ctas=fit_ctas, phases=fit_phases)
     for g0 in range(0, len(P), 16):
         grp = list(range(g0, min(len(P), g0 + 16)))
         disps = emdq.emdq_field_batch([(fits[b]['q'], fits[b]['c'], P[b]['src'], P[b]['grid'],
@@ -83,6 +83,20 @@ def test_batch_equals_component_calls(emdq, warm):
             assert torch.equal(got[b][k], want[b][k]), (b, k)
         # small pairs with many outliers may stop at the iteration cap
         assert emdq.read_fit_info(got[b]['info'])['status_name'] in ('OK', 'ENOCONV')
+        assert torch.equal(P[b]['canvas'], Q[b]['canvas']), b
+
+
+def test_batch_with_fit_phases_equals_component_calls(emdq):
+    """emdq_batch_ex: the fits in phases (emdq_fit_batch_phases), the rest as emdq_batch."""
+    P = _mixed(emdq, 23, 20)
+    Q = _clone_canvases(P)
+    warm_params = emdq.load_warmstart_params()
+    got = emdq.emdq_batch(P, warm_params=warm_params, fit_phases=[5, 9, 14, 20])
+    want = _components(emdq, Q, warm_params, fit_phases=[5, 9, 14, 20])
+    torch.cuda.synchronize()
+    for b in range(len(P)):
+        for k in ('q', 'c', 'p', 'info'):
+            assert torch.equal(got[b][k], want[b][k]), (b, k)
         assert torch.equal(P[b]['canvas'], Q[b]['canvas']), b
 
 
