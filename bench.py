@@ -58,6 +58,13 @@ def _src_hash(name: str) -> str:
     return hashlib.sha256(open(p, 'rb').read()).hexdigest()[:16] if os.path.exists(p) else ''
 
 
+def fused_group_size(batch: int, cap: int = 16) -> int:
+    """Frames per emdq_mosaic_batch call for a fit batch of `batch` frames: the fewest calls of
+    at most `cap` frames, the frames spread evenly over them (13 for 50)."""
+    calls = -(-batch // cap)
+    return -(-batch // calls)
+
+
 def fit_phase_candidates(iters, max_iters=20):
     """Round schedules for emdq_fit_batch_phases at quantiles of `iters` (the rounds each fit
     took in a warm-up): None (one launch) first."""
@@ -444,7 +451,7 @@ def run_gpu(args, ws, rank, local):
     elif args.field_group > 0:
         G = max(1, min(16 if group_fused else 8, args.field_group))
     elif group_fused:
-        G = -(-B // -(-B // 16))          # ceil(B / calls), calls = ceil(B / 16)
+        G = fused_group_size(B)
     else:
         G = 4
     warp_stream = (torch.cuda.Stream(device=dev) if piped and not args.one_stream and not group_fused

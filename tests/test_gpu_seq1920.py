@@ -1,9 +1,9 @@
 """GPU parity at the full size of the 500-frame 1920x1080 sequence (N = 5000 matches per
 frame, 8192^2 canvas), in the launch configuration the sequence benchmark times: the fits
-of 8 frames in one emdq_fit_batch launch, the BF16 fields of 4 frames in one
-emdq_field_batch call and their warps in one mosaic_warp_batch call.  The oracle runs the
-whole fit of four of the frames; fields are compared on sampled pixels, the canvas
-everywhere."""
+of 8 frames in one emdq_fit_batch launch and their fields and warps in one emdq_mosaic_batch
+call, checked against the split calls (the BF16 fields of 4 frames in one emdq_field_batch
+call, their warps in one mosaic_warp_batch call).  The oracle runs the whole fit of four of
+the frames; fields are compared on sampled pixels, the canvas everywhere."""
 import numpy as np
 import pytest
 import torch
@@ -136,3 +136,35 @@ def test_warp_batch_of_4_on_the_8192_canvas(emdq, orc, seq):
     assert diff.max() <= 1
     touched = cv_o[..., 3] > 1
     assert (diff[touched] > 0).mean() < 1e-3
+
+
+def test_fused_group_of_8_equals_field_then_warp(emdq, seq):
+    """The benchmark's group call on this sequence: the fields and warps of the 8 frames (their
+    GPU fits; windows spread along the camera's path, so the union holds tiles that some frames
+    do not meet) in one emdq_mosaic_batch call leave the 8192^2 canvas bit for bit as
+    emdq_field_batch followed by mosaic_warp_batch, in frame order."""
+    sc = seq['sc']
+    cw, chh, origin = seq['cw'], seq['chh'], seq['origin']
+    src = {t: torch.from_numpy(seq['matches'][t][0]).cuda() for t in FRAMES}
+    dst = {t: torch.from_numpy(seq['matches'][t][1]).cuda() for t in FRAMES}
+    fits = dict(zip(FRAMES, emdq.emdq_fit_batch([(src[t], dst[t], sc.w, sc.h) for t in FRAMES])))
+    grids = {t: footprint_window(sc, t, cw, chh) for t in FRAMES}
+    frames = {t: render_frame(sc, t, device='cuda') for t in FRAMES}
+    alpha = emdq.alpha_for_frame(sc.w, sc.h)
+    base = torch.zeros((chh, cw, 4), dtype=torch.uint8, device='cuda')
+    ox, oy = origin
+    base[oy:oy + sc.h, ox:ox + sc.w, :3] = 90
+    base[oy:oy + sc.h, ox:ox + sc.w, 3] = 1
+    want = base.clone()
+    disps = emdq.emdq_field_batch([(fits[t]['q'], fits[t]['c'], src[t], grids[t], alpha) for t in FRAMES])
+    emdq.mosaic_warp_batch([frames[t] for t in FRAMES], disps, [grids[t] for t in FRAMES], want, origin)
+    got = base.clone()
+    emdq.emdq_mosaic_batch([(fits[t]['q'], fits[t]['c'], src[t], grids[t], alpha, frames[t]) for t in FRAMES],
+                           got, origin)
+    torch.cuda.synchronize()
+    assert torch.equal(got, want)
+    touched = int((got[..., 3] > 1).sum())
+    print(f'{touched} canvas pixels blended; union of the windows '
+          f'{max(g[0] + g[2] for g in grids.values()) - min(g[0] for g in grids.values())} x '
+          f'{max(g[1] + g[3] for g in grids.values()) - min(g[1] for g in grids.values())}')
+    assert touched > sc.w * sc.h
