@@ -78,19 +78,16 @@ __device__ __forceinline__ void near8_offer(Near8 &L, float d, int i)
 // The warp's 8 nearest over all lanes' lists, ascending (consumes the lists).
 __device__ __forceinline__ void near8_merge(Near8 &L, float (&nd)[kKnn], int (&ni)[kKnn])
 {
+    // round r: the least (d, i) of the lanes' heads.  Squared distances are +0 or positive
+    // (NaN is never kept, empty slots are +inf), so their bits order as unsigned integers:
+    // the warp minimum of the bits, then the least index among the lanes that hold it
 #pragma unroll
     for (int r = 0; r < kKnn; ++r) {
-        float cd = L.d[0];
-        int ci = L.i[0];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float od = __shfl_xor_sync(0xffffffffu, cd, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
-            if (near8_before(od, oi, cd, ci)) {
-                cd = od;
-                ci = oi;
-            }
-        }
+        const unsigned hb = __float_as_uint(L.d[0]);
+        const unsigned mb = __reduce_min_sync(0xffffffffu, hb);
+        const int ci = static_cast<int>(__reduce_min_sync(
+            0xffffffffu, hb == mb ? static_cast<unsigned>(L.i[0]) : 0xffffffffu));
+        const float cd = __uint_as_float(mb);
         nd[r] = cd;
         ni[r] = ci;
         if (L.i[0] == ci) {          // this lane held the winner: pop its head
@@ -142,10 +139,16 @@ __device__ __forceinline__ void near8_features(const float2 *__restrict__ src,
             f1[k] = lo;
             f1[k + 1] = hi;
         }
+    // the distances (already ascending): lane k < 8 takes the k-th, all lanes get all 8
+    float dk = nd[0];
+#pragma unroll
+    for (int k = 1; k < kKnn; ++k)
+        if (lane == k) dk = nd[k];
+    const float lk = log1pf(sqrtf(dk));
 #pragma unroll
     for (int k = 0; k < kKnn; ++k) {
         f[k] = f1[k];
-        f[kKnn + k] = log1pf(sqrtf(nd[k]));      // distances, already ascending
+        f[kKnn + k] = __shfl_sync(0xffffffffu, lk, k);
     }
 }
 
@@ -185,10 +188,15 @@ __global__ void __launch_bounds__(256) warm_features_kernel(const float2 *__rest
 }
 
 // ------------------------------------------------------------------ network ------------
-// Parameters rounded to BF16, staged in shared memory as floats, with W1 and W2 transposed
-// ([in][out]) so that lane-per-output reads are conflict-free.
-constexpr int kSwW1T = 0, kSwB1 = kSwW1T + kNin * kNh, kSwW2T = kSwB1 + kNh,
-              kSwB2 = kSwW2T + kNh * kNh, kSwW3 = kSwB2 + kNh, kSwB3 = kSwW3 + kNh;
+// Parameters rounded to BF16, staged in shared memory as floats: W1 and W2 by output row
+// ([out][in]), each row padded to a multiple of 4 floats plus 4, so that the lanes' 16-byte
+// reads of four inputs of their own rows fall in distinct banks; then per warp 64 floats for the
+// hidden layer (every lane reads its values by broadcast).
+constexpr int kSwLd1 = kNin + 4, kSwLd2 = kNh + 4;
+constexpr int kSwW1 = 0, kSwB1 = kSwW1 + kNh * kSwLd1, kSwW2 = kSwB1 + kNh,
+              kSwB2 = kSwW2 + kNh * kSwLd2, kSwW3 = kSwB2 + kNh, kSwB3 = kSwW3 + kNh,
+              kSwH = (kSwB3 + 1 + 3) / 4 * 4;
+static_assert(kSwW1 % 4 == 0 && kSwW2 % 4 == 0 && kSwLd1 % 4 == 0 && kSwLd2 % 4 == 0, "16-byte rows");
 
 // Parameters rounded to BF16 in their stored layout (for the training kernel).
 __device__ __forceinline__ void stage_params(const float *__restrict__ w, float *sw)
@@ -202,9 +210,9 @@ __device__ __forceinline__ void stage_params_t(const float *__restrict__ w, floa
     for (int k = threadIdx.x; k < kNParams; k += blockDim.x) {
         const float v = bf(w[k]);
         int d;
-        if (k < kOffB1) d = kSwW1T + (k % kNin) * kNh + k / kNin;                  // W1[o][m]
+        if (k < kOffB1) d = kSwW1 + (k / kNin) * kSwLd1 + k % kNin;                 // W1[o][m]
         else if (k < kOffW2) d = kSwB1 + (k - kOffB1);
-        else if (k < kOffB2) d = kSwW2T + ((k - kOffW2) % kNh) * kNh + (k - kOffW2) / kNh;
+        else if (k < kOffB2) d = kSwW2 + ((k - kOffW2) / kNh) * kSwLd2 + (k - kOffW2) % kNh;
         else if (k < kOffW3) d = kSwB2 + (k - kOffB2);
         else if (k < kOffB3) d = kSwW3 + (k - kOffW3);
         else d = kSwB3;
@@ -214,27 +222,49 @@ __device__ __forceinline__ void stage_params_t(const float *__restrict__ w, floa
 }
 
 // One sample per warp: lane l computes hidden units l and l + 32 of both layers; inputs
-// rounded to BF16, FP32 accumulation; returns the logit z in every lane.
+// rounded to BF16, FP32 accumulation in input order; returns the logit z in every lane.  hs:
+// this warp's 64 floats of shared scratch (the first hidden layer, read by broadcast).
 __device__ __forceinline__ float mlp_forward_warp(const float *sw, const float (&f)[2 * kKnn],
-                                                  int lane)
+                                                  int lane, float *hs)
 {
     float x[kNin];
 #pragma unroll
     for (int m = 0; m < kNin; ++m) x[m] = bf(f[m]);
     float a0 = sw[kSwB1 + lane], a1 = sw[kSwB1 + lane + 32];
+    const float *r0 = sw + kSwW1 + lane * kSwLd1, *r1 = sw + kSwW1 + (lane + 32) * kSwLd1;
 #pragma unroll
-    for (int m = 0; m < kNin; ++m) {
-        a0 = fmaf(sw[kSwW1T + m * kNh + lane], x[m], a0);
-        a1 = fmaf(sw[kSwW1T + m * kNh + lane + 32], x[m], a1);
+    for (int m = 0; m < kNin; m += 4) {
+        const float4 u = *reinterpret_cast<const float4 *>(r0 + m);
+        const float4 v = *reinterpret_cast<const float4 *>(r1 + m);
+        a0 = fmaf(u.x, x[m], a0);
+        a0 = fmaf(u.y, x[m + 1], a0);
+        a0 = fmaf(u.z, x[m + 2], a0);
+        a0 = fmaf(u.w, x[m + 3], a0);
+        a1 = fmaf(v.x, x[m], a1);
+        a1 = fmaf(v.y, x[m + 1], a1);
+        a1 = fmaf(v.z, x[m + 2], a1);
+        a1 = fmaf(v.w, x[m + 3], a1);
     }
-    const float h0 = bf(fmaxf(a0, 0.f)), h1 = bf(fmaxf(a1, 0.f));
+    hs[lane] = bf(fmaxf(a0, 0.f));
+    hs[lane + 32] = bf(fmaxf(a1, 0.f));
+    __syncwarp();
     float c0 = sw[kSwB2 + lane], c1 = sw[kSwB2 + lane + 32];
+    const float *q0 = sw + kSwW2 + lane * kSwLd2, *q1 = sw + kSwW2 + (lane + 32) * kSwLd2;
 #pragma unroll
-    for (int k = 0; k < kNh; ++k) {
-        const float hk = __shfl_sync(0xffffffffu, k < 32 ? h0 : h1, k & 31);
-        c0 = fmaf(sw[kSwW2T + k * kNh + lane], hk, c0);
-        c1 = fmaf(sw[kSwW2T + k * kNh + lane + 32], hk, c1);
+    for (int k = 0; k < kNh; k += 4) {
+        const float4 h = *reinterpret_cast<const float4 *>(hs + k);
+        const float4 u = *reinterpret_cast<const float4 *>(q0 + k);
+        const float4 v = *reinterpret_cast<const float4 *>(q1 + k);
+        c0 = fmaf(u.x, h.x, c0);
+        c0 = fmaf(u.y, h.y, c0);
+        c0 = fmaf(u.z, h.z, c0);
+        c0 = fmaf(u.w, h.w, c0);
+        c1 = fmaf(v.x, h.x, c1);
+        c1 = fmaf(v.y, h.y, c1);
+        c1 = fmaf(v.z, h.z, c1);
+        c1 = fmaf(v.w, h.w, c1);
     }
+    __syncwarp();                           // the scratch is free for the next sample
     float z = sw[kSwW3 + lane] * bf(fmaxf(c0, 0.f)) + sw[kSwW3 + lane + 32] * bf(fmaxf(c1, 0.f));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
@@ -242,21 +272,22 @@ __device__ __forceinline__ float mlp_forward_warp(const float *sw, const float (
 }
 
 constexpr int kNetThreads = 256;
-constexpr int kNetSmem = kNParams * sizeof(float);
+constexpr int kSwTotal = kSwH + 64 * (kNetThreads / 32);   // staged network + hidden scratch
 
 __global__ void __launch_bounds__(kNetThreads) warm_infer_kernel(const float *__restrict__ feat,
                                                                  int n, const float *__restrict__ w,
                                                                  float *__restrict__ p0)
 {
-    __shared__ float sw[kNParams];
+    __shared__ __align__(16) float sw[kSwTotal];
     stage_params_t(w, sw);
     const int lane = threadIdx.x & 31;
+    float *hs = sw + kSwH + 64 * (threadIdx.x >> 5);
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += nw) {
         float f[2 * kKnn];
 #pragma unroll
         for (int m = 0; m < 2 * kKnn; ++m) f[m] = feat[16 * (size_t)j + m];
-        const float z = mlp_forward_warp(sw, f, lane);
+        const float z = mlp_forward_warp(sw, f, lane, hs);
         if (lane == 0) p0[j] = 1.f / (1.f + expf(-z));
     }
 }
@@ -275,9 +306,10 @@ struct WarmBatch {
 __global__ void __launch_bounds__(kNetThreads) warm_start_batch_kernel(
     const __grid_constant__ WarmBatch B, const float *__restrict__ w)
 {
-    __shared__ float sw[kNParams];
+    __shared__ __align__(16) float sw[kSwTotal];
     stage_params_t(w, sw);
     const int lane = threadIdx.x & 31;
+    float *hs = sw + kSwH + 64 * (threadIdx.x >> 5);
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int total = B.first[B.count];
     int b = 0;
@@ -286,7 +318,7 @@ __global__ void __launch_bounds__(kNetThreads) warm_start_batch_kernel(
         const int j = g - B.first[b];
         float f[2 * kKnn];
         knn_features_warp(B.src[b], B.dst[b], B.n[b], j, lane, f);
-        const float z = mlp_forward_warp(sw, f, lane);
+        const float z = mlp_forward_warp(sw, f, lane, hs);
         if (lane == 0) B.p0[b][j] = 1.f / (1.f + expf(-z));
     }
 }
@@ -326,7 +358,7 @@ __host__ __device__ inline size_t al16(size_t v) { return (v + 15) / 16 * 16; }
 __host__ __device__ inline GridLayout grid_layout(int nmax)
 {
     GridLayout L;
-    L.pts = al16(sizeof(float) * kNParams);
+    L.pts = al16(sizeof(float) * kSwTotal);
     L.idx = L.pts + al16(sizeof(float2) * (size_t)nmax);
     L.start = L.idx + al16(sizeof(unsigned short) * (size_t)nmax);
     L.cur = L.start + al16(sizeof(int) * (kGridCells + 1));
@@ -353,6 +385,7 @@ __global__ void __launch_bounds__(kNetThreads) warm_start_grid_kernel(
     extern __shared__ __align__(16) unsigned char smem[];
     const GridLayout SL = grid_layout(B.nmax);
     float *sw = reinterpret_cast<float *>(smem);
+    float *hs = sw + kSwH + 64 * (threadIdx.x >> 5);
     float2 *pts = reinterpret_cast<float2 *>(smem + SL.pts);
     unsigned short *idx = reinterpret_cast<unsigned short *>(smem + SL.idx);
     int *start = reinterpret_cast<int *>(smem + SL.start);
@@ -499,7 +532,7 @@ __global__ void __launch_bounds__(kNetThreads) warm_start_grid_kernel(
         }
         float f[2 * kKnn];
         near8_features(src, B.dst[b], j, n, nd, ni, lane, f);
-        const float z = mlp_forward_warp(sw, f, lane);
+        const float z = mlp_forward_warp(sw, f, lane, hs);
         if (lane == 0) B.p0[b][j] = 1.f / (1.f + expf(-z));
     }
 }
