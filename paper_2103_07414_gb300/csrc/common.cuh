@@ -28,6 +28,15 @@ __device__ __forceinline__ float ex2_ftz(float x)
     return y;
 }
 
+// 1/x with one MUFU.RCP (rcp.approx.ftz.f32: within one ulp of the quotient for normal x;
+// subnormal x flushes to zero and gives +inf).
+__device__ __forceinline__ float rcp_approx_ftz(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Blended planar DQ (a, b, u, v) = (r_w, r_z, d_x, d_y), not normalised, and scale s,
 // applied to p: s (R p + t) with R, t of the normalised DQ.  With n2 = a^2 + b^2:
 //   cos th = (a^2 - b^2)/n2, sin th = 2ab/n2, t = 2 (a u - b v, b u + a v)/n2

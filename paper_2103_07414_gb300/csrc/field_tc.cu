@@ -117,6 +117,29 @@ inline size_t tc_operand_bytes_max(int n, int gw, int gh)
     return b;
 }
 
+// The displacement d = W(p) - p of pixel p from its six accumulated sums (Eqs. 1-3): the
+// blended row is the reference row plus the weighted differences over their weight w > 0,
+// then the blend is normalised and applied.  Both reciprocals (1/w and the real part's
+// 1/|r|^2) are the single-instruction approximation (rcp.approx.ftz: within one ulp), not
+// the correctly rounded division: an error of 2^-23 relative in a displacement of a few
+// thousand pixels is far below the BF16 operands' 2^-9, and the division sequences were
+// about a tenth of the fused epilogue's instructions.  The field call and the fused field +
+// warp call both take d from here, so their canvases stay the same bits.
+__device__ __forceinline__ float2 tc_displacement(float f0, float f1, float f2, float f3, float f4,
+                                                  float w, float ra, float rb, float ru, float rv,
+                                                  float rs, float px, float py)
+{
+    const float inv = rcp_approx_ftz(w);
+    const float a = ra + f0 * inv, b = rb + f1 * inv, u = ru + f2 * inv, v = rv + f3 * inv;
+    const float s = rs + f4 * inv;
+    const float in2 = rcp_approx_ftz(a * a + b * b);
+    const float ct = (a * a - b * b) * in2;
+    const float st = 2.0f * a * b * in2;
+    const float tx = 2.0f * (a * u - b * v) * in2;
+    const float ty = 2.0f * (b * u + a * v) * in2;
+    return make_float2(s * (ct * px - st * py + tx) - px, s * (st * px + ct * py + ty) - py);
+}
+
 // Columns of the GEMM: the matches with c_i != 0 in index order (a match of weight 0 adds
 // exactly nothing to any of the six sums), found by every block with the same block scan.
 // Returns their number m; col(k) = the k-th such match.  Above kCompactMax matches the
@@ -455,14 +478,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(const __grid_co
                 for (int j = 0; j < 8; ++j) {
                     const float py = static_cast<float>(gy0 + ty * PY + g * 8 + j);
                     d[j] = make_float2(NAN, NAN);
-                    const float w = F[5][j];
-                    if (w > 0.f) {
-                        const float inv = 1.f / w;
-                        const float2 xp = apply_blend(ra + F[0][j] * inv, rb + F[1][j] * inv,
-                                                      ru + F[2][j] * inv, rv + F[3][j] * inv,
-                                                      rs + F[4][j] * inv, px, py);
-                        d[j] = make_float2(xp.x - px, xp.y - py);
-                    }
+                    if (F[5][j] > 0.f)
+                        d[j] = tc_displacement(F[0][j], F[1][j], F[2][j], F[3][j], F[4][j], F[5][j],
+                                               ra, rb, ru, rv, rs, px, py);
                 }
                 const int y0 = ty * PY + g * 8;
 #pragma unroll
@@ -717,14 +735,12 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
                             const float py = static_cast<float>(y0 + g * 8 + h + j);
                             dx[j] = NAN;
                             dy[j] = NAN;
-                            const float w = F[5][j];
-                            if (w > 0.f) {
-                                const float inv = 1.f / w;
-                                const float2 xp = apply_blend(ra + F[0][j] * inv, rb + F[1][j] * inv,
-                                                              ru + F[2][j] * inv, rv + F[3][j] * inv,
-                                                              rs + F[4][j] * inv, px, py);
-                                dx[j] = xp.x - px;
-                                dy[j] = xp.y - py;
+                            if (F[5][j] > 0.f) {
+                                const float2 d = tc_displacement(F[0][j], F[1][j], F[2][j], F[3][j],
+                                                                 F[4][j], F[5][j], ra, rb, ru, rv, rs,
+                                                                 px, py);
+                                dx[j] = d.x;
+                                dy[j] = d.y;
                             }
                         }
 #pragma unroll
