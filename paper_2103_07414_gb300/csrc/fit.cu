@@ -158,6 +158,10 @@ __device__ __forceinline__ void rows4_sum(const float (&v)[4][K], int lane, floa
     }
 }
 
+// Largest squared distance (scaled units) of a row from its group's origin for which the
+// row's Gaussian weights are taken from the expanded exponent (mstep_group, residual_rows).
+constexpr float kExpandMax = 4.f;
+
 // Gaussian weight 2^(lp - |d|^2) of a scaled offset d.
 __device__ __forceinline__ float gauss_w(float2 d, float lp)
 {
@@ -300,22 +304,63 @@ __device__ void mstep_group(const FitArgs &A, const FitSmem &S, const int *rows,
         W[r] = 0.f;
         su[r] = sv[r] = sq[r] = sc[r] = make_float2(0.f, 0.f);
     }
-#pragma unroll 2
-    for (int j = lane; j < n; j += 32) {
-        const float2 xj = S.x[j], yj = S.y[j];
-        const float lpj = S.lp[j];
-        const float2 u = __fadd2_rn(xj, nox), v = __fadd2_rn(yj, noy);
-        const float2 g1 = make_float2(fmaf(u.x, u.x, u.y * u.y), fmaf(v.x, v.x, v.y * v.y));
-        const float2 g2 = make_float2(fmaf(u.x, v.x, u.y * v.y), fmaf(u.x, v.y, -(u.y * v.x)));
+    // The Gaussian exponent about o: with e = x_i - o and u = x_j - o,
+    //     lp_j - |x_j - x_i|^2 = (lp_j - |u|^2) + 2 e.u - |e|^2,
+    // where |u|^2 is one of the moment features and the last term is the same for every j of
+    // row i: a factor 2^(-|e|^2) common to the row's nine sums, which every ratio of Eqs.
+    // 18-20 cancels.  So the row's weights are taken as om 2^(|e|^2) = 2^((lp_j - |u|^2) +
+    // 2 e.u): two FMAs per pair, where the offset x_j - x_i took a two-lane add more.  Used
+    // when every row of the group lies within |e|^2 <= kExpandMax of o (scaled units; 2^4
+    // at most as factor, and the rounding of the expanded exponent, about 2^-24 (|u|^2 +
+    // 2 |e.u|), stays near 2^-20 for the pairs of non-negligible weight); other groups sum
+    // the offsets as before.
+    float2 e2[R];
+    float emax = 0.f;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float om = gauss_w(__fadd2_rn(xj, nxi[r]), lpj);
-            const float2 om2 = make_float2(om, om);
-            W[r] += om;
-            su[r] = __ffma2_rn(om2, u, su[r]);
-            sv[r] = __ffma2_rn(om2, v, sv[r]);
-            sq[r] = __ffma2_rn(om2, g1, sq[r]);
-            sc[r] = __ffma2_rn(om2, g2, sc[r]);
+    for (int r = 0; r < R; ++r) {
+        const float2 e = __fadd2_rn(neg2(nxi[r]), nox);
+        emax = fmaxf(emax, fmaf(e.x, e.x, e.y * e.y));
+        e2[r] = make_float2(2.f * e.x, 2.f * e.y);
+    }
+    if (emax <= kExpandMax) {
+#pragma unroll 2
+        for (int j = lane; j < n; j += 32) {
+            const float2 xj = S.x[j], yj = S.y[j];
+            const float lpj = S.lp[j];
+            const float2 u = __fadd2_rn(xj, nox), v = __fadd2_rn(yj, noy);
+            const float uu = fmaf(u.x, u.x, u.y * u.y);
+            const float2 g1 = make_float2(uu, fmaf(v.x, v.x, v.y * v.y));
+            const float2 g2 = make_float2(fmaf(u.x, v.x, u.y * v.y), fmaf(u.x, v.y, -(u.y * v.x)));
+            const float cj = lpj - uu;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float om = ex2_ftz(fmaf(e2[r].x, u.x, fmaf(e2[r].y, u.y, cj)));
+                const float2 om2 = make_float2(om, om);
+                W[r] += om;
+                su[r] = __ffma2_rn(om2, u, su[r]);
+                sv[r] = __ffma2_rn(om2, v, sv[r]);
+                sq[r] = __ffma2_rn(om2, g1, sq[r]);
+                sc[r] = __ffma2_rn(om2, g2, sc[r]);
+            }
+        }
+    } else {
+#pragma unroll 2
+        for (int j = lane; j < n; j += 32) {
+            const float2 xj = S.x[j], yj = S.y[j];
+            const float lpj = S.lp[j];
+            const float2 u = __fadd2_rn(xj, nox), v = __fadd2_rn(yj, noy);
+            const float2 g1 = make_float2(fmaf(u.x, u.x, u.y * u.y), fmaf(v.x, v.x, v.y * v.y));
+            const float2 g2 = make_float2(fmaf(u.x, v.x, u.y * v.y), fmaf(u.x, v.y, -(u.y * v.x)));
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float om = gauss_w(__fadd2_rn(xj, nxi[r]), lpj);
+                const float2 om2 = make_float2(om, om);
+                W[r] += om;
+                su[r] = __ffma2_rn(om2, u, su[r]);
+                sv[r] = __ffma2_rn(om2, v, sv[r]);
+                sq[r] = __ffma2_rn(om2, g1, sq[r]);
+                sc[r] = __ffma2_rn(om2, g2, sc[r]);
+            }
         }
     }
     // the warp totals of the R rows: lanes 4 slot .. 4 slot + R - 1 keep them
@@ -376,10 +421,18 @@ __device__ __forceinline__ unsigned hilbert_index(unsigned x, unsigned y)
 // bit as in the loop -- is subtracted afterwards; where the rest of the weight is smaller
 // than that term (an isolated match), the subtraction would cancel and the sum over
 // i != j is taken again exactly.
+// The rows of a group are neighbours in the Hilbert order; their Gaussian exponents are
+// expanded about the first row's position o, as in the M-step: with e = x_j - o and
+// u = x_i - o, lp_i - |x_i - x_j|^2 = (lp_i - |u|^2) + 2 e.u - |e|^2, and the factor
+// 2^(-|e|^2), common to the row's six sums, cancels in the blend and in the comparison of
+// the own term with the rest.  Groups whose rows lie farther than kExpandMax from o sum
+// the offsets x_i - x_j as before.
 // The totals of a residual row as one lane keeps them until the row is evaluated: the six
-// sums over every i (the term i = j included) and the row (-1: none).
+// sums over every i (the term i = j included), the group's origin (negated; NaN: offsets
+// summed directly) and the row (-1: none).
 struct ResSums {
     float t[6];
+    float2 no;
     int j;
 };
 
@@ -399,21 +452,53 @@ __device__ void residual_rows(const FitArgs &A, const FitSmem &S, const int *row
         A1[r] = A2[r] = make_float2(0.f, 0.f);
         W[r] = As[r] = 0.f;
     }
-#pragma unroll 2
-    for (int i = lane; i < n; i += 32) {
-        const float2 xi = S.x[i];
-        const float lpi = S.lp[i];
-        const float4 qi = S.q[i];
-        const float qsi = S.qs[i];
-        const float2 qab = make_float2(qi.x, qi.y), quv = make_float2(qi.z, qi.w);
+    const float2 no = nxj[0];
+    float2 e2[R];
+    float emax = 0.f;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float w = gauss_w(__fadd2_rn(xi, nxj[r]), lpi);
-            const float2 w2 = make_float2(w, w);
-            W[r] += w;
-            A1[r] = __ffma2_rn(w2, qab, A1[r]);
-            A2[r] = __ffma2_rn(w2, quv, A2[r]);
-            As[r] = fmaf(w, qsi, As[r]);
+    for (int r = 0; r < R; ++r) {
+        const float2 e = __fadd2_rn(neg2(nxj[r]), no);
+        emax = fmaxf(emax, fmaf(e.x, e.x, e.y * e.y));
+        e2[r] = make_float2(2.f * e.x, 2.f * e.y);
+    }
+    const bool expand = emax <= kExpandMax;
+    if (expand) {
+#pragma unroll 2
+        for (int i = lane; i < n; i += 32) {
+            const float2 xi = S.x[i];
+            const float lpi = S.lp[i];
+            const float4 qi = S.q[i];
+            const float qsi = S.qs[i];
+            const float2 qab = make_float2(qi.x, qi.y), quv = make_float2(qi.z, qi.w);
+            const float2 u = __fadd2_rn(xi, no);
+            const float ci = fmaf(-u.x, u.x, fmaf(-u.y, u.y, lpi));
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float w = ex2_ftz(fmaf(e2[r].x, u.x, fmaf(e2[r].y, u.y, ci)));
+                const float2 w2 = make_float2(w, w);
+                W[r] += w;
+                A1[r] = __ffma2_rn(w2, qab, A1[r]);
+                A2[r] = __ffma2_rn(w2, quv, A2[r]);
+                As[r] = fmaf(w, qsi, As[r]);
+            }
+        }
+    } else {
+#pragma unroll 2
+        for (int i = lane; i < n; i += 32) {
+            const float2 xi = S.x[i];
+            const float lpi = S.lp[i];
+            const float4 qi = S.q[i];
+            const float qsi = S.qs[i];
+            const float2 qab = make_float2(qi.x, qi.y), quv = make_float2(qi.z, qi.w);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float w = gauss_w(__fadd2_rn(xi, nxj[r]), lpi);
+                const float2 w2 = make_float2(w, w);
+                W[r] += w;
+                A1[r] = __ffma2_rn(w2, qab, A1[r]);
+                A2[r] = __ffma2_rn(w2, quv, A2[r]);
+                As[r] = fmaf(w, qsi, As[r]);
+            }
         }
     }
     // the warp totals of the R rows: lanes 4 slot .. 4 slot + R - 1 keep them
@@ -437,6 +522,7 @@ __device__ void residual_rows(const FitArgs &A, const FitSmem &S, const int *row
     for (int rr = 0; rr < R; ++rr)
         if (r == rr) j = rows[rr];
     keep.j = j;
+    keep.no = expand ? no : make_float2(NAN, NAN);
 #pragma unroll
     for (int k = 0; k < 6; ++k) keep.t[k] = t[k];
 }
@@ -450,8 +536,16 @@ __device__ void residual_finish(const FitArgs &A, const FitSmem &S, const ResSum
     const bool has = keep.j >= 0;
     const int jl = has ? keep.j : 0;
     const float *t = keep.t;
-    // the term i = j: offset (0, 0), so its weight is exactly 2^lp_j
-    const float wjj = ex2_ftz(S.lp[jl]);
+    // the term i = j, the same bits as in the loop: offset (0, 0), so its weight is exactly
+    // 2^lp_j, or with the exponent expanded about o, the loop's expression at u = e
+    float wjj;
+    if (isnan(keep.no.x)) {
+        wjj = ex2_ftz(S.lp[jl]);
+    } else {
+        const float2 u = __fadd2_rn(S.x[jl], keep.no);
+        const float cj = fmaf(-u.x, u.x, fmaf(-u.y, u.y, S.lp[jl]));
+        wjj = ex2_ftz(fmaf(2.f * u.x, u.x, fmaf(2.f * u.y, u.y, cj)));
+    }
     const float4 qj = S.q[jl];
     const float qsj = S.qs[jl];
     float wl = t[0] - wjj;
@@ -706,26 +800,30 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta, c
         ResSums keep;
         keep.j = -1;
         int slot = 0;
-        int j = gwarp;
-        for (; j + 3 * nwarps < n; j += 4 * nwarps) {
-            const int rows[4] = {j, j + nwarps, j + 2 * nwarps, j + 3 * nwarps};
-            residual_rows<4>(A, S, rows, lane, slot, keep);
+        // groups of 4 consecutive positions of the Hilbert order (every CTA's M-step positions
+        // are written before the barrier that precedes this pass), dealt to the warps of the
+        // whole group of CTAs in turn; the last group holds the 1-3 positions left
+        for (int t = 4 * gwarp; t < n; t += 4 * nwarps) {
+            const int left = n - t;
+            if (left >= 4) {
+                const int rows[4] = {__ldcg(A.ord + t), __ldcg(A.ord + t + 1), __ldcg(A.ord + t + 2),
+                                     __ldcg(A.ord + t + 3)};
+                residual_rows<4>(A, S, rows, lane, slot, keep);
+            } else if (left == 3) {
+                const int rows[3] = {__ldcg(A.ord + t), __ldcg(A.ord + t + 1), __ldcg(A.ord + t + 2)};
+                residual_rows<3>(A, S, rows, lane, slot, keep);
+            } else if (left == 2) {
+                const int rows[2] = {__ldcg(A.ord + t), __ldcg(A.ord + t + 1)};
+                residual_rows<2>(A, S, rows, lane, slot, keep);
+            } else {
+                const int rows[1] = {__ldcg(A.ord + t)};
+                residual_rows<1>(A, S, rows, lane, slot, keep);
+            }
             if (++slot == 8) {
                 residual_finish(A, S, keep, lane, q0, qs0, pe, ps);
                 keep.j = -1;
                 slot = 0;
             }
-        }
-        const int rem = j < n ? (n - 1 - j) / nwarps + 1 : 0;     // 0..3 rows left
-        if (rem == 3) {
-            const int rows[3] = {j, j + nwarps, j + 2 * nwarps};
-            residual_rows<3>(A, S, rows, lane, slot, keep);
-        } else if (rem == 2) {
-            const int rows[2] = {j, j + nwarps};
-            residual_rows<2>(A, S, rows, lane, slot, keep);
-        } else if (rem == 1) {
-            const int rows[1] = {j};
-            residual_rows<1>(A, S, rows, lane, slot, keep);
         }
         residual_finish(A, S, keep, lane, q0, qs0, pe, ps);
         const float2 t = block_sum2<NT>(pe, ps, red);
