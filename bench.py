@@ -160,6 +160,10 @@ def parse_args():
                          'mosaic_warp_batch (at most 8; 16 for the mixed batch) call (BF16, '
                          'pipelined path); 0: for emdq_mosaic_batch the fewest calls per fit '
                          'batch, frames spread evenly (13 for batches of 50), else 4')
+    ap.add_argument('--split-pairs', action='store_true',
+                    help='mixed batch: each group of pairs as emdq_field_batch, then their '
+                         'mosaic_warp calls on a second stream (default: one emdq_mosaic_pairs call '
+                         'per group of up to 16 pairs, field and warp fused, the field never written)')
     ap.add_argument('--split-group', action='store_true',
                     help='a group of frames as emdq_field_batch, then mosaic_warp_batch on a second '
                          'stream (default for the sequence: one emdq_mosaic_batch call, field and '
@@ -1260,7 +1264,9 @@ def mixed_config(args, ws, pairs, ctas=None) -> dict:
 
 def run_gpu_mixed(args, ws, rank, local):
     """The mixed-size batch: 64 independent pairs per step, one warm-start launch, one
-    autotuned fit launch, then field + warp per pair, the whole step one CUDA graph."""
+    autotuned fit launch (or the fits in phases), then the fields and warps of 16 pairs per
+    emdq_mosaic_pairs call (--split-pairs: emdq_field_batch + mosaic_warp), the whole step one
+    CUDA graph."""
     import numpy as np
     import torch
     import paper_2103_07414_gb300 as emdq
@@ -1308,22 +1314,35 @@ def run_gpu_mixed(args, ws, rank, local):
         fit_tune = dict(chosen='one launch (autotuned split)' if fit_phases is None else fit_phases,
                         ms_per_launch=ms)
 
-    # the fields of a group of G pairs in one emdq_field_batch call (main stream), their
-    # warps on the warp stream beside the next group's fields; buffers double-buffered
-    G = max(1, min(16, args.field_group or 4))
+    # fused (default): the fields and warps of a group of up to 16 pairs in one
+    # emdq_mosaic_pairs call; split: the fields of a group of G pairs in one emdq_field_batch
+    # call (main stream), their warps on the warp stream beside the next group's fields,
+    # buffers double-buffered
+    fused = not args.split_pairs
+    G = max(1, min(16, args.field_group or (16 if fused else 4)))
     warp_stream = torch.cuda.Stream(device=dev)
     groups = [list(range(b0, min(len(P), b0 + G))) for b0 in range(0, len(P), G)]
-    gws = max(emdq.field_batch_workspace_size([(P[b]['out']['q'], P[b]['out']['c'], P[b]['src'],
-                                                P[b]['grid'], P[b]['alpha']) for b in grp])
-              for grp in groups)
+
+    def pair_args(b):
+        x = P[b]
+        return (x['out']['q'], x['out']['c'], x['src'], x['grid'], x['alpha'], x['frame'], x['canvas'],
+                x['origin'])
+
+    if fused:
+        gws = max(emdq.mosaic_pairs_workspace_size([pair_args(b) for b in grp]) for grp in groups)
+    else:
+        gws = max(emdq.field_batch_workspace_size([(P[b]['out']['q'], P[b]['out']['c'], P[b]['src'],
+                                                    P[b]['grid'], P[b]['alpha']) for b in grp])
+                  for grp in groups)
     grp_ws = [torch.empty(gws, dtype=torch.uint8, device=dev) for _ in range(2)]
     max_px = max(x['grid'][2] * x['grid'][3] for x in P)
-    grp_disp = [[torch.empty(max_px * 2, dtype=torch.float32, device=dev) for _ in range(G)]
-                for _ in range(2)]
+    grp_disp = [] if fused else [[torch.empty(max_px * 2, dtype=torch.float32, device=dev) for _ in range(G)]
+                                 for _ in range(2)]
 
     def one_pass(ev=None):
-        # ev[0] start, ev[1] warm start done, ev[2] fits done, then per pair b: ev[3 + 3b]
-        # field done (its group's call), ev[4 + 3b] / ev[5 + 3b] warp start / done
+        # ev[0] start, ev[1] warm start done, ev[2] fits done, then fused: ev[3 + g] group g's
+        # call done; split: per pair b ev[3 + 3b] field done (its group's call), ev[4 + 3b] /
+        # ev[5 + 3b] warp start / done
         main = torch.cuda.current_stream()
         if ev: ev[0].record()
         emdq.warm_start(probs_sd, warm_params, outs=[x['p0'] for x in P])
@@ -1331,6 +1350,13 @@ def run_gpu_mixed(args, ws, rank, local):
         emdq.emdq_fit_batch(fit_probs, outs=[x['out'] for x in P], workspace=batch_ws,
                             ctas=ctas if fit_phases is None else None, phases=fit_phases)
         if ev: ev[2].record()
+        if fused:
+            for gi, grp in enumerate(groups):
+                emdq.emdq_mosaic_pairs([pair_args(b) for b in grp], workspace=grp_ws[0])
+                if ev: ev[3 + gi].record(main)
+            for b, x in enumerate(P):
+                infos[b].copy_(x['out']['info'])
+            return
         free = [None, None]
         for gi, grp in enumerate(groups):
             slot = gi % 2
@@ -1365,19 +1391,19 @@ def run_gpu_mixed(args, ws, rank, local):
         torch.cuda.synchronize()
         w += 1
     # the field tile height of every group, chosen by the library's autotuner (recorded per
-    # size class, so the step's emdq_field_batch calls use it)
+    # size class, so the step's emdq_field_batch calls use it; the fused calls take 40 rows)
     field_tiles = []
-    for grp in groups:
+    for grp in ([] if fused else groups):
         disps = [grp_disp[0][i][: P[b]['grid'][2] * P[b]['grid'][3] * 2].view(
                  P[b]['grid'][3], P[b]['grid'][2], 2) for i, b in enumerate(grp)]
         py, _ = emdq.field_batch_autotune([(P[b]['out']['q'], P[b]['out']['c'], P[b]['src'], P[b]['grid'],
                                             P[b]['alpha']) for b in grp], reps=3, outs=disps,
                                           workspace=grp_ws[0])
         field_tiles.append(py)
-    field_tiles = [emdq.field_batch_tile_rows([(P[b]['out']['q'], P[b]['out']['c'], P[b]['src'],
-                                                P[b]['grid'], P[b]['alpha']) for b in grp])
-                   for grp in groups]
-    n_ev = 3 + 3 * len(P)
+    field_tiles = [40] * len(groups) if fused else [
+        emdq.field_batch_tile_rows([(P[b]['out']['q'], P[b]['out']['c'], P[b]['src'], P[b]['grid'],
+                                     P[b]['alpha']) for b in grp]) for grp in groups]
+    n_ev = 3 + (len(groups) if fused else 3 * len(P))
     graph, graph_note = None, None
     gev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(n_ev)]
     if not args.no_graph:
@@ -1391,12 +1417,17 @@ def run_gpu_mixed(args, ws, rank, local):
         except Exception as ex:
             graph_note = f'capture failed, calls issued directly: {type(ex).__name__}: {ex}'[:300]
         torch.cuda.synchronize()
-    warm_ms, fit_ms, field_ms, warp_ms, step_ms = [], [], [], [], []
+    warm_ms, fit_ms, field_ms, warp_ms, mosaic_ms, step_ms = [], [], [], [], [], []
 
     def collect(ev):
         warm_ms.append(ev[0].elapsed_time(ev[1]))
         fit_ms.append(ev[1].elapsed_time(ev[2]))
         prev = ev[2]
+        if fused:
+            for gi in range(len(groups)):
+                mosaic_ms.append(prev.elapsed_time(ev[3 + gi]))
+                prev = ev[3 + gi]
+            return
         for b in range(len(P)):
             field_ms.append(prev.elapsed_time(ev[3 + 3 * b]))
             warp_ms.append(ev[4 + 3 * b].elapsed_time(ev[5 + 3 * b]))
@@ -1488,8 +1519,11 @@ def run_gpu_mixed(args, ws, rank, local):
     peaks = measured_peaks()
     sm_mhz = (clk or {}).get('sm_mhz') or peaks['sm_max_mhz']
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    totals = dict(fit=float(np.sum(fit_ms)), warm=float(np.sum(warm_ms)), field=float(np.sum(field_ms)),
-                  warp=float(np.sum(warp_ms)))
+    totals = dict(fit=float(np.sum(fit_ms)), warm=float(np.sum(warm_ms)))
+    if fused:
+        totals['mosaic'] = float(np.sum(mosaic_ms))
+    else:
+        totals.update(field=float(np.sum(field_ms)), warp=float(np.sum(warp_ms)))
     dom = max(totals, key=totals.get)
     ns = np.array([x['n'] for x in P], dtype=np.float64)
     win = np.array([x['grid'][2] * x['grid'][3] for x in P], dtype=np.float64)
@@ -1507,6 +1541,14 @@ def run_gpu_mixed(args, ws, rank, local):
                     peak=peaks['bf16_tflops'], unit='TFLOP/s', peak_source=peaks['source'] + ' bf16 burst',
                     launches=len(field_ms), mean_launch_ms=float(np.mean(field_ms)),
                     work='2 x 6 x window pixels x matches of nonzero weight, summed over the pairs')
+    elif dom == 'mosaic':
+        flops = 2.0 * 6 * float(np.sum(win * np.array(nz)))
+        roof = dict(bound='tensor', kernel='emdq_mosaic_pairs: field_tc_prep_kernel + mosaic_tc_kernel (pairs)',
+                    achieved=flops / (np.sum(mosaic_ms) / args.steps * 1e-3) / 1e12,
+                    peak=peaks['bf16_tflops'], unit='TFLOP/s', peak_source=peaks['source'] + ' bf16 burst',
+                    launches=len(mosaic_ms), mean_launch_ms=float(np.mean(mosaic_ms)),
+                    work='2 x 6 x window pixels x matches of nonzero weight, summed over the pairs '
+                         '(the warp and blend in the epilogue are not counted as work)')
     elif dom == 'warm':
         flops = float(np.sum(ns * (4.0 * ns + 2 * 5184)))
         roof = dict(bound='alu', kernel='warm_start_batch_kernel', achieved=flops / (np.mean(warm_ms) * 1e-3) / 1e12,
@@ -1529,14 +1571,16 @@ def run_gpu_mixed(args, ws, rank, local):
         kernel_ms_per_step={k: v / args.steps for k, v in totals.items()},
         path='learned warm start (one launch) + ' +
              ('emdq_fit_batch (one launch, autotuned CTA split)' if fit_phases is None else
-              f'emdq_fit_batch in phases {fit_phases} (emdq_fit_batch_phases)') + ' + '
-             f'emdq_field_batch ({G} pairs per call, bf16), their mosaic_warp on a second stream' +
+              f'emdq_fit_batch in phases {fit_phases} (emdq_fit_batch_phases)') + ' + ' +
+             (f'emdq_mosaic_pairs ({G} pairs per call, bf16 field and warp fused)' if fused else
+              f'emdq_field_batch ({G} pairs per call, bf16), their mosaic_warp on a second stream') +
              (', the step replayed from one CUDA graph' if graph is not None else ''),
         cuda_graph=graph is not None, **({'cuda_graph_note': graph_note} if graph_note else {}),
         autotune_fit_ms=tune_ms, fit_schedule=fit_tune, field_tile_rows=field_tiles,
         mean_em_iters=float(np.mean(iters)),
         roofline=roof,
-        gpu_launches=args.steps * (2 + (len(fit_phases) - 1 if fit_phases else 0) + 2 * len(groups) + len(P)),
+        gpu_launches=args.steps * (2 + (len(fit_phases) - 1 if fit_phases else 0) + 2 * len(groups) +
+                                   (0 if fused else len(P))),
         clocks=clk, e2e=e2e, fit_status=statuses,
         emdq_batch_device_ms=native_ms,
         p50_note='per step: the whole batch of 64 pairs is one unit of latency')

@@ -475,11 +475,13 @@ EMDQ_API emdq_status mosaic_warp_batch(const mosaic_frame *frames, int count, in
  * The whole path for a batch of independent pairs in one call (not in the paper: a
  * batching front end).  On `stream`, in order: the learned warm start of every pair (when
  * warm_params is not NULL; else plain EM from p = 1), all EMDQ fits in one cooperative
- * launch (CTAs split per fit_ctas, or in proportion to n^2 when it is NULL), the BF16
- * fields of up to 16 pairs per emdq_field_batch call, and after each such call the warps of
- * its pairs in array order (pairs that share a canvas are blended in that order).  Every
- * pair's results are those of emdq_warm_start, emdq_fit_batch_ex, emdq_field (EMDQ_BF16)
- * and mosaic_warp on the same arguments.  Capturable into a CUDA graph.
+ * launch (CTAs split per fit_ctas, or in proportion to n^2 when it is NULL), then per group
+ * of up to 16 pairs their BF16 fields and warps fused in one emdq_mosaic_pairs call, or,
+ * where two pairs of the group update overlapping canvas rows or differ in channels (or the
+ * fused call refuses the group), one emdq_field_batch call followed by the warps of its pairs
+ * in array order (pairs that share a canvas are blended in that order).  Every pair's
+ * results are those of emdq_warm_start, emdq_fit_batch_ex, emdq_field (EMDQ_BF16) and
+ * mosaic_warp on the same arguments.  Capturable into a CUDA graph.
  *
  *   pairs        host array of `count` descriptors (1..64)
  *   prm          host; NULL = defaults; alpha = 0 derives each pair's from its frame size
@@ -577,6 +579,50 @@ EMDQ_API emdq_status emdq_mosaic_batch_ex(const emdq_mosaic_problem *problems, i
                                           int canvas_w, int canvas_h, int canvas_pitch,
                                           int origin_x, int origin_y, int tile_rows,
                                           void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------ emdq_mosaic_pairs -
+ * The dense field and the mosaic update of up to 16 independent pairs in one pass (Eqs. 1-4
+ * and Sec. III-F, Eqs. 23-24): each pair has its own frame (size and pitch), window and
+ * canvas, and each pair's canvas ends bit for bit as after emdq_field (EMDQ_BF16) and
+ * mosaic_warp of that pair; the field itself is never written.  One operand-preparation
+ * launch, then one persistent tensor-core launch over the tiles of every pair's window (the
+ * tiles of emdq_mosaic_batch, 128 x 40 pixels), each tile's field followed at every pixel by
+ * the pair's frame sampled at p + d(p) and the capped running average.  Not a step of the
+ * paper: the fusion of two of its steps for a batch of unrelated pairs.
+ *
+ *   pairs         host array of `count` descriptors (1 <= count <= 16): a fit (q, c, src, n
+ *                 as emdq_field), its window (grid_*, reference coordinates; not empty;
+ *                 inside the pair's canvas after the origin shift), alpha, the device frame
+ *                 t (fw x fh, rows frame_pitch bytes apart), and the device canvas (4-byte
+ *                 pixels (c0, c1, c2, w) as mosaic_warp; canvas_pitch bytes per row) with the
+ *                 origin of the reference frame in it
+ *   channels      1 or 3, the same for every pair
+ *   workspace     device scratch of emdq_mosaic_pairs_workspace_size(pairs, count) bytes,
+ *                 256-byte aligned, not shared with a call in flight
+ * The pairs' tiles run in no fixed order, so no two pairs may update the same canvas bytes:
+ * EMDQ_EINVAL if the spans of canvas rows of two pairs' windows (first to last byte)
+ * overlap.  Asynchronous on `stream`.  Returns EMDQ_EINVAL for a bad descriptor or a window
+ * outside its canvas, EMDQ_ENOTSUP for count > 16, a frame of 2^31 bytes or more or a device
+ * without tcgen05, EMDQ_EWORKSPACE / EMDQ_ECUDA as emdq_field; a bounded device wait that
+ * gives up (about 2 s) is recorded as EMDQ_ETIMEOUT in the workspace's first word (the
+ * canvases are then undefined).
+ */
+typedef struct {
+    const float *q;             /* device, n x 8 warp rows (emdq_fit's q_out) */
+    const float *c;             /* device, n field weights (emdq_fit's c_out) */
+    const float *src;           /* device, n x 2 match positions in the reference frame */
+    int n;
+    int grid_x0, grid_y0, grid_w, grid_h;   /* the pixel window, reference coordinates */
+    float alpha;                /* Gaussian weight exp(-alpha |p - x_i|^2) */
+    const uint8_t *frame;       /* device frame t: fh rows of frame_pitch bytes */
+    int fw, fh, frame_pitch;
+    uint8_t *canvas;            /* device, canvas_h rows of canvas_pitch bytes */
+    int canvas_w, canvas_h, canvas_pitch, origin_x, origin_y;
+} emdq_mosaic_pair;
+
+EMDQ_API size_t      emdq_mosaic_pairs_workspace_size(const emdq_mosaic_pair *pairs, int count);
+EMDQ_API emdq_status emdq_mosaic_pairs(const emdq_mosaic_pair *pairs, int count, int channels,
+                                       void *workspace, size_t workspace_bytes, void *stream);
 
 /* ------------------------------------------------------------------ learned warm start
  * Not in the paper (the paper's EMDQ starts EM without a prior).  A 16-64-64-1 network

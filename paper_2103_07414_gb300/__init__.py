@@ -18,7 +18,7 @@ from ._build import LIB as _LIB_PATH, build  # noqa: F401
 
 __all__ = ['emdq_fit', 'emdq_fit_batch', 'emdq_field', 'emdq_field_batch', 'field_batch_autotune',
            'field_batch_tile_rows', 'emdq_mosaic_batch', 'mosaic_batch_workspace_size', 'mosaic_warp',
-           'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic', 'emdq_uncertainty', 'node_track', 'node_merge', 'node_restrict', 'feature_uncertainty',
+           'mosaic_warp_batch', 'emdq_batch', 'emdq_mosaic_pairs', 'mosaic_pairs_workspace_size', 'emdq_mosaic', 'emdq_uncertainty', 'node_track', 'node_merge', 'node_restrict', 'feature_uncertainty',
            'keyframe_distances', 'hex_nodes', 'node_init', 'arap_smooth',
            'mosaic_insert_reference',
            'alpha_for_frame', 'fit_workspace_size', 'field_workspace_size', 'EmdqError',
@@ -51,6 +51,16 @@ class _FieldProblem(ctypes.Structure):
                 ('n', ctypes.c_int), ('grid_x0', ctypes.c_int), ('grid_y0', ctypes.c_int),
                 ('grid_w', ctypes.c_int), ('grid_h', ctypes.c_int), ('alpha', ctypes.c_float),
                 ('disp_out', ctypes.c_void_p)]
+
+
+class _MosaicPair(ctypes.Structure):
+    _fields_ = [('q', ctypes.c_void_p), ('c', ctypes.c_void_p), ('src', ctypes.c_void_p),
+                ('n', ctypes.c_int), ('grid_x0', ctypes.c_int), ('grid_y0', ctypes.c_int),
+                ('grid_w', ctypes.c_int), ('grid_h', ctypes.c_int), ('alpha', ctypes.c_float),
+                ('frame', ctypes.c_void_p), ('fw', ctypes.c_int), ('fh', ctypes.c_int),
+                ('frame_pitch', ctypes.c_int), ('canvas', ctypes.c_void_p), ('canvas_w', ctypes.c_int),
+                ('canvas_h', ctypes.c_int), ('canvas_pitch', ctypes.c_int), ('origin_x', ctypes.c_int),
+                ('origin_y', ctypes.c_int)]
 
 
 class _MosaicProblem(ctypes.Structure):
@@ -133,6 +143,10 @@ def lib() -> ctypes.CDLL:
             L.emdq_mosaic_batch_ex.restype = I
             L.emdq_mosaic_batch_ex.argtypes = [P, I, I, I, I, I, P, I, I, I, I, I, I, P, Z, P]
             L.emdq_mosaic_batch.restype = I
+            L.emdq_mosaic_pairs_workspace_size.restype = Z
+            L.emdq_mosaic_pairs_workspace_size.argtypes = [P, I]
+            L.emdq_mosaic_pairs.restype = I
+            L.emdq_mosaic_pairs.argtypes = [P, I, I, P, Z, P]
             L.emdq_mosaic_batch.argtypes = [P, I, I, I, I, I, P, I, I, I, I, I, P, Z, P]
             L.emdq_field.restype = I
             L.emdq_field.argtypes = [P, P, P, I, I, I, I, I, F, I, P, P, Z, P]
@@ -479,6 +493,52 @@ def emdq_mosaic_batch(problems, canvas: torch.Tensor, origin, *, tile_rows: int 
         rc = lib().emdq_mosaic_batch_ex(*args, int(tile_rows), _ptr(ws), ws.numel(), _stream(stream))
     if rc != 0:
         raise EmdqError('emdq_mosaic_batch', rc)
+
+
+def _mosaic_pairs(pairs):
+    arr = (_MosaicPair * max(1, len(pairs)))()
+    chs = set()
+    for b, (q, c, src, grid, alpha, frame, canvas, origin) in enumerate(pairs):
+        n = c.shape[0]
+        _check(q, 'q', torch.float32, (n, 8))
+        _check(c, 'c', torch.float32, (n,))
+        _check(src, 'src', torch.float32, (n, 2))
+        fw, fh, ch, pitch = _frame_args(frame)
+        chs.add(ch)
+        _check(canvas, 'canvas', torch.uint8)
+        if canvas.dim() != 3 or canvas.shape[2] != 4:
+            raise ValueError('canvas must be [h, w, 4] uint8')
+        x0, y0, gw, gh = (int(v) for v in grid)
+        ox, oy = (int(v) for v in origin)
+        arr[b] = _MosaicPair(_ptr(q), _ptr(c), _ptr(src), n, x0, y0, gw, gh, float(alpha), _ptr(frame),
+                             fw, fh, pitch, _ptr(canvas), canvas.shape[1], canvas.shape[0],
+                             canvas.shape[1] * 4, ox, oy)
+    if len(chs) > 1:
+        raise ValueError('every pair of one call needs the same channel count')
+    return arr, (chs.pop() if chs else 1)
+
+
+def mosaic_pairs_workspace_size(pairs) -> int:
+    arr, _ = _mosaic_pairs(pairs)
+    return lib().emdq_mosaic_pairs_workspace_size(ctypes.cast(arr, ctypes.c_void_p), len(pairs))
+
+
+def emdq_mosaic_pairs(pairs, *, workspace: torch.Tensor | None = None, stream=None) -> None:
+    """BF16 field and mosaic update of up to 16 independent pairs in one pass:
+    pairs = [(q, c, src, grid, alpha, frame, canvas, origin), ...], each with its own frame and
+    canvas; every canvas ends bit for bit as after emdq_field (BF16) then mosaic_warp."""
+    count = len(pairs)
+    if count < 1:
+        raise ValueError('at least one pair')
+    arr, ch = _mosaic_pairs(pairs)
+    need = lib().emdq_mosaic_pairs_workspace_size(ctypes.cast(arr, ctypes.c_void_p), count)
+    if need == 0:
+        raise EmdqError('emdq_mosaic_pairs_workspace_size', 1)
+    ws = _workspace(need, pairs[0][0].device, workspace)
+    rc = lib().emdq_mosaic_pairs(ctypes.cast(arr, ctypes.c_void_p), count, ch, _ptr(ws), ws.numel(),
+                                 _stream(stream))
+    if rc != 0:
+        raise EmdqError('emdq_mosaic_pairs', rc)
 
 
 def field_batch_tile_rows(problems) -> int:

@@ -1,6 +1,8 @@
 // emdq_batch: the whole hot path for a batch of independent pairs in one call -- learned
-// warm start (optional), all EMDQ fits in one cooperative launch, the BF16 fields of up to
-// 16 pairs per operand + tensor-core launch pair, and each pair's warp into its canvas, in
+// warm start (optional), all EMDQ fits in one cooperative launch, then per group of up to 16
+// pairs their BF16 fields and warps fused in one operand + tensor-core launch pair
+// (emdq_mosaic_pairs), or, for a group whose pairs update overlapping canvas rows or differ
+// in channels, the fields of the group in one launch pair followed by each pair's warp in
 // pair order -- all on the caller's stream, with every scratch buffer in one workspace.
 #include "common.cuh"
 
@@ -118,9 +120,31 @@ extern "C" emdq_status emdq_batch_ex(const emdq_pair *pairs, int count, const em
                        : emdq_fit_batch_ex(fp, count, &P, fit_ctas, ws + L.fit, L.field - L.fit, stream);
         if (rc != EMDQ_OK) return rc;
     }
-    // 3. fields of up to 16 pairs per launch pair, then their warps in pair order
+    // 3. per group of up to 16 pairs: fields and warps fused; or the fields in one launch
+    //    pair, then their warps in pair order
     for (int g0 = 0; g0 < count; g0 += kFieldGroup) {
         const int gc = count - g0 < kFieldGroup ? count - g0 : kFieldGroup;
+        {
+            emdq_mosaic_pair m[kFieldGroup];
+            bool same_ch = true;
+            for (int i = 0; i < gc; ++i) {
+                const emdq_pair &p = pairs[g0 + i];
+                const float alpha = P.alpha > 0.f ? P.alpha : emdq_alpha_for_frame(p.frame_w, p.frame_h);
+                m[i] = emdq_mosaic_pair{p.q_out, p.c_out, p.src, p.n, p.grid_x0, p.grid_y0,
+                                        p.grid_w, p.grid_h, alpha, p.frame, p.frame_w, p.frame_h,
+                                        p.frame_pitch, p.canvas, p.canvas_w, p.canvas_h,
+                                        p.canvas_pitch, p.origin_x, p.origin_y};
+                same_ch = same_ch && p.channels == pairs[g0].channels;
+            }
+            if (same_ch) {
+                // argument refusals (EINVAL: overlapping canvas rows among others; ENOTSUP)
+                // come before any launch: the group then takes the unfused calls
+                const emdq_status rc =
+                    emdq_mosaic_pairs(m, gc, pairs[g0].channels, ws + L.field, L.disp - L.field, stream);
+                if (rc == EMDQ_OK) continue;
+                if (rc != EMDQ_EINVAL && rc != EMDQ_ENOTSUP) return rc;
+            }
+        }
         emdq_field_problem f[kFieldGroup];
         size_t off = L.disp;
         for (int i = 0; i < gc; ++i) {

@@ -509,15 +509,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) field_tc_kernel(const __grid_co
 }
 
 // ------------------------------------------------------------------------- fused mosaic
+// A pair's own canvas and frame geometry (independent pairs, emdq_mosaic_pairs).
+struct MosaicTarget {
+    uchar4 *canvas;
+    int cpitch4, ox, oy;
+    int fw, fh, pitch;
+};
+
 // Frames and canvas of a group of frames blended in one pass; the tiles are those of the
-// union of the group's windows (reference coordinates).
+// union of the group's windows (reference coordinates).  For independent pairs (PAIRS
+// kernels) every problem has its own canvas and frame geometry in tgt[] and the tiles are
+// those of each problem's own window (the GEMM's tiles: Bt.p[b].tile0 ...).
 struct MosaicBatch {
     const uint8_t *frame[kFieldBatchMax];
     int fw, fh, pitch;
     uchar4 *canvas;
     int cpitch4, ox, oy;
     int ux0, uy0, uw, uh;     // union of the windows
-    int ntx, ntiles;          // tiles across / in all of the union
+    int ntx, ntiles;          // tiles across / in all of the union (PAIRS: all problems' tiles)
+    MosaicTarget tgt[kFieldBatchMax];
 };
 
 // Does problem P's window meet the tile at (x0, y0)?
@@ -536,8 +546,33 @@ __device__ __forceinline__ int next_meeting(const TcBatch &Bt, int b, int x0, in
     return b;
 }
 
+// A tile's origin and its first item (Bt.count: none): the union's tiles and the frames
+// meeting each, or (PAIRS) each problem's own tiles, one item each.
+template <int PY, bool PAIRS>
+__device__ __forceinline__ int tile_first(const TcBatch &Bt, const MosaicBatch &M, int tile, int &x0,
+                                          int &y0)
+{
+    if (PAIRS) {
+        const int b = problem_of_tile(Bt, tile);
+        const TcProblem &P = Bt.p[b];
+        const int l = tile - P.tile0;
+        x0 = P.gx0 + (l % P.ntx) * kTcM;
+        y0 = P.gy0 + (l / P.ntx) * PY;
+        return b;
+    }
+    x0 = M.ux0 + (tile % M.ntx) * kTcM;
+    y0 = M.uy0 + (tile / M.ntx) * PY;
+    return next_meeting<PY>(Bt, -1, x0, y0);
+}
+
+template <int PY, bool PAIRS>
+__device__ __forceinline__ int tile_next(const TcBatch &Bt, int b, int x0, int y0)
+{
+    return PAIRS ? Bt.count : next_meeting<PY>(Bt, b, x0, y0);
+}
+
 // Items: (tile, frame) pairs, tiles of the union in this CTA's turn, the frames meeting each
-// in order.  The TMA and MMA warps run them as field_tc_kernel runs tiles (the operand rows
+// in order (PAIRS: a problem's tile and its own frame).  The TMA and MMA warps run them as field_tc_kernel runs tiles (the operand rows
 // of the tile's pixels in that frame's operands; outside its padded window TMA fills zeros,
 // and outside its window the operands are zero, so the weight channel there is 0).  The
 // epilogue warps: TMEM lane quadrant q = warp % 4, thread = pixel x; warp set s (four warps,
@@ -545,7 +580,7 @@ __device__ __forceinline__ int next_meeting(const TcBatch &Bt, int b, int x0, in
 // words once per tile, updates them through the tile's frames in order (each pixel's
 // displacement from Eq. 1, then the sample and the capped running average of
 // mosaic_warp_batch) and writes them back once.
-template <int CH, int PY>
+template <int CH, int PY, bool PAIRS>
 __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_constant__ TcBatch Bt,
                                                                  const __grid_constant__ MosaicBatch M)
 {
@@ -604,9 +639,9 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
         if (lane == 0) {
             int chunk = 0;
             for (int tile = blockIdx.x; tile < M.ntiles && !*abort_flag; tile += gridDim.x) {
-                const int x0 = M.ux0 + (tile % M.ntx) * kTcM, y0 = M.uy0 + (tile / M.ntx) * PY;
-                for (int b = next_meeting<PY>(Bt, -1, x0, y0); b < Bt.count && !*abort_flag;
-                     b = next_meeting<PY>(Bt, b, x0, y0)) {
+                int x0, y0;
+                for (int b = tile_first<PY, PAIRS>(Bt, M, tile, x0, y0); b < Bt.count && !*abort_flag;
+                     b = tile_next<PY, PAIRS>(Bt, b, x0, y0)) {
                     const TcProblem &P = Bt.p[b];
                     const int nchunks = *P.kcount / kTcK;
                     for (int k = 0; k < nchunks; ++k, ++chunk) {
@@ -631,9 +666,9 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
             int chunk = 0, it = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < M.ntiles && ok; tile += gridDim.x) {
-                const int x0 = M.ux0 + (tile % M.ntx) * kTcM, y0 = M.uy0 + (tile / M.ntx) * PY;
-                for (int b = next_meeting<PY>(Bt, -1, x0, y0); b < Bt.count && ok;
-                     b = next_meeting<PY>(Bt, b, x0, y0), ++it) {
+                int x0, y0;
+                for (int b = tile_first<PY, PAIRS>(Bt, M, tile, x0, y0); b < Bt.count && ok;
+                     b = tile_next<PY, PAIRS>(Bt, b, x0, y0), ++it) {
                     const int a = it & 1;
                     if (it >= 2 && !tc::mbar_wait(acc_empty + a, ((it >> 1) - 1) & 1, kWaitLimit, false)) {
                         ok = false;
@@ -673,11 +708,16 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
         int it = 0;
         bool alive = true;
         for (int tile = blockIdx.x; tile < M.ntiles && alive; tile += gridDim.x) {
-            const int x0 = M.ux0 + (tile % M.ntx) * kTcM, y0 = M.uy0 + (tile / M.ntx) * PY;
-            int b = next_meeting<PY>(Bt, -1, x0, y0);
+            int x0, y0;
+            int b = tile_first<PY, PAIRS>(Bt, M, tile, x0, y0);
             if (b >= Bt.count) continue;                 // no window meets this tile
+            // the tile's canvas and the end of the pixels it may update: the group's canvas and
+            // the union of the windows, or (PAIRS) the pair's canvas and its window
+            const int bt = b;
+#define EMDQ_TGT(f) (PAIRS ? M.tgt[bt].f : M.f)
+#define EMDQ_YE (PAIRS ? Bt.p[bt].gy0 + Bt.p[bt].gh : M.uy0 + M.uh)
             const int x = x0 + q * 32 + lane;
-            const bool col_in = x < M.ux0 + M.uw;
+            const bool col_in = x < (PAIRS ? Bt.p[bt].gx0 + Bt.p[bt].gw : M.ux0 + M.uw);
             const float px = static_cast<float>(x);
             uchar4 cv[kMyGroups][8];
 #pragma unroll
@@ -686,11 +726,12 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int y = y0 + g * 8 + j;
-                    if (g < kAllGroups && col_in && y < M.uy0 + M.uh)
-                        cv[gi][j] = M.canvas[(size_t)(y + M.oy) * M.cpitch4 + (x + M.ox)];
+                    if (g < kAllGroups && col_in && y < EMDQ_YE)
+                        cv[gi][j] = EMDQ_TGT(canvas)[(size_t)(y + EMDQ_TGT(oy)) * EMDQ_TGT(cpitch4) +
+                                                     (x + EMDQ_TGT(ox))];
                 }
             }
-            for (; b < Bt.count; b = next_meeting<PY>(Bt, b, x0, y0), ++it) {
+            for (; b < Bt.count; b = tile_next<PY, PAIRS>(Bt, b, x0, y0), ++it) {
                 const int a = it & 1;
                 const bool ok = tc::mbar_wait(acc_full + a, (it >> 1) & 1, kWaitLimit, true);
                 tc::fence_after_sync();
@@ -746,9 +787,9 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
                             const int y = y0 + g * 8 + h + j;
-                            Tap t = tap_setup<CH>(M.fw, M.fh, M.pitch, px, static_cast<float>(y),
-                                                  dx[j], dy[j]);
-                            t.ok = t.ok && col_in && y < M.uy0 + M.uh;
+                            Tap t = tap_setup<CH>(EMDQ_TGT(fw), EMDQ_TGT(fh), EMDQ_TGT(pitch), px,
+                                                  static_cast<float>(y), dx[j], dy[j]);
+                            t.ok = t.ok && col_in && y < EMDQ_YE;
                             float v[CH];
                             if (t.ok) tap_sample<CH>(frame, t, v);
                             if (t.ok)
@@ -764,12 +805,15 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int y = y0 + g * 8 + j;
-                    if (g < kAllGroups && col_in && y < M.uy0 + M.uh)
-                        M.canvas[(size_t)(y + M.oy) * M.cpitch4 + (x + M.ox)] = cv[gi][j];
+                    if (g < kAllGroups && col_in && y < EMDQ_YE)
+                        EMDQ_TGT(canvas)[(size_t)(y + EMDQ_TGT(oy)) * EMDQ_TGT(cpitch4) +
+                                         (x + EMDQ_TGT(ox))] = cv[gi][j];
                 }
             }
         }
     }
+#undef EMDQ_TGT
+#undef EMDQ_YE
     __syncwarp();
     tc::fence_before_sync();
     __syncthreads();
@@ -943,7 +987,7 @@ emdq_status tc_run(TcBatch &Bt, int py, cudaStream_t st)
     return e == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }
 
-template <int CH, int PY>
+template <int CH, int PY, bool PAIRS = false>
 cudaError_t mosaic_launch(cudaLaunchConfig_t &cfg, const TcBatch &Bt, const MosaicBatch &M)
 {
     static std::mutex mu;
@@ -951,7 +995,7 @@ cudaError_t mosaic_launch(cudaLaunchConfig_t &cfg, const TcBatch &Bt, const Mosa
     {
         std::lock_guard<std::mutex> lk(mu);
         if (attr_dev != device_info().device) {
-            const cudaError_t e = cudaFuncSetAttribute(mosaic_tc_kernel<CH, PY>,
+            const cudaError_t e = cudaFuncSetAttribute(mosaic_tc_kernel<CH, PY, PAIRS>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                        (int)TcShape<PY>::SmemBytes);
             if (e != cudaSuccess) return e;
@@ -959,7 +1003,7 @@ cudaError_t mosaic_launch(cudaLaunchConfig_t &cfg, const TcBatch &Bt, const Mosa
         }
     }
     cfg.dynamicSmemBytes = TcShape<PY>::SmemBytes;
-    return cudaLaunchKernelEx(&cfg, mosaic_tc_kernel<CH, PY>, Bt, M);
+    return cudaLaunchKernelEx(&cfg, mosaic_tc_kernel<CH, PY, PAIRS>, Bt, M);
 }
 
 template <int CH>
@@ -975,10 +1019,13 @@ cudaError_t mosaic_dispatch(int py, cudaLaunchConfig_t &cfg, const TcBatch &Bt, 
 
 // The prep launch and the fused launch of a group of frames whose problems were filled for
 // tiles of py rows; M carries the frames, the canvas and the origin, and gets the union.
-emdq_status mosaic_run(TcBatch &Bt, MosaicBatch &M, int channels, int py, cudaStream_t st)
+// pairs: independent pairs (every problem's canvas and frame geometry in M.tgt, the tiles
+// those of each problem's window; tiles of kMosPYDefault rows only).
+emdq_status mosaic_run(TcBatch &Bt, MosaicBatch &M, int channels, int py, cudaStream_t st,
+                       bool pairs = false)
 {
     long long ux0 = 0, uy0 = 0, ux1 = 0, uy1 = 0;
-    for (int b = 0; b < Bt.count; ++b) {
+    for (int b = 0; b < (pairs ? 0 : Bt.count); ++b) {
         const TcProblem &P = Bt.p[b];
         const long long x0 = P.gx0, y0 = P.gy0, x1 = x0 + P.gw, y1 = y0 + P.gh;
         ux0 = (b == 0 || x0 < ux0) ? x0 : ux0;
@@ -997,13 +1044,19 @@ emdq_status mosaic_run(TcBatch &Bt, MosaicBatch &M, int channels, int py, cudaSt
     M.ntiles = (int)(ntx * nty);
     const TcProblem &last = Bt.p[Bt.count - 1];
     Bt.total_tiles = last.tile0 + last.ntiles;
+    if (pairs) {
+        if (py != kMosPYDefault) return EMDQ_ENOTSUP;
+        M.ntiles = Bt.total_tiles;
+    }
     field_tc_prep_kernel<<<last.block0 + last.nblocks, kPrepThreads, 0, st>>>(Bt);
     if (cudaGetLastError() != cudaSuccess) return EMDQ_ECUDA;
     const DeviceInfo &D = device_info();
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = pdl_config(M.ntiles < D.sms ? M.ntiles : D.sms, kMosThreads, st, at);
-    const cudaError_t e = channels == 3 ? mosaic_dispatch<3>(py, cfg, Bt, M)
-                                        : mosaic_dispatch<1>(py, cfg, Bt, M);
+    const cudaError_t e =
+        pairs ? (channels == 3 ? mosaic_launch<3, kMosPYDefault, true>(cfg, Bt, M)
+                               : mosaic_launch<1, kMosPYDefault, true>(cfg, Bt, M))
+              : (channels == 3 ? mosaic_dispatch<3>(py, cfg, Bt, M) : mosaic_dispatch<1>(py, cfg, Bt, M));
     return e == cudaSuccess ? EMDQ_OK : EMDQ_ECUDA;
 }
 
@@ -1295,4 +1348,94 @@ extern "C" emdq_status emdq_mosaic_batch(const emdq_mosaic_problem *problems, in
     return emdq_mosaic_batch_ex(problems, count, fw, fh, channels, frame_pitch, canvas, canvas_w,
                                 canvas_h, canvas_pitch, origin_x, origin_y, kMosPYDefault, workspace,
                                 workspace_bytes, stream);
+}
+
+// ------------------------------------------------------------------ emdq_mosaic_pairs
+namespace {
+
+// The bytes of canvas rows a pair may update: from its window's first pixel to its last.
+void pair_span(const emdq_mosaic_pair &f, uintptr_t &lo, uintptr_t &hi)
+{
+    const uintptr_t base = reinterpret_cast<uintptr_t>(f.canvas);
+    lo = base + (uintptr_t)((long long)(f.grid_y0 + f.origin_y) * f.canvas_pitch +
+                            4LL * (f.grid_x0 + f.origin_x));
+    hi = base + (uintptr_t)((long long)(f.grid_y0 + f.origin_y + f.grid_h - 1) * f.canvas_pitch +
+                            4LL * (f.grid_x0 + f.origin_x + f.grid_w));
+}
+
+}  // namespace
+
+extern "C" size_t emdq_mosaic_pairs_workspace_size(const emdq_mosaic_pair *pairs, int count)
+{
+    if (!pairs || count < 1 || count > kFieldBatchMax) return 0;
+    size_t total = 1024;
+    for (int b = 0; b < count; ++b) {
+        if (pairs[b].n < 1 || pairs[b].grid_w < 0 || pairs[b].grid_h < 0) return 0;
+        total += batch_problem_bytes(pairs[b].n, pairs[b].grid_w, pairs[b].grid_h);
+    }
+    return total;
+}
+
+extern "C" emdq_status emdq_mosaic_pairs(const emdq_mosaic_pair *pairs, int count, int channels,
+                                         void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!pairs || count < 1 || (channels != 1 && channels != 3)) return EMDQ_EINVAL;
+    if (count > kFieldBatchMax) return EMDQ_ENOTSUP;
+    for (int b = 0; b < count; ++b) {
+        const emdq_mosaic_pair &f = pairs[b];
+        if (!f.q || !f.c || !f.src || !f.frame || !f.canvas || f.n < 1 || f.grid_w < 1 ||
+            f.grid_h < 1 || !(f.alpha > 0.f) || !std::isfinite(f.alpha) || f.fw < 1 || f.fh < 1 ||
+            f.frame_pitch < f.fw * channels || f.canvas_w < 1 || f.canvas_h < 1 ||
+            f.canvas_pitch < 4 * f.canvas_w || f.canvas_pitch % 4 != 0)
+            return EMDQ_EINVAL;
+        if (!aligned(f.q, 16) || !aligned(f.c, 4) || !aligned(f.src, 8) || !aligned(f.canvas, 4))
+            return EMDQ_EINVAL;
+        if ((long long)f.grid_x0 + f.origin_x < 0 || (long long)f.grid_y0 + f.origin_y < 0 ||
+            (long long)f.grid_x0 + f.origin_x + f.grid_w > f.canvas_w ||
+            (long long)f.grid_y0 + f.origin_y + f.grid_h > f.canvas_h)
+            return EMDQ_EINVAL;
+        if ((long long)f.fh * f.frame_pitch > 0x7fffffffLL) return EMDQ_ENOTSUP;   // 32-bit tap offsets
+    }
+    // the tiles of different pairs run in no fixed order: no two pairs may update the same
+    // canvas bytes (checked on the spans of canvas rows their windows cover)
+    for (int a = 0; a < count; ++a) {
+        uintptr_t alo, ahi;
+        pair_span(pairs[a], alo, ahi);
+        for (int b = a + 1; b < count; ++b) {
+            uintptr_t blo, bhi;
+            pair_span(pairs[b], blo, bhi);
+            if (alo < bhi && blo < ahi) return EMDQ_EINVAL;
+        }
+    }
+    const size_t need = emdq_mosaic_pairs_workspace_size(pairs, count);
+    if (need == 0) return EMDQ_EINVAL;
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return EMDQ_EWORKSPACE;
+    if (device_info().device < 0) return EMDQ_ECUDA;
+    if (!tc_device_ok()) return EMDQ_ENOTSUP;
+    static thread_local TcBatch Bt;
+    static thread_local MosaicBatch M;
+    char *ws = static_cast<char *>(workspace);
+    Bt.count = count;
+    Bt.err = reinterpret_cast<int *>(ws);
+    size_t off = 1024;
+    for (int b = 0; b < count; ++b) {
+        const emdq_mosaic_pair &f = pairs[b];
+        float *ref = reinterpret_cast<float *>(ws + off);
+        int *kcount = reinterpret_cast<int *>(ws + off + 64);
+        const emdq_status rc = tc_problem(Bt, b, f.q, f.c, f.src, f.n, f.grid_x0, f.grid_y0,
+                                          f.grid_w, f.grid_h, f.alpha, ref, kcount, nullptr,
+                                          ws + off + 1024, kMosPYDefault);
+        if (rc != EMDQ_OK) return rc;
+        M.frame[b] = f.frame;
+        MosaicTarget &T = M.tgt[b];
+        T.canvas = reinterpret_cast<uchar4 *>(f.canvas);
+        T.cpitch4 = f.canvas_pitch / 4;
+        T.ox = f.origin_x;
+        T.oy = f.origin_y;
+        T.fw = f.fw;
+        T.fh = f.fh;
+        T.pitch = f.frame_pitch;
+        off += batch_problem_bytes(f.n, f.grid_w, f.grid_h);
+    }
+    return mosaic_run(Bt, M, channels, kMosPYDefault, static_cast<cudaStream_t>(stream), true);
 }

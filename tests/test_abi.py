@@ -181,6 +181,55 @@ def test_mosaic_batch_argument_errors_on_the_host(libemdq):
     assert L.emdq_mosaic_batch(*args(group(2), 2), ctypes.c_void_p(fake + 16), size, None) == 6
 
 
+def test_mosaic_pairs_argument_errors_on_the_host(libemdq):
+    """emdq_mosaic_pairs rejects bad pair lists before any CUDA call: no pairs, channels other
+    than 1 or 3, a bad frame or canvas description or a window outside its canvas (EMDQ_EINVAL
+    = 1), two pairs whose windows cover overlapping canvas rows (1, whether they share the
+    canvas pointer or not), more than 16 pairs or a frame of 2^31 bytes or more (EMDQ_ENOTSUP =
+    7), and a workspace smaller than its size query or not 256-byte aligned (EMDQ_EWORKSPACE =
+    6).  Pairs on disjoint canvases pass the checks."""
+    import paper_2103_07414_gb300 as pkg
+    L = pkg.lib()
+    fake = 1 << 20                            # aligned and never dereferenced
+    def pairs(specs):
+        arr = (pkg._MosaicPair * len(specs))()
+        for b, sp in enumerate(specs):
+            d = dict(grid=(0, 0, 64, 48), canvas=fake + b * (1 << 24), cw=1000, ch=800, pitch=4000,
+                     origin=(10, 10), fw=640, fh=480, fpitch=1920, n=100)
+            d.update(sp)
+            arr[b] = pkg._MosaicPair(fake, fake, fake, d['n'], *d['grid'], 1e-3, fake, d['fw'], d['fh'],
+                                     d['fpitch'], d['canvas'], d['cw'], d['ch'], d['pitch'], *d['origin'])
+        return ctypes.cast(arr, ctypes.c_void_p), len(specs)
+    ws = ctypes.c_void_p(1 << 40)
+    two = pairs([{}, {}])
+    size = L.emdq_mosaic_pairs_workspace_size(*two)
+    assert size > 1024
+    assert L.emdq_mosaic_pairs_workspace_size(*pairs([{}] * 17)) == 0
+    assert L.emdq_mosaic_pairs(None, 1, 3, ws, size, None) == 1
+    assert L.emdq_mosaic_pairs(two[0], 0, 3, ws, size, None) == 1
+    assert L.emdq_mosaic_pairs(*two, 2, ws, size, None) == 1
+    assert L.emdq_mosaic_pairs(*pairs([{}, {'fpitch': 1000}]), 3, ws, size, None) == 1
+    assert L.emdq_mosaic_pairs(*pairs([{}, {'pitch': 3999}]), 3, ws, size, None) == 1
+    assert L.emdq_mosaic_pairs(*pairs([{}, {'grid': (985, 0, 10, 10)}]), 3, ws, size, None) == 1
+    assert L.emdq_mosaic_pairs(*pairs([{}, {'grid': (0, 0, 0, 48)}]), 3, ws, size, None) == 1
+    # the same canvas: overlapping windows, and windows side by side in the same rows
+    assert L.emdq_mosaic_pairs(*pairs([{'canvas': fake}, {'canvas': fake, 'grid': (30, 20, 64, 48)}]),
+                               3, ws, size, None) == 1
+    assert L.emdq_mosaic_pairs(*pairs([{'canvas': fake}, {'canvas': fake, 'grid': (200, 0, 64, 48)}]),
+                               3, ws, size, None) == 1
+    # a second canvas view that starts inside the first one's rows
+    assert L.emdq_mosaic_pairs(*pairs([{'canvas': fake}, {'canvas': fake + 4000 * 20}]), 3, ws, size,
+                               None) == 1
+    assert L.emdq_mosaic_pairs(*pairs([{}] * 17), 3, ws, size, None) == 7
+    assert L.emdq_mosaic_pairs(*pairs([{}, {'fh': 1024, 'fpitch': 1 << 21}]), 3, ws, size, None) == 7
+    assert L.emdq_mosaic_pairs(*two, 3, ws, size - 1, None) == 6
+    assert L.emdq_mosaic_pairs(*two, 3, ctypes.c_void_p((1 << 40) + 16), size, None) == 6
+    # the same canvas, windows in disjoint rows: accepted by the checks (the workspace is then
+    # refused, so that nothing is launched)
+    assert L.emdq_mosaic_pairs(*pairs([{'canvas': fake}, {'canvas': fake, 'grid': (0, 100, 64, 48)}]),
+                               3, ws, size - 1, None) == 6
+
+
 def test_fit_batch_phases_argument_errors_on_the_host(libemdq):
     """emdq_fit_batch_phases rejects, before any CUDA call (EMDQ_EINVAL = 1): no phases, more
     than 16, counts that do not increase or are below 1, and a problem without p_out (a later
