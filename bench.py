@@ -45,11 +45,11 @@ NCU_TRAFFIC = {
     'field': dict(bytes=20752693, file='field_tc.cu', src='59fcdfa971cfd282'),
     # emdq_mosaic_batch on the 1280x1024 sequence (calls of 13, 13, 13 and 11 frames per
     # 50-frame batch, tiles of 40 pixel rows): per 13-frame call field_tc_prep_kernel about 0.5 MB
-    # read + 90 MB written (operands) and mosaic_tc_kernel about 265 MB read (operands of 13
-    # frames, more than L2 holds, frames, canvas) + 67 MB written (the operands' remaining
+    # read + 89 MB written (operands) and mosaic_tc_kernel about 253 MB read (operands of 13
+    # frames, more than L2 holds, frames, canvas) + 68 MB written (the operands' remaining
     # write-back, the canvas); the 16 launches of the timed pass over its 100 frames, per frame
     # (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --cache-control none)
-    'mosaic': dict(bytes=32413737, file='field_tc.cu', src='00555e07a3b63180'),
+    'mosaic': dict(bytes=31878994, file='field_tc.cu', src='6e5c9557977e6bd1'),
 }
 
 
