@@ -461,7 +461,8 @@ __device__ void residual_rows(const FitArgs &A, const FitSmem &S, const int *row
         emax = fmaxf(emax, fmaf(e.x, e.x, e.y * e.y));
         e2[r] = make_float2(2.f * e.x, 2.f * e.y);
     }
-    const bool expand = emax <= kExpandMax;
+    // (a group of one row gains nothing: its origin is the row itself, e = 0)
+    const bool expand = R >= 2 && emax <= kExpandMax;
     if (expand) {
 #pragma unroll 2
         for (int i = lane; i < n; i += 32) {
@@ -800,11 +801,14 @@ __device__ __forceinline__ void fit_body(const FitArgs &A, int rank, int ncta, c
         ResSums keep;
         keep.j = -1;
         int slot = 0;
-        // groups of 4 consecutive positions of the Hilbert order (every CTA's M-step positions
+        // groups of R consecutive positions of the Hilbert order (every CTA's M-step positions
         // are written before the barrier that precedes this pass), dealt to the warps of the
-        // whole group of CTAs in turn; the last group holds the 1-3 positions left
-        for (int t = 4 * gwarp; t < n; t += 4 * nwarps) {
-            const int left = n - t;
+        // whole group of CTAs in turn, R = 4 unless there are fewer than 4 rows per warp (then
+        // as many as the warps have on average, at least one: every warp gets work); the last
+        // group holds the positions left
+        const int R = min(4, max(1, n / nwarps));
+        for (int t = R * gwarp; t < n; t += R * nwarps) {
+            const int left = min(R, n - t);
             if (left >= 4) {
                 const int rows[4] = {__ldcg(A.ord + t), __ldcg(A.ord + t + 1), __ldcg(A.ord + t + 2),
                                      __ldcg(A.ord + t + 3)};
