@@ -571,6 +571,15 @@ __device__ __forceinline__ int tile_next(const TcBatch &Bt, int b, int x0, int y
     return PAIRS ? Bt.count : next_meeting<PY>(Bt, b, x0, y0);
 }
 
+// The tile of round r for this CTA.  The rounds alternate direction (CTA c takes tile r G + c
+// in even rounds, r G + G - 1 - c in odd ones), so that the CTAs that get a tile in a partial
+// last round are those that got the last tiles of the round before -- the tiles of a window's
+// ragged last rows, whose epilogue is short -- and not those that got full tiles twice.
+__device__ __forceinline__ int round_tile(int r)
+{
+    return r * (int)gridDim.x + ((r & 1) ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x);
+}
+
 // Items: (tile, frame) pairs, tiles of the union in this CTA's turn, the frames meeting each
 // in order (PAIRS: a problem's tile and its own frame).  The TMA and MMA warps run them as field_tc_kernel runs tiles (the operand rows
 // of the tile's pixels in that frame's operands; outside its padded window TMA fills zeros,
@@ -638,7 +647,7 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
     if (warp == 0) {
         if (lane == 0) {
             int chunk = 0;
-            for (int tile = blockIdx.x; tile < M.ntiles && !*abort_flag; tile += gridDim.x) {
+            for (int r = 0, tile = round_tile(0); tile < M.ntiles && !*abort_flag; tile = round_tile(++r)) {
                 int x0, y0;
                 for (int b = tile_first<PY, PAIRS>(Bt, M, tile, x0, y0); b < Bt.count && !*abort_flag;
                      b = tile_next<PY, PAIRS>(Bt, b, x0, y0)) {
@@ -665,7 +674,7 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
             // item it into accumulator it & 1
             int chunk = 0, it = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < M.ntiles && ok; tile += gridDim.x) {
+            for (int r = 0, tile = round_tile(0); tile < M.ntiles && ok; tile = round_tile(++r)) {
                 int x0, y0;
                 for (int b = tile_first<PY, PAIRS>(Bt, M, tile, x0, y0); b < Bt.count && ok;
                      b = tile_next<PY, PAIRS>(Bt, b, x0, y0), ++it) {
@@ -707,7 +716,7 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
         const int g_last = idle ? 0 : set + (kAllGroups - 1 - set) / kSets * kSets;
         int it = 0;
         bool alive = true;
-        for (int tile = blockIdx.x; tile < M.ntiles && alive; tile += gridDim.x) {
+        for (int r = 0, tile = round_tile(0); tile < M.ntiles && alive; tile = round_tile(++r)) {
             int x0, y0;
             int b = tile_first<PY, PAIRS>(Bt, M, tile, x0, y0);
             if (b >= Bt.count) continue;                 // no window meets this tile
