@@ -45,11 +45,11 @@ NCU_TRAFFIC = {
     'field': dict(bytes=20752693, file='field_tc.cu', src='59fcdfa971cfd282'),
     # emdq_mosaic_batch on the 1280x1024 sequence (calls of 13, 13, 13 and 11 frames per
     # 50-frame batch, tiles of 40 pixel rows): per 13-frame call field_tc_prep_kernel about 0.5 MB
-    # read + 89 MB written (operands) and mosaic_tc_kernel about 253 MB read (operands of 13
+    # read + 89 MB written (operands) and mosaic_tc_kernel about 256 MB read (operands of 13
     # frames, more than L2 holds, frames, canvas) + 68 MB written (the operands' remaining
     # write-back, the canvas); the 16 launches of the timed pass over its 100 frames, per frame
     # (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --cache-control none)
-    'mosaic': dict(bytes=31878994, file='field_tc.cu', src='6e5c9557977e6bd1'),
+    'mosaic': dict(bytes=32097587, file='field_tc.cu', src='8bf3f74fdf896e02'),
 }
 
 
@@ -583,6 +583,8 @@ def run_gpu(args, ws, rank, local):
             done.record(fit_stream)
         return done
 
+    group_wait = [None]     # (batch, group) -> makes the main stream wait for the group's frames
+
     def blend_batch(bi, ks, fr_of, s_of, fit_done, ev=None):
         """Field + warp of batch bi in frame order on the main stream, after its fits."""
         stream.wait_event(fit_done)
@@ -590,12 +592,16 @@ def run_gpu(args, ws, rank, local):
         if ev: ev[3].record(stream)
         if piped:
             for j0 in range(0, len(ks), G):
+                if group_wait[0] is not None:
+                    group_wait[0](bi, j0 // G)
                 sub = list(range(j0, min(len(ks), j0 + G)))
                 fields_then_warps([fr_of(ks[j]) for j in sub], [s_of(ks[j]) for j in sub],
                                   [grids[ks[j]] for j in sub], [outs[j] for j in sub],
                                   [ev[4 + 3 * j: 7 + 3 * j] for j in sub] if ev else None)
         else:
             for j, k in enumerate(ks):
+                if group_wait[0] is not None:
+                    group_wait[0](bi, j // G)
                 field_and_warp(fr_of(k), s_of(k), grids[k], outs[j],
                                ev[4 + 3 * j: 7 + 3 * j] if ev else None)
         if warp_stream is not None:
@@ -892,12 +898,12 @@ def run_gpu(args, ws, rank, local):
                                   ms_per_call=float(np.median(a_ms)))
 
     # end to end through the public API from pinned host buffers: every frame and its
-    # matches in pinned host memory; per batch one H2D copy of its frames and one of each
-    # match array (split where the host rows wrap) on a copy stream, into two device slots
-    # used alternately, so a batch's copies run beside the previous batch's compute; a
-    # batch's fits wait for its matches only, its blend for its frames; after its blend the
-    # D2H of its fit records and weights, and the copies of the batch two ahead into the
-    # freed slot
+    # matches in pinned host memory; per batch one H2D copy of each match array and one of
+    # the frames of each field group (split where the host rows wrap) on a copy stream, into
+    # two device slots used alternately, so a batch's copies run beside the previous batch's
+    # compute; a batch's fits wait for its matches only, each group's fused call for that
+    # group's frames; after its blend the D2H of its fit records and weights, and the copies
+    # of the batch two ahead into the freed slot
     e2e = None
     if not args.no_e2e:
         nh = min(n_frames, 100)
@@ -928,10 +934,12 @@ def run_gpu(args, ws, rank, local):
                         dD[sl][j0:j0 + cnt].copy_(hD[h0:h0 + cnt], non_blocking=True)
                     m_ev[i] = torch.cuda.Event()
                     m_ev[i].record(cstream)
-                    for j0, h0, cnt in contiguous_runs(batches[i], nh):
-                        dF[sl][j0:j0 + cnt].copy_(hF[h0:h0 + cnt], non_blocking=True)
-                    f_ev[i] = torch.cuda.Event()
-                    f_ev[i].record(cstream)
+                    ks = batches[i]
+                    for g0 in range(0, len(ks), G):
+                        for j0, h0, cnt in contiguous_runs(ks[g0:g0 + G], nh):
+                            dF[sl][g0 + j0:g0 + j0 + cnt].copy_(hF[h0:h0 + cnt], non_blocking=True)
+                        f_ev[(i, g0 // G)] = torch.cuda.Event()
+                        f_ev[(i, g0 // G)].record(cstream)
 
             def post(i):
                 k0, cnt = batches[i][0], len(batches[i])
@@ -946,10 +954,13 @@ def run_gpu(args, ws, rank, local):
             for i in range(min(2, len(batches))):
                 copy_in(i)
             fit_stream.wait_stream(stream)
-            run_batches(batches, lambda k: dF[pos[k][0]][pos[k][1]], lambda k: dS[pos[k][0]][pos[k][1]],
-                        lambda k: dD[pos[k][0]][pos[k][1]],
-                        ready=lambda i, st: st.wait_event(m_ev[i]),
-                        pre_blend=lambda i: stream.wait_event(f_ev[i]), post_blend=post)
+            group_wait[0] = lambda i, g: stream.wait_event(f_ev[(i, g)])
+            try:
+                run_batches(batches, lambda k: dF[pos[k][0]][pos[k][1]], lambda k: dS[pos[k][0]][pos[k][1]],
+                            lambda k: dD[pos[k][0]][pos[k][1]],
+                            ready=lambda i, st: st.wait_event(m_ev[i]), post_blend=post)
+            finally:
+                group_wait[0] = None
             stream.wait_stream(cstream)
 
         # the step (copies in, calls, copies out) captured once into a CUDA graph like the
