@@ -612,10 +612,10 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
     int *issued = const_cast<int *>(abort_flag + 1);
     int *consumed = issued + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // RN(1 / (w + 1)) for the canvas weights w = 0..30 (the blend's divisor), one shared load per
-    // pixel instead of a reciprocal sequence
-    __shared__ float rw1_of[32];
-    if (threadIdx.x < 32) rw1_of[threadIdx.x] = __frcp_rn(static_cast<float>(threadIdx.x) + 1.f);
+    // RN(1 / (w + 1)) for every canvas weight byte w (the blend's divisor; the blend keeps w <= 30,
+    // the table covers any byte), one shared load per pixel instead of a reciprocal sequence
+    __shared__ float rw1_of[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) rw1_of[i] = __frcp_rn(static_cast<float>(i) + 1.f);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTcStages; ++s) {
@@ -735,6 +735,7 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int y = y0 + g * 8 + j;
+                    cv[gi][j] = make_uchar4(0, 0, 0, 0);       // pixels outside: never written
                     if (g < kAllGroups && col_in && y < EMDQ_YE)
                         cv[gi][j] = EMDQ_TGT(canvas)[(size_t)(y + EMDQ_TGT(oy)) * EMDQ_TGT(cpitch4) +
                                                      (x + EMDQ_TGT(ox))];
@@ -777,6 +778,7 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
                             __syncwarp();
                             if (lane == 0) tc::mbar_arrive(acc_empty + a);
                         }
+                        if (y0 + g * 8 + h >= EMDQ_YE) continue;     // no row of these four is inside
                         // the four displacements first (the channels' registers free
                         // before the taps), then each pixel's sample and update
                         float dx[4], dy[4];
@@ -799,10 +801,13 @@ __global__ void __launch_bounds__(kMosThreads, 1) mosaic_tc_kernel(const __grid_
                             Tap t = tap_setup<CH>(EMDQ_TGT(fw), EMDQ_TGT(fh), EMDQ_TGT(pitch), px,
                                                   static_cast<float>(y), dx[j], dy[j]);
                             t.ok = t.ok && col_in && y < EMDQ_YE;
+                            // sampled and blended without a branch, the update kept where the sample
+                            // is valid (an invalid tap set-up points at the frame's first pixel with
+                            // zero weights, so every load stays inside the frame)
                             float v[CH];
-                            if (t.ok) tap_sample<CH>(frame, t, v);
-                            if (t.ok)
-                                cv[gi][h + j] = blend_update_r<CH>(cv[gi][h + j], v, rw1_of[cv[gi][h + j].w]);
+                            tap_sample<CH>(frame, t, v);
+                            const uchar4 nv = blend_update_r<CH>(cv[gi][h + j], v, rw1_of[cv[gi][h + j].w]);
+                            if (t.ok) cv[gi][h + j] = nv;
                         }
                     }
                 }
